@@ -1,0 +1,430 @@
+"""FP64 CPU oracle of the QuasiGrad penalized objective and its gradient.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this module; the library's product path never does.
+It shares no code with the CUDA path (different layout, different loop order:
+contingencies are evaluated per outage in angle space exactly as Sec. II-E
+describes, not through a flow-space LODF block).
+
+What it computes (plain definitions, numpy FP64):
+
+* AC branch flows of the pi model (Sec. II-F line-flow example fixes the sign
+  convention: d p_fr / d v_to = (-g cos(delta) - b sin(delta)) v_fr / tau), with
+  tau = 1, phi = 0 and no per-end shunt conductance/susceptance.
+* Bus P/Q mismatch (Example 4, consumption positive) and the soft-abs balance
+  penalty (Sec. II-C footnote; scaled by beta as in the homotopy paragraph of
+  Sec. II-F).
+* Thermal penalty on the worse branch end (Example 1) with the soft-ReLU.
+* Generator cost, reserve cost, zonal reserve shortfall, headroom and ramp
+  penalties (the penalized linear constraints rho*sigma_s(Ax) of Eq. nlp_updated,
+  applied to violations).
+* Contingency DC flows (Sec. II-E): base solve of the reduced Laplacian with
+  uniform slack, SMW rank-1 correction per outage (Eq. rank_correct), the
+  directional overload penalty (Eqs. sfr_pen-zctg), the adjoint solve
+  (Eq. 2nd_lin_sys) and the slack correction (Eq. correction).
+  ``mode="brute"`` instead deletes the outaged branch and re-solves the
+  contingency Laplacian directly.
+
+Readings taken where the paper is silent or ambiguous are listed in the
+design notes; the ones that change arithmetic are repeated at their use below.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+
+
+# ------------------------------------------------------------------------------------------
+# smooth penalties (Sec. II-C footnote)
+# ------------------------------------------------------------------------------------------
+
+def soft_abs(x, eps):
+    """|x|_s = sqrt(x^2 + eps^2)."""
+    return np.sqrt(x * x + eps * eps)
+
+
+def soft_abs_grad(x, eps):
+    s = np.sqrt(x * x + eps * eps)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(s > 0, x / np.where(s > 0, s, 1.0), 0.0)
+
+
+def soft_relu(x, eps):
+    """sigma_s(x) = sqrt(max(x, 0)^2 + eps^2)."""
+    m = np.maximum(x, 0.0)
+    return np.sqrt(m * m + eps * eps)
+
+
+def soft_relu_grad(x, eps):
+    m = np.maximum(x, 0.0)
+    s = np.sqrt(m * m + eps * eps)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(s > 0, m / np.where(s > 0, s, 1.0), 0.0)
+
+
+# ------------------------------------------------------------------------------------------
+# variable layout
+# ------------------------------------------------------------------------------------------
+
+def unpack(case, x):
+    """x = [v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G)], period-major rows."""
+    T, n, G = case.T, case.n_bus, case.n_gen
+    x = np.asarray(x, dtype=np.float64)
+    o = 0
+    v = x[o:o + T * n].reshape(T, n); o += T * n
+    th = x[o:o + T * n].reshape(T, n); o += T * n
+    p = x[o:o + T * G].reshape(T, G); o += T * G
+    q = x[o:o + T * G].reshape(T, G); o += T * G
+    r = x[o:o + T * G].reshape(T, G)
+    return v, th, p, q, r
+
+
+def pack(v, th, p, q, r):
+    return np.concatenate([np.ravel(v), np.ravel(th), np.ravel(p), np.ravel(q), np.ravel(r)])
+
+
+def box(case):
+    """Clip box B of Alg. 3 (clip step): v in [vmin, vmax], theta_ref = 0, other theta free,
+    p in [pmin, pmax], q in [qmin, qmax], r in [0, pmax]."""
+    T, n = case.T, case.n_bus
+    lo_th = np.full((T, n), -np.inf)
+    hi_th = np.full((T, n), np.inf)
+    lo_th[:, case.ref_bus] = 0.0
+    hi_th[:, case.ref_bus] = 0.0
+    lo = pack(np.tile(case.vmin, (T, 1)), lo_th, np.tile(case.pmin, (T, 1)), np.tile(case.qmin, (T, 1)),
+              np.zeros((T, case.n_gen)))
+    hi = pack(np.tile(case.vmax, (T, 1)), hi_th, np.tile(case.pmax, (T, 1)), np.tile(case.qmax, (T, 1)),
+              np.tile(case.pmax, (T, 1)))
+    return lo, hi
+
+
+# ------------------------------------------------------------------------------------------
+# AC network (pi model)
+# ------------------------------------------------------------------------------------------
+
+def series_admittance(case):
+    """g_sr + j b_sr = 1 / (r + j x)."""
+    den = case.br_r ** 2 + case.br_x ** 2
+    return case.br_r / den, -case.br_x / den
+
+
+def ac_flows(case, v, th):
+    """Pi-model flows at both ends of every branch, shape (T, M) each.
+
+    p_fr = g v_f^2 + (-g cos d - b sin d) v_f v_o
+    q_fr = -(b + b_ch/2) v_f^2 + (b cos d - g sin d) v_f v_o
+    p_to = g v_o^2 + (-g cos d + b sin d) v_f v_o
+    q_to = -(b + b_ch/2) v_o^2 + (b cos d + g sin d) v_f v_o,   d = theta_f - theta_o.
+    """
+    g, b = series_admittance(case)
+    bch = case.br_b
+    f, o = case.br_from, case.br_to
+    vf, vo = v[:, f], v[:, o]
+    d = th[:, f] - th[:, o]
+    c, s = np.cos(d), np.sin(d)
+    vv = vf * vo
+    pf = g * vf ** 2 + (-g * c - b * s) * vv
+    qf = -(b + bch / 2) * vf ** 2 + (b * c - g * s) * vv
+    pt = g * vo ** 2 + (-g * c + b * s) * vv
+    qt = -(b + bch / 2) * vo ** 2 + (b * c + g * s) * vv
+    return pf, qf, pt, qt
+
+
+def ac_flow_partials(case, v, th):
+    """Partial derivatives of (pf, qf, pt, qt) with respect to (v_f, v_o, delta)."""
+    g, b = series_admittance(case)
+    bch = case.br_b
+    f, o = case.br_from, case.br_to
+    vf, vo = v[:, f], v[:, o]
+    d = th[:, f] - th[:, o]
+    c, s = np.cos(d), np.sin(d)
+    vv = vf * vo
+    out = {
+        "pf": (2 * g * vf + (-g * c - b * s) * vo, (-g * c - b * s) * vf, (g * s - b * c) * vv),
+        "qf": (-2 * (b + bch / 2) * vf + (b * c - g * s) * vo, (b * c - g * s) * vf, (-b * s - g * c) * vv),
+        "pt": ((-g * c + b * s) * vo, 2 * g * vo + (-g * c + b * s) * vf, (g * s + b * c) * vv),
+        "qt": ((b * c + g * s) * vo, -2 * (b + bch / 2) * vo + (b * c + g * s) * vf, (-b * s + g * c) * vv),
+    }
+    return out
+
+
+def bus_mismatch(case, pf, qf, pt, qt, p, q):
+    """Example 4: P_it = sum(loads) + sum(fr flows) + sum(to flows) - sum(generators), same for Q."""
+    f, o = case.br_from, case.br_to
+    P = case.load_p.copy()
+    Q = case.load_q.copy()
+    np.add.at(P.T, f, pf.T)
+    np.add.at(P.T, o, pt.T)
+    np.add.at(Q.T, f, qf.T)
+    np.add.at(Q.T, o, qt.T)
+    np.subtract.at(P.T, case.gen_bus, p.T)
+    np.subtract.at(Q.T, case.gen_bus, q.T)
+    return P, Q
+
+
+# ------------------------------------------------------------------------------------------
+# DC network (Sec. II-E)
+# ------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class DCNet:
+    y: np.ndarray        # [M] branch susceptance -b_sr = x / (r^2 + x^2)
+    E: np.ndarray        # [M, n] signed incidence (+1 at from, -1 at to)
+    keep: np.ndarray     # [n-1] bus ids with the reference bus removed
+    Yhat: np.ndarray     # [n-1, n-1] reduced Laplacian  E_hat^T Y_x E_hat
+    Yinv: np.ndarray     # [n-1, n-1] its inverse (explicit, small cases)
+
+
+def dc_network(case) -> DCNet:
+    """Reading: Y_x holds -b_sr = x / (r^2 + x^2), consistent with p = -b_sr (theta_i - theta_i')."""
+    n, M = case.n_bus, case.n_branch
+    y = case.br_x / (case.br_r ** 2 + case.br_x ** 2)
+    E = np.zeros((M, n))
+    E[np.arange(M), case.br_from] += 1.0
+    E[np.arange(M), case.br_to] -= 1.0
+    keep = np.array([i for i in range(n) if i != case.ref_bus])
+    Eh = E[:, keep]
+    Yhat = Eh.T @ (y[:, None] * Eh)
+    return DCNet(y=y, E=E, keep=keep, Yhat=Yhat, Yinv=np.linalg.inv(Yhat))
+
+
+def dc_injections(case, p):
+    """p_inj = sum of generator output at the bus - load, then the uniform slack:
+    every bus takes 1/n of the imbalance (Sec. II-E slack paragraph)."""
+    inj = -case.load_p.copy()
+    np.add.at(inj.T, case.gen_bus, p.T)
+    pbar = inj - inj.mean(axis=1, keepdims=True)
+    return inj, pbar
+
+
+def dc_base_flows(case, net: DCNet, pbar):
+    """Eq. Yb_solve / p_flow with b_t = 0 (no phase shifters): theta_hat = Yhat^-1 pbar_hat,
+    f = Y_x E_hat theta_hat.  Returns theta (T, n) with theta_ref = 0 and f (T, M)."""
+    th_hat = np.linalg.solve(net.Yhat, pbar[:, net.keep].T).T
+    th = np.zeros_like(pbar)
+    th[:, net.keep] = th_hat
+    f = (th @ net.E.T) * net.y[None, :]
+    return th, f
+
+
+# ------------------------------------------------------------------------------------------
+# contingency penalty and its gradient (Sec. II-E, Alg. 2 with every outage and zeta = 0)
+# ------------------------------------------------------------------------------------------
+
+def _ctg_period_smw(case, net: DCNet, th_hat_b, qmax2, dt, U, den):
+    """One period, all outages, via the paper's rank-1 correction in angle space.
+
+    th_hat_b : [n-1] base-case reduced angles (Eq. Y_base).
+    U        : [n-1, K] u_k = Yhat^-1 a_k with a_k the reduced incidence row of branch k.
+    den      : [K] 1 - y_k a_k^T u_k  (the SMW denominator; reading: Yhat_k = Yhat - y_k a_k a_k^T).
+    Returns (z_tk [K], grad wrt p_inj [n] summed over k, dz/dqmax2 [M] summed over k).
+    """
+    K = case.K
+    ks = case.ctg
+    Eh = net.E[:, net.keep]
+    y = net.y
+    fk = y[ks] * (Eh[ks] @ th_hat_b)                        # base flow on each outaged branch
+    TH = th_hat_b[:, None] + U * (fk / den)[None, :]         # Eq. rank_correct, one column per k
+    P = y[:, None] * (Eh @ TH)                               # Eq. p_flow, [M, K]
+    P[ks, np.arange(K)] = 0.0                                # outaged branch carries nothing
+    s = np.sqrt(P * P + qmax2[:, None])
+    u = s - case.s_max_ctg[:, None]
+    w = dt * case.c_s * case.beta
+    pen = w * soft_relu(u, case.eps)
+    pen[ks, np.arange(K)] = 0.0                              # the outaged branch is not monitored
+    z = pen.sum(axis=0)
+    dsig = w * soft_relu_grad(u, case.eps)
+    dsig[ks, np.arange(K)] = 0.0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        inv_s = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+    D = dsig * P * inv_s                                     # d_k = dz_tk / dp_tk, column per k
+    gq2 = (dsig * 0.5 * inv_s).sum(axis=1)                   # dz / d(qmax^2), summed over k
+    # Eq. 2nd_lin_sys: eta_k = Yhat_k^-1 E_hat^T Y_x,k d_k, with Yhat_k^-1 applied by SMW
+    W = Eh.T @ (y[:, None] * D)                              # [n-1, K]
+    H = net.Yinv @ W
+    H = H + U * ((y[ks] * np.einsum("kj,jk->k", Eh[ks], H)) / den)[None, :]
+    eta = np.zeros((case.n_bus, K))
+    eta[net.keep] = H
+    gin = (eta - eta.mean(axis=0, keepdims=True)).sum(axis=1)  # Eq. correction, summed over k
+    return z, gin, gq2
+
+
+def _ctg_period_brute(case, net: DCNet, pbar_t, qmax2, dt):
+    """One period, every outage re-solved on the outaged Laplacian (no SMW)."""
+    K = case.K
+    Eh = net.E[:, net.keep]
+    y = net.y
+    n = case.n_bus
+    z = np.zeros(K)
+    gin = np.zeros(n)
+    gq2 = np.zeros(case.n_branch)
+    w = dt * case.c_s * case.beta
+    for kk, k in enumerate(case.ctg):
+        yk = y.copy()
+        yk[k] = 0.0
+        Yk = Eh.T @ (yk[:, None] * Eh)
+        thk = np.linalg.solve(Yk, pbar_t[net.keep])
+        P = yk * (Eh @ thk)
+        s = np.sqrt(P * P + qmax2)
+        u = s - case.s_max_ctg
+        pen = w * soft_relu(u, case.eps)
+        pen[k] = 0.0
+        z[kk] = pen.sum()
+        dsig = w * soft_relu_grad(u, case.eps)
+        dsig[k] = 0.0
+        inv_s = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+        d = dsig * P * inv_s
+        gq2 += dsig * 0.5 * inv_s
+        eta_h = np.linalg.solve(Yk, Eh.T @ (yk * d))
+        eta = np.zeros(n)
+        eta[net.keep] = eta_h
+        gin += eta - eta.mean()
+    return z, gin, gq2
+
+
+# ------------------------------------------------------------------------------------------
+# the full objective and gradient
+# ------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Result:
+    obj: float
+    grad: Optional[np.ndarray]
+    terms: dict
+    z_ctg: Optional[np.ndarray] = None  # [T, K]
+    g_inj: Optional[np.ndarray] = None  # [T, n] gradient of the contingency term wrt p_inj
+
+
+TERM_NAMES = ("cost", "zp", "zq", "zs", "zrz", "zhead", "zramp", "zctg")
+
+
+def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[float] = None,
+             periods: Optional[Sequence[int]] = None) -> Result:
+    """Phi(x) and its gradient.
+
+    mode: "smw" (rank-1 corrections, Eq. rank_correct) or "brute" (re-solve each outage).
+    eps : override the soft-abs / soft-ReLU epsilon (eps = 0 gives the hard abs/ReLU used
+          to score a point).
+    periods: restrict the contingency term to these periods (sampling at large sizes);
+          other terms always cover every period.
+    """
+    if eps is not None and eps != case.eps:
+        case = dataclasses.replace(case, eps=eps)
+    T, n, G = case.T, case.n_bus, case.n_gen
+    eps_ = case.eps
+    beta = case.beta
+    dt = case.dt
+    v, th, p, q, r = unpack(case, x)
+    gv = np.zeros((T, n)); gth = np.zeros((T, n)); gp = np.zeros((T, G)); gq = np.zeros((T, G))
+    gr = np.zeros((T, G))
+    terms = {k: 0.0 for k in TERM_NAMES}
+
+    # --- generator energy and reserve cost
+    terms["cost"] = float((dt[:, None] * (case.cost_a * p * p + case.cost_b * p + case.cost_r * r)).sum())
+    gp += dt[:, None] * (2 * case.cost_a * p + case.cost_b)
+    gr += dt[:, None] * case.cost_r
+
+    # --- AC flows and bus balance (Example 4)
+    pf, qf, pt, qt = ac_flows(case, v, th)
+    P, Q = bus_mismatch(case, pf, qf, pt, qt, p, q)
+    wp = dt[:, None] * case.c_p * beta
+    wq = dt[:, None] * case.c_q * beta
+    terms["zp"] = float((wp * soft_abs(P, eps_)).sum())
+    terms["zq"] = float((wq * soft_abs(Q, eps_)).sum())
+    dP = wp * soft_abs_grad(P, eps_)
+    dQ = wq * soft_abs_grad(Q, eps_)
+    f, o = case.br_from, case.br_to
+    g_pf = dP[:, f].copy()
+    g_pt = dP[:, o].copy()
+    g_qf = dQ[:, f].copy()
+    g_qt = dQ[:, o].copy()
+    gp -= dP[:, case.gen_bus]
+    gq -= dQ[:, case.gen_bus]
+
+    # --- thermal limit on the worse end (Example 1)
+    sf = np.sqrt(pf * pf + qf * qf)
+    st = np.sqrt(pt * pt + qt * qt)
+    use_fr = sf >= st                      # reading: ties go to the "fr" end
+    smax_end = np.where(use_fr, sf, st)
+    u = smax_end - case.s_max[None, :]
+    ws = dt[:, None] * case.c_s * beta
+    terms["zs"] = float((ws * soft_relu(u, eps_)).sum())
+    dS = ws * soft_relu_grad(u, eps_)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        kf = np.where(use_fr & (sf > 0), dS / np.where(sf > 0, sf, 1.0), 0.0)
+        kt = np.where(~use_fr & (st > 0), dS / np.where(st > 0, st, 1.0), 0.0)
+    g_pf += kf * pf; g_qf += kf * qf
+    g_pt += kt * pt; g_qt += kt * qt
+
+    # --- zonal reserve shortfall
+    rz = np.zeros((T, case.n_zone))
+    np.add.at(rz.T, case.gen_zone, r.T)
+    uz = case.reserve_req - rz
+    wz = dt[:, None] * case.c_rz * beta
+    terms["zrz"] = float((wz * soft_relu(uz, eps_)).sum())
+    dZ = wz * soft_relu_grad(uz, eps_)
+    gr -= dZ[:, case.gen_zone]
+
+    # --- penalized linear constraints rho * sigma_s(violation): headroom and ramps
+    wr = case.rho * beta
+    uh = p + r - case.pmax[None, :]
+    terms["zhead"] = float((wr * soft_relu(uh, eps_)).sum())
+    dH = wr * soft_relu_grad(uh, eps_)
+    gp += dH
+    gr += dH
+    if T > 1:
+        lim = case.ramp[None, :] * dt[1:, None]
+        up = p[1:] - p[:-1] - lim
+        dn = p[:-1] - p[1:] - lim
+        terms["zramp"] = float((wr * (soft_relu(up, eps_) + soft_relu(dn, eps_))).sum())
+        dU = wr * soft_relu_grad(up, eps_)
+        dD = wr * soft_relu_grad(dn, eps_)
+        gp[1:] += dU - dD
+        gp[:-1] += dD - dU
+
+    # --- contingencies (Sec. II-E)
+    net = dc_network(case)
+    _, pbar = dc_injections(case, p)
+    th_dc, fbase = dc_base_flows(case, net, pbar)
+    use_qf = qf * qf >= qt * qt           # reading: the q of the worse end, ties to "fr"
+    qmax2 = np.where(use_qf, qf * qf, qt * qt)
+    z_ctg = np.zeros((T, case.K))
+    gin_all = np.zeros((T, n))
+    gq2_all = np.zeros((T, case.n_branch))
+    if case.K > 0:
+        Eh = net.E[:, net.keep]
+        U = net.Yinv @ Eh[case.ctg].T                       # u_k, [n-1, K]
+        den = 1.0 - net.y[case.ctg] * np.einsum("kj,jk->k", Eh[case.ctg], U)
+        plist = range(T) if periods is None else periods
+        for t in plist:
+            if mode == "brute":
+                z, gin, gq2 = _ctg_period_brute(case, net, pbar[t], qmax2[t], dt[t])
+            else:
+                z, gin, gq2 = _ctg_period_smw(case, net, th_dc[t, net.keep], qmax2[t], dt[t], U, den)
+            z_ctg[t] = z
+            gin_all[t] = gin
+            gq2_all[t] = gq2
+    terms["zctg"] = float(z_ctg.sum())
+    gp += gin_all[:, case.gen_bus]
+    g_qf += np.where(use_qf, 2 * qf * gq2_all, 0.0)
+    g_qt += np.where(~use_qf, 2 * qt * gq2_all, 0.0)
+
+    # --- pull branch-end adjoints back to (v, theta) and gather per bus
+    part = ac_flow_partials(case, v, th)
+    gvf = g_pf * part["pf"][0] + g_qf * part["qf"][0] + g_pt * part["pt"][0] + g_qt * part["qt"][0]
+    gvo = g_pf * part["pf"][1] + g_qf * part["qf"][1] + g_pt * part["pt"][1] + g_qt * part["qt"][1]
+    gd = g_pf * part["pf"][2] + g_qf * part["qf"][2] + g_pt * part["pt"][2] + g_qt * part["qt"][2]
+    np.add.at(gv.T, f, gvf.T)
+    np.add.at(gv.T, o, gvo.T)
+    np.add.at(gth.T, f, gd.T)
+    np.subtract.at(gth.T, o, gd.T)
+
+    obj = float(sum(terms.values()))
+    grad = pack(gv, gth, gp, gq, gr) if want_grad else None
+    return Result(obj=obj, grad=grad, terms=terms, z_ctg=z_ctg, g_inj=gin_all)
+
+
+def objective(case, x, **kw) -> float:
+    return evaluate(case, x, want_grad=False, **kw).obj
