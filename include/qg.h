@@ -1,0 +1,168 @@
+/*
+ * qg.h -- C ABI of libqg, the GB300 (sm_103a) implementation of the QuasiGrad
+ * hot path: one full evaluation of the penalized, multi-period, security- and
+ * reserve-constrained AC unit-commitment objective and its gradient
+ * (Chevalier, "A Parallelized, Adam-Based Solver for Reserve and Security
+ * Constrained AC Unit Commitment", Sec. II), chained with the projected Adam
+ * update that consumes it (Alg. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: QG_OK (0) or a negative QG_ERR_* code; qg_last_error() gives
+ *    a one-line message for the last failing call on a handle.
+ *  - Host arrays passed to qg_create, qg_create_batch and qg_eval_grad_host are read during the
+ *    call only; the caller keeps ownership.  Device pointers (x, g, m, v, obj)
+ *    belong to the caller; the library never frees them.  Everything else the
+ *    handle allocates is freed by qg_destroy.
+ *  - Device arrays are contiguous; their element type is double in QG_FP64
+ *    mode and float in QG_MIXED mode (obj is always double).
+ *  - All device work is ordered on the stream set by qg_set_stream (default:
+ *    the legacy default stream); no call synchronizes the device except
+ *    qg_create*, qg_eval_grad_host, qg_breakdown and qg_get_state.
+ *  - Variable layout of one instance (qg_layout): five period-major blocks
+ *        x = [ v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G) ]
+ *    and batched instances are concatenated in creation order.
+ *  - Per-unit quantities, periods of dt hours.
+ */
+#ifndef QG_H
+#define QG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QG_OK 0
+#define QG_ERR_INVALID_ARG (-1)   /* a size, index, pointer or parameter is out of range      */
+#define QG_ERR_ISLANDING (-2)     /* an outage disconnects the grid (1 - PTDF_kk ~ 0)          */
+#define QG_ERR_CUDA (-3)          /* a CUDA runtime call failed (message has the CUDA error)   */
+#define QG_ERR_NOT_CONVERGED (-4) /* an iterative solve hit its iteration cap                  */
+#define QG_ERR_TIMEOUT (-5)       /* a device-side wait ran out of its cycle budget            */
+#define QG_ERR_NONFINITE (-6)     /* NaN/Inf found in x or in the objective                    */
+#define QG_ERR_NO_DEVICE (-7)     /* no CUDA device, or not an sm_103 device                   */
+#define QG_ERR_UNSUPPORTED (-8)   /* a valid request this build does not implement             */
+
+enum { QG_FP64 = 0, QG_MIXED = 1 };                              /* qg_options.precision */
+enum { QG_LODF_F32 = 0, QG_LODF_BF16 = 1, QG_LODF_BF16X2 = 2 };  /* qg_options.lodf_dtype (mixed) */
+
+typedef struct qg_ctx qg_ctx; /* opaque handle; owns all device memory it allocates */
+
+/* Network of one instance (Sec. II-B reduced to v, theta, p, q, r; integers
+ * relaxed and fixed on; no transformers: tau = 1, phi = 0).
+ *   br_from/br_to [M]  bus indices in [0, n), from != to
+ *   br_r, br_x [M]     series impedance r + jx (x > 0); g + jb = 1/(r + jx)
+ *   br_b [M]           total line charging b_ch (pi model, b_ch/2 per end)
+ *   s_max [M]          base-case apparent power limit (thermal, Example 1)
+ *   s_max_ctg [M]      post-contingency limit (Eqs. sfr_pen-zctg)
+ *   gen_bus, gen_zone [G], cost_a, cost_b [G] (cost d_t (a p^2 + b p)),
+ *   cost_r [G] (reserve offer), pmin, pmax, qmin, qmax [G], ramp [G] (pu/h)
+ *   vmin, vmax [n]; ref_bus in [0, n) (angle reference, theta_ref clipped to 0) */
+typedef struct {
+  int32_t n_bus, n_branch, n_gen, n_zone, ref_bus;
+  const int32_t *br_from, *br_to;
+  const double *br_r, *br_x, *br_b, *s_max, *s_max_ctg;
+  const int32_t *gen_bus, *gen_zone;
+  const double *cost_a, *cost_b, *cost_r, *pmin, *pmax, *qmin, *qmax, *ramp;
+  const double *vmin, *vmax;
+} qg_network;
+
+/* Horizon: T periods of dt[t] hours; load_p, load_q are T x n period-major;
+ * reserve_req is T x Z (zonal up-reserve requirement). */
+typedef struct {
+  int32_t T;
+  const double *dt, *load_p, *load_q, *reserve_req;
+} qg_horizon;
+
+/* Single-branch outages (Sec. II-E): K distinct branch ids in [0, M). */
+typedef struct {
+  int32_t K;
+  const int32_t *branch;
+} qg_contingencies;
+
+/* Penalty prices and numerics.  c_p, c_q: balance ($/pu h, Example 4); c_s:
+ * thermal and contingency overload (Example 1, Eq. zctg); c_rz: zonal reserve
+ * shortfall; rho: penalized linear constraints (headroom, ramps; Eq.
+ * nlp_updated); eps: soft-abs / soft-ReLU smoothing (Sec. II-C footnote); beta:
+ * homotopy scale on every penalty (Sec. II-F); adam_eps: Adam epsilon. */
+typedef struct {
+  double c_p, c_q, c_s, c_rz, rho, eps, beta, adam_eps;
+  int32_t precision;   /* QG_FP64 or QG_MIXED                                   */
+  int32_t lodf_dtype;  /* QG_LODF_*; QG_FP64 always stores the LODF in FP64     */
+  int32_t adam_paper_eps; /* 1: numerator (mhat + eps) exactly as printed in Alg. 3 */
+  int32_t reserved;
+} qg_options;
+
+/* Fill *opt with the defaults: c_p = c_q = 1e4, c_s = c_rz = rho = 1e3,
+ * eps = 1e-3, beta = 1, adam_eps = 1e-8, QG_FP64, QG_LODF_F32. */
+void qg_default_options(qg_options *opt);
+
+/* Build a handle for one instance: validates the inputs, factors the reduced DC
+ * Laplacian E^T Y_x E (Sec. II-E, Eq. Yb_solve; reference bus removed), builds
+ * the line-outage block L[m,k] = PTDF_mk / (1 - PTDF_kk) of the rank-1 (SMW)
+ * correction (Eq. rank_correct, in flow space) with the denominators in FP64,
+ * and uploads everything to the current CUDA device.  Returns
+ * QG_ERR_ISLANDING if an outage has |1 - PTDF_kk| < 1e-9. */
+int qg_create(qg_ctx **out, const qg_network *net, const qg_horizon *hor, const qg_contingencies *ctg,
+              const qg_options *opt);
+
+/* Same for n_inst independent instances (arrays of n_inst structs) evaluated
+ * together by every later call; instance sizes may differ. */
+int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const qg_horizon *hor,
+                    const qg_contingencies *ctg, const qg_options *opt);
+
+void qg_destroy(qg_ctx *h);
+
+/* Total variable count of the handle (all instances). */
+int64_t qg_num_vars(const qg_ctx *h);
+
+/* Layout of instance `inst`: its first variable in the concatenated x, its
+ * n_x = T (2n + 3G), and the starts of the v, theta, p, q, r blocks relative
+ * to that first variable. */
+int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[5]);
+
+/* Order all later device work on `stream` (a cudaStream_t; NULL = default). */
+int qg_set_stream(qg_ctx *h, void *stream);
+
+/* One full evaluation (Eq. grads): obj[b] = Phi_b(x) for every instance b
+ * (device, n_inst doubles) and g = grad Phi(x) (device, qg_num_vars elements),
+ * covering every period and every contingency (Alg. 2 with K_t = all, zeta = 0).
+ * g may be NULL (objective only).  x is not modified. */
+int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g);
+
+/* qg_eval_grad on host buffers: copies x (qg_num_vars doubles) to the device,
+ * evaluates, and copies obj (n_inst doubles) and g (qg_num_vars doubles, may be
+ * NULL) back; synchronizes.  In QG_MIXED mode the copies convert to/from float. */
+int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g);
+
+/* One projected Adam step (Alg. 3) on every variable, using the gradient of the
+ * last qg_eval_grad on this handle (kept internally):
+ *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; x -= lr mhat/(sqrt(vhat)+eps);
+ *   x = clip(x, box) with v in [vmin, vmax], theta_ref = 0, p in [pmin, pmax],
+ *   q in [qmin, qmax], r in [0, pmax].  The step counter i (bias correction) is
+ *   kept in the handle and advanced by one. */
+int qg_adam_step(qg_ctx *h, void *x, void *m, void *v, double lr, double beta1, double beta2);
+
+/* iters iterations of (qg_eval_grad; qg_adam_step) on x in place, with Adam
+ * moments kept inside the handle (reset when the step counter is 0), replayed
+ * from a CUDA graph.  obj_trace (device, iters x n_inst doubles, may be NULL)
+ * receives the objective evaluated at the start of each iteration. */
+int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace);
+
+/* Per-instance penalty breakdown of the last evaluation, host array of
+ * 8 x n_inst doubles: cost, z_p, z_q, z_s, z_rz, z_headroom, z_ramp, z_ctg.
+ * Synchronizes the stream. */
+int qg_breakdown(qg_ctx *h, double *out);
+
+/* Adam step counter (for checkpoint/resume together with x, m, v). */
+int qg_get_step(qg_ctx *h, int64_t *step);
+int qg_set_step(qg_ctx *h, int64_t step);
+
+const char *qg_last_error(const qg_ctx *h);
+
+/* Build identification: major*10000 + minor*100 + patch. */
+int qg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QG_H */

@@ -1,0 +1,277 @@
+"""ctypes binding of libqg (include/qg.h), same entry-point names.
+
+Argument marshalling only: every step of the evaluation and of the Adam update
+runs in the library's CUDA kernels.  Device buffers are torch CUDA tensors
+(contiguous; float64 in QG_FP64 mode, float32 in QG_MIXED mode; obj float64).
+If the shared library is missing, importing this module raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB
+
+QG_OK = 0
+QG_ERR_INVALID_ARG = -1
+QG_ERR_ISLANDING = -2
+QG_ERR_CUDA = -3
+QG_ERR_NOT_CONVERGED = -4
+QG_ERR_TIMEOUT = -5
+QG_ERR_NONFINITE = -6
+QG_ERR_NO_DEVICE = -7
+QG_ERR_UNSUPPORTED = -8
+QG_FP64, QG_MIXED = 0, 1
+QG_LODF_F32, QG_LODF_BF16, QG_LODF_BF16X2 = 0, 1, 2
+
+TERM_NAMES = ("cost", "zp", "zq", "zs", "zrz", "zhead", "zramp", "zctg")
+
+_I32P = C.POINTER(C.c_int32)
+_F64P = C.POINTER(C.c_double)
+
+
+class qg_network(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("n_gen", C.c_int32), ("n_zone", C.c_int32),
+                ("ref_bus", C.c_int32), ("br_from", _I32P), ("br_to", _I32P), ("br_r", _F64P), ("br_x", _F64P),
+                ("br_b", _F64P), ("s_max", _F64P), ("s_max_ctg", _F64P), ("gen_bus", _I32P), ("gen_zone", _I32P),
+                ("cost_a", _F64P), ("cost_b", _F64P), ("cost_r", _F64P), ("pmin", _F64P), ("pmax", _F64P),
+                ("qmin", _F64P), ("qmax", _F64P), ("ramp", _F64P), ("vmin", _F64P), ("vmax", _F64P)]
+
+
+class qg_horizon(C.Structure):
+    _fields_ = [("T", C.c_int32), ("dt", _F64P), ("load_p", _F64P), ("load_q", _F64P), ("reserve_req", _F64P)]
+
+
+class qg_contingencies(C.Structure):
+    _fields_ = [("K", C.c_int32), ("branch", _I32P)]
+
+
+class qg_options(C.Structure):
+    _fields_ = [("c_p", C.c_double), ("c_q", C.c_double), ("c_s", C.c_double), ("c_rz", C.c_double),
+                ("rho", C.c_double), ("eps", C.c_double), ("beta", C.c_double), ("adam_eps", C.c_double),
+                ("precision", C.c_int32), ("lodf_dtype", C.c_int32), ("adam_paper_eps", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB):
+        raise ImportError(f"libqg.so is not built ({LIB}); run paper_2310_06650_gb300.build.build()")
+    lib = C.CDLL(LIB)
+    vp = C.c_void_p
+    sig = {
+        "qg_default_options": (None, [C.POINTER(qg_options)]),
+        "qg_create": (C.c_int, [C.POINTER(vp), C.POINTER(qg_network), C.POINTER(qg_horizon),
+                                C.POINTER(qg_contingencies), C.POINTER(qg_options)]),
+        "qg_create_batch": (C.c_int, [C.POINTER(vp), C.c_int32, C.POINTER(qg_network), C.POINTER(qg_horizon),
+                                      C.POINTER(qg_contingencies), C.POINTER(qg_options)]),
+        "qg_destroy": (None, [vp]),
+        "qg_num_vars": (C.c_int64, [vp]),
+        "qg_layout": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "qg_set_stream": (C.c_int, [vp, vp]),
+        "qg_eval_grad": (C.c_int, [vp, vp, vp, vp]),
+        "qg_eval_grad_host": (C.c_int, [vp, _F64P, _F64P, _F64P]),
+        "qg_adam_step": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double]),
+        "qg_solve": (C.c_int, [vp, vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp]),
+        "qg_breakdown": (C.c_int, [vp, _F64P]),
+        "qg_get_step": (C.c_int, [vp, C.POINTER(C.c_int64)]),
+        "qg_set_step": (C.c_int, [vp, C.c_int64]),
+        "qg_last_error": (C.c_char_p, [vp]),
+        "qg_version": (C.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
+            "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_adam_step", "qg_solve", "qg_breakdown",
+            "qg_get_step", "qg_set_step", "qg_last_error", "qg_version")
+
+
+class QGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libqg error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, h=None):
+    if rc != QG_OK:
+        raise QGError(rc, _lib.qg_last_error(h).decode(errors="replace"))
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def qg_default_options(**overrides) -> qg_options:
+    o = qg_options()
+    _lib.qg_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class _Keep:
+    """Holds the numpy arrays behind one set of C structs until qg_create returns."""
+
+    def __init__(self):
+        self.arrays = []
+
+    def i32(self, a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        self.arrays.append(a)
+        return a.ctypes.data_as(_I32P)
+
+    def f64(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.arrays.append(a)
+        return a.ctypes.data_as(_F64P)
+
+
+def _structs(case, keep: _Keep):
+    """C structs for one case (any object with the synthetic case's attribute names)."""
+    net = qg_network(
+        n_bus=case.n_bus, n_branch=case.n_branch, n_gen=case.n_gen, n_zone=case.n_zone, ref_bus=case.ref_bus,
+        br_from=keep.i32(case.br_from), br_to=keep.i32(case.br_to), br_r=keep.f64(case.br_r),
+        br_x=keep.f64(case.br_x), br_b=keep.f64(case.br_b), s_max=keep.f64(case.s_max),
+        s_max_ctg=keep.f64(case.s_max_ctg), gen_bus=keep.i32(case.gen_bus), gen_zone=keep.i32(case.gen_zone),
+        cost_a=keep.f64(case.cost_a), cost_b=keep.f64(case.cost_b), cost_r=keep.f64(case.cost_r),
+        pmin=keep.f64(case.pmin), pmax=keep.f64(case.pmax), qmin=keep.f64(case.qmin), qmax=keep.f64(case.qmax),
+        ramp=keep.f64(case.ramp), vmin=keep.f64(case.vmin), vmax=keep.f64(case.vmax))
+    hor = qg_horizon(T=case.T, dt=keep.f64(case.dt), load_p=keep.f64(case.load_p), load_q=keep.f64(case.load_q),
+                     reserve_req=keep.f64(case.reserve_req))
+    ctg = qg_contingencies(K=case.K, branch=keep.i32(case.ctg) if case.K > 0 else None)
+    return net, hor, ctg
+
+
+def case_options(case, precision=QG_FP64, lodf_dtype=QG_LODF_F32, **kw) -> qg_options:
+    """Options carrying the case's penalty prices; keyword arguments override any field."""
+    base = dict(c_p=case.c_p, c_q=case.c_q, c_s=case.c_s, c_rz=case.c_rz, rho=case.rho, eps=case.eps,
+                beta=case.beta, precision=precision, lodf_dtype=lodf_dtype)
+    base.update(kw)
+    return qg_default_options(**base)
+
+
+def qg_create_batch(cases: Sequence, opt: qg_options) -> int:
+    """Returns the opaque handle (an int) for the given cases."""
+    keep = _Keep()
+    nets, hors, ctgs = zip(*[_structs(c, keep) for c in cases])
+    NA = qg_network * len(cases)
+    HA = qg_horizon * len(cases)
+    CA = qg_contingencies * len(cases)
+    h = C.c_void_p()
+    rc = _lib.qg_create_batch(C.byref(h), len(cases), NA(*nets), HA(*hors), CA(*ctgs), C.byref(opt))
+    _check(rc, None)
+    return h.value
+
+
+def qg_create(case, opt: qg_options) -> int:
+    return qg_create_batch([case], opt)
+
+
+def qg_destroy(h: int) -> None:
+    _lib.qg_destroy(h)
+
+
+def qg_num_vars(h: int) -> int:
+    return int(_lib.qg_num_vars(h))
+
+
+def qg_layout(h: int, inst: int = 0):
+    first, n_x = C.c_int64(), C.c_int64()
+    off = (C.c_int64 * 5)()
+    _check(_lib.qg_layout(h, inst, C.byref(first), C.byref(n_x), off), h)
+    return first.value, n_x.value, tuple(off)
+
+
+def qg_set_stream(h: int, stream_ptr: int) -> None:
+    _check(_lib.qg_set_stream(h, stream_ptr), h)
+
+
+def qg_eval_grad(h: int, x, obj, g=None) -> None:
+    _check(_lib.qg_eval_grad(h, _ptr(x), _ptr(obj), _ptr(g)), h)
+
+
+def qg_eval_grad_host(h: int, x: np.ndarray, obj: np.ndarray, g: Optional[np.ndarray] = None) -> None:
+    for a in (x, obj) + ((g,) if g is not None else ()):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(_lib.qg_eval_grad_host(h, x.ctypes.data_as(_F64P), obj.ctypes.data_as(_F64P),
+                                  g.ctypes.data_as(_F64P) if g is not None else None), h)
+
+
+def qg_adam_step(h: int, x, m, v, lr: float, beta1: float = 0.9, beta2: float = 0.999) -> None:
+    _check(_lib.qg_adam_step(h, _ptr(x), _ptr(m), _ptr(v), lr, beta1, beta2), h)
+
+
+def qg_solve(h: int, x, iters: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, obj_trace=None) -> None:
+    _check(_lib.qg_solve(h, _ptr(x), iters, lr, beta1, beta2, _ptr(obj_trace)), h)
+
+
+def qg_breakdown(h: int, n_inst: int = 1) -> np.ndarray:
+    out = np.zeros(8 * n_inst)
+    _check(_lib.qg_breakdown(h, out.ctypes.data_as(_F64P)), h)
+    return out.reshape(n_inst, 8)
+
+
+def qg_get_step(h: int) -> int:
+    s = C.c_int64()
+    _check(_lib.qg_get_step(h, C.byref(s)), h)
+    return s.value
+
+
+def qg_set_step(h: int, step: int) -> None:
+    _check(_lib.qg_set_step(h, step), h)
+
+
+def qg_last_error(h: Optional[int] = None) -> str:
+    return _lib.qg_last_error(h).decode(errors="replace")
+
+
+def qg_version() -> int:
+    return int(_lib.qg_version())
+
+
+class Solver:
+    """Convenience owner of one handle (and its torch device buffers)."""
+
+    def __init__(self, cases, precision=QG_FP64, lodf_dtype=QG_LODF_F32, device="cuda", **opt_kw):
+        import torch
+        self.torch = torch
+        self.cases = list(cases) if isinstance(cases, (list, tuple)) else [cases]
+        self.precision = precision
+        self.dtype = torch.float64 if precision == QG_FP64 else torch.float32
+        self.device = torch.device(device)
+        opt = case_options(self.cases[0], precision=precision, lodf_dtype=lodf_dtype, **opt_kw)
+        self.h = qg_create_batch(self.cases, opt)
+        self.n_x = qg_num_vars(self.h)
+        self.n_inst = len(self.cases)
+        self.obj = torch.zeros(self.n_inst, dtype=torch.float64, device=self.device)
+        self.g = torch.zeros(self.n_x, dtype=self.dtype, device=self.device)
+        qg_set_stream(self.h, torch.cuda.current_stream(self.device).cuda_stream)
+
+    def eval_grad(self, x):
+        qg_eval_grad(self.h, x, self.obj, self.g)
+        return self.obj, self.g
+
+    def breakdown(self):
+        return qg_breakdown(self.h, self.n_inst)
+
+    def close(self):
+        if self.h:
+            qg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,109 @@
+"""The C-ABI library: it builds, loads, exports every entry point of include/qg.h,
+and its host-side validation rejects bad inputs before touching a device."""
+import dataclasses
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def qg():
+    from paper_2310_06650_gb300.build import build
+    build()
+    from paper_2310_06650_gb300 import qg as mod
+    return mod
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "qg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_header_symbol(qg):
+    import ctypes
+    lib = ctypes.CDLL(qg.LIB)
+    names = _header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(qg.EXPORTED)
+    assert qg.qg_version() >= 100
+
+
+def test_default_options(qg):
+    o = qg.qg_default_options()
+    assert (o.c_p, o.c_q, o.c_s, o.c_rz, o.rho, o.eps, o.beta, o.adam_eps) == (1e4, 1e4, 1e3, 1e3, 1e3, 1e-3, 1.0, 1e-8)
+    assert o.precision == qg.QG_FP64 and o.lodf_dtype == qg.QG_LODF_F32
+
+
+def _expect(qg, case, code, **opt):
+    with pytest.raises(qg.QGError) as ei:
+        qg.qg_create(case, qg.case_options(case, **opt))
+    assert ei.value.code == code, str(ei.value)
+    return str(ei.value)
+
+
+def _gpu_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(_gpu_present(), reason="checks the no-device path")
+def test_valid_case_reaches_device_check(qg):
+    msg = _expect(qg, synth.tiny(), qg.QG_ERR_NO_DEVICE)
+    assert "device" in msg
+
+
+def test_invalid_inputs_are_rejected(qg):
+    c = synth.tiny()
+    bad_from = c.br_from.copy(); bad_from[3] = c.n_bus
+    _expect(qg, dataclasses.replace(c, br_from=bad_from), qg.QG_ERR_INVALID_ARG)
+    loop = c.br_to.copy(); loop[0] = c.br_from[0]
+    _expect(qg, dataclasses.replace(c, br_to=loop), qg.QG_ERR_INVALID_ARG)
+    bx = c.br_x.copy(); bx[1] = 0.0
+    _expect(qg, dataclasses.replace(c, br_x=bx), qg.QG_ERR_INVALID_ARG)
+    dup = c.ctg.copy(); dup[1] = dup[0]
+    _expect(qg, dataclasses.replace(c, ctg=dup), qg.QG_ERR_INVALID_ARG)
+    lp = c.load_p.copy(); lp[0, 0] = np.nan
+    _expect(qg, dataclasses.replace(c, load_p=lp), qg.QG_ERR_INVALID_ARG)
+    gz = c.gen_zone.copy(); gz[0] = 5
+    _expect(qg, dataclasses.replace(c, gen_zone=gz), qg.QG_ERR_INVALID_ARG)
+    _expect(qg, c, qg.QG_ERR_INVALID_ARG, eps=-1.0)
+    _expect(qg, c, qg.QG_ERR_INVALID_ARG, precision=7)
+
+
+def _radial(n=5):
+    """A path graph: every branch is a bridge, so every outage islands the grid."""
+    c = synth.tiny()
+    M = n - 1
+    frm = np.arange(M, dtype=np.int32)
+    to = np.arange(1, n, dtype=np.int32)
+    return dataclasses.replace(
+        c, n_bus=n, n_branch=M, br_from=frm, br_to=to, br_r=np.full(M, 0.01), br_x=np.full(M, 0.1),
+        br_b=np.zeros(M), s_max=np.ones(M), s_max_ctg=np.ones(M), n_gen=1, gen_bus=np.array([0], np.int32),
+        gen_zone=np.array([0], np.int32), cost_a=np.ones(1), cost_b=np.ones(1), cost_r=np.ones(1), pmin=np.zeros(1),
+        pmax=np.ones(1), qmin=-np.ones(1), qmax=np.ones(1), ramp=np.ones(1), vmin=np.full(n, 0.9),
+        vmax=np.full(n, 1.1), load_p=np.full((c.T, n), 0.1), load_q=np.zeros((c.T, n)),
+        bus_zone=np.zeros(n, np.int32), ctg=np.array([1, 2], np.int32))
+
+
+def test_islanding_outage_is_rejected(qg):
+    msg = _expect(qg, _radial(), qg.QG_ERR_ISLANDING)
+    assert "islands" in msg
+
+
+def test_disconnected_grid_is_rejected(qg):
+    c = _radial()
+    c = dataclasses.replace(c, br_from=np.array([0, 1, 3, 0], np.int32), br_to=np.array([1, 2, 4, 2], np.int32),
+                            ctg=np.zeros(0, np.int32))
+    _expect(qg, c, qg.QG_ERR_ISLANDING)

@@ -1,0 +1,188 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: the FP64 path agrees with the oracle to 1e-10 relative on the
+objective, on every objective term and on ||g - g_ref|| / ||g_ref||; the mixed
+path (FP32 flows / penalties / adjoints / Adam, double-FP32 DC solves, FP64
+objective accumulation) to 1e-4 on the same quantities.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.copperplate import copper_plate
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def qg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_06650_gb300.build import build
+    build()
+    from paper_2310_06650_gb300 import qg as mod
+    return mod
+
+
+_CASES = {}
+
+
+def case_named(name):
+    if name not in _CASES:
+        _CASES[name] = {"tiny": synth.tiny, "mid": synth.mid, "rt617": synth.rt617,
+                        "b73": lambda: synth.batch(per_shape=1)[0]}[name]()
+    return _CASES[name]
+
+
+def point(case, kind):
+    if kind == "lp":
+        _, p, r = copper_plate(case)
+        return case.flat_start(p, r)
+    if kind == "lp_perturbed":
+        _, p, r = copper_plate(case)
+        x = case.flat_start(p, r) + 0.02 * (synth.random_point(case, 99) - 0.5)
+        lo, hi = oracle.box(case)
+        return np.clip(x, lo, hi)
+    return synth.random_point(case, int(kind))
+
+
+def gpu_eval(qg, cases, x, precision, lodf=0, **kw):
+    s = qg.Solver(cases, precision=precision, lodf_dtype=lodf, **kw)
+    xt = torch.tensor(x, dtype=s.dtype, device="cuda")
+    obj, g = s.eval_grad(xt)
+    torch.cuda.synchronize()
+    out = (obj.cpu().numpy().copy(), g.double().cpu().numpy().copy(), s.breakdown())
+    s.close()
+    return out
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def grel(g, gr):
+    return np.linalg.norm(g - gr) / np.linalg.norm(gr)
+
+
+def check(res, ref, tol):
+    obj, g, terms = res
+    assert rel(obj[0], ref.obj) <= tol, (obj[0], ref.obj)
+    assert grel(g, ref.grad) <= tol, grel(g, ref.grad)
+    for k, name in enumerate(oracle.TERM_NAMES):
+        assert abs(terms[0, k] - ref.terms[name]) <= tol * max(abs(ref.terms[name]), 1e-6 * abs(ref.obj)), name
+
+
+@pytest.mark.parametrize("name,kind", [("tiny", "1"), ("tiny", "lp"), ("mid", "2"), ("mid", "lp_perturbed"),
+                                       ("rt617", "3"), ("rt617", "lp"), ("rt617", "lp_perturbed")])
+def test_fp64_parity(qg, name, kind):
+    c = case_named(name)
+    x = point(c, kind)
+    check(gpu_eval(qg, c, x, qg.QG_FP64), oracle.evaluate(c, x), TOL64)
+
+
+@pytest.mark.parametrize("name,kind", [("tiny", "1"), ("mid", "lp_perturbed"), ("rt617", "lp"),
+                                       ("rt617", "lp_perturbed")])
+def test_mixed_parity(qg, name, kind):
+    c = case_named(name)
+    x = point(c, kind)
+    check(gpu_eval(qg, c, x, qg.QG_MIXED), oracle.evaluate(c, x), TOL32)
+
+
+def test_eps_zero_scoring_parity(qg):
+    """The metric scores points with the hard abs / ReLU (eps = 0)."""
+    c = case_named("mid")
+    x = point(c, "lp_perturbed")
+    res = gpu_eval(qg, c, x, qg.QG_FP64, eps=0.0)
+    ref = oracle.evaluate(c, x, eps=0.0)
+    assert rel(res[0][0], ref.obj) <= TOL64
+    assert grel(res[1], ref.grad) <= TOL64
+
+
+def test_ragged_batch_parity(qg):
+    """Uneven instances in one handle: every instance matches its own oracle evaluation."""
+    cases = [case_named("tiny"), case_named("mid"), case_named("b73"), synth.tiny(seed=5)]
+    xs = [point(c, str(10 + i)) for i, c in enumerate(cases)]
+    for prec, tol in ((qg.QG_FP64, TOL64), (qg.QG_MIXED, TOL32)):
+        obj, g, terms = gpu_eval(qg, cases, np.concatenate(xs), prec)
+        o = 0
+        for b, (c, x) in enumerate(zip(cases, xs)):
+            ref = oracle.evaluate(c, x)
+            assert rel(obj[b], ref.obj) <= tol
+            assert grel(g[o:o + c.n_x], ref.grad) <= tol
+            o += c.n_x
+
+
+def test_evaluation_is_bitwise_deterministic(qg):
+    c = case_named("rt617")
+    x = point(c, "lp_perturbed")
+    for prec in (qg.QG_FP64, qg.QG_MIXED):
+        s = qg.Solver(c, precision=prec)
+        xt = torch.tensor(x, dtype=s.dtype, device="cuda")
+        o1, g1 = (t.clone() for t in s.eval_grad(xt))
+        o2, g2 = (t.clone() for t in s.eval_grad(xt))
+        assert torch.equal(o1, o2) and torch.equal(g1, g2)
+        s.close()
+
+
+def test_host_entry_matches_device_entry(qg):
+    c = case_named("mid")
+    x = point(c, "lp_perturbed")
+    for prec in (qg.QG_FP64, qg.QG_MIXED):
+        s = qg.Solver(c, precision=prec)
+        obj_h = np.zeros(1)
+        g_h = np.zeros(c.n_x)
+        qg.qg_eval_grad_host(s.h, np.ascontiguousarray(x), obj_h, g_h)
+        xt = torch.tensor(x, dtype=s.dtype, device="cuda")
+        obj, g = s.eval_grad(xt)
+        torch.cuda.synchronize()
+        assert obj_h[0] == obj.item()
+        assert np.array_equal(g_h, g.double().cpu().numpy())
+        s.close()
+
+
+def test_adam_step_parity(qg):
+    c = case_named("mid")
+    x = point(c, "lp_perturbed")
+    s = qg.Solver(c, precision=qg.QG_FP64)
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    m = torch.zeros_like(xt)
+    v = torch.zeros_like(xt)
+    lo, hi = oracle.box(c)
+    xr, mr, vr = x.copy(), np.zeros_like(x), np.zeros_like(x)
+    for i in range(1, 6):
+        _, g = s.eval_grad(xt)
+        gr = g.cpu().numpy().copy()
+        qg.qg_adam_step(s.h, xt, m, v, 1e-3, 0.9, 0.999)
+        xr, mr, vr = oracle.adam_step(xr, mr, vr, gr, i, 1e-3, 0.9, 0.999, 1e-8, lo, hi)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(xt.cpu().numpy() - xr)) <= 1e-14
+        assert np.max(np.abs(m.cpu().numpy() - mr)) <= 1e-12 * np.abs(mr).max()
+    assert qg.qg_get_step(s.h) == 5
+    s.close()
+
+
+def test_solve_trajectory_matches_oracle(qg):
+    """qg_solve (graph-replayed eval + Adam) against the oracle's own loop, per iterate."""
+    c = case_named("tiny")
+    x0 = point(c, "lp")
+    iters = 60
+    s = qg.Solver(c, precision=qg.QG_FP64)
+    xt = torch.tensor(x0, dtype=torch.float64, device="cuda")
+    trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
+    qg.qg_solve(s.h, xt, iters, 1e-3, 0.9, 0.999, trace)
+    torch.cuda.synchronize()
+    lo, hi = oracle.box(c)
+    x, m, v = x0.copy(), np.zeros_like(x0), np.zeros_like(x0)
+    tr = trace.cpu().numpy()
+    for i in range(1, iters + 1):
+        ref = oracle.evaluate(c, x)
+        assert rel(tr[i - 1], ref.obj) <= 1e-9, (i, tr[i - 1], ref.obj)
+        x, m, v = oracle.adam_step(x, m, v, ref.grad, i, 1e-3, 0.9, 0.999, 1e-8, lo, hi)
+    assert np.max(np.abs(xt.cpu().numpy() - x)) <= 1e-9
+    s.close()
