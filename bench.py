@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of the QuasiGrad hot path on GB300: full objective + gradient
+evaluations per second (every period, every contingency), each followed by the
+projected Adam update, on the 617-bus / 18-period / 562-outage real-time shape.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one CUDA-graph replay of the nine evaluation kernels and the Adam
+kernel (qg_solve with one iteration).  L2 is flushed (a 512 MB write) before
+every timed step; each step is timed with CUDA events on the launching stream.
+Rank 0 prints one JSON line.  With torchrun (N > 1) every rank runs an
+independent replica (the path has no exchange step) and the result is the sum
+of the ranks' evaluations over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (each step
+evaluates one period's slice of the same workload: 1/T of an evaluation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "full grad evals/s (all periods+ctgs); time to 1% of LP bound vs FP64 plain"
+UNIT = "evals/s"
+WORKLOAD = "rt617"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK, sm_max_mhz=2070.0), "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference), in a fresh interpreter
+# ------------------------------------------------------------------------------------------------
+
+_ORACLE_SNIPPET = r"""
+import json, os, sys, time, dataclasses
+sys.path.insert(0, {root!r})
+import numpy as np
+import synth, oracle
+case = getattr(synth, {workload!r})()
+x = case.flat_start()
+v, th, p, q, r = oracle.unpack(case, x)
+def period_case(t):
+    sl = slice(t, t + 1)
+    return dataclasses.replace(case, T=1, dt=case.dt[sl], load_p=case.load_p[sl], load_q=case.load_q[sl],
+                               reserve_req=case.reserve_req[sl])
+subs = [(period_case(t), oracle.pack(v[t], th[t], p[t], q[t], r[t])) for t in range(case.T)]
+mode, budget, steps, warm = {mode!r}, {budget!r}, {steps!r}, {warm!r}
+for k in range(warm):
+    c, xs = subs[k % case.T]; oracle.evaluate(c, xs)
+times = []
+t_start = time.perf_counter()
+k = 0
+while True:
+    c, xs = subs[k % case.T]
+    t0 = time.perf_counter(); oracle.evaluate(c, xs); times.append(time.perf_counter() - t0)
+    k += 1
+    if mode == "budget" and time.perf_counter() - t_start >= budget and k >= case.T:
+        break
+    if mode == "steps" and k >= steps:
+        break
+print(json.dumps({{"slices": k, "T": case.T, "seconds": sum(times), "times": times}}))
+"""
+
+
+def run_oracle(mode, budget=15.0, steps=0, warm=1):
+    ncpu = os.cpu_count() or 1
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(ncpu)
+    code = _ORACLE_SNIPPET.format(root=ROOT, workload=WORKLOAD, mode=mode, budget=budget, steps=steps, warm=warm)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["cores"] = ncpu
+    return res
+
+
+def oracle_sample_text(res):
+    return (f"{res['slices']} single-period slices of {WORKLOAD} (1/{res['T']} of an evaluation each: AC terms, "
+            f"562 outages, gradient), numpy FP64, {res['cores']} BLAS threads")
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+# algorithmic work per launch (roofline numerators)
+# ------------------------------------------------------------------------------------------------
+
+def algorithmic(case, phase, mixed):
+    """(amount, unit, bound) of one launch of `phase` on `case`."""
+    T, n, M, G, K = case.T, case.n_bus, case.n_branch, case.n_gen, case.K
+    rs = 4 if mixed else 8
+    if phase == "ctg":
+        # per (t, m, k): F = f_m + L f_k and F^2 + (qmax2 - s^2) -> 2 FMA = 4 flop
+        return 4.0 * T * M * K, "flop", "alu"
+    if phase in ("dc_fwd", "dc_adj"):
+        return 2.0 * n * n * T, "flop64", "alu"
+    if phase == "adam":
+        return (9.0 * rs) * case.n_x, "byte", "hbm"
+    if phase in ("fwd1", "bwd1"):
+        return float(T * M * (4 * rs + 4 * rs + 3 * rs + 8)), "byte", "hbm"
+    if phase in ("fwd2", "adj1", "bwd2"):
+        return float(T * n * (6 * 4 * rs + 3 * rs) + T * G * 6 * rs), "byte", "hbm"
+    return 0.0, "byte", "hbm"
+
+
+def roofline(case, phase, ms, mixed, peaks, src, clocks):
+    amount, unit, bound = algorithmic(case, phase, mixed)
+    sec = ms * 1e-3
+    if unit == "byte":
+        ach = amount / sec / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"bound": "hbm", "kernel": phase, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_source": f"hbm_gbs of {src}"}
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    if unit == "flop64" and not mixed:
+        peak = FP64_NOMINAL_TFLOPS
+        note = "FP64 nominal 1.25 TFLOP/s (prompt table)"
+    elif unit == "flop64":
+        # double-FP32 emulation: ~11 FP32 instructions per FP64-class multiply-add
+        amount = amount / 2.0 * 11.0 * 2.0
+        peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        note = "FP32 lanes x 2 x max SM clock; df32 counted as 11 FP32 ops per multiply-add"
+    else:
+        peak = (N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12) if mixed else FP64_NOMINAL_TFLOPS
+        note = "152 SM x 128 FP32 lanes x 2 flop x max SM clock" if mixed else "FP64 nominal"
+    ach = amount / sec / 1e12
+    return {"bound": "alu", "kernel": phase, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": note}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU leg
+# ------------------------------------------------------------------------------------------------
+
+def gpu_leg(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2310_06650_gb300 import qg
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    case = getattr(synth, WORKLOAD)()
+    x0 = case.flat_start()
+    peaks, src = _peaks()
+    results = {}
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for label, prec in (("mixed", qg.QG_MIXED), ("fp64", qg.QG_FP64)):
+        s = qg.Solver(case, precision=prec)
+        x = torch.tensor(x0, dtype=s.dtype, device="cuda")
+        qg.qg_set_profiling(s.h, True)
+        for _ in range(max(args.warmup, 3)):
+            qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+        torch.cuda.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        phases = {}
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                ev0[k].record(stream)
+                qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+                ev1[k].record(stream)
+                for name, v in qg.qg_phase_times(s.h).items():
+                    phases.setdefault(name, []).append(v)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        total_ms = sum(step_ms)
+        if dist:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        # the same loop without the flush (L2-resident, as in a long Adam run), for context
+        qg.qg_set_profiling(s.h, False)
+        qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qg.qg_solve(s.h, x, args.steps, 1e-3, 0.9, 0.999)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        warm_ms = e0.elapsed_time(e1) / args.steps
+        # end to end through host buffers: H2D x, evaluation, D2H objective and gradient
+        xh = torch.tensor(x0, dtype=torch.float64).pin_memory().numpy()
+        oh = torch.zeros(1, dtype=torch.float64).pin_memory().numpy()
+        gh = torch.zeros(case.n_x, dtype=torch.float64).pin_memory().numpy()
+        for _ in range(3):
+            qg.qg_eval_grad_host(s.h, xh, oh, gh)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            qg.qg_eval_grad_host(s.h, xh, oh, gh)
+        e2e_s = time.perf_counter() - t0
+        results[label] = {
+            "step_ms": step_ms, "total_ms": total_ms, "phases": {k: statistics.mean(v) for k, v in phases.items()},
+            "warm_ms": warm_ms, "e2e_s": e2e_s, "clocks": clk.summary(), "obj": float(s.obj[0].item()),
+        }
+        s.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    mix = results["mixed"]
+    K = args.steps
+    value = world * K / (mix["total_ms"] * 1e-3)
+    phases = mix["phases"]
+    eval_phases = {k: v for k, v in phases.items()}
+    dom = max(eval_phases, key=lambda k: eval_phases[k])
+    roof = roofline(case, dom, phases[dom], True, peaks, src, mix["clocks"])
+    f64 = results["fp64"]
+    dom64 = max(f64["phases"], key=lambda k: f64["phases"][k])
+    cpu = run_oracle("budget", budget=args.cpu_budget)
+    cpu_value = cpu["slices"] / cpu["T"] / cpu["seconds"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": mix["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {case.n_bus} buses, {case.n_branch} branches, {case.n_gen} generators, "
+                               f"{case.T} periods, {case.K} single-branch outages (all evaluated, zeta = 0)",
+                   "step": "one full objective+gradient evaluation + projected Adam update (CUDA graph replay)",
+                   "precision": "mixed: FP32 flows/penalties/adjoints/Adam, double-FP32 DC solves, FP64 objective",
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                         "sample": oracle_sample_text(cpu)},
+        "e2e": {"value": world * K / mix["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": 8 * case.n_x,
+                "d2h_bytes_per_step": 8 * (case.n_x + 1),
+                "call": "qg_eval_grad_host (pinned host x -> device, evaluation, objective + gradient -> host)"},
+        "gpu_launches": 10 * K,
+        "clocks": mix["clocks"],
+        "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in phases.items()},
+        "l2_resident": {"value": world / (mix["warm_ms"] * 1e-3), "unit": UNIT,
+                        "note": "same step replayed back to back without the flush"},
+        "fp64_path": {"value": world * K / (f64["total_ms"] * 1e-3), "unit": UNIT,
+                      "ms_per_step": f64["total_ms"] / K,
+                      "roofline": roofline(case, dom64, f64["phases"][dom64], False, peaks, src, f64["clocks"]),
+                      "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in f64["phases"].items()},
+                      "e2e": world * K / f64["e2e_s"]},
+        "paper_context": "24 ms per full gradient on 6 CPU threads for the C3E3.1 617-bus, 18-period, 562-outage case",
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_leg(args, rank, world):
+    if rank != 0:
+        return
+    res = run_oracle("steps", steps=max(args.steps, 1), warm=max(args.warmup, 0))
+    value = res["slices"] / res["T"] / res["seconds"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["slices"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "one single-period slice of the evaluation (1/T of an eval)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": oracle_sample_text(res)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        reference_leg(args, rank, world)
+        return
+    from paper_2310_06650_gb300.build import build
+    build()
+    gpu_leg(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

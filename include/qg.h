@@ -143,8 +143,9 @@ int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g);
 int qg_adam_step(qg_ctx *h, void *x, void *m, void *v, double lr, double beta1, double beta2);
 
 /* iters iterations of (qg_eval_grad; qg_adam_step) on x in place, with Adam
- * moments kept inside the handle (reset when the step counter is 0), replayed
- * from a CUDA graph.  obj_trace (device, iters x n_inst doubles, may be NULL)
+ * moments kept inside the handle (zero after qg_create and after
+ * qg_set_step(h, 0)), replayed from a CUDA graph that is captured on the first
+ * call and re-captured when x, lr, beta1 or beta2 change.  Does not synchronize.  obj_trace (device, iters x n_inst doubles, may be NULL)
  * receives the objective evaluated at the start of each iteration. */
 int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace);
 
@@ -153,9 +154,20 @@ int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double 
  * Synchronizes the stream. */
 int qg_breakdown(qg_ctx *h, double *out);
 
-/* Adam step counter (for checkpoint/resume together with x, m, v). */
+/* Adam step counter (for checkpoint/resume together with x, m, v);
+ * qg_set_step(h, 0) also zeroes the moments that qg_solve keeps in the handle. */
 int qg_get_step(qg_ctx *h, int64_t *step);
 int qg_set_step(qg_ctx *h, int64_t step);
+
+/* Per-kernel timing (CUDA events, no profiler): when on, every evaluation and
+ * Adam step records an event after each kernel, also inside qg_solve's graph.
+ * qg_phase_times writes the durations in ms of the last evaluation's phases,
+ * in launch order (fwd1, fwd2, dc_fwd, ctg, adj1, dc_adj, bwd1, bwd2, obj,
+ * adam), up to cap entries, and returns how many it wrote (adam only when an
+ * Adam step followed the evaluation), or a negative error code.  Waits for
+ * those events. */
+int qg_set_profiling(qg_ctx *h, int on);
+int qg_phase_times(qg_ctx *h, float *ms, int32_t cap);
 
 const char *qg_last_error(const qg_ctx *h);
 

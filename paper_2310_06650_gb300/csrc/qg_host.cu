@@ -63,6 +63,9 @@ struct qg_ctx {
   const void *g_x = nullptr;
   double g_lr = 0, g_b1 = 0, g_b2 = 0;
   double *g_trace = nullptr;
+  // optional per-kernel timing: ev[0..9] bracket the nine evaluation kernels, ev[10] ends Adam
+  bool profiling = false;
+  cudaEvent_t ev[N_PHASES + 1] = {};
   std::string err;
 };
 
@@ -495,6 +498,11 @@ int check_device(qg_ctx *h) {
 void free_all(qg_ctx *h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   h->gexec = nullptr;
+  for (auto &e : h->ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
   for (void *p : h->allocs) cudaFree(p);
   h->allocs.clear();
 }
@@ -502,8 +510,9 @@ void free_all(qg_ctx *h) {
 bool mixed(const qg_ctx *h) { return h->opt.precision == QG_MIXED; }
 
 int run_eval(qg_ctx *h, const void *x) {
-  cudaError_t e = mixed(h) ? launch_eval<float, df32>(h->d32, h->L, x, h->maxT)
-                           : launch_eval<double, double>(h->d64, h->L, x, h->maxT);
+  cudaEvent_t *ev = h->profiling ? h->ev : nullptr;
+  cudaError_t e = mixed(h) ? launch_eval<float, df32>(h->d32, h->L, x, h->maxT, ev)
+                           : launch_eval<double, double>(h->d64, h->L, x, h->maxT, ev);
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("eval launch: ") + cudaGetErrorString(e));
   return QG_OK;
 }
@@ -517,6 +526,12 @@ int run_adam(qg_ctx *h, void *x, void *m, void *v, double lr, double b1, double 
     e = launch_adam<double>((double *)x, (double *)m, (double *)v, (const double *)h->d_g, h->d64.lo, h->d64.hi,
                             h->n_x, h->d_step, lr, b1, b2, h->opt.adam_eps, h->opt.adam_paper_eps, h->stream);
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("adam launch: ") + cudaGetErrorString(e));
+  if (h->profiling) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(h->stream, &st);
+    if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(h->ev[N_PHASES], h->stream, cudaEventRecordExternal);
+    else cudaEventRecord(h->ev[N_PHASES], h->stream);
+  }
   return QG_OK;
 }
 
@@ -740,14 +755,6 @@ int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double 
   if (!h || !x || iters < 0) return h ? fail(h, QG_ERR_INVALID_ARG, "bad solve arguments") : QG_ERR_INVALID_ARG;
   if (!(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1))
     return fail(h, QG_ERR_INVALID_ARG, "Adam parameters out of range");
-  const size_t rs = mixed(h) ? sizeof(float) : sizeof(double);
-  long long step = 0;
-  CUDA_TRY(h, cudaMemcpyAsync(&step, h->d_step, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  if (step == 0) {
-    CUDA_TRY(h, cudaMemsetAsync(h->d_m, 0, rs * h->n_x, h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_v, 0, rs * h->n_x, h->stream));
-  }
   if (iters == 0) return QG_OK;
   const bool same = h->gexec && h->g_x == x && h->g_lr == lr && h->g_b1 == beta1 && h->g_b2 == beta2;
   if (!same) {
@@ -809,9 +816,42 @@ int qg_get_step(qg_ctx *h, int64_t *step) {
 int qg_set_step(qg_ctx *h, int64_t step) {
   if (!h || step < 0) return QG_ERR_INVALID_ARG;
   long long s = step;
+  if (step == 0) {  // a fresh start also clears the moments qg_solve keeps in the handle
+    const size_t rs = mixed(h) ? sizeof(float) : sizeof(double);
+    CUDA_TRY(h, cudaMemsetAsync(h->d_m, 0, rs * h->n_x, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_v, 0, rs * h->n_x, h->stream));
+  }
   CUDA_TRY(h, cudaMemcpyAsync(h->d_step, &s, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return QG_OK;
+}
+
+int qg_set_profiling(qg_ctx *h, int on) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  if (on && !h->ev[0])
+    for (auto &e : h->ev) CUDA_TRY(h, cudaEventCreate(&e));
+  if ((bool)on != h->profiling && h->gexec) {  // the cached graph must be re-captured
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  h->profiling = on != 0;
+  return QG_OK;
+}
+
+int qg_phase_times(qg_ctx *h, float *ms, int32_t cap) {
+  if (!h || !ms || cap < 0) return QG_ERR_INVALID_ARG;
+  if (!h->profiling) return fail(h, QG_ERR_INVALID_ARG, "profiling is off");
+  CUDA_TRY(h, cudaEventSynchronize(h->ev[N_PHASES - 1]));
+  int n = 0;
+  for (int k = 0; k < N_PHASES && k < cap; ++k) {
+    float v = 0.f;
+    cudaEvent_t end = h->ev[k + 1];
+    if (k == N_PHASES - 1 && cudaEventQuery(end) != cudaSuccess) break;
+    if (cudaEventElapsedTime(&v, h->ev[k], end) != cudaSuccess) v = -1.f;
+    ms[n++] = v;
+  }
+  cudaGetLastError();
+  return n;
 }
 
 const char *qg_last_error(const qg_ctx *h) { return h ? h->err.c_str() : g_create_error.c_str(); }

@@ -120,7 +120,10 @@ struct Launch {
 };
 
 template <typename Real, typename Dc>
-cudaError_t launch_eval(const Dev<Real, Dc> &d, const Launch &L, const void *x, int maxT);
+cudaError_t launch_eval(const Dev<Real, Dc> &d, const Launch &L, const void *x, int maxT, cudaEvent_t *ev);
+
+// Number of timed phases: the nine evaluation kernels and the Adam step.
+constexpr int N_PHASES = 10;
 
 template <typename Real, typename Dc>
 cudaError_t prepare_eval(int maxT);

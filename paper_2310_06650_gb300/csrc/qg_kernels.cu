@@ -228,11 +228,16 @@ __global__ void __launch_bounds__(256) k_fwd1(Dev<Real, Dc> d, const Blk *__rest
       dsincos(dl, &sn, &cs);
       const Real g = d.br_g[jg], bb = d.br_b[jg], bc = d.br_bc[jg];
       const Real vv = vf * vo;
-      // pi model: p_fr = g vf^2 + (-g cos - b sin) vf vo, q_fr = -(b + bch/2) vf^2 + (b cos - g sin) vf vo, ...
-      const Real pf = g * vf * vf + (-g * cs - bb * sn) * vv;
-      const Real qf = -bc * vf * vf + (bb * cs - g * sn) * vv;
-      const Real pt = g * vo * vo + (-g * cs + bb * sn) * vv;
-      const Real qt = -bc * vo * vo + (bb * cs + g * sn) * vv;
+      // Pi model, written without the cancellation of g vf^2 against g vf vo cos(d):
+      //   p_fr = g vf (vf - vo) + g vf vo (1 - cos d) - b vf vo sin d, and likewise for the others,
+      // with 1 - cos d = sin^2 d / (1 + cos d) while cos d > 0.
+      const Real dv = vf - vo;
+      const Real omc = cs > Real(0) ? sn * sn / (Real(1) + cs) : Real(1) - cs;
+      const Real hch = bc - bb;  // b_ch / 2
+      const Real pf = g * vf * dv + g * vv * omc - bb * vv * sn;
+      const Real pt = -g * vo * dv + g * vv * omc + bb * vv * sn;
+      const Real qf = -bb * vf * dv - hch * vf * vf - bb * vv * omc - g * vv * sn;
+      const Real qt = bb * vo * dv - hch * vo * vo - bb * vv * omc + g * vv * sn;
       const long long e = I.tm0 + (long long)t * I.M + j;
       d.pf[e] = pf;
       d.qf[e] = qf;
@@ -829,20 +834,39 @@ size_t ctg_smem_bytes(int T) {
   return sizeof(Real) * ((size_t)T * (3 * CT_BM + CT_BK) + 3 * CT_BM + 8 * CT_BK);
 }
 
+// Record a timing event on s; inside stream capture it becomes an external event node.
+static inline void mark(cudaEvent_t *ev, int k, cudaStream_t s) {
+  if (!ev) return;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &st);
+  if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal);
+  else cudaEventRecord(ev[k], s);
+}
+
 template <typename Real, typename Dc>
-cudaError_t launch_eval(const Dev<Real, Dc> &d, const Launch &L, const void *xv, int maxT) {
+cudaError_t launch_eval(const Dev<Real, Dc> &d, const Launch &L, const void *xv, int maxT, cudaEvent_t *ev) {
   const Real *x = static_cast<const Real *>(xv);
   cudaStream_t s = L.stream;
+  mark(ev, 0, s);
   k_fwd1<Real, Dc><<<L.n_fwd1, 256, 0, s>>>(d, L.blk_fwd1, x, L.obj_fwd1);
+  mark(ev, 1, s);
   k_fwd2<Real, Dc><<<L.n_fwd2, 256, 0, s>>>(d, L.blk_fwd2, x, L.obj_fwd2);
+  mark(ev, 2, s);
   k_dc<Real, Dc, false><<<L.n_dct, DC_ROWS * 32, 0, s>>>(d, L.dct);
+  mark(ev, 3, s);
   const size_t sm = ctg_smem_bytes<Real, Dc>(maxT);
   if (L.n_ctt > 0) k_ctg<Real, Dc><<<L.n_ctt, 256, sm, s>>>(d, L.ctt, L.obj_ctg, L.lodf_dtype);
+  mark(ev, 4, s);
   k_adj1<Real, Dc><<<L.n_adj1, 256, 0, s>>>(d, L.blk_adj1);
+  mark(ev, 5, s);
   k_dc<Real, Dc, true><<<L.n_dct, DC_ROWS * 32, 0, s>>>(d, L.dct);
+  mark(ev, 6, s);
   k_bwd1<Real, Dc><<<L.n_bwd1, 256, 0, s>>>(d, L.blk_bwd1, x);
+  mark(ev, 7, s);
   k_bwd2<Real, Dc><<<L.n_bwd2, 256, 0, s>>>(d, L.blk_bwd2, x, L.obj_bwd2);
+  mark(ev, 8, s);
   k_obj<Real, Dc><<<d.n_inst, 256, 0, s>>>(d, L.slot_inst, L.n_obj_slots);
+  mark(ev, 9, s);
   return cudaGetLastError();
 }
 
@@ -863,8 +887,10 @@ cudaError_t launch_adam(Real *x, Real *m, Real *v, const Real *g, const Real *lo
   return cudaGetLastError();
 }
 
-template cudaError_t launch_eval<double, double>(const Dev<double, double> &, const Launch &, const void *, int);
-template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Launch &, const void *, int);
+template cudaError_t launch_eval<double, double>(const Dev<double, double> &, const Launch &, const void *, int,
+                                                 cudaEvent_t *);
+template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Launch &, const void *, int,
+                                               cudaEvent_t *);
 template cudaError_t prepare_eval<double, double>(int);
 template cudaError_t prepare_eval<float, df32>(int);
 template cudaError_t launch_adam<double>(double *, double *, double *, const double *, const double *, const double *,

@@ -79,6 +79,8 @@ def _load():
         "qg_breakdown": (C.c_int, [vp, _F64P]),
         "qg_get_step": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "qg_set_step": (C.c_int, [vp, C.c_int64]),
+        "qg_set_profiling": (C.c_int, [vp, C.c_int]),
+        "qg_phase_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int32]),
         "qg_last_error": (C.c_char_p, [vp]),
         "qg_version": (C.c_int, []),
     }
@@ -92,7 +94,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_adam_step", "qg_solve", "qg_breakdown",
-            "qg_get_step", "qg_set_step", "qg_last_error", "qg_version")
+            "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_last_error", "qg_version")
+PHASES = ("fwd1", "fwd2", "dc_fwd", "ctg", "adj1", "dc_adj", "bwd1", "bwd2", "obj", "adam")
 
 
 class QGError(RuntimeError):
@@ -230,6 +233,18 @@ def qg_get_step(h: int) -> int:
 
 def qg_set_step(h: int, step: int) -> None:
     _check(_lib.qg_set_step(h, step), h)
+
+
+def qg_set_profiling(h: int, on: bool) -> None:
+    _check(_lib.qg_set_profiling(h, 1 if on else 0), h)
+
+
+def qg_phase_times(h: int) -> dict:
+    buf = (C.c_float * len(PHASES))()
+    n = _lib.qg_phase_times(h, buf, len(PHASES))
+    if n < 0:
+        _check(n, h)
+    return {PHASES[k]: float(buf[k]) for k in range(n)}
 
 
 def qg_last_error(h: Optional[int] = None) -> str:

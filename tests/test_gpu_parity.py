@@ -62,6 +62,10 @@ def gpu_eval(qg, cases, x, precision, lodf=0, **kw):
     return out
 
 
+def as_f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
 def rel(a, b):
     return abs(a - b) / max(abs(b), 1e-300)
 
@@ -89,8 +93,9 @@ def test_fp64_parity(qg, name, kind):
 @pytest.mark.parametrize("name,kind", [("tiny", "1"), ("mid", "lp_perturbed"), ("rt617", "lp"),
                                        ("rt617", "lp_perturbed")])
 def test_mixed_parity(qg, name, kind):
+    """The mixed path keeps x in FP32, so the oracle is evaluated at the same FP32-rounded point."""
     c = case_named(name)
-    x = point(c, kind)
+    x = as_f32(point(c, kind))
     check(gpu_eval(qg, c, x, qg.QG_MIXED), oracle.evaluate(c, x), TOL32)
 
 
@@ -107,7 +112,7 @@ def test_eps_zero_scoring_parity(qg):
 def test_ragged_batch_parity(qg):
     """Uneven instances in one handle: every instance matches its own oracle evaluation."""
     cases = [case_named("tiny"), case_named("mid"), case_named("b73"), synth.tiny(seed=5)]
-    xs = [point(c, str(10 + i)) for i, c in enumerate(cases)]
+    xs = [as_f32(point(c, str(10 + i))) for i, c in enumerate(cases)]
     for prec, tol in ((qg.QG_FP64, TOL64), (qg.QG_MIXED, TOL32)):
         obj, g, terms = gpu_eval(qg, cases, np.concatenate(xs), prec)
         o = 0
