@@ -5,8 +5,8 @@ projected Adam update, on the 617-bus / 18-period / 562-outage real-time shape.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one CUDA-graph replay of the nine evaluation kernels and the Adam
-kernel (qg_solve with one iteration).  L2 is flushed (a 512 MB write) before
+One step = one CUDA-graph replay of the five stage kernels of an evaluation
+with the projected Adam update fused into the last two (qg_solve, one iteration).  L2 is flushed (a 512 MB write) before
 every timed step; each step is timed with CUDA events on the launching stream.
 Rank 0 prints one JSON line.  With torchrun (N > 1) every rank runs an
 independent replica (the path has no exchange step) and the result is the sum
@@ -162,21 +162,21 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 
 def algorithmic(case, phase, mixed):
-    """(amount, unit, bound) of one launch of `phase` on `case`."""
+    """(amount, unit, bound) of the dominant role of one launch of stage `phase` on `case`."""
     T, n, M, G, K = case.T, case.n_bus, case.n_branch, case.n_gen, case.K
     rs = 4 if mixed else 8
-    if phase == "ctg":
-        # per (t, m, k): F = f_m + L f_k and F^2 + (qmax2 - s^2) -> 2 FMA = 4 flop
+    if phase == "s2":
+        # contingency tiles: per (t, m, k) F = f_m + L f_k and F^2 + (qmax2 - s^2): 2 FMA = 4 flop
         return 4.0 * T * M * K, "flop", "alu"
-    if phase in ("dc_fwd", "dc_adj"):
-        return 2.0 * n * n * T, "flop64", "alu"
+    if phase in ("s1", "s4"):
+        # DC products with the PTDF columns of the generator buses: T x M x Gb multiply-adds
+        return 2.0 * T * M * G, "flop64", "alu"
     if phase == "adam":
         return (9.0 * rs) * case.n_x, "byte", "hbm"
-    if phase in ("fwd1", "bwd1"):
-        return float(T * M * (4 * rs + 4 * rs + 3 * rs + 8)), "byte", "hbm"
-    if phase in ("fwd2", "adj1", "bwd2"):
-        return float(T * n * (6 * 4 * rs + 3 * rs) + T * G * 6 * rs), "byte", "hbm"
-    return 0.0, "byte", "hbm"
+    if phase == "s3":
+        nk = -(-K // 64)
+        return float(T * M * (2 * nk * rs + 10 * rs)), "byte", "hbm"
+    return float(T * G * 12 * rs), "byte", "hbm"
 
 
 def roofline(case, phase, ms, mixed, peaks, src, clocks):
@@ -310,7 +310,7 @@ def gpu_leg(args, rank, world, local_rank):
         "e2e": {"value": world * K / mix["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": 8 * case.n_x,
                 "d2h_bytes_per_step": 8 * (case.n_x + 1),
                 "call": "qg_eval_grad_host (pinned host x -> device, evaluation, objective + gradient -> host)"},
-        "gpu_launches": 10 * K,
+        "gpu_launches": 5 * K,
         "clocks": mix["clocks"],
         "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in phases.items()},
         "l2_resident": {"value": world / (mix["warm_ms"] * 1e-3), "unit": UNIT,

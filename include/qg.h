@@ -161,11 +161,13 @@ int qg_set_step(qg_ctx *h, int64_t step);
 
 /* Per-kernel timing (CUDA events, no profiler): when on, every evaluation and
  * Adam step records an event after each kernel, also inside qg_solve's graph.
- * qg_phase_times writes the durations in ms of the last evaluation's phases,
- * in launch order (fwd1, fwd2, dc_fwd, ctg, adj1, dc_adj, bwd1, bwd2, obj,
- * adam), up to cap entries, and returns how many it wrote (adam only when an
- * Adam step followed the evaluation), or a negative error code.  Waits for
- * those events. */
+ * qg_phase_times writes the durations in ms of the last evaluation's five
+ * stage kernels in launch order (s1: branch flows, zonal sums and base DC
+ * flows; s2: bus balance and contingencies; s3: contingency sums and branch
+ * adjoints; s4: bus adjoint gather and adjoint DC products; s5: generator
+ * gradients and the objective), then that of a stand-alone qg_adam_step if one
+ * followed, up to cap entries; returns how many it wrote or a negative error
+ * code.  Waits for those events. */
 int qg_set_profiling(qg_ctx *h, int on);
 int qg_phase_times(qg_ctx *h, float *ms, int32_t cap);
 

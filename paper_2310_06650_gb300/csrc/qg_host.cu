@@ -1,6 +1,7 @@
-// Host side of libqg: input validation, set-up of the network data, the dense
-// reduced-Laplacian inverse and the line-outage block, descriptor tables for
-// the kernels, and the C ABI declared in include/qg.h.
+// Host side of libqg: input validation, FP64 set-up of the DC network data
+// (reduced-Laplacian inverse, PTDF rows at generator buses, line-outage block),
+// warp-aligned CSR packs and block spans for the stage kernels, and the C ABI
+// declared in include/qg.h.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -23,20 +24,24 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int BLK = 256;
-constexpr int DENSE_MAX_N = 8192;  // dense Yhat^-1 is n^2 doubles
+constexpr int DENSE_MAX_N = 8192;  // the dense inverse used at set-up holds n^2 doubles
 
 struct HostInst {
-  // copies of the caller's arrays (double / int)
   int n, M, G, Z, T, K, ref;
   std::vector<int> from, to, gen_bus, gen_zone, ctg;
   std::vector<double> r, x, bch, smax, sctg, ca, cb, cr, pmin, pmax, qmin, qmax, ramp, vmin, vmax;
   std::vector<double> dt, load_p, load_q, rreq;
-  // derived
+  // derived (FP64)
   std::vector<double> y, gsr, bsr;
-  std::vector<double> zinv;  // n x n, ref row/col zero
-  std::vector<double> z1;    // n
-  std::vector<double> lodf;  // M x K
+  std::vector<int> gbus;      // distinct generator buses, ascending
+  std::vector<int> gen_gb;    // generator -> index into gbus
+  std::vector<double> ptdfg;  // M x Gb
+  std::vector<double> cload;  // T x M
+  std::vector<double> rsum;   // M
+  std::vector<double> ltot;   // T
+  std::vector<double> lodf;   // M x K
+  // warp packs (code, row) of the two bus CSRs
+  std::vector<int> bal_code, bal_row, adj_code, adj_row;
 };
 
 }  // namespace
@@ -45,25 +50,25 @@ struct qg_ctx {
   int n_inst = 0;
   qg_options opt{};
   std::vector<HostInst> hi;
-  std::vector<Inst> inst;
+  Plan plan{};
   long long n_x = 0;
-  int maxT = 0;
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
   Dev<double, double> d64{};
   Dev<float, df32> d32{};
-  Launch L{};
   double *d_obj = nullptr, *d_terms = nullptr;
   void *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
-  void *d_xs = nullptr;     // staging for qg_eval_grad_host (Real)
-  double *d_xd = nullptr;   // staging doubles (mixed mode conversions)
-  long long *d_step = nullptr;
-  // cached CUDA graph of one (eval + Adam) iteration for qg_solve
+  void *d_xs = nullptr;    // staging for qg_eval_grad_host (Real)
+  double *d_xd = nullptr;  // staging doubles
+  long long *d_step = nullptr, *d_step0 = nullptr;
+  unsigned int *d_ticket = nullptr;
+  // cached CUDA graph of one (evaluation + fused Adam) iteration for qg_solve
   cudaGraphExec_t gexec = nullptr;
   const void *g_x = nullptr;
   double g_lr = 0, g_b1 = 0, g_b2 = 0;
   double *g_trace = nullptr;
-  // optional per-kernel timing: ev[0..9] bracket the nine evaluation kernels, ev[10] ends Adam
+  int g_trace_len = 0;
+  // optional per-kernel timing: ev[0..5] bracket the five stage kernels, ev[6] ends a stand-alone Adam step
   bool profiling = false;
   cudaEvent_t ev[N_PHASES + 1] = {};
   std::string err;
@@ -77,9 +82,9 @@ int fail(qg_ctx *h, int code, const std::string &msg) {
   return code;
 }
 
-#define CUDA_TRY(h, call)                                                                 \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
+#define CUDA_TRY(h, call)                                                                                      \
+  do {                                                                                                         \
+    cudaError_t e_ = (call);                                                                                   \
     if (e_ != cudaSuccess) return fail((h), QG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
@@ -90,6 +95,8 @@ int dalloc(qg_ctx *h, T **p, size_t count) {
   cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   h->allocs.push_back(*p);
+  e = cudaMemset(*p, 0, count * sizeof(T));
+  if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
   return QG_OK;
 }
 
@@ -160,12 +167,37 @@ int read_instance(qg_ctx *h, const qg_network &N, const qg_horizon &H, const qg_
   return QG_OK;
 }
 
-// DC network set-up (Sec. II-E): y_j = -b_sr = x / (r^2 + x^2); reduced Laplacian with the
-// reference bus removed; Yhat^-1 columns by sparse LDL^T solves; line-outage block
-//   L[m,k] = y_m (u_k[f_m] - u_k[o_m]) / (1 - y_k (u_k[f_k] - u_k[o_k])),  u_k = Yhat^-1 a_k,
-// which is the rank-1 SMW correction of Eq. rank_correct expressed on branch flows.
+// Warp packs of a bus CSR: rows (buses) in order, each row's entries contiguous and never
+// straddling a pack of PACK lanes; unused lanes are pads (code kind 3, row -1).
+bool pack_rows(const std::vector<std::vector<int>> &rows, std::vector<int> &code, std::vector<int> &row) {
+  code.clear();
+  row.clear();
+  int fill = 0;
+  for (size_t i = 0; i < rows.size(); ++i) {
+    const int len = (int)rows[i].size();
+    if (len > PACK) return false;
+    if (fill + len > PACK) {
+      for (; fill < PACK; ++fill) { code.push_back(3); row.push_back(-1); }
+      fill = 0;
+    }
+    for (int c : rows[i]) { code.push_back(c); row.push_back((int)i); }
+    fill += len;
+    if (fill == PACK) fill = 0;
+  }
+  if (fill > 0)
+    for (; fill < PACK; ++fill) { code.push_back(3); row.push_back(-1); }
+  return true;
+}
+
+// DC network set-up (Sec. II-E), all in FP64:
+//   y_j = -b_sr = x / (r^2 + x^2);  Yhat = E_hat^T Y_x E_hat (reference bus removed);
+//   Z = Yhat^-1 (zero row and column at the reference bus), from sparse LDL^T solves;
+//   PTDF[m, i] = y_m (Z[f_m, i] - Z[o_m, i]) (flow on m per unit injection at i, withdrawn at the reference);
+//   line-outage block L[m, k] = PTDF u_k / (1 - PTDF_kk), u_k = Z (e_f - e_o): the rank-1 SMW
+//   correction of Eq. rank_correct written on branch flows.
+// Kept for the kernels: PTDF columns of the generator buses, PTDF load_t and PTDF 1.
 int build_dc(qg_ctx *h, HostInst &I, int b) {
-  const int n = I.n, M = I.M, K = I.K;
+  const int n = I.n, M = I.M, K = I.K, T = I.T;
   I.y.resize(M); I.gsr.resize(M); I.bsr.resize(M);
   for (int j = 0; j < M; ++j) {
     const double den = I.r[j] * I.r[j] + I.x[j] * I.x[j];
@@ -173,7 +205,6 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
     I.gsr[j] = I.r[j] / den;
     I.bsr[j] = -I.x[j] / den;
   }
-  // reduced index: bus i -> i' (ref removed)
   std::vector<int> red(n, -1);
   int c = 0;
   for (int i = 0; i < n; ++i)
@@ -195,44 +226,66 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
     return fail(h, QG_ERR_ISLANDING, "instance " + std::to_string(b) + ": the DC Laplacian is singular (disconnected grid)");
   if (n > DENSE_MAX_N)
     return fail(h, QG_ERR_UNSUPPORTED, "instance " + std::to_string(b) + ": n = " + std::to_string(n) +
-                                           " exceeds the dense-inverse limit " + std::to_string(DENSE_MAX_N));
-  // dense inverse (n x n, zero ref row and column), columns by solves
-  I.zinv.assign((size_t)n * n, 0.0);
+                                           " exceeds the dense set-up limit " + std::to_string(DENSE_MAX_N));
+  std::vector<double> Zm((size_t)n * n, 0.0);
   std::vector<double> col(nr);
   for (int cc = 0; cc < nr; ++cc) {
     std::fill(col.begin(), col.end(), 0.0);
     col[cc] = 1.0;
     F.solve(col.data());
-    // bus id of reduced column cc
     const int bc = cc < I.ref ? cc : cc + 1;
-    for (int rr = 0; rr < nr; ++rr) {
-      const int br = rr < I.ref ? rr : rr + 1;
-      I.zinv[(size_t)br * n + bc] = col[rr];
-    }
+    for (int rr = 0; rr < nr; ++rr) Zm[(size_t)(rr < I.ref ? rr : rr + 1) * n + bc] = col[rr];
   }
-  // symmetrize (the two triangles agree to rounding; keep one value for bitwise symmetry)
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j) {
-      const double v = 0.5 * (I.zinv[(size_t)i * n + j] + I.zinv[(size_t)j * n + i]);
-      I.zinv[(size_t)i * n + j] = v;
-      I.zinv[(size_t)j * n + i] = v;
+      const double v = 0.5 * (Zm[(size_t)i * n + j] + Zm[(size_t)j * n + i]);
+      Zm[(size_t)i * n + j] = v;
+      Zm[(size_t)j * n + i] = v;
     }
-  I.z1.assign(n, 0.0);
-  for (int i = 0; i < n; ++i) {
+  // generator buses
+  std::vector<int> gmap(n, -1);
+  I.gbus.clear();
+  for (int g = 0; g < I.G; ++g) gmap[I.gen_bus[g]] = 0;
+  for (int i = 0; i < n; ++i)
+    if (gmap[i] == 0) {
+      gmap[i] = (int)I.gbus.size();
+      I.gbus.push_back(i);
+    }
+  I.gen_gb.resize(I.G);
+  for (int g = 0; g < I.G; ++g) I.gen_gb[g] = gmap[I.gen_bus[g]];
+  const int Gb = (int)I.gbus.size();
+  // PTDF rows: generator-bus columns, load products and row sums
+  I.ptdfg.assign((size_t)M * Gb, 0.0);
+  I.cload.assign((size_t)T * M, 0.0);
+  I.rsum.assign(M, 0.0);
+  std::vector<double> row(n);
+  for (int m = 0; m < M; ++m) {
+    const double *zf = &Zm[(size_t)I.from[m] * n], *zo = &Zm[(size_t)I.to[m] * n];
     double s = 0.0;
-    for (int j = 0; j < n; ++j) s += I.zinv[(size_t)i * n + j];
-    I.z1[i] = s;
+    for (int i = 0; i < n; ++i) {
+      row[i] = I.y[m] * (zf[i] - zo[i]);
+      s += row[i];
+    }
+    I.rsum[m] = s;
+    for (int q = 0; q < Gb; ++q) I.ptdfg[(size_t)m * Gb + q] = row[I.gbus[q]];
+    for (int t = 0; t < T; ++t) {
+      const double *lp = &I.load_p[(size_t)t * n];
+      double a = 0.0;
+      for (int i = 0; i < n; ++i) a += row[i] * lp[i];
+      I.cload[(size_t)t * M + m] = a;
+    }
   }
+  I.ltot.assign(T, 0.0);
+  for (int t = 0; t < T; ++t)
+    for (int i = 0; i < n; ++i) I.ltot[t] += I.load_p[(size_t)t * n + i];
   // line-outage block
   I.lodf.assign((size_t)M * K, 0.0);
   std::vector<int> bad_k;
   for (int k = 0; k < K; ++k) {
     const int jk = I.ctg[k];
-    // u_k = Z (e_f - e_o), read from the dense inverse
     const int fk = I.from[jk], ok = I.to[jk];
-    auto u = [&](int bus) { return I.zinv[(size_t)bus * n + fk] - I.zinv[(size_t)bus * n + ok]; };
-    const double ptdf_kk = I.y[jk] * (u(fk) - u(ok));
-    const double den = 1.0 - ptdf_kk;
+    auto u = [&](int bus) { return Zm[(size_t)bus * n + fk] - Zm[(size_t)bus * n + ok]; };
+    const double den = 1.0 - I.y[jk] * (u(fk) - u(ok));
     if (std::fabs(den) < 1e-9) {
       bad_k.push_back(jk);
       continue;
@@ -245,6 +298,17 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
     s += " islands the grid (|1 - PTDF_kk| < 1e-9)";
     return fail(h, QG_ERR_ISLANDING, s);
   }
+  // bus CSR packs: balance (branch ends, then generators) and branch-end adjoints
+  std::vector<std::vector<int>> bal(n), adj(n);
+  for (int j = 0; j < M; ++j) {
+    bal[I.from[j]].push_back(j << 2 | 0);
+    bal[I.to[j]].push_back(j << 2 | 1);
+    adj[I.from[j]].push_back(j << 2 | 0);
+    adj[I.to[j]].push_back(j << 2 | 1);
+  }
+  for (int g = 0; g < I.G; ++g) bal[I.gen_bus[g]].push_back(g << 2 | 2);
+  if (!pack_rows(bal, I.bal_code, I.bal_row) || !pack_rows(adj, I.adj_code, I.adj_row))
+    return fail(h, QG_ERR_UNSUPPORTED, "instance " + std::to_string(b) + ": a bus has more than 32 incident entries");
   return QG_OK;
 }
 
@@ -271,128 +335,185 @@ std::vector<df32> to_dc<df32>(const std::vector<double> &v) {
   return o;
 }
 
+void add_span(Spans &S, int per_t, int nt, int inst, int role) {
+  if (per_t <= 0 || nt <= 0) return;
+  Span &s = S.s[S.n++];
+  s.first = S.n_blocks;
+  s.per_t = per_t;
+  s.nt = nt;
+  s.inst = inst;
+  s.role = role;
+  S.n_blocks += per_t * nt;
+}
+
+int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Instance table, spans of the five stage kernels and objective-slot owners.
+int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
+  Plan &P = h->plan;
+  const int B = h->n_inst;
+  std::memset(&P, 0, sizeof(P));
+  P.tab.n_inst = B;
+  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0, sp0 = 0;
+  int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
+  for (int b = 0; b < B; ++b) {
+    const HostInst &H = h->hi[b];
+    Inst &D = P.tab.I[b];
+    D.n = H.n; D.M = H.M; D.G = H.G; D.Z = H.Z; D.T = H.T; D.K = H.K; D.Gb = (int)H.gbus.size();
+    D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.gb0 = gb0; D.tp0 = tp0;
+    D.n_mt = ceil_div(H.M, CT_BM);
+    D.n_kt = ceil_div(H.K, CT_BK);
+    D.n_mch = ceil_div(H.M, DCA_BM);
+    D.n_sb = ceil_div(H.M, NTHR);
+    D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
+    D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
+    D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
+    D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0; D.sp0 = sp0;
+    D.inv_n = 1.0 / H.n;
+    D.wfloor_ctg = h->opt.c_s * h->opt.beta * h->opt.eps * ((double)H.M * H.K - H.K);
+    x0 += (long long)H.T * (2LL * H.n + 3LL * H.G);
+    tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
+    tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gb; l0 += (long long)H.M * H.K;
+    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mt * H.T * H.K; gi0 += (long long)D.n_mch * H.T * D.Gb;
+    sp0 += (long long)H.T * D.n_sb;
+    bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.K; gb0 += D.Gb; tp0 += H.T;
+    bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
+    P.maxT = std::max(P.maxT, H.T);
+  }
+  P.n_x = x0;
+  auto &I = P.tab.I;
+  // roles with the longest blocks first in each launch
+  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, DCF_BM), ceil_div(I[b].T, DCF_TC), b, R_DCF);
+  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, NTHR), I[b].T, b, R_BRANCH);
+  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].Z, NTHR), I[b].T, b, R_ZONE);
+  for (int b = 0; b < B; ++b) add_span(P.s2, I[b].n_mt * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
+  for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
+  for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
+  for (int b = 0; b < B; ++b) add_span(P.s4, I[b].n_mch, ceil_div(I[b].T, DCA_TC), b, R_DCA);
+  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
+  for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].G, NTHR), I[b].T, b, R_GEN);
+  // objective slots: blocks of s1, then s2, then s5
+  slot_inst.clear();
+  for (const Spans *S : {&P.s1, &P.s2, &P.s5})
+    for (int k = 0; k < S->n; ++k)
+      for (int q = 0; q < S->s[k].per_t * S->s[k].nt; ++q) slot_inst.push_back(S->s[k].inst);
+  return QG_OK;
+}
+
 // Build every device array of one precision flavour.
 template <typename Real, typename Dc>
-int build_device(qg_ctx *h, Dev<Real, Dc> &d) {
+int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst) {
   const int B = h->n_inst;
-  std::vector<Inst> &inst = h->inst;
-  // global arrays
-  std::vector<int> br_from, br_to, br_kidx, gen_bus, gen_zone, inc_ptr{0}, inc, bgen_ptr{0}, bgen, zgen_ptr{0}, zgen, ctg_br;
-  std::vector<double> br_g, br_b, br_bc, br_smax, br_sctg, br_y, ga, gb, gcr, gpmax, gramp, load_p, load_q, rreq, dt, lo, hi;
-  std::vector<double> zinv, z1;
-  std::vector<double> lodf;
+  const Plan &P = h->plan;
+  std::vector<int2> br_end;
+  std::vector<int> br_kidx, gen_bus, gen_zone, gen_gb, gb_ptr{0}, gb_gen, zgen_ptr{0}, zgen, ctg_br, bal_code, bal_row,
+      adj_code, adj_row;
+  std::vector<double> br_g, br_b, br_hch, br_smax, br_s2, ga, gbv, gcr, gpmax, gramp, load_p, load_q, rreq, dt, lo, hi,
+      ltot, ptdfg, cload, rsum, lodf;
   for (int b = 0; b < B; ++b) {
-    const HostInst &I = h->hi[b];
-    const Inst &D = inst[b];
-    for (int j = 0; j < I.M; ++j) {
-      br_from.push_back(D.bus0 + I.from[j]);
-      br_to.push_back(D.bus0 + I.to[j]);
+    const HostInst &H = h->hi[b];
+    const Inst &D = P.tab.I[b];
+    for (int j = 0; j < H.M; ++j) {
+      br_end.push_back(make_int2(H.from[j], H.to[j]));
       br_kidx.push_back(-1);
-      br_g.push_back(I.gsr[j]);
-      br_b.push_back(I.bsr[j]);
-      br_bc.push_back(I.bsr[j] + 0.5 * I.bch[j]);
-      br_smax.push_back(I.smax[j]);
-      br_sctg.push_back(I.sctg[j]);
-      br_y.push_back(I.y[j]);
+      br_g.push_back(H.gsr[j]);
+      br_b.push_back(H.bsr[j]);
+      br_hch.push_back(0.5 * H.bch[j]);
+      br_smax.push_back(H.smax[j]);
+      br_s2.push_back(H.sctg[j] * H.sctg[j]);
     }
-    for (int k = 0; k < I.K; ++k) {
-      br_kidx[D.br0 + I.ctg[k]] = k;
-      ctg_br.push_back(D.br0 + I.ctg[k]);
+    for (int k = 0; k < H.K; ++k) {
+      br_kidx[D.br0 + H.ctg[k]] = k;
+      ctg_br.push_back(H.ctg[k]);
     }
-    for (int g = 0; g < I.G; ++g) {
-      gen_bus.push_back(D.bus0 + I.gen_bus[g]);
-      gen_zone.push_back(D.zone0 + I.gen_zone[g]);
-      ga.push_back(I.ca[g]); gb.push_back(I.cb[g]); gcr.push_back(I.cr[g]); gpmax.push_back(I.pmax[g]);
-      gramp.push_back(I.ramp[g]);
+    for (int g = 0; g < H.G; ++g) {
+      gen_bus.push_back(H.gen_bus[g]);
+      gen_zone.push_back(H.gen_zone[g]);
+      gen_gb.push_back(H.gen_gb[g]);
+      ga.push_back(H.ca[g]); gbv.push_back(H.cb[g]); gcr.push_back(H.cr[g]); gpmax.push_back(H.pmax[g]);
+      gramp.push_back(H.ramp[g]);
     }
-    // CSR: bus -> branch ends, bus -> generators (entries in branch / generator order)
-    std::vector<std::vector<int>> ends(I.n), gens(I.n), zg(I.Z);
-    for (int j = 0; j < I.M; ++j) {
-      ends[I.from[j]].push_back(((D.br0 + j) << 1) | 0);
-      ends[I.to[j]].push_back(((D.br0 + j) << 1) | 1);
+    std::vector<std::vector<int>> gbg(H.gbus.size()), zg(H.Z);
+    for (int g = 0; g < H.G; ++g) {
+      gbg[H.gen_gb[g]].push_back(D.gen0 + g);
+      zg[H.gen_zone[g]].push_back(D.gen0 + g);
     }
-    for (int g = 0; g < I.G; ++g) {
-      gens[I.gen_bus[g]].push_back(D.gen0 + g);
-      zg[I.gen_zone[g]].push_back(D.gen0 + g);
+    for (auto &v : gbg) {
+      gb_gen.insert(gb_gen.end(), v.begin(), v.end());
+      gb_ptr.push_back((int)gb_gen.size());
     }
-    for (int i = 0; i < I.n; ++i) {
-      inc.insert(inc.end(), ends[i].begin(), ends[i].end());
-      inc_ptr.push_back((int)inc.size());
-      bgen.insert(bgen.end(), gens[i].begin(), gens[i].end());
-      bgen_ptr.push_back((int)bgen.size());
-    }
-    for (int z = 0; z < I.Z; ++z) {
-      zgen.insert(zgen.end(), zg[z].begin(), zg[z].end());
+    for (auto &v : zg) {
+      zgen.insert(zgen.end(), v.begin(), v.end());
       zgen_ptr.push_back((int)zgen.size());
     }
-    load_p.insert(load_p.end(), I.load_p.begin(), I.load_p.end());
-    load_q.insert(load_q.end(), I.load_q.begin(), I.load_q.end());
-    rreq.insert(rreq.end(), I.rreq.begin(), I.rreq.end());
-    dt.insert(dt.end(), I.dt.begin(), I.dt.end());
-    zinv.insert(zinv.end(), I.zinv.begin(), I.zinv.end());
-    z1.insert(z1.end(), I.z1.begin(), I.z1.end());
-    lodf.insert(lodf.end(), I.lodf.begin(), I.lodf.end());
-    // clip box: v, theta (ref pinned at 0), p, q, r
+    bal_code.insert(bal_code.end(), H.bal_code.begin(), H.bal_code.end());
+    bal_row.insert(bal_row.end(), H.bal_row.begin(), H.bal_row.end());
+    adj_code.insert(adj_code.end(), H.adj_code.begin(), H.adj_code.end());
+    adj_row.insert(adj_row.end(), H.adj_row.begin(), H.adj_row.end());
+    load_p.insert(load_p.end(), H.load_p.begin(), H.load_p.end());
+    load_q.insert(load_q.end(), H.load_q.begin(), H.load_q.end());
+    rreq.insert(rreq.end(), H.rreq.begin(), H.rreq.end());
+    dt.insert(dt.end(), H.dt.begin(), H.dt.end());
+    ltot.insert(ltot.end(), H.ltot.begin(), H.ltot.end());
+    ptdfg.insert(ptdfg.end(), H.ptdfg.begin(), H.ptdfg.end());
+    cload.insert(cload.end(), H.cload.begin(), H.cload.end());
+    rsum.insert(rsum.end(), H.rsum.begin(), H.rsum.end());
+    lodf.insert(lodf.end(), H.lodf.begin(), H.lodf.end());
     const double inf = INFINITY;
-    for (int t = 0; t < I.T; ++t)
-      for (int i = 0; i < I.n; ++i) { lo.push_back(I.vmin[i]); hi.push_back(I.vmax[i]); }
-    for (int t = 0; t < I.T; ++t)
-      for (int i = 0; i < I.n; ++i) {
-        lo.push_back(i == I.ref ? 0.0 : -inf);
-        hi.push_back(i == I.ref ? 0.0 : inf);
+    for (int t = 0; t < H.T; ++t)
+      for (int i = 0; i < H.n; ++i) { lo.push_back(H.vmin[i]); hi.push_back(H.vmax[i]); }
+    for (int t = 0; t < H.T; ++t)
+      for (int i = 0; i < H.n; ++i) {
+        lo.push_back(i == H.ref ? 0.0 : -inf);
+        hi.push_back(i == H.ref ? 0.0 : inf);
       }
-    for (int t = 0; t < I.T; ++t)
-      for (int g = 0; g < I.G; ++g) { lo.push_back(I.pmin[g]); hi.push_back(I.pmax[g]); }
-    for (int t = 0; t < I.T; ++t)
-      for (int g = 0; g < I.G; ++g) { lo.push_back(I.qmin[g]); hi.push_back(I.qmax[g]); }
-    for (int t = 0; t < I.T; ++t)
-      for (int g = 0; g < I.G; ++g) { lo.push_back(0.0); hi.push_back(I.pmax[g]); }
+    for (int t = 0; t < H.T; ++t)
+      for (int g = 0; g < H.G; ++g) { lo.push_back(H.pmin[g]); hi.push_back(H.pmax[g]); }
+    for (int t = 0; t < H.T; ++t)
+      for (int g = 0; g < H.G; ++g) { lo.push_back(H.qmin[g]); hi.push_back(H.qmax[g]); }
+    for (int t = 0; t < H.T; ++t)
+      for (int g = 0; g < H.G; ++g) { lo.push_back(0.0); hi.push_back(H.pmax[g]); }
   }
   int rc = 0;
-  Inst *dinst;
-  if ((rc = upload(h, &dinst, inst))) return rc;
-  d.inst = dinst;
-  d.n_inst = B;
+  {
+    int2 *p2;
+    if ((rc = upload(h, &p2, br_end))) return rc;
+    d.br_end = p2;
+  }
   int *p;
   Real *r;
   Dc *z;
 #define UPI(field, vec) if ((rc = upload(h, &p, vec))) return rc; d.field = p;
 #define UPR(field, vec) { auto tmp_ = cast<Real>(vec); if ((rc = upload(h, &r, tmp_))) return rc; d.field = r; }
-  UPI(br_from, br_from) UPI(br_to, br_to) UPI(br_kidx, br_kidx) UPI(gen_bus, gen_bus) UPI(gen_zone, gen_zone)
-  UPI(inc_ptr, inc_ptr) UPI(inc, inc) UPI(bgen_ptr, bgen_ptr) UPI(bgen, bgen) UPI(zgen_ptr, zgen_ptr) UPI(zgen, zgen)
-  UPI(ctg_br, ctg_br)
-  UPR(br_g, br_g) UPR(br_b, br_b) UPR(br_bc, br_bc) UPR(br_smax, br_smax) UPR(br_sctg, br_sctg) UPR(br_y, br_y)
-  UPR(gen_a, ga) UPR(gen_b, gb) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax) UPR(gen_ramp, gramp)
+#define UPD(field, vec) { auto tmp_ = to_dc<Dc>(vec); if ((rc = upload(h, &z, tmp_))) return rc; d.field = z; }
+  UPI(br_kidx, br_kidx) UPI(gen_bus, gen_bus) UPI(gen_zone, gen_zone) UPI(gen_gb, gen_gb) UPI(gb_ptr, gb_ptr)
+  UPI(gb_gen, gb_gen) UPI(zgen_ptr, zgen_ptr) UPI(zgen, zgen) UPI(ctg_br, ctg_br) UPI(bal_code, bal_code)
+  UPI(bal_row, bal_row) UPI(adj_code, adj_code) UPI(adj_row, adj_row)
+  UPR(br_g, br_g) UPR(br_b, br_b) UPR(br_hch, br_hch) UPR(br_smax, br_smax) UPR(br_s2ctg, br_s2)
+  UPR(gen_a, ga) UPR(gen_b, gbv) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax) UPR(gen_ramp, gramp)
   UPR(load_p, load_p) UPR(load_q, load_q) UPR(rreq, rreq) UPR(dt, dt) UPR(lo, lo) UPR(hi, hi)
+  UPD(ltot, ltot) UPD(ptdfg, ptdfg) UPD(cload, cload) UPD(rsum, rsum)
 #undef UPI
 #undef UPR
-  {
-    auto zz = to_dc<Dc>(zinv);
-    if ((rc = upload(h, &z, zz))) return rc;
-    d.zinv = z;
-    auto z1d = to_dc<Dc>(z1);
-    if ((rc = upload(h, &z, z1d))) return rc;
-    d.z1 = z;
-  }
-  // line-outage block in the requested storage type
-  if (sizeof(Real) == 8) {
-    double *q;
-    if ((rc = upload(h, &q, lodf))) return rc;
-    d.lodf = q;
-  } else if (h->opt.lodf_dtype == QG_LODF_BF16) {
+#undef UPD
+  // line-outage block: the arithmetic copy of the mixed path (FP32 / BF16 / BF16 hi+lo), or the
+  // FP32 screening copy plus the exact FP64 copy of the FP64 path
+  const bool f64 = sizeof(Real) == 8;
+  const int dtype = f64 ? QG_LODF_F32 : h->opt.lodf_dtype;
+  d.lodf_dtype = dtype;
+  if (dtype == QG_LODF_BF16) {
     std::vector<__nv_bfloat16> v(lodf.size());
     for (size_t i = 0; i < v.size(); ++i) v[i] = __float2bfloat16_rn((float)lodf[i]);
     __nv_bfloat16 *q;
     if ((rc = upload(h, &q, v))) return rc;
     d.lodf = q;
-  } else if (h->opt.lodf_dtype == QG_LODF_BF16X2) {
+  } else if (dtype == QG_LODF_BF16X2) {
     std::vector<__nv_bfloat162> v(lodf.size());
     for (size_t i = 0; i < v.size(); ++i) {
       const float f = (float)lodf[i];
       const __nv_bfloat16 hb = __float2bfloat16_rn(f);
-      const __nv_bfloat16 lb = __float2bfloat16_rn(f - __bfloat162float(hb));
       v[i].x = hb;
-      v[i].y = lb;
+      v[i].y = __float2bfloat16_rn(f - __bfloat162float(hb));
     }
     __nv_bfloat162 *q;
     if ((rc = upload(h, &q, v))) return rc;
@@ -403,84 +524,55 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d) {
     if ((rc = upload(h, &q, v))) return rc;
     d.lodf = q;
   }
-  d.c_p = (Real)h->opt.c_p; d.c_q = (Real)h->opt.c_q; d.c_s = (Real)h->opt.c_s; d.c_rz = (Real)h->opt.c_rz;
-  d.rho = (Real)h->opt.rho; d.eps = (Real)h->opt.eps; d.beta = (Real)h->opt.beta;
+  if (f64) {
+    double *q;
+    if ((rc = upload(h, &q, lodf))) return rc;
+    d.lodf64 = q;
+  }
+  const qg_options &o = h->opt;
+  d.c_p = (Real)o.c_p; d.c_q = (Real)o.c_q; d.c_s = (Real)o.c_s; d.c_rz = (Real)o.c_rz;
+  d.rho = (Real)o.rho; d.eps = (Real)o.eps; d.beta = (Real)o.beta;
   // work buffers
-  long long sTM = 0, sTn = 0, sTZ = 0, sIB = 0, sPM = 0, sPK = 0;
-  for (const Inst &I : inst) {
+  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0, sSP = 0;
+  for (int b = 0; b < B; ++b) {
+    const Inst &I = P.tab.I[b];
     sTM += (long long)I.T * I.M; sTn += (long long)I.T * I.n; sTZ += (long long)I.T * I.Z;
-    sIB += (long long)I.T * I.n_ib; sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mt * I.T * I.K;
+    sTK += (long long)I.T * I.K; sTG += (long long)I.T * I.G;
+    sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mt * I.T * I.K;
+    sGI += (long long)I.n_mch * I.T * I.Gb; sSP += (long long)I.T * I.n_sb;
   }
   Real *w;
   Dc *c;
+  float *fl;
 #define WR(field, cnt) if ((rc = dalloc(h, &w, (size_t)(cnt)))) return rc; d.field = w;
 #define WD(field, cnt) if ((rc = dalloc(h, &c, (size_t)(cnt)))) return rc; d.field = c;
-  WR(pf, sTM) WR(qf, sTM) WR(pt, sTM) WR(qt, sTM) WR(qm2, sTM) WR(dP, sTn) WR(dQ, sTn) WR(dZ, sTZ)
-  WR(pm, sPM) WR(pq, sPM) WR(pk, sPK) WR(avf, sTM) WR(avo, sTM) WR(ad, sTM)
-  WD(pinj, sTn) WD(th, sTn) WD(w, sTn) WD(ginj, sTn) WD(mupart, sIB) WD(spart, sIB)
+#define WF(field, cnt) if ((rc = dalloc(h, &fl, (size_t)(cnt)))) return rc; d.field = fl;
+  WR(pf, sTM) WR(qf, sTM) WR(pt, sTM) WR(qt, sTM) WR(qm2, sTM) WR(fre, sTM) WR(fk, sTK) WR(pold, sTG)
+  WR(dP, sTn) WR(dQ, sTn) WR(dZ, sTZ) WR(pm, sPM) WR(pq, sPM) WR(pk, sPK) WR(gF, sTM) WR(avf, sTM) WR(avo, sTM)
+  WR(ad, sTM)
+  WD(spart, sSP) WD(gip, sGI)
+  WF(f32, sTM) WF(fk32, sTK)
 #undef WR
 #undef WD
+#undef WF
   unsigned char *qs;
   if ((rc = dalloc(h, &qs, (size_t)sTM))) return rc;
   d.qside = qs;
   double *op;
-  if ((rc = dalloc(h, &op, (size_t)h->L.n_obj_slots * N_TERMS))) return rc;
+  d.n_obj_slots = (int)slot_inst.size();
+  if ((rc = dalloc(h, &op, (size_t)d.n_obj_slots * N_TERMS))) return rc;
   d.objp = op;
+  int *si;
+  if ((rc = upload(h, &si, slot_inst))) return rc;
+  d.slot_inst = si;
   d.obj = h->d_obj;
   d.terms = h->d_terms;
   d.g = static_cast<Real *>(h->d_g);
+  d.ticket = h->d_ticket;
   d.step = h->d_step;
-  return QG_OK;
-}
-
-int build_tables(qg_ctx *h) {
-  std::vector<Blk> fwd1, fwd2, bus, bwd1, bwd2;
-  std::vector<DcTile> dct;
-  std::vector<CtgTile> ctt;
-  for (int b = 0; b < h->n_inst; ++b) {
-    const Inst &I = h->inst[b];
-    for (int t = 0; t < I.T; ++t) {
-      for (int j0 = 0; j0 < I.M; j0 += BLK) fwd1.push_back({R_BRANCH, b, t, j0, 0});
-      for (int z0 = 0; z0 < I.Z; z0 += BLK) fwd1.push_back({R_ZONE, b, t, z0, 0});
-      int ib = 0;
-      for (int i0 = 0; i0 < I.n; i0 += BLK, ++ib) bus.push_back({R_BUS, b, t, i0, ib});
-      for (int g0 = 0; g0 < I.G; g0 += BLK) bwd2.push_back({R_GEN, b, t, g0, 0});
-    }
-    for (int i0 = 0; i0 < I.n; i0 += 4) dct.push_back({b, i0});
-    for (int mt = 0; mt < I.n_mt; ++mt)
-      for (int kt = 0; kt < I.n_kt; ++kt) ctt.push_back({b, mt * 64, kt * 64, mt, kt});
-  }
-  fwd2 = bus;
-  for (const Blk &x : fwd1)
-    if (x.role == R_BRANCH) bwd1.push_back(x);
-  std::vector<Blk> b2 = bus;
-  b2.insert(b2.end(), bwd2.begin(), bwd2.end());
-  bwd2 = b2;
-  int rc;
-  Blk *p;
-  if ((rc = upload(h, &p, fwd1))) return rc; h->L.blk_fwd1 = p; h->L.n_fwd1 = (int)fwd1.size();
-  if ((rc = upload(h, &p, fwd2))) return rc; h->L.blk_fwd2 = p; h->L.n_fwd2 = (int)fwd2.size();
-  if ((rc = upload(h, &p, bus))) return rc; h->L.blk_adj1 = p; h->L.n_adj1 = (int)bus.size();
-  if ((rc = upload(h, &p, bwd1))) return rc; h->L.blk_bwd1 = p; h->L.n_bwd1 = (int)bwd1.size();
-  if ((rc = upload(h, &p, bwd2))) return rc; h->L.blk_bwd2 = p; h->L.n_bwd2 = (int)bwd2.size();
-  DcTile *q;
-  if ((rc = upload(h, &q, dct))) return rc; h->L.dct = q; h->L.n_dct = (int)dct.size();
-  CtgTile *cq;
-  if ((rc = upload(h, &cq, ctt))) return rc; h->L.ctt = cq; h->L.n_ctt = (int)ctt.size();
-  // objective slots: one per block of fwd1, fwd2, ctg, bwd2
-  std::vector<int> slot_inst;
-  h->L.obj_fwd1 = (int)slot_inst.size();
-  for (auto &x : fwd1) slot_inst.push_back(x.inst);
-  h->L.obj_fwd2 = (int)slot_inst.size();
-  for (auto &x : fwd2) slot_inst.push_back(x.inst);
-  h->L.obj_ctg = (int)slot_inst.size();
-  for (auto &x : ctt) slot_inst.push_back(x.inst);
-  h->L.obj_bwd2 = (int)slot_inst.size();
-  for (auto &x : bwd2) slot_inst.push_back(x.inst);
-  h->L.n_obj_slots = (int)slot_inst.size();
-  int *si;
-  if ((rc = upload(h, &si, slot_inst))) return rc;
-  h->L.slot_inst = si;
+  d.trace_step0 = h->d_step0;
+  d.am = static_cast<Real *>(h->d_m);
+  d.av = static_cast<Real *>(h->d_v);
   return QG_OK;
 }
 
@@ -509,11 +601,23 @@ void free_all(qg_ctx *h) {
 
 bool mixed(const qg_ctx *h) { return h->opt.precision == QG_MIXED; }
 
-int run_eval(qg_ctx *h, const void *x) {
+// One evaluation; with adam, the projected Adam update is fused into stages 4 and 5 using the
+// handle's moments and the given hyper-parameters.
+int run_eval(qg_ctx *h, const void *x, bool adam, double lr, double b1, double b2, double *trace, int trace_len) {
   cudaEvent_t *ev = h->profiling ? h->ev : nullptr;
-  cudaError_t e = mixed(h) ? launch_eval<float, df32>(h->d32, h->L, x, h->maxT, ev)
-                           : launch_eval<double, double>(h->d64, h->L, x, h->maxT, ev);
-  if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("eval launch: ") + cudaGetErrorString(e));
+  cudaError_t e;
+  if (mixed(h)) {
+    Dev<float, df32> d = h->d32;
+    d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
+    d.trace = trace; d.trace_len = trace_len;
+    e = launch_eval<float, df32>(d, h->plan, x, adam, h->stream, ev);
+  } else {
+    Dev<double, double> d = h->d64;
+    d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
+    d.trace = trace; d.trace_len = trace_len;
+    e = launch_eval<double, double>(d, h->plan, x, adam, h->stream, ev);
+  }
+  if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("evaluation launch: ") + cudaGetErrorString(e));
   return QG_OK;
 }
 
@@ -521,10 +625,11 @@ int run_adam(qg_ctx *h, void *x, void *m, void *v, double lr, double b1, double 
   cudaError_t e;
   if (mixed(h))
     e = launch_adam<float>((float *)x, (float *)m, (float *)v, (const float *)h->d_g, h->d32.lo, h->d32.hi, h->n_x,
-                           h->d_step, lr, b1, b2, h->opt.adam_eps, h->opt.adam_paper_eps, h->stream);
+                           h->d_step, h->d_ticket, lr, b1, b2, h->opt.adam_eps, h->opt.adam_paper_eps, h->stream);
   else
     e = launch_adam<double>((double *)x, (double *)m, (double *)v, (const double *)h->d_g, h->d64.lo, h->d64.hi,
-                            h->n_x, h->d_step, lr, b1, b2, h->opt.adam_eps, h->opt.adam_paper_eps, h->stream);
+                            h->n_x, h->d_step, h->d_ticket, lr, b1, b2, h->opt.adam_eps, h->opt.adam_paper_eps,
+                            h->stream);
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("adam launch: ") + cudaGetErrorString(e));
   if (h->profiling) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -566,18 +671,22 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
   if (!out) return fail(nullptr, QG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n_inst < 1 || !net || !hor || !ctg) return fail(nullptr, QG_ERR_INVALID_ARG, "bad batch arguments");
+  if (n_inst > MAXB)
+    return fail(nullptr, QG_ERR_UNSUPPORTED, "at most " + std::to_string(MAXB) + " instances per handle");
   qg_ctx *h = new qg_ctx();
   if (opt) h->opt = *opt;
   else qg_default_options(&h->opt);
   const qg_options &o = h->opt;
-  if (o.precision != QG_FP64 && o.precision != QG_MIXED) { fail(h, QG_ERR_INVALID_ARG, "precision"); delete h; return QG_ERR_INVALID_ARG; }
-  if (o.lodf_dtype < 0 || o.lodf_dtype > 2) { fail(h, QG_ERR_INVALID_ARG, "lodf_dtype"); delete h; return QG_ERR_INVALID_ARG; }
-  if (!(o.eps >= 0) || !(o.beta >= 0) || !(o.c_p >= 0) || !(o.c_q >= 0) || !(o.c_s >= 0) || !(o.c_rz >= 0) ||
-      !(o.rho >= 0) || !(o.adam_eps >= 0)) {
-    fail(h, QG_ERR_INVALID_ARG, "penalty parameters must be finite and >= 0");
+  auto reject = [&](int code, const std::string &m) {
+    fail(h, code, m);
     delete h;
-    return QG_ERR_INVALID_ARG;
-  }
+    return code;
+  };
+  if (o.precision != QG_FP64 && o.precision != QG_MIXED) return reject(QG_ERR_INVALID_ARG, "precision");
+  if (o.lodf_dtype < 0 || o.lodf_dtype > 2) return reject(QG_ERR_INVALID_ARG, "lodf_dtype");
+  if (!(o.eps >= 0) || !(o.beta >= 0) || !(o.c_p >= 0) || !(o.c_q >= 0) || !(o.c_s >= 0) || !(o.c_rz >= 0) ||
+      !(o.rho >= 0) || !(o.adam_eps >= 0) || !std::isfinite(o.eps + o.beta + o.c_p + o.c_q + o.c_s + o.c_rz + o.rho))
+    return reject(QG_ERR_INVALID_ARG, "penalty parameters must be finite and >= 0");
   int rc = QG_OK;
   h->n_inst = n_inst;
   h->hi.resize(n_inst);
@@ -585,11 +694,10 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
     rc = read_instance(h, net[b], hor[b], ctg[b], h->hi[b], b);
     if (rc) { delete h; return rc; }
   }
-  // dense inverse + line-outage block per instance, in parallel over instances
-  {
+  {  // FP64 network set-up per instance, in parallel over instances
     std::vector<int> rcs(n_inst, 0);
     std::vector<std::string> errs(n_inst);
-    unsigned nth = std::max(1u, std::min((unsigned)n_inst, std::thread::hardware_concurrency()));
+    const unsigned nth = std::max(1u, std::min((unsigned)n_inst, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
     for (unsigned w = 0; w < nth; ++w)
       pool.emplace_back([&, w]() {
@@ -601,76 +709,39 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
       });
     for (auto &t : pool) t.join();
     for (int b = 0; b < n_inst; ++b)
-      if (rcs[b]) {
-        fail(h, rcs[b], errs[b]);
-        rc = rcs[b];
-        delete h;
-        return rc;
-      }
+      if (rcs[b]) return reject(rcs[b], errs[b]);
   }
+  std::vector<int> slot_inst;
+  build_plan(h, slot_inst);
+  if (h->plan.s1.n > MAXSPAN || h->plan.s2.n > MAXSPAN) return reject(QG_ERR_UNSUPPORTED, "too many block spans");
   // everything above is host-side validation and set-up; from here on the device is needed
   rc = check_device(h);
   if (rc) { delete h; return rc; }
-  // instance descriptors
-  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, z0 = 0, l0 = 0, pm0 = 0, pk0 = 0, ib0 = 0;
-  int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, tp0 = 0;
-  for (int b = 0; b < n_inst; ++b) {
-    const HostInst &I = h->hi[b];
-    Inst D{};
-    D.n = I.n; D.M = I.M; D.G = I.G; D.Z = I.Z; D.T = I.T; D.K = I.K; D.ref = I.ref;
-    D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.tp0 = tp0;
-    D.n_mt = (I.M + 63) / 64;
-    D.n_kt = (I.K + 63) / 64;
-    D.n_ib = (I.n + BLK - 1) / BLK;
-    D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.z0 = z0; D.l0 = l0;
-    D.pm0 = pm0; D.pk0 = pk0; D.ib0 = ib0;
-    D.wfloor_ctg = o.c_s * o.beta * o.eps * ((double)I.M * I.K - I.K);
-    D.inv_n = 1.0 / I.n;
-    df32 s = split(D.inv_n);
-    D.inv_n_hi = s.hi; D.inv_n_lo = s.lo;
-    h->inst.push_back(D);
-    x0 += (long long)I.T * (2LL * I.n + 3LL * I.G);
-    tb0 += (long long)I.T * I.n; tm0 += (long long)I.T * I.M; tg0 += (long long)I.T * I.G; tz0 += (long long)I.T * I.Z;
-    z0 += (long long)I.n * I.n; l0 += (long long)I.M * I.K;
-    pm0 += (long long)D.n_kt * I.T * I.M; pk0 += (long long)D.n_mt * I.T * I.K; ib0 += (long long)I.T * D.n_ib;
-    bus0 += I.n; br0 += I.M; gen0 += I.G; zone0 += I.Z; ctg0 += I.K; tp0 += I.T;
-    h->maxT = std::max(h->maxT, I.T);
-  }
-  h->n_x = x0;
-  h->L.n_x = x0;
-  h->L.lodf_dtype = o.precision == QG_MIXED ? o.lodf_dtype : QG_LODF_F32;
-  h->L.stream = nullptr;
+  h->n_x = h->plan.n_x;
   const size_t rs = mixed(h) ? sizeof(float) : sizeof(double);
-  if ((rc = build_tables(h)) || (rc = dalloc(h, &h->d_obj, (size_t)n_inst)) ||
-      (rc = dalloc(h, &h->d_terms, (size_t)n_inst * N_TERMS)) || (rc = dalloc(h, (char **)&h->d_g, rs * h->n_x)) ||
-      (rc = dalloc(h, (char **)&h->d_m, rs * h->n_x)) || (rc = dalloc(h, (char **)&h->d_v, rs * h->n_x)) ||
-      (rc = dalloc(h, (char **)&h->d_xs, rs * h->n_x)) || (rc = dalloc(h, &h->d_xd, (size_t)h->n_x)) ||
-      (rc = dalloc(h, &h->d_step, 1))) {
+  if ((rc = dalloc(h, &h->d_obj, (size_t)n_inst)) || (rc = dalloc(h, &h->d_terms, (size_t)n_inst * N_TERMS)) ||
+      (rc = dalloc(h, (char **)&h->d_g, rs * h->n_x)) || (rc = dalloc(h, (char **)&h->d_m, rs * h->n_x)) ||
+      (rc = dalloc(h, (char **)&h->d_v, rs * h->n_x)) || (rc = dalloc(h, (char **)&h->d_xs, rs * h->n_x)) ||
+      (rc = dalloc(h, &h->d_xd, (size_t)h->n_x)) || (rc = dalloc(h, &h->d_step, 1)) ||
+      (rc = dalloc(h, &h->d_step0, 1)) || (rc = dalloc(h, &h->d_ticket, 1))) {
     free_all(h);
     delete h;
     return rc;
   }
-  if (cudaMemset(h->d_step, 0, sizeof(long long)) != cudaSuccess ||
-      cudaMemset(h->d_m, 0, rs * h->n_x) != cudaSuccess || cudaMemset(h->d_v, 0, rs * h->n_x) != cudaSuccess) {
-    fail(h, QG_ERR_CUDA, "cudaMemset");
-    free_all(h);
-    delete h;
-    return QG_ERR_CUDA;
-  }
-  rc = mixed(h) ? build_device<float, df32>(h, h->d32) : build_device<double, double>(h, h->d64);
+  rc = mixed(h) ? build_device<float, df32>(h, h->d32, slot_inst) : build_device<double, double>(h, h->d64, slot_inst);
   if (!rc) {
-    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->maxT) : prepare_eval<double, double>(h->maxT);
-    if (e != cudaSuccess) rc = fail(h, QG_ERR_CUDA, std::string("prepare_eval: ") + cudaGetErrorString(e));
+    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->plan.maxT) : prepare_eval<double, double>(h->plan.maxT);
+    if (e != cudaSuccess) rc = fail(h, QG_ERR_UNSUPPORTED, std::string("prepare_eval: ") + cudaGetErrorString(e));
   }
   if (rc) {
     free_all(h);
     delete h;
     return rc;
   }
-  // host copies no longer needed beyond sizes
-  for (auto &I : h->hi) {
-    I.zinv.clear(); I.zinv.shrink_to_fit();
+  for (auto &I : h->hi) {  // the device holds the set-up products now
+    I.ptdfg.clear(); I.ptdfg.shrink_to_fit();
     I.lodf.clear(); I.lodf.shrink_to_fit();
+    I.cload.clear(); I.cload.shrink_to_fit();
   }
   *out = h;
   return QG_OK;
@@ -691,7 +762,7 @@ int64_t qg_num_vars(const qg_ctx *h) { return h ? h->n_x : 0; }
 
 int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[5]) {
   if (!h || inst < 0 || inst >= h->n_inst) return QG_ERR_INVALID_ARG;
-  const Inst &I = h->inst[inst];
+  const Inst &I = h->plan.tab.I[inst];
   const int64_t Tn = (int64_t)I.T * I.n, TG = (int64_t)I.T * I.G;
   if (first) *first = I.x0;
   if (n_x) *n_x = 2 * Tn + 3 * TG;
@@ -704,13 +775,12 @@ int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64
 int qg_set_stream(qg_ctx *h, void *stream) {
   if (!h) return QG_ERR_INVALID_ARG;
   h->stream = (cudaStream_t)stream;
-  h->L.stream = h->stream;
   return QG_OK;
 }
 
 int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g) {
   if (!h || !x) return h ? fail(h, QG_ERR_INVALID_ARG, "x is NULL") : QG_ERR_INVALID_ARG;
-  int rc = run_eval(h, x);
+  int rc = run_eval(h, x, false, 0, 0, 0, nullptr, 0);
   if (rc) return rc;
   const size_t rs = mixed(h) ? sizeof(float) : sizeof(double);
   if (obj) CUDA_TRY(h, cudaMemcpyAsync(obj, h->d_obj, sizeof(double) * h->n_inst, cudaMemcpyDeviceToDevice, h->stream));
@@ -728,7 +798,7 @@ int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {
   } else {
     CUDA_TRY(h, cudaMemcpyAsync(h->d_xs, x, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
   }
-  int rc = run_eval(h, h->d_xs);
+  int rc = run_eval(h, h->d_xs, false, 0, 0, 0, nullptr, 0);
   if (rc) return rc;
   if (g) {
     if (mixed(h)) {
@@ -756,7 +826,10 @@ int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double 
   if (!(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1))
     return fail(h, QG_ERR_INVALID_ARG, "Adam parameters out of range");
   if (iters == 0) return QG_OK;
-  const bool same = h->gexec && h->g_x == x && h->g_lr == lr && h->g_b1 == beta1 && h->g_b2 == beta2;
+  // the trace is indexed by (step - step at the start of this call)
+  if (obj_trace) CUDA_TRY(h, cudaMemcpyAsync(h->d_step0, h->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
+  const bool same = h->gexec && h->g_x == x && h->g_lr == lr && h->g_b1 == beta1 && h->g_b2 == beta2 &&
+                    h->g_trace == obj_trace && (obj_trace == nullptr || h->g_trace_len >= iters);
   if (!same) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
@@ -766,13 +839,11 @@ int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double 
     CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaStream_t saved = h->stream;
     h->stream = cs;
-    h->L.stream = cs;
     cudaGraph_t graph;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int rc = QG_OK;
     if (e == cudaSuccess) {
-      rc = run_eval(h, x);
-      if (!rc) rc = run_adam(h, x, h->d_m, h->d_v, lr, beta1, beta2);
+      rc = run_eval(h, x, true, lr, beta1, beta2, obj_trace, obj_trace ? iters : 0);
       cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
       if (!rc && e2 == cudaSuccess) {
         e = cudaGraphInstantiate(&h->gexec, graph, 0);
@@ -782,18 +853,13 @@ int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double 
       }
     }
     h->stream = saved;
-    h->L.stream = saved;
     cudaStreamDestroy(cs);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    h->g_x = x; h->g_lr = lr; h->g_b1 = beta1; h->g_b2 = beta2;
+    h->g_x = x; h->g_lr = lr; h->g_b1 = beta1; h->g_b2 = beta2; h->g_trace = obj_trace;
+    h->g_trace_len = obj_trace ? iters : 0;
   }
-  for (int it = 0; it < iters; ++it) {
-    CUDA_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
-    if (obj_trace)
-      CUDA_TRY(h, cudaMemcpyAsync(obj_trace + (size_t)it * h->n_inst, h->d_obj, sizeof(double) * h->n_inst,
-                                  cudaMemcpyDeviceToDevice, h->stream));
-  }
+  for (int it = 0; it < iters; ++it) CUDA_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
   return QG_OK;
 }
 
@@ -830,7 +896,7 @@ int qg_set_profiling(qg_ctx *h, int on) {
   if (!h) return QG_ERR_INVALID_ARG;
   if (on && !h->ev[0])
     for (auto &e : h->ev) CUDA_TRY(h, cudaEventCreate(&e));
-  if ((bool)on != h->profiling && h->gexec) {  // the cached graph must be re-captured
+  if ((on != 0) != h->profiling && h->gexec) {  // the cached graph must be re-captured
     cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
   }
@@ -843,11 +909,13 @@ int qg_phase_times(qg_ctx *h, float *ms, int32_t cap) {
   if (!h->profiling) return fail(h, QG_ERR_INVALID_ARG, "profiling is off");
   CUDA_TRY(h, cudaEventSynchronize(h->ev[N_PHASES - 1]));
   int n = 0;
-  for (int k = 0; k < N_PHASES && k < cap; ++k) {
+  for (int k = 0; k < N_PHASES && n < cap; ++k) {
     float v = 0.f;
-    cudaEvent_t end = h->ev[k + 1];
-    if (k == N_PHASES - 1 && cudaEventQuery(end) != cudaSuccess) break;
-    if (cudaEventElapsedTime(&v, h->ev[k], end) != cudaSuccess) v = -1.f;
+    if (k == N_PHASES - 1 && cudaEventQuery(h->ev[N_PHASES]) != cudaSuccess) break;
+    if (cudaEventElapsedTime(&v, h->ev[k], h->ev[k + 1]) != cudaSuccess) {
+      if (k == N_PHASES - 1) break;  // no stand-alone Adam step followed the evaluation
+      v = -1.f;
+    }
     ms[n++] = v;
   }
   cudaGetLastError();
@@ -856,6 +924,6 @@ int qg_phase_times(qg_ctx *h, float *ms, int32_t cap) {
 
 const char *qg_last_error(const qg_ctx *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int qg_version(void) { return 100; }
+int qg_version(void) { return 200; }
 
 }  // extern "C"

@@ -1,4 +1,4 @@
-// Internal declarations shared by the host setup (qg_host.cu) and the device
+// Internal declarations shared by the host set-up (qg_host.cu) and the device
 // kernels (qg_kernels.cu) of libqg.  Not part of the public ABI.
 #pragma once
 
@@ -12,126 +12,143 @@ namespace qg {
 // Objective terms, in the order qg_breakdown reports them.
 enum Term { T_COST = 0, T_ZP, T_ZQ, T_ZS, T_ZRZ, T_ZHEAD, T_ZRAMP, T_ZCTG, N_TERMS };
 
-// One instance of a batch.  Entity ids inside the kernels are global (offset
-// by bus0/br0/gen0/zone0/ctg0); per-period arrays are period-major blocks that
-// start at tb0 (T x n), tm0 (T x M), tg0 (T x G), tz0 (T x Z), tp0 (T).
+constexpr int MAXB = 32;       // instances per handle (the instance table travels as a kernel parameter)
+constexpr int MAXSPAN = 192;   // block spans per launch
+constexpr int NTHR = 256;      // threads per block of every stage kernel
+constexpr int CT_BM = 64, CT_BK = 64;  // contingency tile: monitored branches x outages
+constexpr int DCF_BM = 32, DCF_TC = 8; // forward DC tile: 32 branches x 8 periods
+constexpr int DCA_BM = 32, DCA_TC = 8; // adjoint DC tile: 32 branches (split-K chunk) x 8 periods
+constexpr int PACK = 32;               // CSR entries per warp pack (rows never straddle packs)
+constexpr int PACKS_PER_BLOCK = NTHR / 32;
+
+// One instance of a batch.  Entity ids inside the kernels are global (offset by
+// bus0 / br0 / gen0 / zone0 / ctg0 / gb0); per-period arrays are period-major
+// blocks starting at tb0 (T x n), tm0 (T x M), tg0 (T x G), tz0 (T x Z), tk0
+// (T x K) and tp0 (T).
 struct Inst {
-  int n, M, G, Z, T, K, ref;
-  int bus0, br0, gen0, zone0, ctg0, tp0;
-  int n_mt, n_kt;          // contingency tiles along monitored branches / outages
-  long long x0;            // first variable of this instance
-  long long tb0, tm0, tg0, tz0;
-  long long z0;            // dense Laplacian inverse, n x n (ref row/col zero)
-  long long l0;            // line-outage block, M x K (row m, column k)
-  long long pm0, pk0;      // contingency partials: [n_kt][T][M] and [n_mt][T][K]
-  long long ib0;           // per-period bus-block partials: [T][n_ib]
-  int n_ib;                // bus blocks per period
-  double wfloor_ctg;       // c_s * beta * eps * (M*K - K): soft-ReLU floor of the contingency term per hour
-  double inv_n;            // 1 / n, and its double-FP32 split
-  float inv_n_hi, inv_n_lo;
+  int n, M, G, Z, T, K, Gb;
+  int bus0, br0, gen0, zone0, ctg0, gb0, tp0;
+  int n_mt, n_kt;        // contingency tiles along monitored branches / outages
+  int n_mch;             // adjoint DC split-K chunks (DCA_BM branches each)
+  int n_sb;              // stage-3 branch blocks per period (partials of r . dz/df)
+  int bal0, n_bal_pack;  // first entry / number of warp packs of the balance CSR
+  int adj0, n_adj_pack;  // same for the branch-end adjoint CSR
+  long long x0;          // first variable of this instance
+  long long tb0, tm0, tg0, tz0, tk0;
+  long long pg0;         // PTDF restricted to generator buses: M x Gb, row m
+  long long l0;          // line-outage block, M x K, row m
+  long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mt][T][K]
+  long long gi0;         // adjoint DC partials: [n_mch][T][Gb]
+  long long sp0;         // partials of r . dz/df: [T][n_sb]
+  double inv_n;          // 1 / n
+  double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
 };
 
-// Block roles of the descriptor-driven kernels.
-enum Role : int { R_BRANCH = 0, R_ZONE = 1, R_BUS = 2, R_GEN = 3, R_NONE = 7 };
+// Roles of the blocks of the fused stage kernels.
+enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN };
 
-// One thread block of a descriptor-driven launch: which instance, which period,
-// which slice of entities [base, base + blockDim) and what to do.
-struct Blk {
-  int role;
-  int inst;
-  int t;
-  int base;
-  int ib;  // bus-block index within the period (R_BUS)
+// A run of blocks with one role for one instance: blocks [first, first + per_t * nt);
+// block b of the span has period (or period chunk) (b - first) / per_t and slice (b - first) % per_t.
+struct Span {
+  int first, per_t, nt, inst, role;
 };
 
-// Tile of the dense DC apply: rows [i0, i0 + rows) of instance inst.
-struct DcTile {
-  int inst;
-  int i0;
+struct Spans {
+  Span s[MAXSPAN];
+  int n;
+  int n_blocks;
 };
 
-// Tile of the contingency kernel: monitored rows [m0, m0+BM) x outages [k0, k0+BK).
-struct CtgTile {
-  int inst;
-  int m0, k0;
-  int mt, kt;
+struct InstTab {
+  Inst I[MAXB];
+  int n_inst;
 };
 
-// Double-FP32 value (unevaluated sum hi + lo), used for the FP64-accurate DC
-// solves of the mixed path: GB300's FP64 pipe is ~1/60 of its FP32 rate.
+// Double-FP32 value (unevaluated sum hi + lo) carrying the FP64-accurate DC
+// products of the mixed path: GB300's FP64 pipe runs at ~1/60 of its FP32 rate.
 struct df32 {
   float hi, lo;
 };
 
-// Device-side arrays.  Real is double (QG_FP64) or float (QG_MIXED); Dc is
-// double or df32 (the DC-solve value type); Lodf is the line-outage storage type.
+// Device arrays.  Real is double (QG_FP64) or float (QG_MIXED); Dc is the DC
+// product type: double, or df32 in the mixed path.
 template <typename Real, typename Dc>
 struct Dev {
-  int n_inst;
-  const Inst *inst;
-  // network (global entity ids)
-  const int *br_from, *br_to, *br_kidx;  // kidx: outage index of the branch within its instance, -1 if none
-  const Real *br_g, *br_b, *br_bc, *br_smax, *br_sctg, *br_y;  // bc = b + b_ch/2
-  const int *gen_bus, *gen_zone;
+  // network (global ids)
+  const int2 *br_end;                 // [sum M] (from, to) bus ids local to the instance
+  const int *br_kidx;                 // [sum M] outage index of the branch within its instance, -1 if none
+  const Real *br_g, *br_b, *br_hch, *br_smax, *br_s2ctg;  // g_sr, b_sr, b_ch / 2, s_max, s_ctg^2
+  const int *gen_bus, *gen_zone, *gen_gb;                 // local bus, local zone, local generator-bus index
   const Real *gen_a, *gen_b, *gen_cr, *gen_pmax, *gen_ramp;
-  const int *inc_ptr, *inc;           // bus -> (branch << 1 | side), side 1 = "to" end
-  const int *bgen_ptr, *bgen;         // bus -> generators
-  const int *zgen_ptr, *zgen;         // zone -> generators
-  const int *ctg_br;                  // [K total] global branch id of each outage
+  const int *gb_ptr, *gb_gen;         // generator bus -> generators (global ids); gb_ptr indexed by gb0 + gb + inst
+  const int *zgen_ptr, *zgen;         // zone -> generators (global ids); zgen_ptr indexed by zone0 + z + inst
+  const int *ctg_br;                  // [sum K] local branch id of each outage
+  const int *bal_code, *bal_row;      // balance CSR packs: code = j<<2|kind (0 from-end, 1 to-end, 2 generator, 3 pad)
+  const int *adj_code, *adj_row;      // branch-end CSR packs (kind 0 / 1 / 3)
   const Real *load_p, *load_q;        // [sum T n]
   const Real *rreq;                   // [sum T Z]
   const Real *dt;                     // [sum T]
-  const Dc *zinv;                     // [sum n^2]
-  const Dc *z1;                       // [sum n] row sums of zinv (global bus id)
-  const void *lodf;                   // [sum M K], element type per lodf_dtype
-  const Real *lo, *hi;                // Adam clip box [n_x]
+  const Dc *ltot;                     // [sum T] total load per period
+  const Dc *ptdfg;                    // [sum M Gb] PTDF columns of generator buses
+  const Dc *cload;                    // [sum T M] PTDF * load_t
+  const Dc *rsum;                     // [sum M] PTDF * 1
+  const void *lodf;                   // [sum M K]: float / bf16 / bf16x2 (mixed) or float screening copy (FP64)
+  const double *lodf64;               // [sum M K] FP64 path only
+  const Real *lo, *hi;                // clip box [n_x]
   // penalty parameters
   Real c_p, c_q, c_s, c_rz, rho, eps, beta;
+  int lodf_dtype;
   // work buffers
   Real *pf, *qf, *pt, *qt, *qm2;      // [sum T M]
   unsigned char *qside;               // [sum T M] 1 if the "to" end carries the larger |q|
+  Real *fre;                          // [sum T M] base DC flows
+  float *f32;                         // [sum T M] FP32 copy (FP64 path screening)
+  Real *fk;                           // [sum T K] base flows on outaged branches
+  float *fk32;                        // [sum T K]
+  Real *pold;                         // [sum T G] dispatch snapshot for the fused Adam ramp terms
   Real *dP, *dQ;                      // [sum T n]
   Real *dZ;                           // [sum T Z]
-  Dc *pinj, *th, *w, *ginj;           // [sum T n]
-  Dc *mupart, *spart;                 // [sum T n_ib]
   Real *pm, *pq, *pk;                 // contingency partials
+  Real *gF;                           // [sum T M] dz/df
+  Dc *spart;                          // [sum T n_sb]
+  Dc *gip;                            // adjoint DC partials
   Real *avf, *avo, *ad;               // branch-end adjoints [sum T M]
   double *objp;                       // [n_obj_slots][N_TERMS]
+  int n_obj_slots;
+  const int *slot_inst;               // [n_obj_slots]
   double *obj, *terms;                // [n_inst], [n_inst][N_TERMS]
-  Real *g;                            // [n_x]
-  long long *step;                    // Adam step counter (device)
+  Real *g;                            // gradient [n_x]
+  unsigned int *ticket;               // last-block counter of stage 5
+  long long *step;                    // Adam step counter
+  // fused Adam (qg_solve): moments and hyper-parameters
+  Real *am, *av;
+  double lr, b1, b2, aeps;
+  int paper_eps;
+  double *trace;                      // optional objective trace (qg_solve), [trace_len][n_inst]
+  long long *trace_step0;             // step count at the start of the traced solve
+  int trace_len;
 };
 
-struct Launch {
-  cudaStream_t stream;
-  // descriptor tables (device) and their sizes
-  const Blk *blk_fwd1; int n_fwd1;
-  const Blk *blk_fwd2; int n_fwd2;
-  const Blk *blk_adj1; int n_adj1;
-  const Blk *blk_bwd1; int n_bwd1;
-  const Blk *blk_bwd2; int n_bwd2;
-  const DcTile *dct; int n_dct;
-  const CtgTile *ctt; int n_ctt;
-  int obj_fwd1, obj_fwd2, obj_ctg, obj_bwd2;  // first objective slot of each launch
-  int n_obj_slots;
-  const int *slot_inst;  // instance of every objective slot
-  int lodf_dtype;
+struct Plan {
+  Spans s1, s2, s3, s4, s5;
+  InstTab tab;
   long long n_x;
+  int maxT;
 };
 
 template <typename Real, typename Dc>
-cudaError_t launch_eval(const Dev<Real, Dc> &d, const Launch &L, const void *x, int maxT, cudaEvent_t *ev);
-
-// Number of timed phases: the nine evaluation kernels and the Adam step.
-constexpr int N_PHASES = 10;
+cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *x, bool adam, cudaStream_t s,
+                        cudaEvent_t *ev);
 
 template <typename Real, typename Dc>
 cudaError_t prepare_eval(int maxT);
 
 template <typename Real>
 cudaError_t launch_adam(Real *x, Real *m, Real *v, const Real *g, const Real *lo, const Real *hi, long long n,
-                        long long *step, double lr, double b1, double b2, double eps, int paper_eps,
-                        cudaStream_t s);
+                        long long *step, unsigned int *ticket, double lr, double b1, double b2, double eps,
+                        int paper_eps, cudaStream_t s);
 
+// Timed phases: the five stage kernels and the stand-alone Adam step.
+constexpr int N_PHASES = 6;
 
 }  // namespace qg

@@ -95,7 +95,7 @@ _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_adam_step", "qg_solve", "qg_breakdown",
             "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_last_error", "qg_version")
-PHASES = ("fwd1", "fwd2", "dc_fwd", "ctg", "adj1", "dc_adj", "bwd1", "bwd2", "obj", "adam")
+PHASES = ("s1", "s2", "s3", "s4", "s5", "adam")
 
 
 class QGError(RuntimeError):
