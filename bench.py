@@ -62,7 +62,7 @@ sys.path.insert(0, {root!r})
 import numpy as np
 import synth, oracle
 case = getattr(synth, {workload!r})()
-x = case.flat_start()
+x, _ = synth.lp_start(case)
 v, th, p, q, r = oracle.unpack(case, x)
 def period_case(t):
     sl = slice(t, t + 1)
@@ -221,7 +221,7 @@ def gpu_leg(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     case = getattr(synth, WORKLOAD)()
-    x0 = case.flat_start()
+    x0, _ = synth.lp_start(case)
     peaks, src = _peaks()
     results = {}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -303,7 +303,8 @@ def gpu_leg(args, rank, world, local_rank):
                                f"{case.T} periods, {case.K} single-branch outages (all evaluated, zeta = 0)",
                    "step": "one full objective+gradient evaluation + projected Adam update (CUDA graph replay)",
                    "precision": "mixed: FP32 flows/penalties/adjoints/Adam, double-FP32 DC solves, FP64 objective",
-                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
+                   "x0": "copper-plate dispatch (stored), flat voltage, zero angles"},
         "roofline": roof,
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
                          "sample": oracle_sample_text(cpu)},

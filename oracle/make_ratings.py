@@ -1,4 +1,5 @@
-"""Writes the thermal ratings of the named synthetic cases (run by hand; output is committed).
+"""Writes the thermal ratings and copper-plate starts of the named synthetic cases
+(run by hand; output is committed).
 
 TEST INFRASTRUCTURE (see qg_oracle.py).  For each case the generator draws every
 input except the ratings; this script dispatches generation in merit order
@@ -6,6 +7,12 @@ input except the ratings; this script dispatches generation in merit order
 the oracle's own solve (Sec. II-E, Eq. Yb_solve/p_flow) and sets
     s_max_j = s_max_ctg_j = max(RATING_FLOOR, RATING_MARGIN * max_t |f_jt|),
 stored as float32 in synth/ratings/<case name>.npy.  The generator reads them back.
+
+For the cases the tests and the benchmark start from (tiny14, mid150, rt617) it
+also stores the copper-plate dispatch of Sec. III-A (oracle.copperplate, exact
+tangent-cut QP) and its bound in synth/ratings/<case name>_lp.npz: the start
+x0 = (flat voltage, zero angles and q, copper-plate p and r) and the reference
+value of the "within 1% of the LP bound" metric.
 
     python -m oracle.make_ratings            # every named case
 """
@@ -18,7 +25,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .copperplate import lambda_dispatch
+from .copperplate import copper_plate, lambda_dispatch
 
 RATING_MARGIN = 2.0
 RATING_FLOOR = 0.5
@@ -61,6 +68,11 @@ def main(argv):
         r = ratings_for(c)
         np.save(os.path.join(OUT, c.name + ".npy"), r)
         print(c.name, c.n_branch, float(r.min()), float(r.max()))
+    for mk in (synth.tiny, synth.mid, synth.rt617):
+        c = mk()
+        bound, p, rr = copper_plate(c)
+        np.savez(os.path.join(OUT, c.name + "_lp.npz"), p=p, r=rr, bound=np.array(bound))
+        print(c.name, "copper-plate bound", bound)
 
 
 if __name__ == "__main__":

@@ -354,7 +354,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
   const int B = h->n_inst;
   std::memset(&P, 0, sizeof(P));
   P.tab.n_inst = B;
-  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0, sp0 = 0;
+  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0;
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
@@ -363,19 +363,17 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
     D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.gb0 = gb0; D.tp0 = tp0;
     D.n_mt = ceil_div(H.M, CT_BM);
     D.n_kt = ceil_div(H.K, CT_BK);
-    D.n_mch = ceil_div(H.M, DCA_BM);
     D.n_sb = ceil_div(H.M, NTHR);
     D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
     D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
     D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
-    D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0; D.sp0 = sp0;
+    D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0;
     D.inv_n = 1.0 / H.n;
     D.wfloor_ctg = h->opt.c_s * h->opt.beta * h->opt.eps * ((double)H.M * H.K - H.K);
     x0 += (long long)H.T * (2LL * H.n + 3LL * H.G);
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
     tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gb; l0 += (long long)H.M * H.K;
-    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mt * H.T * H.K; gi0 += (long long)D.n_mch * H.T * D.Gb;
-    sp0 += (long long)H.T * D.n_sb;
+    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mt * H.T * H.K; gi0 += (long long)H.T * (D.Gb + 1);
     bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.K; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
     P.maxT = std::max(P.maxT, H.T);
@@ -385,11 +383,11 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
   // roles with the longest blocks first in each launch
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, DCF_BM), ceil_div(I[b].T, DCF_TC), b, R_DCF);
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, NTHR), I[b].T, b, R_BRANCH);
-  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].Z, NTHR), I[b].T, b, R_ZONE);
+  for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
   for (int b = 0; b < B; ++b) add_span(P.s2, I[b].n_mt * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
   for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
-  for (int b = 0; b < B; ++b) add_span(P.s4, I[b].n_mch, ceil_div(I[b].T, DCA_TC), b, R_DCA);
+  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gb + 1, NTHR / 32), I[b].T, b, R_DCA);
   for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].G, NTHR), I[b].T, b, R_GEN);
   // objective slots: blocks of s1, then s2, then s5
@@ -409,7 +407,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
   std::vector<int> br_kidx, gen_bus, gen_zone, gen_gb, gb_ptr{0}, gb_gen, zgen_ptr{0}, zgen, ctg_br, bal_code, bal_row,
       adj_code, adj_row;
   std::vector<double> br_g, br_b, br_hch, br_smax, br_s2, ga, gbv, gcr, gpmax, gramp, load_p, load_q, rreq, dt, lo, hi,
-      ltot, ptdfg, cload, rsum, lodf;
+      ltot, ptdfg, ptdfgT, cload, rsum, lodf;
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
     const Inst &D = P.tab.I[b];
@@ -456,6 +454,9 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
     dt.insert(dt.end(), H.dt.begin(), H.dt.end());
     ltot.insert(ltot.end(), H.ltot.begin(), H.ltot.end());
     ptdfg.insert(ptdfg.end(), H.ptdfg.begin(), H.ptdfg.end());
+    const int Gb = (int)H.gbus.size();
+    for (int q = 0; q < Gb; ++q)
+      for (int m = 0; m < H.M; ++m) ptdfgT.push_back(H.ptdfg[(size_t)m * Gb + q]);
     cload.insert(cload.end(), H.cload.begin(), H.cload.end());
     rsum.insert(rsum.end(), H.rsum.begin(), H.rsum.end());
     lodf.insert(lodf.end(), H.lodf.begin(), H.lodf.end());
@@ -492,7 +493,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
   UPR(br_g, br_g) UPR(br_b, br_b) UPR(br_hch, br_hch) UPR(br_smax, br_smax) UPR(br_s2ctg, br_s2)
   UPR(gen_a, ga) UPR(gen_b, gbv) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax) UPR(gen_ramp, gramp)
   UPR(load_p, load_p) UPR(load_q, load_q) UPR(rreq, rreq) UPR(dt, dt) UPR(lo, lo) UPR(hi, hi)
-  UPD(ltot, ltot) UPD(ptdfg, ptdfg) UPD(cload, cload) UPD(rsum, rsum)
+  UPD(ltot, ltot) UPD(ptdfg, ptdfg) UPD(ptdfgT, ptdfgT) UPD(cload, cload) UPD(rsum, rsum)
 #undef UPI
 #undef UPR
 #undef UPD
@@ -533,13 +534,13 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
   d.c_p = (Real)o.c_p; d.c_q = (Real)o.c_q; d.c_s = (Real)o.c_s; d.c_rz = (Real)o.c_rz;
   d.rho = (Real)o.rho; d.eps = (Real)o.eps; d.beta = (Real)o.beta;
   // work buffers
-  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0, sSP = 0;
+  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0;
   for (int b = 0; b < B; ++b) {
     const Inst &I = P.tab.I[b];
     sTM += (long long)I.T * I.M; sTn += (long long)I.T * I.n; sTZ += (long long)I.T * I.Z;
     sTK += (long long)I.T * I.K; sTG += (long long)I.T * I.G;
     sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mt * I.T * I.K;
-    sGI += (long long)I.n_mch * I.T * I.Gb; sSP += (long long)I.T * I.n_sb;
+    sGI += (long long)I.T * (I.Gb + 1);
   }
   Real *w;
   Dc *c;
@@ -550,7 +551,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
   WR(pf, sTM) WR(qf, sTM) WR(pt, sTM) WR(qt, sTM) WR(qm2, sTM) WR(fre, sTM) WR(fk, sTK) WR(pold, sTG)
   WR(dP, sTn) WR(dQ, sTn) WR(dZ, sTZ) WR(pm, sPM) WR(pq, sPM) WR(pk, sPK) WR(gF, sTM) WR(avf, sTM) WR(avo, sTM)
   WR(ad, sTM)
-  WD(spart, sSP) WD(gip, sGI)
+  WD(gip, sGI)
   WF(f32, sTM) WF(fk32, sTK)
 #undef WR
 #undef WD

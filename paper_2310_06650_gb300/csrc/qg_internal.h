@@ -17,7 +17,6 @@ constexpr int MAXSPAN = 192;   // block spans per launch
 constexpr int NTHR = 256;      // threads per block of every stage kernel
 constexpr int CT_BM = 64, CT_BK = 64;  // contingency tile: monitored branches x outages
 constexpr int DCF_BM = 32, DCF_TC = 8; // forward DC tile: 32 branches x 8 periods
-constexpr int DCA_BM = 32, DCA_TC = 8; // adjoint DC tile: 32 branches (split-K chunk) x 8 periods
 constexpr int PACK = 32;               // CSR entries per warp pack (rows never straddle packs)
 constexpr int PACKS_PER_BLOCK = NTHR / 32;
 
@@ -29,8 +28,7 @@ struct Inst {
   int n, M, G, Z, T, K, Gb;
   int bus0, br0, gen0, zone0, ctg0, gb0, tp0;
   int n_mt, n_kt;        // contingency tiles along monitored branches / outages
-  int n_mch;             // adjoint DC split-K chunks (DCA_BM branches each)
-  int n_sb;              // stage-3 branch blocks per period (partials of r . dz/df)
+  int n_sb;              // stage-3 branch blocks per period
   int bal0, n_bal_pack;  // first entry / number of warp packs of the balance CSR
   int adj0, n_adj_pack;  // same for the branch-end adjoint CSR
   long long x0;          // first variable of this instance
@@ -38,8 +36,7 @@ struct Inst {
   long long pg0;         // PTDF restricted to generator buses: M x Gb, row m
   long long l0;          // line-outage block, M x K, row m
   long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mt][T][K]
-  long long gi0;         // adjoint DC partials: [n_mch][T][Gb]
-  long long sp0;         // partials of r . dz/df: [T][n_sb]
+  long long gi0;         // adjoint DC products at the generator buses: [T][Gb + 1]
   double inv_n;          // 1 / n
   double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
 };
@@ -80,8 +77,8 @@ struct Dev {
   const Real *br_g, *br_b, *br_hch, *br_smax, *br_s2ctg;  // g_sr, b_sr, b_ch / 2, s_max, s_ctg^2
   const int *gen_bus, *gen_zone, *gen_gb;                 // local bus, local zone, local generator-bus index
   const Real *gen_a, *gen_b, *gen_cr, *gen_pmax, *gen_ramp;
-  const int *gb_ptr, *gb_gen;         // generator bus -> generators (global ids); gb_ptr indexed by gb0 + gb + inst
-  const int *zgen_ptr, *zgen;         // zone -> generators (global ids); zgen_ptr indexed by zone0 + z + inst
+  const int *gb_ptr, *gb_gen;         // generator bus -> generators: one CSR over the batch's generator buses
+  const int *zgen_ptr, *zgen;         // zone -> generators: one CSR over the batch's zones (global ids)
   const int *ctg_br;                  // [sum K] local branch id of each outage
   const int *bal_code, *bal_row;      // balance CSR packs: code = j<<2|kind (0 from-end, 1 to-end, 2 generator, 3 pad)
   const int *adj_code, *adj_row;      // branch-end CSR packs (kind 0 / 1 / 3)
@@ -89,7 +86,8 @@ struct Dev {
   const Real *rreq;                   // [sum T Z]
   const Real *dt;                     // [sum T]
   const Dc *ltot;                     // [sum T] total load per period
-  const Dc *ptdfg;                    // [sum M Gb] PTDF columns of generator buses
+  const Dc *ptdfg;                    // [sum M Gb] PTDF columns of generator buses, row m
+  const Dc *ptdfgT;                   // [sum Gb M] the same, row gb
   const Dc *cload;                    // [sum T M] PTDF * load_t
   const Dc *rsum;                     // [sum M] PTDF * 1
   const void *lodf;                   // [sum M K]: float / bf16 / bf16x2 (mixed) or float screening copy (FP64)
@@ -110,8 +108,7 @@ struct Dev {
   Real *dZ;                           // [sum T Z]
   Real *pm, *pq, *pk;                 // contingency partials
   Real *gF;                           // [sum T M] dz/df
-  Dc *spart;                          // [sum T n_sb]
-  Dc *gip;                            // adjoint DC partials
+  Dc *gip;                            // adjoint DC products [sum T (Gb + 1)]
   Real *avf, *avo, *ad;               // branch-end adjoints [sum T M]
   double *objp;                       // [n_obj_slots][N_TERMS]
   int n_obj_slots;

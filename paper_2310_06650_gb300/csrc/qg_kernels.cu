@@ -263,22 +263,31 @@ __device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub,
   acc[T_ZS] = (double)(d.dt[I.tp0 + t] * d.c_s * d.beta * val);
 }
 
+// Zonal reserve shortfall of zone `sub` in period t: the block sums the zone's reserve
+// offers (fixed order), then sigma_s(R_zt - sum r) and its derivative.
 template <typename Real, typename Dc>
-__device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
+__device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, const Real *__restrict__ x,
                         double (&acc)[N_TERMS]) {
-  const int z = sub * NTHR + threadIdx.x;
-  if (z >= I.Z) return;
+  __shared__ Real red[NTHR / 32];
   const int zg = I.zone0 + z;  // global zone id; zgen_ptr is one CSR over all zones of the batch
   const Real *r = x + I.x0 + 2LL * I.T * I.n + 2LL * I.T * I.G + (long long)t * I.G;
-  Real sr = 0;
   const int e0 = d.zgen_ptr[zg], e1 = d.zgen_ptr[zg + 1];
-  for (int e = e0; e < e1; ++e) sr += r[d.zgen[e] - I.gen0];
-  const long long k = I.tz0 + (long long)t * I.Z + z;
-  Real val, der;
-  soft_relu(d.rreq[k] - sr, d.eps, val, der);
-  const Real w = d.dt[I.tp0 + t] * d.c_rz * d.beta;
-  d.dZ[k] = w * der;
-  acc[T_ZRZ] = (double)(w * val);
+  Real sr = 0;
+  for (int e = e0 + threadIdx.x; e < e1; e += NTHR) sr += r[d.zgen[e] - I.gen0];
+  sr = warp_sum(sr);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Real tot = 0;
+#pragma unroll
+    for (int w = 0; w < NTHR / 32; ++w) tot += red[w];
+    const long long k = I.tz0 + (long long)t * I.Z + z;
+    Real val, der;
+    soft_relu(d.rreq[k] - tot, d.eps, val, der);
+    const Real w = d.dt[I.tp0 + t] * d.c_rz * d.beta;
+    d.dZ[k] = w * der;
+    acc[T_ZRZ] = (double)(w * val);
+  }
 }
 
 // Base DC flows of branches [m0, m0+32) in periods [t0, t0+8):
@@ -593,21 +602,24 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
   const Inst &I = tab.I[w.inst];
   const int t = w.t;
   const int j = w.sub * NTHR + threadIdx.x;
-  Dc rg = DcOps<Dc>::zero();
   if (j < I.M) {
     const int jg = I.br0 + j;
     const long long e = I.tm0 + (long long)t * I.M + j;
     Real gF = 0, gq2 = 0;
+#pragma unroll 8
     for (int kt = 0; kt < I.n_kt; ++kt) {
       const long long q = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
       gF += d.pm[q];
       gq2 += d.pq[q];
     }
     const int kx = d.br_kidx[jg];
-    if (kx >= 0)
-      for (int mt = 0; mt < I.n_mt; ++mt) gF += d.pk[I.pk0 + ((long long)mt * I.T + t) * I.K + kx];
+    if (kx >= 0) {
+      Real gk = 0;
+#pragma unroll 8
+      for (int mt = 0; mt < I.n_mt; ++mt) gk += d.pk[I.pk0 + ((long long)mt * I.T + t) * I.K + kx];
+      gF += gk;
+    }
     d.gF[e] = gF;
-    rg = DcOps<Dc>::mul(d.rsum[jg], DcOps<Dc>::from_real(gF));
     // adjoints of the four end flows
     const int2 ft = d.br_end[jg];
     const long long tb = I.tb0 + (long long)t * I.n;
@@ -645,8 +657,6 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
     d.ad[e] = vv * (gpf * (g * sn - bb * cs) + gqf * (-bb * sn - g * cs) + gpt * (g * sn + bb * cs) +
                     gqt * (-bb * sn + g * cs));
   }
-  const Dc s = block_sum_dc(rg);
-  if (threadIdx.x == 0) d.spart[I.sp0 + (long long)t * I.n_sb + w.sub] = s;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -715,34 +725,28 @@ __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Re
   }
 }
 
-// Partial adjoint DC products for branches [m0, m0+32) (split-K chunk) and periods [t0, t0+8):
-//   gip[chunk][t][gb] = sum_{m in chunk} dz/df[t,m] PTDF_G[m,gb]   (eta at generator buses).
+// Adjoint DC products (Eq. 2nd_lin_sys at the generator buses): one warp per output,
+//   eta[t, gb] = sum_m dz/df[t,m] PTDF[m, gb]       (gb < Gb),
+//   eta[t, Gb] = sum_m dz/df[t,m] (PTDF 1)[m]        (n times the mean of eta, Eq. correction),
+// lanes striding over the branches, then a fixed-order shuffle reduction.
 template <typename Real, typename Dc>
-__device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub) {
-  __shared__ Dc s_gf[DCA_TC][DCA_BM];
-  __shared__ Dc s_pt[DCA_BM][GBC + 1];
-  const int t0 = tc * DCA_TC, m0 = sub * DCA_BM;
-  for (int e = threadIdx.x; e < DCA_TC * DCA_BM; e += NTHR) {
-    const int r = e / DCA_BM, c = e % DCA_BM, t = t0 + r, m = m0 + c;
-    s_gf[r][c] = (t < I.T && m < I.M) ? DcOps<Dc>::from_real(d.gF[I.tm0 + (long long)t * I.M + m]) : DcOps<Dc>::zero();
+__device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
+  const int o = sub * (NTHR / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (o > I.Gb) return;
+  const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
+  const Dc *col = o < I.Gb ? d.ptdfgT + I.pg0 + (long long)o * I.M : d.rsum + I.br0;
+  Dc a0 = DcOps<Dc>::zero(), a1 = DcOps<Dc>::zero();
+  int m = lane;
+  for (; m + 32 < I.M; m += 64) {
+    DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
+    DcOps<Dc>::mac(a1, col[m + 32], DcOps<Dc>::from_real(gf[m + 32]));
   }
-  for (int c0 = 0; c0 < I.Gb; c0 += GBC) {
-    const int cn = min(GBC, I.Gb - c0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < DCA_BM * cn; e += NTHR) {
-      const int r = e / cn, c = e % cn;
-      s_pt[r][c] = (m0 + r < I.M) ? d.ptdfg[I.pg0 + (long long)(m0 + r) * I.Gb + c0 + c] : DcOps<Dc>::zero();
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < DCA_TC * cn; o += NTHR) {
-      const int r = o / cn, c = o % cn, t = t0 + r;
-      if (t >= I.T) continue;
-      Dc acc = DcOps<Dc>::zero();
-#pragma unroll 8
-      for (int q = 0; q < DCA_BM; ++q) DcOps<Dc>::mac(acc, s_gf[r][q], s_pt[q][c]);
-      d.gip[I.gi0 + ((long long)sub * I.T + t) * I.Gb + c0 + c] = acc;
-    }
-  }
+  if (m < I.M) DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
+  Dc acc = DcOps<Dc>::add(a0, a1);
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) acc = DcOps<Dc>::add(acc, DcOps<Dc>::shfl_down(acc, k));
+  if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + o] = acc;
 }
 
 template <typename Real, typename Dc, bool ADAM>
@@ -764,10 +768,11 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int b = wid; b < tab.n_inst; b += NTHR / 32) {
     double a[N_TERMS] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
     for (int s = lane; s < d.n_obj_slots; s += 32) {
-      if (d.slot_inst[s] != b) continue;
+      const bool mine = d.slot_inst[s] == b;
 #pragma unroll
-      for (int k = 0; k < N_TERMS; ++k) a[k] += d.objp[(long long)s * N_TERMS + k];
+      for (int k = 0; k < N_TERMS; ++k) a[k] += mine ? d.objp[(long long)s * N_TERMS + k] : 0.0;
     }
 #pragma unroll
     for (int k = 0; k < N_TERMS; ++k) a[k] = warp_sum(a[k]);
@@ -811,11 +816,8 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
     const Real p = x[kp], r = x[kr];
     const Real a = d.gen_a[gg], bl = d.gen_b[gg], cr = d.gen_cr[gg], pmax = d.gen_pmax[gg], ramp = d.gen_ramp[gg];
     // injection adjoint at the generator's bus: eta_gb - mean(eta)   (Eqs. 2nd_lin_sys, correction)
-    Dc eta = DcOps<Dc>::zero();
-    for (int ch = 0; ch < I.n_mch; ++ch) eta = DcOps<Dc>::add(eta, d.gip[I.gi0 + ((long long)ch * T + t) * I.Gb + gb]);
-    Dc sm = DcOps<Dc>::zero();
-    for (int q = 0; q < I.n_sb; ++q) sm = DcOps<Dc>::add(sm, d.spart[I.sp0 + (long long)t * I.n_sb + q]);
-    eta = DcOps<Dc>::add(eta, DcOps<Dc>::neg(DcOps<Dc>::mul(sm, DcOps<Dc>::inv_n(I))));
+    const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gb + 1);
+    const Dc eta = DcOps<Dc>::add(et[gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gb], DcOps<Dc>::inv_n(I))));
     const long long tb = I.tb0 + (long long)t * I.n;
     Real gp = dt * (2 * a * p + bl) - d.dP[tb + bus] + DcOps<Dc>::to_real(eta);
     const Real gq = -d.dQ[tb + bus];

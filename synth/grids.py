@@ -35,6 +35,8 @@ from typing import List, Optional
 
 import numpy as np
 
+_RATINGS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "ratings")
+
 
 @dataclasses.dataclass
 class Case:
@@ -110,6 +112,16 @@ class Case:
         if r is not None:
             x[orr:orr + T * G] = np.asarray(r, dtype=np.float64).reshape(T * G)
         return x
+
+
+def lp_start(case: Case):
+    """(x0, bound): the stored copper-plate start of a named case (flat voltage, zero angles and q,
+    copper-plate p and r) and its copper-plate bound.  Written by oracle/make_ratings.py."""
+    path = os.path.join(_RATINGS_DIR, case.name + "_lp.npz")
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"no stored copper-plate start for {case.name}")
+    d = np.load(path)
+    return case.flat_start(d["p"], d["r"]), float(d["bound"])
 
 
 def proportional_dispatch(case: Case) -> np.ndarray:
@@ -211,9 +223,6 @@ def _multi_source_bfs(n: int, frm: np.ndarray, to: np.ndarray, seeds: np.ndarray
 # --------------------------------------------------------------------------------------------
 # the generator
 # --------------------------------------------------------------------------------------------
-
-_RATINGS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "ratings")
-
 
 def _stored_ratings(name: str, M: int) -> Optional[np.ndarray]:
     """Ratings of a named case, sized offline from its merit-order DC flows (float32 on disk)."""
