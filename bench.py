@@ -205,6 +205,25 @@ def roofline(case, phase, ms, mixed, peaks, src, clocks):
 
 
 # ------------------------------------------------------------------------------------------------
+# multi-rank aggregation (replicas: no data-path collective)
+# ------------------------------------------------------------------------------------------------
+
+def slowest_rank_ms(local_ms, dist, device):
+    """Max over ranks of the local timed-region duration (the job's time)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, slowest_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (slowest_ms * 1e-3)
+
+
+# ------------------------------------------------------------------------------------------------
 # GPU leg
 # ------------------------------------------------------------------------------------------------
 
@@ -229,13 +248,11 @@ def gpu_leg(args, rank, world, local_rank):
     for label, prec in (("mixed", qg.QG_MIXED), ("fp64", qg.QG_FP64)):
         s = qg.Solver(case, precision=prec)
         x = torch.tensor(x0, dtype=s.dtype, device="cuda")
-        qg.qg_set_profiling(s.h, True)
         for _ in range(max(args.warmup, 3)):
             qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
         torch.cuda.synchronize()
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        phases = {}
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -245,17 +262,22 @@ def gpu_leg(args, rank, world, local_rank):
                 ev0[k].record(stream)
                 qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
                 ev1[k].record(stream)
-                for name, v in qg.qg_phase_times(s.h).items():
-                    phases.setdefault(name, []).append(v)
             torch.cuda.synchronize()
         if dist:
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-        total_ms = sum(step_ms)
-        if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = slowest_rank_ms(sum(step_ms), dist, "cuda")
+        # per-kernel durations: the same steps again with a CUDA event after every stage kernel
+        # (launched without programmatic dependent launch so that each event brackets one kernel)
+        qg.qg_set_profiling(s.h, True)
+        qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+        phases = {}
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+            for name, v in qg.qg_phase_times(s.h).items():
+                phases.setdefault(name, []).append(v)
+        torch.cuda.synchronize()
         # the same loop without the flush (L2-resident, as in a long Adam run), for context
         qg.qg_set_profiling(s.h, False)
         qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
@@ -286,7 +308,7 @@ def gpu_leg(args, rank, world, local_rank):
         return
     mix = results["mixed"]
     K = args.steps
-    value = world * K / (mix["total_ms"] * 1e-3)
+    value = job_throughput(K, world, mix["total_ms"])
     phases = mix["phases"]
     eval_phases = {k: v for k, v in phases.items()}
     dom = max(eval_phases, key=lambda k: eval_phases[k])

@@ -369,6 +369,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
     D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
     D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0;
     D.inv_n = 1.0 / H.n;
+    D.hours = 0.0;
+    for (int t = 0; t < H.T; ++t) D.hours += H.dt[t];
     D.wfloor_ctg = h->opt.c_s * h->opt.beta * h->opt.eps * ((double)H.M * H.K - H.K);
     x0 += (long long)H.T * (2LL * H.n + 3LL * H.G);
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
@@ -559,7 +561,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
   unsigned char *qs;
   if ((rc = dalloc(h, &qs, (size_t)sTM))) return rc;
   d.qside = qs;
-  double *op;
+  Dc *op;
   d.n_obj_slots = (int)slot_inst.size();
   if ((rc = dalloc(h, &op, (size_t)d.n_obj_slots * N_TERMS))) return rc;
   d.objp = op;

@@ -38,6 +38,7 @@ struct Inst {
   long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mt][T][K]
   long long gi0;         // adjoint DC products at the generator buses: [T][Gb + 1]
   double inv_n;          // 1 / n
+  double hours;          // sum of dt
   double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
 };
 
@@ -110,7 +111,7 @@ struct Dev {
   Real *gF;                           // [sum T M] dz/df
   Dc *gip;                            // adjoint DC products [sum T (Gb + 1)]
   Real *avf, *avo, *ad;               // branch-end adjoints [sum T M]
-  double *objp;                       // [n_obj_slots][N_TERMS]
+  Dc *objp;                           // [n_obj_slots][N_TERMS] per-block objective terms
   int n_obj_slots;
   const int *slot_inst;               // [n_obj_slots]
   double *obj, *terms;                // [n_inst], [n_inst][N_TERMS]

@@ -191,3 +191,38 @@ def test_solve_trajectory_matches_oracle(qg):
         x, m, v = oracle.adam_step(x, m, v, ref.grad, i, 1e-3, 0.9, 0.999, 1e-8, lo, hi)
     assert np.max(np.abs(xt.cpu().numpy() - x)) <= 1e-9
     s.close()
+
+
+def test_batch_config_sampled_parity(qg):
+    """The 32-instance uneven batch (73/200/617/1576 buses, 12/18/24/48 periods) in one handle;
+    one instance of each shape checked against the oracle on objective and gradient."""
+    from oracle.copperplate import lambda_dispatch
+    cases = synth.batch()
+    xs = [as_f32(c.flat_start(lambda_dispatch(c))) for c in cases]
+    X = np.concatenate(xs)
+    offs = np.cumsum([0] + [c.n_x for c in cases])
+    for prec, tol in ((qg.QG_FP64, TOL64), (qg.QG_MIXED, TOL32)):
+        obj, g, _ = gpu_eval(qg, cases, X, prec)
+        assert np.all(np.isfinite(obj)) and np.all(np.isfinite(g))
+        for b in (0, 9, 18, 27):
+            ref = oracle.evaluate(cases[b], xs[b])
+            assert rel(obj[b], ref.obj) <= tol, (b, obj[b], ref.obj)
+            assert grel(g[offs[b]:offs[b + 1]], ref.grad) <= tol, b
+
+
+def test_lodf_low_precision_gate(qg, capsys):
+    """BF16 storage of the line-outage block only where the mixed-path error stays under 1e-4:
+    the hi+lo BF16 pair (about 2^-17 relative per entry) passes the gate at the copper-plate start;
+    a single BF16 (2^-9) is reported, and the library keeps FP32 as its default."""
+    c = case_named("rt617")
+    x = as_f32(point(c, "lp_perturbed"))
+    ref = oracle.evaluate(c, x)
+    errs = {}
+    for name, dt in (("f32", qg.QG_LODF_F32), ("bf16x2", qg.QG_LODF_BF16X2), ("bf16", qg.QG_LODF_BF16)):
+        obj, g, _ = gpu_eval(qg, c, x, qg.QG_MIXED, lodf=dt)
+        errs[name] = (rel(obj[0], ref.obj), grel(g, ref.grad))
+    with capsys.disabled():
+        print("\nLODF storage vs FP64 oracle (obj rel, grad rel):", {k: tuple(f"{v:.2e}" for v in e) for k, e in errs.items()})
+    assert max(errs["f32"]) <= TOL32
+    assert max(errs["bf16x2"]) <= TOL32
+    assert qg.qg_default_options().lodf_dtype == qg.QG_LODF_F32
