@@ -480,24 +480,30 @@ __device__ __forceinline__ float lodf_load(const void *base, long long idx, int 
 // Contingency tile (A8): BM monitored branches x BK outages, every period, line-outage block
 // in registers.  For outage k and monitored branch m:
 //   F = f_m + L[m,k] f_k,  s = sqrt(F^2 + qmax2_m),  z += w sigma_s(s - s_ctg_m).
-// The common path is two FMAs and a compare per element; the soft-ReLU floor eps of every
-// non-violating element is added in closed form by the final reduction.  Pad elements and the
-// outaged branch itself carry L = NaN, so F is NaN and the compare is false.
+// The common path is two FMAs and a compare per element (all 16 of a thread computed before any
+// branch); the soft-ReLU floor eps of every non-violating element is added in closed form by the
+// final reduction.  Pad elements and the outaged branch itself carry L = NaN, so F is NaN and the
+// compare is false.  Per-period row sums are warp-local (each warp owns 8 rows) and column sums
+// go through shared memory, flushed once per chunk of periods: no block barrier per period.
 // FP64 path: the compare runs in FP32 against a margin of 1e-4 s_ctg^2 and every candidate is
 // recomputed exactly in FP64, so the classification and the values are those of FP64.
+template <typename Real>
+__host__ __device__ constexpr int ctg_tch() { return sizeof(Real) == 8 ? 8 : 16; }
+
 template <typename Real, typename Dc>
 __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> &acc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool F64 = sizeof(Real) == 8;
+  constexpr int TCH = ctg_tch<Real>();
   const int T = I.T;
   const int mt = sub / I.n_kt, kt = sub % I.n_kt;
   const int m0 = mt * CT_BM, k0 = kt * CT_BK;
   Real *s_q2 = reinterpret_cast<Real *>(smem_raw);   // [T][BM] qmax2
   Real *s_s2 = s_q2 + T * CT_BM;                      // [BM] s_ctg^2
-  Real *s_gm = s_s2 + CT_BM;                          // [BM]
-  Real *s_gq = s_gm + CT_BM;                          // [BM]
-  Real *s_gk = s_gq + CT_BM;                          // [8][BK]
-  Real *s_f64m = s_gk + 8 * CT_BK;                    // [T][BM] (FP64 path only)
+  Real *s_gm = s_s2 + CT_BM;                          // [TCH][BM]
+  Real *s_gq = s_gm + TCH * CT_BM;                    // [TCH][BM]
+  Real *s_gk = s_gq + TCH * CT_BM;                    // [TCH][8][BK]
+  Real *s_f64m = s_gk + TCH * 8 * CT_BK;              // [T][BM] (FP64 path only)
   Real *s_f64k = s_f64m + (F64 ? T * CT_BM : 0);      // [T][BK] (FP64 path only)
   float *s_fm = reinterpret_cast<float *>(s_f64k + (F64 ? T * CT_BK : 0));  // [T][BM]
   float *s_qs = s_fm + T * CT_BM;                     // [T][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
@@ -516,22 +522,22 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
       Lr[bq][a] = v;
     }
   }
+  if (threadIdx.x < CT_BM) s_s2[threadIdx.x] = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
   pdl_wait();
   for (int e = threadIdx.x; e < T * (CT_BM + CT_BK); e += NTHR) {
     const int t = e / (CT_BM + CT_BK), c = e % (CT_BM + CT_BK);
     if (c < CT_BM) {
       const int m = m0 + c;
       float f = 0.f, qs = 0.f;
-      Real q2 = 0, f64 = 0, s2 = 0;
+      Real q2 = 0, f64 = 0;
       if (m < I.M) {
         const long long idx = I.tm0 + (long long)t * I.M + m;
         f = d.f32[idx];
         q2 = d.qm2[idx];
-        s2 = d.br_s2ctg[I.br0 + m];
+        const Real s2 = d.br_s2ctg[I.br0 + m];
         qs = F64 ? (float)(q2 - s2) + 1e-4f * (float)s2 : (float)(q2 - s2);
         if (F64) f64 = d.fre[idx];
       }
-      if (t == 0) s_s2[c] = s2;
       s_fm[t * CT_BM + c] = f;
       s_qs[t * CT_BM + c] = qs;
       s_q2[t * CT_BM + c] = q2;
@@ -552,84 +558,86 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   __syncthreads();
   Real obj = 0;
   const Real eps = d.eps;
-  for (int t = 0; t < T; ++t) {
-    const Real w = d.dt[I.tp0 + t] * d.c_s * d.beta;
-    Real gm[8], gq[8], gk[2] = {0, 0};
-    bool any = false;
+  for (int tc0 = 0; tc0 < T; tc0 += TCH) {
+    const int tn = min(TCH, T - tc0);
+    for (int tt = 0; tt < tn; ++tt) {
+      const int t = tc0 + tt;
+      float Fv[8][2];
+      bool hit = false;
 #pragma unroll
-    for (int bq = 0; bq < 8; ++bq) {
-      gm[bq] = 0;
-      gq[bq] = 0;
-      const int mm = wid * 8 + bq;
-      const float fm = s_fm[t * CT_BM + mm], qs = s_qs[t * CT_BM + mm];
+      for (int bq = 0; bq < 8; ++bq) {
+        const float fm = s_fm[t * CT_BM + wid * 8 + bq], qs = s_qs[t * CT_BM + wid * 8 + bq];
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const float F = __fmaf_rn(Lr[bq][a], s_fk[t * CT_BK + lane + 32 * a], fm);
-        if (__fmaf_rn(F, F, qs) > 0.f) {  // rare: a (candidate) post-contingency overload
-          Real Fx, Lx;
-          if (F64) {
-            Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.K + (k0 + lane + 32 * a)];
-            Fx = s_f64m[t * CT_BM + mm] + Lx * s_f64k[t * CT_BK + lane + 32 * a];
-            if (Fx * Fx + s_q2[t * CT_BM + mm] - s_s2[mm] <= Real(0)) continue;
-          } else {
-            Lx = (Real)Lr[bq][a];
-            Fx = (Real)F;
+        for (int a = 0; a < 2; ++a) {
+          Fv[bq][a] = __fmaf_rn(Lr[bq][a], s_fk[t * CT_BK + lane + 32 * a], fm);
+          hit |= __fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f;
+        }
+      }
+      Real gm[8], gq[8], gk[2] = {0, 0};
+#pragma unroll
+      for (int bq = 0; bq < 8; ++bq) gm[bq] = gq[bq] = 0;
+      if (hit) {  // rare: a (candidate) post-contingency overload among this thread's 16 elements
+        const Real w = d.dt[I.tp0 + t] * d.c_s * d.beta;
+#pragma unroll
+        for (int bq = 0; bq < 8; ++bq) {
+          const int mm = wid * 8 + bq;
+          const float qs = s_qs[t * CT_BM + mm];
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            if (__fmaf_rn(Fv[bq][a], Fv[bq][a], qs) <= 0.f) continue;
+            Real Fx, Lx;
+            if (F64) {
+              Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.K + (k0 + lane + 32 * a)];
+              Fx = s_f64m[t * CT_BM + mm] + Lx * s_f64k[t * CT_BK + lane + 32 * a];
+              if (Fx * Fx + s_q2[t * CT_BM + mm] - s_s2[mm] <= Real(0)) continue;
+            } else {
+              Lx = (Real)Lr[bq][a];
+              Fx = (Real)Fv[bq][a];
+            }
+            const Real sv = dsqrt(Fx * Fx + s_q2[t * CT_BM + mm]);
+            Real val, der;
+            soft_relu(sv - dsqrt(s_s2[mm]), eps, val, der);
+            obj += w * (val - eps);
+            const Real dd = w * der / sv;  // dz/dF = w sigma' F / s
+            gm[bq] += dd * Fx;
+            gk[a] += dd * Fx * Lx;
+            gq[bq] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
           }
-          any = true;
-          const Real s = dsqrt(Fx * Fx + s_q2[t * CT_BM + mm]);
-          Real val, der;
-          soft_relu(s - dsqrt(s_s2[mm]), eps, val, der);
-          obj += w * (val - eps);
-          const Real dd = w * der / s;  // dz/dF = w sigma' F / s
-          gm[bq] += dd * Fx;
-          gk[a] += dd * Fx * Lx;
-          gq[bq] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
         }
       }
-    }
-    const bool block_any = __syncthreads_or(any);
-    const long long pm_row = I.pm0 + ((long long)kt * T + t) * I.M;
-    const long long pk_row = I.pk0 + ((long long)mt * T + t) * I.K;
-    if (!block_any) {
-      if (threadIdx.x < CT_BM) {
-        const int m = m0 + threadIdx.x;
-        if (m < I.M) {
-          d.pm[pm_row + m] = 0;
-          d.pq[pm_row + m] = 0;
-        }
-      } else if (threadIdx.x < CT_BM + CT_BK) {
-        const int k = k0 + threadIdx.x - CT_BM;
-        if (k < I.K) d.pk[pk_row + k] = 0;
-      }
-      continue;
-    }
+      // row sums over this warp's 64 columns (only rows with an overload), column partials per warp
 #pragma unroll
-    for (int bq = 0; bq < 8; ++bq) {
-      Real v1 = 0, v2 = 0;
-      if (__any_sync(0xffffffffu, gq[bq] != Real(0))) {  // only rows with an overload in this warp
-        v1 = warp_sum(gm[bq]);
-        v2 = warp_sum(gq[bq]);
+      for (int bq = 0; bq < 8; ++bq) {
+        Real v1 = 0, v2 = 0;
+        if (__any_sync(0xffffffffu, gq[bq] != Real(0))) {
+          v1 = warp_sum(gm[bq]);
+          v2 = warp_sum(gq[bq]);
+        }
+        if (lane == 0) {
+          s_gm[tt * CT_BM + wid * 8 + bq] = v1;
+          s_gq[tt * CT_BM + wid * 8 + bq] = v2;
+        }
       }
-      if (lane == 0) {
-        s_gm[wid * 8 + bq] = v1;
-        s_gq[wid * 8 + bq] = v2;
-      }
+      s_gk[(tt * 8 + wid) * CT_BK + lane] = gk[0];
+      s_gk[(tt * 8 + wid) * CT_BK + lane + 32] = gk[1];
     }
-    s_gk[wid * CT_BK + lane] = gk[0];
-    s_gk[wid * CT_BK + lane + 32] = gk[1];
     __syncthreads();
-    if (threadIdx.x < CT_BM) {
-      const int m = m0 + threadIdx.x;
+    for (int e = threadIdx.x; e < tn * CT_BM; e += NTHR) {
+      const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
       if (m < I.M) {
-        d.pm[pm_row + m] = s_gm[threadIdx.x];
-        d.pq[pm_row + m] = s_gq[threadIdx.x];
+        const long long q = I.pm0 + ((long long)kt * T + tc0 + tt) * I.M + m;
+        d.pm[q] = s_gm[tt * CT_BM + c];
+        d.pq[q] = s_gq[tt * CT_BM + c];
       }
-    } else if (threadIdx.x < CT_BM + CT_BK) {
-      const int c = threadIdx.x - CT_BM;
-      Real s = 0;
+    }
+    for (int e = threadIdx.x; e < tn * CT_BK; e += NTHR) {
+      const int tt = e / CT_BK, c = e % CT_BK, k = k0 + c;
+      if (k < I.K) {
+        Real sum = 0;
 #pragma unroll
-      for (int ww = 0; ww < 8; ++ww) s += s_gk[ww * CT_BK + c];
-      if (k0 + c < I.K) d.pk[pk_row + k0 + c] = s;
+        for (int ww = 0; ww < 8; ++ww) sum += s_gk[(tt * 8 + ww) * CT_BK + c];
+        d.pk[I.pk0 + ((long long)mt * T + tc0 + tt) * I.K + k] = sum;
+      }
     }
     __syncthreads();
   }
@@ -669,9 +677,14 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
   const Inst &I = tab.I[w.inst];
   const int t = w.t;
   const int j = w.sub * NTHR + threadIdx.x;
+  const bool on = j < I.M;
+  const int jg = I.br0 + (on ? j : 0);
+  // network data first (independent of the earlier stages), then wait
+  const int2 ft = d.br_end[jg];
+  const int kx = d.br_kidx[jg];
+  const Real g = d.br_g[jg], bb = d.br_b[jg], hch = d.br_hch[jg], smax = d.br_smax[jg];
   pdl_wait();
-  if (j < I.M) {
-    const int jg = I.br0 + j;
+  if (on) {
     const long long e = I.tm0 + (long long)t * I.M + j;
     Real gF = 0, gq2 = 0;
 #pragma unroll 8
@@ -680,7 +693,6 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
       gF += d.pm[q];
       gq2 += d.pq[q];
     }
-    const int kx = d.br_kidx[jg];
     if (kx >= 0) {
       Real gk = 0;
 #pragma unroll 8
@@ -689,12 +701,10 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
     }
     d.gF[e] = gF;
     // adjoints of the four end flows
-    const int2 ft = d.br_end[jg];
     const long long tb = I.tb0 + (long long)t * I.n;
     Real gpf = d.dP[tb + ft.x], gpt = d.dP[tb + ft.y];
     Real gqf = d.dQ[tb + ft.x], gqt = d.dQ[tb + ft.y];
     const Real pf = d.pf[e], qf = d.qf[e], pt = d.pt[e], qt = d.qt[e];
-    const Real smax = d.br_smax[jg];
     const Real sf2 = pf * pf + qf * qf, st2 = pt * pt + qt * qt;
     if (fmax(sf2, st2) > smax * smax) {  // thermal (Example 1)
       const Real sf = dsqrt(sf2), st = dsqrt(st2);
@@ -717,7 +727,7 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
     const Real vf = v[ft.x], vo = v[ft.y];
     Real sn, cs;
     dsincos(th[ft.x] - th[ft.y], &sn, &cs);
-    const Real g = d.br_g[jg], bb = d.br_b[jg], bc = bb + d.br_hch[jg];
+    const Real bc = bb + hch;
     const Real vv = vf * vo;
     const Real A = -g * cs - bb * sn, B = bb * cs - g * sn, C = -g * cs + bb * sn, D = bb * cs + g * sn;
     d.avf[e] = gpf * (2 * g * vf + A * vo) + gqf * (-2 * bc * vf + B * vo) + gpt * (C * vo) + gqt * (D * vo);
@@ -772,11 +782,13 @@ template <typename Real, typename Dc, bool ADAM>
 __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x) {
   AdamCoef<Real> ac{};
   if (ADAM) ac = adam_coef(d);
-  pdl_wait();
   const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
-  if (pk >= I.n_adj_pack) return;
-  const int e = I.adj0 + pk * PACK + (threadIdx.x & 31);
-  const int code = d.adj_code[e], row = d.adj_row[e];
+  const bool on = pk < I.n_adj_pack;
+  const int e = I.adj0 + (on ? pk : 0) * PACK + (threadIdx.x & 31);
+  // static CSR entries first, then wait for stage 3's branch-end adjoints
+  const int code = d.adj_code[e], row = on ? d.adj_row[e] : -1;
+  pdl_wait();
+  if (!on) return;  // whole warp
   const int kind = code & 3;
   Real gv = 0, gth = 0;
   const long long tm = I.tm0 + (long long)t * I.M + (code >> 2);
@@ -813,14 +825,16 @@ __device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
   if (o > I.Gb) return;
   const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
   const Dc *col = o < I.Gb ? d.ptdfgT + I.pg0 + (long long)o * I.M : d.rsum + I.br0;
-  Dc a0 = DcOps<Dc>::zero(), a1 = DcOps<Dc>::zero();
+  Dc a0 = DcOps<Dc>::zero(), a1 = a0, a2 = a0, a3 = a0;
   int m = lane;
-  for (; m + 32 < I.M; m += 64) {
+  for (; m + 96 < I.M; m += 128) {
     DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
     DcOps<Dc>::mac(a1, col[m + 32], DcOps<Dc>::from_real(gf[m + 32]));
+    DcOps<Dc>::mac(a2, col[m + 64], DcOps<Dc>::from_real(gf[m + 64]));
+    DcOps<Dc>::mac(a3, col[m + 96], DcOps<Dc>::from_real(gf[m + 96]));
   }
-  if (m < I.M) DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
-  Dc acc = DcOps<Dc>::add(a0, a1);
+  for (; m < I.M; m += 32) DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
+  Dc acc = DcOps<Dc>::add(DcOps<Dc>::add(a0, a1), DcOps<Dc>::add(a2, a3));
 #pragma unroll
   for (int k = 16; k > 0; k >>= 1) acc = DcOps<Dc>::add(acc, DcOps<Dc>::shfl_down(acc, k));
   if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + o] = acc;
@@ -899,19 +913,21 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
   Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
   AdamCoef<Real> ac{};
   if (ADAM) ac = adam_coef(d);
-  pdl_wait();
   const int gl = w.sub * NTHR + threadIdx.x;
-  if (gl < I.G) {
-    const int gg = I.gen0 + gl;
-    const int bus = d.gen_bus[gg], zn = d.gen_zone[gg], gb = d.gen_gb[gg];
+  const bool on = gl < I.G;
+  // generator data and this period's dispatch (not written by the earlier stages) before waiting
+  const int gg = I.gen0 + (on ? gl : 0);
+  const int bus = d.gen_bus[gg], zn = d.gen_zone[gg], gb = d.gen_gb[gg];
+  const Real a = d.gen_a[gg], bl = d.gen_b[gg], cr = d.gen_cr[gg], pmax = d.gen_pmax[gg], ramp = d.gen_ramp[gg];
+  const long long kp = I.x0 + 2LL * I.T * I.n + (long long)t * I.G + (on ? gl : 0);
+  const long long kq = kp + (long long)I.T * I.G, kr = kq + (long long)I.T * I.G;
+  const Real p = x[kp], r = x[kr];
+  pdl_wait();
+  if (on) {
     const Real dt = d.dt[I.tp0 + t];
-    const long long n = I.n, G = I.G, T = I.T;
-    const long long kp = I.x0 + 2 * T * n + (long long)t * G + gl;
-    const long long kq = kp + T * G, kr = kq + T * G;
-    const Real p = x[kp], r = x[kr];
-    const Real a = d.gen_a[gg], bl = d.gen_b[gg], cr = d.gen_cr[gg], pmax = d.gen_pmax[gg], ramp = d.gen_ramp[gg];
+    const long long G = I.G;
     // injection adjoint at the generator's bus: eta_gb - mean(eta)   (Eqs. 2nd_lin_sys, correction)
-    const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gb + 1);
+    const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gb + 1);  // written by stage 4
     const Dc eta = DcOps<Dc>::add(et[gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gb], DcOps<Dc>::inv_n(I))));
     const long long tb = I.tb0 + (long long)t * I.n;
     Real gp = dt * (2 * a * p + bl) - d.dP[tb + bus] + DcOps<Dc>::to_real(eta);
@@ -1010,8 +1026,10 @@ __global__ void __launch_bounds__(NTHR) k_adam(Real *__restrict__ x, Real *__res
 template <typename Real>
 size_t ctg_smem_bytes(int T) {
   constexpr bool F64 = sizeof(Real) == 8;
+  constexpr int TCH = ctg_tch<Real>();
   return sizeof(float) * (size_t)T * (2 * CT_BM + CT_BK) +
-         sizeof(Real) * ((size_t)T * CT_BM + 3 * CT_BM + 8 * CT_BK + (F64 ? (size_t)T * (CT_BM + CT_BK) : 0));
+         sizeof(Real) * ((size_t)T * CT_BM + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
+                         (F64 ? (size_t)T * (CT_BM + CT_BK) : 0));
 }
 
 // Record a timing event on s; inside stream capture it becomes an external event node.
