@@ -173,6 +173,39 @@ int qg_phase_times(qg_ctx *h, float *ms, int32_t cap);
 
 const char *qg_last_error(const qg_ctx *h);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned warm start (an AI-systems addition; the paper's future-work remark in Sec. V motivates
+ * it): an MLP  Y = W3 relu(W2 relu(W1 X + b1) + b2) + b3  mapping a load profile to an initial
+ * point, trained on the GPU by the library's own BF16 tensor-core GEMMs (FP32 accumulation) and
+ * an Adam step.  GEMM operands (X, the weights, the hidden activations, and the back-propagated
+ * dY, dZ2, dZ1) are rounded to BF16 where they enter a GEMM; the master weights, biases, bias
+ * gradients and Adam moments are FP32.  Parameters are laid out as W1 (H x I, row-major), b1
+ * (H), W2 (H x H), b2, W3 (O x H), b3 (O).  All pointers are device pointers; x is batch x I
+ * row-major, y and target batch x O.  Weights start from seeded He-scaled normal draws.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct qg_mlp qg_mlp;
+
+int qg_mlp_create(qg_mlp **out, int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, uint64_t seed);
+void qg_mlp_destroy(qg_mlp *m);
+int64_t qg_mlp_num_params(const qg_mlp *m);
+int qg_mlp_set_stream(qg_mlp *m, void *stream);
+
+/* Inference: y = MLP(x) for `batch` rows (batch <= max_batch). */
+int qg_mlp_forward(qg_mlp *m, const float *x, int32_t batch, float *y);
+
+/* One training step on the mean squared error mean((Y - target)^2): forward, backward, and (if
+ * lr > 0) an Adam update with the given lr, beta1, beta2 (eps 1e-8).  loss (device double, may
+ * be NULL) receives the batch loss before the update. */
+int qg_mlp_train_step(qg_mlp *m, const float *x, const float *target, int32_t batch, double lr, double beta1,
+                      double beta2, double *loss);
+
+/* FP32 master parameters and the gradient of the last training step (device arrays of
+ * qg_mlp_num_params floats). */
+int qg_mlp_get_params(qg_mlp *m, float *w);
+int qg_mlp_set_params(qg_mlp *m, const float *w);
+int qg_mlp_get_grads(qg_mlp *m, float *g);
+const char *qg_mlp_last_error(const qg_mlp *m);
+
 /* Build identification: major*10000 + minor*100 + patch. */
 int qg_version(void);
 

@@ -2,7 +2,7 @@
 
     python -m paper_2310_06650_gb300.build
 
-The two translation units compile in parallel; the shared library lands in
+The translation units compile in parallel; the shared library lands in
 paper_2310_06650_gb300/_build/ (git-ignored).
 """
 from __future__ import annotations
@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqg.so")
-SOURCES = ["qg_kernels.cu", "qg_host.cu"]
+SOURCES = ["qg_kernels.cu", "qg_host.cu", "qg_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

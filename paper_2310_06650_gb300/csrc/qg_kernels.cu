@@ -584,7 +584,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           const float qs = s_qs[t * CT_BM + mm];
 #pragma unroll
           for (int a = 0; a < 2; ++a) {
-            if (__fmaf_rn(Fv[bq][a], Fv[bq][a], qs) <= 0.f) continue;
+            if (!(__fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f)) continue;  // NaN (pad, outaged branch) fails too
             Real Fx, Lx;
             if (F64) {
               Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.K + (k0 + lane + 32 * a)];

@@ -83,6 +83,16 @@ def _load():
         "qg_phase_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int32]),
         "qg_last_error": (C.c_char_p, [vp]),
         "qg_version": (C.c_int, []),
+        "qg_mlp_create": (C.c_int, [C.POINTER(vp), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64]),
+        "qg_mlp_destroy": (None, [vp]),
+        "qg_mlp_num_params": (C.c_int64, [vp]),
+        "qg_mlp_set_stream": (C.c_int, [vp, vp]),
+        "qg_mlp_forward": (C.c_int, [vp, vp, C.c_int32, vp]),
+        "qg_mlp_train_step": (C.c_int, [vp, vp, vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp]),
+        "qg_mlp_get_params": (C.c_int, [vp, vp]),
+        "qg_mlp_set_params": (C.c_int, [vp, vp]),
+        "qg_mlp_get_grads": (C.c_int, [vp, vp]),
+        "qg_mlp_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -94,7 +104,9 @@ def _load():
 _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_adam_step", "qg_solve", "qg_breakdown",
-            "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_last_error", "qg_version")
+            "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_last_error", "qg_version",
+            "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
+            "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
 PHASES = ("s1", "s2", "s3", "s4", "s5", "adam")
 
 
@@ -290,3 +302,55 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------------------------------------
+# learned warm start (MLP)
+# ------------------------------------------------------------------------------------------------
+
+def _mcheck(rc: int, m=None):
+    if rc != QG_OK:
+        raise QGError(rc, _lib.qg_mlp_last_error(m).decode(errors="replace"))
+
+
+def qg_mlp_create(n_in: int, n_hidden: int, n_out: int, max_batch: int, seed: int = 0) -> int:
+    m = C.c_void_p()
+    _mcheck(_lib.qg_mlp_create(C.byref(m), n_in, n_hidden, n_out, max_batch, seed), None)
+    return m.value
+
+
+def qg_mlp_destroy(m: int) -> None:
+    _lib.qg_mlp_destroy(m)
+
+
+def qg_mlp_num_params(m: int) -> int:
+    return int(_lib.qg_mlp_num_params(m))
+
+
+def qg_mlp_set_stream(m: int, stream_ptr: int) -> None:
+    _mcheck(_lib.qg_mlp_set_stream(m, stream_ptr), m)
+
+
+def qg_mlp_forward(m: int, x, batch: int, y) -> None:
+    _mcheck(_lib.qg_mlp_forward(m, _ptr(x), batch, _ptr(y)), m)
+
+
+def qg_mlp_train_step(m: int, x, target, batch: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                      loss=None) -> None:
+    _mcheck(_lib.qg_mlp_train_step(m, _ptr(x), _ptr(target), batch, lr, beta1, beta2, _ptr(loss)), m)
+
+
+def qg_mlp_get_params(m: int, w) -> None:
+    _mcheck(_lib.qg_mlp_get_params(m, _ptr(w)), m)
+
+
+def qg_mlp_set_params(m: int, w) -> None:
+    _mcheck(_lib.qg_mlp_set_params(m, _ptr(w)), m)
+
+
+def qg_mlp_get_grads(m: int, g) -> None:
+    _mcheck(_lib.qg_mlp_get_grads(m, _ptr(g)), m)
+
+
+def qg_mlp_last_error(m: Optional[int] = None) -> str:
+    return _lib.qg_mlp_last_error(m).decode(errors="replace")

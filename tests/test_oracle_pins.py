@@ -370,3 +370,33 @@ def test_planted_wrong_smw_sign_is_caught(monkeypatch):
         return orig(case, net, th_hat_b, qmax2, dt, U, 2.0 - den)  # 1 + y a^T u instead of 1 - y a^T u
     monkeypatch.setattr(Q, "_ctg_period_smw", bad)
     assert abs(oracle.evaluate(c, x, mode="smw").obj - good.obj) > 1e-6 * abs(good.obj)
+
+
+# --------------------------------------------------------------------------------------------
+# warm-start MLP oracle
+# --------------------------------------------------------------------------------------------
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    n_in, n_h, n_out, B = 7, 5, 3, 4
+    npar = n_h * n_in + n_h + n_h * n_h + n_h + n_out * n_h + n_out
+    w = rng.normal(0, 0.5, npar)
+    X = rng.normal(size=(B, n_in))
+    Tg = rng.normal(size=(B, n_out))
+    _, _, g = mlp.forward_backward(w, X, Tg, n_in, n_h, n_out, quantize=False)
+    h = 1e-6
+    for i in range(npar):
+        wp = w.copy(); wp[i] += h
+        wm = w.copy(); wm[i] -= h
+        fd = (mlp.loss_only(wp, X, Tg, n_in, n_h, n_out) - mlp.loss_only(wm, X, Tg, n_in, n_h, n_out)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), i
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    a = np.concatenate([rng.normal(size=1000) * 10.0 ** rng.integers(-8, 8, 1000), [0.0, -0.0, 1.0, 3.0e38]])
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(a), ref)
