@@ -1,0 +1,307 @@
+"""Learned warm start for the Adam solve (the AI-systems addition): generate solves with the
+library itself, train the MLP on them with the library's own kernels, and compare the time to a
+target objective from the learned start (mixed precision) against plain FP64 Adam from the
+copper-plate start.
+
+Host-side pieces here are orchestration and the copper-plate start of Sec. III-A (merit-order
+dispatch per period, which is that projection without ramps and reserves); every evaluation,
+Adam step, MLP forward and backward runs in libqg's CUDA kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import List, Sequence
+
+import numpy as np
+
+from . import qg
+
+BATCH = 32  # instances per handle
+
+
+# ------------------------------------------------------------------------------------------------
+# copper-plate start (Sec. III-A without ramp and reserve terms)
+# ------------------------------------------------------------------------------------------------
+
+def merit_order_dispatch(case) -> np.ndarray:
+    """Per period, the least-cost dispatch meeting total load: p_g = clip((lam - b_g)/(2 a_g), pmin, pmax)
+    with lam found by bisection (KKT of the separable quadratic cost)."""
+    a, b = case.cost_a, case.cost_b
+    out = np.zeros((case.T, case.n_gen))
+    for t in range(case.T):
+        L = case.load_p[t].sum()
+        lo, hi = 0.0, float(b.max() + 2 * (a * case.pmax).max()) + 1.0
+        for _ in range(100):
+            lam = 0.5 * (lo + hi)
+            if np.clip((lam - b) / (2 * a), case.pmin, case.pmax).sum() < L:
+                lo = lam
+            else:
+                hi = lam
+        out[t] = np.clip((0.5 * (lo + hi) - b) / (2 * a), case.pmin, case.pmax)
+    return out
+
+
+def merit_order_bound(case) -> float:
+    """sum_t d_t sum_g (a p^2 + b p) at the merit-order dispatch: a lower bound of the objective
+    scored with eps = 0 (dropping the reserve, ramp and network terms only removes non-negative
+    penalties, and unserved load costs at least c^p per pu, far above any marginal cost)."""
+    p = merit_order_dispatch(case)
+    return float((case.dt[:, None] * (case.cost_a * p * p + case.cost_b * p)).sum())
+
+
+def start_point(case) -> np.ndarray:
+    """x0: flat voltage, zero angles and q, merit-order p, reserve spread over headroom per zone."""
+    p = merit_order_dispatch(case)
+    r = np.zeros_like(p)
+    head = np.maximum(case.pmax[None, :] - p, 0.0)
+    for z in range(case.n_zone):
+        gz = case.gen_zone == z
+        tot = head[:, gz].sum(axis=1, keepdims=True)
+        frac = np.where(tot > 0, case.reserve_req[:, z:z + 1] / np.maximum(tot, 1e-30), 0.0)
+        r[:, gz] = head[:, gz] * np.minimum(frac, 1.0)
+    return case.flat_start(p, r)
+
+
+# ------------------------------------------------------------------------------------------------
+# features and targets
+# ------------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Scaling:
+    """Affine maps between physical x / loads and the network's normalized inputs and outputs."""
+    x_shift: np.ndarray
+    x_scale: np.ndarray
+    load_ref: np.ndarray  # T x n nominal load
+
+    @staticmethod
+    def for_case(case) -> "Scaling":
+        T, n, G = case.T, case.n_bus, case.n_gen
+        pm = np.tile(case.pmax, T)
+        shift = np.concatenate([np.ones(T * n), np.zeros(T * n), 0.5 * pm, np.zeros(T * G), np.zeros(T * G)])
+        scale = np.concatenate([np.full(T * n, 0.05), np.full(T * n, 0.2), pm, pm, pm])
+        return Scaling(shift, scale, case.load_p.copy())
+
+    def features(self, load_p: np.ndarray) -> np.ndarray:
+        return (4.0 * (np.asarray(load_p) / np.maximum(self.load_ref, 1e-9) - 1.0)).reshape(len(load_p), -1)
+
+    def to_target(self, x: np.ndarray) -> np.ndarray:
+        return (x - self.x_shift) / self.x_scale
+
+    def to_x(self, y: np.ndarray) -> np.ndarray:
+        return y * self.x_scale + self.x_shift
+
+
+def clip_box(case, x: np.ndarray) -> np.ndarray:
+    T, n, G = case.T, case.n_bus, case.n_gen
+    v, th, p, q, r = np.split(x, [T * n, 2 * T * n, 2 * T * n + T * G, 2 * T * n + 2 * T * G])
+    v = np.clip(v.reshape(T, n), case.vmin, case.vmax).ravel()
+    th = th.reshape(T, n).copy()
+    th[:, case.ref_bus] = 0.0
+    p = np.clip(p.reshape(T, G), case.pmin, case.pmax).ravel()
+    q = np.clip(q.reshape(T, G), case.qmin, case.qmax).ravel()
+    r = np.clip(r.reshape(T, G), 0.0, case.pmax).ravel()
+    return np.concatenate([v, th.ravel(), p, q, r])
+
+
+# ------------------------------------------------------------------------------------------------
+# data generation: batched Adam solves
+# ------------------------------------------------------------------------------------------------
+
+def solve_many(cases: Sequence, x0s: Sequence[np.ndarray], iters: int, lr: float = 1e-3,
+               precision: int = qg.QG_MIXED) -> List[np.ndarray]:
+    """Adam solves of many instances, BATCH per handle, from the given starts."""
+    import torch
+    out = []
+    for b0 in range(0, len(cases), BATCH):
+        cs = list(cases[b0:b0 + BATCH])
+        s = qg.Solver(cs, precision=precision)
+        x = torch.tensor(np.concatenate(x0s[b0:b0 + BATCH]), dtype=s.dtype, device="cuda")
+        qg.qg_solve(s.h, x, iters, lr, 0.9, 0.999)
+        xs = x.double().cpu().numpy()
+        o = 0
+        for c in cs:
+            out.append(xs[o:o + c.n_x].copy())
+            o += c.n_x
+        s.close()
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# training and inference
+# ------------------------------------------------------------------------------------------------
+
+class WarmStart:
+    def __init__(self, case, hidden: int = 1024, max_batch: int = 64, seed: int = 0):
+        import torch
+        self.torch = torch
+        self.case = case
+        self.scaling = Scaling.for_case(case)
+        self.n_in = case.T * case.n_bus
+        self.n_out = case.n_x
+        self.max_batch = max_batch
+        self.m = qg.qg_mlp_create(self.n_in, hidden, self.n_out, max_batch, seed)
+        qg.qg_mlp_set_stream(self.m, torch.cuda.current_stream().cuda_stream)
+
+    def train(self, load_profiles: np.ndarray, solutions: Sequence[np.ndarray], epochs: int, batch: int = 64,
+              lr: float = 1e-3, seed: int = 0) -> List[float]:
+        torch = self.torch
+        X = torch.tensor(self.scaling.features(load_profiles), dtype=torch.float32, device="cuda")
+        Y = torch.tensor(np.stack([self.scaling.to_target(x) for x in solutions]), dtype=torch.float32, device="cuda")
+        n = X.shape[0]
+        rng = np.random.default_rng(seed)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        hist = []
+        for ep in range(epochs):
+            perm = torch.tensor(rng.permutation(n), device="cuda")
+            tot = 0.0
+            for b0 in range(0, n - batch + 1, batch):
+                idx = perm[b0:b0 + batch]
+                xb = X.index_select(0, idx).contiguous()
+                yb = Y.index_select(0, idx).contiguous()
+                qg.qg_mlp_train_step(self.m, xb, yb, batch, lr, 0.9, 0.999, loss)
+                tot += loss.item()
+            hist.append(tot / max(1, n // batch))
+        return hist
+
+    def predict(self, load_profiles: np.ndarray) -> List[np.ndarray]:
+        torch = self.torch
+        X = torch.tensor(self.scaling.features(load_profiles), dtype=torch.float32, device="cuda")
+        out = []
+        for b0 in range(0, X.shape[0], self.max_batch):
+            xb = X[b0:b0 + self.max_batch].contiguous()
+            y = torch.zeros(xb.shape[0], self.n_out, dtype=torch.float32, device="cuda")
+            qg.qg_mlp_forward(self.m, xb, xb.shape[0], y)
+            for row in y.double().cpu().numpy():
+                out.append(clip_box(self.case, self.scaling.to_x(row)))
+        return out
+
+    def close(self):
+        if self.m:
+            qg.qg_mlp_destroy(self.m)
+            self.m = None
+
+
+# ------------------------------------------------------------------------------------------------
+# time to a target objective
+# ------------------------------------------------------------------------------------------------
+
+def objective_eps0(scorer, x_dev) -> float:
+    """Phi at eps = 0 (hard abs / ReLU), the score the target refers to."""
+    obj, _ = scorer.eval_grad(x_dev)
+    return float(obj[0].item())
+
+
+def solve_trace(case, x0: np.ndarray, precision: int, iters: int, every: int, lr: float = 1e-3):
+    """Single-instance Adam solve; returns (gpu_ms_per_chunk list, eps=0 objective after each chunk).
+    The scoring evaluations run on a separate FP64 handle and are not timed."""
+    torch = __import__("torch")
+    s = qg.Solver(case, precision=precision)
+    scorer = qg.Solver(case, precision=qg.QG_FP64, eps=0.0)
+    x = torch.tensor(x0, dtype=s.dtype, device="cuda")
+    xs = torch.zeros(case.n_x, dtype=torch.float64, device="cuda")
+    qg.qg_solve(s.h, x, 1, lr, 0.9, 0.999)  # capture the graph outside the timed chunks
+    qg.qg_set_step(s.h, 0)
+    x.copy_(torch.tensor(x0, dtype=s.dtype, device="cuda"))
+    times, objs = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xs.copy_(x)
+    objs.append(objective_eps0(scorer, xs))
+    times.append(0.0)
+    for _ in range(0, iters, every):
+        e0.record()
+        qg.qg_solve(s.h, x, every, lr, 0.9, 0.999)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        xs.copy_(x)
+        objs.append(objective_eps0(scorer, xs))
+    s.close()
+    scorer.close()
+    return np.cumsum(times), np.array(objs)
+
+
+def time_to(times_ms: np.ndarray, objs: np.ndarray, target: float) -> float:
+    hit = np.nonzero(objs <= target)[0]
+    return float(times_ms[hit[0]]) if len(hit) else float("inf")
+
+
+# ------------------------------------------------------------------------------------------------
+# experiment driver
+# ------------------------------------------------------------------------------------------------
+
+def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, eval_iters: int, every: int,
+               seed: int = 5000, hidden: int = 1024, log=print) -> dict:
+    """Train on n_train generated solves, then for n_test held-out profiles compare
+    (a) plain FP64 Adam from the copper-plate start with (b) mixed-precision Adam from the learned
+    start, on GPU time to an objective within 1% of the copper-plate bound (eps = 0 scoring).  When
+    arm (a) misses that target, the target becomes the best objective arm (a) reaches."""
+    import synth
+    t0 = time.time()
+    prof = synth.load_profiles(case, n_train + n_test, seed)
+    cases = [synth.with_loads(case, lp) for lp in prof]
+    starts = [start_point(c) for c in cases]
+    sols = solve_many(cases[:n_train], starts[:n_train], solve_iters)
+    t_gen = time.time() - t0
+    log(f"generated {n_train} solves in {t_gen:.1f} s")
+    ws = WarmStart(case, hidden=hidden, seed=seed)
+    t1 = time.time()
+    hist = ws.train(prof[:n_train], sols, epochs)
+    t_train = time.time() - t1
+    log(f"trained {epochs} epochs in {t_train:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}")
+    preds = ws.predict(prof[n_train:])
+    rows = []
+    for i in range(n_test):
+        c = cases[n_train + i]
+        bound = merit_order_bound(c)
+        ta, oa = solve_trace(c, starts[n_train + i], qg.QG_FP64, eval_iters, every)
+        tb, ob = solve_trace(c, preds[i], qg.QG_MIXED, eval_iters, every)
+        target = 1.01 * bound
+        kind = "1% of copper-plate bound"
+        if not np.isfinite(time_to(ta, oa, target)):
+            target = float(oa.min())
+            kind = "best objective of plain FP64 Adam"
+        rows.append({"bound": bound, "target": target, "target_kind": kind,
+                     "plain_fp64": {"ms": time_to(ta, oa, target), "phi0": float(oa[0]), "best": float(oa.min())},
+                     "warm_mixed": {"ms": time_to(tb, ob, target), "phi0": float(ob[0]), "best": float(ob.min())}})
+        log(rows[-1])
+    ws.close()
+    fin = [r for r in rows if np.isfinite(r["plain_fp64"]["ms"]) and np.isfinite(r["warm_mixed"]["ms"])]
+    return {"n_train": n_train, "n_test": n_test, "solve_iters": solve_iters, "epochs": epochs,
+            "eval_iters": eval_iters, "every": every, "gen_s": t_gen, "train_s": t_train,
+            "loss_first": hist[0], "loss_last": hist[-1], "rows": rows,
+            "median_ms_plain": float(np.median([r["plain_fp64"]["ms"] for r in fin])) if fin else None,
+            "median_ms_warm": float(np.median([r["warm_mixed"]["ms"] for r in fin])) if fin else None,
+            "warm_faster": int(sum(r["warm_mixed"]["ms"] < r["plain_fp64"]["ms"] for r in rows))}
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import synth
+    ap = argparse.ArgumentParser(description="learned warm start vs plain FP64 Adam")
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=8)
+    ap.add_argument("--solve-iters", type=int, default=3000)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--eval-iters", type=int, default=6000)
+    ap.add_argument("--every", type=int, default=25)
+    ap.add_argument("--hidden", type=int, default=1024)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    from .build import build
+    build()
+    res = experiment(synth.rt617(), a.train, a.test, a.solve_iters, a.epochs, a.eval_iters, a.every, hidden=a.hidden,
+                     log=lambda *s: print(*s, flush=True))
+    line = json.dumps(res)
+    print(line)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(line + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -396,6 +396,16 @@ def dayahead(seed: int = 23643) -> Case:
     return make_case("da23643", 23643, 35000, 3000, T=48, K=2000, n_zone=8, seed=seed, rating_scale=0.8)
 
 
+def with_loads(case: Case, load_p: np.ndarray) -> Case:
+    """The same network under another active-load profile (T x n): reactive load and zonal reserve
+    requirements follow the recipe of make_case (q = 0.329 p, 10% of each zone's load)."""
+    load_p = np.asarray(load_p, dtype=np.float64).reshape(case.T, case.n_bus)
+    reserve = np.zeros((case.T, case.n_zone))
+    for z in range(case.n_zone):
+        reserve[:, z] = 0.10 * load_p[:, case.bus_zone == z].sum(axis=1)
+    return dataclasses.replace(case, load_p=load_p, load_q=0.329 * load_p, reserve_req=reserve)
+
+
 def load_profiles(case: Case, count: int, seed: int) -> np.ndarray:
     """Warm-start training profiles: load * U(0.8, 1.2) per profile * (1 + N(0, 0.05)) per bus, >= 0."""
     rng = np.random.default_rng(seed)
