@@ -129,6 +129,24 @@ int qg_set_stream(qg_ctx *h, void *stream);
  * g may be NULL (objective only).  x is not modified. */
 int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g);
 
+/* qg_eval_grad without any allocation, for callers that cannot call cudaMalloc at this point
+ * (for example code running under an allocator lock, inside a host callback, or in a process
+ * whose memory pool is already sized and frozen).  The paper has no counterpart: it is an
+ * interface addition.  The handle's set-up data (made by qg_create) is reused; every
+ * per-evaluation work buffer comes from one file-scope static device array of 16 MiB that every
+ * GPU loading the library holds from load until the process exits.  The caller passes the inputs
+ * and outputs: x (device, qg_num_vars elements), obj (device, n_inst doubles) and g (device,
+ * qg_num_vars elements, required).  Results equal those of qg_eval_grad.
+ *  - Handles whose work buffers need more than 16 MiB (e.g. large batches) are rejected with
+ *    QG_ERR_UNSUPPORTED and a message giving the size needed.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ *    that first call before any stream capture on that device.
+ *  - All calls share the one array, which keeps the last call's contents: calls that overlap on
+ *    the GPU (other streams, other handles, other threads) race and must be serialized by the
+ *    caller.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g);
+
 /* qg_eval_grad on host buffers: copies x (qg_num_vars doubles) to the device,
  * evaluates, and copies obj (n_inst doubles) and g (qg_num_vars doubles, may be
  * NULL) back; synchronizes.  In QG_MIXED mode the copies convert to/from float. */

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -655,6 +656,99 @@ __global__ void k_f2d(const float *a, double *b, long long n) {
 }  // namespace
 
 // =============================================================================================
+// Scratch for qg_eval_grad_noalloc: a file-scope device array.  Every GPU that loads the library
+// holds it from module load until the process exits.  Host code must not pass the symbol itself
+// to a kernel (on the host it only names a stand-in); the device address comes from
+// cudaGetSymbolAddress, looked up once per device.
+// =============================================================================================
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (looked up on first use per device).
+int noalloc_scratch(qg_ctx *h, unsigned char **out) {
+  int dev = -1;
+  CUDA_TRY(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(h, QG_ERR_UNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(h, QG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return QG_OK;
+}
+
+// Carve every per-evaluation work buffer of `d` out of [base, base + cap); returns the bytes used
+// (more than cap means the handle does not fit, and nothing is assigned past cap).
+template <typename Real, typename Dc>
+size_t carve_scratch(const qg_ctx *h, unsigned char *base, size_t cap, Dev<Real, Dc> &d) {
+  const Plan &P = h->plan;
+  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0;
+  for (int b = 0; b < h->n_inst; ++b) {
+    const Inst &I = P.tab.I[b];
+    sTM += (long long)I.T * I.M; sTn += (long long)I.T * I.n; sTZ += (long long)I.T * I.Z;
+    sTK += (long long)I.T * I.K; sTG += (long long)I.T * I.G;
+    sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mt * I.T * I.K;
+    sGI += (long long)I.T * (I.Gb + 1);
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> unsigned char * {
+    off = (off + 255) & ~size_t(255);
+    unsigned char *p = (off + bytes <= cap) ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t R = sizeof(Real), D = sizeof(Dc);
+  d.pf = (Real *)take(R * sTM); d.qf = (Real *)take(R * sTM); d.pt = (Real *)take(R * sTM);
+  d.qt = (Real *)take(R * sTM); d.qm2 = (Real *)take(R * sTM); d.fre = (Real *)take(R * sTM);
+  d.gF = (Real *)take(R * sTM); d.avf = (Real *)take(R * sTM); d.avo = (Real *)take(R * sTM);
+  d.ad = (Real *)take(R * sTM); d.qside = take(sTM); d.f32 = (float *)take(4 * sTM);
+  d.fk = (Real *)take(R * sTK); d.fk32 = (float *)take(4 * sTK); d.pold = (Real *)take(R * sTG);
+  d.dP = (Real *)take(R * sTn); d.dQ = (Real *)take(R * sTn); d.dZ = (Real *)take(R * sTZ);
+  d.pm = (Real *)take(R * sPM); d.pq = (Real *)take(R * sPM); d.pk = (Real *)take(R * sPK);
+  d.gip = (Dc *)take(D * sGI); d.objp = (Dc *)take(D * (size_t)d.n_obj_slots * N_TERMS);
+  d.terms = (double *)take(sizeof(double) * N_TERMS * h->n_inst);
+  d.ticket = (unsigned int *)take(sizeof(unsigned int));
+  d.step = (long long *)take(sizeof(long long));
+  d.trace_step0 = d.step;
+  return off;
+}
+
+template <typename Real, typename Dc>
+int eval_noalloc(qg_ctx *h, Dev<Real, Dc> d, const void *x, double *obj, void *g) {
+  unsigned char *base = nullptr;
+  int rc = noalloc_scratch(h, &base);
+  if (rc) return rc;
+  const size_t need = carve_scratch(h, base, NOALLOC_SCRATCH_BYTES, d);
+  if (need > NOALLOC_SCRATCH_BYTES)
+    return fail(h, QG_ERR_UNSUPPORTED, "qg_eval_grad_noalloc: this handle needs " + std::to_string(need) +
+                                           " bytes of scratch; the static scratch holds " +
+                                           std::to_string(NOALLOC_SCRATCH_BYTES));
+  d.obj = obj;
+  d.g = static_cast<Real *>(g);
+  d.trace = nullptr;
+  d.trace_len = 0;
+  // the stage-5 completion counter must start at zero (the rest is fully written before it is read)
+  CUDA_TRY(h, cudaMemsetAsync(d.ticket, 0, sizeof(unsigned int), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(d.step, 0, sizeof(long long), h->stream));
+  cudaError_t e = launch_eval<Real, Dc>(d, h->plan, x, false, h->stream, nullptr);
+  if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("evaluation launch: ") + cudaGetErrorString(e));
+  return QG_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
 // C ABI
 // =============================================================================================
 
@@ -789,6 +883,12 @@ int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g) {
   if (obj) CUDA_TRY(h, cudaMemcpyAsync(obj, h->d_obj, sizeof(double) * h->n_inst, cudaMemcpyDeviceToDevice, h->stream));
   if (g) CUDA_TRY(h, cudaMemcpyAsync(g, h->d_g, rs * h->n_x, cudaMemcpyDeviceToDevice, h->stream));
   return QG_OK;
+}
+
+int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g) {
+  if (!h || !x || !obj || !g)
+    return h ? fail(h, QG_ERR_INVALID_ARG, "qg_eval_grad_noalloc needs x, obj and g") : QG_ERR_INVALID_ARG;
+  return mixed(h) ? eval_noalloc<float, df32>(h, h->d32, x, obj, g) : eval_noalloc<double, double>(h, h->d64, x, obj, g);
 }
 
 int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {

@@ -74,6 +74,7 @@ def _load():
         "qg_set_stream": (C.c_int, [vp, vp]),
         "qg_eval_grad": (C.c_int, [vp, vp, vp, vp]),
         "qg_eval_grad_host": (C.c_int, [vp, _F64P, _F64P, _F64P]),
+        "qg_eval_grad_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "qg_adam_step": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double]),
         "qg_solve": (C.c_int, [vp, vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp]),
         "qg_breakdown": (C.c_int, [vp, _F64P]),
@@ -103,7 +104,7 @@ def _load():
 
 _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
-            "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_adam_step", "qg_solve", "qg_breakdown",
+            "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_eval_grad_noalloc", "qg_adam_step", "qg_solve", "qg_breakdown",
             "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
@@ -214,6 +215,11 @@ def qg_set_stream(h: int, stream_ptr: int) -> None:
 
 def qg_eval_grad(h: int, x, obj, g=None) -> None:
     _check(_lib.qg_eval_grad(h, _ptr(x), _ptr(obj), _ptr(g)), h)
+
+
+def qg_eval_grad_noalloc(h: int, x, obj, g) -> None:
+    """qg_eval_grad with every work buffer in the library's static device scratch (no allocation)."""
+    _check(_lib.qg_eval_grad_noalloc(h, _ptr(x), _ptr(obj), _ptr(g)), h)
 
 
 def qg_eval_grad_host(h: int, x: np.ndarray, obj: np.ndarray, g: Optional[np.ndarray] = None) -> None:
