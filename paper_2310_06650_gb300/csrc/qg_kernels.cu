@@ -355,6 +355,7 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   const int t = t0 + tl, m = m0 + ml;
   const Real *p = x + I.x0 + 2LL * I.T * I.n;
   if (sub == 0) {  // dispatch snapshot for the ramp terms of a fused Adam update
+#pragma unroll 4
     for (int e = threadIdx.x; e < DCF_TC * I.G; e += NTHR) {
       const int tt = t0 + e / I.G, gl = e % I.G;
       if (tt < I.T) d.pold[I.tg0 + (long long)tt * I.G + gl] = p[(long long)tt * I.G + gl];
@@ -365,6 +366,7 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   for (int c0 = 0; c0 < I.Gb; c0 += GBC) {
     const int cn = min(GBC, I.Gb - c0);
     __syncthreads();
+#pragma unroll 4
     for (int e = threadIdx.x; e < DCF_TC * cn; e += NTHR) {
       const int r = e / cn, c = e % cn, tt = t0 + r;
       Dc s = DcOps<Dc>::zero();
@@ -376,6 +378,7 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
       }
       s_pg[r][c] = s;
     }
+#pragma unroll 8
     for (int e = threadIdx.x; e < DCF_BM * cn; e += NTHR) {
       const int r = e / cn, c = e % cn;
       s_pt[r][c] = (m0 + r < I.M) ? d.ptdfg[I.pg0 + (long long)(m0 + r) * I.Gb + c0 + c] : DcOps<Dc>::zero();
@@ -524,6 +527,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   }
   if (threadIdx.x < CT_BM) s_s2[threadIdx.x] = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
   pdl_wait();
+#pragma unroll 8
   for (int e = threadIdx.x; e < T * (CT_BM + CT_BK); e += NTHR) {
     const int t = e / (CT_BM + CT_BK), c = e % (CT_BM + CT_BK);
     if (c < CT_BM) {
@@ -868,6 +872,7 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
     Dc a[N_TERMS];
 #pragma unroll
     for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
+#pragma unroll 4
     for (int s = threadIdx.x; s < d.n_obj_slots; s += NTHR) {
       if (d.slot_inst[s] != b) continue;
 #pragma unroll

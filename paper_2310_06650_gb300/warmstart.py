@@ -69,8 +69,8 @@ def start_point(case) -> np.ndarray:
 
 @dataclasses.dataclass
 class Scaling:
-    """Affine maps between physical x / loads and the network's normalized inputs and outputs."""
-    x_shift: np.ndarray
+    """The network learns a correction to the copper-plate start: target = (x* - x0) / scale,
+    inputs are relative load deviations from the nominal profile."""
     x_scale: np.ndarray
     load_ref: np.ndarray  # T x n nominal load
 
@@ -78,18 +78,17 @@ class Scaling:
     def for_case(case) -> "Scaling":
         T, n, G = case.T, case.n_bus, case.n_gen
         pm = np.tile(case.pmax, T)
-        shift = np.concatenate([np.ones(T * n), np.zeros(T * n), 0.5 * pm, np.zeros(T * G), np.zeros(T * G)])
         scale = np.concatenate([np.full(T * n, 0.05), np.full(T * n, 0.2), pm, pm, pm])
-        return Scaling(shift, scale, case.load_p.copy())
+        return Scaling(scale, case.load_p.copy())
 
     def features(self, load_p: np.ndarray) -> np.ndarray:
         return (4.0 * (np.asarray(load_p) / np.maximum(self.load_ref, 1e-9) - 1.0)).reshape(len(load_p), -1)
 
-    def to_target(self, x: np.ndarray) -> np.ndarray:
-        return (x - self.x_shift) / self.x_scale
+    def to_target(self, x: np.ndarray, x0: np.ndarray) -> np.ndarray:
+        return (x - x0) / self.x_scale
 
-    def to_x(self, y: np.ndarray) -> np.ndarray:
-        return y * self.x_scale + self.x_shift
+    def to_x(self, y: np.ndarray, x0: np.ndarray) -> np.ndarray:
+        return x0 + y * self.x_scale
 
 
 def clip_box(case, x: np.ndarray) -> np.ndarray:
@@ -142,12 +141,19 @@ class WarmStart:
         self.max_batch = max_batch
         self.m = qg.qg_mlp_create(self.n_in, hidden, self.n_out, max_batch, seed)
         qg.qg_mlp_set_stream(self.m, torch.cuda.current_stream().cuda_stream)
+        # start from a near-zero correction: shrink the output layer's initial weights
+        w = torch.zeros(qg.qg_mlp_num_params(self.m), dtype=torch.float32, device="cuda")
+        qg.qg_mlp_get_params(self.m, w)
+        o3 = hidden * self.n_in + hidden + hidden * hidden + hidden
+        w[o3:o3 + self.n_out * hidden] *= 0.01
+        qg.qg_mlp_set_params(self.m, w)
 
-    def train(self, load_profiles: np.ndarray, solutions: Sequence[np.ndarray], epochs: int, batch: int = 64,
-              lr: float = 1e-3, seed: int = 0) -> List[float]:
+    def train(self, load_profiles: np.ndarray, starts: Sequence[np.ndarray], solutions: Sequence[np.ndarray],
+              epochs: int, batch: int = 64, lr: float = 1e-3, seed: int = 0) -> List[float]:
         torch = self.torch
         X = torch.tensor(self.scaling.features(load_profiles), dtype=torch.float32, device="cuda")
-        Y = torch.tensor(np.stack([self.scaling.to_target(x) for x in solutions]), dtype=torch.float32, device="cuda")
+        Y = torch.tensor(np.stack([self.scaling.to_target(x, x0) for x, x0 in zip(solutions, starts)]),
+                         dtype=torch.float32, device="cuda")
         n = X.shape[0]
         rng = np.random.default_rng(seed)
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -164,7 +170,7 @@ class WarmStart:
             hist.append(tot / max(1, n // batch))
         return hist
 
-    def predict(self, load_profiles: np.ndarray) -> List[np.ndarray]:
+    def predict(self, load_profiles: np.ndarray, starts: Sequence[np.ndarray]) -> List[np.ndarray]:
         torch = self.torch
         X = torch.tensor(self.scaling.features(load_profiles), dtype=torch.float32, device="cuda")
         out = []
@@ -172,8 +178,8 @@ class WarmStart:
             xb = X[b0:b0 + self.max_batch].contiguous()
             y = torch.zeros(xb.shape[0], self.n_out, dtype=torch.float32, device="cuda")
             qg.qg_mlp_forward(self.m, xb, xb.shape[0], y)
-            for row in y.double().cpu().numpy():
-                out.append(clip_box(self.case, self.scaling.to_x(row)))
+            for k, row in enumerate(y.double().cpu().numpy()):
+                out.append(clip_box(self.case, self.scaling.to_x(row, starts[b0 + k])))
         return out
 
     def close(self):
@@ -246,10 +252,10 @@ def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, e
     log(f"generated {n_train} solves in {t_gen:.1f} s")
     ws = WarmStart(case, hidden=hidden, seed=seed)
     t1 = time.time()
-    hist = ws.train(prof[:n_train], sols, epochs)
+    hist = ws.train(prof[:n_train], starts[:n_train], sols, epochs)
     t_train = time.time() - t1
     log(f"trained {epochs} epochs in {t_train:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}")
-    preds = ws.predict(prof[n_train:])
+    preds = ws.predict(prof[n_train:], starts[n_train:])
     rows = []
     for i in range(n_test):
         c = cases[n_train + i]
