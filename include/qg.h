@@ -44,6 +44,7 @@ extern "C" {
 
 enum { QG_FP64 = 0, QG_MIXED = 1 };                              /* qg_options.precision */
 enum { QG_LODF_F32 = 0, QG_LODF_BF16 = 1, QG_LODF_BF16X2 = 2 };  /* qg_options.lodf_dtype (mixed) */
+enum { QG_DC_AUTO = 0, QG_DC_DENSE = 1, QG_DC_SPARSE = 2 };      /* qg_options.dc_solver */
 
 typedef struct qg_ctx qg_ctx; /* opaque handle; owns all device memory it allocates */
 
@@ -89,7 +90,16 @@ typedef struct {
   int32_t precision;   /* QG_FP64 or QG_MIXED                                   */
   int32_t lodf_dtype;  /* QG_LODF_*; QG_FP64 always stores the LODF in FP64     */
   int32_t adam_paper_eps; /* 1: numerator (mhat + eps) exactly as printed in Alg. 3 */
-  int32_t reserved;
+  int32_t dc_solver;   /* how the DC solves of Sec. II-E run on the device:
+                        * QG_DC_DENSE: products with the PTDF rows of the generator buses
+                        *   (set-up holds Yhat^-1 densely; n <= 8192);
+                        * QG_DC_SPARSE: the sparse factor Yhat = L diag(D_S, S) L^T with a dense
+                        *   tail, two gathers and one dense product per solve, for the base flows
+                        *   (Eq. Yb_solve) and the adjoint (Eq. 2nd_lin_sys); no PTDF is formed.
+                        *   One instance per handle (QG_ERR_UNSUPPORTED otherwise);
+                        * QG_DC_AUTO (0, the default): sparse for a single instance of more
+                        *   than 4096 buses, dense otherwise.
+                        * Both compute the same quantities (the results agree to rounding). */
 } qg_options;
 
 /* Fill *opt with the defaults: c_p = c_q = 1e4, c_s = c_rz = rho = 1e3,
@@ -138,7 +148,8 @@ int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g);
  * and outputs: x (device, qg_num_vars elements), obj (device, n_inst doubles) and g (device,
  * qg_num_vars elements, required).  Results equal those of qg_eval_grad.
  *  - Handles whose work buffers need more than 16 MiB (e.g. large batches) are rejected with
- *    QG_ERR_UNSUPPORTED and a message giving the size needed.
+ *    QG_ERR_UNSUPPORTED and a message giving the size needed; so are handles on the sparse DC
+ *    solver (QG_DC_SPARSE), whose solve buffers are not carved from the array.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
  *    that first call before any stream capture on that device.
  *  - All calls share the one array, which keeps the last call's contents: calls that overlap on

@@ -24,6 +24,9 @@ What it computes (plain definitions, numpy FP64):
   (Eq. 2nd_lin_sys) and the slack correction (Eq. correction).
   ``mode="brute"`` instead deletes the outaged branch and re-solves the
   contingency Laplacian directly.
+  Linear solves with the reduced Laplacian use its explicit inverse for small
+  grids and a sparse LU factorization (scipy SuperLU) above SPARSE_N buses;
+  both are the same solve of Eqs. Yb_solve and 2nd_lin_sys.
 
 Readings taken where the paper is silent or ambiguous are listed in the
 design notes; the ones that change arithmetic are repeated at their use below.
@@ -34,6 +37,10 @@ import dataclasses
 from typing import Optional, Sequence
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+SPARSE_N = 4096  # grids above this many buses are solved through a sparse factorization
 
 
 # ------------------------------------------------------------------------------------------
@@ -171,23 +178,63 @@ def bus_mismatch(case, pf, qf, pt, qt, p, q):
 @dataclasses.dataclass
 class DCNet:
     y: np.ndarray        # [M] branch susceptance -b_sr = x / (r^2 + x^2)
-    E: np.ndarray        # [M, n] signed incidence (+1 at from, -1 at to)
+    E: object            # [M, n] signed incidence (+1 at from, -1 at to); scipy CSR when sparse
     keep: np.ndarray     # [n-1] bus ids with the reference bus removed
-    Yhat: np.ndarray     # [n-1, n-1] reduced Laplacian  E_hat^T Y_x E_hat
-    Yinv: np.ndarray     # [n-1, n-1] its inverse (explicit, small cases)
+    Yhat: object         # [n-1, n-1] reduced Laplacian  E_hat^T Y_x E_hat
+    Yinv: Optional[np.ndarray] = None  # its inverse (explicit, small cases)
+    lu: object = None    # its sparse LU factorization (large cases)
+    U: Optional[np.ndarray] = None     # cached u_k = Yhat^-1 a_k for the outage list ctg_of_U
+    den: Optional[np.ndarray] = None
+    ctg_of_U: Optional[np.ndarray] = None
+
+    @property
+    def sparse(self) -> bool:
+        return self.lu is not None
+
+    def solve(self, B):
+        """Yhat^-1 B for a dense right-hand side (vector or matrix)."""
+        return self.Yinv @ B if self.lu is None else self.lu.solve(np.asarray(B, dtype=np.float64))
 
 
-def dc_network(case) -> DCNet:
+def dc_network(case, sparse: Optional[bool] = None) -> DCNet:
     """Reading: Y_x holds -b_sr = x / (r^2 + x^2), consistent with p = -b_sr (theta_i - theta_i')."""
     n, M = case.n_bus, case.n_branch
     y = case.br_x / (case.br_r ** 2 + case.br_x ** 2)
+    keep = np.array([i for i in range(n) if i != case.ref_bus])
+    if sparse is None:
+        sparse = n > SPARSE_N
+    if sparse:
+        E = sp.csr_matrix((np.r_[np.ones(M), -np.ones(M)],
+                           (np.r_[np.arange(M), np.arange(M)], np.r_[case.br_from, case.br_to])), shape=(M, n))
+        Eh = E[:, keep]
+        Yhat = (Eh.T @ sp.diags(y) @ Eh).tocsc()
+        return DCNet(y=y, E=E, keep=keep, Yhat=Yhat, lu=spla.splu(Yhat, permc_spec="MMD_AT_PLUS_A"))
     E = np.zeros((M, n))
     E[np.arange(M), case.br_from] += 1.0
     E[np.arange(M), case.br_to] -= 1.0
-    keep = np.array([i for i in range(n) if i != case.ref_bus])
     Eh = E[:, keep]
     Yhat = Eh.T @ (y[:, None] * Eh)
     return DCNet(y=y, E=E, keep=keep, Yhat=Yhat, Yinv=np.linalg.inv(Yhat))
+
+
+def _kdot(Ek, H):
+    """[K] column-wise a_k^T H[:, k] for the rows a_k of Ek (dense or sparse)."""
+    if sp.issparse(Ek):
+        return np.asarray(Ek.multiply(H.T).sum(axis=1)).ravel()
+    return np.einsum("kj,jk->k", Ek, H)
+
+
+def outage_columns(case, net: DCNet):
+    """u_k = Yhat^-1 a_k (a_k the reduced incidence row of outaged branch k) and the SMW
+    denominators 1 - y_k a_k^T u_k (reading: Yhat_k = Yhat - y_k a_k a_k^T); cached on net."""
+    if net.U is not None and np.array_equal(net.ctg_of_U, case.ctg):
+        return net.U, net.den
+    Eh = net.E[:, net.keep]
+    Ak = Eh[case.ctg]
+    U = net.solve(Ak.T.toarray() if net.sparse else Ak.T)
+    den = 1.0 - net.y[case.ctg] * _kdot(Ak, U)
+    net.U, net.den, net.ctg_of_U = U, den, np.array(case.ctg)
+    return U, den
 
 
 def dc_injections(case, p):
@@ -202,10 +249,13 @@ def dc_injections(case, p):
 def dc_base_flows(case, net: DCNet, pbar):
     """Eq. Yb_solve / p_flow with b_t = 0 (no phase shifters): theta_hat = Yhat^-1 pbar_hat,
     f = Y_x E_hat theta_hat.  Returns theta (T, n) with theta_ref = 0 and f (T, M)."""
-    th_hat = np.linalg.solve(net.Yhat, pbar[:, net.keep].T).T
+    if net.sparse:
+        th_hat = net.solve(pbar[:, net.keep].T).T
+    else:
+        th_hat = np.linalg.solve(net.Yhat, pbar[:, net.keep].T).T
     th = np.zeros_like(pbar)
     th[:, net.keep] = th_hat
-    f = (th @ net.E.T) * net.y[None, :]
+    f = (net.E @ th.T).T * net.y[None, :] if net.sparse else (th @ net.E.T) * net.y[None, :]
     return th, f
 
 
@@ -243,8 +293,8 @@ def _ctg_period_smw(case, net: DCNet, th_hat_b, qmax2, dt, U, den):
     gq2 = (dsig * 0.5 * inv_s).sum(axis=1)                   # dz / d(qmax^2), summed over k
     # Eq. 2nd_lin_sys: eta_k = Yhat_k^-1 E_hat^T Y_x,k d_k, with Yhat_k^-1 applied by SMW
     W = Eh.T @ (y[:, None] * D)                              # [n-1, K]
-    H = net.Yinv @ W
-    H = H + U * ((y[ks] * np.einsum("kj,jk->k", Eh[ks], H)) / den)[None, :]
+    H = net.solve(W)
+    H = H + U * ((y[ks] * _kdot(Eh[ks], H)) / den)[None, :]
     eta = np.zeros((case.n_bus, K))
     eta[net.keep] = H
     gin = (eta - eta.mean(axis=0, keepdims=True)).sum(axis=1)  # Eq. correction, summed over k
@@ -253,6 +303,8 @@ def _ctg_period_smw(case, net: DCNet, th_hat_b, qmax2, dt, U, den):
 
 def _ctg_period_brute(case, net: DCNet, pbar_t, qmax2, dt):
     """One period, every outage re-solved on the outaged Laplacian (no SMW)."""
+    if net.sparse:
+        raise ValueError("brute mode takes small (dense) grids only")
     K = case.K
     Eh = net.E[:, net.keep]
     y = net.y
@@ -301,7 +353,7 @@ TERM_NAMES = ("cost", "zp", "zq", "zs", "zrz", "zhead", "zramp", "zctg")
 
 
 def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[float] = None,
-             periods: Optional[Sequence[int]] = None) -> Result:
+             periods: Optional[Sequence[int]] = None, net: Optional[DCNet] = None) -> Result:
     """Phi(x) and its gradient.
 
     mode: "smw" (rank-1 corrections, Eq. rank_correct) or "brute" (re-solve each outage).
@@ -309,6 +361,7 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
           to score a point).
     periods: restrict the contingency term to these periods (sampling at large sizes);
           other terms always cover every period.
+    net : the case's DC network (dc_network), to reuse its factorization across calls.
     """
     if eps is not None and eps != case.eps:
         case = dataclasses.replace(case, eps=eps)
@@ -385,7 +438,8 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
         gp[:-1] += dD - dU
 
     # --- contingencies (Sec. II-E)
-    net = dc_network(case)
+    if net is None:
+        net = dc_network(case)
     _, pbar = dc_injections(case, p)
     th_dc, fbase = dc_base_flows(case, net, pbar)
     use_qf = qf * qf >= qt * qt           # reading: the q of the worse end, ties to "fr"
@@ -394,9 +448,7 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     gin_all = np.zeros((T, n))
     gq2_all = np.zeros((T, case.n_branch))
     if case.K > 0:
-        Eh = net.E[:, net.keep]
-        U = net.Yinv @ Eh[case.ctg].T                       # u_k, [n-1, K]
-        den = 1.0 - net.y[case.ctg] * np.einsum("kj,jk->k", Eh[case.ctg], U)
+        U, den = outage_columns(case, net)                 # u_k [n-1, K], SMW denominators [K]
         plist = range(T) if periods is None else periods
         for t in plist:
             if mode == "brute":

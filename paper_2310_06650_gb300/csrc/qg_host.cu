@@ -26,6 +26,8 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int DENSE_MAX_N = 8192;  // the dense inverse used at set-up holds n^2 doubles
+constexpr int SPARSE_AUTO_N = 4096; // QG_DC_AUTO picks the sparse factor above this many buses
+constexpr int TAIL_DEGREE = 32;     // minimum-degree elimination stops above this degree
 
 struct HostInst {
   int n, M, G, Z, T, K, ref;
@@ -43,6 +45,11 @@ struct HostInst {
   std::vector<double> lodf;   // M x K
   // warp packs (code, row) of the two bus CSRs
   std::vector<int> bal_code, bal_row, adj_code, adj_row;
+  // sparse DC mode: factor with a dense tail, node positions, gather lists (see qg_sparse.h)
+  bool sparse = false;
+  int nS = 0, nT = 0, levels = 0;
+  std::vector<int> bus_pos, pos_bus, pos_gb, fw_ptr, fw_col, bw_ptr, bw_col, inc_ptr, inc_code, adj_rows;
+  std::vector<double> fw_val, bw_val, dinv, sinv, z1;
 };
 
 }  // namespace
@@ -190,6 +197,120 @@ bool pack_rows(const std::vector<std::vector<int>> &rows, std::vector<int> &code
   return true;
 }
 
+int build_packs(qg_ctx *h, HostInst &I, int b);
+
+// Error for outages whose SMW denominator vanishes (the outage islands the grid).
+int islanding_error(qg_ctx *h, int b, const std::vector<int> &bad_k) {
+  std::string s = "instance " + std::to_string(b) + ": outage of branch(es)";
+  for (size_t q = 0; q < bad_k.size() && q < 8; ++q) s += " " + std::to_string(bad_k[q]);
+  s += " islands the grid (|1 - PTDF_kk| < 1e-9)";
+  return fail(h, QG_ERR_ISLANDING, s);
+}
+
+// Sparse DC set-up (Sec. II-E) for large grids, all in FP64: the factor Yhat = L diag(D_S, S) L^T
+// with minimum-degree elimination up to degree TAIL_DEGREE and the inverse of the dense tail
+// Schur complement S; node positions (eliminated nodes in order, then the tail); the forward
+// gather rows of [M1; M2] and the backward gather rows (the reach columns, see qg_sparse.h);
+// z1 = Yhat^-1 1 and PTDF 1 = y_m (z1_f - z1_o) for the uniform slack; and the line-outage block
+// L[m,k] = y_m a_m^T u_k / (1 - y_k a_k^T u_k) from the solves u_k = Yhat^-1 a_k.  No PTDF.
+int build_dc_sparse(qg_ctx *h, HostInst &I, int b, const std::vector<int> &red,
+                    std::vector<std::map<int, double>> &off, std::vector<double> &diag) {
+  const int n = I.n, M = I.M, K = I.K, nr = n - 1;
+  TailLDL F;
+  if (!F.factor(nr, off, diag, TAIL_DEGREE))
+    return fail(h, QG_ERR_ISLANDING, "instance " + std::to_string(b) + ": the DC Laplacian is singular (disconnected grid)");
+  off.clear();
+  I.nS = F.n_sparse();
+  I.nT = (int)F.tail.size();
+  I.levels = F.levels;
+  const std::vector<int> pos = F.positions();  // reduced id -> position
+  I.bus_pos.assign(n, -1);
+  I.pos_bus.assign(nr, -1);
+  I.pos_gb.assign(nr, -1);
+  std::vector<int> gmap(n, -1);
+  for (size_t q = 0; q < I.gbus.size(); ++q) gmap[I.gbus[q]] = (int)q;
+  for (int i = 0; i < n; ++i)
+    if (red[i] >= 0) {
+      const int p = pos[red[i]];
+      I.bus_pos[i] = p;
+      I.pos_bus[p] = i;
+      I.pos_gb[p] = gmap[i];
+    }
+  std::vector<std::vector<std::pair<int, double>>> R;
+  F.reach_columns(R);
+  // backward rows: the reach columns themselves; forward rows: their transpose
+  I.bw_ptr.assign(1, 0);
+  I.bw_col.clear();
+  I.bw_val.clear();
+  std::vector<int> cnt(nr, 0);
+  for (int q = 0; q < I.nS; ++q) {
+    for (auto &e : R[q]) {
+      I.bw_col.push_back(e.first);
+      I.bw_val.push_back(e.second);
+      ++cnt[e.first];
+    }
+    I.bw_ptr.push_back((int)I.bw_col.size());
+  }
+  I.fw_ptr.assign(nr + 1, 0);
+  for (int p = 0; p < nr; ++p) I.fw_ptr[p + 1] = I.fw_ptr[p] + cnt[p];
+  I.fw_col.assign(I.fw_ptr[nr], 0);
+  I.fw_val.assign(I.fw_ptr[nr], 0.0);
+  std::vector<int> fill(I.fw_ptr.begin(), I.fw_ptr.end() - 1);
+  for (int q = 0; q < I.nS; ++q)
+    for (auto &e : R[q]) {
+      I.fw_col[fill[e.first]] = q;
+      I.fw_val[fill[e.first]++] = e.second;
+    }
+  I.dinv.resize(I.nS);
+  for (int q = 0; q < I.nS; ++q) I.dinv[q] = 1.0 / F.cols[q].d;
+  I.sinv = F.Sinv;
+  I.adj_rows.clear();
+  for (int q = 0; q < I.nS; ++q)
+    if (I.pos_gb[q] >= 0) I.adj_rows.push_back(q);
+  // incident branches per position (+ at the from-end)
+  std::vector<std::vector<int>> inc(nr);
+  for (int j = 0; j < M; ++j) {
+    if (I.bus_pos[I.from[j]] >= 0) inc[I.bus_pos[I.from[j]]].push_back(j << 1);
+    if (I.bus_pos[I.to[j]] >= 0) inc[I.bus_pos[I.to[j]]].push_back(j << 1 | 1);
+  }
+  I.inc_ptr.assign(1, 0);
+  I.inc_code.clear();
+  for (int p = 0; p < nr; ++p) {
+    I.inc_code.insert(I.inc_code.end(), inc[p].begin(), inc[p].end());
+    I.inc_ptr.push_back((int)I.inc_code.size());
+  }
+  // z1 = Yhat^-1 1, PTDF 1
+  std::vector<double> ones(nr, 1.0);
+  F.solve(ones.data());
+  I.z1.assign(nr, 0.0);
+  for (int r = 0; r < nr; ++r) I.z1[pos[r]] = ones[r];
+  auto zb = [&](int bus) { return red[bus] >= 0 ? ones[red[bus]] : 0.0; };
+  I.rsum.assign(M, 0.0);
+  for (int m = 0; m < M; ++m) I.rsum[m] = I.y[m] * (zb(I.from[m]) - zb(I.to[m]));
+  // line-outage block from K solves
+  I.lodf.assign((size_t)M * K, 0.0);
+  std::vector<char> bad(K, 0);
+  parallel_for(K, [&](int k) {
+    const int jk = I.ctg[k];
+    std::vector<double> u(nr, 0.0);
+    if (red[I.from[jk]] >= 0) u[red[I.from[jk]]] += 1.0;
+    if (red[I.to[jk]] >= 0) u[red[I.to[jk]]] -= 1.0;
+    F.solve(u.data());
+    auto ub = [&](int bus) { return red[bus] >= 0 ? u[red[bus]] : 0.0; };
+    const double den = 1.0 - I.y[jk] * (ub(I.from[jk]) - ub(I.to[jk]));
+    if (std::fabs(den) < 1e-9) {
+      bad[k] = 1;
+      return;
+    }
+    for (int m = 0; m < M; ++m) I.lodf[(size_t)m * K + k] = I.y[m] * (ub(I.from[m]) - ub(I.to[m])) / den;
+  });
+  std::vector<int> bad_k;
+  for (int k = 0; k < K; ++k)
+    if (bad[k]) bad_k.push_back(I.ctg[k]);
+  if (!bad_k.empty()) return islanding_error(h, b, bad_k);
+  return QG_OK;
+}
+
 // DC network set-up (Sec. II-E), all in FP64:
 //   y_j = -b_sr = x / (r^2 + x^2);  Yhat = E_hat^T Y_x E_hat (reference bus removed);
 //   Z = Yhat^-1 (zero row and column at the reference bus), from sparse LDL^T solves;
@@ -199,6 +320,20 @@ bool pack_rows(const std::vector<std::vector<int>> &rows, std::vector<int> &code
 // Kept for the kernels: PTDF columns of the generator buses, PTDF load_t and PTDF 1.
 int build_dc(qg_ctx *h, HostInst &I, int b) {
   const int n = I.n, M = I.M, K = I.K, T = I.T;
+  // generator buses
+  std::vector<int> gmap(n, -1);
+  I.gbus.clear();
+  for (int g = 0; g < I.G; ++g) gmap[I.gen_bus[g]] = 0;
+  for (int i = 0; i < n; ++i)
+    if (gmap[i] == 0) {
+      gmap[i] = (int)I.gbus.size();
+      I.gbus.push_back(i);
+    }
+  I.gen_gb.resize(I.G);
+  for (int g = 0; g < I.G; ++g) I.gen_gb[g] = gmap[I.gen_bus[g]];
+  I.ltot.assign(T, 0.0);
+  for (int t = 0; t < T; ++t)
+    for (int i = 0; i < n; ++i) I.ltot[t] += I.load_p[(size_t)t * n + i];
   I.y.resize(M); I.gsr.resize(M); I.bsr.resize(M);
   for (int j = 0; j < M; ++j) {
     const double den = I.r[j] * I.r[j] + I.x[j] * I.x[j];
@@ -222,6 +357,11 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
       off[bb][a] -= I.y[j];
     }
   }
+  if (I.sparse) {
+    int rc = build_dc_sparse(h, I, b, red, off, diag);
+    if (rc) return rc;
+    return build_packs(h, I, b);
+  }
   SparseLDL F;
   if (!F.factor(nr, off, diag))
     return fail(h, QG_ERR_ISLANDING, "instance " + std::to_string(b) + ": the DC Laplacian is singular (disconnected grid)");
@@ -243,17 +383,6 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
       Zm[(size_t)i * n + j] = v;
       Zm[(size_t)j * n + i] = v;
     }
-  // generator buses
-  std::vector<int> gmap(n, -1);
-  I.gbus.clear();
-  for (int g = 0; g < I.G; ++g) gmap[I.gen_bus[g]] = 0;
-  for (int i = 0; i < n; ++i)
-    if (gmap[i] == 0) {
-      gmap[i] = (int)I.gbus.size();
-      I.gbus.push_back(i);
-    }
-  I.gen_gb.resize(I.G);
-  for (int g = 0; g < I.G; ++g) I.gen_gb[g] = gmap[I.gen_bus[g]];
   const int Gb = (int)I.gbus.size();
   // PTDF rows: generator-bus columns, load products and row sums
   I.ptdfg.assign((size_t)M * Gb, 0.0);
@@ -276,9 +405,6 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
       I.cload[(size_t)t * M + m] = a;
     }
   }
-  I.ltot.assign(T, 0.0);
-  for (int t = 0; t < T; ++t)
-    for (int i = 0; i < n; ++i) I.ltot[t] += I.load_p[(size_t)t * n + i];
   // line-outage block
   I.lodf.assign((size_t)M * K, 0.0);
   std::vector<int> bad_k;
@@ -293,13 +419,13 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
     }
     for (int m = 0; m < M; ++m) I.lodf[(size_t)m * K + k] = I.y[m] * (u(I.from[m]) - u(I.to[m])) / den;
   }
-  if (!bad_k.empty()) {
-    std::string s = "instance " + std::to_string(b) + ": outage of branch(es)";
-    for (size_t q = 0; q < bad_k.size() && q < 8; ++q) s += " " + std::to_string(bad_k[q]);
-    s += " islands the grid (|1 - PTDF_kk| < 1e-9)";
-    return fail(h, QG_ERR_ISLANDING, s);
-  }
-  // bus CSR packs: balance (branch ends, then generators) and branch-end adjoints
+  if (!bad_k.empty()) return islanding_error(h, b, bad_k);
+  return build_packs(h, I, b);
+}
+
+// Bus CSR packs: balance (branch ends, then generators) and branch-end adjoints.
+int build_packs(qg_ctx *h, HostInst &I, int b) {
+  const int n = I.n, M = I.M;
   std::vector<std::vector<int>> bal(n), adj(n);
   for (int j = 0; j < M; ++j) {
     bal[I.from[j]].push_back(j << 2 | 0);
@@ -384,13 +510,26 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
   P.n_x = x0;
   auto &I = P.tab.I;
   // roles with the longest blocks first in each launch
-  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, DCF_BM), ceil_div(I[b].T, DCF_TC), b, R_DCF);
+  const HostInst &H0 = h->hi[0];
+  P.sp = H0.sparse ? 1 : 0;
+  if (P.sp) {
+    const int nr = H0.n - 1;
+    P.sp_inj_blocks = ceil_div((long long)nr * H0.T, NTHR);
+    P.sp_fw_blocks = ceil_div(nr, NTHR / 32);
+    P.sp_tail_blocks = ceil_div(H0.nT, SP_RB);
+    P.sp_bw_blocks = ceil_div(H0.nS, NTHR / 32);
+    P.sp_bwa_blocks = ceil_div((long long)H0.adj_rows.size(), NTHR / 32);
+  }
+  const int dcf = P.sp ? R_SDCF : R_DCF;
+  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, DCF_BM), ceil_div(I[b].T, DCF_TC), b, dcf);
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, NTHR), I[b].T, b, R_BRANCH);
   for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
   for (int b = 0; b < B; ++b) add_span(P.s2, I[b].n_mt * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
   for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
-  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gb + 1, NTHR / 32), I[b].T, b, R_DCA);
+  if (P.sp) add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
+  else
+    for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gb + 1, NTHR / 32), I[b].T, b, R_DCA);
   for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].G, NTHR), I[b].T, b, R_GEN);
   // objective slots: blocks of s1, then s2, then s5
@@ -456,11 +595,13 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
     rreq.insert(rreq.end(), H.rreq.begin(), H.rreq.end());
     dt.insert(dt.end(), H.dt.begin(), H.dt.end());
     ltot.insert(ltot.end(), H.ltot.begin(), H.ltot.end());
-    ptdfg.insert(ptdfg.end(), H.ptdfg.begin(), H.ptdfg.end());
-    const int Gb = (int)H.gbus.size();
-    for (int q = 0; q < Gb; ++q)
-      for (int m = 0; m < H.M; ++m) ptdfgT.push_back(H.ptdfg[(size_t)m * Gb + q]);
-    cload.insert(cload.end(), H.cload.begin(), H.cload.end());
+    if (!H.sparse) {
+      ptdfg.insert(ptdfg.end(), H.ptdfg.begin(), H.ptdfg.end());
+      const int Gb = (int)H.gbus.size();
+      for (int q = 0; q < Gb; ++q)
+        for (int m = 0; m < H.M; ++m) ptdfgT.push_back(H.ptdfg[(size_t)m * Gb + q]);
+      cload.insert(cload.end(), H.cload.begin(), H.cload.end());
+    }
     rsum.insert(rsum.end(), H.rsum.begin(), H.rsum.end());
     lodf.insert(lodf.end(), H.lodf.begin(), H.lodf.end());
     const double inf = INFINITY;
@@ -532,6 +673,40 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
     double *q;
     if ((rc = upload(h, &q, lodf))) return rc;
     d.lodf64 = q;
+  }
+  // sparse DC mode (instance 0)
+  d.sp = P.sp;
+  if (P.sp) {
+    const HostInst &H = h->hi[0];
+    d.nr = H.n - 1;
+    d.nS = H.nS;
+    d.nT = H.nT;
+    d.n_pchunk = ceil_div(d.nr, 32);
+    d.n_adj_rows = (int)H.adj_rows.size();
+    std::vector<double> ydc(H.y);
+#define UPI(field, vec) if ((rc = upload(h, &p, vec))) return rc; d.field = p;
+#define UPD(field, vec) { auto tmp_ = to_dc<Dc>(vec); if ((rc = upload(h, &z, tmp_))) return rc; d.field = z; }
+    UPI(bus_pos, H.bus_pos) UPI(pos_gb, H.pos_gb) UPI(pos_bus, H.pos_bus) UPI(fw_ptr, H.fw_ptr) UPI(fw_col, H.fw_col)
+    UPI(bw_ptr, H.bw_ptr) UPI(bw_col, H.bw_col) UPI(adj_rows, H.adj_rows) UPI(inc_ptr, H.inc_ptr)
+    UPI(inc_code, H.inc_code)
+    UPD(fw_val, H.fw_val) UPD(bw_val, H.bw_val) UPD(dinv, H.dinv) UPD(sinv, H.sinv) UPD(z1, H.z1) UPD(ydc, ydc)
+    UPD(load_dc, H.load_p)
+#undef UPI
+#undef UPD
+    const long long nrT = (long long)d.nr * H.T;
+    Dc *c;
+    if ((rc = dalloc(h, &c, (size_t)nrT))) return rc;
+    d.sp_rhs = c;
+    if ((rc = dalloc(h, &c, (size_t)nrT))) return rc;
+    d.sp_u = c;
+    if ((rc = dalloc(h, &c, (size_t)nrT))) return rc;
+    d.sp_th = c;
+    if ((rc = dalloc(h, &c, (size_t)std::max(1LL, (long long)d.nT * H.T)))) return rc;
+    d.sp_zt = c;
+    if ((rc = dalloc(h, &c, (size_t)H.T))) return rc;
+    d.sp_mu = c;
+    if ((rc = dalloc(h, &c, (size_t)d.n_pchunk * H.T))) return rc;
+    d.sp_part = c;
   }
   const qg_options &o = h->opt;
   d.c_p = (Real)o.c_p; d.c_q = (Real)o.c_q; d.c_s = (Real)o.c_s; d.c_rz = (Real)o.c_rz;
@@ -781,6 +956,9 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
   };
   if (o.precision != QG_FP64 && o.precision != QG_MIXED) return reject(QG_ERR_INVALID_ARG, "precision");
   if (o.lodf_dtype < 0 || o.lodf_dtype > 2) return reject(QG_ERR_INVALID_ARG, "lodf_dtype");
+  if (o.dc_solver < QG_DC_AUTO || o.dc_solver > QG_DC_SPARSE) return reject(QG_ERR_INVALID_ARG, "dc_solver");
+  if (o.dc_solver == QG_DC_SPARSE && n_inst > 1)
+    return reject(QG_ERR_UNSUPPORTED, "the sparse DC solver takes one instance per handle");
   if (!(o.eps >= 0) || !(o.beta >= 0) || !(o.c_p >= 0) || !(o.c_q >= 0) || !(o.c_s >= 0) || !(o.c_rz >= 0) ||
       !(o.rho >= 0) || !(o.adam_eps >= 0) || !std::isfinite(o.eps + o.beta + o.c_p + o.c_q + o.c_s + o.c_rz + o.rho))
     return reject(QG_ERR_INVALID_ARG, "penalty parameters must be finite and >= 0");
@@ -791,6 +969,7 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
     rc = read_instance(h, net[b], hor[b], ctg[b], h->hi[b], b);
     if (rc) { delete h; return rc; }
   }
+  h->hi[0].sparse = o.dc_solver == QG_DC_SPARSE || (o.dc_solver == QG_DC_AUTO && n_inst == 1 && h->hi[0].n > SPARSE_AUTO_N);
   {  // FP64 network set-up per instance, in parallel over instances
     std::vector<int> rcs(n_inst, 0);
     std::vector<std::string> errs(n_inst);
@@ -888,6 +1067,8 @@ int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g) {
 int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g) {
   if (!h || !x || !obj || !g)
     return h ? fail(h, QG_ERR_INVALID_ARG, "qg_eval_grad_noalloc needs x, obj and g") : QG_ERR_INVALID_ARG;
+  if (h->plan.sp)
+    return fail(h, QG_ERR_UNSUPPORTED, "qg_eval_grad_noalloc: handles on the sparse DC solver do not fit its scratch");
   return mixed(h) ? eval_noalloc<float, df32>(h, h->d32, x, obj, g) : eval_noalloc<double, double>(h, h->d64, x, obj, g);
 }
 

@@ -42,8 +42,14 @@ struct Inst {
   double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
 };
 
-// Roles of the blocks of the fused stage kernels.
-enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN };
+// Roles of the blocks of the fused stage kernels.  R_DCF / R_DCA are the dense DC products;
+// R_SDCF / R_SDCA their counterparts around the sparse-factor solves (flows from the solved
+// angles; right-hand side of the adjoint solve).
+enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN, R_SDCF, R_SDCA };
+
+constexpr int SP_RB = 16;   // dense tail product: rows per block
+constexpr int SP_BK = 32;   // dense tail product: columns per shared-memory chunk
+constexpr int SP_TMAX = 64; // periods per pass of the dense tail product
 
 // A run of blocks with one role for one instance: blocks [first, first + per_t * nt);
 // block b of the span has period (or period chunk) (b - first) / per_t and slice (b - first) % per_t.
@@ -87,6 +93,7 @@ struct Dev {
   const Real *rreq;                   // [sum T Z]
   const Real *dt;                     // [sum T]
   const Dc *ltot;                     // [sum T] total load per period
+  const Dc *load_dc;                  // [T n] active load in the DC product type (sparse mode)
   const Dc *ptdfg;                    // [sum M Gb] PTDF columns of generator buses, row m
   const Dc *ptdfgT;                   // [sum Gb M] the same, row gb
   const Dc *cload;                    // [sum T M] PTDF * load_t
@@ -94,6 +101,29 @@ struct Dev {
   const void *lodf;                   // [sum M K]: float / bf16 / bf16x2 (mixed) or float screening copy (FP64)
   const double *lodf64;               // [sum M K] FP64 path only
   const Real *lo, *hi;                // clip box [n_x]
+  // sparse DC mode (one instance): node positions = eliminated nodes in elimination order, then
+  // the tail nodes whose Schur complement S is held through its inverse; node-major work arrays
+  // [position][T].  Yhat^-1 b = (forward gather, D_S^-1, S^-1, backward gather), see qg_sparse.h.
+  int sp;                             // 1: DC solves through the sparse factor (no PTDF)
+  int nr, nS, nT;                     // reduced nodes (n - 1), eliminated nodes, tail nodes
+  int n_pchunk;                       // position chunks of 32 (adjoint right-hand-side blocks)
+  int n_adj_rows;                     // eliminated positions that are generator buses
+  const int *bus_pos;                 // [n] position of each bus, -1 at the reference bus
+  const int *pos_gb;                  // [nr] generator-bus index at each position, -1 if none
+  const int *pos_bus;                 // [nr] bus at each position
+  const int *fw_ptr, *fw_col;         // forward gather rows [nr + 1] / entries (positions)
+  const Dc *fw_val;
+  const int *bw_ptr, *bw_col;         // backward gather rows [nS + 1] / entries (positions)
+  const Dc *bw_val;
+  const int *adj_rows;                // [n_adj_rows]
+  const Dc *dinv;                     // [nS] 1 / D_S
+  const Dc *sinv;                     // [nT nT] S^-1, row-major
+  const Dc *z1;                       // [nr] Yhat^-1 1 at each position
+  const int *inc_ptr, *inc_code;      // position -> incident branches, code = j << 1 | (1 at the to-end)
+  const Dc *ydc;                      // [M] y_j = -b_sr
+  Dc *sp_rhs, *sp_u, *sp_th, *sp_zt;  // [nr T], [nr T], [nr T], [nT T]
+  Dc *sp_mu;                          // [T] mean injection (uniform slack)
+  Dc *sp_part;                        // [n_pchunk][T] partial sums of z1 . w
   // penalty parameters
   Real c_p, c_q, c_s, c_rz, rho, eps, beta;
   int lodf_dtype;
@@ -132,6 +162,13 @@ struct Plan {
   InstTab tab;
   long long n_x;
   int maxT;
+  // sparse DC mode (instance 0 only): grids of the solve kernels
+  int sp;
+  int sp_inj_blocks;   // right-hand-side blocks of k_sp_inj (T more compute the mean injection)
+  int sp_fw_blocks;    // k_sp_fwd rows / 8
+  int sp_tail_blocks;  // k_sp_tail, 0 without a tail
+  int sp_bw_blocks;    // k_sp_back forward pass
+  int sp_bwa_blocks;   // k_sp_back adjoint pass
 };
 
 template <typename Real, typename Dc>

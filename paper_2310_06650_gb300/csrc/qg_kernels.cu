@@ -408,6 +408,43 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   }
 }
 
+// Base DC flows in the sparse mode, from the angles theta' = Yhat^-1 p_inj solved by the sparse
+// factor (0 at the reference bus): f[t,m] = y_m (theta'_f - theta'_o) - mu_t (PTDF 1)_m, the last
+// term being the uniform slack (Sec. II-E) with mu_t the mean injection.
+template <typename Real, typename Dc>
+__device__ void s1_sdcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, const Real *__restrict__ x) {
+  const int t0 = tc * DCF_TC, m0 = sub * DCF_BM;
+  const int t = t0 + (threadIdx.x >> 5), m = m0 + (threadIdx.x & 31);
+  if (sub == 0) {  // dispatch snapshot for the ramp terms of a fused Adam update
+    const Real *p = x + I.x0 + 2LL * I.T * I.n;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < DCF_TC * I.G; e += NTHR) {
+      const int tt = t0 + e / I.G, gl = e % I.G;
+      if (tt < I.T) d.pold[I.tg0 + (long long)tt * I.G + gl] = p[(long long)tt * I.G + gl];
+    }
+  }
+  const bool on = t < I.T && m < I.M;
+  const int2 ft = d.br_end[I.br0 + (on ? m : 0)];
+  const int pf = d.bus_pos[ft.x], po = d.bus_pos[ft.y];
+  const Dc y = d.ydc[I.br0 + (on ? m : 0)], rs = d.rsum[I.br0 + (on ? m : 0)];
+  pdl_wait();
+  if (!on) return;
+  Dc a = pf >= 0 ? d.sp_th[(long long)pf * I.T + t] : DcOps<Dc>::zero();
+  if (po >= 0) a = DcOps<Dc>::add(a, DcOps<Dc>::neg(d.sp_th[(long long)po * I.T + t]));
+  Dc f = DcOps<Dc>::mul(y, a);
+  f = DcOps<Dc>::add(f, DcOps<Dc>::neg(DcOps<Dc>::mul(d.sp_mu[t], rs)));
+  const long long e = I.tm0 + (long long)t * I.M + m;
+  const Real fr = DcOps<Dc>::to_real(f);
+  d.fre[e] = fr;
+  d.f32[e] = DcOps<Dc>::to_float(f);
+  const int kx = d.br_kidx[I.br0 + m];
+  if (kx >= 0) {
+    const long long ek = I.tk0 + (long long)t * I.K + kx;
+    d.fk[ek] = fr;
+    d.fk32[ek] = DcOps<Dc>::to_float(f);
+  }
+}
+
 template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
@@ -418,6 +455,8 @@ __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, D
   Obj3<Dc> acc = obj3<Dc>(-1);
   if (w.role == R_DCF) {
     s1_dcf(d, I, w.t, w.sub, x);
+  } else if (w.role == R_SDCF) {
+    s1_sdcf(d, I, w.t, w.sub, x);
   } else if (w.role == R_BRANCH) {
     acc.id[0] = T_ZS;
     s1_branch(d, I, w.t, w.sub, x, acc);
@@ -844,6 +883,34 @@ __device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
   if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + o] = acc;
 }
 
+// Right-hand side of the adjoint solve in the sparse mode (Eq. 2nd_lin_sys): w = E_hat^T Y_x dz/df
+// at 32 positions x 8 periods per block, w_i = sum over incident branches of +-y_j dz/df_j (+ at
+// the from-end); plus per-chunk partial sums of z1 . w = 1^T eta (n times the mean of eta, Eq.
+// correction), finished in fixed order by the adjoint gather.
+template <typename Real, typename Dc>
+__device__ void s4_sdca(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub) {
+  const int t = tc * DCF_TC + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int pos = sub * 32 + lane;
+  const bool on = t < I.T && pos < d.nr;
+  const int q0 = on ? d.inc_ptr[pos] : 0, q1 = on ? d.inc_ptr[pos + 1] : 0;
+  const Dc z1 = on ? d.z1[pos] : DcOps<Dc>::zero();
+  pdl_wait();
+  Dc w = DcOps<Dc>::zero();
+  if (on) {
+    const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
+    for (int q = q0; q < q1; ++q) {
+      const int c = d.inc_code[q], j = c >> 1;
+      const Real g = (c & 1) ? -gf[j] : gf[j];
+      DcOps<Dc>::mac(w, d.ydc[I.br0 + j], DcOps<Dc>::from_real(g));
+    }
+    d.sp_rhs[(long long)pos * I.T + t] = w;
+  }
+  Dc s = DcOps<Dc>::mul(z1, w);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = DcOps<Dc>::add(s, DcOps<Dc>::shfl_down(s, o));
+  if (lane == 0 && t < I.T) d.sp_part[(long long)sub * I.T + t] = s;
+}
+
 template <typename Real, typename Dc, bool ADAM>
 __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
@@ -852,6 +919,7 @@ __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, D
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
   if (w.role == R_BUS) s4_bus<Real, Dc, ADAM>(d, I, w.t, w.sub, x);
+  else if (w.role == R_SDCA) s4_sdca(d, I, w.t, w.sub);
   else {
     pdl_wait();
     s4_dca(d, I, w.t, w.sub);
@@ -1025,6 +1093,182 @@ __global__ void __launch_bounds__(NTHR) k_adam(Real *__restrict__ x, Real *__res
 }
 
 // ---------------------------------------------------------------------------------------------
+// sparse DC mode: Yhat^-1 through the sparse factor with a dense tail (no PTDF).  The factor
+// Yhat = L diag(D_S, S) L^T eliminates the low-degree nodes first; with M1 = L_SS^-1 and
+// M2 = -L_TS L_SS^-1 held explicitly as gather lists, a solve is
+//   z_S = M1 b_S, z_T = b_T + M2 b_S  ->  x_T = S^-1 z_T  ->  x_S = M1^T (D_S^-1 z_S) + M2^T x_T,
+// for all periods at once (node-major arrays [position][T]).
+// ---------------------------------------------------------------------------------------------
+
+// Forward right-hand sides p_inj[pos][t] = (dispatch at the bus) - load (blocks [0, nb)), and the
+// mean injection mu_t = (sum_g p_gt - total load_t) / n (one block per period after those).
+template <typename Real, typename Dc>
+__global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Real, Dc> d,
+                                                 const __grid_constant__ Inst I, const Real *__restrict__ x, int nb) {
+  pdl_launch_dependents();
+  const Real *p = x + I.x0 + 2LL * I.T * I.n;
+  if ((int)blockIdx.x < nb) {
+    const long long e = (long long)blockIdx.x * NTHR + threadIdx.x;
+    if (e >= (long long)d.nr * I.T) return;
+    const int pos = (int)(e / I.T), t = (int)(e % I.T);
+    const int bus = d.pos_bus[pos], gb = d.pos_gb[pos];
+    Dc s = DcOps<Dc>::neg(d.load_dc[I.tb0 + (long long)t * I.n + bus]);
+    if (gb >= 0) {
+      const int q0 = d.gb_ptr[I.gb0 + gb], q1 = d.gb_ptr[I.gb0 + gb + 1];
+      for (int q = q0; q < q1; ++q)
+        s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(p[(long long)t * I.G + (d.gb_gen[q] - I.gen0)]));
+    }
+    d.sp_rhs[e] = s;
+  } else {
+    const int t = blockIdx.x - nb;
+    Dc s = DcOps<Dc>::zero();
+    for (int g = threadIdx.x; g < I.G; g += NTHR) s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(p[(long long)t * I.G + g]));
+    s = block_sum_dc(s);
+    if (threadIdx.x == 0)
+      d.sp_mu[t] = DcOps<Dc>::mul(DcOps<Dc>::add(s, DcOps<Dc>::neg(d.ltot[I.tp0 + t])), DcOps<Dc>::inv_n(I));
+  }
+}
+
+// Forward gather z = [M1; M2] b, one warp per position, lanes over periods.  Eliminated rows
+// (their list holds the unit diagonal) store u = z / D; tail rows store z_T = b_T + M2 b_S.  In the
+// adjoint pass one extra block finishes 1^T eta from the per-chunk partials of stage 4.
+template <typename Real, typename Dc, bool ADJ>
+__global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Real, Dc> d,
+                                                 const __grid_constant__ Inst I, int nrow_blocks) {
+  pdl_launch_dependents();
+  const int T = I.T;
+  if (ADJ && (int)blockIdx.x == nrow_blocks) {
+    pdl_wait();
+    for (int t = threadIdx.x; t < T; t += NTHR) {
+      Dc s = DcOps<Dc>::zero();
+      for (int c = 0; c < d.n_pchunk; ++c) s = DcOps<Dc>::add(s, d.sp_part[(long long)c * T + t]);
+      d.gip[I.gi0 + (long long)t * (I.Gb + 1) + I.Gb] = s;
+    }
+    return;
+  }
+  const int row = blockIdx.x * (NTHR / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const bool on = row < d.nr;
+  const int e0 = on ? d.fw_ptr[row] : 0, e1 = on ? d.fw_ptr[row + 1] : 0;
+  pdl_wait();
+  if (!on) return;
+  for (int t0 = 0; t0 < T; t0 += 64) {
+    const int ta = t0 + lane, tb = t0 + 32 + lane;
+    Dc a0 = DcOps<Dc>::zero(), a1 = DcOps<Dc>::zero();
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+      const Dc v = d.fw_val[e];
+      const Dc *b = d.sp_rhs + (long long)d.fw_col[e] * T;
+      if (ta < T) DcOps<Dc>::mac(a0, v, b[ta]);
+      if (tb < T) DcOps<Dc>::mac(a1, v, b[tb]);
+    }
+    if (row < d.nS) {
+      const Dc di = d.dinv[row];
+      Dc *u = d.sp_u + (long long)row * T;
+      if (ta < T) u[ta] = DcOps<Dc>::mul(a0, di);
+      if (tb < T) u[tb] = DcOps<Dc>::mul(a1, di);
+    } else {
+      const Dc *b = d.sp_rhs + (long long)row * T;
+      Dc *z = d.sp_zt + (long long)(row - d.nS) * T;
+      if (ta < T) z[ta] = DcOps<Dc>::add(b[ta], a0);
+      if (tb < T) z[tb] = DcOps<Dc>::add(b[tb], a1);
+    }
+  }
+}
+
+// Dense tail x_T = S^-1 z_T: SP_RB rows per block (16 rows x 16 period lanes, up to SP_TMAX
+// periods per pass), S^-1 and z_T staged through shared memory in chunks of SP_BK columns.  The
+// result goes to u (for the backward gather) and to the solution (forward pass) or to the
+// generator-bus adjoints (adjoint pass).
+template <typename Real, typename Dc, bool ADJ>
+__global__ void __launch_bounds__(NTHR) k_sp_tail(const __grid_constant__ Dev<Real, Dc> d,
+                                                  const __grid_constant__ Inst I) {
+  __shared__ Dc s_s[SP_RB][SP_BK + 1];
+  __shared__ Dc s_z[SP_BK][SP_TMAX];
+  pdl_launch_dependents();
+  const int T = I.T, m = d.nT;
+  const int r = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  const int a = blockIdx.x * SP_RB + r;
+  pdl_wait();
+  for (int t0 = 0; t0 < T; t0 += SP_TMAX) {
+    const int tn = min(SP_TMAX, T - t0);
+    Dc acc[SP_TMAX / 16];
+#pragma unroll
+    for (int j = 0; j < SP_TMAX / 16; ++j) acc[j] = DcOps<Dc>::zero();
+    for (int b0 = 0; b0 < m; b0 += SP_BK) {
+      const int bn = min(SP_BK, m - b0);
+      __syncthreads();
+#pragma unroll
+      for (int e = threadIdx.x; e < SP_RB * SP_BK; e += NTHR) {
+        const int rr = e / SP_BK, cc = e % SP_BK, ar = blockIdx.x * SP_RB + rr;
+        s_s[rr][cc] = (ar < m && cc < bn) ? d.sinv[(long long)ar * m + b0 + cc] : DcOps<Dc>::zero();
+      }
+#pragma unroll
+      for (int e = threadIdx.x; e < SP_BK * SP_TMAX; e += NTHR) {
+        const int rr = e / SP_TMAX, cc = e % SP_TMAX;
+        s_z[rr][cc] = (rr < bn && cc < tn) ? d.sp_zt[(long long)(b0 + rr) * T + t0 + cc] : DcOps<Dc>::zero();
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int b = 0; b < SP_BK; ++b) {
+        const Dc sv = s_s[r][b];
+#pragma unroll
+        for (int j = 0; j < SP_TMAX / 16; ++j)
+          if (tc + 16 * j < tn) DcOps<Dc>::mac(acc[j], sv, s_z[b][tc + 16 * j]);
+      }
+    }
+    if (a < m) {
+      const int pos = d.nS + a;
+      const int gb = ADJ ? d.pos_gb[pos] : -1;
+#pragma unroll
+      for (int j = 0; j < SP_TMAX / 16; ++j) {
+        const int t = t0 + tc + 16 * j;
+        if (tc + 16 * j >= tn) continue;
+        d.sp_u[(long long)pos * T + t] = acc[j];
+        if (!ADJ) d.sp_th[(long long)pos * T + t] = acc[j];
+        else if (gb >= 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + gb] = acc[j];
+      }
+    }
+  }
+}
+
+// Backward gather x_S = M1^T u_S + M2^T u_T (u_S = D_S^-1 z_S, u_T = x_T), one warp per eliminated
+// position: every one on the forward pass (angles), the generator buses on the adjoint pass.
+template <typename Real, typename Dc, bool ADJ>
+__global__ void __launch_bounds__(NTHR) k_sp_back(const __grid_constant__ Dev<Real, Dc> d,
+                                                  const __grid_constant__ Inst I) {
+  pdl_launch_dependents();
+  const int T = I.T;
+  const int w = blockIdx.x * (NTHR / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int nrows = ADJ ? d.n_adj_rows : d.nS;
+  const bool on = w < nrows;
+  const int q = on ? (ADJ ? d.adj_rows[w] : w) : 0;
+  const int e0 = on ? d.bw_ptr[q] : 0, e1 = on ? d.bw_ptr[q + 1] : 0;
+  const int gb = (on && ADJ) ? d.pos_gb[q] : -1;
+  pdl_wait();
+  if (!on) return;
+  for (int t0 = 0; t0 < T; t0 += 64) {
+    const int ta = t0 + lane, tb = t0 + 32 + lane;
+    Dc a0 = DcOps<Dc>::zero(), a1 = DcOps<Dc>::zero();
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+      const Dc v = d.bw_val[e];
+      const Dc *u = d.sp_u + (long long)d.bw_col[e] * T;
+      if (ta < T) DcOps<Dc>::mac(a0, v, u[ta]);
+      if (tb < T) DcOps<Dc>::mac(a1, v, u[tb]);
+    }
+    if (ADJ) {
+      Dc *g = d.gip + I.gi0 + gb;
+      if (ta < T) g[(long long)ta * (I.Gb + 1)] = a0;
+      if (tb < T) g[(long long)tb * (I.Gb + 1)] = a1;
+    } else {
+      Dc *th = d.sp_th + (long long)q * T;
+      if (ta < T) th[ta] = a0;
+      if (tb < T) th[tb] = a1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
 
@@ -1080,8 +1324,19 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     }
   };
   mark(ev, 0, s);
-  k_s1<Real, Dc><<<P.s1.n_blocks, NTHR, 0, s>>>(d, P.tab, P.s1, x, 0);
-  e = cudaGetLastError();
+  if (P.sp) {
+    // sparse mode: forward solve theta' = Yhat^-1 p_inj before the flows of stage 1
+    const Inst &I = P.tab.I[0];
+    k_sp_inj<Real, Dc><<<P.sp_inj_blocks + I.T, NTHR, 0, s>>>(d, I, (const Real *)x, P.sp_inj_blocks);
+    e = cudaGetLastError();
+    go(k_sp_fwd<Real, Dc, false>, P.sp_fw_blocks, 0, d, I, P.sp_fw_blocks);
+    if (P.sp_tail_blocks > 0) go(k_sp_tail<Real, Dc, false>, P.sp_tail_blocks, 0, d, I);
+    if (P.sp_bw_blocks > 0) go(k_sp_back<Real, Dc, false>, P.sp_bw_blocks, 0, d, I);
+    go(k_s1<Real, Dc>, P.s1.n_blocks, 0, d, P.tab, P.s1, (const Real *)x, 0);
+  } else {
+    k_s1<Real, Dc><<<P.s1.n_blocks, NTHR, 0, s>>>(d, P.tab, P.s1, x, 0);
+    e = cudaGetLastError();
+  }
   mark(ev, 1, s);
   go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxT), d, P.tab, P.s2, (const Real *)x, o2);
   mark(ev, 2, s);
@@ -1089,6 +1344,13 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
   mark(ev, 3, s);
   if (adam) go(k_s4<Real, Dc, true>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
   else go(k_s4<Real, Dc, false>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
+  if (P.sp) {
+    // sparse mode: adjoint solve eta = Yhat^-1 w at the generator buses, and 1^T eta
+    const Inst &I = P.tab.I[0];
+    go(k_sp_fwd<Real, Dc, true>, P.sp_fw_blocks + 1, 0, d, I, P.sp_fw_blocks);
+    if (P.sp_tail_blocks > 0) go(k_sp_tail<Real, Dc, true>, P.sp_tail_blocks, 0, d, I);
+    if (P.sp_bwa_blocks > 0) go(k_sp_back<Real, Dc, true>, P.sp_bwa_blocks, 0, d, I);
+  }
   mark(ev, 4, s);
   if (adam) go(k_s5<Real, Dc, true>, P.s5.n_blocks, 0, d, P.tab, P.s5, x, o5);
   else go(k_s5<Real, Dc, false>, P.s5.n_blocks, 0, d, P.tab, P.s5, x, o5);

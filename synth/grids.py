@@ -406,6 +406,12 @@ def with_loads(case: Case, load_p: np.ndarray) -> Case:
     return dataclasses.replace(case, load_p=load_p, load_q=0.329 * load_p, reserve_req=reserve)
 
 
+def horizon_slice(case: Case, t0: int, t1: int) -> Case:
+    """The same network over periods [t0, t1) of the horizon only."""
+    return dataclasses.replace(case, T=t1 - t0, dt=case.dt[t0:t1].copy(), load_p=case.load_p[t0:t1].copy(),
+                               load_q=case.load_q[t0:t1].copy(), reserve_req=case.reserve_req[t0:t1].copy())
+
+
 def load_profiles(case: Case, count: int, seed: int) -> np.ndarray:
     """Warm-start training profiles: load * U(0.8, 1.2) per profile * (1 + N(0, 0.05)) per bus, >= 0."""
     rng = np.random.default_rng(seed)

@@ -107,3 +107,29 @@ def test_disconnected_grid_is_rejected(qg):
     c = dataclasses.replace(c, br_from=np.array([0, 1, 3, 0], np.int32), br_to=np.array([1, 2, 4, 2], np.int32),
                             ctg=np.zeros(0, np.int32))
     _expect(qg, c, qg.QG_ERR_ISLANDING)
+
+
+def test_sparse_dc_solver_options_are_validated(qg):
+    c = synth.tiny()
+    _expect(qg, c, qg.QG_ERR_INVALID_ARG, dc_solver=3)
+    with pytest.raises(qg.QGError) as ei:
+        qg.qg_create_batch([c, c], qg.case_options(c, dc_solver=qg.QG_DC_SPARSE))
+    assert ei.value.code == qg.QG_ERR_UNSUPPORTED and "one instance" in str(ei.value)
+
+
+def test_sparse_dc_set_up_rejects_islanding_and_disconnected_grids(qg):
+    msg = _expect(qg, _radial(), qg.QG_ERR_ISLANDING, dc_solver=qg.QG_DC_SPARSE)
+    assert "islands" in msg
+    c = _radial()
+    c = dataclasses.replace(c, br_from=np.array([0, 1, 3, 0], np.int32), br_to=np.array([1, 2, 4, 2], np.int32),
+                            ctg=np.zeros(0, np.int32))
+    _expect(qg, c, qg.QG_ERR_ISLANDING, dc_solver=qg.QG_DC_SPARSE)
+
+
+@pytest.mark.skipif(_gpu_present(), reason="checks the no-device path")
+@pytest.mark.parametrize("name", ["tiny", "rt617"])
+def test_sparse_dc_set_up_runs_on_the_host(qg, name):
+    """The whole FP64 set-up of the sparse solver (factor, dense tail inverse, gather lists,
+    line-outage block) runs before the device is needed."""
+    c = {"tiny": synth.tiny, "rt617": synth.rt617}[name]()
+    _expect(qg, c, qg.QG_ERR_NO_DEVICE, dc_solver=qg.QG_DC_SPARSE)

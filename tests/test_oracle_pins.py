@@ -400,3 +400,17 @@ def test_bf16_rounding_matches_torch():
     a = np.concatenate([rng.normal(size=1000) * 10.0 ** rng.integers(-8, 8, 1000), [0.0, -0.0, 1.0, 3.0e38]])
     ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(mlp.bf16(a), ref)
+
+
+def test_sparse_lu_route_agrees_with_the_explicit_inverse():
+    """Large grids go through a sparse LU factorization of the reduced Laplacian, small ones through
+    its explicit inverse: the same solves (Eqs. Yb_solve, 2nd_lin_sys), equal to rounding on a grid
+    both can take.  The explicit-inverse route is pinned by the tests above."""
+    c = synth.mid()
+    x = synth.random_point(c, 3)
+    rd = oracle.evaluate(c, x, net=oracle.dc_network(c, sparse=False))
+    rs = oracle.evaluate(c, x, net=oracle.dc_network(c, sparse=True))
+    assert abs(rs.obj - rd.obj) <= 1e-11 * abs(rd.obj)
+    assert np.linalg.norm(rs.grad - rd.grad) <= 1e-10 * np.linalg.norm(rd.grad)
+    for k in oracle.TERM_NAMES:
+        assert abs(rs.terms[k] - rd.terms[k]) <= 1e-11 * max(abs(rd.terms[k]), 1e-6 * abs(rd.obj))
