@@ -14,6 +14,10 @@ of the ranks' evaluations over the slowest rank's time.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (each step
 evaluates one period's slice of the same workload: 1/T of an evaluation).
+
+The line also carries a "dayahead" object: the same step on the 23,643-bus / 48-period /
+2,000-outage day-ahead grid (mixed precision, sparse DC solver), whose working set is larger
+than L2 (--no-dayahead skips it).
 """
 from __future__ import annotations
 
@@ -33,6 +37,9 @@ METRIC = "full grad evals/s (all periods+ctgs); time to 1% of LP bound vs FP64 p
 UNIT = "evals/s"
 WORKLOAD = "rt617"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the current
+# kernel code (profiles/k_s2_rt617.md); None where no capture of the current code exists
+NCU_TRAFFIC = {}
 FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
 
 
@@ -180,6 +187,12 @@ def algorithmic(case, phase, mixed):
 
 
 def roofline(case, phase, ms, mixed, peaks, src, clocks):
+    out = _roofline(case, phase, ms, mixed, peaks, src, clocks)
+    out["traffic"] = NCU_TRAFFIC.get((case.name, phase, mixed))
+    return out
+
+
+def _roofline(case, phase, ms, mixed, peaks, src, clocks):
     amount, unit, bound = algorithmic(case, phase, mixed)
     sec = ms * 1e-3
     if unit == "byte":
@@ -345,9 +358,78 @@ def gpu_leg(args, rank, world, local_rank):
                       "e2e": world * K / f64["e2e_s"]},
         "paper_context": "24 ms per full gradient on 6 CPU threads for the C3E3.1 617-bus, 18-period, 562-outage case",
     }
+    if not args.no_dayahead:
+        line["dayahead"] = dayahead_leg(args, peaks, src, local_rank)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def dayahead_leg(args, peaks, src, local_rank):
+    """The bench step on the day-ahead grid: mixed precision, sparse DC solver (chosen by the
+    library above 4,096 buses), merit-order start.  Its line-outage block alone (280 MB) exceeds
+    L2, so no flush is written between steps."""
+    import torch
+
+    import synth
+    from paper_2310_06650_gb300 import qg, warmstart
+
+    case = synth.dayahead()
+    t0 = time.perf_counter()
+    s = qg.Solver(case, precision=qg.QG_MIXED)
+    setup_s = time.perf_counter() - t0
+    x0 = warmstart.start_point(case)
+    x = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    steps = max(5, min(args.steps, 50))
+    for _ in range(max(args.warmup, 3)):
+        qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with ClockSampler(local_rank) as clk:
+        for k in range(steps):
+            ev0[k].record(stream)
+            qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    qg.qg_set_profiling(s.h, True)
+    qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+    phases = {}
+    for _ in range(steps):
+        qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+        for name, v in qg.qg_phase_times(s.h).items():
+            phases.setdefault(name, []).append(v)
+    torch.cuda.synchronize()
+    qg.qg_set_profiling(s.h, False)
+    ph = {k: statistics.mean(v) for k, v in phases.items()}
+    ms = sum(step_ms) / steps
+    # contingency stage: the line-outage block is read once per evaluation
+    T, M, K = case.T, case.n_branch, case.K
+    s2_bytes = 4.0 * M * K + 4.0 * T * (3 * M + K)
+    s2_gbs = s2_bytes / (ph["s2"] * 1e-3) / 1e9
+    s2_tflops = 4.0 * T * M * K / (ph["s2"] * 1e-3) / 1e12
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    out = {
+        "value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+        "config": {"workload": f"dayahead: {case.n_bus} buses, {case.n_branch} branches, {case.n_gen} generators, "
+                               f"{case.n_zone} zones, {case.T} periods, {case.K} outages (all evaluated)",
+                   "precision": "mixed", "dc_solver": "sparse factor with dense tail (no PTDF)",
+                   "l2": "working set larger than L2 (line-outage block 280 MB); no flush",
+                   "x0": "merit-order dispatch, flat voltage, zero angles"},
+        "setup_s": setup_s,
+        "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in ph.items()},
+        "phases_note": "s1 includes the forward DC solve (injections, forward gather, tail product, backward "
+                       "gather); s4 includes the adjoint DC solve",
+        "s2": {"algorithmic_bytes": s2_bytes, "hbm_gbs": s2_gbs, "hbm_frac": s2_gbs / peaks["hbm_gbs"],
+               "tflops": s2_tflops, "alu_frac": s2_tflops / fp32_peak,
+               "note": "line-outage block (FP32) + flows and q-limits per launch; 4 FP32 flop per (t, m, k)"},
+        "clocks": clk.summary(),
+    }
+    s.close()
+    return out
 
 
 def reference_leg(args, rank, world):
@@ -374,6 +456,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-dayahead", action="store_true", help="skip the day-ahead grid")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

@@ -28,6 +28,7 @@ thread_local std::string g_create_error;
 constexpr int DENSE_MAX_N = 8192;  // the dense inverse used at set-up holds n^2 doubles
 constexpr int SPARSE_AUTO_N = 4096; // QG_DC_AUTO picks the sparse factor above this many buses
 constexpr int TAIL_DEGREE = 32;     // minimum-degree elimination stops above this degree
+constexpr long long CTG_WAVE = 152 * 3;  // contingency blocks resident at once (152 SMs x 3 blocks)
 
 struct HostInst {
   int n, M, G, Z, T, K, ref;
@@ -476,12 +477,20 @@ void add_span(Spans &S, int per_t, int nt, int inst, int role) {
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Instance table, spans of the five stage kernels and objective-slot owners.
-int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
+int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   Plan &P = h->plan;
   const int B = h->n_inst;
   std::memset(&P, 0, sizeof(P));
   P.tab.n_inst = B;
   long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0;
+  // Contingency block shape, shared by the batch: about one wave of CTG_WAVE blocks when the
+  // 64 x 64 tiles are few (the periods split across blocks), several waves when they are many
+  // (tiles grouped per block, so fewer column partials are written and summed).
+  long long tiles = 0;
+  for (int b = 0; b < B; ++b)
+    if (h->hi[b].K > 0) tiles += (long long)ceil_div(h->hi[b].M, CT_BM) * ceil_div(h->hi[b].K, CT_BK);
+  const int ntc_all = (int)std::max(1LL, tiles > 0 ? CTG_WAVE / tiles : 1);
+  const int mg_all = (int)std::max(1LL, tiles / (4LL * CTG_WAVE));
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
@@ -490,6 +499,10 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
     D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.gb0 = gb0; D.tp0 = tp0;
     D.n_mt = ceil_div(H.M, CT_BM);
     D.n_kt = ceil_div(H.K, CT_BK);
+    D.ctg_mg = std::min(mg_all, D.n_mt);
+    D.n_mg = ceil_div(D.n_mt, D.ctg_mg);
+    D.ctg_tb = ceil_div(H.T, std::min(ntc_all, H.T));
+    D.ctg_ntc = ceil_div(H.T, D.ctg_tb);
     D.n_sb = ceil_div(H.M, NTHR);
     D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
     D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
@@ -502,10 +515,11 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
     x0 += (long long)H.T * (2LL * H.n + 3LL * H.G);
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
     tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gb; l0 += (long long)H.M * H.K;
-    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mt * H.T * H.K; gi0 += (long long)H.T * (D.Gb + 1);
+    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.K; gi0 += (long long)H.T * (D.Gb + 1);
     bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.K; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
     P.maxT = std::max(P.maxT, H.T);
+    P.maxTB = std::max(P.maxTB, D.ctg_tb);
   }
   P.n_x = x0;
   auto &I = P.tab.I;
@@ -524,7 +538,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, DCF_BM), ceil_div(I[b].T, DCF_TC), b, dcf);
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, NTHR), I[b].T, b, R_BRANCH);
   for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
-  for (int b = 0; b < B; ++b) add_span(P.s2, I[b].n_mt * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
+  for (int b = 0; b < B; ++b) add_span(P.s2, I[b].ctg_ntc * I[b].n_mg * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
   for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
   if (P.sp) add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
@@ -532,17 +546,30 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_inst) {
     for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gb + 1, NTHR / 32), I[b].T, b, R_DCA);
   for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].G, NTHR), I[b].T, b, R_GEN);
-  // objective slots: blocks of s1, then s2, then s5
-  slot_inst.clear();
-  for (const Spans *S : {&P.s1, &P.s2, &P.s5})
+  // objective slots: the blocks of s1 and s2 in launch order, renumbered instance-major so that each
+  // instance's slots are one contiguous range; then one slot per s5 block
+  std::vector<int> owner;
+  for (const Spans *S : {&P.s1, &P.s2})
     for (int k = 0; k < S->n; ++k)
-      for (int q = 0; q < S->s[k].per_t * S->s[k].nt; ++q) slot_inst.push_back(S->s[k].inst);
+      for (int q = 0; q < S->s[k].per_t * S->s[k].nt; ++q) owner.push_back(S->s[k].inst);
+  std::vector<int> count(B, 0);
+  for (int o : owner) ++count[o];
+  int lo = 0;
+  for (int b = 0; b < B; ++b) {
+    I[b].obj_lo = lo;
+    I[b].obj_n = count[b];
+    lo += count[b];
+  }
+  slot_map.assign(owner.size(), 0);
+  std::vector<int> next(B);
+  for (int b = 0; b < B; ++b) next[b] = I[b].obj_lo;
+  for (size_t q = 0; q < owner.size(); ++q) slot_map[q] = next[owner[q]]++;
   return QG_OK;
 }
 
 // Build every device array of one precision flavour.
 template <typename Real, typename Dc>
-int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst) {
+int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) {
   const int B = h->n_inst;
   const Plan &P = h->plan;
   std::vector<int2> br_end;
@@ -717,7 +744,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
     const Inst &I = P.tab.I[b];
     sTM += (long long)I.T * I.M; sTn += (long long)I.T * I.n; sTZ += (long long)I.T * I.Z;
     sTK += (long long)I.T * I.K; sTG += (long long)I.T * I.G;
-    sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mt * I.T * I.K;
+    sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mg * I.T * I.K;
     sGI += (long long)I.T * (I.Gb + 1);
   }
   Real *w;
@@ -738,12 +765,13 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_inst)
   if ((rc = dalloc(h, &qs, (size_t)sTM))) return rc;
   d.qside = qs;
   Dc *op;
-  d.n_obj_slots = (int)slot_inst.size();
+  d.n_obj12 = (int)slot_map.size();
+  d.n_obj_slots = d.n_obj12 + P.s5.n_blocks;
   if ((rc = dalloc(h, &op, (size_t)d.n_obj_slots * N_TERMS))) return rc;
   d.objp = op;
   int *si;
-  if ((rc = upload(h, &si, slot_inst))) return rc;
-  d.slot_inst = si;
+  if ((rc = upload(h, &si, slot_map))) return rc;
+  d.slot_map = si;
   d.obj = h->d_obj;
   d.terms = h->d_terms;
   d.g = static_cast<Real *>(h->d_g);
@@ -873,7 +901,7 @@ size_t carve_scratch(const qg_ctx *h, unsigned char *base, size_t cap, Dev<Real,
     const Inst &I = P.tab.I[b];
     sTM += (long long)I.T * I.M; sTn += (long long)I.T * I.n; sTZ += (long long)I.T * I.Z;
     sTK += (long long)I.T * I.K; sTG += (long long)I.T * I.G;
-    sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mt * I.T * I.K;
+    sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mg * I.T * I.K;
     sGI += (long long)I.T * (I.Gb + 1);
   }
   size_t off = 0;
@@ -987,8 +1015,8 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
     for (int b = 0; b < n_inst; ++b)
       if (rcs[b]) return reject(rcs[b], errs[b]);
   }
-  std::vector<int> slot_inst;
-  build_plan(h, slot_inst);
+  std::vector<int> slot_map;
+  build_plan(h, slot_map);
   if (h->plan.s1.n > MAXSPAN || h->plan.s2.n > MAXSPAN) return reject(QG_ERR_UNSUPPORTED, "too many block spans");
   // everything above is host-side validation and set-up; from here on the device is needed
   rc = check_device(h);
@@ -1004,9 +1032,9 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
     delete h;
     return rc;
   }
-  rc = mixed(h) ? build_device<float, df32>(h, h->d32, slot_inst) : build_device<double, double>(h, h->d64, slot_inst);
+  rc = mixed(h) ? build_device<float, df32>(h, h->d32, slot_map) : build_device<double, double>(h, h->d64, slot_map);
   if (!rc) {
-    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->plan.maxT) : prepare_eval<double, double>(h->plan.maxT);
+    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->plan.maxTB) : prepare_eval<double, double>(h->plan.maxTB);
     if (e != cudaSuccess) rc = fail(h, QG_ERR_UNSUPPORTED, std::string("prepare_eval: ") + cudaGetErrorString(e));
   }
   if (rc) {

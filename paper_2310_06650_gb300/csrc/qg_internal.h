@@ -28,6 +28,8 @@ struct Inst {
   int n, M, G, Z, T, K, Gb;
   int bus0, br0, gen0, zone0, ctg0, gb0, tp0;
   int n_mt, n_kt;        // contingency tiles along monitored branches / outages
+  int ctg_mg, n_mg;      // monitored-branch tiles per contingency block, and the number of such groups
+  int ctg_tb, ctg_ntc;   // periods per contingency block, and the number of period chunks
   int n_sb;              // stage-3 branch blocks per period
   int bal0, n_bal_pack;  // first entry / number of warp packs of the balance CSR
   int adj0, n_adj_pack;  // same for the branch-end adjoint CSR
@@ -35,11 +37,12 @@ struct Inst {
   long long tb0, tm0, tg0, tz0, tk0;
   long long pg0;         // PTDF restricted to generator buses: M x Gb, row m
   long long l0;          // line-outage block, M x K, row m
-  long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mt][T][K]
+  long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mg][T][K]
   long long gi0;         // adjoint DC products at the generator buses: [T][Gb + 1]
   double inv_n;          // 1 / n
   double hours;          // sum of dt
   double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
+  int obj_lo, obj_n;     // this instance's stage-1/2 objective slots
 };
 
 // Roles of the blocks of the fused stage kernels.  R_DCF / R_DCA are the dense DC products;
@@ -141,9 +144,10 @@ struct Dev {
   Real *gF;                           // [sum T M] dz/df
   Dc *gip;                            // adjoint DC products [sum T (Gb + 1)]
   Real *avf, *avo, *ad;               // branch-end adjoints [sum T M]
-  Dc *objp;                           // [n_obj_slots][N_TERMS] per-block objective terms
-  int n_obj_slots;
-  const int *slot_inst;               // [n_obj_slots]
+  Dc *objp;                           // [n_obj_slots][N_TERMS] per-block objective terms: the
+                                      // stage-1/2 blocks' slots, instance-major, then one per stage-5 block
+  int n_obj_slots, n_obj12;           // all slots; stage-1/2 slots
+  const int *slot_map;                // [n_obj12] stage-1/2 block (launch order) -> slot
   double *obj, *terms;                // [n_inst], [n_inst][N_TERMS]
   Real *g;                            // gradient [n_x]
   unsigned int *ticket;               // last-block counter of stage 5
@@ -162,6 +166,7 @@ struct Plan {
   InstTab tab;
   long long n_x;
   int maxT;
+  int maxTB;  // largest period chunk of a contingency block (sizes its shared memory)
   // sparse DC mode (instance 0 only): grids of the solve kernels
   int sp;
   int sp_inj_blocks;   // right-hand-side blocks of k_sp_inj (T more compute the mean injection)

@@ -222,9 +222,10 @@ __device__ void write_obj(Dc *objp, int slot, Obj3<Dc> o) {
   }
 }
 
-// Programmatic dependent launch: let the next stage start its independent prologue early, and
-// wait for the previous stage's results before reading them.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Programmatic dependent launch: a stage may begin as its predecessor's blocks exit and waits
+// (griddepcontrol.wait) for the predecessor's completion before reading its results; loads of
+// data no earlier stage writes come before the wait.  No stage triggers its dependents early:
+// blocks of the next stage parked at the wait slowed the long sparse-solve kernels (measured).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ float f_nan() { return __int_as_float(0x7fc00000); }
@@ -449,7 +450,6 @@ template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x, int slot0) {
-  pdl_launch_dependents();
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
   Obj3<Dc> acc = obj3<Dc>(-1);
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, D
     acc.id[0] = T_ZRZ;
     s1_zone(d, I, w.t, w.sub, x, acc);
   }
-  write_obj(d.objp, slot0 + blockIdx.x, acc);
+  write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -532,166 +532,185 @@ __device__ __forceinline__ float lodf_load(const void *base, long long idx, int 
 template <typename Real>
 __host__ __device__ constexpr int ctg_tch() { return sizeof(Real) == 8 ? 8 : 16; }
 
+// Contingency block (Sec. II-E, Eqs. rank_correct, sfr_pen-zctg) for outages [k0, k0 + 64), the
+// monitored-branch tiles of one group (64 branches each) and one chunk of periods:
+//   F[t,m,k] = f[t,m] + L[m,k] f[t,k],   s = sqrt(F^2 + qmax2[t,m]),
+//   z += w sigma_s(s - s_ctg_m),  dz/dF = w sigma' F / s,
+// screened in FP32 (an element is exact-evaluated only if F^2 + qmax2 - s_ctg^2 > 0; the FP64 path
+// adds a 1e-4 s_ctg^2 margin and recomputes candidates from the FP64 block).  Row sums
+// (dz/df_m, dz/dqmax2_m) go to the partials pm, pq per outage tile; column sums (dz/df_k through
+// L[m,k]) accumulate over the group's tiles in shared memory and go to pk per group.
 template <typename Real, typename Dc>
 __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> &acc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
-  const int T = I.T;
-  const int mt = sub / I.n_kt, kt = sub % I.n_kt;
-  const int m0 = mt * CT_BM, k0 = kt * CT_BK;
-  Real *s_q2 = reinterpret_cast<Real *>(smem_raw);   // [T][BM] qmax2
-  Real *s_s2 = s_q2 + T * CT_BM;                      // [BM] s_ctg^2
+  const int T = I.T, TBM = I.ctg_tb;
+  const int per_chunk = I.n_mg * I.n_kt;
+  const int tci = sub / per_chunk, rem = sub % per_chunk, mg = rem / I.n_kt, kt = rem % I.n_kt;
+  const int t0 = tci * TBM, TB = min(TBM, T - t0);
+  const int k0 = kt * CT_BK;
+  const int mt0 = mg * I.ctg_mg, mt1 = min(I.n_mt, mt0 + I.ctg_mg);
+  Real *s_q2 = reinterpret_cast<Real *>(smem_raw);   // [TB][BM] qmax2
+  Real *s_s2 = s_q2 + TBM * CT_BM;                    // [BM] s_ctg^2
   Real *s_gm = s_s2 + CT_BM;                          // [TCH][BM]
   Real *s_gq = s_gm + TCH * CT_BM;                    // [TCH][BM]
   Real *s_gk = s_gq + TCH * CT_BM;                    // [TCH][8][BK]
-  Real *s_f64m = s_gk + TCH * 8 * CT_BK;              // [T][BM] (FP64 path only)
-  Real *s_f64k = s_f64m + (F64 ? T * CT_BM : 0);      // [T][BK] (FP64 path only)
-  float *s_fm = reinterpret_cast<float *>(s_f64k + (F64 ? T * CT_BK : 0));  // [T][BM]
-  float *s_qs = s_fm + T * CT_BM;                     // [T][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
-  float *s_fk = s_qs + T * CT_BM;                     // [T][BK]
+  Real *s_ga = s_gk + TCH * 8 * CT_BK;                // [TB][BK] column sums over the group
+  Real *s_f64m = s_ga + TBM * CT_BK;                  // [TB][BM] (FP64 path only)
+  Real *s_f64k = s_f64m + (F64 ? TBM * CT_BM : 0);    // [TB][BK] (FP64 path only)
+  float *s_fm = reinterpret_cast<float *>(s_f64k + (F64 ? TBM * CT_BK : 0));  // [TB][BM]
+  float *s_qs = s_fm + TBM * CT_BM;                   // [TB][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
+  float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // the line-outage block does not depend on stage 1: load it before waiting
-  float Lr[8][2];
+  Real obj = 0;
+  const Real eps = d.eps;
+  for (int mt = mt0; mt < mt1; ++mt) {
+    const int m0 = mt * CT_BM;
+    // the line-outage block does not depend on stage 1 (the first tile loads before waiting)
+    float Lr[8][2];
 #pragma unroll
-  for (int bq = 0; bq < 8; ++bq) {
-    const int m = m0 + wid * 8 + bq;
+    for (int bq = 0; bq < 8; ++bq) {
+      const int m = m0 + wid * 8 + bq;
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int k = k0 + lane + 32 * a;
-      float v = f_nan();
-      if (m < I.M && k < I.K && d.ctg_br[I.ctg0 + k] != m) v = lodf_load(d.lodf, I.l0 + (long long)m * I.K + k, d.lodf_dtype);
-      Lr[bq][a] = v;
+      for (int a = 0; a < 2; ++a) {
+        const int k = k0 + lane + 32 * a;
+        float v = f_nan();
+        if (m < I.M && k < I.K && d.ctg_br[I.ctg0 + k] != m) v = lodf_load(d.lodf, I.l0 + (long long)m * I.K + k, d.lodf_dtype);
+        Lr[bq][a] = v;
+      }
     }
-  }
-  if (threadIdx.x < CT_BM) s_s2[threadIdx.x] = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
-  pdl_wait();
+    if (mt == mt0) {
+      pdl_wait();
+#pragma unroll 4
+      for (int e = threadIdx.x; e < TB * CT_BK; e += NTHR) {
+        const int tt = e / CT_BK, c = e % CT_BK, k = k0 + c;
+        float f = 0.f;
+        Real f64 = 0;
+        if (k < I.K) {
+          const long long idx = I.tk0 + (long long)(t0 + tt) * I.K + k;
+          f = d.fk32[idx];
+          if (F64) f64 = d.fk[idx];
+        }
+        s_fk[tt * CT_BK + c] = f;
+        if (F64) s_f64k[tt * CT_BK + c] = f64;
+        s_ga[tt * CT_BK + c] = 0;
+      }
+    }
+    __syncthreads();  // the previous tile is done with s_q2, s_fm, s_qs, s_s2
+    if (threadIdx.x < CT_BM) s_s2[threadIdx.x] = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
 #pragma unroll 8
-  for (int e = threadIdx.x; e < T * (CT_BM + CT_BK); e += NTHR) {
-    const int t = e / (CT_BM + CT_BK), c = e % (CT_BM + CT_BK);
-    if (c < CT_BM) {
-      const int m = m0 + c;
+    for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) {
+      const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
       float f = 0.f, qs = 0.f;
       Real q2 = 0, f64 = 0;
       if (m < I.M) {
-        const long long idx = I.tm0 + (long long)t * I.M + m;
+        const long long idx = I.tm0 + (long long)(t0 + tt) * I.M + m;
         f = d.f32[idx];
         q2 = d.qm2[idx];
         const Real s2 = d.br_s2ctg[I.br0 + m];
         qs = F64 ? (float)(q2 - s2) + 1e-4f * (float)s2 : (float)(q2 - s2);
         if (F64) f64 = d.fre[idx];
       }
-      s_fm[t * CT_BM + c] = f;
-      s_qs[t * CT_BM + c] = qs;
-      s_q2[t * CT_BM + c] = q2;
-      if (F64) s_f64m[t * CT_BM + c] = f64;
-    } else {
-      const int k = k0 + c - CT_BM;
-      float f = 0.f;
-      Real f64 = 0;
-      if (k < I.K) {
-        const long long idx = I.tk0 + (long long)t * I.K + k;
-        f = d.fk32[idx];
-        if (F64) f64 = d.fk[idx];
-      }
-      s_fk[t * CT_BK + c - CT_BM] = f;
-      if (F64) s_f64k[t * CT_BK + c - CT_BM] = f64;
+      s_fm[tt * CT_BM + c] = f;
+      s_qs[tt * CT_BM + c] = qs;
+      s_q2[tt * CT_BM + c] = q2;
+      if (F64) s_f64m[tt * CT_BM + c] = f64;
     }
-  }
-  __syncthreads();
-  Real obj = 0;
-  const Real eps = d.eps;
-  for (int tc0 = 0; tc0 < T; tc0 += TCH) {
-    const int tn = min(TCH, T - tc0);
-    for (int tt = 0; tt < tn; ++tt) {
-      const int t = tc0 + tt;
-      float Fv[8][2];
-      bool hit = false;
-#pragma unroll
-      for (int bq = 0; bq < 8; ++bq) {
-        const float fm = s_fm[t * CT_BM + wid * 8 + bq], qs = s_qs[t * CT_BM + wid * 8 + bq];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          Fv[bq][a] = __fmaf_rn(Lr[bq][a], s_fk[t * CT_BK + lane + 32 * a], fm);
-          hit |= __fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f;
-        }
-      }
-      Real gm[8], gq[8], gk[2] = {0, 0};
-#pragma unroll
-      for (int bq = 0; bq < 8; ++bq) gm[bq] = gq[bq] = 0;
-      if (hit) {  // rare: a (candidate) post-contingency overload among this thread's 16 elements
-        const Real w = d.dt[I.tp0 + t] * d.c_s * d.beta;
+    __syncthreads();
+    for (int tc0 = 0; tc0 < TB; tc0 += TCH) {
+      const int tn = min(TCH, TB - tc0);
+      for (int tt = 0; tt < tn; ++tt) {
+        const int tl = tc0 + tt, t = t0 + tl;
+        float Fv[8][2];
+        bool hit = false;
 #pragma unroll
         for (int bq = 0; bq < 8; ++bq) {
-          const int mm = wid * 8 + bq;
-          const float qs = s_qs[t * CT_BM + mm];
+          const float fm = s_fm[tl * CT_BM + wid * 8 + bq], qs = s_qs[tl * CT_BM + wid * 8 + bq];
 #pragma unroll
           for (int a = 0; a < 2; ++a) {
-            if (!(__fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f)) continue;  // NaN (pad, outaged branch) fails too
-            Real Fx, Lx;
-            if (F64) {
-              Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.K + (k0 + lane + 32 * a)];
-              Fx = s_f64m[t * CT_BM + mm] + Lx * s_f64k[t * CT_BK + lane + 32 * a];
-              if (Fx * Fx + s_q2[t * CT_BM + mm] - s_s2[mm] <= Real(0)) continue;
-            } else {
-              Lx = (Real)Lr[bq][a];
-              Fx = (Real)Fv[bq][a];
-            }
-            const Real sv = dsqrt(Fx * Fx + s_q2[t * CT_BM + mm]);
-            Real val, der;
-            soft_relu(sv - dsqrt(s_s2[mm]), eps, val, der);
-            obj += w * (val - eps);
-            const Real dd = w * der / sv;  // dz/dF = w sigma' F / s
-            gm[bq] += dd * Fx;
-            gk[a] += dd * Fx * Lx;
-            gq[bq] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
+            Fv[bq][a] = __fmaf_rn(Lr[bq][a], s_fk[tl * CT_BK + lane + 32 * a], fm);
+            hit |= __fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f;
           }
         }
-      }
-      // row sums over this warp's 64 columns (only rows with an overload), column partials per warp
+        Real gm[8], gq[8], gk[2] = {0, 0};
 #pragma unroll
-      for (int bq = 0; bq < 8; ++bq) {
-        Real v1 = 0, v2 = 0;
-        if (__any_sync(0xffffffffu, gq[bq] != Real(0))) {
-          v1 = warp_sum(gm[bq]);
-          v2 = warp_sum(gq[bq]);
+        for (int bq = 0; bq < 8; ++bq) gm[bq] = gq[bq] = 0;
+        if (hit) {  // a (candidate) post-contingency overload among this thread's 16 elements
+          const Real w = d.dt[I.tp0 + t] * d.c_s * d.beta;
+#pragma unroll
+          for (int bq = 0; bq < 8; ++bq) {
+            const int mm = wid * 8 + bq;
+            const float qs = s_qs[tl * CT_BM + mm];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+              if (!(__fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f)) continue;  // NaN (pad, outaged branch) fails too
+              Real Fx, Lx;
+              if (F64) {
+                Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.K + (k0 + lane + 32 * a)];
+                Fx = s_f64m[tl * CT_BM + mm] + Lx * s_f64k[tl * CT_BK + lane + 32 * a];
+                if (Fx * Fx + s_q2[tl * CT_BM + mm] - s_s2[mm] <= Real(0)) continue;
+              } else {
+                Lx = (Real)Lr[bq][a];
+                Fx = (Real)Fv[bq][a];
+              }
+              const Real sv = dsqrt(Fx * Fx + s_q2[tl * CT_BM + mm]);
+              Real val, der;
+              soft_relu(sv - dsqrt(s_s2[mm]), eps, val, der);
+              obj += w * (val - eps);
+              const Real dd = w * der / sv;  // dz/dF = w sigma' F / s
+              gm[bq] += dd * Fx;
+              gk[a] += dd * Fx * Lx;
+              gq[bq] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
+            }
+          }
         }
-        if (lane == 0) {
-          s_gm[tt * CT_BM + wid * 8 + bq] = v1;
-          s_gq[tt * CT_BM + wid * 8 + bq] = v2;
+        // row sums over this warp's 64 columns (only rows with an overload), column partials per warp
+#pragma unroll
+        for (int bq = 0; bq < 8; ++bq) {
+          Real v1 = 0, v2 = 0;
+          if (__any_sync(0xffffffffu, gq[bq] != Real(0))) {
+            v1 = warp_sum(gm[bq]);
+            v2 = warp_sum(gq[bq]);
+          }
+          if (lane == 0) {
+            s_gm[tt * CT_BM + wid * 8 + bq] = v1;
+            s_gq[tt * CT_BM + wid * 8 + bq] = v2;
+          }
+        }
+        s_gk[(tt * 8 + wid) * CT_BK + lane] = gk[0];
+        s_gk[(tt * 8 + wid) * CT_BK + lane + 32] = gk[1];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < tn * CT_BM; e += NTHR) {
+        const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
+        if (m < I.M) {
+          const long long q = I.pm0 + ((long long)kt * T + t0 + tc0 + tt) * I.M + m;
+          d.pm[q] = s_gm[tt * CT_BM + c];
+          d.pq[q] = s_gq[tt * CT_BM + c];
         }
       }
-      s_gk[(tt * 8 + wid) * CT_BK + lane] = gk[0];
-      s_gk[(tt * 8 + wid) * CT_BK + lane + 32] = gk[1];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < tn * CT_BM; e += NTHR) {
-      const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
-      if (m < I.M) {
-        const long long q = I.pm0 + ((long long)kt * T + tc0 + tt) * I.M + m;
-        d.pm[q] = s_gm[tt * CT_BM + c];
-        d.pq[q] = s_gq[tt * CT_BM + c];
-      }
-    }
-    for (int e = threadIdx.x; e < tn * CT_BK; e += NTHR) {
-      const int tt = e / CT_BK, c = e % CT_BK, k = k0 + c;
-      if (k < I.K) {
-        Real sum = 0;
+      for (int e = threadIdx.x; e < tn * CT_BK; e += NTHR) {
+        const int tt = e / CT_BK, c = e % CT_BK;
+        Real sum = s_ga[(tc0 + tt) * CT_BK + c];
 #pragma unroll
         for (int ww = 0; ww < 8; ++ww) sum += s_gk[(tt * 8 + ww) * CT_BK + c];
-        d.pk[I.pk0 + ((long long)mt * T + tc0 + tt) * I.K + k] = sum;
+        s_ga[(tc0 + tt) * CT_BK + c] = sum;
       }
+      __syncthreads();
     }
-    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < TB * CT_BK; e += NTHR) {
+    const int tt = e / CT_BK, c = e % CT_BK, k = k0 + c;
+    if (k < I.K) d.pk[I.pk0 + ((long long)mg * T + t0 + tt) * I.K + k] = s_ga[tt * CT_BK + c];
   }
   acc.v[0] = DcOps<Dc>::from_real(obj);
 }
 
 template <typename Real, typename Dc>
-__global__ void __launch_bounds__(NTHR) k_s2(const __grid_constant__ Dev<Real, Dc> d,
+__global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x, int slot0) {
-  pdl_launch_dependents();
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
   Obj3<Dc> acc = obj3<Dc>(-1);
@@ -704,7 +723,7 @@ __global__ void __launch_bounds__(NTHR) k_s2(const __grid_constant__ Dev<Real, D
     acc.id[0] = T_ZCTG;
     s2_ctg(d, I, w.sub, acc);
   }
-  write_obj(d.objp, slot0 + blockIdx.x, acc);
+  write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -715,7 +734,6 @@ template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x) {
-  pdl_launch_dependents();
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
   const int t = w.t;
@@ -739,7 +757,7 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
     if (kx >= 0) {
       Real gk = 0;
 #pragma unroll 8
-      for (int mt = 0; mt < I.n_mt; ++mt) gk += d.pk[I.pk0 + ((long long)mt * I.T + t) * I.K + kx];
+      for (int mg = 0; mg < I.n_mg; ++mg) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
       gF += gk;
     }
     d.gF[e] = gF;
@@ -915,7 +933,6 @@ template <typename Real, typename Dc, bool ADAM>
 __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              Real *__restrict__ x) {
-  pdl_launch_dependents();
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
   if (w.role == R_BUS) s4_bus<Real, Dc, ADAM>(d, I, w.t, w.sub, x);
@@ -930,42 +947,78 @@ __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, D
 // stage 5: generator gradients (+ Adam), objective reduction, step counter
 // ---------------------------------------------------------------------------------------------
 
-// Objective of every instance from the block slots (fixed order), plus the closed-form soft-ReLU
-// floor of the contingency term; run by the last block of stage 5.
-template <typename Real, typename Dc>
-__device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
+// Deterministic block sum of N_TERMS values per thread; the result is valid in thread 0.
+template <typename Dc>
+__device__ void block_sum_terms(Dc (&a)[N_TERMS]) {
   __shared__ Dc red[NTHR / 32][N_TERMS];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N_TERMS; ++k)
+#pragma unroll
+    for (int q = 16; q > 0; q >>= 1) a[k] = DcOps<Dc>::add(a[k], DcOps<Dc>::shfl_down(a[k], q));
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) red[wid][k] = a[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) {
+      Dc v = red[0][k];
+#pragma unroll
+      for (int q = 1; q < NTHR / 32; ++q) v = DcOps<Dc>::add(v, red[q][k]);
+      a[k] = v;
+    }
+}
+
+// Objective reduction, level 1, run by every stage-5 block: its own terms plus an equal share of
+// its instance's stage-1/2 block slots (instance-major, so a share is a contiguous range) go to
+// the block's stage-5 slot.  The stage-1/2 slots are complete: stage 5 waits on stage 4, which
+// waited on stages 3, 2 and 1.
+template <typename Real, typename Dc>
+__device__ void reduce_share(const Dev<Real, Dc> &d, const Inst &I, const Span &sp, Obj3<Dc> own) {
+  const int nb = sp.per_t * sp.nt, r = blockIdx.x - sp.first;
+  const int chunk = (I.obj_n + nb - 1) / nb;
+  const int lo = I.obj_lo + min(I.obj_n, r * chunk), hi = I.obj_lo + min(I.obj_n, (r + 1) * chunk);
+  const int slot = d.n_obj12 + blockIdx.x;
+  write_obj(d.objp, slot, own);
+  Dc a[N_TERMS];
+#pragma unroll
+  for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
+  for (int s = lo + threadIdx.x; s < hi; s += NTHR)
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::add(a[k], d.objp[(long long)s * N_TERMS + k]);
+  block_sum_terms(a);
+  if (threadIdx.x == 0) {
+    Dc *dst = d.objp + (long long)slot * N_TERMS;
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) dst[k] = DcOps<Dc>::add(dst[k], a[k]);
+  }
+}
+
+// Objective reduction, level 2, run by the last block of stage 5: per instance, the stage-5 slots
+// of its blocks in fixed order, plus the closed-form soft-ReLU floor of the contingency term.
+template <typename Real, typename Dc>
+__device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab, const Spans &S) {
   for (int b = 0; b < tab.n_inst; ++b) {
+    const Span &sp = S.s[b];
+    const int nb = sp.per_t * sp.nt;
     Dc a[N_TERMS];
 #pragma unroll
     for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
-#pragma unroll 4
-    for (int s = threadIdx.x; s < d.n_obj_slots; s += NTHR) {
-      if (d.slot_inst[s] != b) continue;
+    for (int j = threadIdx.x; j < nb; j += NTHR)
 #pragma unroll
-      for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::add(a[k], d.objp[(long long)s * N_TERMS + k]);
-    }
-#pragma unroll
-    for (int k = 0; k < N_TERMS; ++k)
-#pragma unroll
-      for (int q = 16; q > 0; q >>= 1) a[k] = DcOps<Dc>::add(a[k], DcOps<Dc>::shfl_down(a[k], q));
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < N_TERMS; ++k) red[wid][k] = a[k];
-    __syncthreads();
-    if (threadIdx.x < N_TERMS) {
-      Dc v = red[0][threadIdx.x];
-#pragma unroll
-      for (int q = 1; q < NTHR / 32; ++q) v = DcOps<Dc>::add(v, red[q][threadIdx.x]);
-      double tv = to_double(v);
-      if (threadIdx.x == T_ZCTG) tv += tab.I[b].hours * tab.I[b].wfloor_ctg;
-      d.terms[b * N_TERMS + threadIdx.x] = tv;
-    }
-    __syncthreads();
+      for (int k = 0; k < N_TERMS; ++k)
+        a[k] = DcOps<Dc>::add(a[k], d.objp[(long long)(d.n_obj12 + sp.first + j) * N_TERMS + k]);
+    block_sum_terms(a);
     if (threadIdx.x == 0) {
       double tot = 0.0;
-      for (int k = 0; k < N_TERMS; ++k) tot += d.terms[b * N_TERMS + k];
+      for (int k = 0; k < N_TERMS; ++k) {
+        double tv = to_double(a[k]);
+        if (k == T_ZCTG) tv += tab.I[b].hours * tab.I[b].wfloor_ctg;
+        d.terms[b * N_TERMS + k] = tv;
+        tot += tv;
+      }
       d.obj[b] = tot;
       if (d.trace) {
         const long long it = *d.step - *d.trace_step0;
@@ -978,8 +1031,7 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
 template <typename Real, typename Dc, bool ADAM>
 __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
-                                             Real *__restrict__ x, int slot0) {
-  pdl_launch_dependents();
+                                             Real *__restrict__ x) {
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
   const int t = w.t;
@@ -1044,7 +1096,7 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
       d.g[kr] = gr;
     }
   }
-  write_obj(d.objp, slot0 + blockIdx.x, acc);
+  reduce_share(d, I, S.s[w.inst], acc);
   // the last block to finish reduces the objective and advances the step counter
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -1054,7 +1106,7 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
   __syncthreads();
   if (!last) return;
   __threadfence();
-  final_reduce(d, tab);
+  final_reduce(d, tab, S);
   __syncthreads();
   if (threadIdx.x == 0) {
     *d.ticket = 0;
@@ -1105,7 +1157,6 @@ __global__ void __launch_bounds__(NTHR) k_adam(Real *__restrict__ x, Real *__res
 template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Real, Dc> d,
                                                  const __grid_constant__ Inst I, const Real *__restrict__ x, int nb) {
-  pdl_launch_dependents();
   const Real *p = x + I.x0 + 2LL * I.T * I.n;
   if ((int)blockIdx.x < nb) {
     const long long e = (long long)blockIdx.x * NTHR + threadIdx.x;
@@ -1135,7 +1186,6 @@ __global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Rea
 template <typename Real, typename Dc, bool ADJ>
 __global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Real, Dc> d,
                                                  const __grid_constant__ Inst I, int nrow_blocks) {
-  pdl_launch_dependents();
   const int T = I.T;
   if (ADJ && (int)blockIdx.x == nrow_blocks) {
     pdl_wait();
@@ -1184,7 +1234,6 @@ __global__ void __launch_bounds__(NTHR) k_sp_tail(const __grid_constant__ Dev<Re
                                                   const __grid_constant__ Inst I) {
   __shared__ Dc s_s[SP_RB][SP_BK + 1];
   __shared__ Dc s_z[SP_BK][SP_TMAX];
-  pdl_launch_dependents();
   const int T = I.T, m = d.nT;
   const int r = threadIdx.x >> 4, tc = threadIdx.x & 15;
   const int a = blockIdx.x * SP_RB + r;
@@ -1236,7 +1285,6 @@ __global__ void __launch_bounds__(NTHR) k_sp_tail(const __grid_constant__ Dev<Re
 template <typename Real, typename Dc, bool ADJ>
 __global__ void __launch_bounds__(NTHR) k_sp_back(const __grid_constant__ Dev<Real, Dc> d,
                                                   const __grid_constant__ Inst I) {
-  pdl_launch_dependents();
   const int T = I.T;
   const int w = blockIdx.x * (NTHR / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   const int nrows = ADJ ? d.n_adj_rows : d.nS;
@@ -1273,12 +1321,12 @@ __global__ void __launch_bounds__(NTHR) k_sp_back(const __grid_constant__ Dev<Re
 // ---------------------------------------------------------------------------------------------
 
 template <typename Real>
-size_t ctg_smem_bytes(int T) {
+size_t ctg_smem_bytes(int TB) {
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
-  return sizeof(float) * (size_t)T * (2 * CT_BM + CT_BK) +
-         sizeof(Real) * ((size_t)T * CT_BM + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
-                         (F64 ? (size_t)T * (CT_BM + CT_BK) : 0));
+  return sizeof(float) * (size_t)TB * (2 * CT_BM + CT_BK) +
+         sizeof(Real) * ((size_t)TB * (CT_BM + CT_BK) + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
+                         (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0));
 }
 
 // Record a timing event on s; inside stream capture it becomes an external event node.
@@ -1291,7 +1339,8 @@ static inline void mark(cudaEvent_t *ev, int k, cudaStream_t s) {
 }
 
 // Launch with programmatic stream serialization: the kernel may begin while its predecessor
-// drains; it waits (griddepcontrol.wait) before reading the predecessor's results.
+// drains (no early trigger, so as the predecessor's blocks exit); it waits (griddepcontrol.wait)
+// before reading the predecessor's results.
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s, Args &&...args) {
   cudaLaunchConfig_t cfg = {};
@@ -1311,7 +1360,7 @@ template <typename Real, typename Dc>
 cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, bool adam, cudaStream_t s,
                         cudaEvent_t *ev) {
   Real *x = const_cast<Real *>(static_cast<const Real *>(xv));
-  const int o2 = P.s1.n_blocks, o5 = P.s1.n_blocks + P.s2.n_blocks;
+  const int o2 = P.s1.n_blocks;
   // with timing events between the kernels, launch them plainly so each event brackets one kernel
   const bool pdl = ev == nullptr;
   cudaError_t e = cudaSuccess;
@@ -1338,7 +1387,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     e = cudaGetLastError();
   }
   mark(ev, 1, s);
-  go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxT), d, P.tab, P.s2, (const Real *)x, o2);
+  go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB), d, P.tab, P.s2, (const Real *)x, o2);
   mark(ev, 2, s);
   go(k_s3<Real, Dc>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
   mark(ev, 3, s);
@@ -1352,15 +1401,15 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     if (P.sp_bwa_blocks > 0) go(k_sp_back<Real, Dc, true>, P.sp_bwa_blocks, 0, d, I);
   }
   mark(ev, 4, s);
-  if (adam) go(k_s5<Real, Dc, true>, P.s5.n_blocks, 0, d, P.tab, P.s5, x, o5);
-  else go(k_s5<Real, Dc, false>, P.s5.n_blocks, 0, d, P.tab, P.s5, x, o5);
+  if (adam) go(k_s5<Real, Dc, true>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
+  else go(k_s5<Real, Dc, false>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
   mark(ev, 5, s);
   return e;
 }
 
 template <typename Real, typename Dc>
-cudaError_t prepare_eval(int maxT) {
-  const size_t sm = ctg_smem_bytes<Real>(maxT);
+cudaError_t prepare_eval(int maxTB) {
+  const size_t sm = ctg_smem_bytes<Real>(maxTB);
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(k_s2<Real, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
