@@ -457,6 +457,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-dayahead", action="store_true", help="skip the day-ahead grid")
+    ap.add_argument("--dayahead-only", action="store_true",
+                    help="time only the day-ahead grid and print its object as the line (profiling runs)")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
@@ -466,6 +468,13 @@ def main():
         return
     from paper_2310_06650_gb300.build import build
     build()
+    if args.dayahead_only:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(local_rank)
+            peaks, src = _peaks()
+            print(json.dumps(dict(dayahead_leg(args, peaks, src, local_rank), workload="dayahead")), flush=True)
+        return
     gpu_leg(args, rank, world, local_rank)
 
 

@@ -496,6 +496,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     const HostInst &H = h->hi[b];
     Inst &D = P.tab.I[b];
     D.n = H.n; D.M = H.M; D.G = H.G; D.Z = H.Z; D.T = H.T; D.K = H.K; D.Gb = (int)H.gbus.size();
+    D.Kp = ceil_div(H.K, 4) * 4;
     D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.gb0 = gb0; D.tp0 = tp0;
     D.n_mt = ceil_div(H.M, CT_BM);
     D.n_kt = ceil_div(H.K, CT_BK);
@@ -514,7 +515,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     D.wfloor_ctg = h->opt.c_s * h->opt.beta * h->opt.eps * ((double)H.M * H.K - H.K);
     x0 += (long long)H.T * (2LL * H.n + 3LL * H.G);
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
-    tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gb; l0 += (long long)H.M * H.K;
+    tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gb; l0 += (long long)H.M * D.Kp;
     pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.K; gi0 += (long long)H.T * (D.Gb + 1);
     bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.K; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
@@ -530,7 +531,12 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     const int nr = H0.n - 1;
     P.sp_inj_blocks = ceil_div((long long)nr * H0.T, NTHR);
     P.sp_fw_blocks = ceil_div(nr, NTHR / 32);
-    P.sp_tail_blocks = ceil_div(H0.nT, SP_RB);
+    // column splits: about two waves of tail blocks, at least SP_BK columns per split
+    const int n_rt = ceil_div(H0.nT, SP_RB);
+    const int ks0 = n_rt > 0 ? std::max(1, std::min(ceil_div(2 * CTG_WAVE, n_rt), ceil_div(H0.nT, SP_BK))) : 1;
+    P.sp_tail_kc = std::max(SP_BK, ceil_div(ceil_div(H0.nT, ks0), SP_BK) * SP_BK);
+    P.sp_tail_ks = std::max(1, ceil_div(H0.nT, P.sp_tail_kc));
+    P.sp_tail_blocks = n_rt * P.sp_tail_ks;
     P.sp_bw_blocks = ceil_div(H0.nS, NTHR / 32);
     P.sp_bwa_blocks = ceil_div((long long)H0.adj_rows.size(), NTHR / 32);
   }
@@ -630,7 +636,16 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
       cload.insert(cload.end(), H.cload.begin(), H.cload.end());
     }
     rsum.insert(rsum.end(), H.rsum.begin(), H.rsum.end());
-    lodf.insert(lodf.end(), H.lodf.begin(), H.lodf.end());
+    // line-outage block with its row stride padded to Kp; NaN marks the pads and each outage's own
+    // branch (the contingency kernel's screen rejects NaN elements)
+    {
+      const int Kp = P.tab.I[b].Kp;
+      const size_t base = lodf.size();
+      lodf.resize(base + (size_t)H.M * Kp, NAN);
+      for (int m = 0; m < H.M; ++m)
+        for (int k = 0; k < H.K; ++k)
+          if (H.ctg[k] != m) lodf[base + (size_t)m * Kp + k] = H.lodf[(size_t)m * H.K + k];
+    }
     const double inf = INFINITY;
     for (int t = 0; t < H.T; ++t)
       for (int i = 0; i < H.n; ++i) { lo.push_back(H.vmin[i]); hi.push_back(H.vmax[i]); }
@@ -697,6 +712,8 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
     d.lodf = q;
   }
   if (f64) {
+    for (double &v : lodf)
+      if (std::isnan(v)) v = 0.0;  // never read: only elements that pass the FP32 screen are recomputed
     double *q;
     if ((rc = upload(h, &q, lodf))) return rc;
     d.lodf64 = q;
@@ -734,6 +751,11 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
     d.sp_mu = c;
     if ((rc = dalloc(h, &c, (size_t)d.n_pchunk * H.T))) return rc;
     d.sp_part = c;
+    if ((rc = dalloc(h, &c, (size_t)std::max(1LL, (long long)P.sp_tail_ks * d.nT * H.T)))) return rc;
+    d.sp_tpart = c;
+    unsigned int *tk;
+    if ((rc = dalloc(h, &tk, (size_t)std::max(1, ceil_div(d.nT, SP_RB))))) return rc;
+    d.sp_tick = tk;
   }
   const qg_options &o = h->opt;
   d.c_p = (Real)o.c_p; d.c_q = (Real)o.c_q; d.c_s = (Real)o.c_s; d.c_rz = (Real)o.c_rz;

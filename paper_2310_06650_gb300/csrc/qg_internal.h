@@ -26,6 +26,7 @@ constexpr int PACKS_PER_BLOCK = NTHR / 32;
 // (T x K) and tp0 (T).
 struct Inst {
   int n, M, G, Z, T, K, Gb;
+  int Kp;                // row stride of the line-outage block: K rounded up to a multiple of 4
   int bus0, br0, gen0, zone0, ctg0, gb0, tp0;
   int n_mt, n_kt;        // contingency tiles along monitored branches / outages
   int ctg_mg, n_mg;      // monitored-branch tiles per contingency block, and the number of such groups
@@ -36,7 +37,7 @@ struct Inst {
   long long x0;          // first variable of this instance
   long long tb0, tm0, tg0, tz0, tk0;
   long long pg0;         // PTDF restricted to generator buses: M x Gb, row m
-  long long l0;          // line-outage block, M x K, row m
+  long long l0;          // line-outage block, M x Kp, row m
   long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mg][T][K]
   long long gi0;         // adjoint DC products at the generator buses: [T][Gb + 1]
   double inv_n;          // 1 / n
@@ -50,9 +51,9 @@ struct Inst {
 // angles; right-hand side of the adjoint solve).
 enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN, R_SDCF, R_SDCA };
 
-constexpr int SP_RB = 16;   // dense tail product: rows per block
+constexpr int SP_RB = 64;   // dense tail product: rows per block
 constexpr int SP_BK = 32;   // dense tail product: columns per shared-memory chunk
-constexpr int SP_TMAX = 64; // periods per pass of the dense tail product
+constexpr int SP_TMAX = 48; // periods per pass of the dense tail product (16 lanes x 3)
 
 // A run of blocks with one role for one instance: blocks [first, first + per_t * nt);
 // block b of the span has period (or period chunk) (b - first) / per_t and slice (b - first) % per_t.
@@ -101,8 +102,9 @@ struct Dev {
   const Dc *ptdfgT;                   // [sum Gb M] the same, row gb
   const Dc *cload;                    // [sum T M] PTDF * load_t
   const Dc *rsum;                     // [sum M] PTDF * 1
-  const void *lodf;                   // [sum M K]: float / bf16 / bf16x2 (mixed) or float screening copy (FP64)
-  const double *lodf64;               // [sum M K] FP64 path only
+  const void *lodf;                   // [sum M Kp]: float / bf16 / bf16x2 (mixed) or float screening copy
+                                      // (FP64); NaN at pads and at each outage's own branch
+  const double *lodf64;               // [sum M Kp] FP64 path only
   const Real *lo, *hi;                // clip box [n_x]
   // sparse DC mode (one instance): node positions = eliminated nodes in elimination order, then
   // the tail nodes whose Schur complement S is held through its inverse; node-major work arrays
@@ -127,6 +129,8 @@ struct Dev {
   Dc *sp_rhs, *sp_u, *sp_th, *sp_zt;  // [nr T], [nr T], [nr T], [nT T]
   Dc *sp_mu;                          // [T] mean injection (uniform slack)
   Dc *sp_part;                        // [n_pchunk][T] partial sums of z1 . w
+  Dc *sp_tpart;                       // [tail splits][nT][T] partial sums of the dense tail product
+  unsigned int *sp_tick;              // [tail row tiles] last-split tickets (zero between launches)
   // penalty parameters
   Real c_p, c_q, c_s, c_rz, rho, eps, beta;
   int lodf_dtype;
@@ -172,6 +176,8 @@ struct Plan {
   int sp_inj_blocks;   // right-hand-side blocks of k_sp_inj (T more compute the mean injection)
   int sp_fw_blocks;    // k_sp_fwd rows / 8
   int sp_tail_blocks;  // k_sp_tail, 0 without a tail
+  int sp_tail_ks;      // column splits of the dense tail product
+  int sp_tail_kc;      // columns per split (a multiple of SP_BK)
   int sp_bw_blocks;    // k_sp_back forward pass
   int sp_bwa_blocks;   // k_sp_back adjoint pass
 };

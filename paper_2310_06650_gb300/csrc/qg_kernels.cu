@@ -510,36 +510,45 @@ __device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, co
   }
 }
 
-__device__ __forceinline__ float lodf_load(const void *base, long long idx, int dtype) {
-  if (dtype == QG_LODF_BF16) return __bfloat162float(static_cast<const __nv_bfloat16 *>(base)[idx]);
-  if (dtype == QG_LODF_BF16X2) {
-    const __nv_bfloat162 h = static_cast<const __nv_bfloat162 *>(base)[idx];
-    return __bfloat162float(h.x) + __bfloat162float(h.y);
+// Four consecutive entries of the line-outage block (row stride padded to a multiple of 4, so
+// the group is one aligned vector load) as floats.
+__device__ __forceinline__ void lodf_load4(const void *base, long long idx, int dtype, float (&v)[4]) {
+  if (dtype == QG_LODF_BF16) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(static_cast<const __nv_bfloat16 *>(base) + idx);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x), b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+    v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
+  } else if (dtype == QG_LODF_BF16X2) {
+    const uint4 u = *reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat162 *>(base) + idx);
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[j]);
+      v[j] = __low2float(h) + __high2float(h);
+    }
+  } else {
+    const float4 f = *reinterpret_cast<const float4 *>(static_cast<const float *>(base) + idx);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
   }
-  return static_cast<const float *>(base)[idx];
 }
 
-// Contingency tile (A8): BM monitored branches x BK outages, every period, line-outage block
-// in registers.  For outage k and monitored branch m:
-//   F = f_m + L[m,k] f_k,  s = sqrt(F^2 + qmax2_m),  z += w sigma_s(s - s_ctg_m).
-// The common path is two FMAs and a compare per element (all 16 of a thread computed before any
-// branch); the soft-ReLU floor eps of every non-violating element is added in closed form by the
-// final reduction.  Pad elements and the outaged branch itself carry L = NaN, so F is NaN and the
-// compare is false.  Per-period row sums are warp-local (each warp owns 8 rows) and column sums
-// go through shared memory, flushed once per chunk of periods: no block barrier per period.
-// FP64 path: the compare runs in FP32 against a margin of 1e-4 s_ctg^2 and every candidate is
-// recomputed exactly in FP64, so the classification and the values are those of FP64.
 template <typename Real>
-__host__ __device__ constexpr int ctg_tch() { return sizeof(Real) == 8 ? 8 : 16; }
+__host__ __device__ constexpr int ctg_tch() { return 8; }
 
 // Contingency block (Sec. II-E, Eqs. rank_correct, sfr_pen-zctg) for outages [k0, k0 + 64), the
 // monitored-branch tiles of one group (64 branches each) and one chunk of periods:
 //   F[t,m,k] = f[t,m] + L[m,k] f[t,k],   s = sqrt(F^2 + qmax2[t,m]),
-//   z += w sigma_s(s - s_ctg_m),  dz/dF = w sigma' F / s,
-// screened in FP32 (an element is exact-evaluated only if F^2 + qmax2 - s_ctg^2 > 0; the FP64 path
-// adds a 1e-4 s_ctg^2 margin and recomputes candidates from the FP64 block).  Row sums
-// (dz/df_m, dz/dqmax2_m) go to the partials pm, pq per outage tile; column sums (dz/df_k through
-// L[m,k]) accumulate over the group's tiles in shared memory and go to pk per group.
+//   z += w sigma_s(s - s_ctg_m),  dz/dF = w sigma' F / s.
+// Thread (row quad rq, column quad cq) holds a 4 x 4 piece of the line-outage tile in registers;
+// per period it reads f, qmax2 - s_ctg^2 of its rows and f_k of its columns as three 128-bit
+// shared loads and screens its 16 elements in FP32 with two FMAs and a max each: an element can
+// only be overloaded if F^2 + qmax2 - s_ctg^2 > 0 (the FP64 path adds a 1e-4 s_ctg^2 margin and
+// recomputes candidates exactly from the FP64 block).  Pads and the outaged branch itself carry
+// L = NaN, which the max ignores and every compare rejects.  Only warps with a candidate take
+// the exact path and write partial sums (the buffers are zeroed per chunk of periods): row sums
+// (dz/df_m, dz/dqmax2_m) by shuffles across the 16 column quads, flushed to the partials pm, pq
+// per outage tile; column sums (dz/df_k through L[m,k]) across the block's row quads through
+// shared memory, accumulated over the group's tiles and written to pk per group.  The soft-ReLU
+// floor eps of every non-violating element is added in closed form by the final reduction.
 template <typename Real, typename Dc>
 __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> &acc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -551,33 +560,35 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   const int t0 = tci * TBM, TB = min(TBM, T - t0);
   const int k0 = kt * CT_BK;
   const int mt0 = mg * I.ctg_mg, mt1 = min(I.n_mt, mt0 + I.ctg_mg);
-  Real *s_q2 = reinterpret_cast<Real *>(smem_raw);   // [TB][BM] qmax2
-  Real *s_s2 = s_q2 + TBM * CT_BM;                    // [BM] s_ctg^2
+  float *s_fm = reinterpret_cast<float *>(smem_raw);  // [TB][BM] base flow of the monitored branch
+  float *s_qs = s_fm + TBM * CT_BM;                   // [TB][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
+  float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK] base flow of the outaged branch
+  Real *s_s2 = reinterpret_cast<Real *>(s_fk + TBM * CT_BK);  // [BM] s_ctg^2
   Real *s_gm = s_s2 + CT_BM;                          // [TCH][BM]
   Real *s_gq = s_gm + TCH * CT_BM;                    // [TCH][BM]
   Real *s_gk = s_gq + TCH * CT_BM;                    // [TCH][8][BK]
   Real *s_ga = s_gk + TCH * 8 * CT_BK;                // [TB][BK] column sums over the group
   Real *s_f64m = s_ga + TBM * CT_BK;                  // [TB][BM] (FP64 path only)
   Real *s_f64k = s_f64m + (F64 ? TBM * CT_BM : 0);    // [TB][BK] (FP64 path only)
-  float *s_fm = reinterpret_cast<float *>(s_f64k + (F64 ? TBM * CT_BK : 0));  // [TB][BM]
-  float *s_qs = s_fm + TBM * CT_BM;                   // [TB][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
-  float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rq = threadIdx.x >> 4, cq = threadIdx.x & 15;
+  const int kc = k0 + cq * 4;  // first of this thread's four outages
+  for (int e = threadIdx.x; e < TCH * CT_BM; e += NTHR) s_gm[e] = s_gq[e] = 0;
+  for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gk[e] = 0;
   Real obj = 0;
   const Real eps = d.eps;
   for (int mt = mt0; mt < mt1; ++mt) {
     const int m0 = mt * CT_BM;
     // the line-outage block does not depend on stage 1 (the first tile loads before waiting)
-    float Lr[8][2];
+    float L[4][4];
 #pragma unroll
-    for (int bq = 0; bq < 8; ++bq) {
-      const int m = m0 + wid * 8 + bq;
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + rq * 4 + i;
+      if (m < I.M && kc < I.Kp) {
+        lodf_load4(d.lodf, I.l0 + (long long)m * I.Kp + kc, d.lodf_dtype, L[i]);
+      } else {
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int k = k0 + lane + 32 * a;
-        float v = f_nan();
-        if (m < I.M && k < I.K && d.ctg_br[I.ctg0 + k] != m) v = lodf_load(d.lodf, I.l0 + (long long)m * I.K + k, d.lodf_dtype);
-        Lr[bq][a] = v;
+        for (int j = 0; j < 4; ++j) L[i][j] = f_nan();
       }
     }
     if (mt == mt0) {
@@ -597,24 +608,22 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         s_ga[tt * CT_BK + c] = 0;
       }
     }
-    __syncthreads();  // the previous tile is done with s_q2, s_fm, s_qs, s_s2
+    __syncthreads();  // the previous tile is done with s_fm, s_qs, s_s2
     if (threadIdx.x < CT_BM) s_s2[threadIdx.x] = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
 #pragma unroll 8
     for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) {
       const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
       float f = 0.f, qs = 0.f;
-      Real q2 = 0, f64 = 0;
+      Real f64 = 0;
       if (m < I.M) {
         const long long idx = I.tm0 + (long long)(t0 + tt) * I.M + m;
         f = d.f32[idx];
-        q2 = d.qm2[idx];
-        const Real s2 = d.br_s2ctg[I.br0 + m];
+        const Real q2 = d.qm2[idx], s2 = d.br_s2ctg[I.br0 + m];
         qs = F64 ? (float)(q2 - s2) + 1e-4f * (float)s2 : (float)(q2 - s2);
         if (F64) f64 = d.fre[idx];
       }
       s_fm[tt * CT_BM + c] = f;
       s_qs[tt * CT_BM + c] = qs;
-      s_q2[tt * CT_BM + c] = q2;
       if (F64) s_f64m[tt * CT_BM + c] = f64;
     }
     __syncthreads();
@@ -622,79 +631,94 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
       const int tn = min(TCH, TB - tc0);
       for (int tt = 0; tt < tn; ++tt) {
         const int tl = tc0 + tt, t = t0 + tl;
-        float Fv[8][2];
-        bool hit = false;
+        const float4 fm4 = *reinterpret_cast<const float4 *>(s_fm + tl * CT_BM + rq * 4);
+        const float4 qs4 = *reinterpret_cast<const float4 *>(s_qs + tl * CT_BM + rq * 4);
+        const float4 fk4 = *reinterpret_cast<const float4 *>(s_fk + tl * CT_BK + cq * 4);
+        const float fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w}, qs[4] = {qs4.x, qs4.y, qs4.z, qs4.w};
+        const float fk[4] = {fk4.x, fk4.y, fk4.z, fk4.w};
+        float F[4][4];
+        float mx = -INFINITY;
 #pragma unroll
-        for (int bq = 0; bq < 8; ++bq) {
-          const float fm = s_fm[tl * CT_BM + wid * 8 + bq], qs = s_qs[tl * CT_BM + wid * 8 + bq];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            Fv[bq][a] = __fmaf_rn(Lr[bq][a], s_fk[tl * CT_BK + lane + 32 * a], fm);
-            hit |= __fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f;
+          for (int j = 0; j < 4; ++j) {
+            F[i][j] = __fmaf_rn(L[i][j], fk[j], fm[i]);
+            mx = fmaxf(mx, __fmaf_rn(F[i][j], F[i][j], qs[i]));  // NaN operands are ignored
           }
-        }
-        Real gm[8], gq[8], gk[2] = {0, 0};
+        if (!__any_sync(0xffffffffu, mx > 0.f)) continue;
+        // a (candidate) post-contingency overload in this warp
+        const Real w = d.dt[I.tp0 + t] * d.c_s * d.beta;
+        Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0};
+        if (mx > 0.f) {
 #pragma unroll
-        for (int bq = 0; bq < 8; ++bq) gm[bq] = gq[bq] = 0;
-        if (hit) {  // a (candidate) post-contingency overload among this thread's 16 elements
-          const Real w = d.dt[I.tp0 + t] * d.c_s * d.beta;
+          for (int i = 0; i < 4; ++i) {
+            const int mm = rq * 4 + i;
 #pragma unroll
-          for (int bq = 0; bq < 8; ++bq) {
-            const int mm = wid * 8 + bq;
-            const float qs = s_qs[tl * CT_BM + mm];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-              if (!(__fmaf_rn(Fv[bq][a], Fv[bq][a], qs) > 0.f)) continue;  // NaN (pad, outaged branch) fails too
+            for (int j = 0; j < 4; ++j) {
+              if (!(__fmaf_rn(F[i][j], F[i][j], qs[i]) > 0.f)) continue;  // NaN (pad, outaged branch) fails too
+              const long long tmi = I.tm0 + (long long)t * I.M + m0 + mm;
+              const Real q2 = d.qm2[tmi];
               Real Fx, Lx;
               if (F64) {
-                Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.K + (k0 + lane + 32 * a)];
-                Fx = s_f64m[tl * CT_BM + mm] + Lx * s_f64k[tl * CT_BK + lane + 32 * a];
-                if (Fx * Fx + s_q2[tl * CT_BM + mm] - s_s2[mm] <= Real(0)) continue;
+                Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.Kp + kc + j];
+                Fx = s_f64m[tl * CT_BM + mm] + Lx * s_f64k[tl * CT_BK + cq * 4 + j];
+                if (Fx * Fx + q2 - s_s2[mm] <= Real(0)) continue;
               } else {
-                Lx = (Real)Lr[bq][a];
-                Fx = (Real)Fv[bq][a];
+                Lx = (Real)L[i][j];
+                Fx = (Real)F[i][j];
               }
-              const Real sv = dsqrt(Fx * Fx + s_q2[tl * CT_BM + mm]);
+              const Real sv = dsqrt(Fx * Fx + q2);
               Real val, der;
               soft_relu(sv - dsqrt(s_s2[mm]), eps, val, der);
               obj += w * (val - eps);
               const Real dd = w * der / sv;  // dz/dF = w sigma' F / s
-              gm[bq] += dd * Fx;
-              gk[a] += dd * Fx * Lx;
-              gq[bq] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
+              gm[i] += dd * Fx;
+              gk[j] += dd * Fx * Lx;
+              gq[i] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
             }
           }
         }
-        // row sums over this warp's 64 columns (only rows with an overload), column partials per warp
+        // row sums across the 16 column quads of each half-warp
 #pragma unroll
-        for (int bq = 0; bq < 8; ++bq) {
-          Real v1 = 0, v2 = 0;
-          if (__any_sync(0xffffffffu, gq[bq] != Real(0))) {
-            v1 = warp_sum(gm[bq]);
-            v2 = warp_sum(gq[bq]);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int o = 1; o < 16; o <<= 1) {
+            gm[i] += __shfl_xor_sync(0xffffffffu, gm[i], o);
+            gq[i] += __shfl_xor_sync(0xffffffffu, gq[i], o);
           }
-          if (lane == 0) {
-            s_gm[tt * CT_BM + wid * 8 + bq] = v1;
-            s_gq[tt * CT_BM + wid * 8 + bq] = v2;
+        if (cq == 0)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            s_gm[tt * CT_BM + rq * 4 + i] = gm[i];
+            s_gq[tt * CT_BM + rq * 4 + i] = gq[i];
           }
-        }
-        s_gk[(tt * 8 + wid) * CT_BK + lane] = gk[0];
-        s_gk[(tt * 8 + wid) * CT_BK + lane + 32] = gk[1];
+        // column sums across the two row quads of this warp, then per warp through shared memory
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gk[j] += __shfl_xor_sync(0xffffffffu, gk[j], 16);
+        if (lane < 16)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) s_gk[(tt * 8 + wid) * CT_BK + cq * 4 + j] = gk[j];
       }
       __syncthreads();
+      // flush the chunk: each entry is read and re-zeroed by the same thread
       for (int e = threadIdx.x; e < tn * CT_BM; e += NTHR) {
         const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
         if (m < I.M) {
           const long long q = I.pm0 + ((long long)kt * T + t0 + tc0 + tt) * I.M + m;
-          d.pm[q] = s_gm[tt * CT_BM + c];
-          d.pq[q] = s_gq[tt * CT_BM + c];
+          d.pm[q] = s_gm[e];
+          d.pq[q] = s_gq[e];
         }
+        s_gm[e] = s_gq[e] = 0;
       }
       for (int e = threadIdx.x; e < tn * CT_BK; e += NTHR) {
         const int tt = e / CT_BK, c = e % CT_BK;
         Real sum = s_ga[(tc0 + tt) * CT_BK + c];
 #pragma unroll
-        for (int ww = 0; ww < 8; ++ww) sum += s_gk[(tt * 8 + ww) * CT_BK + c];
+        for (int ww = 0; ww < 8; ++ww) {
+          Real &g = s_gk[(tt * 8 + ww) * CT_BK + c];
+          sum += g;
+          g = 0;
+        }
         s_ga[(tc0 + tt) * CT_BK + c] = sum;
       }
       __syncthreads();
@@ -1225,30 +1249,38 @@ __global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Rea
   }
 }
 
-// Dense tail x_T = S^-1 z_T: SP_RB rows per block (16 rows x 16 period lanes, up to SP_TMAX
-// periods per pass), S^-1 and z_T staged through shared memory in chunks of SP_BK columns.  The
-// result goes to u (for the backward gather) and to the solution (forward pass) or to the
+// Dense tail x_T = S^-1 z_T (a dense contraction, but in double-FP32 for the FP64-accurate DC
+// solve, so on the FP32 pipes).  Block (row tile, column split): SP_RB rows x the split's share of
+// the columns x all periods (up to SP_TMAX per pass); thread (row group, period lane) holds 4 rows
+// x 4 periods of accumulators; S^-1 and z_T staged through shared memory SP_BK columns at a time.
+// Each split writes its partial sums; the last split of a row tile to finish (ticket) adds them in
+// split order and writes u (for the backward gather) and the solution (forward pass) or the
 // generator-bus adjoints (adjoint pass).
 template <typename Real, typename Dc, bool ADJ>
-__global__ void __launch_bounds__(NTHR) k_sp_tail(const __grid_constant__ Dev<Real, Dc> d,
-                                                  const __grid_constant__ Inst I) {
+__global__ void __launch_bounds__(NTHR, 2) k_sp_tail(const __grid_constant__ Dev<Real, Dc> d,
+                                                  const __grid_constant__ Inst I, int ks, int kchunk) {
   __shared__ Dc s_s[SP_RB][SP_BK + 1];
   __shared__ Dc s_z[SP_BK][SP_TMAX];
+  __shared__ bool last;
   const int T = I.T, m = d.nT;
-  const int r = threadIdx.x >> 4, tc = threadIdx.x & 15;
-  const int a = blockIdx.x * SP_RB + r;
+  const int rt = blockIdx.x / ks, kp = blockIdx.x % ks;
+  const int a0 = rt * SP_RB;
+  const int b_lo = min(m, kp * kchunk), b_hi = min(m, b_lo + kchunk);
+  const int rg = threadIdx.x >> 4, tc = threadIdx.x & 15;
   pdl_wait();
   for (int t0 = 0; t0 < T; t0 += SP_TMAX) {
     const int tn = min(SP_TMAX, T - t0);
-    Dc acc[SP_TMAX / 16];
+    Dc acc[4][SP_TMAX / 16];
 #pragma unroll
-    for (int j = 0; j < SP_TMAX / 16; ++j) acc[j] = DcOps<Dc>::zero();
-    for (int b0 = 0; b0 < m; b0 += SP_BK) {
-      const int bn = min(SP_BK, m - b0);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < SP_TMAX / 16; ++j) acc[i][j] = DcOps<Dc>::zero();
+    for (int b0 = b_lo; b0 < b_hi; b0 += SP_BK) {
+      const int bn = min(SP_BK, b_hi - b0);
       __syncthreads();
 #pragma unroll
       for (int e = threadIdx.x; e < SP_RB * SP_BK; e += NTHR) {
-        const int rr = e / SP_BK, cc = e % SP_BK, ar = blockIdx.x * SP_RB + rr;
+        const int rr = e / SP_BK, cc = e % SP_BK, ar = a0 + rr;
         s_s[rr][cc] = (ar < m && cc < bn) ? d.sinv[(long long)ar * m + b0 + cc] : DcOps<Dc>::zero();
       }
 #pragma unroll
@@ -1257,27 +1289,50 @@ __global__ void __launch_bounds__(NTHR) k_sp_tail(const __grid_constant__ Dev<Re
         s_z[rr][cc] = (rr < bn && cc < tn) ? d.sp_zt[(long long)(b0 + rr) * T + t0 + cc] : DcOps<Dc>::zero();
       }
       __syncthreads();
-#pragma unroll 4
-      for (int b = 0; b < SP_BK; ++b) {
-        const Dc sv = s_s[r][b];
+#pragma unroll 2
+      for (int k = 0; k < SP_BK; ++k) {
+        Dc sv[4], zv[SP_TMAX / 16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sv[i] = s_s[rg * 4 + i][k];
+#pragma unroll
+        for (int j = 0; j < SP_TMAX / 16; ++j) zv[j] = s_z[k][tc + 16 * j];
 #pragma unroll
         for (int j = 0; j < SP_TMAX / 16; ++j)
-          if (tc + 16 * j < tn) DcOps<Dc>::mac(acc[j], sv, s_z[b][tc + 16 * j]);
+          if (tc + 16 * j < tn)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) DcOps<Dc>::mac(acc[i][j], sv[i], zv[j]);
       }
     }
-    if (a < m) {
-      const int pos = d.nS + a;
-      const int gb = ADJ ? d.pos_gb[pos] : -1;
 #pragma unroll
-      for (int j = 0; j < SP_TMAX / 16; ++j) {
-        const int t = t0 + tc + 16 * j;
-        if (tc + 16 * j >= tn) continue;
-        d.sp_u[(long long)pos * T + t] = acc[j];
-        if (!ADJ) d.sp_th[(long long)pos * T + t] = acc[j];
-        else if (gb >= 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + gb] = acc[j];
-      }
+    for (int i = 0; i < 4; ++i) {
+      const int a = a0 + rg * 4 + i;
+      if (a >= m) continue;
+#pragma unroll
+      for (int j = 0; j < SP_TMAX / 16; ++j)
+        if (tc + 16 * j < tn) d.sp_tpart[((long long)kp * m + a) * T + t0 + tc + 16 * j] = acc[i][j];
     }
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(d.sp_tick + rt, 1u) == (unsigned)(ks - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < SP_RB * T; e += NTHR) {
+    const int a = a0 + e / T, t = e % T;
+    if (a >= m) continue;
+    Dc v = DcOps<Dc>::zero();
+    for (int q = 0; q < ks; ++q) v = DcOps<Dc>::add(v, d.sp_tpart[((long long)q * m + a) * T + t]);
+    const int pos = d.nS + a;
+    d.sp_u[(long long)pos * T + t] = v;
+    if (!ADJ) {
+      d.sp_th[(long long)pos * T + t] = v;
+    } else {
+      const int gb = d.pos_gb[pos];
+      if (gb >= 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + gb] = v;
+    }
+  }
+  if (threadIdx.x == 0) d.sp_tick[rt] = 0u;
 }
 
 // Backward gather x_S = M1^T u_S + M2^T u_T (u_S = D_S^-1 z_S, u_T = x_T), one warp per eliminated
@@ -1325,7 +1380,7 @@ size_t ctg_smem_bytes(int TB) {
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
   return sizeof(float) * (size_t)TB * (2 * CT_BM + CT_BK) +
-         sizeof(Real) * ((size_t)TB * (CT_BM + CT_BK) + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
+         sizeof(Real) * ((size_t)TB * CT_BK + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
                          (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0));
 }
 
@@ -1379,7 +1434,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     k_sp_inj<Real, Dc><<<P.sp_inj_blocks + I.T, NTHR, 0, s>>>(d, I, (const Real *)x, P.sp_inj_blocks);
     e = cudaGetLastError();
     go(k_sp_fwd<Real, Dc, false>, P.sp_fw_blocks, 0, d, I, P.sp_fw_blocks);
-    if (P.sp_tail_blocks > 0) go(k_sp_tail<Real, Dc, false>, P.sp_tail_blocks, 0, d, I);
+    if (P.sp_tail_blocks > 0) go(k_sp_tail<Real, Dc, false>, P.sp_tail_blocks, 0, d, I, P.sp_tail_ks, P.sp_tail_kc);
     if (P.sp_bw_blocks > 0) go(k_sp_back<Real, Dc, false>, P.sp_bw_blocks, 0, d, I);
     go(k_s1<Real, Dc>, P.s1.n_blocks, 0, d, P.tab, P.s1, (const Real *)x, 0);
   } else {
@@ -1397,7 +1452,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     // sparse mode: adjoint solve eta = Yhat^-1 w at the generator buses, and 1^T eta
     const Inst &I = P.tab.I[0];
     go(k_sp_fwd<Real, Dc, true>, P.sp_fw_blocks + 1, 0, d, I, P.sp_fw_blocks);
-    if (P.sp_tail_blocks > 0) go(k_sp_tail<Real, Dc, true>, P.sp_tail_blocks, 0, d, I);
+    if (P.sp_tail_blocks > 0) go(k_sp_tail<Real, Dc, true>, P.sp_tail_blocks, 0, d, I, P.sp_tail_ks, P.sp_tail_kc);
     if (P.sp_bwa_blocks > 0) go(k_sp_back<Real, Dc, true>, P.sp_bwa_blocks, 0, d, I);
   }
   mark(ev, 4, s);
