@@ -5,8 +5,8 @@ projected Adam update, on the 617-bus / 18-period / 562-outage real-time shape.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one CUDA-graph replay of the five stage kernels of an evaluation
-with the projected Adam update fused into the last two (qg_solve, one iteration).  L2 is flushed (a 512 MB write) before
+One step = one CUDA-graph replay of the stage kernels of an evaluation
+with the projected Adam update fused into the bus and generator stages (qg_solve, one iteration).  L2 is flushed (a 512 MB write) before
 every timed step; each step is timed with CUDA events on the launching stream.
 Rank 0 prints one JSON line.  With torchrun (N > 1) every rank runs an
 independent replica (the path has no exchange step) and the result is the sum
@@ -39,7 +39,7 @@ WORKLOAD = "rt617"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the current
 # kernel code (profiles/k_s2_rt617.md); None where no capture of the current code exists
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("rt617", "s2", True): 2650624.0, ("rt617", "s2", False): 3390976.0}
 FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
 
 
@@ -313,6 +313,7 @@ def gpu_leg(args, rank, world, local_rank):
         results[label] = {
             "step_ms": step_ms, "total_ms": total_ms, "phases": {k: statistics.mean(v) for k, v in phases.items()},
             "warm_ms": warm_ms, "e2e_s": e2e_s, "clocks": clk.summary(), "obj": float(s.obj[0].item()),
+            "launches": qg.qg_launches_per_eval(s.h),
         }
         s.close()
     if rank != 0:
@@ -346,7 +347,7 @@ def gpu_leg(args, rank, world, local_rank):
         "e2e": {"value": world * K / mix["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": 8 * case.n_x,
                 "d2h_bytes_per_step": 8 * (case.n_x + 1),
                 "call": "qg_eval_grad_host (pinned host x -> device, evaluation, objective + gradient -> host)"},
-        "gpu_launches": 5 * K,
+        "gpu_launches": mix["launches"] * K,
         "clocks": mix["clocks"],
         "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in phases.items()},
         "l2_resident": {"value": world / (mix["warm_ms"] * 1e-3), "unit": UNIT,
@@ -405,6 +406,7 @@ def dayahead_leg(args, peaks, src, local_rank):
     qg.qg_set_profiling(s.h, False)
     ph = {k: statistics.mean(v) for k, v in phases.items()}
     ms = sum(step_ms) / steps
+    launches = qg.qg_launches_per_eval(s.h)
     # contingency stage: the line-outage block is read once per evaluation
     T, M, K = case.T, case.n_branch, case.K
     s2_bytes = 4.0 * M * K + 4.0 * T * (3 * M + K)
@@ -420,9 +422,10 @@ def dayahead_leg(args, peaks, src, local_rank):
                    "l2": "working set larger than L2 (line-outage block 280 MB); no flush",
                    "x0": "merit-order dispatch, flat voltage, zero angles"},
         "setup_s": setup_s,
+        "gpu_launches": launches * steps,
         "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in ph.items()},
         "phases_note": "s1 includes the forward DC solve (injections, forward gather, tail product, backward "
-                       "gather); s4 includes the adjoint DC solve",
+                       "gather); s4 includes the adjoint DC solve; s5 is the generator stage",
         "s2": {"algorithmic_bytes": s2_bytes, "hbm_gbs": s2_gbs, "hbm_frac": s2_gbs / peaks["hbm_gbs"],
                "tflops": s2_tflops, "alu_frac": s2_tflops / fp32_peak,
                "note": "line-outage block (FP32) + flows and q-limits per launch; 4 FP32 flop per (t, m, k)"},

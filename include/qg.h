@@ -189,16 +189,22 @@ int qg_get_step(qg_ctx *h, int64_t *step);
 int qg_set_step(qg_ctx *h, int64_t step);
 
 /* Per-kernel timing (CUDA events, no profiler): when on, every evaluation and
- * Adam step records an event after each kernel, also inside qg_solve's graph.
+ * Adam step records an event after each stage, also inside qg_solve's graph.
  * qg_phase_times writes the durations in ms of the last evaluation's five
- * stage kernels in launch order (s1: branch flows, zonal sums and base DC
- * flows; s2: bus balance and contingencies; s3: contingency sums and branch
- * adjoints; s4: bus adjoint gather and adjoint DC products; s5: generator
- * gradients and the objective), then that of a stand-alone qg_adam_step if one
+ * stages in launch order (s1: branch flows, zonal sums and base DC flows;
+ * s2: bus balance and contingencies; s3: contingency sums and branch adjoints;
+ * s4: bus adjoint gather and adjoint DC products; s5: generator gradients and
+ * the objective; with the sparse DC solver s1 includes the forward solve and
+ * s4 the adjoint solve), then that of a stand-alone qg_adam_step if one
  * followed, up to cap entries; returns how many it wrote or a negative error
  * code.  Waits for those events. */
 int qg_set_profiling(qg_ctx *h, int on);
 int qg_phase_times(qg_ctx *h, float *ms, int32_t cap);
+
+/* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: the
+ * 5 stage kernels, plus 3 to 7 solve kernels with the sparse DC solver.  Returns a negative
+ * error code for a NULL handle. */
+int32_t qg_launches_per_eval(const qg_ctx *h);
 
 const char *qg_last_error(const qg_ctx *h);
 

@@ -547,11 +547,21 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   for (int b = 0; b < B; ++b) add_span(P.s2, I[b].ctg_ntc * I[b].n_mg * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
   for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
+  // generator blocks (stage 5)
+  int gen_slot = 0;
+  auto gen_span = [&](Spans &S, int per, int b) {
+    I[b].gen_first = S.n_blocks;
+    I[b].gen_nb = per * I[b].T;
+    I[b].gen_slot0 = gen_slot;
+    gen_slot += I[b].gen_nb;
+    add_span(S, per, I[b].T, b, R_GEN);
+  };
   if (P.sp) add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
   else
     for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gb + 1, NTHR / 32), I[b].T, b, R_DCA);
   for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
-  for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].G, NTHR), I[b].T, b, R_GEN);
+  for (int b = 0; b < B; ++b) gen_span(P.s5, ceil_div(I[b].G, NTHR), b);
+  P.n_gen_slots = gen_slot;
   // objective slots: the blocks of s1 and s2 in launch order, renumbered instance-major so that each
   // instance's slots are one contiguous range; then one slot per s5 block
   std::vector<int> owner;
@@ -788,7 +798,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   d.qside = qs;
   Dc *op;
   d.n_obj12 = (int)slot_map.size();
-  d.n_obj_slots = d.n_obj12 + P.s5.n_blocks;
+  d.n_obj_slots = d.n_obj12 + P.n_gen_slots;
   if ((rc = dalloc(h, &op, (size_t)d.n_obj_slots * N_TERMS))) return rc;
   d.objp = op;
   int *si;
@@ -1258,6 +1268,13 @@ int qg_phase_times(qg_ctx *h, float *ms, int32_t cap) {
 
 const char *qg_last_error(const qg_ctx *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int qg_version(void) { return 200; }
+int32_t qg_launches_per_eval(const qg_ctx *h) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  const Plan &P = h->plan;
+  if (!P.sp) return 5;
+  return 5 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0);
+}
+
+int qg_version(void) { return 201; }
 
 }  // extern "C"

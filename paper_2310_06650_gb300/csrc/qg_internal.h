@@ -44,6 +44,8 @@ struct Inst {
   double hours;          // sum of dt
   double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
   int obj_lo, obj_n;     // this instance's stage-1/2 objective slots
+  int gen_first, gen_nb; // its generator blocks: first block in their launch, count
+  int gen_slot0;         // first reduction slot of those blocks (after the stage-1/2 slots)
 };
 
 // Roles of the blocks of the fused stage kernels.  R_DCF / R_DCA are the dense DC products;
@@ -171,6 +173,7 @@ struct Plan {
   long long n_x;
   int maxT;
   int maxTB;  // largest period chunk of a contingency block (sizes its shared memory)
+  int n_gen_slots;  // objective reduction slots of the generator blocks
   // sparse DC mode (instance 0 only): grids of the solve kernels
   int sp;
   int sp_inj_blocks;   // right-hand-side blocks of k_sp_inj (T more compute the mean injection)

@@ -6,15 +6,19 @@
 // mixes independent work and serves uneven batched instances:
 //   s1  branch flows (pi model) + thermal penalty | zonal reserve sums |
 //       base DC flows f = PTDF_G p_G - PTDF load - mean(p_inj) PTDF 1
+//       (sparse DC mode: flows from the angles of the forward solve)
 //   s2  bus P/Q balance by warp-segmented CSR reduction + soft-abs penalty |
 //       contingency flows F = f_m + L[m,k] f_k, overload penalty and both
 //       backward sums (the SMW rank-1 correction of Eq. rank_correct in flow space)
 //   s3  dz/df summed over contingency tiles; branch-end adjoints (chain rule)
 //   s4  bus gather of branch-end adjoints (warp-segmented) -> g_v, g_theta
 //       [+ fused Adam] | adjoint DC products PTDF_G^T dz/df (Eq. 2nd_lin_sys)
+//       (sparse DC mode: the right-hand side of the adjoint solve)
 //   s5  generator gradients incl. the slack-corrected injection adjoint
 //       eta - mean(eta) (Eq. correction) [+ fused Adam]; the last block reduces
 //       the objective in FP64 and advances the Adam step counter.
+// Sparse DC mode: k_sp_inj, k_sp_fwd, k_sp_tail, k_sp_back solve Yhat theta = b
+// through the sparse factor with a dense tail, before s1 and after s4.
 // No floating-point atomics: every sum has a fixed order, so repeated
 // evaluations are bitwise identical.
 #include <cuda_bf16.h>
@@ -864,16 +868,15 @@ __device__ AdamCoef<Real> adam_coef(const Dev<Real, Dc> &d) {
 }
 
 template <typename Real, typename Dc, bool ADAM>
-__device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x) {
-  AdamCoef<Real> ac{};
-  if (ADAM) ac = adam_coef(d);
+__device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x,
+                       const AdamCoef<Real> &ac) {
   const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
   const bool on = pk < I.n_adj_pack;
   const int e = I.adj0 + (on ? pk : 0) * PACK + (threadIdx.x & 31);
   // static CSR entries first, then wait for stage 3's branch-end adjoints
   const int code = d.adj_code[e], row = on ? d.adj_row[e] : -1;
   pdl_wait();
-  if (!on) return;  // whole warp
+  if (!on) return;  // whole warp (the caller's block-wide steps come before this role)
   const int kind = code & 3;
   Real gv = 0, gth = 0;
   const long long tm = I.tm0 + (long long)t * I.M + (code >> 2);
@@ -896,74 +899,6 @@ __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Re
       d.g[kv] = gv;
       d.g[kth] = gth;
     }
-  }
-}
-
-// Adjoint DC products (Eq. 2nd_lin_sys at the generator buses): one warp per output,
-//   eta[t, gb] = sum_m dz/df[t,m] PTDF[m, gb]       (gb < Gb),
-//   eta[t, Gb] = sum_m dz/df[t,m] (PTDF 1)[m]        (n times the mean of eta, Eq. correction),
-// lanes striding over the branches, then a fixed-order shuffle reduction.
-template <typename Real, typename Dc>
-__device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
-  const int o = sub * (NTHR / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (o > I.Gb) return;
-  const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
-  const Dc *col = o < I.Gb ? d.ptdfgT + I.pg0 + (long long)o * I.M : d.rsum + I.br0;
-  Dc a0 = DcOps<Dc>::zero(), a1 = a0, a2 = a0, a3 = a0;
-  int m = lane;
-  for (; m + 96 < I.M; m += 128) {
-    DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
-    DcOps<Dc>::mac(a1, col[m + 32], DcOps<Dc>::from_real(gf[m + 32]));
-    DcOps<Dc>::mac(a2, col[m + 64], DcOps<Dc>::from_real(gf[m + 64]));
-    DcOps<Dc>::mac(a3, col[m + 96], DcOps<Dc>::from_real(gf[m + 96]));
-  }
-  for (; m < I.M; m += 32) DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
-  Dc acc = DcOps<Dc>::add(DcOps<Dc>::add(a0, a1), DcOps<Dc>::add(a2, a3));
-#pragma unroll
-  for (int k = 16; k > 0; k >>= 1) acc = DcOps<Dc>::add(acc, DcOps<Dc>::shfl_down(acc, k));
-  if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + o] = acc;
-}
-
-// Right-hand side of the adjoint solve in the sparse mode (Eq. 2nd_lin_sys): w = E_hat^T Y_x dz/df
-// at 32 positions x 8 periods per block, w_i = sum over incident branches of +-y_j dz/df_j (+ at
-// the from-end); plus per-chunk partial sums of z1 . w = 1^T eta (n times the mean of eta, Eq.
-// correction), finished in fixed order by the adjoint gather.
-template <typename Real, typename Dc>
-__device__ void s4_sdca(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub) {
-  const int t = tc * DCF_TC + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  const int pos = sub * 32 + lane;
-  const bool on = t < I.T && pos < d.nr;
-  const int q0 = on ? d.inc_ptr[pos] : 0, q1 = on ? d.inc_ptr[pos + 1] : 0;
-  const Dc z1 = on ? d.z1[pos] : DcOps<Dc>::zero();
-  pdl_wait();
-  Dc w = DcOps<Dc>::zero();
-  if (on) {
-    const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
-    for (int q = q0; q < q1; ++q) {
-      const int c = d.inc_code[q], j = c >> 1;
-      const Real g = (c & 1) ? -gf[j] : gf[j];
-      DcOps<Dc>::mac(w, d.ydc[I.br0 + j], DcOps<Dc>::from_real(g));
-    }
-    d.sp_rhs[(long long)pos * I.T + t] = w;
-  }
-  Dc s = DcOps<Dc>::mul(z1, w);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s = DcOps<Dc>::add(s, DcOps<Dc>::shfl_down(s, o));
-  if (lane == 0 && t < I.T) d.sp_part[(long long)sub * I.T + t] = s;
-}
-
-template <typename Real, typename Dc, bool ADAM>
-__global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, Dc> d,
-                                             const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
-                                             Real *__restrict__ x) {
-  const Where w = locate(S);
-  const Inst &I = tab.I[w.inst];
-  if (w.role == R_BUS) s4_bus<Real, Dc, ADAM>(d, I, w.t, w.sub, x);
-  else if (w.role == R_SDCA) s4_sdca(d, I, w.t, w.sub);
-  else {
-    pdl_wait();
-    s4_dca(d, I, w.t, w.sub);
   }
 }
 
@@ -995,16 +930,17 @@ __device__ void block_sum_terms(Dc (&a)[N_TERMS]) {
     }
 }
 
-// Objective reduction, level 1, run by every stage-5 block: its own terms plus an equal share of
-// its instance's stage-1/2 block slots (instance-major, so a share is a contiguous range) go to
-// the block's stage-5 slot.  The stage-1/2 slots are complete: stage 5 waits on stage 4, which
-// waited on stages 3, 2 and 1.
+// Objective reduction, level 1, run by every generator block (stage 5 in the sparse mode, the
+// generator role of stage 4 otherwise): its own terms plus an equal share of its instance's
+// stage-1/2 block slots (instance-major, so a share is a contiguous range) go to the block's
+// reduction slot.  The stage-1/2 slots are complete: the generator blocks run after stage 3,
+// which waited on stages 2 and 1.
 template <typename Real, typename Dc>
-__device__ void reduce_share(const Dev<Real, Dc> &d, const Inst &I, const Span &sp, Obj3<Dc> own) {
-  const int nb = sp.per_t * sp.nt, r = blockIdx.x - sp.first;
+__device__ void reduce_share(const Dev<Real, Dc> &d, const Inst &I, int r, Obj3<Dc> own) {
+  const int nb = I.gen_nb;
   const int chunk = (I.obj_n + nb - 1) / nb;
   const int lo = I.obj_lo + min(I.obj_n, r * chunk), hi = I.obj_lo + min(I.obj_n, (r + 1) * chunk);
-  const int slot = d.n_obj12 + blockIdx.x;
+  const int slot = d.n_obj12 + I.gen_slot0 + r;
   write_obj(d.objp, slot, own);
   Dc a[N_TERMS];
 #pragma unroll
@@ -1020,20 +956,20 @@ __device__ void reduce_share(const Dev<Real, Dc> &d, const Inst &I, const Span &
   }
 }
 
-// Objective reduction, level 2, run by the last block of stage 5: per instance, the stage-5 slots
-// of its blocks in fixed order, plus the closed-form soft-ReLU floor of the contingency term.
+// Objective reduction, level 2, run by the last block of the launch: per instance, the reduction
+// slots of its generator blocks in fixed order, plus the closed-form soft-ReLU floor of the
+// contingency term.
 template <typename Real, typename Dc>
-__device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab, const Spans &S) {
+__device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
   for (int b = 0; b < tab.n_inst; ++b) {
-    const Span &sp = S.s[b];
-    const int nb = sp.per_t * sp.nt;
+    const Inst &I = tab.I[b];
     Dc a[N_TERMS];
 #pragma unroll
     for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
-    for (int j = threadIdx.x; j < nb; j += NTHR)
+    for (int j = threadIdx.x; j < I.gen_nb; j += NTHR)
 #pragma unroll
       for (int k = 0; k < N_TERMS; ++k)
-        a[k] = DcOps<Dc>::add(a[k], d.objp[(long long)(d.n_obj12 + sp.first + j) * N_TERMS + k]);
+        a[k] = DcOps<Dc>::add(a[k], d.objp[(long long)(d.n_obj12 + I.gen_slot0 + j) * N_TERMS + k]);
     block_sum_terms(a);
     if (threadIdx.x == 0) {
       double tot = 0.0;
@@ -1052,6 +988,126 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab, const S
   }
 }
 
+// Generator-level data of one (generator, period), loaded before the wait (no stage writes it).
+template <typename Real>
+struct GenIn {
+  int bus, zn, gb;
+  Real a, bl, cr, pmax, ramp, p, r;
+  long long kp, kq, kr;
+  Real am[3], av[3], lo[3], hi[3];  // Adam moments and box of p, q, r (fused Adam only)
+};
+
+template <typename Real, typename Dc, bool ADAM>
+__device__ GenIn<Real> gen_load(const Dev<Real, Dc> &d, const Inst &I, int t, int gl, const Real *x) {
+  GenIn<Real> g;
+  const int gg = I.gen0 + gl;
+  g.bus = d.gen_bus[gg];
+  g.zn = d.gen_zone[gg];
+  g.gb = d.gen_gb[gg];
+  g.a = d.gen_a[gg];
+  g.bl = d.gen_b[gg];
+  g.cr = d.gen_cr[gg];
+  g.pmax = d.gen_pmax[gg];
+  g.ramp = d.gen_ramp[gg];
+  g.kp = I.x0 + 2LL * I.T * I.n + (long long)t * I.G + gl;
+  g.kq = g.kp + (long long)I.T * I.G;
+  g.kr = g.kq + (long long)I.T * I.G;
+  g.p = x[g.kp];
+  g.r = x[g.kr];
+  if (ADAM) {
+    const long long k3[3] = {g.kp, g.kq, g.kr};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      g.am[c] = d.am[k3[c]];
+      g.av[c] = d.av[k3[c]];
+      g.lo[c] = d.lo[k3[c]];
+      g.hi[c] = d.hi[k3[c]];
+    }
+  }
+  return g;
+}
+
+// Generator terms of period t (cost, reserve cost, headroom, ramps; Eq. nlp_updated) and the
+// gradient wrt p, q, r, with the injection adjoint eta_gb - mean(eta) (Eqs. 2nd_lin_sys,
+// correction) at the generator's bus; [+ the projected Adam update of p, q, r].
+template <typename Real, typename Dc, bool ADAM>
+__device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl, const GenIn<Real> &g, Dc eta,
+                           const AdamCoef<Real> &ac, Obj3<Dc> &acc, Real *__restrict__ x) {
+  const Real dt = d.dt[I.tp0 + t];
+  const long long G = I.G;
+  const Real p = g.p, r = g.r;
+  const long long tb = I.tb0 + (long long)t * I.n;
+  Real gp = dt * (2 * g.a * p + g.bl) - d.dP[tb + g.bus] + DcOps<Dc>::to_real(eta);
+  const Real gq = -d.dQ[tb + g.bus];
+  Real gr = dt * g.cr - d.dZ[I.tz0 + (long long)t * I.Z + g.zn];
+  acc.v[0] = DcOps<Dc>::from_real(dt * (g.a * p * p + g.bl * p + g.cr * r));
+  const Real wr = d.rho * d.beta;
+  Real val, der;
+  soft_relu(p + r - g.pmax, d.eps, val, der);
+  acc.v[1] = DcOps<Dc>::from_real(wr * val);
+  gp += wr * der;
+  gr += wr * der;
+  const long long ko = I.tg0 + (long long)t * G + gl;
+  if (t >= 1) {  // ramp terms of period t
+    const Real pp = ADAM ? d.pold[ko - G] : x[g.kp - G];
+    const Real lim = g.ramp * dt;
+    Real v1, d1, v2, d2;
+    soft_relu(p - pp - lim, d.eps, v1, d1);
+    soft_relu(pp - p - lim, d.eps, v2, d2);
+    acc.v[2] = DcOps<Dc>::from_real(wr * (v1 + v2));
+    gp += wr * (d1 - d2);
+  }
+  if (t + 1 < I.T) {  // ramp terms of period t + 1 that involve p_t
+    const Real pn = ADAM ? d.pold[ko + G] : x[g.kp + G];
+    const Real lim = g.ramp * d.dt[I.tp0 + t + 1];
+    Real v1, d1, v2, d2;
+    soft_relu(pn - p - lim, d.eps, v1, d1);
+    soft_relu(p - pn - lim, d.eps, v2, d2);
+    gp += wr * (d2 - d1);
+  }
+  if (ADAM) {
+    const long long k3[3] = {g.kp, g.kq, g.kr};
+    const Real g3[3] = {gp, gq, gr};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Real xk = c == 0 ? g.p : (c == 2 ? g.r : x[g.kq]), mk = g.am[c], vk = g.av[c];
+      adam_update(xk, g3[c], mk, vk, g.lo[c], g.hi[c], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps, d.paper_eps);
+      x[k3[c]] = xk;
+      d.am[k3[c]] = mk;
+      d.av[k3[c]] = vk;
+    }
+  } else {
+    d.g[g.kp] = gp;
+    d.g[g.kq] = gq;
+    d.g[g.kr] = gr;
+  }
+}
+
+// End of an evaluation: the last block of the launch to finish (ticket) reduces the objective and
+// advances the Adam step counter.  Every block of the launch calls this (all its threads), after
+// its last read of the step counter.
+template <typename Real, typename Dc, bool ADAM>
+__device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(d.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  final_reduce(d, tab);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *d.ticket = 0;
+    if (ADAM) *d.step += 1;
+    __threadfence();
+  }
+}
+
+// Stage 5: generators of one period, with eta from stage 4's adjoint DC products (dense DC mode) or
+// from the adjoint solve (sparse mode); the last block reduces the objective.
 template <typename Real, typename Dc, bool ADAM>
 __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
@@ -1064,78 +1120,89 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
   if (ADAM) ac = adam_coef(d);
   const int gl = w.sub * NTHR + threadIdx.x;
   const bool on = gl < I.G;
-  // generator data and this period's dispatch (not written by the earlier stages) before waiting
-  const int gg = I.gen0 + (on ? gl : 0);
-  const int bus = d.gen_bus[gg], zn = d.gen_zone[gg], gb = d.gen_gb[gg];
-  const Real a = d.gen_a[gg], bl = d.gen_b[gg], cr = d.gen_cr[gg], pmax = d.gen_pmax[gg], ramp = d.gen_ramp[gg];
-  const long long kp = I.x0 + 2LL * I.T * I.n + (long long)t * I.G + (on ? gl : 0);
-  const long long kq = kp + (long long)I.T * I.G, kr = kq + (long long)I.T * I.G;
-  const Real p = x[kp], r = x[kr];
+  const GenIn<Real> g = gen_load<Real, Dc, ADAM>(d, I, t, on ? gl : 0, x);
   pdl_wait();
   if (on) {
-    const Real dt = d.dt[I.tp0 + t];
-    const long long G = I.G;
-    // injection adjoint at the generator's bus: eta_gb - mean(eta)   (Eqs. 2nd_lin_sys, correction)
-    const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gb + 1);  // written by stage 4
-    const Dc eta = DcOps<Dc>::add(et[gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gb], DcOps<Dc>::inv_n(I))));
-    const long long tb = I.tb0 + (long long)t * I.n;
-    Real gp = dt * (2 * a * p + bl) - d.dP[tb + bus] + DcOps<Dc>::to_real(eta);
-    const Real gq = -d.dQ[tb + bus];
-    Real gr = dt * cr - d.dZ[I.tz0 + (long long)t * I.Z + zn];
-    acc.v[0] = DcOps<Dc>::from_real(dt * (a * p * p + bl * p + cr * r));
-    const Real wr = d.rho * d.beta;
-    Real val, der;
-    soft_relu(p + r - pmax, d.eps, val, der);
-    acc.v[1] = DcOps<Dc>::from_real(wr * val);
-    gp += wr * der;
-    gr += wr * der;
-    const long long ko = I.tg0 + (long long)t * G + gl;
-    if (t >= 1) {  // ramp terms of period t
-      const Real pp = ADAM ? d.pold[ko - G] : x[kp - G];
-      const Real lim = ramp * dt;
-      Real v1, d1, v2, d2;
-      soft_relu(p - pp - lim, d.eps, v1, d1);
-      soft_relu(pp - p - lim, d.eps, v2, d2);
-      acc.v[2] = DcOps<Dc>::from_real(wr * (v1 + v2));
-      gp += wr * (d1 - d2);
-    }
-    if (t + 1 < I.T) {  // ramp terms of period t + 1 that involve p_t
-      const Real pn = ADAM ? d.pold[ko + G] : x[kp + G];
-      const Real lim = ramp * d.dt[I.tp0 + t + 1];
-      Real v1, d1, v2, d2;
-      soft_relu(pn - p - lim, d.eps, v1, d1);
-      soft_relu(p - pn - lim, d.eps, v2, d2);
-      gp += wr * (d2 - d1);
-    }
-    if (ADAM) {
-      adam_update(x[kp], gp, d.am[kp], d.av[kp], d.lo[kp], d.hi[kp], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
-                  d.paper_eps);
-      adam_update(x[kq], gq, d.am[kq], d.av[kq], d.lo[kq], d.hi[kq], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
-                  d.paper_eps);
-      adam_update(x[kr], gr, d.am[kr], d.av[kr], d.lo[kr], d.hi[kr], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
-                  d.paper_eps);
-    } else {
-      d.g[kp] = gp;
-      d.g[kq] = gq;
-      d.g[kr] = gr;
-    }
+    const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gb + 1);  // written by the adjoint solve
+    const Dc eta = DcOps<Dc>::add(et[g.gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gb], DcOps<Dc>::inv_n(I))));
+    gen_update<Real, Dc, ADAM>(d, I, t, gl, g, eta, ac, acc, x);
   }
-  reduce_share(d, I, S.s[w.inst], acc);
-  // the last block to finish reduces the objective and advances the step counter
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(d.ticket, 1u) == gridDim.x - 1;
+  reduce_share(d, I, blockIdx.x - I.gen_first, acc);
+  finish_eval<Real, Dc, ADAM>(d, tab);
+}
+
+// Right-hand side of the adjoint solve in the sparse mode (Eq. 2nd_lin_sys): w = E_hat^T Y_x dz/df
+// at 32 positions x 8 periods per block, w_i = sum over incident branches of +-y_j dz/df_j (+ at
+// the from-end); plus per-chunk partial sums of z1 . w = 1^T eta (n times the mean of eta, Eq.
+// correction), finished in fixed order by the adjoint gather.
+template <typename Real, typename Dc>
+__device__ void s4_sdca(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub) {
+  const int t = tc * DCF_TC + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int pos = sub * 32 + lane;
+  const bool on = t < I.T && pos < d.nr;
+  const int q0 = on ? d.inc_ptr[pos] : 0, q1 = on ? d.inc_ptr[pos + 1] : 0;
+  const Dc z1 = on ? d.z1[pos] : DcOps<Dc>::zero();
+  pdl_wait();
+  Dc w = DcOps<Dc>::zero();
+  if (on) {
+    const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
+    for (int q = q0; q < q1; ++q) {
+      const int c = d.inc_code[q], j = c >> 1;
+      const Real g = (c & 1) ? -gf[j] : gf[j];
+      DcOps<Dc>::mac(w, d.ydc[I.br0 + j], DcOps<Dc>::from_real(g));
+    }
+    d.sp_rhs[(long long)pos * I.T + t] = w;
   }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  final_reduce(d, tab, S);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    *d.ticket = 0;
-    if (ADAM) *d.step += 1;
-    __threadfence();
+  Dc s = DcOps<Dc>::mul(z1, w);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = DcOps<Dc>::add(s, DcOps<Dc>::shfl_down(s, o));
+  if (lane == 0 && t < I.T) d.sp_part[(long long)sub * I.T + t] = s;
+}
+
+// Adjoint DC products (Eq. 2nd_lin_sys at the generator buses): one warp per output,
+//   eta[t, gb] = sum_m dz/df[t,m] PTDF[m, gb]       (gb < Gb),
+//   eta[t, Gb] = sum_m dz/df[t,m] (PTDF 1)[m]        (n times the mean of eta, Eq. correction),
+// lanes striding over the branches, then a fixed-order shuffle reduction.
+template <typename Real, typename Dc>
+__device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
+  const int o = sub * (NTHR / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (o > I.Gb) return;
+  const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
+  const Dc *col = o < I.Gb ? d.ptdfgT + I.pg0 + (long long)o * I.M : d.rsum + I.br0;
+  Dc a0 = DcOps<Dc>::zero(), a1 = a0, a2 = a0, a3 = a0;
+  int m = lane;
+  for (; m + 96 < I.M; m += 128) {
+    DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
+    DcOps<Dc>::mac(a1, col[m + 32], DcOps<Dc>::from_real(gf[m + 32]));
+    DcOps<Dc>::mac(a2, col[m + 64], DcOps<Dc>::from_real(gf[m + 64]));
+    DcOps<Dc>::mac(a3, col[m + 96], DcOps<Dc>::from_real(gf[m + 96]));
+  }
+  for (; m < I.M; m += 32) DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
+  Dc acc = DcOps<Dc>::add(DcOps<Dc>::add(a0, a1), DcOps<Dc>::add(a2, a3));
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) acc = DcOps<Dc>::add(acc, DcOps<Dc>::shfl_down(acc, k));
+  if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + o] = acc;
+}
+
+// Stage 4: bus gather of the branch-end adjoints (-> g_v, g_theta) [+ Adam on v, theta]; the
+// adjoint DC products at the generator buses (dense DC mode) or the right-hand side of the
+// adjoint solve (sparse mode).
+template <typename Real, typename Dc, bool ADAM>
+__global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, Dc> d,
+                                             const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
+                                             Real *__restrict__ x) {
+  const Where w = locate(S);
+  const Inst &I = tab.I[w.inst];
+  if (w.role == R_BUS) {
+    AdamCoef<Real> ac{};
+    if (ADAM) ac = adam_coef(d);
+    s4_bus<Real, Dc, ADAM>(d, I, w.t, w.sub, x, ac);
+  } else if (w.role == R_SDCA) {
+    s4_sdca(d, I, w.t, w.sub);
+  } else {
+    pdl_wait();
+    s4_dca(d, I, w.t, w.sub);
   }
 }
 

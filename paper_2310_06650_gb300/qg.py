@@ -85,6 +85,7 @@ def _load():
         "qg_phase_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int32]),
         "qg_last_error": (C.c_char_p, [vp]),
         "qg_version": (C.c_int, []),
+        "qg_launches_per_eval": (C.c_int32, [vp]),
         "qg_mlp_create": (C.c_int, [C.POINTER(vp), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64]),
         "qg_mlp_destroy": (None, [vp]),
         "qg_mlp_num_params": (C.c_int64, [vp]),
@@ -106,7 +107,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_eval_grad_noalloc", "qg_adam_step", "qg_solve", "qg_breakdown",
-            "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_last_error", "qg_version",
+            "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_launches_per_eval",
+            "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
 PHASES = ("s1", "s2", "s3", "s4", "s5", "adam")
@@ -272,6 +274,13 @@ def qg_last_error(h: Optional[int] = None) -> str:
 
 def qg_version() -> int:
     return int(_lib.qg_version())
+
+
+def qg_launches_per_eval(h: int) -> int:
+    n = int(_lib.qg_launches_per_eval(h))
+    if n < 0:
+        _check(n, h)
+    return n
 
 
 class Solver:
