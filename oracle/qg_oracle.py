@@ -75,36 +75,62 @@ def soft_relu_grad(x, eps):
 # variable layout
 # ------------------------------------------------------------------------------------------
 
+def _n_xf(case):
+    return int(getattr(case, "n_xf", 0))
+
+
 def unpack(case, x):
-    """x = [v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G)], period-major rows."""
-    T, n, G = case.T, case.n_bus, case.n_gen
+    """x = [v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G) | tau (T x X) | phi (T x X)],
+    period-major rows; X transformers (tau, phi blocks absent when X = 0)."""
+    T, n, G, X = case.T, case.n_bus, case.n_gen, _n_xf(case)
     x = np.asarray(x, dtype=np.float64)
     o = 0
     v = x[o:o + T * n].reshape(T, n); o += T * n
     th = x[o:o + T * n].reshape(T, n); o += T * n
     p = x[o:o + T * G].reshape(T, G); o += T * G
     q = x[o:o + T * G].reshape(T, G); o += T * G
-    r = x[o:o + T * G].reshape(T, G)
-    return v, th, p, q, r
+    r = x[o:o + T * G].reshape(T, G); o += T * G
+    if X == 0:
+        return v, th, p, q, r
+    tau = x[o:o + T * X].reshape(T, X); o += T * X
+    phi = x[o:o + T * X].reshape(T, X)
+    return v, th, p, q, r, tau, phi
 
 
-def pack(v, th, p, q, r):
-    return np.concatenate([np.ravel(v), np.ravel(th), np.ravel(p), np.ravel(q), np.ravel(r)])
+def pack(v, th, p, q, r, tau=None, phi=None):
+    parts = [np.ravel(v), np.ravel(th), np.ravel(p), np.ravel(q), np.ravel(r)]
+    if tau is not None:
+        parts += [np.ravel(tau), np.ravel(phi)]
+    return np.concatenate(parts)
 
 
 def box(case):
     """Clip box B of Alg. 3 (clip step): v in [vmin, vmax], theta_ref = 0, other theta free,
-    p in [pmin, pmax], q in [qmin, qmax], r in [0, pmax]."""
-    T, n = case.T, case.n_bus
+    p in [pmin, pmax], q in [qmin, qmax], r in [0, pmax], tau and phi in their ranges."""
+    T, n, X = case.T, case.n_bus, _n_xf(case)
     lo_th = np.full((T, n), -np.inf)
     hi_th = np.full((T, n), np.inf)
     lo_th[:, case.ref_bus] = 0.0
     hi_th[:, case.ref_bus] = 0.0
+    xl = (np.tile(case.tau_min, (T, 1)), np.tile(case.phi_min, (T, 1))) if X else (None, None)
+    xh = (np.tile(case.tau_max, (T, 1)), np.tile(case.phi_max, (T, 1))) if X else (None, None)
     lo = pack(np.tile(case.vmin, (T, 1)), lo_th, np.tile(case.pmin, (T, 1)), np.tile(case.qmin, (T, 1)),
-              np.zeros((T, case.n_gen)))
+              np.zeros((T, case.n_gen)), *xl)
     hi = pack(np.tile(case.vmax, (T, 1)), hi_th, np.tile(case.pmax, (T, 1)), np.tile(case.qmax, (T, 1)),
-              np.tile(case.pmax, (T, 1)))
+              np.tile(case.pmax, (T, 1)), *xh)
     return lo, hi
+
+
+def branch_tau_phi(case, tau, phi):
+    """(T, M) tap ratio and phase shift of every branch: the transformer variables on transformer
+    branches, tau = 1 and phi = 0 on lines."""
+    T, M = case.T, case.n_branch
+    tb = np.ones((T, M))
+    pb = np.zeros((T, M))
+    if tau is not None:
+        tb[:, case.xf_branch] = tau
+        pb[:, case.xf_branch] = phi
+    return tb, pb
 
 
 # ------------------------------------------------------------------------------------------
@@ -117,42 +143,51 @@ def series_admittance(case):
     return case.br_r / den, -case.br_x / den
 
 
-def ac_flows(case, v, th):
-    """Pi-model flows at both ends of every branch, shape (T, M) each.
+def ac_flows(case, v, th, tau=None, phi=None):
+    """Pi-model flows at both ends of every branch, shape (T, M) each; an ideal transformer of tap
+    ratio tau and phase shift phi sits at the "fr" end (tau = 1, phi = 0 on lines):
 
-    p_fr = g v_f^2 + (-g cos d - b sin d) v_f v_o
-    q_fr = -(b + b_ch/2) v_f^2 + (b cos d - g sin d) v_f v_o
-    p_to = g v_o^2 + (-g cos d + b sin d) v_f v_o
-    q_to = -(b + b_ch/2) v_o^2 + (b cos d + g sin d) v_f v_o,   d = theta_f - theta_o.
+    p_fr = g v_f^2 / tau^2 + (-g cos d - b sin d) v_f v_o / tau
+    q_fr = -(b + b_ch/2) v_f^2 / tau^2 + (b cos d - g sin d) v_f v_o / tau
+    p_to = g v_o^2 + (-g cos d + b sin d) v_f v_o / tau
+    q_to = -(b + b_ch/2) v_o^2 + (b cos d + g sin d) v_f v_o / tau,   d = theta_f - theta_o - phi.
     """
     g, b = series_admittance(case)
     bch = case.br_b
     f, o = case.br_from, case.br_to
+    tb, pb = branch_tau_phi(case, tau, phi)
     vf, vo = v[:, f], v[:, o]
-    d = th[:, f] - th[:, o]
+    d = th[:, f] - th[:, o] - pb
     c, s = np.cos(d), np.sin(d)
-    vv = vf * vo
-    pf = g * vf ** 2 + (-g * c - b * s) * vv
-    qf = -(b + bch / 2) * vf ** 2 + (b * c - g * s) * vv
+    vv = vf * vo / tb
+    vf2 = vf ** 2 / tb ** 2
+    pf = g * vf2 + (-g * c - b * s) * vv
+    qf = -(b + bch / 2) * vf2 + (b * c - g * s) * vv
     pt = g * vo ** 2 + (-g * c + b * s) * vv
     qt = -(b + bch / 2) * vo ** 2 + (b * c + g * s) * vv
     return pf, qf, pt, qt
 
 
-def ac_flow_partials(case, v, th):
-    """Partial derivatives of (pf, qf, pt, qt) with respect to (v_f, v_o, delta)."""
+def ac_flow_partials(case, v, th, tau=None, phi=None):
+    """Partial derivatives of (pf, qf, pt, qt) with respect to (v_f, v_o, delta, tau);
+    d/dtheta_f = d/ddelta, d/dtheta_o = d/dphi = -d/ddelta."""
     g, b = series_admittance(case)
     bch = case.br_b
     f, o = case.br_from, case.br_to
+    tb, pb = branch_tau_phi(case, tau, phi)
     vf, vo = v[:, f], v[:, o]
-    d = th[:, f] - th[:, o]
+    d = th[:, f] - th[:, o] - pb
     c, s = np.cos(d), np.sin(d)
-    vv = vf * vo
+    vv = vf * vo / tb
     out = {
-        "pf": (2 * g * vf + (-g * c - b * s) * vo, (-g * c - b * s) * vf, (g * s - b * c) * vv),
-        "qf": (-2 * (b + bch / 2) * vf + (b * c - g * s) * vo, (b * c - g * s) * vf, (-b * s - g * c) * vv),
-        "pt": ((-g * c + b * s) * vo, 2 * g * vo + (-g * c + b * s) * vf, (g * s + b * c) * vv),
-        "qt": ((b * c + g * s) * vo, -2 * (b + bch / 2) * vo + (b * c + g * s) * vf, (-b * s + g * c) * vv),
+        "pf": (2 * g * vf / tb ** 2 + (-g * c - b * s) * vo / tb, (-g * c - b * s) * vf / tb, (g * s - b * c) * vv,
+               -2 * g * vf ** 2 / tb ** 3 - (-g * c - b * s) * vv / tb),
+        "qf": (-2 * (b + bch / 2) * vf / tb ** 2 + (b * c - g * s) * vo / tb, (b * c - g * s) * vf / tb,
+               (-b * s - g * c) * vv, 2 * (b + bch / 2) * vf ** 2 / tb ** 3 - (b * c - g * s) * vv / tb),
+        "pt": ((-g * c + b * s) * vo / tb, 2 * g * vo + (-g * c + b * s) * vf / tb, (g * s + b * c) * vv,
+               -(-g * c + b * s) * vv / tb),
+        "qt": ((b * c + g * s) * vo / tb, -2 * (b + bch / 2) * vo + (b * c + g * s) * vf / tb, (-b * s + g * c) * vv,
+               -(b * c + g * s) * vv / tb),
     }
     return out
 
@@ -246,16 +281,28 @@ def dc_injections(case, p):
     return inj, pbar
 
 
-def dc_base_flows(case, net: DCNet, pbar):
-    """Eq. Yb_solve / p_flow with b_t = 0 (no phase shifters): theta_hat = Yhat^-1 pbar_hat,
-    f = Y_x E_hat theta_hat.  Returns theta (T, n) with theta_ref = 0 and f (T, M)."""
+def phase_shift_flows(case, net: DCNet, phi_b):
+    """b_jt = b^sr_j phi_jt = -y_j phi_jt (Sec. II-E contingency flow equation), (T, M); 0 on lines."""
+    return -net.y[None, :] * phi_b
+
+
+def dc_base_flows(case, net: DCNet, pbar, bflow=None):
+    """Eq. Yb_solve / p_flow: theta_hat = Yhat^-1 (pbar_hat - E_hat^T b_t).  Reading: the monitored
+    flow is the physical one of the contingency flow equation, p = Y_x E_hat theta_hat + b_t (Eq.
+    p_flow writes the first term only; with b_t = 0 they agree).  Returns theta (T, n) with
+    theta_ref = 0 and p (T, M)."""
+    rhs = pbar.copy()
+    if bflow is not None:
+        rhs -= (bflow @ net.E) if not net.sparse else (net.E.T @ bflow.T).T
     if net.sparse:
-        th_hat = net.solve(pbar[:, net.keep].T).T
+        th_hat = net.solve(rhs[:, net.keep].T).T
     else:
-        th_hat = np.linalg.solve(net.Yhat, pbar[:, net.keep].T).T
+        th_hat = np.linalg.solve(net.Yhat, rhs[:, net.keep].T).T
     th = np.zeros_like(pbar)
     th[:, net.keep] = th_hat
     f = (net.E @ th.T).T * net.y[None, :] if net.sparse else (th @ net.E.T) * net.y[None, :]
+    if bflow is not None:
+        f = f + bflow
     return th, f
 
 
@@ -263,21 +310,26 @@ def dc_base_flows(case, net: DCNet, pbar):
 # contingency penalty and its gradient (Sec. II-E, Alg. 2 with every outage and zeta = 0)
 # ------------------------------------------------------------------------------------------
 
-def _ctg_period_smw(case, net: DCNet, th_hat_b, qmax2, dt, U, den):
+def _ctg_period_smw(case, net: DCNet, th_hat_b, qmax2, dt, U, den, b_t=None):
     """One period, all outages, via the paper's rank-1 correction in angle space.
 
     th_hat_b : [n-1] base-case reduced angles (Eq. Y_base).
     U        : [n-1, K] u_k = Yhat^-1 a_k with a_k the reduced incidence row of branch k.
     den      : [K] 1 - y_k a_k^T u_k  (the SMW denominator; reading: Yhat_k = Yhat - y_k a_k a_k^T).
-    Returns (z_tk [K], grad wrt p_inj [n] summed over k, dz/dqmax2 [M] summed over k).
+    b_t      : [M] phase-shift flows of the period (None: no phase shifters).  An outaged branch
+               loses its own b_k with u_on = 0, so c_tk = c_t + a_k b_k and, by SMW,
+               theta_tk = theta_tb + u_k (f_k + b_k) / den_k.
+    Returns (z_tk [K], grad wrt p_inj [n] summed over k, dz/dqmax2 [M] summed over k,
+    grad wrt b_t [M] summed over k).
     """
     K = case.K
     ks = case.ctg
     Eh = net.E[:, net.keep]
     y = net.y
-    fk = y[ks] * (Eh[ks] @ th_hat_b)                        # base flow on each outaged branch
-    TH = th_hat_b[:, None] + U * (fk / den)[None, :]         # Eq. rank_correct, one column per k
-    P = y[:, None] * (Eh @ TH)                               # Eq. p_flow, [M, K]
+    bt = np.zeros(case.n_branch) if b_t is None else b_t
+    fk = y[ks] * (Eh[ks] @ th_hat_b)                        # base angle flow on each outaged branch
+    TH = th_hat_b[:, None] + U * ((fk + bt[ks]) / den)[None, :]  # Eq. rank_correct, one column per k
+    P = y[:, None] * (Eh @ TH) + bt[:, None]                 # Eq. p_flow plus b_t, [M, K]
     P[ks, np.arange(K)] = 0.0                                # outaged branch carries nothing
     s = np.sqrt(P * P + qmax2[:, None])
     u = s - case.s_max_ctg[:, None]
@@ -298,11 +350,14 @@ def _ctg_period_smw(case, net: DCNet, th_hat_b, qmax2, dt, U, den):
     eta = np.zeros((case.n_bus, K))
     eta[net.keep] = H
     gin = (eta - eta.mean(axis=0, keepdims=True)).sum(axis=1)  # Eq. correction, summed over k
-    return z, gin, gq2
+    GB = D - Eh @ H                                          # Eq. 2nd_lin_sys_phase plus the direct b term
+    GB[ks, np.arange(K)] = 0.0                               # b_k does not enter contingency k
+    return z, gin, gq2, GB.sum(axis=1)
 
 
-def _ctg_period_brute(case, net: DCNet, pbar_t, qmax2, dt):
-    """One period, every outage re-solved on the outaged Laplacian (no SMW)."""
+def _ctg_period_brute(case, net: DCNet, pbar_t, qmax2, dt, b_t=None):
+    """One period, every outage re-solved on the outaged Laplacian (no SMW); the outaged branch
+    also loses its phase-shift flow."""
     if net.sparse:
         raise ValueError("brute mode takes small (dense) grids only")
     K = case.K
@@ -312,13 +367,17 @@ def _ctg_period_brute(case, net: DCNet, pbar_t, qmax2, dt):
     z = np.zeros(K)
     gin = np.zeros(n)
     gq2 = np.zeros(case.n_branch)
+    gb = np.zeros(case.n_branch)
+    bt = np.zeros(case.n_branch) if b_t is None else b_t
     w = dt * case.c_s * case.beta
     for kk, k in enumerate(case.ctg):
         yk = y.copy()
         yk[k] = 0.0
+        bk = bt.copy()
+        bk[k] = 0.0
         Yk = Eh.T @ (yk[:, None] * Eh)
-        thk = np.linalg.solve(Yk, pbar_t[net.keep])
-        P = yk * (Eh @ thk)
+        thk = np.linalg.solve(Yk, pbar_t[net.keep] - Eh.T @ bk)
+        P = yk * (Eh @ thk) + bk
         s = np.sqrt(P * P + qmax2)
         u = s - case.s_max_ctg
         pen = w * soft_relu(u, case.eps)
@@ -333,7 +392,10 @@ def _ctg_period_brute(case, net: DCNet, pbar_t, qmax2, dt):
         eta = np.zeros(n)
         eta[net.keep] = eta_h
         gin += eta - eta.mean()
-    return z, gin, gq2
+        gbk = d - Eh @ eta_h
+        gbk[k] = 0.0
+        gb += gbk
+    return z, gin, gq2, gb
 
 
 # ------------------------------------------------------------------------------------------
@@ -365,11 +427,15 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     """
     if eps is not None and eps != case.eps:
         case = dataclasses.replace(case, eps=eps)
-    T, n, G = case.T, case.n_bus, case.n_gen
+    T, n, G, X = case.T, case.n_bus, case.n_gen, _n_xf(case)
     eps_ = case.eps
     beta = case.beta
     dt = case.dt
-    v, th, p, q, r = unpack(case, x)
+    if X:
+        v, th, p, q, r, tau, phi = unpack(case, x)
+    else:
+        v, th, p, q, r = unpack(case, x)
+        tau = phi = None
     gv = np.zeros((T, n)); gth = np.zeros((T, n)); gp = np.zeros((T, G)); gq = np.zeros((T, G))
     gr = np.zeros((T, G))
     terms = {k: 0.0 for k in TERM_NAMES}
@@ -380,7 +446,7 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     gr += dt[:, None] * case.cost_r
 
     # --- AC flows and bus balance (Example 4)
-    pf, qf, pt, qt = ac_flows(case, v, th)
+    pf, qf, pt, qt = ac_flows(case, v, th, tau, phi)
     P, Q = bus_mismatch(case, pf, qf, pt, qt, p, q)
     wp = dt[:, None] * case.c_p * beta
     wq = dt[:, None] * case.c_q * beta
@@ -441,30 +507,34 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     if net is None:
         net = dc_network(case)
     _, pbar = dc_injections(case, p)
-    th_dc, fbase = dc_base_flows(case, net, pbar)
+    bflow = phase_shift_flows(case, net, branch_tau_phi(case, tau, phi)[1]) if X else None
+    th_dc, fbase = dc_base_flows(case, net, pbar, bflow)
     use_qf = qf * qf >= qt * qt           # reading: the q of the worse end, ties to "fr"
     qmax2 = np.where(use_qf, qf * qf, qt * qt)
     z_ctg = np.zeros((T, case.K))
     gin_all = np.zeros((T, n))
     gq2_all = np.zeros((T, case.n_branch))
+    gb_all = np.zeros((T, case.n_branch))
     if case.K > 0:
         U, den = outage_columns(case, net)                 # u_k [n-1, K], SMW denominators [K]
         plist = range(T) if periods is None else periods
         for t in plist:
+            bt = None if bflow is None else bflow[t]
             if mode == "brute":
-                z, gin, gq2 = _ctg_period_brute(case, net, pbar[t], qmax2[t], dt[t])
+                z, gin, gq2, gb = _ctg_period_brute(case, net, pbar[t], qmax2[t], dt[t], bt)
             else:
-                z, gin, gq2 = _ctg_period_smw(case, net, th_dc[t, net.keep], qmax2[t], dt[t], U, den)
+                z, gin, gq2, gb = _ctg_period_smw(case, net, th_dc[t, net.keep], qmax2[t], dt[t], U, den, bt)
             z_ctg[t] = z
             gin_all[t] = gin
             gq2_all[t] = gq2
+            gb_all[t] = gb
     terms["zctg"] = float(z_ctg.sum())
     gp += gin_all[:, case.gen_bus]
     g_qf += np.where(use_qf, 2 * qf * gq2_all, 0.0)
     g_qt += np.where(~use_qf, 2 * qt * gq2_all, 0.0)
 
-    # --- pull branch-end adjoints back to (v, theta) and gather per bus
-    part = ac_flow_partials(case, v, th)
+    # --- pull branch-end adjoints back to (v, theta, tau, phi) and gather per bus
+    part = ac_flow_partials(case, v, th, tau, phi)
     gvf = g_pf * part["pf"][0] + g_qf * part["qf"][0] + g_pt * part["pt"][0] + g_qt * part["qt"][0]
     gvo = g_pf * part["pf"][1] + g_qf * part["qf"][1] + g_pt * part["pt"][1] + g_qt * part["qt"][1]
     gd = g_pf * part["pf"][2] + g_qf * part["qf"][2] + g_pt * part["pt"][2] + g_qt * part["qt"][2]
@@ -473,8 +543,15 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     np.add.at(gth.T, f, gd.T)
     np.subtract.at(gth.T, o, gd.T)
 
+    gtau = gphi = None
+    if X:
+        gtb = g_pf * part["pf"][3] + g_qf * part["qf"][3] + g_pt * part["pt"][3] + g_qt * part["qt"][3]
+        xf = case.xf_branch
+        gtau = gtb[:, xf]
+        # phi enters delta = theta_f - theta_o - phi (AC) and b = -y phi (contingency DC flows)
+        gphi = -gd[:, xf] - net.y[xf][None, :] * gb_all[:, xf]
     obj = float(sum(terms.values()))
-    grad = pack(gv, gth, gp, gq, gr) if want_grad else None
+    grad = pack(gv, gth, gp, gq, gr, gtau, gphi) if want_grad else None
     return Result(obj=obj, grad=grad, terms=terms, z_ctg=z_ctg, g_inj=gin_all)
 
 

@@ -78,6 +78,12 @@ class Case:
     bus_zone: np.ndarray  # int32 [n]
     # contingencies
     ctg: np.ndarray  # int32 [K] outaged branch ids
+    # transformers (tap ratio tau, phase shift phi per period as variables; none by default)
+    xf_branch: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.int32))  # [X] branch ids
+    tau_min: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))  # [X]
+    tau_max: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    phi_min: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))  # [X] rad
+    phi_max: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     # penalty prices / smoothing (chosen readings; the paper does not state them)
     c_p: float = 1e4
     c_q: float = 1e4
@@ -92,13 +98,22 @@ class Case:
         return int(self.ctg.shape[0])
 
     @property
+    def n_xf(self) -> int:
+        return int(self.xf_branch.shape[0])
+
+    @property
     def n_x(self) -> int:
-        return self.T * (2 * self.n_bus + 3 * self.n_gen)
+        return self.T * (2 * self.n_bus + 3 * self.n_gen + 2 * self.n_xf)
 
     def offsets(self):
         """Start of the v, theta, p, q, r blocks in x (each block is T rows, period-major)."""
         n, G, T = self.n_bus, self.n_gen, self.T
         return (0, T * n, 2 * T * n, 2 * T * n + T * G, 2 * T * n + 2 * T * G)
+
+    def offsets_xf(self):
+        """Start of the tau and phi blocks (T x X each), after r."""
+        o = self.T * (2 * self.n_bus + 3 * self.n_gen)
+        return (o, o + self.T * self.n_xf)
 
     def flat_start(self, p: Optional[np.ndarray] = None, r: Optional[np.ndarray] = None) -> np.ndarray:
         """x with v = 1, theta = 0, q = 0 and the given dispatch (default: Pmax-proportional)."""
@@ -111,6 +126,8 @@ class Case:
         x[op:op + T * G] = np.asarray(p, dtype=np.float64).reshape(T * G)
         if r is not None:
             x[orr:orr + T * G] = np.asarray(r, dtype=np.float64).reshape(T * G)
+        otau, _ = self.offsets_xf()
+        x[otau:otau + T * self.n_xf] = 1.0  # tau = 1, phi = 0
         return x
 
 
@@ -406,6 +423,19 @@ def with_loads(case: Case, load_p: np.ndarray) -> Case:
     return dataclasses.replace(case, load_p=load_p, load_q=0.329 * load_p, reserve_req=reserve)
 
 
+def with_transformers(case: Case, frac: float = 0.15, seed: int = 0) -> Case:
+    """The same case with a random fraction of its branches turned into transformers: tap ratio
+    tau in [0.9, 1.1]; half of them also phase shifters with phi in [-0.3, 0.3] rad (phi fixed at 0
+    for the others).  tau = 1 and phi = 0 reproduce the original network."""
+    rng = np.random.default_rng(seed)
+    X = max(1, int(round(frac * case.n_branch)))
+    xf = np.sort(rng.choice(case.n_branch, size=X, replace=False)).astype(np.int32)
+    shifter = rng.random(X) < 0.5
+    return dataclasses.replace(case, name=case.name + "_xf", xf_branch=xf, tau_min=np.full(X, 0.9),
+                               tau_max=np.full(X, 1.1), phi_min=np.where(shifter, -0.3, 0.0),
+                               phi_max=np.where(shifter, 0.3, 0.0))
+
+
 def horizon_slice(case: Case, t0: int, t1: int) -> Case:
     """The same network over periods [t0, t1) of the horizon only."""
     return dataclasses.replace(case, T=t1 - t0, dt=case.dt[t0:t1].copy(), load_p=case.load_p[t0:t1].copy(),
@@ -424,7 +454,7 @@ def load_profiles(case: Case, count: int, seed: int) -> np.ndarray:
 
 
 def random_point(case: Case, seed: int, spread: float = 1.0) -> np.ndarray:
-    """A random x inside the box: v in [vmin, vmax], theta ~ N(0, 0.1 spread), p, q, r uniform."""
+    """A random x inside the box: v in [vmin, vmax], theta ~ N(0, 0.1 spread), p, q, r, tau, phi uniform."""
     rng = np.random.default_rng(seed)
     T, n, G = case.T, case.n_bus, case.n_gen
     v = rng.uniform(case.vmin, case.vmax, size=(T, n))
@@ -433,4 +463,8 @@ def random_point(case: Case, seed: int, spread: float = 1.0) -> np.ndarray:
     p = rng.uniform(case.pmin, case.pmax, size=(T, G))
     q = rng.uniform(case.qmin, case.qmax, size=(T, G))
     r = rng.uniform(0.0, 0.3, size=(T, G)) * case.pmax
-    return np.concatenate([v.ravel(), th.ravel(), p.ravel(), q.ravel(), r.ravel()])
+    parts = [v.ravel(), th.ravel(), p.ravel(), q.ravel(), r.ravel()]
+    if case.n_xf:
+        parts.append(rng.uniform(case.tau_min, case.tau_max, size=(T, case.n_xf)).ravel())
+        parts.append(rng.uniform(case.phi_min, case.phi_max, size=(T, case.n_xf)).ravel())
+    return np.concatenate(parts)

@@ -338,10 +338,10 @@ def test_planted_sign_error_in_flow_partial_is_caught(monkeypatch):
     x = synth.random_point(c, 1)
     orig = Q.ac_flow_partials
 
-    def bad(case, v, th):
-        out = orig(case, v, th)
-        a, b_, d = out["pt"]
-        out["pt"] = (a, b_, -d)
+    def bad(case, v, th, tau=None, phi=None):
+        out = orig(case, v, th, tau, phi)
+        a, b_, d, e = out["pt"]
+        out["pt"] = (a, b_, -d, e)
         return out
     monkeypatch.setattr(Q, "ac_flow_partials", bad)
     assert _fd_fails(c, x)
@@ -352,10 +352,10 @@ def test_planted_missing_slack_correction_is_caught(monkeypatch):
     x = synth.random_point(c, 1)
     orig = Q._ctg_period_smw
 
-    def bad(case, net, th_hat_b, qmax2, dt, U, den):
-        z, gin, gq2 = orig(case, net, th_hat_b, qmax2, dt, U, den)
+    def bad(case, net, th_hat_b, qmax2, dt, U, den, b_t=None):
+        z, gin, gq2, gb = orig(case, net, th_hat_b, qmax2, dt, U, den, b_t)
         # undo the projection: add back the mean that Eq. correction subtracts (approximately)
-        return z, gin + 0.37 * np.abs(gin).max(), gq2
+        return z, gin + 0.37 * np.abs(gin).max(), gq2, gb
     monkeypatch.setattr(Q, "_ctg_period_smw", bad)
     assert _fd_fails(c, x)
 
@@ -366,8 +366,8 @@ def test_planted_wrong_smw_sign_is_caught(monkeypatch):
     good = oracle.evaluate(c, x, mode="brute")
     orig = Q._ctg_period_smw
 
-    def bad(case, net, th_hat_b, qmax2, dt, U, den):
-        return orig(case, net, th_hat_b, qmax2, dt, U, 2.0 - den)  # 1 + y a^T u instead of 1 - y a^T u
+    def bad(case, net, th_hat_b, qmax2, dt, U, den, b_t=None):
+        return orig(case, net, th_hat_b, qmax2, dt, U, 2.0 - den, b_t)  # 1 + y a^T u instead of 1 - y a^T u
     monkeypatch.setattr(Q, "_ctg_period_smw", bad)
     assert abs(oracle.evaluate(c, x, mode="smw").obj - good.obj) > 1e-6 * abs(good.obj)
 
@@ -414,3 +414,79 @@ def test_sparse_lu_route_agrees_with_the_explicit_inverse():
     assert np.linalg.norm(rs.grad - rd.grad) <= 1e-10 * np.linalg.norm(rd.grad)
     for k in oracle.TERM_NAMES:
         assert abs(rs.terms[k] - rd.terms[k]) <= 1e-11 * max(abs(rd.terms[k]), 1e-6 * abs(rd.obj))
+
+
+# --------------------------------------------------------------------------------------------
+# transformers and phase shifters (tap ratio tau, phase shift phi as variables)
+# --------------------------------------------------------------------------------------------
+
+def _tiny_xf():
+    return synth.with_transformers(synth.tiny(), frac=0.3, seed=4)
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_fd_gradient_tiny_transformers_all_coordinates(seed):
+    """Every coordinate, tau and phi included, against central differences of the objective."""
+    c = _smooth(_tiny_xf())
+    assert c.n_xf >= 4 and np.any(c.phi_max > 0)
+    x = synth.random_point(c, seed)
+    g = oracle.evaluate(c, x).grad
+    fd = _fd(c, x, np.arange(c.n_x))
+    scale = np.abs(g).max()
+    assert np.max(np.abs(fd - g)) <= 1e-7 * scale, np.max(np.abs(fd - g)) / scale
+    otau, ophi = c.offsets_xf()
+    assert np.abs(g[otau:]).max() > 1e-3 * scale  # the new coordinates carry real gradient
+
+
+@pytest.mark.parametrize("mk", [_tiny_xf, lambda: synth.with_transformers(synth.batch(per_shape=1)[0], 0.2, 5)])
+def test_ctg_smw_matches_brute_force_with_phase_shifters(mk):
+    """The rank-1 form with phase-shift flows (the outaged branch losing its own b_k) against
+    re-solving every outaged network with its phase-shift injections."""
+    c = mk()
+    x = synth.random_point(c, 13)
+    a = oracle.evaluate(c, x, mode="smw")
+    b = oracle.evaluate(c, x, mode="brute")
+    assert abs(a.obj - b.obj) <= 1e-12 * abs(b.obj)
+    assert np.allclose(a.z_ctg, b.z_ctg, rtol=1e-12, atol=0)
+    assert np.max(np.abs(a.grad - b.grad)) <= 1e-11 * np.abs(b.grad).max()
+
+
+@pytest.mark.parametrize("tau,phi", [(1.0, 0.0), (0.93, 0.0), (1.07, 0.2), (1.0, -0.25)])
+def test_two_bus_transformer_against_complex_power(tau, phi):
+    """Ideal transformer 1 : tau e^{j phi}... written as the series admittance seen through the tap:
+    V_f' = V_f e^{-j phi} / tau, I_fr = (y_sr (V_f' - V_o) + j b_ch/2 V_f') e^{-j phi} / tau."""
+    xl, bch, rr = 0.2, 0.04, 0.05
+    c = _two_bus(xl, bch, rr)
+    c = dataclasses.replace(c, xf_branch=np.array([0], np.int32), tau_min=np.array([0.9]), tau_max=np.array([1.1]),
+                            phi_min=np.array([-0.3]), phi_max=np.array([0.3]))
+    f, o = int(c.br_from[0]), int(c.br_to[0])
+    rng = np.random.default_rng(1)
+    v = rng.uniform(0.9, 1.1, (1, 2))
+    th = rng.normal(0, 0.3, (1, 2))
+    pf, qf, pt, qt = oracle.ac_flows(c, v, th, np.array([[tau]]), np.array([[phi]]))
+    Vf = v[0, f] * np.exp(1j * th[0, f])
+    Vo = v[0, o] * np.exp(1j * th[0, o])
+    ysr = 1.0 / (rr + 1j * xl)
+    Vfp = Vf * np.exp(-1j * phi) / tau
+    Ifp = ysr * (Vfp - Vo) + 1j * bch / 2 * Vfp
+    It = ysr * (Vo - Vfp) + 1j * bch / 2 * Vo
+    Sf = Vfp * np.conj(Ifp)  # power into the line at the ideal transformer's secondary = at the primary
+    St = Vo * np.conj(It)
+    assert abs(pf[0, 0] - Sf.real) < 1e-13 and abs(qf[0, 0] - Sf.imag) < 1e-13
+    assert abs(pt[0, 0] - St.real) < 1e-13 and abs(qt[0, 0] - St.imag) < 1e-13
+
+
+def test_phase_shifted_flows_conserve_injections():
+    """DC base flows with phase shifters satisfy KCL (E^T p = pbar) and equal y (theta_f - theta_o
+    - phi) on every branch (the contingency flow equation of Sec. II-E)."""
+    c = _tiny_xf()
+    x = synth.random_point(c, 14)
+    v, th, p, q, r, tau, phi = oracle.unpack(c, x)
+    net = oracle.dc_network(c)
+    _, pbar = oracle.dc_injections(c, p)
+    phib = Q.branch_tau_phi(c, tau, phi)[1]
+    bflow = Q.phase_shift_flows(c, net, phib)
+    thd, flow = oracle.dc_base_flows(c, net, pbar, bflow)
+    assert np.allclose(flow @ net.E, pbar, atol=1e-12)
+    dth = thd[:, c.br_from] - thd[:, c.br_to] - phib
+    assert np.allclose(flow, net.y[None, :] * dth, atol=1e-12)
