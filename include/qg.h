@@ -18,9 +18,11 @@
  *  - All device work is ordered on the stream set by qg_set_stream (default:
  *    the legacy default stream); no call synchronizes the device except
  *    qg_create*, qg_eval_grad_host, qg_breakdown and qg_get_state.
- *  - Variable layout of one instance (qg_layout): five period-major blocks
- *        x = [ v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G) ]
- *    and batched instances are concatenated in creation order.
+ *  - Variable layout of one instance (qg_layout): period-major blocks
+ *        x = [ v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G)
+ *              | tau (T x X) | phi (T x X) ]
+ *    (the transformer blocks are empty when X = 0), and batched instances are
+ *    concatenated in creation order.
  *  - Per-unit quantities, periods of dt hours.
  */
 #ifndef QG_H
@@ -48,8 +50,8 @@ enum { QG_DC_AUTO = 0, QG_DC_DENSE = 1, QG_DC_SPARSE = 2 };      /* qg_options.d
 
 typedef struct qg_ctx qg_ctx; /* opaque handle; owns all device memory it allocates */
 
-/* Network of one instance (Sec. II-B reduced to v, theta, p, q, r; integers
- * relaxed and fixed on; no transformers: tau = 1, phi = 0).
+/* Network of one instance (Sec. II-B reduced to v, theta, p, q, r and the
+ * transformer variables tau, phi; integers relaxed and fixed on).
  *   br_from/br_to [M]  bus indices in [0, n), from != to
  *   br_r, br_x [M]     series impedance r + jx (x > 0); g + jb = 1/(r + jx)
  *   br_b [M]           total line charging b_ch (pi model, b_ch/2 per end)
@@ -57,7 +59,13 @@ typedef struct qg_ctx qg_ctx; /* opaque handle; owns all device memory it alloca
  *   s_max_ctg [M]      post-contingency limit (Eqs. sfr_pen-zctg)
  *   gen_bus, gen_zone [G], cost_a, cost_b [G] (cost d_t (a p^2 + b p)),
  *   cost_r [G] (reserve offer), pmin, pmax, qmin, qmax [G], ramp [G] (pu/h)
- *   vmin, vmax [n]; ref_bus in [0, n) (angle reference, theta_ref clipped to 0) */
+ *   vmin, vmax [n]; ref_bus in [0, n) (angle reference, theta_ref clipped to 0)
+ *   n_xf, xf_branch [X]  branches that are transformers (distinct ids in [0, M); X = 0 allowed,
+ *                       with NULL arrays): an ideal transformer of tap ratio tau and phase
+ *                       shift phi at the "fr" end (Sec. II-F line-flow example; the AC flows
+ *                       use v_f / tau and delta = theta_f - theta_o - phi) whose DC contingency
+ *                       flow is -b_sr (theta_f - theta_o - phi) (Sec. II-E); tau, phi are
+ *                       per-period variables in [tau_min, tau_max] (> 0), [phi_min, phi_max] */
 typedef struct {
   int32_t n_bus, n_branch, n_gen, n_zone, ref_bus;
   const int32_t *br_from, *br_to;
@@ -65,6 +73,9 @@ typedef struct {
   const int32_t *gen_bus, *gen_zone;
   const double *cost_a, *cost_b, *cost_r, *pmin, *pmax, *qmin, *qmax, *ramp;
   const double *vmin, *vmax;
+  int32_t n_xf;
+  const int32_t *xf_branch;
+  const double *tau_min, *tau_max, *phi_min, *phi_max;
 } qg_network;
 
 /* Horizon: T periods of dt[t] hours; load_p, load_q are T x n period-major;
@@ -126,9 +137,9 @@ void qg_destroy(qg_ctx *h);
 int64_t qg_num_vars(const qg_ctx *h);
 
 /* Layout of instance `inst`: its first variable in the concatenated x, its
- * n_x = T (2n + 3G), and the starts of the v, theta, p, q, r blocks relative
- * to that first variable. */
-int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[5]);
+ * n_x = T (2n + 3G + 2X), and the starts of the v, theta, p, q, r, tau, phi
+ * blocks relative to that first variable. */
+int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[7]);
 
 /* Order all later device work on `stream` (a cudaStream_t; NULL = default). */
 int qg_set_stream(qg_ctx *h, void *stream);

@@ -31,12 +31,16 @@ constexpr int TAIL_DEGREE = 32;     // minimum-degree elimination stops above th
 constexpr long long CTG_WAVE = 152 * 3;  // contingency blocks resident at once (152 SMs x 3 blocks)
 
 struct HostInst {
-  int n, M, G, Z, T, K, ref;
+  int n, M, G, Z, T, K, ref, X = 0;
   std::vector<int> from, to, gen_bus, gen_zone, ctg;
+  std::vector<int> xf;         // transformer branch ids [X]
+  std::vector<int> br_xf;      // branch -> transformer index, -1 for lines [M]
+  std::vector<double> tau_lo, tau_hi, phi_lo, phi_hi;
   std::vector<double> r, x, bch, smax, sctg, ca, cb, cr, pmin, pmax, qmin, qmax, ramp, vmin, vmax;
   std::vector<double> dt, load_p, load_q, rreq;
   // derived (FP64)
   std::vector<double> y, gsr, bsr;
+  int Gc = 0;                 // dense DC product columns: generator buses, then transformers
   std::vector<int> gbus;      // distinct generator buses, ascending
   std::vector<int> gen_gb;    // generator -> index into gbus
   std::vector<double> ptdfg;  // M x Gb
@@ -170,8 +174,26 @@ int read_instance(qg_ctx *h, const qg_network &N, const qg_horizon &H, const qg_
     if (seen[I.ctg[k]]) return bad("duplicate contingency");
     seen[I.ctg[k]] = 1;
   }
+  if (N.n_xf < 0 || N.n_xf > M) return bad("n_xf out of range");
+  I.X = N.n_xf;
+  I.br_xf.assign(M, -1);
+  if (I.X > 0) {
+    if (!N.xf_branch || !N.tau_min || !N.tau_max || !N.phi_min || !N.phi_max) return bad("null transformer array");
+    I.xf.assign(N.xf_branch, N.xf_branch + I.X);
+    I.tau_lo = cp(N.tau_min, I.X); I.tau_hi = cp(N.tau_max, I.X);
+    I.phi_lo = cp(N.phi_min, I.X); I.phi_hi = cp(N.phi_max, I.X);
+    for (int q = 0; q < I.X; ++q) {
+      const int j = I.xf[q];
+      if (j < 0 || j >= M) return bad("transformer branch out of range");
+      if (I.br_xf[j] >= 0) return bad("duplicate transformer branch");
+      I.br_xf[j] = q;
+      if (!(I.tau_lo[q] > 0.0) || !(I.tau_lo[q] <= I.tau_hi[q]) || !(I.phi_lo[q] <= I.phi_hi[q]))
+        return bad("transformer limits");
+    }
+  }
   for (auto *v : {&I.r, &I.x, &I.bch, &I.smax, &I.sctg, &I.ca, &I.cb, &I.cr, &I.pmin, &I.pmax, &I.qmin, &I.qmax,
-                  &I.ramp, &I.vmin, &I.vmax, &I.dt, &I.load_p, &I.load_q, &I.rreq})
+                  &I.ramp, &I.vmin, &I.vmax, &I.dt, &I.load_p, &I.load_q, &I.rreq, &I.tau_lo, &I.tau_hi, &I.phi_lo,
+                  &I.phi_hi})
     if (!finite_all(*v)) return bad("non-finite input");
   return QG_OK;
 }
@@ -265,9 +287,17 @@ int build_dc_sparse(qg_ctx *h, HostInst &I, int b, const std::vector<int> &red,
   I.dinv.resize(I.nS);
   for (int q = 0; q < I.nS; ++q) I.dinv[q] = 1.0 / F.cols[q].d;
   I.sinv = F.Sinv;
+  I.Gc = (int)I.gbus.size();
+  // adjoint back-gather rows: eliminated positions at generator buses or transformer ends
+  std::vector<char> need(nr, 0);
+  for (int q = 0; q < I.nS; ++q)
+    if (I.pos_gb[q] >= 0) need[q] = 1;
+  for (int q = 0; q < I.X; ++q)
+    for (int bus : {I.from[I.xf[q]], I.to[I.xf[q]]})
+      if (I.bus_pos[bus] >= 0) need[I.bus_pos[bus]] = 1;
   I.adj_rows.clear();
   for (int q = 0; q < I.nS; ++q)
-    if (I.pos_gb[q] >= 0) I.adj_rows.push_back(q);
+    if (need[q]) I.adj_rows.push_back(q);
   // incident branches per position (+ at the from-end)
   std::vector<std::vector<int>> inc(nr);
   for (int j = 0; j < M; ++j) {
@@ -385,8 +415,12 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
       Zm[(size_t)j * n + i] = v;
     }
   const int Gb = (int)I.gbus.size();
-  // PTDF rows: generator-bus columns, load products and row sums
-  I.ptdfg.assign((size_t)M * Gb, 0.0);
+  const int Gc = Gb + I.X;
+  I.Gc = Gc;
+  // PTDF rows: generator-bus columns, then per transformer x the column -PSDF[:, x] =
+  // -Y_x E_hat Yhat^-1 a_x (flow change per unit phase-shift flow b_x, Eq. Yb_solve with
+  // c_t = p_inj - E^T b_t), load products and row sums
+  I.ptdfg.assign((size_t)M * Gc, 0.0);
   I.cload.assign((size_t)T * M, 0.0);
   I.rsum.assign(M, 0.0);
   std::vector<double> row(n);
@@ -398,7 +432,11 @@ int build_dc(qg_ctx *h, HostInst &I, int b) {
       s += row[i];
     }
     I.rsum[m] = s;
-    for (int q = 0; q < Gb; ++q) I.ptdfg[(size_t)m * Gb + q] = row[I.gbus[q]];
+    for (int q = 0; q < Gb; ++q) I.ptdfg[(size_t)m * Gc + q] = row[I.gbus[q]];
+    for (int q = 0; q < I.X; ++q) {
+      const int fx = I.from[I.xf[q]], ox = I.to[I.xf[q]];
+      I.ptdfg[(size_t)m * Gc + Gb + q] = -(row[fx] - row[ox]);
+    }
     for (int t = 0; t < T; ++t) {
       const double *lp = &I.load_p[(size_t)t * n];
       double a = 0.0;
@@ -482,7 +520,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   const int B = h->n_inst;
   std::memset(&P, 0, sizeof(P));
   P.tab.n_inst = B;
-  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0;
+  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0, tx0 = 0;
+  int xf0 = 0;
   // Contingency block shape, shared by the batch: about one wave of CTG_WAVE blocks when the
   // 64 x 64 tiles are few (the periods split across blocks), several waves when they are many
   // (tiles grouped per block, so fewer column partials are written and summed).
@@ -497,6 +536,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     Inst &D = P.tab.I[b];
     D.n = H.n; D.M = H.M; D.G = H.G; D.Z = H.Z; D.T = H.T; D.K = H.K; D.Gb = (int)H.gbus.size();
     D.Kp = ceil_div(H.K, 4) * 4;
+    D.X = H.X; D.xf0 = xf0; D.Gc = H.Gc; D.tx0 = tx0;
+    D.xtau0 = x0 + (long long)H.T * (2LL * H.n + 3LL * H.G);
     D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.gb0 = gb0; D.tp0 = tp0;
     D.n_mt = ceil_div(H.M, CT_BM);
     D.n_kt = ceil_div(H.K, CT_BK);
@@ -513,10 +554,11 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     D.hours = 0.0;
     for (int t = 0; t < H.T; ++t) D.hours += H.dt[t];
     D.wfloor_ctg = h->opt.c_s * h->opt.beta * h->opt.eps * ((double)H.M * H.K - H.K);
-    x0 += (long long)H.T * (2LL * H.n + 3LL * H.G);
+    x0 += (long long)H.T * (2LL * H.n + 3LL * H.G + 2LL * H.X);
+    tx0 += (long long)H.T * H.X; xf0 += H.X;
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
-    tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gb; l0 += (long long)H.M * D.Kp;
-    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.K; gi0 += (long long)H.T * (D.Gb + 1);
+    tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gc; l0 += (long long)H.M * D.Kp;
+    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.K; gi0 += (long long)H.T * (D.Gc + 1);
     bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.K; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
     P.maxT = std::max(P.maxT, H.T);
@@ -558,9 +600,10 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   };
   if (P.sp) add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
   else
-    for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gb + 1, NTHR / 32), I[b].T, b, R_DCA);
+    for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gc + 1, NTHR / 32), I[b].T, b, R_DCA);
   for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) gen_span(P.s5, ceil_div(I[b].G, NTHR), b);
+  for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].X, NTHR), I[b].T, b, R_XF);
   P.n_gen_slots = gen_slot;
   // objective slots: the blocks of s1 and s2 in launch order, renumbered instance-major so that each
   // instance's slots are one contiguous range; then one slot per s5 block
@@ -590,7 +633,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   const Plan &P = h->plan;
   std::vector<int2> br_end;
   std::vector<int> br_kidx, gen_bus, gen_zone, gen_gb, gb_ptr{0}, gb_gen, zgen_ptr{0}, zgen, ctg_br, bal_code, bal_row,
-      adj_code, adj_row;
+      adj_code, adj_row, br_xf, xf_br;
   std::vector<double> br_g, br_b, br_hch, br_smax, br_s2, ga, gbv, gcr, gpmax, gramp, load_p, load_q, rreq, dt, lo, hi,
       ltot, ptdfg, ptdfgT, cload, rsum, lodf;
   for (int b = 0; b < B; ++b) {
@@ -609,6 +652,8 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
       br_kidx[D.br0 + H.ctg[k]] = k;
       ctg_br.push_back(H.ctg[k]);
     }
+    br_xf.insert(br_xf.end(), H.br_xf.begin(), H.br_xf.end());
+    xf_br.insert(xf_br.end(), H.xf.begin(), H.xf.end());
     for (int g = 0; g < H.G; ++g) {
       gen_bus.push_back(H.gen_bus[g]);
       gen_zone.push_back(H.gen_zone[g]);
@@ -640,9 +685,9 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
     ltot.insert(ltot.end(), H.ltot.begin(), H.ltot.end());
     if (!H.sparse) {
       ptdfg.insert(ptdfg.end(), H.ptdfg.begin(), H.ptdfg.end());
-      const int Gb = (int)H.gbus.size();
-      for (int q = 0; q < Gb; ++q)
-        for (int m = 0; m < H.M; ++m) ptdfgT.push_back(H.ptdfg[(size_t)m * Gb + q]);
+      const int Gc = H.Gc;
+      for (int q = 0; q < Gc; ++q)
+        for (int m = 0; m < H.M; ++m) ptdfgT.push_back(H.ptdfg[(size_t)m * Gc + q]);
       cload.insert(cload.end(), H.cload.begin(), H.cload.end());
     }
     rsum.insert(rsum.end(), H.rsum.begin(), H.rsum.end());
@@ -670,6 +715,10 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
       for (int g = 0; g < H.G; ++g) { lo.push_back(H.qmin[g]); hi.push_back(H.qmax[g]); }
     for (int t = 0; t < H.T; ++t)
       for (int g = 0; g < H.G; ++g) { lo.push_back(0.0); hi.push_back(H.pmax[g]); }
+    for (int t = 0; t < H.T; ++t)
+      for (int q = 0; q < H.X; ++q) { lo.push_back(H.tau_lo[q]); hi.push_back(H.tau_hi[q]); }
+    for (int t = 0; t < H.T; ++t)
+      for (int q = 0; q < H.X; ++q) { lo.push_back(H.phi_lo[q]); hi.push_back(H.phi_hi[q]); }
   }
   int rc = 0;
   {
@@ -685,7 +734,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
 #define UPD(field, vec) { auto tmp_ = to_dc<Dc>(vec); if ((rc = upload(h, &z, tmp_))) return rc; d.field = z; }
   UPI(br_kidx, br_kidx) UPI(gen_bus, gen_bus) UPI(gen_zone, gen_zone) UPI(gen_gb, gen_gb) UPI(gb_ptr, gb_ptr)
   UPI(gb_gen, gb_gen) UPI(zgen_ptr, zgen_ptr) UPI(zgen, zgen) UPI(ctg_br, ctg_br) UPI(bal_code, bal_code)
-  UPI(bal_row, bal_row) UPI(adj_code, adj_code) UPI(adj_row, adj_row)
+  UPI(bal_row, bal_row) UPI(adj_code, adj_code) UPI(adj_row, adj_row) UPI(br_xf, br_xf) UPI(xf_br, xf_br)
   UPR(br_g, br_g) UPR(br_b, br_b) UPR(br_hch, br_hch) UPR(br_smax, br_smax) UPR(br_s2ctg, br_s2)
   UPR(gen_a, ga) UPR(gen_b, gbv) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax) UPR(gen_ramp, gramp)
   UPR(load_p, load_p) UPR(load_q, load_q) UPR(rreq, rreq) UPR(dt, dt) UPR(lo, lo) UPR(hi, hi)
@@ -771,13 +820,13 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   d.c_p = (Real)o.c_p; d.c_q = (Real)o.c_q; d.c_s = (Real)o.c_s; d.c_rz = (Real)o.c_rz;
   d.rho = (Real)o.rho; d.eps = (Real)o.eps; d.beta = (Real)o.beta;
   // work buffers
-  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0;
+  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0, sTX = 0;
   for (int b = 0; b < B; ++b) {
     const Inst &I = P.tab.I[b];
     sTM += (long long)I.T * I.M; sTn += (long long)I.T * I.n; sTZ += (long long)I.T * I.Z;
     sTK += (long long)I.T * I.K; sTG += (long long)I.T * I.G;
     sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mg * I.T * I.K;
-    sGI += (long long)I.T * (I.Gb + 1);
+    sGI += (long long)I.T * (I.Gc + 1); sTX += (long long)I.T * I.X;
   }
   Real *w;
   Dc *c;
@@ -787,7 +836,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
 #define WF(field, cnt) if ((rc = dalloc(h, &fl, (size_t)(cnt)))) return rc; d.field = fl;
   WR(pf, sTM) WR(qf, sTM) WR(pt, sTM) WR(qt, sTM) WR(qm2, sTM) WR(fre, sTM) WR(fk, sTK) WR(pold, sTG)
   WR(dP, sTn) WR(dQ, sTn) WR(dZ, sTZ) WR(pm, sPM) WR(pq, sPM) WR(pk, sPK) WR(gF, sTM) WR(avf, sTM) WR(avo, sTM)
-  WR(ad, sTM)
+  WR(ad, sTM) WR(atx, sTX)
   WD(gip, sGI)
   WF(f32, sTM) WF(fk32, sTK)
 #undef WR
@@ -928,13 +977,13 @@ int noalloc_scratch(qg_ctx *h, unsigned char **out) {
 template <typename Real, typename Dc>
 size_t carve_scratch(const qg_ctx *h, unsigned char *base, size_t cap, Dev<Real, Dc> &d) {
   const Plan &P = h->plan;
-  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0;
+  long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0, sTX = 0;
   for (int b = 0; b < h->n_inst; ++b) {
     const Inst &I = P.tab.I[b];
     sTM += (long long)I.T * I.M; sTn += (long long)I.T * I.n; sTZ += (long long)I.T * I.Z;
     sTK += (long long)I.T * I.K; sTG += (long long)I.T * I.G;
     sPM += (long long)I.n_kt * I.T * I.M; sPK += (long long)I.n_mg * I.T * I.K;
-    sGI += (long long)I.T * (I.Gb + 1);
+    sGI += (long long)I.T * (I.Gc + 1); sTX += (long long)I.T * I.X;
   }
   size_t off = 0;
   auto take = [&](size_t bytes) -> unsigned char * {
@@ -948,6 +997,7 @@ size_t carve_scratch(const qg_ctx *h, unsigned char *base, size_t cap, Dev<Real,
   d.qt = (Real *)take(R * sTM); d.qm2 = (Real *)take(R * sTM); d.fre = (Real *)take(R * sTM);
   d.gF = (Real *)take(R * sTM); d.avf = (Real *)take(R * sTM); d.avo = (Real *)take(R * sTM);
   d.ad = (Real *)take(R * sTM); d.qside = take(sTM); d.f32 = (float *)take(4 * sTM);
+  d.atx = (Real *)take(R * std::max(1LL, sTX));
   d.fk = (Real *)take(R * sTK); d.fk32 = (float *)take(4 * sTK); d.pold = (Real *)take(R * sTG);
   d.dP = (Real *)take(R * sTn); d.dQ = (Real *)take(R * sTn); d.dZ = (Real *)take(R * sTZ);
   d.pm = (Real *)take(R * sPM); d.pq = (Real *)take(R * sPM); d.pk = (Real *)take(R * sPK);
@@ -1096,14 +1146,15 @@ void qg_destroy(qg_ctx *h) {
 
 int64_t qg_num_vars(const qg_ctx *h) { return h ? h->n_x : 0; }
 
-int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[5]) {
+int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[7]) {
   if (!h || inst < 0 || inst >= h->n_inst) return QG_ERR_INVALID_ARG;
   const Inst &I = h->plan.tab.I[inst];
-  const int64_t Tn = (int64_t)I.T * I.n, TG = (int64_t)I.T * I.G;
+  const int64_t Tn = (int64_t)I.T * I.n, TG = (int64_t)I.T * I.G, TX = (int64_t)I.T * I.X;
   if (first) *first = I.x0;
-  if (n_x) *n_x = 2 * Tn + 3 * TG;
+  if (n_x) *n_x = 2 * Tn + 3 * TG + 2 * TX;
   if (offsets) {
     offsets[0] = 0; offsets[1] = Tn; offsets[2] = 2 * Tn; offsets[3] = 2 * Tn + TG; offsets[4] = 2 * Tn + 2 * TG;
+    offsets[5] = 2 * Tn + 3 * TG; offsets[6] = 2 * Tn + 3 * TG + TX;
   }
   return QG_OK;
 }

@@ -27,6 +27,9 @@ constexpr int PACKS_PER_BLOCK = NTHR / 32;
 struct Inst {
   int n, M, G, Z, T, K, Gb;
   int Kp;                // row stride of the line-outage block: K rounded up to a multiple of 4
+  int X, xf0;            // transformers; first global transformer id
+  int Gc;                // columns of the dense DC products: generator buses, then (dense mode)
+                         // one column per transformer (its phase-shift flow)
   int bus0, br0, gen0, zone0, ctg0, gb0, tp0;
   int n_mt, n_kt;        // contingency tiles along monitored branches / outages
   int ctg_mg, n_mg;      // monitored-branch tiles per contingency block, and the number of such groups
@@ -39,7 +42,9 @@ struct Inst {
   long long pg0;         // PTDF restricted to generator buses: M x Gb, row m
   long long l0;          // line-outage block, M x Kp, row m
   long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mg][T][K]
-  long long gi0;         // adjoint DC products at the generator buses: [T][Gb + 1]
+  long long gi0;         // adjoint DC products: [T][Gc + 1] (generator buses, transformers, then n mean(eta))
+  long long tx0;         // per-period transformer arrays: [T][X]
+  long long xtau0;       // first tau variable (x0 + T (2n + 3G)); phi follow after T X
   double inv_n;          // 1 / n
   double hours;          // sum of dt
   double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
@@ -51,7 +56,7 @@ struct Inst {
 // Roles of the blocks of the fused stage kernels.  R_DCF / R_DCA are the dense DC products;
 // R_SDCF / R_SDCA their counterparts around the sparse-factor solves (flows from the solved
 // angles; right-hand side of the adjoint solve).
-enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN, R_SDCF, R_SDCA };
+enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN, R_SDCF, R_SDCA, R_XF };
 
 constexpr int SP_RB = 64;   // dense tail product: rows per block
 constexpr int SP_BK = 32;   // dense tail product: columns per shared-memory chunk
@@ -93,6 +98,8 @@ struct Dev {
   const int *gb_ptr, *gb_gen;         // generator bus -> generators: one CSR over the batch's generator buses
   const int *zgen_ptr, *zgen;         // zone -> generators: one CSR over the batch's zones (global ids)
   const int *ctg_br;                  // [sum K] local branch id of each outage
+  const int *br_xf;                   // [sum M] local transformer index of each branch, -1 for lines
+  const int *xf_br;                   // [sum X] local branch id of each transformer
   const int *bal_code, *bal_row;      // balance CSR packs: code = j<<2|kind (0 from-end, 1 to-end, 2 generator, 3 pad)
   const int *adj_code, *adj_row;      // branch-end CSR packs (kind 0 / 1 / 3)
   const Real *load_p, *load_q;        // [sum T n]
@@ -150,6 +157,7 @@ struct Dev {
   Real *gF;                           // [sum T M] dz/df
   Dc *gip;                            // adjoint DC products [sum T (Gb + 1)]
   Real *avf, *avo, *ad;               // branch-end adjoints [sum T M]
+  Real *atx;                          // dPhi/dtau of the AC terms per transformer [sum T X]
   Dc *objp;                           // [n_obj_slots][N_TERMS] per-block objective terms: the
                                       // stage-1/2 blocks' slots, instance-major, then one per stage-5 block
   int n_obj_slots, n_obj12;           // all slots; stage-1/2 slots

@@ -271,6 +271,21 @@ __device__ __forceinline__ bool seg_sum2(int row, Real &a, Real &b) {
   return lane == 31 || rn != row;
 }
 
+// Tap ratio and phase shift of branch j (local id) in period t: the transformer variables, or
+// (1, 0) on lines.
+template <typename Real, typename Dc>
+__device__ __forceinline__ void branch_tap(const Dev<Real, Dc> &d, const Inst &I, int t, int jg,
+                                           const Real *__restrict__ x, Real &tau, Real &phi, int &xi) {
+  xi = d.br_xf[jg];
+  tau = Real(1);
+  phi = Real(0);
+  if (xi >= 0) {
+    const long long k = I.xtau0 + (long long)t * I.X + xi;
+    tau = x[k];
+    phi = x[k + (long long)I.T * I.X];
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // stage 1
 // ---------------------------------------------------------------------------------------------
@@ -286,13 +301,17 @@ __device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub,
   const int2 ft = d.br_end[jg];
   const Real *v = x + I.x0 + (long long)t * I.n;
   const Real *th = v + (long long)I.T * I.n;
-  const Real vf = v[ft.x], vo = v[ft.y];
-  const Real dl = th[ft.x] - th[ft.y];
+  Real tau, phi;
+  int xi;
+  branch_tap(d, I, t, jg, x, tau, phi, xi);
+  // a transformer's tap enters through vf / tau, its phase shift through d = theta_f - theta_o - phi
+  const Real vf = v[ft.x] / tau, vo = v[ft.y];
+  const Real dl = th[ft.x] - th[ft.y] - phi;
   const Real g = d.br_g[jg], bb = d.br_b[jg], hch = d.br_hch[jg], smax = d.br_smax[jg];
   Real sn, cs;
   dsincos(dl, &sn, &cs);
   const Real vv = vf * vo;
-  // Pi model without the cancellation of g vf^2 against g vf vo cos(d):
+  // Pi model (vf standing for v_f / tau) without the cancellation of g vf^2 against g vf vo cos(d):
   //   p_fr = g vf (vf - vo) + g vf vo (1 - cos d) - b vf vo sin d,  and likewise for the others,
   // with 1 - cos d = sin^2 d / (1 + cos d) while cos d > 0.
   const Real dv = vf - vo;
@@ -368,29 +387,34 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   }
   Dc acc = DcOps<Dc>::zero();
   Dc tot = DcOps<Dc>::zero();  // running sum of p_G over generator buses for mu_t (warp tl)
-  for (int c0 = 0; c0 < I.Gb; c0 += GBC) {
-    const int cn = min(GBC, I.Gb - c0);
+  // columns: generator buses (their dispatch), then transformers (their phase-shift flow b = b_sr phi)
+  for (int c0 = 0; c0 < I.Gc; c0 += GBC) {
+    const int cn = min(GBC, I.Gc - c0);
     __syncthreads();
 #pragma unroll 4
     for (int e = threadIdx.x; e < DCF_TC * cn; e += NTHR) {
-      const int r = e / cn, c = e % cn, tt = t0 + r;
+      const int r = e / cn, c = e % cn, tt = t0 + r, cc = c0 + c;
       Dc s = DcOps<Dc>::zero();
-      if (tt < I.T) {
-        const int gbp = I.gb0 + c0 + c;  // global generator-bus id; gb_ptr is one CSR over the batch
+      if (tt < I.T && cc < I.Gb) {
+        const int gbp = I.gb0 + cc;  // global generator-bus id; gb_ptr is one CSR over the batch
         const int q0 = d.gb_ptr[gbp], q1 = d.gb_ptr[gbp + 1];
         for (int q = q0; q < q1; ++q)
           s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(p[(long long)tt * I.G + (d.gb_gen[q] - I.gen0)]));
+      } else if (tt < I.T) {
+        const int xi = cc - I.Gb;
+        const Real phi = x[I.xtau0 + (long long)(I.T + tt) * I.X + xi];
+        s = DcOps<Dc>::from_real(d.br_b[I.br0 + d.xf_br[I.xf0 + xi]] * phi);
       }
       s_pg[r][c] = s;
     }
 #pragma unroll 8
     for (int e = threadIdx.x; e < DCF_BM * cn; e += NTHR) {
       const int r = e / cn, c = e % cn;
-      s_pt[r][c] = (m0 + r < I.M) ? d.ptdfg[I.pg0 + (long long)(m0 + r) * I.Gb + c0 + c] : DcOps<Dc>::zero();
+      s_pt[r][c] = (m0 + r < I.M) ? d.ptdfg[I.pg0 + (long long)(m0 + r) * I.Gc + c0 + c] : DcOps<Dc>::zero();
     }
     __syncthreads();
     for (int c = 0; c < cn; ++c) DcOps<Dc>::mac(acc, s_pt[ml][c], s_pg[tl][c]);
-    for (int c = ml; c < cn; c += 32) tot = DcOps<Dc>::add(tot, s_pg[tl][c]);
+    for (int c = ml; c < cn && c0 + c < I.Gb; c += 32) tot = DcOps<Dc>::add(tot, s_pg[tl][c]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tot = DcOps<Dc>::add(tot, DcOps<Dc>::shfl_down(tot, o));
@@ -401,6 +425,9 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
     const long long e = I.tm0 + (long long)t * I.M + m;
     Dc f = DcOps<Dc>::add(acc, DcOps<Dc>::neg(d.cload[e]));
     f = DcOps<Dc>::add(f, DcOps<Dc>::neg(DcOps<Dc>::mul(s_mu[tl], d.rsum[I.br0 + m])));
+    const int xi = d.br_xf[I.br0 + m];  // a phase shifter's own flow b adds to the monitored flow
+    if (xi >= 0)
+      f = DcOps<Dc>::add(f, DcOps<Dc>::from_real(d.br_b[I.br0 + m] * x[I.xtau0 + (long long)(I.T + t) * I.X + xi]));
     const Real fr = DcOps<Dc>::to_real(f);
     d.fre[e] = fr;
     d.f32[e] = DcOps<Dc>::to_float(f);
@@ -438,6 +465,9 @@ __device__ void s1_sdcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, 
   if (po >= 0) a = DcOps<Dc>::add(a, DcOps<Dc>::neg(d.sp_th[(long long)po * I.T + t]));
   Dc f = DcOps<Dc>::mul(y, a);
   f = DcOps<Dc>::add(f, DcOps<Dc>::neg(DcOps<Dc>::mul(d.sp_mu[t], rs)));
+  const int xi = d.br_xf[I.br0 + m];  // a phase shifter's own flow b adds to the monitored flow
+  if (xi >= 0)
+    f = DcOps<Dc>::add(f, DcOps<Dc>::from_real(d.br_b[I.br0 + m] * x[I.xtau0 + (long long)(I.T + t) * I.X + xi]));
   const long long e = I.tm0 + (long long)t * I.M + m;
   const Real fr = DcOps<Dc>::to_real(f);
   d.fre[e] = fr;
@@ -813,13 +843,19 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
     else gqf += Real(2) * qf * gq2;
     const Real *v = x + I.x0 + (long long)t * I.n;
     const Real *th = v + (long long)I.T * I.n;
-    const Real vf = v[ft.x], vo = v[ft.y];
+    Real tau, phi;
+    int xi;
+    branch_tap(d, I, t, jg, x, tau, phi, xi);
+    const Real vf = v[ft.x] / tau, vo = v[ft.y];  // vf stands for v_f / tau
     Real sn, cs;
-    dsincos(th[ft.x] - th[ft.y], &sn, &cs);
+    dsincos(th[ft.x] - th[ft.y] - phi, &sn, &cs);
     const Real bc = bb + hch;
     const Real vv = vf * vo;
     const Real A = -g * cs - bb * sn, B = bb * cs - g * sn, C = -g * cs + bb * sn, D = bb * cs + g * sn;
-    d.avf[e] = gpf * (2 * g * vf + A * vo) + gqf * (-2 * bc * vf + B * vo) + gpt * (C * vo) + gqt * (D * vo);
+    // adjoint of v_f / tau; d/dv_f = (1/tau) d/d(v_f/tau), d/dtau = -(v_f/tau^2) d/d(v_f/tau)
+    const Real au = gpf * (2 * g * vf + A * vo) + gqf * (-2 * bc * vf + B * vo) + gpt * (C * vo) + gqt * (D * vo);
+    d.avf[e] = au / tau;
+    if (xi >= 0) d.atx[I.tx0 + (long long)t * I.X + xi] = -au * vf / tau;
     d.avo[e] = gpf * (A * vf) + gqf * (B * vf) + gpt * (2 * g * vo + C * vf) + gqt * (-2 * bc * vo + D * vf);
     d.ad[e] = vv * (gpf * (g * sn - bb * cs) + gqf * (-bb * sn - g * cs) + gpt * (g * sn + bb * cs) +
                     gqt * (-bb * sn + g * cs));
@@ -1106,8 +1142,45 @@ __device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab) {
   }
 }
 
+// Transformer x of period t: dPhi/dtau from the AC terms (stage 3), and dPhi/dphi = -(the AC
+// adjoint of delta) + b_sr dPhi/db, where dPhi/db = dz/dp_x - (E_hat eta)_x is the contingency
+// term's phase-shift gradient (Eq. 2nd_lin_sys_phase plus the direct term of p = f + b);
+// [+ the projected Adam update of tau and phi].
+template <typename Real, typename Dc, bool ADAM>
+__device__ void s5_xf(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x,
+                      const AdamCoef<Real> &ac) {
+  const int xi = sub * NTHR + threadIdx.x;
+  if (xi >= I.X) return;
+  const int j = d.xf_br[I.xf0 + xi];
+  const long long e = I.tm0 + (long long)t * I.M + j;
+  Real eterm;
+  if (d.sp) {
+    const int2 ft = d.br_end[I.br0 + j];
+    const int pf = d.bus_pos[ft.x], po = d.bus_pos[ft.y];
+    const Dc ef = pf >= 0 ? d.sp_th[(long long)pf * I.T + t] : DcOps<Dc>::zero();
+    const Dc eo = po >= 0 ? d.sp_th[(long long)po * I.T + t] : DcOps<Dc>::zero();
+    eterm = -DcOps<Dc>::to_real(DcOps<Dc>::add(ef, DcOps<Dc>::neg(eo)));
+  } else {
+    eterm = DcOps<Dc>::to_real(d.gip[I.gi0 + (long long)t * (I.Gc + 1) + I.Gb + xi]);
+  }
+  const Real gb = d.gF[e] + eterm;
+  const Real gphi = -d.ad[e] + d.br_b[I.br0 + j] * gb;
+  const Real gtau = d.atx[I.tx0 + (long long)t * I.X + xi];
+  const long long kt = I.xtau0 + (long long)t * I.X + xi, kp = kt + (long long)I.T * I.X;
+  if (ADAM) {
+    adam_update(x[kt], gtau, d.am[kt], d.av[kt], d.lo[kt], d.hi[kt], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
+                d.paper_eps);
+    adam_update(x[kp], gphi, d.am[kp], d.av[kp], d.lo[kp], d.hi[kp], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
+                d.paper_eps);
+  } else {
+    d.g[kt] = gtau;
+    d.g[kp] = gphi;
+  }
+}
+
 // Stage 5: generators of one period, with eta from stage 4's adjoint DC products (dense DC mode) or
-// from the adjoint solve (sparse mode); the last block reduces the objective.
+// from the adjoint solve (sparse mode) | transformers of one period; the last block reduces the
+// objective.
 template <typename Real, typename Dc, bool ADAM>
 __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
@@ -1115,19 +1188,24 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
   const int t = w.t;
-  Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
   AdamCoef<Real> ac{};
   if (ADAM) ac = adam_coef(d);
-  const int gl = w.sub * NTHR + threadIdx.x;
-  const bool on = gl < I.G;
-  const GenIn<Real> g = gen_load<Real, Dc, ADAM>(d, I, t, on ? gl : 0, x);
-  pdl_wait();
-  if (on) {
-    const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gb + 1);  // written by the adjoint solve
-    const Dc eta = DcOps<Dc>::add(et[g.gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gb], DcOps<Dc>::inv_n(I))));
-    gen_update<Real, Dc, ADAM>(d, I, t, gl, g, eta, ac, acc, x);
+  if (w.role == R_XF) {
+    pdl_wait();
+    s5_xf<Real, Dc, ADAM>(d, I, t, w.sub, x, ac);
+  } else {
+    Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
+    const int gl = w.sub * NTHR + threadIdx.x;
+    const bool on = gl < I.G;
+    const GenIn<Real> g = gen_load<Real, Dc, ADAM>(d, I, t, on ? gl : 0, x);
+    pdl_wait();
+    if (on) {
+      const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gc + 1);  // written by stage 4 or the adjoint solve
+      const Dc eta = DcOps<Dc>::add(et[g.gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gc], DcOps<Dc>::inv_n(I))));
+      gen_update<Real, Dc, ADAM>(d, I, t, gl, g, eta, ac, acc, x);
+    }
+    reduce_share(d, I, blockIdx.x - I.gen_first, acc);
   }
-  reduce_share(d, I, blockIdx.x - I.gen_first, acc);
   finish_eval<Real, Dc, ADAM>(d, tab);
 }
 
@@ -1161,15 +1239,17 @@ __device__ void s4_sdca(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub) 
 
 // Adjoint DC products (Eq. 2nd_lin_sys at the generator buses): one warp per output,
 //   eta[t, gb] = sum_m dz/df[t,m] PTDF[m, gb]       (gb < Gb),
-//   eta[t, Gb] = sum_m dz/df[t,m] (PTDF 1)[m]        (n times the mean of eta, Eq. correction),
+//   eta[t, Gb + x] = -sum_m dz/df[t,m] PSDF[m, x] = -(E_hat eta)_x   (transformer x, Eq.
+//                                                    2nd_lin_sys_phase),
+//   eta[t, Gc] = sum_m dz/df[t,m] (PTDF 1)[m]        (n times the mean of eta, Eq. correction),
 // lanes striding over the branches, then a fixed-order shuffle reduction.
 template <typename Real, typename Dc>
 __device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
   const int o = sub * (NTHR / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (o > I.Gb) return;
+  if (o > I.Gc) return;
   const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
-  const Dc *col = o < I.Gb ? d.ptdfgT + I.pg0 + (long long)o * I.M : d.rsum + I.br0;
+  const Dc *col = o < I.Gc ? d.ptdfgT + I.pg0 + (long long)o * I.M : d.rsum + I.br0;
   Dc a0 = DcOps<Dc>::zero(), a1 = a0, a2 = a0, a3 = a0;
   int m = lane;
   for (; m + 96 < I.M; m += 128) {
@@ -1182,7 +1262,7 @@ __device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
   Dc acc = DcOps<Dc>::add(DcOps<Dc>::add(a0, a1), DcOps<Dc>::add(a2, a3));
 #pragma unroll
   for (int k = 16; k > 0; k >>= 1) acc = DcOps<Dc>::add(acc, DcOps<Dc>::shfl_down(acc, k));
-  if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + o] = acc;
+  if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gc + 1) + o] = acc;
 }
 
 // Stage 4: bus gather of the branch-end adjoints (-> g_v, g_theta) [+ Adam on v, theta]; the
@@ -1260,6 +1340,14 @@ __global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Rea
       for (int q = q0; q < q1; ++q)
         s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(p[(long long)t * I.G + (d.gb_gen[q] - I.gen0)]));
     }
+    if (I.X > 0) {  // - E^T b: a phase-shift flow leaves its from end and enters its to end
+      for (int q = d.inc_ptr[pos]; q < d.inc_ptr[pos + 1]; ++q) {
+        const int c = d.inc_code[q], j = c >> 1, xi = d.br_xf[I.br0 + j];
+        if (xi < 0) continue;
+        const Real b = d.br_b[I.br0 + j] * x[I.xtau0 + (long long)(I.T + t) * I.X + xi];
+        s = DcOps<Dc>::add(s, DcOps<Dc>::from_real((c & 1) ? b : -b));
+      }
+    }
     d.sp_rhs[e] = s;
   } else {
     const int t = blockIdx.x - nb;
@@ -1283,7 +1371,7 @@ __global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Rea
     for (int t = threadIdx.x; t < T; t += NTHR) {
       Dc s = DcOps<Dc>::zero();
       for (int c = 0; c < d.n_pchunk; ++c) s = DcOps<Dc>::add(s, d.sp_part[(long long)c * T + t]);
-      d.gip[I.gi0 + (long long)t * (I.Gb + 1) + I.Gb] = s;
+      d.gip[I.gi0 + (long long)t * (I.Gc + 1) + I.Gc] = s;
     }
     return;
   }
@@ -1392,18 +1480,18 @@ __global__ void __launch_bounds__(NTHR, 2) k_sp_tail(const __grid_constant__ Dev
     for (int q = 0; q < ks; ++q) v = DcOps<Dc>::add(v, d.sp_tpart[((long long)q * m + a) * T + t]);
     const int pos = d.nS + a;
     d.sp_u[(long long)pos * T + t] = v;
-    if (!ADJ) {
-      d.sp_th[(long long)pos * T + t] = v;
-    } else {
+    d.sp_th[(long long)pos * T + t] = v;  // forward: the angles; adjoint: eta (transformer gradients)
+    if (ADJ) {
       const int gb = d.pos_gb[pos];
-      if (gb >= 0) d.gip[I.gi0 + (long long)t * (I.Gb + 1) + gb] = v;
+      if (gb >= 0) d.gip[I.gi0 + (long long)t * (I.Gc + 1) + gb] = v;
     }
   }
   if (threadIdx.x == 0) d.sp_tick[rt] = 0u;
 }
 
 // Backward gather x_S = M1^T u_S + M2^T u_T (u_S = D_S^-1 z_S, u_T = x_T), one warp per eliminated
-// position: every one on the forward pass (angles), the generator buses on the adjoint pass.
+// position: every one on the forward pass (angles), the generator buses and transformer ends on
+// the adjoint pass.
 template <typename Real, typename Dc, bool ADJ>
 __global__ void __launch_bounds__(NTHR) k_sp_back(const __grid_constant__ Dev<Real, Dc> d,
                                                   const __grid_constant__ Inst I) {
@@ -1426,15 +1514,14 @@ __global__ void __launch_bounds__(NTHR) k_sp_back(const __grid_constant__ Dev<Re
       if (ta < T) DcOps<Dc>::mac(a0, v, u[ta]);
       if (tb < T) DcOps<Dc>::mac(a1, v, u[tb]);
     }
-    if (ADJ) {
+    if (ADJ && gb >= 0) {
       Dc *g = d.gip + I.gi0 + gb;
-      if (ta < T) g[(long long)ta * (I.Gb + 1)] = a0;
-      if (tb < T) g[(long long)tb * (I.Gb + 1)] = a1;
-    } else {
-      Dc *th = d.sp_th + (long long)q * T;
-      if (ta < T) th[ta] = a0;
-      if (tb < T) th[tb] = a1;
+      if (ta < T) g[(long long)ta * (I.Gc + 1)] = a0;
+      if (tb < T) g[(long long)tb * (I.Gc + 1)] = a1;
     }
+    Dc *th = d.sp_th + (long long)q * T;  // forward: the angles; adjoint: eta (transformer gradients)
+    if (ta < T) th[ta] = a0;
+    if (tb < T) th[tb] = a1;
   }
 }
 

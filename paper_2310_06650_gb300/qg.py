@@ -40,7 +40,9 @@ class qg_network(C.Structure):
                 ("ref_bus", C.c_int32), ("br_from", _I32P), ("br_to", _I32P), ("br_r", _F64P), ("br_x", _F64P),
                 ("br_b", _F64P), ("s_max", _F64P), ("s_max_ctg", _F64P), ("gen_bus", _I32P), ("gen_zone", _I32P),
                 ("cost_a", _F64P), ("cost_b", _F64P), ("cost_r", _F64P), ("pmin", _F64P), ("pmax", _F64P),
-                ("qmin", _F64P), ("qmax", _F64P), ("ramp", _F64P), ("vmin", _F64P), ("vmax", _F64P)]
+                ("qmin", _F64P), ("qmax", _F64P), ("ramp", _F64P), ("vmin", _F64P), ("vmax", _F64P),
+                ("n_xf", C.c_int32), ("xf_branch", _I32P), ("tau_min", _F64P), ("tau_max", _F64P),
+                ("phi_min", _F64P), ("phi_max", _F64P)]
 
 
 class qg_horizon(C.Structure):
@@ -166,6 +168,12 @@ def _structs(case, keep: _Keep):
         cost_a=keep.f64(case.cost_a), cost_b=keep.f64(case.cost_b), cost_r=keep.f64(case.cost_r),
         pmin=keep.f64(case.pmin), pmax=keep.f64(case.pmax), qmin=keep.f64(case.qmin), qmax=keep.f64(case.qmax),
         ramp=keep.f64(case.ramp), vmin=keep.f64(case.vmin), vmax=keep.f64(case.vmax))
+    X = int(getattr(case, "n_xf", 0))
+    if X:
+        net.n_xf = X
+        net.xf_branch = keep.i32(case.xf_branch)
+        net.tau_min, net.tau_max = keep.f64(case.tau_min), keep.f64(case.tau_max)
+        net.phi_min, net.phi_max = keep.f64(case.phi_min), keep.f64(case.phi_max)
     hor = qg_horizon(T=case.T, dt=keep.f64(case.dt), load_p=keep.f64(case.load_p), load_q=keep.f64(case.load_q),
                      reserve_req=keep.f64(case.reserve_req))
     ctg = qg_contingencies(K=case.K, branch=keep.i32(case.ctg) if case.K > 0 else None)
@@ -207,7 +215,7 @@ def qg_num_vars(h: int) -> int:
 
 def qg_layout(h: int, inst: int = 0):
     first, n_x = C.c_int64(), C.c_int64()
-    off = (C.c_int64 * 5)()
+    off = (C.c_int64 * 7)()
     _check(_lib.qg_layout(h, inst, C.byref(first), C.byref(n_x), off), h)
     return first.value, n_x.value, tuple(off)
 

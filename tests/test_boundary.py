@@ -133,3 +133,22 @@ def test_sparse_dc_set_up_runs_on_the_host(qg, name):
     line-outage block) runs before the device is needed."""
     c = {"tiny": synth.tiny, "rt617": synth.rt617}[name]()
     _expect(qg, c, qg.QG_ERR_NO_DEVICE, dc_solver=qg.QG_DC_SPARSE)
+
+
+def test_transformer_inputs_are_validated(qg):
+    c = synth.with_transformers(synth.tiny(), 0.3, 4)
+    dup = c.xf_branch.copy(); dup[1] = dup[0]
+    _expect(qg, dataclasses.replace(c, xf_branch=dup), qg.QG_ERR_INVALID_ARG)
+    far = c.xf_branch.copy(); far[0] = c.n_branch
+    _expect(qg, dataclasses.replace(c, xf_branch=far), qg.QG_ERR_INVALID_ARG)
+    tl = c.tau_min.copy(); tl[0] = 0.0
+    _expect(qg, dataclasses.replace(c, tau_min=tl), qg.QG_ERR_INVALID_ARG)
+    ph = c.phi_min.copy(); ph[0] = 1.0
+    _expect(qg, dataclasses.replace(c, phi_min=ph), qg.QG_ERR_INVALID_ARG)
+
+
+@pytest.mark.skipif(_gpu_present(), reason="checks the no-device path")
+def test_transformer_case_reaches_device_check(qg):
+    c = synth.with_transformers(synth.mid(), 0.15, 5)
+    for dc in (qg.QG_DC_DENSE, qg.QG_DC_SPARSE):
+        _expect(qg, c, qg.QG_ERR_NO_DEVICE, dc_solver=dc)
