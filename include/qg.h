@@ -185,9 +185,30 @@ int qg_adam_step(qg_ctx *h, void *x, void *m, void *v, double lr, double beta1, 
 /* iters iterations of (qg_eval_grad; qg_adam_step) on x in place, with Adam
  * moments kept inside the handle (zero after qg_create and after
  * qg_set_step(h, 0)), replayed from a CUDA graph that is captured on the first
- * call and re-captured when x, lr, beta1 or beta2 change.  Does not synchronize.  obj_trace (device, iters x n_inst doubles, may be NULL)
- * receives the objective evaluated at the start of each iteration. */
+ * call and re-captured when x, lr, beta1, beta2, obj_trace or (with a trace) iters change.  Does not
+ * synchronize.  obj_trace (device, iters x n_inst doubles, may be NULL) receives the objective
+ * evaluated at the start of each iteration. */
 int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace);
+
+/* qg_solve with the schedules of Sec. II-F: iteration i of this call (i = 0 .. iters - 1) takes its
+ * Adam step size, soft-abs / soft-ReLU epsilon and homotopy scale beta from sched[3 i .. 3 i + 2]
+ * (device array of iters x 3 doubles: lr, eps, beta; e.g. written by qg_schedule), in place of lr
+ * and of the handle's eps and beta options.  obj_trace records each iteration's objective at its own
+ * eps and beta.  The graph is re-captured when x, sched, beta1, beta2, obj_trace or iters change. */
+int qg_solve_schedule(qg_ctx *h, void *x, int32_t iters, const double *sched, double beta1, double beta2,
+                      double *obj_trace);
+
+/* The per-iteration schedule of Sec. II-F for `iters` iterations, written to out (host, iters x 3
+ * doubles).  Time is the iteration fraction (reading of the wall-clock time of Eq. norm_t):
+ * t_i = 2 i / (iters - 1) - 1 (t = -1 for iters = 1), s(t) = e^{4t} / (0.6 + e^{4t}) (Eq. mag_scale):
+ *   lr_i   = lr0 10^{s(t_i) log10(lrf / lr0)}                (Eq. step_size)
+ *   eps_i  = eps0 10^{s(t_i - lag) log10(epsf / eps0)}       (soft-abs / soft-ReLU tightening, which
+ *                                                             lags the step-size decay by `lag`)
+ *   beta_i = beta0 + (beta1 - beta0) (t_i + 1) / 2           (homotopy scale, linear)
+ * Host-only (no device needed).  Returns QG_ERR_INVALID_ARG for iters < 1, non-positive lr0, lrf,
+ * eps0, epsf or non-finite beta0, beta1, lag. */
+int qg_schedule(double *out, int32_t iters, double lr0, double lrf, double eps0, double epsf, double beta0,
+                double beta1, double lag);
 
 /* Per-instance penalty breakdown of the last evaluation, host array of
  * 8 x n_inst doubles: cost, z_p, z_q, z_s, z_rz, z_headroom, z_ramp, z_ctg.

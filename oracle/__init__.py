@@ -5,4 +5,4 @@ benchmark's CPU-baseline leg, never by the library's product path.
 """
 from .qg_oracle import evaluate, objective, unpack, pack, box, ac_flows, bus_mismatch, dc_network, \
     dc_injections, dc_base_flows, soft_abs, soft_relu, TERM_NAMES  # noqa: F401
-from .adam import adam_step, normalized_time, magnitude_scale, step_size  # noqa: F401
+from .adam import adam_step, normalized_time, magnitude_scale, step_size, schedule_table  # noqa: F401

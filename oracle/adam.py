@@ -42,3 +42,21 @@ def step_size(alpha0, alphaf, tw, t0, tf):
     """Eq. step_size: alpha0 * 10^(beta * log10(alphaf / alpha0))."""
     b = magnitude_scale(normalized_time(tw, t0, tf))
     return alpha0 * 10.0 ** (b * math.log10(alphaf / alpha0))
+
+
+def schedule_table(iters, lr0, lrf, eps0, epsf, beta0, beta1, lag):
+    """Per-iteration (lr, eps, beta) of Sec. II-F with time measured as the iteration fraction:
+    lr from Eqs. norm_t, mag_scale, step_size over [0, iters - 1]; eps with the same law over its
+    own range, its normalized time lagging by `lag` (the step size decay leads the tightening);
+    beta rising linearly from beta0 to beta1 (the homotopy scale)."""
+    out = np.zeros((iters, 3))
+    for i in range(iters):
+        if iters > 1:
+            that = normalized_time(i, 0, iters - 1)
+        else:
+            that = -1.0
+        out[i, 0] = step_size(lr0, lrf, i, 0, max(iters - 1, 1)) if iters > 1 else \
+            lr0 * 10.0 ** (magnitude_scale(-1.0) * math.log10(lrf / lr0))
+        out[i, 1] = eps0 * 10.0 ** (magnitude_scale(that - lag) * math.log10(epsf / eps0))
+        out[i, 2] = beta0 + (beta1 - beta0) * (that + 1.0) / 2.0
+    return out

@@ -80,6 +80,7 @@ struct qg_ctx {
   const void *g_x = nullptr;
   double g_lr = 0, g_b1 = 0, g_b2 = 0;
   double *g_trace = nullptr;
+  const double *g_sched = nullptr;
   int g_trace_len = 0;
   // optional per-kernel timing: ev[0..5] bracket the five stage kernels, ev[6] ends a stand-alone Adam step
   bool profiling = false;
@@ -553,7 +554,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     D.inv_n = 1.0 / H.n;
     D.hours = 0.0;
     for (int t = 0; t < H.T; ++t) D.hours += H.dt[t];
-    D.wfloor_ctg = h->opt.c_s * h->opt.beta * h->opt.eps * ((double)H.M * H.K - H.K);
+    D.nfloor_ctg = (double)H.M * H.K - H.K;
     x0 += (long long)H.T * (2LL * H.n + 3LL * H.G + 2LL * H.X);
     tx0 += (long long)H.T * H.X; xf0 += H.X;
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
@@ -819,6 +820,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   const qg_options &o = h->opt;
   d.c_p = (Real)o.c_p; d.c_q = (Real)o.c_q; d.c_s = (Real)o.c_s; d.c_rz = (Real)o.c_rz;
   d.rho = (Real)o.rho; d.eps = (Real)o.eps; d.beta = (Real)o.beta;
+  d.c_s64 = o.c_s; d.eps64 = o.eps; d.beta64 = o.beta;
   // work buffers
   long long sTM = 0, sTn = 0, sTZ = 0, sTK = 0, sTG = 0, sPM = 0, sPK = 0, sGI = 0, sTX = 0;
   for (int b = 0; b < B; ++b) {
@@ -891,18 +893,19 @@ bool mixed(const qg_ctx *h) { return h->opt.precision == QG_MIXED; }
 
 // One evaluation; with adam, the projected Adam update is fused into stages 4 and 5 using the
 // handle's moments and the given hyper-parameters.
-int run_eval(qg_ctx *h, const void *x, bool adam, double lr, double b1, double b2, double *trace, int trace_len) {
+int run_eval(qg_ctx *h, const void *x, bool adam, double lr, double b1, double b2, double *trace, int trace_len,
+             const double *sched = nullptr, int sched_len = 0) {
   cudaEvent_t *ev = h->profiling ? h->ev : nullptr;
   cudaError_t e;
   if (mixed(h)) {
     Dev<float, df32> d = h->d32;
     d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
-    d.trace = trace; d.trace_len = trace_len;
+    d.trace = trace; d.trace_len = trace_len; d.sched = sched; d.sched_len = sched_len;
     e = launch_eval<float, df32>(d, h->plan, x, adam, h->stream, ev);
   } else {
     Dev<double, double> d = h->d64;
     d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
-    d.trace = trace; d.trace_len = trace_len;
+    d.trace = trace; d.trace_len = trace_len; d.sched = sched; d.sched_len = sched_len;
     e = launch_eval<double, double>(d, h->plan, x, adam, h->stream, ev);
   }
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("evaluation launch: ") + cudaGetErrorString(e));
@@ -1216,15 +1219,24 @@ int qg_adam_step(qg_ctx *h, void *x, void *m, void *v, double lr, double beta1, 
   return run_adam(h, x, m, v, lr, beta1, beta2);
 }
 
-int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace) {
+}  // extern "C"
+
+namespace {
+
+// qg_solve and qg_solve_schedule: replay the cached graph of one (evaluation + fused Adam)
+// iteration `iters` times, capturing it first when the arguments differ from the cached ones.
+int solve_graph(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace,
+                const double *sched) {
   if (!h || !x || iters < 0) return h ? fail(h, QG_ERR_INVALID_ARG, "bad solve arguments") : QG_ERR_INVALID_ARG;
   if (!(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1))
     return fail(h, QG_ERR_INVALID_ARG, "Adam parameters out of range");
   if (iters == 0) return QG_OK;
-  // the trace is indexed by (step - step at the start of this call)
-  if (obj_trace) CUDA_TRY(h, cudaMemcpyAsync(h->d_step0, h->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
+  // the trace and the schedule are indexed by (step - step at the start of this call)
+  if (obj_trace || sched)
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_step0, h->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
+  const int len = (obj_trace || sched) ? iters : 0;
   const bool same = h->gexec && h->g_x == x && h->g_lr == lr && h->g_b1 == beta1 && h->g_b2 == beta2 &&
-                    h->g_trace == obj_trace && (obj_trace == nullptr || h->g_trace_len >= iters);
+                    h->g_trace == obj_trace && h->g_sched == sched && h->g_trace_len == len;
   if (!same) {
     if (h->gexec) {
       cudaGraphExecDestroy(h->gexec);
@@ -1238,7 +1250,7 @@ int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double 
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int rc = QG_OK;
     if (e == cudaSuccess) {
-      rc = run_eval(h, x, true, lr, beta1, beta2, obj_trace, obj_trace ? iters : 0);
+      rc = run_eval(h, x, true, lr, beta1, beta2, obj_trace, obj_trace ? len : 0, sched, sched ? len : 0);
       cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
       if (!rc && e2 == cudaSuccess) {
         e = cudaGraphInstantiate(&h->gexec, graph, 0);
@@ -1251,10 +1263,44 @@ int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double 
     cudaStreamDestroy(cs);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    h->g_x = x; h->g_lr = lr; h->g_b1 = beta1; h->g_b2 = beta2; h->g_trace = obj_trace;
-    h->g_trace_len = obj_trace ? iters : 0;
+    h->g_x = x; h->g_lr = lr; h->g_b1 = beta1; h->g_b2 = beta2; h->g_trace = obj_trace; h->g_sched = sched;
+    h->g_trace_len = len;
   }
   for (int it = 0; it < iters; ++it) CUDA_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
+  return QG_OK;
+}
+
+// Reflected sigmoid of Eq. mag_scale.
+double mag_scale(double t) {
+  const double e = std::exp(4.0 * t);
+  return e / (0.6 + e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace) {
+  return solve_graph(h, x, iters, lr, beta1, beta2, obj_trace, nullptr);
+}
+
+int qg_solve_schedule(qg_ctx *h, void *x, int32_t iters, const double *sched, double beta1, double beta2,
+                      double *obj_trace) {
+  if (!sched) return h ? fail(h, QG_ERR_INVALID_ARG, "sched is NULL") : QG_ERR_INVALID_ARG;
+  return solve_graph(h, x, iters, 0.0, beta1, beta2, obj_trace, sched);
+}
+
+int qg_schedule(double *out, int32_t iters, double lr0, double lrf, double eps0, double epsf, double beta0,
+                double beta1, double lag) {
+  if (!out || iters < 1 || !(lr0 > 0) || !(lrf > 0) || !(eps0 > 0) || !(epsf > 0) || !std::isfinite(beta0) ||
+      !std::isfinite(beta1) || !std::isfinite(lag))
+    return QG_ERR_INVALID_ARG;
+  for (int i = 0; i < iters; ++i) {
+    const double t = iters > 1 ? 2.0 * i / (iters - 1) - 1.0 : -1.0;  // Eq. norm_t on the iteration fraction
+    out[3 * i + 0] = lr0 * std::pow(10.0, mag_scale(t) * std::log10(lrf / lr0));          // Eq. step_size
+    out[3 * i + 1] = eps0 * std::pow(10.0, mag_scale(t - lag) * std::log10(epsf / eps0));  // tightening
+    out[3 * i + 2] = beta0 + (beta1 - beta0) * 0.5 * (t + 1.0);                               // homotopy
+  }
   return QG_OK;
 }
 

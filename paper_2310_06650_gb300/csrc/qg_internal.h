@@ -47,7 +47,7 @@ struct Inst {
   long long xtau0;       // first tau variable (x0 + T (2n + 3G)); phi follow after T X
   double inv_n;          // 1 / n
   double hours;          // sum of dt
-  double wfloor_ctg;     // c_s * beta * eps * (M K - K): soft-ReLU floor of the contingency term per hour
+  double nfloor_ctg;     // M K - K: elements whose soft-ReLU floor eps the contingency term adds in closed form
   int obj_lo, obj_n;     // this instance's stage-1/2 objective slots
   int gen_first, gen_nb; // its generator blocks: first block in their launch, count
   int gen_slot0;         // first reduction slot of those blocks (after the stage-1/2 slots)
@@ -142,6 +142,7 @@ struct Dev {
   unsigned int *sp_tick;              // [tail row tiles] last-split tickets (zero between launches)
   // penalty parameters
   Real c_p, c_q, c_s, c_rz, rho, eps, beta;
+  double c_s64, eps64, beta64;        // the same options in FP64 (closed-form objective floor)
   int lodf_dtype;
   // work buffers
   Real *pf, *qf, *pt, *qt, *qm2;      // [sum T M]
@@ -170,6 +171,8 @@ struct Dev {
   Real *am, *av;
   double lr, b1, b2, aeps;
   int paper_eps;
+  const double *sched;                // optional per-iteration (lr, eps, beta) of a scheduled solve, [sched_len][3]
+  int sched_len;
   double *trace;                      // optional objective trace (qg_solve), [trace_len][n_inst]
   long long *trace_step0;             // step count at the start of the traced solve
   int trace_len;

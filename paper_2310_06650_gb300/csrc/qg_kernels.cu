@@ -238,6 +238,26 @@ struct Where {
   int role, inst, t, sub;
 };
 
+// Penalty smoothing eps and homotopy scale beta of this evaluation (Sec. II-F): the handle's options,
+// or iteration i of a scheduled solve (i counted from the step at the start of that solve).
+template <typename Real>
+struct HP {
+  Real eps, beta;
+};
+
+template <typename Real, typename Dc>
+__device__ __forceinline__ long long sched_index(const Dev<Real, Dc> &d) {
+  long long it = *d.step - *d.trace_step0;
+  return it < 0 ? 0 : (it >= d.sched_len ? d.sched_len - 1 : it);
+}
+
+template <typename Real, typename Dc>
+__device__ __forceinline__ HP<Real> hparams(const Dev<Real, Dc> &d) {
+  if (!d.sched) return {d.eps, d.beta};
+  const long long it = sched_index(d);
+  return {(Real)d.sched[3 * it + 1], (Real)d.sched[3 * it + 2]};
+}
+
 // Block -> (role, instance, period or period chunk, slice) by binary search over the spans.
 __device__ __forceinline__ Where locate(const Spans &S) {
   const int bid = blockIdx.x;
@@ -294,7 +314,7 @@ constexpr int GBC = 128;  // generator-bus chunk of the DC products
 
 template <typename Real, typename Dc>
 __device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
-                          Obj3<Dc> &acc) {
+                          Obj3<Dc> &acc, const HP<Real> hp) {
   const int j = sub * NTHR + threadIdx.x;
   if (j >= I.M) return;
   const int jg = I.br0 + j;
@@ -331,19 +351,19 @@ __device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub,
   d.qside[e] = qto ? 1 : 0;
   // thermal penalty on the worse end (Example 1)
   const Real sm2 = fmax(pf * pf + qf * qf, pt * pt + qt * qt);
-  Real val = d.eps;
+  Real val = hp.eps;
   if (sm2 > smax * smax) {
     Real der;
-    soft_relu(dsqrt(sm2) - smax, d.eps, val, der);
+    soft_relu(dsqrt(sm2) - smax, hp.eps, val, der);
   }
-  acc.v[0] = DcOps<Dc>::from_real(d.dt[I.tp0 + t] * d.c_s * d.beta * val);
+  acc.v[0] = DcOps<Dc>::from_real(d.dt[I.tp0 + t] * d.c_s * hp.beta * val);
 }
 
 // Zonal reserve shortfall of zone `sub` in period t: the block sums the zone's reserve
 // offers (fixed order), then sigma_s(R_zt - sum r) and its derivative.
 template <typename Real, typename Dc>
 __device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, const Real *__restrict__ x,
-                        Obj3<Dc> &acc) {
+                        Obj3<Dc> &acc, const HP<Real> hp) {
   __shared__ Real red[NTHR / 32];
   const int zg = I.zone0 + z;  // global zone id; zgen_ptr is one CSR over all zones of the batch
   const Real *r = x + I.x0 + 2LL * I.T * I.n + 2LL * I.T * I.G + (long long)t * I.G;
@@ -359,8 +379,8 @@ __device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, con
     for (int w = 0; w < NTHR / 32; ++w) tot += red[w];
     const long long k = I.tz0 + (long long)t * I.Z + z;
     Real val, der;
-    soft_relu(d.rreq[k] - tot, d.eps, val, der);
-    const Real w = d.dt[I.tp0 + t] * d.c_rz * d.beta;
+    soft_relu(d.rreq[k] - tot, hp.eps, val, der);
+    const Real w = d.dt[I.tp0 + t] * d.c_rz * hp.beta;
     d.dZ[k] = w * der;
     acc.v[0] = DcOps<Dc>::from_real(w * val);
   }
@@ -493,10 +513,10 @@ __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, D
     s1_sdcf(d, I, w.t, w.sub, x);
   } else if (w.role == R_BRANCH) {
     acc.id[0] = T_ZS;
-    s1_branch(d, I, w.t, w.sub, x, acc);
+    s1_branch(d, I, w.t, w.sub, x, acc, hparams(d));
   } else {
     acc.id[0] = T_ZRZ;
-    s1_zone(d, I, w.t, w.sub, x, acc);
+    s1_zone(d, I, w.t, w.sub, x, acc, hparams(d));
   }
   write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
 }
@@ -509,7 +529,7 @@ __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, D
 // warp-segmented reduction over the bus's CSR entries; soft-abs penalty and its derivative.
 template <typename Real, typename Dc>
 __device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
-                       Obj3<Dc> &acc) {
+                       Obj3<Dc> &acc, const HP<Real> hp) {
   const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
   if (pk >= I.n_bal_pack) return;  // whole warp
   const int e = I.bal0 + pk * PACK + (threadIdx.x & 31);
@@ -533,10 +553,10 @@ __device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, co
     P += d.load_p[ti];
     Q += d.load_q[ti];
     Real vp, dp, vq, dq;
-    soft_abs(P, d.eps, vp, dp);
-    soft_abs(Q, d.eps, vq, dq);
+    soft_abs(P, hp.eps, vp, dp);
+    soft_abs(Q, hp.eps, vq, dq);
     const Real dt = d.dt[I.tp0 + t];
-    const Real wp = dt * d.c_p * d.beta, wq = dt * d.c_q * d.beta;
+    const Real wp = dt * d.c_p * hp.beta, wq = dt * d.c_q * hp.beta;
     d.dP[ti] = wp * dp;
     d.dQ[ti] = wq * dq;
     acc.v[0] = DcOps<Dc>::from_real(wp * vp);
@@ -584,7 +604,7 @@ __host__ __device__ constexpr int ctg_tch() { return 8; }
 // shared memory, accumulated over the group's tiles and written to pk per group.  The soft-ReLU
 // floor eps of every non-violating element is added in closed form by the final reduction.
 template <typename Real, typename Dc>
-__device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> &acc) {
+__device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> &acc, const HP<Real> hp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
@@ -610,7 +630,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   for (int e = threadIdx.x; e < TCH * CT_BM; e += NTHR) s_gm[e] = s_gq[e] = 0;
   for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gk[e] = 0;
   Real obj = 0;
-  const Real eps = d.eps;
+  const Real eps = hp.eps;
   for (int mt = mt0; mt < mt1; ++mt) {
     const int m0 = mt * CT_BM;
     // the line-outage block does not depend on stage 1 (the first tile loads before waiting)
@@ -681,7 +701,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           }
         if (!__any_sync(0xffffffffu, mx > 0.f)) continue;
         // a (candidate) post-contingency overload in this warp
-        const Real w = d.dt[I.tp0 + t] * d.c_s * d.beta;
+        const Real w = d.dt[I.tp0 + t] * d.c_s * hp.beta;
         Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0};
         if (mx > 0.f) {
 #pragma unroll
@@ -776,10 +796,10 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
     acc.id[0] = T_ZP;
     acc.id[1] = T_ZQ;
     pdl_wait();
-    s2_bus(d, I, w.t, w.sub, x, acc);
+    s2_bus(d, I, w.t, w.sub, x, acc, hparams(d));
   } else {
     acc.id[0] = T_ZCTG;
-    s2_ctg(d, I, w.sub, acc);
+    s2_ctg(d, I, w.sub, acc, hparams(d));
   }
   write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
 }
@@ -829,8 +849,9 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
       const Real sf = dsqrt(sf2), st = dsqrt(st2);
       const bool fr = sf >= st;
       Real val, der;
-      soft_relu((fr ? sf : st) - smax, d.eps, val, der);
-      const Real k = d.dt[I.tp0 + t] * d.c_s * d.beta * der / (fr ? sf : st);
+      const HP<Real> hp = hparams(d);
+      soft_relu((fr ? sf : st) - smax, hp.eps, val, der);
+      const Real k = d.dt[I.tp0 + t] * d.c_s * hp.beta * der / (fr ? sf : st);
       if (fr) {
         gpf += k * pf;
         gqf += k * qf;
@@ -897,10 +918,13 @@ __device__ __forceinline__ void bias_corr(double b1, double b2, long long step, 
 
 template <typename Real, typename Dc>
 __device__ AdamCoef<Real> adam_coef(const Dev<Real, Dc> &d) {
-  __shared__ Real sc[2];
-  if (threadIdx.x == 0) bias_corr(d.b1, d.b2, *d.step, sc[0], sc[1]);
+  __shared__ Real sc[3];
+  if (threadIdx.x == 0) {
+    bias_corr(d.b1, d.b2, *d.step, sc[0], sc[1]);
+    sc[2] = (Real)(d.sched ? d.sched[3 * sched_index(d)] : d.lr);  // step size (Eq. step_size schedule)
+  }
   __syncthreads();
-  return {(Real)d.b1, (Real)d.b2, sc[0], sc[1], (Real)d.lr, (Real)d.aeps};
+  return {(Real)d.b1, (Real)d.b2, sc[0], sc[1], sc[2], (Real)d.aeps};
 }
 
 template <typename Real, typename Dc, bool ADAM>
@@ -1011,7 +1035,15 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
       double tot = 0.0;
       for (int k = 0; k < N_TERMS; ++k) {
         double tv = to_double(a[k]);
-        if (k == T_ZCTG) tv += tab.I[b].hours * tab.I[b].wfloor_ctg;
+        if (k == T_ZCTG) {
+          double eps = d.eps64, beta = d.beta64;
+          if (d.sched) {
+            const long long it = sched_index(d);
+            eps = d.sched[3 * it + 1];
+            beta = d.sched[3 * it + 2];
+          }
+          tv += tab.I[b].hours * d.c_s64 * beta * eps * tab.I[b].nfloor_ctg;
+        }
         d.terms[b * N_TERMS + k] = tv;
         tot += tv;
       }
@@ -1077,9 +1109,10 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
   const Real gq = -d.dQ[tb + g.bus];
   Real gr = dt * g.cr - d.dZ[I.tz0 + (long long)t * I.Z + g.zn];
   acc.v[0] = DcOps<Dc>::from_real(dt * (g.a * p * p + g.bl * p + g.cr * r));
-  const Real wr = d.rho * d.beta;
+  const HP<Real> hp = hparams(d);
+  const Real wr = d.rho * hp.beta;
   Real val, der;
-  soft_relu(p + r - g.pmax, d.eps, val, der);
+  soft_relu(p + r - g.pmax, hp.eps, val, der);
   acc.v[1] = DcOps<Dc>::from_real(wr * val);
   gp += wr * der;
   gr += wr * der;
@@ -1088,8 +1121,8 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
     const Real pp = ADAM ? d.pold[ko - G] : x[g.kp - G];
     const Real lim = g.ramp * dt;
     Real v1, d1, v2, d2;
-    soft_relu(p - pp - lim, d.eps, v1, d1);
-    soft_relu(pp - p - lim, d.eps, v2, d2);
+    soft_relu(p - pp - lim, hp.eps, v1, d1);
+    soft_relu(pp - p - lim, hp.eps, v2, d2);
     acc.v[2] = DcOps<Dc>::from_real(wr * (v1 + v2));
     gp += wr * (d1 - d2);
   }
@@ -1097,8 +1130,8 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
     const Real pn = ADAM ? d.pold[ko + G] : x[g.kp + G];
     const Real lim = g.ramp * d.dt[I.tp0 + t + 1];
     Real v1, d1, v2, d2;
-    soft_relu(pn - p - lim, d.eps, v1, d1);
-    soft_relu(p - pn - lim, d.eps, v2, d2);
+    soft_relu(pn - p - lim, hp.eps, v1, d1);
+    soft_relu(p - pn - lim, hp.eps, v2, d2);
     gp += wr * (d2 - d1);
   }
   if (ADAM) {

@@ -88,6 +88,9 @@ def _load():
         "qg_last_error": (C.c_char_p, [vp]),
         "qg_version": (C.c_int, []),
         "qg_launches_per_eval": (C.c_int32, [vp]),
+        "qg_solve_schedule": (C.c_int, [vp, vp, C.c_int32, vp, C.c_double, C.c_double, vp]),
+        "qg_schedule": (C.c_int, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, C.c_double]),
         "qg_mlp_create": (C.c_int, [C.POINTER(vp), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64]),
         "qg_mlp_destroy": (None, [vp]),
         "qg_mlp_num_params": (C.c_int64, [vp]),
@@ -110,6 +113,7 @@ _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_eval_grad_noalloc", "qg_adam_step", "qg_solve", "qg_breakdown",
             "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_launches_per_eval",
+            "qg_solve_schedule", "qg_schedule",
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
@@ -246,6 +250,22 @@ def qg_adam_step(h: int, x, m, v, lr: float, beta1: float = 0.9, beta2: float = 
 
 def qg_solve(h: int, x, iters: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, obj_trace=None) -> None:
     _check(_lib.qg_solve(h, _ptr(x), iters, lr, beta1, beta2, _ptr(obj_trace)), h)
+
+
+def qg_solve_schedule(h: int, x, iters: int, sched, beta1: float = 0.9, beta2: float = 0.999,
+                      obj_trace=None) -> None:
+    """sched: device tensor of iters x 3 doubles (lr, eps, beta per iteration)."""
+    _check(_lib.qg_solve_schedule(h, _ptr(x), iters, _ptr(sched), beta1, beta2, _ptr(obj_trace)), h)
+
+
+def qg_schedule(iters: int, lr0: float, lrf: float, eps0: float, epsf: float, beta0: float = 0.1,
+                beta1: float = 1.0, lag: float = 0.25) -> np.ndarray:
+    """The Sec. II-F schedule table (host, iters x 3: lr, eps, beta) computed by the library."""
+    out = np.zeros((iters, 3))
+    rc = _lib.qg_schedule(out.ctypes.data_as(C.c_void_p), iters, lr0, lrf, eps0, epsf, beta0, beta1, lag)
+    if rc != QG_OK:
+        raise QGError(rc, "qg_schedule: invalid arguments")
+    return out
 
 
 def qg_breakdown(h: int, n_inst: int = 1) -> np.ndarray:

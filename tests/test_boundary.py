@@ -7,6 +7,7 @@ import re
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -152,3 +153,16 @@ def test_transformer_case_reaches_device_check(qg):
     c = synth.with_transformers(synth.mid(), 0.15, 5)
     for dc in (qg.QG_DC_DENSE, qg.QG_DC_SPARSE):
         _expect(qg, c, qg.QG_ERR_NO_DEVICE, dc_solver=dc)
+
+
+@pytest.mark.parametrize("iters", [1, 2, 7, 500])
+def test_library_schedule_matches_the_closed_forms(qg, iters):
+    """qg_schedule (host code of the library) against Eqs. norm_t, mag_scale and step_size as the
+    oracle writes them (pinned in test_oracle_pins), plus the eps lag and the linear beta."""
+    got = qg.qg_schedule(iters, 5e-3, 1e-5, 1e-1, 1e-5, 0.1, 1.0, 0.25)
+    ref = oracle.schedule_table(iters, 5e-3, 1e-5, 1e-1, 1e-5, 0.1, 1.0, 0.25)
+    assert np.allclose(got, ref, rtol=1e-13, atol=0)
+    assert got[0, 2] == pytest.approx(0.1) and got[-1, 2] == pytest.approx(1.0 if iters > 1 else 0.1)
+    assert np.all(np.diff(got[:, 0]) <= 0) and np.all(np.diff(got[:, 1]) <= 0)
+    with pytest.raises(qg.QGError):
+        qg.qg_schedule(0, 5e-3, 1e-5, 1e-1, 1e-5)
