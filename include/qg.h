@@ -190,13 +190,16 @@ int qg_adam_step(qg_ctx *h, void *x, void *m, void *v, double lr, double beta1, 
  * evaluated at the start of each iteration. */
 int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace);
 
-/* qg_solve with the schedules of Sec. II-F: iteration i of this call (i = 0 .. iters - 1) takes its
- * Adam step size, soft-abs / soft-ReLU epsilon and homotopy scale beta from sched[3 i .. 3 i + 2]
- * (device array of iters x 3 doubles: lr, eps, beta; e.g. written by qg_schedule), in place of lr
- * and of the handle's eps and beta options.  obj_trace records each iteration's objective at its own
- * eps and beta.  The graph is re-captured when x, sched, beta1, beta2, obj_trace or iters change. */
-int qg_solve_schedule(qg_ctx *h, void *x, int32_t iters, const double *sched, double beta1, double beta2,
-                      double *obj_trace);
+/* qg_solve with the schedules of Sec. II-F: iteration i of a scheduled run takes its Adam step size,
+ * soft-abs / soft-ReLU epsilon and homotopy scale beta from sched[3 i .. 3 i + 2] (device array of
+ * sched_len x 3 doubles: lr, eps, beta; e.g. written by qg_schedule; rows past the end repeat the
+ * last), in place of lr and of the handle's eps and beta options.  A run starts at a call with
+ * restart != 0 (i = 0 at its first iteration); calls with restart = 0 continue the run, so it can
+ * be driven in chunks.  obj_trace (device, sched_len x n_inst doubles, may be NULL) receives each
+ * iteration's objective at its own eps and beta, indexed by i.  The graph is re-captured when x,
+ * sched, sched_len, beta1, beta2 or obj_trace change; a changed iters or restart does not. */
+int qg_solve_schedule(qg_ctx *h, void *x, int32_t iters, const double *sched, int32_t sched_len, int32_t restart,
+                      double beta1, double beta2, double *obj_trace);
 
 /* The per-iteration schedule of Sec. II-F for `iters` iterations, written to out (host, iters x 3
  * doubles).  Time is the iteration fraction (reading of the wall-clock time of Eq. norm_t):

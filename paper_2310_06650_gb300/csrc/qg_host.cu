@@ -1226,15 +1226,15 @@ namespace {
 // qg_solve and qg_solve_schedule: replay the cached graph of one (evaluation + fused Adam)
 // iteration `iters` times, capturing it first when the arguments differ from the cached ones.
 int solve_graph(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace,
-                const double *sched) {
+                const double *sched, int len, bool restart) {
   if (!h || !x || iters < 0) return h ? fail(h, QG_ERR_INVALID_ARG, "bad solve arguments") : QG_ERR_INVALID_ARG;
   if (!(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1))
     return fail(h, QG_ERR_INVALID_ARG, "Adam parameters out of range");
   if (iters == 0) return QG_OK;
-  // the trace and the schedule are indexed by (step - step at the start of this call)
-  if (obj_trace || sched)
+  // the trace and the schedule are indexed by (step - step at the origin of the run)
+  if ((obj_trace || sched) && restart)
     CUDA_TRY(h, cudaMemcpyAsync(h->d_step0, h->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
-  const int len = (obj_trace || sched) ? iters : 0;
+  if (!obj_trace && !sched) len = 0;
   const bool same = h->gexec && h->g_x == x && h->g_lr == lr && h->g_b1 == beta1 && h->g_b2 == beta2 &&
                     h->g_trace == obj_trace && h->g_sched == sched && h->g_trace_len == len;
   if (!same) {
@@ -1281,13 +1281,13 @@ double mag_scale(double t) {
 extern "C" {
 
 int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace) {
-  return solve_graph(h, x, iters, lr, beta1, beta2, obj_trace, nullptr);
+  return solve_graph(h, x, iters, lr, beta1, beta2, obj_trace, nullptr, iters, true);
 }
 
-int qg_solve_schedule(qg_ctx *h, void *x, int32_t iters, const double *sched, double beta1, double beta2,
-                      double *obj_trace) {
-  if (!sched) return h ? fail(h, QG_ERR_INVALID_ARG, "sched is NULL") : QG_ERR_INVALID_ARG;
-  return solve_graph(h, x, iters, 0.0, beta1, beta2, obj_trace, sched);
+int qg_solve_schedule(qg_ctx *h, void *x, int32_t iters, const double *sched, int32_t sched_len, int32_t restart,
+                      double beta1, double beta2, double *obj_trace) {
+  if (!sched || sched_len < 1) return h ? fail(h, QG_ERR_INVALID_ARG, "empty schedule") : QG_ERR_INVALID_ARG;
+  return solve_graph(h, x, iters, 0.0, beta1, beta2, obj_trace, sched, sched_len, restart != 0);
 }
 
 int qg_schedule(double *out, int32_t iters, double lr0, double lrf, double eps0, double epsf, double beta0,

@@ -88,7 +88,7 @@ def _load():
         "qg_last_error": (C.c_char_p, [vp]),
         "qg_version": (C.c_int, []),
         "qg_launches_per_eval": (C.c_int32, [vp]),
-        "qg_solve_schedule": (C.c_int, [vp, vp, C.c_int32, vp, C.c_double, C.c_double, vp]),
+        "qg_solve_schedule": (C.c_int, [vp, vp, C.c_int32, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, vp]),
         "qg_schedule": (C.c_int, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                   C.c_double, C.c_double]),
         "qg_mlp_create": (C.c_int, [C.POINTER(vp), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64]),
@@ -252,10 +252,11 @@ def qg_solve(h: int, x, iters: int, lr: float, beta1: float = 0.9, beta2: float 
     _check(_lib.qg_solve(h, _ptr(x), iters, lr, beta1, beta2, _ptr(obj_trace)), h)
 
 
-def qg_solve_schedule(h: int, x, iters: int, sched, beta1: float = 0.9, beta2: float = 0.999,
-                      obj_trace=None) -> None:
-    """sched: device tensor of iters x 3 doubles (lr, eps, beta per iteration)."""
-    _check(_lib.qg_solve_schedule(h, _ptr(x), iters, _ptr(sched), beta1, beta2, _ptr(obj_trace)), h)
+def qg_solve_schedule(h: int, x, iters: int, sched, restart: bool = True, beta1: float = 0.9,
+                      beta2: float = 0.999, obj_trace=None) -> None:
+    """sched: device tensor of L x 3 doubles (lr, eps, beta per iteration of the run)."""
+    _check(_lib.qg_solve_schedule(h, _ptr(x), iters, _ptr(sched), int(sched.shape[0]), 1 if restart else 0,
+                                  beta1, beta2, _ptr(obj_trace)), h)
 
 
 def qg_schedule(iters: int, lr0: float, lrf: float, eps0: float, epsf: float, beta0: float = 0.1,

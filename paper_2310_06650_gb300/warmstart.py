@@ -107,16 +107,32 @@ def clip_box(case, x: np.ndarray) -> np.ndarray:
 # data generation: batched Adam solves
 # ------------------------------------------------------------------------------------------------
 
+# Sec. II-F schedule used by the solves below (lr0, lrf, eps0, epsf, beta0, beta1, lag): the step size
+# decays over three decades, the smoothing over four, and the homotopy scale rises from 0.1 to 1.
+SCHEDULE = (1e-2, 1e-5, 5e-2, 1e-5, 0.1, 1.0, 0.25)
+
+
+def schedule_table(iters: int, spec=SCHEDULE):
+    """Device table (iters x 3: lr, eps, beta) of the Sec. II-F schedule, written by the library."""
+    import torch
+    return torch.tensor(qg.qg_schedule(iters, *spec), dtype=torch.float64, device="cuda")
+
+
 def solve_many(cases: Sequence, x0s: Sequence[np.ndarray], iters: int, lr: float = 1e-3,
-               precision: int = qg.QG_MIXED) -> List[np.ndarray]:
-    """Adam solves of many instances, BATCH per handle, from the given starts."""
+               precision: int = qg.QG_MIXED, schedule=None) -> List[np.ndarray]:
+    """Adam solves of many instances, BATCH per handle, from the given starts; with a schedule spec,
+    the Sec. II-F step-size and homotopy schedules over the iterations instead of a constant lr."""
     import torch
     out = []
+    table = schedule_table(iters, schedule) if schedule else None
     for b0 in range(0, len(cases), BATCH):
         cs = list(cases[b0:b0 + BATCH])
         s = qg.Solver(cs, precision=precision)
         x = torch.tensor(np.concatenate(x0s[b0:b0 + BATCH]), dtype=s.dtype, device="cuda")
-        qg.qg_solve(s.h, x, iters, lr, 0.9, 0.999)
+        if table is not None:
+            qg.qg_solve_schedule(s.h, x, iters, table, True, 0.9, 0.999)
+        else:
+            qg.qg_solve(s.h, x, iters, lr, 0.9, 0.999)
         xs = x.double().cpu().numpy()
         o = 0
         for c in cs:
@@ -198,25 +214,35 @@ def objective_eps0(scorer, x_dev) -> float:
     return float(obj[0].item())
 
 
-def solve_trace(case, x0: np.ndarray, precision: int, iters: int, every: int, lr: float = 1e-3):
-    """Single-instance Adam solve; returns (gpu_ms_per_chunk list, eps=0 objective after each chunk).
-    The scoring evaluations run on a separate FP64 handle and are not timed."""
+def solve_trace(case, x0: np.ndarray, precision: int, iters: int, every: int, lr: float = 1e-3, table=None,
+                t_start_ms: float = 0.0):
+    """Single-instance Adam solve; returns (cumulative GPU ms after each chunk, eps = 0 objective
+    after each chunk).  With a schedule table (device, rows x 3) the run follows it from its first
+    row.  The scoring evaluations run on a separate FP64 handle and are not timed; t_start_ms (e.g.
+    the MLP inference that produced x0) is added to every time."""
     torch = __import__("torch")
     s = qg.Solver(case, precision=precision)
     scorer = qg.Solver(case, precision=qg.QG_FP64, eps=0.0)
     x = torch.tensor(x0, dtype=s.dtype, device="cuda")
     xs = torch.zeros(case.n_x, dtype=torch.float64, device="cuda")
-    qg.qg_solve(s.h, x, 1, lr, 0.9, 0.999)  # capture the graph outside the timed chunks
+
+    def run(n, first):
+        if table is not None:
+            qg.qg_solve_schedule(s.h, x, n, table, first, 0.9, 0.999)
+        else:
+            qg.qg_solve(s.h, x, n, lr, 0.9, 0.999)
+
+    run(every, True)  # capture the graph outside the timed chunks
     qg.qg_set_step(s.h, 0)
     x.copy_(torch.tensor(x0, dtype=s.dtype, device="cuda"))
     times, objs = [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     xs.copy_(x)
     objs.append(objective_eps0(scorer, xs))
-    times.append(0.0)
-    for _ in range(0, iters, every):
+    times.append(t_start_ms)
+    for k in range(0, iters, every):
         e0.record()
-        qg.qg_solve(s.h, x, every, lr, 0.9, 0.999)
+        run(every, k == 0)
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -237,17 +263,23 @@ def time_to(times_ms: np.ndarray, objs: np.ndarray, target: float) -> float:
 # ------------------------------------------------------------------------------------------------
 
 def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, eval_iters: int, every: int,
-               seed: int = 5000, hidden: int = 1024, log=print) -> dict:
+               seed: int = 5000, hidden: int = 1024, schedule=SCHEDULE, warm_skip: float = 0.25,
+               const_arm: bool = False, log=print) -> dict:
     """Train on n_train generated solves, then for n_test held-out profiles compare
     (a) plain FP64 Adam from the copper-plate start with (b) mixed-precision Adam from the learned
     start, on GPU time to an objective within 1% of the copper-plate bound (eps = 0 scoring).  When
-    arm (a) misses that target, the target becomes the best objective arm (a) reaches."""
+    arm (a) misses that target within eval_iters, the target becomes the best objective arm (a)
+    reaches.  Both arms follow the Sec. II-F schedule of eval_iters iterations (schedule=None: a
+    constant lr of 1e-3); arm (b) enters it after the first warm_skip fraction (the learned start
+    takes the place of the early large steps) and its time includes the MLP inference.  const_arm
+    adds, for context, plain FP64 Adam with a constant lr of 1e-3."""
     import synth
+    torch = __import__("torch")
     t0 = time.time()
     prof = synth.load_profiles(case, n_train + n_test, seed)
     cases = [synth.with_loads(case, lp) for lp in prof]
     starts = [start_point(c) for c in cases]
-    sols = solve_many(cases[:n_train], starts[:n_train], solve_iters)
+    sols = solve_many(cases[:n_train], starts[:n_train], solve_iters, schedule=schedule)
     t_gen = time.time() - t0
     log(f"generated {n_train} solves in {t_gen:.1f} s")
     ws = WarmStart(case, hidden=hidden, seed=seed)
@@ -255,30 +287,46 @@ def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, e
     hist = ws.train(prof[:n_train], starts[:n_train], sols, epochs)
     t_train = time.time() - t1
     log(f"trained {epochs} epochs in {t_train:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}")
-    preds = ws.predict(prof[n_train:], starts[n_train:])
+    table = schedule_table(eval_iters, schedule) if schedule else None
+    skip = int(round(warm_skip * eval_iters)) if schedule else 0
+    table_b = table[skip:].contiguous() if table is not None else None
     rows = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for i in range(n_test):
         c = cases[n_train + i]
         bound = merit_order_bound(c)
-        ta, oa = solve_trace(c, starts[n_train + i], qg.QG_FP64, eval_iters, every)
-        tb, ob = solve_trace(c, preds[i], qg.QG_MIXED, eval_iters, every)
+        e0.record()
+        pred = ws.predict(prof[n_train + i:n_train + i + 1], starts[n_train + i:n_train + i + 1])[0]
+        e1.record()
+        e1.synchronize()
+        t_mlp = e0.elapsed_time(e1)
+        ta, oa = solve_trace(c, starts[n_train + i], qg.QG_FP64, eval_iters, every, table=table)
+        tb, ob = solve_trace(c, pred, qg.QG_MIXED, eval_iters, every, table=table_b, t_start_ms=t_mlp)
         target = 1.01 * bound
         kind = "1% of copper-plate bound"
         if not np.isfinite(time_to(ta, oa, target)):
             target = float(oa.min())
             kind = "best objective of plain FP64 Adam"
-        rows.append({"bound": bound, "target": target, "target_kind": kind,
-                     "plain_fp64": {"ms": time_to(ta, oa, target), "phi0": float(oa[0]), "best": float(oa.min())},
-                     "warm_mixed": {"ms": time_to(tb, ob, target), "phi0": float(ob[0]), "best": float(ob.min())}})
-        log(rows[-1])
+        row = {"bound": bound, "target": target, "target_kind": kind, "mlp_ms": t_mlp,
+               "plain_fp64": {"ms": time_to(ta, oa, target), "phi0": float(oa[0]), "best": float(oa.min()),
+                              "ms_total": float(ta[-1])},
+               "warm_mixed": {"ms": time_to(tb, ob, target), "phi0": float(ob[0]), "best": float(ob.min()),
+                              "ms_total": float(tb[-1])}}
+        if const_arm:
+            tc, oc = solve_trace(c, starts[n_train + i], qg.QG_FP64, eval_iters, every)
+            row["plain_fp64_const_lr"] = {"ms": time_to(tc, oc, target), "best": float(oc.min())}
+        rows.append(row)
+        log(row)
     ws.close()
     fin = [r for r in rows if np.isfinite(r["plain_fp64"]["ms"]) and np.isfinite(r["warm_mixed"]["ms"])]
     return {"n_train": n_train, "n_test": n_test, "solve_iters": solve_iters, "epochs": epochs,
-            "eval_iters": eval_iters, "every": every, "gen_s": t_gen, "train_s": t_train,
+            "eval_iters": eval_iters, "every": every, "schedule": list(schedule) if schedule else None,
+            "warm_skip": warm_skip if schedule else 0.0, "gen_s": t_gen, "train_s": t_train,
             "loss_first": hist[0], "loss_last": hist[-1], "rows": rows,
             "median_ms_plain": float(np.median([r["plain_fp64"]["ms"] for r in fin])) if fin else None,
             "median_ms_warm": float(np.median([r["warm_mixed"]["ms"] for r in fin])) if fin else None,
-            "warm_faster": int(sum(r["warm_mixed"]["ms"] < r["plain_fp64"]["ms"] for r in rows))}
+            "warm_faster": int(sum(r["warm_mixed"]["ms"] < r["plain_fp64"]["ms"] for r in rows)),
+            "reached_1pct": int(sum(r["target_kind"].startswith("1%") for r in rows))}
 
 
 def main(argv=None):
@@ -291,16 +339,20 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="learned warm start vs plain FP64 Adam")
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--test", type=int, default=8)
-    ap.add_argument("--solve-iters", type=int, default=3000)
+    ap.add_argument("--solve-iters", type=int, default=5000)
     ap.add_argument("--epochs", type=int, default=40)
-    ap.add_argument("--eval-iters", type=int, default=6000)
-    ap.add_argument("--every", type=int, default=25)
+    ap.add_argument("--eval-iters", type=int, default=20000)
+    ap.add_argument("--every", type=int, default=100)
     ap.add_argument("--hidden", type=int, default=1024)
+    ap.add_argument("--warm-skip", type=float, default=0.25)
+    ap.add_argument("--constant-lr", action="store_true", help="constant lr 1e-3 instead of the Sec. II-F schedule")
+    ap.add_argument("--const-arm", action="store_true", help="add plain FP64 Adam at a constant lr for context")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     from .build import build
     build()
     res = experiment(synth.rt617(), a.train, a.test, a.solve_iters, a.epochs, a.eval_iters, a.every, hidden=a.hidden,
+                     schedule=None if a.constant_lr else SCHEDULE, warm_skip=a.warm_skip, const_arm=a.const_arm,
                      log=lambda *s: print(*s, flush=True))
     line = json.dumps(res)
     print(line)

@@ -40,7 +40,9 @@ def test_scheduled_solve_matches_oracle_loop(qg, mk, dc):
     xt = torch.tensor(x0, dtype=torch.float64, device="cuda")
     st = torch.tensor(sched, dtype=torch.float64, device="cuda")
     trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
-    qg.qg_solve_schedule(s.h, xt, iters, st, 0.9, 0.999, trace)
+    # two chunks of one run: the second continues the schedule and the trace
+    qg.qg_solve_schedule(s.h, xt, 12, st, True, 0.9, 0.999, trace)
+    qg.qg_solve_schedule(s.h, xt, iters - 12, st, False, 0.9, 0.999, trace)
     torch.cuda.synchronize()
     lo, hi = oracle.box(c)
     x, m, v = x0.copy(), np.zeros_like(x0), np.zeros_like(x0)
