@@ -111,6 +111,11 @@ typedef struct {
                         * QG_DC_AUTO (0, the default): sparse for a single instance of more
                         *   than 4096 buses, dense otherwise.
                         * Both compute the same quantities (the results agree to rounding). */
+  double ctg_frac;     /* contingency screening (Alg. 2): 0 (the default) or >= 1 evaluates every
+                        * outage; in (0, 1) each evaluation covers a selected subset of
+                        * Ks = ceil(ctg_frac K) outages per instance (qg_ctg_select; initially the
+                        * first Ks), through a compacted line-outage block, and records their
+                        * scores (qg_ctg_scores) */
 } qg_options;
 
 /* Fill *opt with the defaults: c_p = c_q = 1e4, c_s = c_rz = rho = 1e3,
@@ -235,6 +240,20 @@ int qg_set_step(qg_ctx *h, int64_t step);
  * code.  Waits for those events. */
 int qg_set_profiling(qg_ctx *h, int on);
 int qg_phase_times(qg_ctx *h, float *ms, int32_t cap);
+
+/* Contingency screening (Alg. 2; handles created with 0 < ctg_frac < 1).  qg_ctg_select makes the
+ * n outages ids[0 .. n - 1] (host array of distinct indices into the instance's contingency list,
+ * n = its Ks) the ones later evaluations of instance `inst` cover: their columns of the line-outage
+ * block are gathered on the device and the instance's contingency term and gradient become those of
+ * the subset.  The reading of Alg. 2 here: one subset for all periods of the instance (the union of
+ * the per-period sets K_t and S_t).  Synchronizes the handle's stream.
+ * qg_ctg_scores copies to `z` (host, sum over instances of T x Ks doubles, period-major per
+ * instance, instances in order) the score of every evaluated (period, outage) of the last
+ * evaluation: z_tk of Eq. zctg without the soft-ReLU floor, i.e. sum_m d_t c_s beta
+ * (sigma_s(s - s_ctg) - eps) over the monitored branches, in the order of the current selection.
+ * Both return QG_ERR_UNSUPPORTED on a handle without screening. */
+int qg_ctg_select(qg_ctx *h, int32_t inst, const int32_t *ids, int32_t n);
+int qg_ctg_scores(qg_ctx *h, double *z);
 
 /* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: the
  * 5 stage kernels, plus 3 to 7 solve kernels with the sparse DC solver.  Returns a negative

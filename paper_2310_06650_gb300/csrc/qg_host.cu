@@ -48,6 +48,8 @@ struct HostInst {
   std::vector<double> rsum;   // M
   std::vector<double> ltot;   // T
   std::vector<double> lodf;   // M x K
+  int Ks = 0;                 // outages each evaluation covers (K without screening)
+  std::vector<int> sel;       // their indices into ctg (screening: the current selection)
   // warp packs (code, row) of the two bus CSRs
   std::vector<int> bal_code, bal_row, adj_code, adj_row;
   // sparse DC mode: factor with a dense tail, node positions, gather lists (see qg_sparse.h)
@@ -83,6 +85,11 @@ struct qg_ctx {
   const double *g_sched = nullptr;
   int g_trace_len = 0;
   // optional per-kernel timing: ev[0..5] bracket the five stage kernels, ev[6] ends a stand-alone Adam step
+  bool screen = false;                 // contingency screening (0 < ctg_frac < 1)
+  std::vector<long long> lf0;          // per instance: offset of its full line-outage block (screening)
+  void *lodf_full = nullptr;           // screening: the full block (element type of d32/d64.lodf)
+  double *lodf64_full = nullptr;       // screening, FP64 path: the full exact block
+  int *d_sel = nullptr;                // screening: [sum Ks] selected outage indices per instance
   bool profiling = false;
   cudaEvent_t ev[N_PHASES + 1] = {};
   std::string err;
@@ -528,20 +535,20 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   // (tiles grouped per block, so fewer column partials are written and summed).
   long long tiles = 0;
   for (int b = 0; b < B; ++b)
-    if (h->hi[b].K > 0) tiles += (long long)ceil_div(h->hi[b].M, CT_BM) * ceil_div(h->hi[b].K, CT_BK);
+    if (h->hi[b].Ks > 0) tiles += (long long)ceil_div(h->hi[b].M, CT_BM) * ceil_div(h->hi[b].Ks, CT_BK);
   const int ntc_all = (int)std::max(1LL, tiles > 0 ? CTG_WAVE / tiles : 1);
   const int mg_all = (int)std::max(1LL, tiles / (4LL * CTG_WAVE));
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
     Inst &D = P.tab.I[b];
-    D.n = H.n; D.M = H.M; D.G = H.G; D.Z = H.Z; D.T = H.T; D.K = H.K; D.Gb = (int)H.gbus.size();
-    D.Kp = ceil_div(H.K, 4) * 4;
+    D.n = H.n; D.M = H.M; D.G = H.G; D.Z = H.Z; D.T = H.T; D.K = H.Ks; D.Gb = (int)H.gbus.size();
+    D.Kp = ceil_div(H.Ks, 4) * 4;
     D.X = H.X; D.xf0 = xf0; D.Gc = H.Gc; D.tx0 = tx0;
     D.xtau0 = x0 + (long long)H.T * (2LL * H.n + 3LL * H.G);
     D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.gb0 = gb0; D.tp0 = tp0;
     D.n_mt = ceil_div(H.M, CT_BM);
-    D.n_kt = ceil_div(H.K, CT_BK);
+    D.n_kt = ceil_div(H.Ks, CT_BK);
     D.ctg_mg = std::min(mg_all, D.n_mt);
     D.n_mg = ceil_div(D.n_mt, D.ctg_mg);
     D.ctg_tb = ceil_div(H.T, std::min(ntc_all, H.T));
@@ -554,13 +561,13 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     D.inv_n = 1.0 / H.n;
     D.hours = 0.0;
     for (int t = 0; t < H.T; ++t) D.hours += H.dt[t];
-    D.nfloor_ctg = (double)H.M * H.K - H.K;
+    D.nfloor_ctg = (double)H.M * H.Ks - H.Ks;
     x0 += (long long)H.T * (2LL * H.n + 3LL * H.G + 2LL * H.X);
     tx0 += (long long)H.T * H.X; xf0 += H.X;
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
-    tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.K; pg0 += (long long)H.M * D.Gc; l0 += (long long)H.M * D.Kp;
-    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.K; gi0 += (long long)H.T * (D.Gc + 1);
-    bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.K; gb0 += D.Gb; tp0 += H.T;
+    tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.Ks; pg0 += (long long)H.M * D.Gc; l0 += (long long)H.M * D.Kp;
+    pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.Ks; gi0 += (long long)H.T * (D.Gc + 1);
+    bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.Ks; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
     P.maxT = std::max(P.maxT, H.T);
     P.maxTB = std::max(P.maxTB, D.ctg_tb);
@@ -627,6 +634,53 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   return QG_OK;
 }
 
+// Compacted line-outage block of one instance: column j < Ks is the full block's column sel[j];
+// columns up to the padded stride are `pad` (NaN for the screening copies).
+template <typename E>
+__global__ void k_lodf_gather(const E *__restrict__ full, E *__restrict__ comp, const int *__restrict__ sel, int M,
+                              int Kpf, int Ks, int Kpc, E pad) {
+  const long long n = (long long)M * Kpc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / Kpc), j = (int)(i % Kpc);
+    comp[i] = j < Ks ? full[(long long)m * Kpf + sel[j]] : pad;
+  }
+}
+
+template <typename E>
+cudaError_t launch_gather(const void *full, const void *comp, const int *sel, long long f0, long long c0, int M, int Kpf,
+                          int Ks, int Kpc, E pad, cudaStream_t s) {
+  const long long n = (long long)M * Kpc;
+  const int nb = (int)std::max(1LL, std::min((n + 255) / 256, 152LL * 16));
+  k_lodf_gather<E><<<nb, 256, 0, s>>>(static_cast<const E *>(full) + f0, const_cast<E *>(static_cast<const E *>(comp)) + c0,
+                                      sel, M, Kpf, Ks, Kpc, pad);
+  return cudaGetLastError();
+}
+
+// Gather instance b's selected columns of the full line-outage block(s) into the compacted copies.
+template <typename Real, typename Dc>
+int gather_lodf(qg_ctx *h, const Dev<Real, Dc> &d, int b) {
+  const Inst &I = h->plan.tab.I[b];
+  const HostInst &H = h->hi[b];
+  const int Kpf = ceil_div(H.K, 4) * 4;
+  const long long f0 = h->lf0[b];
+  const int *sel = h->d_sel + I.ctg0;
+  cudaError_t e;
+  if (d.lodf_dtype == QG_LODF_BF16) {
+    e = launch_gather<__nv_bfloat16>(h->lodf_full, d.lodf, sel, f0, I.l0, H.M, Kpf, I.K, I.Kp,
+                                     __float2bfloat16_rn(NAN), h->stream);
+  } else if (d.lodf_dtype == QG_LODF_BF16X2) {
+    __nv_bfloat162 pad;
+    pad.x = pad.y = __float2bfloat16_rn(NAN);
+    e = launch_gather<__nv_bfloat162>(h->lodf_full, d.lodf, sel, f0, I.l0, H.M, Kpf, I.K, I.Kp, pad, h->stream);
+  } else {
+    e = launch_gather<float>(h->lodf_full, d.lodf, sel, f0, I.l0, H.M, Kpf, I.K, I.Kp, NAN, h->stream);
+  }
+  if (e == cudaSuccess && d.lodf64)
+    e = launch_gather<double>(h->lodf64_full, d.lodf64, sel, f0, I.l0, H.M, Kpf, I.K, I.Kp, 0.0, h->stream);
+  if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("line-outage gather: ") + cudaGetErrorString(e));
+  return QG_OK;
+}
+
 // Build every device array of one precision flavour.
 template <typename Real, typename Dc>
 int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) {
@@ -649,9 +703,9 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
       br_smax.push_back(H.smax[j]);
       br_s2.push_back(H.sctg[j] * H.sctg[j]);
     }
-    for (int k = 0; k < H.K; ++k) {
-      br_kidx[D.br0 + H.ctg[k]] = k;
-      ctg_br.push_back(H.ctg[k]);
+    for (int j = 0; j < H.Ks; ++j) {
+      br_kidx[D.br0 + H.ctg[H.sel[j]]] = j;
+      ctg_br.push_back(H.ctg[H.sel[j]]);
     }
     br_xf.insert(br_xf.end(), H.br_xf.begin(), H.br_xf.end());
     xf_br.insert(xf_br.end(), H.xf.begin(), H.xf.end());
@@ -694,9 +748,10 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
     rsum.insert(rsum.end(), H.rsum.begin(), H.rsum.end());
     // line-outage block with its row stride padded to Kp; NaN marks the pads and each outage's own
     // branch (the contingency kernel's screen rejects NaN elements)
-    {
-      const int Kp = P.tab.I[b].Kp;
+    {  // with screening this is the full block (every outage), gathered per selection on the device
+      const int Kp = h->screen ? ceil_div(H.K, 4) * 4 : P.tab.I[b].Kp;
       const size_t base = lodf.size();
+      if (h->screen) h->lf0.push_back((long long)base);
       lodf.resize(base + (size_t)H.M * Kp, NAN);
       for (int m = 0; m < H.M; ++m)
         for (int k = 0; k < H.K; ++k)
@@ -777,6 +832,39 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
     double *q;
     if ((rc = upload(h, &q, lodf))) return rc;
     d.lodf64 = q;
+  }
+  if (h->screen) {  // the uploaded blocks are the full ones; the kernels read compacted copies
+    h->lodf_full = const_cast<void *>(d.lodf);
+    h->lodf64_full = const_cast<double *>(d.lodf64);
+    long long lc = 0;
+    std::vector<int> sel;
+    for (int b = 0; b < B; ++b) {
+      lc += (long long)h->hi[b].M * P.tab.I[b].Kp;
+      sel.insert(sel.end(), h->hi[b].sel.begin(), h->hi[b].sel.end());
+    }
+    const size_t esz = dtype == QG_LODF_BF16 ? 2 : 4;
+    unsigned char *cq;
+    if ((rc = dalloc(h, &cq, (size_t)lc * esz))) return rc;
+    d.lodf = cq;
+    if (f64) {
+      double *c64;
+      if ((rc = dalloc(h, &c64, (size_t)lc))) return rc;
+      d.lodf64 = c64;
+    }
+    if ((rc = upload(h, &h->d_sel, sel))) return rc;
+    Real *pz, *zs;
+    long long spk = 0, stk = 0;
+    for (int b = 0; b < B; ++b) {
+      spk += (long long)P.tab.I[b].n_mg * P.tab.I[b].T * P.tab.I[b].K;
+      stk += (long long)P.tab.I[b].T * P.tab.I[b].K;
+    }
+    if ((rc = dalloc(h, &pz, (size_t)spk)) || (rc = dalloc(h, &zs, (size_t)stk))) return rc;
+    d.pz = pz;
+    d.zs = zs;
+    d.score = 1;
+    for (int b = 0; b < B; ++b)
+      if ((rc = gather_lodf(h, d, b))) return rc;
+    CUDA_TRY(h, cudaDeviceSynchronize());
   }
   // sparse DC mode (instance 0)
   d.sp = P.sp;
@@ -1070,6 +1158,7 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
   if (o.precision != QG_FP64 && o.precision != QG_MIXED) return reject(QG_ERR_INVALID_ARG, "precision");
   if (o.lodf_dtype < 0 || o.lodf_dtype > 2) return reject(QG_ERR_INVALID_ARG, "lodf_dtype");
   if (o.dc_solver < QG_DC_AUTO || o.dc_solver > QG_DC_SPARSE) return reject(QG_ERR_INVALID_ARG, "dc_solver");
+  if (!(o.ctg_frac >= 0.0) || !std::isfinite(o.ctg_frac)) return reject(QG_ERR_INVALID_ARG, "ctg_frac");
   if (o.dc_solver == QG_DC_SPARSE && n_inst > 1)
     return reject(QG_ERR_UNSUPPORTED, "the sparse DC solver takes one instance per handle");
   if (!(o.eps >= 0) || !(o.beta >= 0) || !(o.c_p >= 0) || !(o.c_q >= 0) || !(o.c_s >= 0) || !(o.c_rz >= 0) ||
@@ -1083,6 +1172,12 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
     if (rc) { delete h; return rc; }
   }
   h->hi[0].sparse = o.dc_solver == QG_DC_SPARSE || (o.dc_solver == QG_DC_AUTO && n_inst == 1 && h->hi[0].n > SPARSE_AUTO_N);
+  h->screen = o.ctg_frac > 0.0 && o.ctg_frac < 1.0;
+  for (auto &H : h->hi) {  // outages per evaluation; the first Ks until qg_ctg_select
+    H.Ks = h->screen ? std::max(std::min(H.K, 1), (int)std::ceil(o.ctg_frac * H.K)) : H.K;
+    H.sel.resize(H.Ks);
+    for (int j = 0; j < H.Ks; ++j) H.sel[j] = j;
+  }
   {  // FP64 network set-up per instance, in parallel over instances
     std::vector<int> rcs(n_inst, 0);
     std::vector<std::string> errs(n_inst);
@@ -1119,7 +1214,8 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
   }
   rc = mixed(h) ? build_device<float, df32>(h, h->d32, slot_map) : build_device<double, double>(h, h->d64, slot_map);
   if (!rc) {
-    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->plan.maxTB) : prepare_eval<double, double>(h->plan.maxTB);
+    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->plan.maxTB, h->screen)
+                             : prepare_eval<double, double>(h->plan.maxTB, h->screen);
     if (e != cudaSuccess) rc = fail(h, QG_ERR_UNSUPPORTED, std::string("prepare_eval: ") + cudaGetErrorString(e));
   }
   if (rc) {
@@ -1183,6 +1279,8 @@ int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g) {
     return h ? fail(h, QG_ERR_INVALID_ARG, "qg_eval_grad_noalloc needs x, obj and g") : QG_ERR_INVALID_ARG;
   if (h->plan.sp)
     return fail(h, QG_ERR_UNSUPPORTED, "qg_eval_grad_noalloc: handles on the sparse DC solver do not fit its scratch");
+  if (h->screen)
+    return fail(h, QG_ERR_UNSUPPORTED, "qg_eval_grad_noalloc: handles with contingency screening do not fit its scratch");
   return mixed(h) ? eval_noalloc<float, df32>(h, h->d32, x, obj, g) : eval_noalloc<double, double>(h, h->d64, x, obj, g);
 }
 
@@ -1364,6 +1462,53 @@ int qg_phase_times(qg_ctx *h, float *ms, int32_t cap) {
 }
 
 const char *qg_last_error(const qg_ctx *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int qg_ctg_select(qg_ctx *h, int32_t inst, const int32_t *ids, int32_t n) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  if (!h->screen) return fail(h, QG_ERR_UNSUPPORTED, "qg_ctg_select: the handle has no contingency screening");
+  if (inst < 0 || inst >= h->n_inst || !ids) return fail(h, QG_ERR_INVALID_ARG, "qg_ctg_select: bad instance or ids");
+  HostInst &H = h->hi[inst];
+  const Inst &I = h->plan.tab.I[inst];
+  if (n != H.Ks) return fail(h, QG_ERR_INVALID_ARG, "qg_ctg_select: n must equal the instance's Ks = " + std::to_string(H.Ks));
+  std::vector<char> seen(H.K, 0);
+  for (int j = 0; j < n; ++j) {
+    if (ids[j] < 0 || ids[j] >= H.K || seen[ids[j]]) return fail(h, QG_ERR_INVALID_ARG, "qg_ctg_select: ids must be distinct in [0, K)");
+    seen[ids[j]] = 1;
+  }
+  H.sel.assign(ids, ids + n);
+  std::vector<int> kidx(H.M, -1), cbr(n);
+  for (int j = 0; j < n; ++j) {
+    kidx[H.ctg[H.sel[j]]] = j;
+    cbr[j] = H.ctg[H.sel[j]];
+  }
+  const bool mx = mixed(h);
+  const int *d_kidx = mx ? h->d32.br_kidx : h->d64.br_kidx;
+  const int *d_cbr = mx ? h->d32.ctg_br : h->d64.ctg_br;
+  CUDA_TRY(h, cudaMemcpyAsync(const_cast<int *>(d_kidx) + I.br0, kidx.data(), sizeof(int) * H.M, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(const_cast<int *>(d_cbr) + I.ctg0, cbr.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_sel + I.ctg0, H.sel.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  const int rc = mx ? gather_lodf(h, h->d32, inst) : gather_lodf(h, h->d64, inst);
+  if (rc) return rc;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return QG_OK;
+}
+
+int qg_ctg_scores(qg_ctx *h, double *z) {
+  if (!h || !z) return QG_ERR_INVALID_ARG;
+  if (!h->screen) return fail(h, QG_ERR_UNSUPPORTED, "qg_ctg_scores: the handle has no contingency screening");
+  long long n = 0;
+  for (int b = 0; b < h->n_inst; ++b) n += (long long)h->plan.tab.I[b].T * h->plan.tab.I[b].K;
+  if (mixed(h)) {
+    std::vector<float> tmp(n);
+    CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), h->d32.zs, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (long long i = 0; i < n; ++i) z[i] = tmp[i];
+  } else {
+    CUDA_TRY(h, cudaMemcpyAsync(z, h->d64.zs, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return QG_OK;
+}
 
 int32_t qg_launches_per_eval(const qg_ctx *h) {
   if (!h) return QG_ERR_INVALID_ARG;

@@ -155,6 +155,9 @@ struct Dev {
   Real *dP, *dQ;                      // [sum T n]
   Real *dZ;                           // [sum T Z]
   Real *pm, *pq, *pk;                 // contingency partials
+  int score;                          // 1: record per-(period, outage) scores (contingency screening)
+  Real *pz;                           // score partials [n_mg][T][K] per instance (at pk0)
+  Real *zs;                           // scores [sum T K] (at tk0)
   Real *gF;                           // [sum T M] dz/df
   Dc *gip;                            // adjoint DC products [sum T (Gb + 1)]
   Real *avf, *avo, *ad;               // branch-end adjoints [sum T M]
@@ -201,7 +204,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *x, bo
                         cudaEvent_t *ev);
 
 template <typename Real, typename Dc>
-cudaError_t prepare_eval(int maxT);
+cudaError_t prepare_eval(int maxTB, bool score);
 
 template <typename Real>
 cudaError_t launch_adam(Real *x, Real *m, Real *v, const Real *g, const Real *lo, const Real *hi, long long n,

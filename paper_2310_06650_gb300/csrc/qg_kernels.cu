@@ -624,11 +624,16 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   Real *s_ga = s_gk + TCH * 8 * CT_BK;                // [TB][BK] column sums over the group
   Real *s_f64m = s_ga + TBM * CT_BK;                  // [TB][BM] (FP64 path only)
   Real *s_f64k = s_f64m + (F64 ? TBM * CT_BM : 0);    // [TB][BK] (FP64 path only)
+  Real *s_gz = s_f64k + (F64 ? TBM * CT_BK : 0);      // [TCH][8][BK] score column sums (screening only)
+  Real *s_za = s_gz + (d.score ? TCH * 8 * CT_BK : 0);  // [TB][BK] scores over the group (screening only)
+  const bool score = d.score != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rq = threadIdx.x >> 4, cq = threadIdx.x & 15;
   const int kc = k0 + cq * 4;  // first of this thread's four outages
   for (int e = threadIdx.x; e < TCH * CT_BM; e += NTHR) s_gm[e] = s_gq[e] = 0;
   for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gk[e] = 0;
+  if (score)
+    for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gz[e] = 0;
   Real obj = 0;
   const Real eps = hp.eps;
   for (int mt = mt0; mt < mt1; ++mt) {
@@ -660,6 +665,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         s_fk[tt * CT_BK + c] = f;
         if (F64) s_f64k[tt * CT_BK + c] = f64;
         s_ga[tt * CT_BK + c] = 0;
+        if (score) s_za[tt * CT_BK + c] = 0;
       }
     }
     __syncthreads();  // the previous tile is done with s_fm, s_qs, s_s2
@@ -702,7 +708,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         if (!__any_sync(0xffffffffu, mx > 0.f)) continue;
         // a (candidate) post-contingency overload in this warp
         const Real w = d.dt[I.tp0 + t] * d.c_s * hp.beta;
-        Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0};
+        Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
         if (mx > 0.f) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -725,6 +731,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
               Real val, der;
               soft_relu(sv - dsqrt(s_s2[mm]), eps, val, der);
               obj += w * (val - eps);
+              zc[j] += w * (val - eps);
               const Real dd = w * der / sv;  // dz/dF = w sigma' F / s
               gm[i] += dd * Fx;
               gk[j] += dd * Fx * Lx;
@@ -752,6 +759,13 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         if (lane < 16)
 #pragma unroll
           for (int j = 0; j < 4; ++j) s_gk[(tt * 8 + wid) * CT_BK + cq * 4 + j] = gk[j];
+        if (score) {  // per-outage scores for the screening list, the same way as the column sums
+#pragma unroll
+          for (int j = 0; j < 4; ++j) zc[j] += __shfl_xor_sync(0xffffffffu, zc[j], 16);
+          if (lane < 16)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s_gz[(tt * 8 + wid) * CT_BK + cq * 4 + j] = zc[j];
+        }
       }
       __syncthreads();
       // flush the chunk: each entry is read and re-zeroed by the same thread
@@ -774,13 +788,27 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           g = 0;
         }
         s_ga[(tc0 + tt) * CT_BK + c] = sum;
+        if (score) {
+          Real zsum = s_za[(tc0 + tt) * CT_BK + c];
+#pragma unroll
+          for (int ww = 0; ww < 8; ++ww) {
+            Real &zz = s_gz[(tt * 8 + ww) * CT_BK + c];
+            zsum += zz;
+            zz = 0;
+          }
+          s_za[(tc0 + tt) * CT_BK + c] = zsum;
+        }
       }
       __syncthreads();
     }
   }
   for (int e = threadIdx.x; e < TB * CT_BK; e += NTHR) {
     const int tt = e / CT_BK, c = e % CT_BK, k = k0 + c;
-    if (k < I.K) d.pk[I.pk0 + ((long long)mg * T + t0 + tt) * I.K + k] = s_ga[tt * CT_BK + c];
+    if (k < I.K) {
+      const long long q = I.pk0 + ((long long)mg * T + t0 + tt) * I.K + k;
+      d.pk[q] = s_ga[tt * CT_BK + c];
+      if (score) d.pz[q] = s_za[tt * CT_BK + c];
+    }
   }
   acc.v[0] = DcOps<Dc>::from_real(obj);
 }
@@ -833,10 +861,14 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
       gq2 += d.pq[q];
     }
     if (kx >= 0) {
-      Real gk = 0;
+      Real gk = 0, zk = 0;
 #pragma unroll 8
       for (int mg = 0; mg < I.n_mg; ++mg) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
       gF += gk;
+      if (d.score) {
+        for (int mg = 0; mg < I.n_mg; ++mg) zk += d.pz[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
+        d.zs[I.tk0 + (long long)t * I.K + kx] = zk;
+      }
     }
     d.gF[e] = gF;
     // adjoints of the four end flows
@@ -1563,12 +1595,13 @@ __global__ void __launch_bounds__(NTHR) k_sp_back(const __grid_constant__ Dev<Re
 // ---------------------------------------------------------------------------------------------
 
 template <typename Real>
-size_t ctg_smem_bytes(int TB) {
+size_t ctg_smem_bytes(int TB, bool score) {
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
   return sizeof(float) * (size_t)TB * (2 * CT_BM + CT_BK) +
          sizeof(Real) * ((size_t)TB * CT_BK + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
-                         (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0));
+                         (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0) +
+                         (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0));
 }
 
 // Record a timing event on s; inside stream capture it becomes an external event node.
@@ -1629,7 +1662,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     e = cudaGetLastError();
   }
   mark(ev, 1, s);
-  go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB), d, P.tab, P.s2, (const Real *)x, o2);
+  go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB, d.score != 0), d, P.tab, P.s2, (const Real *)x, o2);
   mark(ev, 2, s);
   go(k_s3<Real, Dc>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
   mark(ev, 3, s);
@@ -1650,8 +1683,8 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
 }
 
 template <typename Real, typename Dc>
-cudaError_t prepare_eval(int maxTB) {
-  const size_t sm = ctg_smem_bytes<Real>(maxTB);
+cudaError_t prepare_eval(int maxTB, bool score) {
+  const size_t sm = ctg_smem_bytes<Real>(maxTB, score);
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(k_s2<Real, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
@@ -1671,8 +1704,8 @@ template cudaError_t launch_eval<double, double>(const Dev<double, double> &, co
                                                  cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Plan &, const void *, bool,
                                               cudaStream_t, cudaEvent_t *);
-template cudaError_t prepare_eval<double, double>(int);
-template cudaError_t prepare_eval<float, df32>(int);
+template cudaError_t prepare_eval<double, double>(int, bool);
+template cudaError_t prepare_eval<float, df32>(int, bool);
 template cudaError_t launch_adam<double>(double *, double *, double *, const double *, const double *, const double *,
                                          long long, long long *, unsigned int *, double, double, double, double, int,
                                          cudaStream_t);

@@ -57,7 +57,7 @@ class qg_options(C.Structure):
     _fields_ = [("c_p", C.c_double), ("c_q", C.c_double), ("c_s", C.c_double), ("c_rz", C.c_double),
                 ("rho", C.c_double), ("eps", C.c_double), ("beta", C.c_double), ("adam_eps", C.c_double),
                 ("precision", C.c_int32), ("lodf_dtype", C.c_int32), ("adam_paper_eps", C.c_int32),
-                ("dc_solver", C.c_int32)]
+                ("dc_solver", C.c_int32), ("ctg_frac", C.c_double)]
 
 
 def _load():
@@ -88,6 +88,8 @@ def _load():
         "qg_last_error": (C.c_char_p, [vp]),
         "qg_version": (C.c_int, []),
         "qg_launches_per_eval": (C.c_int32, [vp]),
+        "qg_ctg_select": (C.c_int, [vp, C.c_int32, vp, C.c_int32]),
+        "qg_ctg_scores": (C.c_int, [vp, vp]),
         "qg_solve_schedule": (C.c_int, [vp, vp, C.c_int32, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, vp]),
         "qg_schedule": (C.c_int, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                   C.c_double, C.c_double]),
@@ -113,7 +115,7 @@ _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_eval_grad_noalloc", "qg_adam_step", "qg_solve", "qg_breakdown",
             "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_launches_per_eval",
-            "qg_solve_schedule", "qg_schedule",
+            "qg_solve_schedule", "qg_schedule", "qg_ctg_select", "qg_ctg_scores",
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
@@ -269,6 +271,18 @@ def qg_schedule(iters: int, lr0: float, lrf: float, eps0: float, epsf: float, be
     return out
 
 
+def qg_ctg_select(h: int, inst: int, ids) -> None:
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    _check(_lib.qg_ctg_select(h, inst, ids.ctypes.data_as(C.c_void_p), int(ids.shape[0])), h)
+
+
+def qg_ctg_scores(h: int, count: int) -> np.ndarray:
+    """Scores of the last evaluation's (period, selected outage) pairs: `count` doubles."""
+    out = np.zeros(count)
+    _check(_lib.qg_ctg_scores(h, out.ctypes.data_as(C.c_void_p)), h)
+    return out
+
+
 def qg_breakdown(h: int, n_inst: int = 1) -> np.ndarray:
     out = np.zeros(8 * n_inst)
     _check(_lib.qg_breakdown(h, out.ctypes.data_as(_F64P)), h)
@@ -323,6 +337,7 @@ class Solver:
         self.dtype = torch.float64 if precision == QG_FP64 else torch.float32
         self.device = torch.device(device)
         opt = case_options(self.cases[0], precision=precision, lodf_dtype=lodf_dtype, **opt_kw)
+        self.ctg_frac = opt.ctg_frac
         self.h = qg_create_batch(self.cases, opt)
         self.n_x = qg_num_vars(self.h)
         self.n_inst = len(self.cases)
