@@ -432,6 +432,23 @@ def dayahead_leg(args, peaks, src, local_rank):
         "clocks": clk.summary(),
     }
     s.close()
+    # contingency screening (Alg. 2): the same step covering a fifth of the outages per evaluation
+    frac = 0.2
+    s = qg.Solver(case, precision=qg.QG_MIXED, ctg_frac=frac)
+    x.copy_(torch.tensor(x0, dtype=torch.float32, device="cuda"))
+    for _ in range(max(args.warmup, 3)):
+        qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        ev0[k].record(stream)
+        qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    ms_s = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / steps
+    out["screened"] = {"ctg_frac": frac, "value": 1e3 / ms_s, "unit": UNIT, "ms_per_step": ms_s,
+                       "note": "Alg. 2 screening: each evaluation covers ceil(0.2 K) outages (a compacted "
+                               "line-outage block); the subset is whatever qg_ctg_select last chose"}
+    s.close()
     return out
 
 

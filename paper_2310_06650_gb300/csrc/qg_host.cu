@@ -580,7 +580,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   if (P.sp) {
     const int nr = H0.n - 1;
     P.sp_inj_blocks = ceil_div((long long)nr * H0.T, NTHR);
-    P.sp_fw_blocks = ceil_div(nr, NTHR / 32);
+    P.sp_fw_blocks = ceil_div(H0.nS, NTHR / 32) + H0.nT;  // eliminated rows 8 per block, tail rows 1 per block
     // column splits: about two waves of tail blocks, at least SP_BK columns per split
     const int n_rt = ceil_div(H0.nT, SP_RB);
     const int ks0 = n_rt > 0 ? std::max(1, std::min(ceil_div(2 * CTG_WAVE, n_rt), ceil_div(H0.nT, SP_BK))) : 1;

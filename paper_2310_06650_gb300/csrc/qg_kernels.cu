@@ -386,6 +386,20 @@ __device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, con
   }
 }
 
+// Dispatch snapshot for the ramp terms of a fused Adam update (stage 5 reads the pre-update p of the
+// neighbouring periods): the periods [t0, t0 + 8) of a DC-flow block row, split evenly over the
+// row's blocks.
+template <typename Real, typename Dc>
+__device__ __forceinline__ void pold_share(const Dev<Real, Dc> &d, const Inst &I, int t0, int sub,
+                                           const Real *__restrict__ p) {
+  const int tn = min(DCF_TC, I.T - t0);
+  const int n = tn * I.G, nsub = (I.M + DCF_BM - 1) / DCF_BM;
+  const int per = (n + nsub - 1) / nsub;
+  const int lo = min(n, sub * per), hi = min(n, lo + per);
+  const long long base = (long long)t0 * I.G;
+  for (int e = lo + threadIdx.x; e < hi; e += NTHR) d.pold[I.tg0 + base + e] = p[base + e];
+}
+
 // Base DC flows of branches [m0, m0+32) in periods [t0, t0+8):
 //   f[t,m] = sum_gb PTDF_G[m,gb] p_G[t,gb] - (PTDF load_t)[m] - mu_t (PTDF 1)[m],
 //   mu_t = (sum_g p[t,g] - load_t) / n   (uniform slack, Sec. II-E).
@@ -398,13 +412,7 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   const int tl = threadIdx.x >> 5, ml = threadIdx.x & 31;
   const int t = t0 + tl, m = m0 + ml;
   const Real *p = x + I.x0 + 2LL * I.T * I.n;
-  if (sub == 0) {  // dispatch snapshot for the ramp terms of a fused Adam update
-#pragma unroll 4
-    for (int e = threadIdx.x; e < DCF_TC * I.G; e += NTHR) {
-      const int tt = t0 + e / I.G, gl = e % I.G;
-      if (tt < I.T) d.pold[I.tg0 + (long long)tt * I.G + gl] = p[(long long)tt * I.G + gl];
-    }
-  }
+  pold_share(d, I, t0, sub, p);
   Dc acc = DcOps<Dc>::zero();
   Dc tot = DcOps<Dc>::zero();  // running sum of p_G over generator buses for mu_t (warp tl)
   // columns: generator buses (their dispatch), then transformers (their phase-shift flow b = b_sr phi)
@@ -467,14 +475,7 @@ template <typename Real, typename Dc>
 __device__ void s1_sdcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, const Real *__restrict__ x) {
   const int t0 = tc * DCF_TC, m0 = sub * DCF_BM;
   const int t = t0 + (threadIdx.x >> 5), m = m0 + (threadIdx.x & 31);
-  if (sub == 0) {  // dispatch snapshot for the ramp terms of a fused Adam update
-    const Real *p = x + I.x0 + 2LL * I.T * I.n;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < DCF_TC * I.G; e += NTHR) {
-      const int tt = t0 + e / I.G, gl = e % I.G;
-      if (tt < I.T) d.pold[I.tg0 + (long long)tt * I.G + gl] = p[(long long)tt * I.G + gl];
-    }
-  }
+  pold_share(d, I, t0, sub, x + I.x0 + 2LL * I.T * I.n);
   const bool on = t < I.T && m < I.M;
   const int2 ft = d.br_end[I.br0 + (on ? m : 0)];
   const int pf = d.bus_pos[ft.x], po = d.bus_pos[ft.y];
@@ -739,20 +740,21 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
             }
           }
         }
-        // row sums across the 16 column quads of each half-warp
+        // row sums across the 16 column quads of each half-warp, for rows with an overload in this
+        // warp (the buffers hold zeros for the others)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
+          if (!__any_sync(0xffffffffu, gq[i] != Real(0))) continue;
 #pragma unroll
           for (int o = 1; o < 16; o <<= 1) {
             gm[i] += __shfl_xor_sync(0xffffffffu, gm[i], o);
             gq[i] += __shfl_xor_sync(0xffffffffu, gq[i], o);
           }
-        if (cq == 0)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          if (cq == 0) {
             s_gm[tt * CT_BM + rq * 4 + i] = gm[i];
             s_gq[tt * CT_BM + rq * 4 + i] = gq[i];
           }
+        }
         // column sums across the two row quads of this warp, then per warp through shared memory
 #pragma unroll
         for (int j = 0; j < 4; ++j) gk[j] += __shfl_xor_sync(0xffffffffu, gk[j], 16);
@@ -1424,12 +1426,15 @@ __global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Rea
   }
 }
 
-// Forward gather z = [M1; M2] b, one warp per position, lanes over periods.  Eliminated rows
-// (their list holds the unit diagonal) store u = z / D; tail rows store z_T = b_T + M2 b_S.  In the
-// adjoint pass one extra block finishes 1^T eta from the per-chunk partials of stage 4.
+// Forward gather z = [M1; M2] b, lanes over periods.  Eliminated rows (a few entries each, their
+// list holding the unit diagonal; one warp per row) store u = z / D; tail rows (the long M2 rows;
+// one block per row, its 8 warps taking contiguous parts of the list, summed in warp order) store
+// z_T = b_T + M2 b_S.  In the adjoint pass one extra block finishes 1^T eta from the per-chunk
+// partials of stage 4.
 template <typename Real, typename Dc, bool ADJ>
 __global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Real, Dc> d,
                                                  const __grid_constant__ Inst I, int nrow_blocks) {
+  __shared__ Dc s_part[NTHR / 32][64];
   const int T = I.T;
   if (ADJ && (int)blockIdx.x == nrow_blocks) {
     pdl_wait();
@@ -1440,11 +1445,19 @@ __global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Rea
     }
     return;
   }
-  const int row = blockIdx.x * (NTHR / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  const bool on = row < d.nr;
-  const int e0 = on ? d.fw_ptr[row] : 0, e1 = on ? d.fw_ptr[row + 1] : 0;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nsb = (d.nS + NTHR / 32 - 1) / (NTHR / 32);
+  const bool tail = (int)blockIdx.x >= nsb;
+  const int row = tail ? d.nS + (blockIdx.x - nsb) : blockIdx.x * (NTHR / 32) + wid;
+  const bool on = tail || row < d.nS;
+  int e0 = on ? d.fw_ptr[row] : 0, e1 = on ? d.fw_ptr[row + 1] : 0;
+  if (tail) {
+    const int per = (e1 - e0 + NTHR / 32 - 1) / (NTHR / 32);
+    e0 = min(e1, e0 + wid * per);
+    e1 = min(e1, e0 + per);
+  }
   pdl_wait();
-  if (!on) return;
+  if (!on) return;  // whole warp (eliminated rows only)
   for (int t0 = 0; t0 < T; t0 += 64) {
     const int ta = t0 + lane, tb = t0 + 32 + lane;
     Dc a0 = DcOps<Dc>::zero(), a1 = DcOps<Dc>::zero();
@@ -1455,16 +1468,28 @@ __global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Rea
       if (ta < T) DcOps<Dc>::mac(a0, v, b[ta]);
       if (tb < T) DcOps<Dc>::mac(a1, v, b[tb]);
     }
-    if (row < d.nS) {
+    if (!tail) {
       const Dc di = d.dinv[row];
       Dc *u = d.sp_u + (long long)row * T;
       if (ta < T) u[ta] = DcOps<Dc>::mul(a0, di);
       if (tb < T) u[tb] = DcOps<Dc>::mul(a1, di);
     } else {
-      const Dc *b = d.sp_rhs + (long long)row * T;
-      Dc *z = d.sp_zt + (long long)(row - d.nS) * T;
-      if (ta < T) z[ta] = DcOps<Dc>::add(b[ta], a0);
-      if (tb < T) z[tb] = DcOps<Dc>::add(b[tb], a1);
+      s_part[wid][lane] = a0;
+      s_part[wid][32 + lane] = a1;
+      __syncthreads();
+      if (wid == 0) {
+        Dc z0 = s_part[0][lane], z1 = s_part[0][32 + lane];
+#pragma unroll
+        for (int w = 1; w < NTHR / 32; ++w) {
+          z0 = DcOps<Dc>::add(z0, s_part[w][lane]);
+          z1 = DcOps<Dc>::add(z1, s_part[w][32 + lane]);
+        }
+        const Dc *b = d.sp_rhs + (long long)row * T;
+        Dc *z = d.sp_zt + (long long)(row - d.nS) * T;
+        if (ta < T) z[ta] = DcOps<Dc>::add(b[ta], z0);
+        if (tb < T) z[tb] = DcOps<Dc>::add(b[tb], z1);
+      }
+      __syncthreads();
     }
   }
 }
