@@ -528,7 +528,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   const int B = h->n_inst;
   std::memset(&P, 0, sizeof(P));
   P.tab.n_inst = B;
-  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0, tx0 = 0;
+  long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0, tx0 = 0,
+            pf0 = 0;
   int xf0 = 0;
   // Contingency block shape, shared by the batch: about one wave of CTG_WAVE blocks when the
   // 64 x 64 tiles are few (the periods split across blocks), several waves when they are many
@@ -557,7 +558,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
     D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
     D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
-    D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0;
+    D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0; D.pf0 = pf0;
     D.inv_n = 1.0 / H.n;
     D.hours = 0.0;
     for (int t = 0; t < H.T; ++t) D.hours += H.dt[t];
@@ -566,6 +567,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     tx0 += (long long)H.T * H.X; xf0 += H.X;
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
     tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.Ks; pg0 += (long long)H.M * D.Gc; l0 += (long long)H.M * D.Kp;
+    pf0 += (long long)D.n_kt * H.T * D.n_mt;
     pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.Ks; gi0 += (long long)H.T * (D.Gc + 1);
     bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.Ks; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
@@ -935,6 +937,11 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   unsigned char *qs;
   if ((rc = dalloc(h, &qs, (size_t)sTM))) return rc;
   d.qside = qs;
+  long long sPF = 0;
+  for (int b = 0; b < B; ++b) sPF += (long long)P.tab.I[b].n_kt * P.tab.I[b].T * P.tab.I[b].n_mt;
+  unsigned char *pf;
+  if ((rc = dalloc(h, &pf, (size_t)std::max(1LL, sPF)))) return rc;
+  d.pmf = pf;
   Dc *op;
   d.n_obj12 = (int)slot_map.size();
   d.n_obj_slots = d.n_obj12 + P.n_gen_slots;
@@ -1092,6 +1099,11 @@ size_t carve_scratch(const qg_ctx *h, unsigned char *base, size_t cap, Dev<Real,
   d.fk = (Real *)take(R * sTK); d.fk32 = (float *)take(4 * sTK); d.pold = (Real *)take(R * sTG);
   d.dP = (Real *)take(R * sTn); d.dQ = (Real *)take(R * sTn); d.dZ = (Real *)take(R * sTZ);
   d.pm = (Real *)take(R * sPM); d.pq = (Real *)take(R * sPM); d.pk = (Real *)take(R * sPK);
+  {
+    long long sPF = 0;
+    for (int b = 0; b < h->n_inst; ++b) sPF += (long long)P.tab.I[b].n_kt * P.tab.I[b].T * P.tab.I[b].n_mt;
+    d.pmf = take(std::max(1LL, sPF));
+  }
   d.gip = (Dc *)take(D * sGI); d.objp = (Dc *)take(D * (size_t)d.n_obj_slots * N_TERMS);
   d.terms = (double *)take(sizeof(double) * N_TERMS * h->n_inst);
   d.ticket = (unsigned int *)take(sizeof(unsigned int));

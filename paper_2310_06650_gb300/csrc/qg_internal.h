@@ -42,6 +42,7 @@ struct Inst {
   long long pg0;         // PTDF restricted to generator buses: M x Gb, row m
   long long l0;          // line-outage block, M x Kp, row m
   long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mg][T][K]
+  long long pf0;         // flags of the row partials: [n_kt][T][n_mt], 1 where a 64-row tile has any
   long long gi0;         // adjoint DC products: [T][Gc + 1] (generator buses, transformers, then n mean(eta))
   long long tx0;         // per-period transformer arrays: [T][X]
   long long xtau0;       // first tau variable (x0 + T (2n + 3G)); phi follow after T X
@@ -155,6 +156,7 @@ struct Dev {
   Real *dP, *dQ;                      // [sum T n]
   Real *dZ;                           // [sum T Z]
   Real *pm, *pq, *pk;                 // contingency partials
+  unsigned char *pmf;                 // row-partial flags (pm, pq are written and read only where set)
   int score;                          // 1: record per-(period, outage) scores (contingency screening)
   Real *pz;                           // score partials [n_mg][T][K] per instance (at pk0)
   Real *zs;                           // scores [sum T K] (at tk0)

@@ -631,6 +631,8 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rq = threadIdx.x >> 4, cq = threadIdx.x & 15;
   const int kc = k0 + cq * 4;  // first of this thread's four outages
+  __shared__ int s_hit[ctg_tch<Real>()];  // per period of the chunk: some row of the tile has a partial
+  if (threadIdx.x < TCH) s_hit[threadIdx.x] = 0;
   for (int e = threadIdx.x; e < TCH * CT_BM; e += NTHR) s_gm[e] = s_gq[e] = 0;
   for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gk[e] = 0;
   if (score)
@@ -740,20 +742,23 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
             }
           }
         }
-        // row sums across the 16 column quads of each half-warp, for rows with an overload in this
-        // warp (the buffers hold zeros for the others)
+        // row sums across the 16 column quads of each half-warp, when some row of this warp has an
+        // overload (the buffers hold zeros otherwise)
+        if (__any_sync(0xffffffffu, (gq[0] != Real(0)) | (gq[1] != Real(0)) | (gq[2] != Real(0)) | (gq[3] != Real(0)))) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (!__any_sync(0xffffffffu, gq[i] != Real(0))) continue;
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int o = 1; o < 16; o <<= 1) {
-            gm[i] += __shfl_xor_sync(0xffffffffu, gm[i], o);
-            gq[i] += __shfl_xor_sync(0xffffffffu, gq[i], o);
-          }
-          if (cq == 0) {
-            s_gm[tt * CT_BM + rq * 4 + i] = gm[i];
-            s_gq[tt * CT_BM + rq * 4 + i] = gq[i];
-          }
+            for (int o = 1; o < 16; o <<= 1) {
+              gm[i] += __shfl_xor_sync(0xffffffffu, gm[i], o);
+              gq[i] += __shfl_xor_sync(0xffffffffu, gq[i], o);
+            }
+          if (cq == 0)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              s_gm[tt * CT_BM + rq * 4 + i] = gm[i];
+              s_gq[tt * CT_BM + rq * 4 + i] = gq[i];
+            }
+          if (lane == 0) s_hit[tt] = 1;
         }
         // column sums across the two row quads of this warp, then per warp through shared memory
 #pragma unroll
@@ -770,9 +775,11 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         }
       }
       __syncthreads();
-      // flush the chunk: each entry is read and re-zeroed by the same thread
+      // flush the chunk: the row partials of periods with an overload (and their flags); each
+      // entry is read and re-zeroed by the same thread
       for (int e = threadIdx.x; e < tn * CT_BM; e += NTHR) {
         const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
+        if (!s_hit[tt]) continue;
         if (m < I.M) {
           const long long q = I.pm0 + ((long long)kt * T + t0 + tc0 + tt) * I.M + m;
           d.pm[q] = s_gm[e];
@@ -780,6 +787,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         }
         s_gm[e] = s_gq[e] = 0;
       }
+      if (threadIdx.x < tn) d.pmf[I.pf0 + ((long long)kt * T + t0 + tc0 + threadIdx.x) * I.n_mt + mt] = (unsigned char)s_hit[threadIdx.x];
       for (int e = threadIdx.x; e < tn * CT_BK; e += NTHR) {
         const int tt = e / CT_BK, c = e % CT_BK;
         Real sum = s_ga[(tc0 + tt) * CT_BK + c];
@@ -801,6 +809,8 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           s_za[(tc0 + tt) * CT_BK + c] = zsum;
         }
       }
+      __syncthreads();
+      if (threadIdx.x < TCH) s_hit[threadIdx.x] = 0;
       __syncthreads();
     }
   }
@@ -857,10 +867,24 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
     const long long e = I.tm0 + (long long)t * I.M + j;
     Real gF = 0, gq2 = 0;
 #pragma unroll 8
-    for (int kt = 0; kt < I.n_kt; ++kt) {
-      const long long q = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
-      gF += d.pm[q];
-      gq2 += d.pq[q];
+    // row partials of the outage tiles whose 64-row tile had an overload (flagged by stage 2): few
+    // tiles are read unconditionally and selected (no dependent load), many are skipped
+    if (I.n_kt <= 16) {
+#pragma unroll 8
+      for (int kt = 0; kt < I.n_kt; ++kt) {
+        const long long q = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
+        const bool f = d.pmf[I.pf0 + ((long long)kt * I.T + t) * I.n_mt + (j >> 6)] != 0;
+        const Real a = d.pm[q], b = d.pq[q];
+        gF += f ? a : Real(0);
+        gq2 += f ? b : Real(0);
+      }
+    } else {
+      for (int kt = 0; kt < I.n_kt; ++kt) {
+        if (!d.pmf[I.pf0 + ((long long)kt * I.T + t) * I.n_mt + (j >> 6)]) continue;
+        const long long q = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
+        gF += d.pm[q];
+        gq2 += d.pq[q];
+      }
     }
     if (kx >= 0) {
       Real gk = 0, zk = 0;
@@ -1429,20 +1453,22 @@ __global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Rea
 // Forward gather z = [M1; M2] b, lanes over periods.  Eliminated rows (a few entries each, their
 // list holding the unit diagonal; one warp per row) store u = z / D; tail rows (the long M2 rows;
 // one block per row, its 8 warps taking contiguous parts of the list, summed in warp order) store
-// z_T = b_T + M2 b_S.  In the adjoint pass one extra block finishes 1^T eta from the per-chunk
-// partials of stage 4.
+// z_T = b_T + M2 b_S.  In the adjoint pass extra blocks finish 1^T eta from the per-chunk partials
+// of stage 4 (one warp per period).
 template <typename Real, typename Dc, bool ADJ>
 __global__ void __launch_bounds__(NTHR) k_sp_fwd(const __grid_constant__ Dev<Real, Dc> d,
                                                  const __grid_constant__ Inst I, int nrow_blocks) {
   __shared__ Dc s_part[NTHR / 32][64];
   const int T = I.T;
-  if (ADJ && (int)blockIdx.x == nrow_blocks) {
+  if (ADJ && (int)blockIdx.x >= nrow_blocks) {  // 1^T eta: one warp per period, lanes over the chunks
     pdl_wait();
-    for (int t = threadIdx.x; t < T; t += NTHR) {
-      Dc s = DcOps<Dc>::zero();
-      for (int c = 0; c < d.n_pchunk; ++c) s = DcOps<Dc>::add(s, d.sp_part[(long long)c * T + t]);
-      d.gip[I.gi0 + (long long)t * (I.Gc + 1) + I.Gc] = s;
-    }
+    const int t = (blockIdx.x - nrow_blocks) * (NTHR / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= T) return;
+    Dc s = DcOps<Dc>::zero();
+    for (int c = lane; c < d.n_pchunk; c += 32) s = DcOps<Dc>::add(s, d.sp_part[(long long)c * T + t]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = DcOps<Dc>::add(s, DcOps<Dc>::shfl_down(s, o));
+    if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gc + 1) + I.Gc] = s;
     return;
   }
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1696,7 +1722,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
   if (P.sp) {
     // sparse mode: adjoint solve eta = Yhat^-1 w at the generator buses, and 1^T eta
     const Inst &I = P.tab.I[0];
-    go(k_sp_fwd<Real, Dc, true>, P.sp_fw_blocks + 1, 0, d, I, P.sp_fw_blocks);
+    go(k_sp_fwd<Real, Dc, true>, P.sp_fw_blocks + (I.T + NTHR / 32 - 1) / (NTHR / 32), 0, d, I, P.sp_fw_blocks);
     if (P.sp_tail_blocks > 0) go(k_sp_tail<Real, Dc, true>, P.sp_tail_blocks, 0, d, I, P.sp_tail_ks, P.sp_tail_kc);
     if (P.sp_bwa_blocks > 0) go(k_sp_back<Real, Dc, true>, P.sp_bwa_blocks, 0, d, I);
   }
