@@ -97,27 +97,54 @@ def unpack(case, x):
     return v, th, p, q, r, tau, phi
 
 
-def pack(v, th, p, q, r, tau=None, phi=None):
+def unpack_u(case, x):
+    """The on-status block u (T x G) that follows phi when the case has commitment, else None."""
+    if not getattr(case, "commit", False):
+        return None
+    T, G = case.T, case.n_gen
+    o = T * (2 * case.n_bus + 3 * G + 2 * _n_xf(case))
+    return np.asarray(x, dtype=np.float64)[o:o + T * G].reshape(T, G)
+
+
+def pack(v, th, p, q, r, tau=None, phi=None, u=None):
     parts = [np.ravel(v), np.ravel(th), np.ravel(p), np.ravel(q), np.ravel(r)]
     if tau is not None:
         parts += [np.ravel(tau), np.ravel(phi)]
+    if u is not None:
+        parts.append(np.ravel(u))
     return np.concatenate(parts)
+
+
+def device_sign(case):
+    """+1 for producers, -1 for consumers: the sign with which a device's p, q enter as supply."""
+    cons = getattr(case, "dev_cons", None)
+    if cons is None or len(cons) == 0:
+        return np.ones(case.n_gen)
+    return np.where(np.asarray(cons, bool), -1.0, 1.0)
 
 
 def box(case):
     """Clip box B of Alg. 3 (clip step): v in [vmin, vmax], theta_ref = 0, other theta free,
-    p in [pmin, pmax], q in [qmin, qmax], r in [0, pmax], tau and phi in their ranges."""
-    T, n, X = case.T, case.n_bus, _n_xf(case)
+    p in [pmin, pmax], q in [qmin, qmax], r in [0, pmax] (consumers: r = 0), tau and phi in their
+    ranges.  With commitment the limits scaled by u become penalized constraints, and the box keeps
+    p in [0, pmax], q in [min(qmin, 0), max(qmax, 0)] and u in [0, 1]."""
+    T, n, G, X = case.T, case.n_bus, case.n_gen, _n_xf(case)
+    commit = bool(getattr(case, "commit", False))
     lo_th = np.full((T, n), -np.inf)
     hi_th = np.full((T, n), np.inf)
     lo_th[:, case.ref_bus] = 0.0
     hi_th[:, case.ref_bus] = 0.0
     xl = (np.tile(case.tau_min, (T, 1)), np.tile(case.phi_min, (T, 1))) if X else (None, None)
     xh = (np.tile(case.tau_max, (T, 1)), np.tile(case.phi_max, (T, 1))) if X else (None, None)
-    lo = pack(np.tile(case.vmin, (T, 1)), lo_th, np.tile(case.pmin, (T, 1)), np.tile(case.qmin, (T, 1)),
-              np.zeros((T, case.n_gen)), *xl)
-    hi = pack(np.tile(case.vmax, (T, 1)), hi_th, np.tile(case.pmax, (T, 1)), np.tile(case.qmax, (T, 1)),
-              np.tile(case.pmax, (T, 1)), *xh)
+    plo = np.zeros(G) if commit else case.pmin
+    qlo = np.minimum(case.qmin, 0.0) if commit else case.qmin
+    qhi = np.maximum(case.qmax, 0.0) if commit else case.qmax
+    rhi = np.where(device_sign(case) < 0, 0.0, case.pmax)
+    ul, uh = (np.zeros((T, G)), np.ones((T, G))) if commit else (None, None)
+    lo = pack(np.tile(case.vmin, (T, 1)), lo_th, np.tile(plo, (T, 1)), np.tile(qlo, (T, 1)),
+              np.zeros((T, G)), *xl, u=ul)
+    hi = pack(np.tile(case.vmax, (T, 1)), hi_th, np.tile(case.pmax, (T, 1)), np.tile(qhi, (T, 1)),
+              np.tile(rhi, (T, 1)), *xh, u=uh)
     return lo, hi
 
 
@@ -192,8 +219,34 @@ def ac_flow_partials(case, v, th, tau=None, phi=None):
     return out
 
 
+def energy_cost(case, p):
+    """(z, dz/dp), each (T, G): the energy cost (producers) or value (consumers) per hour before d_t.
+    A device with bid blocks (Example 3): z = sum_l c_l max(min(p - P_{l-1}, w_l), 0) with
+    P_{l-1} = w_1 + ... + w_{l-1}; its derivative is taken from the right (the price of the block
+    that p is entering: the one with 0 <= p - P_{l-1} < w_l, and 0 past the last block).  Devices
+    without blocks (all widths 0): z = a p^2 + b p."""
+    z = case.cost_a * p * p + case.cost_b * p
+    dz = 2 * case.cost_a * p + case.cost_b
+    W = getattr(case, "blk_width", None)
+    if W is None or W.size == 0:
+        return z, dz
+    C = case.blk_price
+    has = W.sum(axis=1) > 0
+    lo = np.zeros_like(W)
+    for l in range(1, W.shape[1]):
+        lo[:, l] = lo[:, l - 1] + W[:, l - 1]
+    zb = np.zeros_like(p)
+    db = np.zeros_like(p)
+    for l in range(W.shape[1]):
+        d = p - lo[None, :, l]
+        zb += C[None, :, l] * np.maximum(np.minimum(d, W[None, :, l]), 0.0)
+        db += np.where((d >= 0) & (d < W[None, :, l]), C[None, :, l], 0.0)
+    return np.where(has[None, :], zb, z), np.where(has[None, :], db, dz)
+
+
 def bus_mismatch(case, pf, qf, pt, qt, p, q):
-    """Example 4: P_it = sum(loads) + sum(fr flows) + sum(to flows) - sum(generators), same for Q."""
+    """Example 4: P_it = sum(loads) + sum(consumers) + sum(fr flows) + sum(to flows) - sum(producers),
+    same for Q (the fixed loads are consumption that has no variable)."""
     f, o = case.br_from, case.br_to
     P = case.load_p.copy()
     Q = case.load_q.copy()
@@ -201,8 +254,9 @@ def bus_mismatch(case, pf, qf, pt, qt, p, q):
     np.add.at(P.T, o, pt.T)
     np.add.at(Q.T, f, qf.T)
     np.add.at(Q.T, o, qt.T)
-    np.subtract.at(P.T, case.gen_bus, p.T)
-    np.subtract.at(Q.T, case.gen_bus, q.T)
+    sg = device_sign(case)
+    np.subtract.at(P.T, case.gen_bus, (sg * p).T)
+    np.subtract.at(Q.T, case.gen_bus, (sg * q).T)
     return P, Q
 
 
@@ -273,10 +327,10 @@ def outage_columns(case, net: DCNet):
 
 
 def dc_injections(case, p):
-    """p_inj = sum of generator output at the bus - load, then the uniform slack:
+    """p_inj = producers' output - consumers' draw at the bus - load, then the uniform slack:
     every bus takes 1/n of the imbalance (Sec. II-E slack paragraph)."""
     inj = -case.load_p.copy()
-    np.add.at(inj.T, case.gen_bus, p.T)
+    np.add.at(inj.T, case.gen_bus, (device_sign(case) * p).T)
     pbar = inj - inj.mean(axis=1, keepdims=True)
     return inj, pbar
 
@@ -439,11 +493,26 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     gv = np.zeros((T, n)); gth = np.zeros((T, n)); gp = np.zeros((T, G)); gq = np.zeros((T, G))
     gr = np.zeros((T, G))
     terms = {k: 0.0 for k in TERM_NAMES}
+    sg = device_sign(case)
+    uo = unpack_u(case, x)
+    gu = None if uo is None else np.zeros((T, G))
 
-    # --- generator energy and reserve cost
-    terms["cost"] = float((dt[:, None] * (case.cost_a * p * p + case.cost_b * p + case.cost_r * r)).sum())
-    gp += dt[:, None] * (2 * case.cost_a * p + case.cost_b)
+    # --- device energy cost / value (Example 3; a consumer's value enters with a minus sign, so that
+    #     minimizing the objective maximizes the market surplus) and reserve cost
+    zen, dzen = energy_cost(case, p)
+    terms["cost"] = float((dt[:, None] * (sg * zen + case.cost_r * r)).sum())
+    gp += dt[:, None] * sg * dzen
     gr += dt[:, None] * case.cost_r
+
+    # --- on/off status (Example 2): on cost d_t c_on u, startup c_su max(u_t - u_{t-1}, 0) and shutdown
+    #     c_sd max(u_{t-1} - u_t, 0), with u_init before period 0 (derivative of max(., 0) at 0 taken as 0)
+    if uo is not None:
+        du = uo - np.vstack([case.u_init[None, :], uo[:-1]])
+        terms["cost"] += float((dt[:, None] * case.c_on * uo + case.c_su * np.maximum(du, 0.0)
+                                + case.c_sd * np.maximum(-du, 0.0)).sum())
+        ddu = np.where(du > 0, case.c_su, 0.0) - np.where(du < 0, case.c_sd, 0.0)
+        gu += dt[:, None] * case.c_on + ddu
+        gu[:-1] -= ddu[1:]
 
     # --- AC flows and bus balance (Example 4)
     pf, qf, pt, qt = ac_flows(case, v, th, tau, phi)
@@ -459,8 +528,8 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     g_pt = dP[:, o].copy()
     g_qf = dQ[:, f].copy()
     g_qt = dQ[:, o].copy()
-    gp -= dP[:, case.gen_bus]
-    gq -= dQ[:, case.gen_bus]
+    gp -= sg * dP[:, case.gen_bus]
+    gq -= sg * dQ[:, case.gen_bus]
 
     # --- thermal limit on the worse end (Example 1)
     sf = np.sqrt(pf * pf + qf * qf)
@@ -486,13 +555,24 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
     dZ = wz * soft_relu_grad(uz, eps_)
     gr -= dZ[:, case.gen_zone]
 
-    # --- penalized linear constraints rho * sigma_s(violation): headroom and ramps
+    # --- penalized linear constraints rho * sigma_s(violation): headroom and ramps; with on/off
+    #     status the limits scale by u: p + r <= pmax u, p >= pmin u, qmin u <= q <= qmax u
     wr = case.rho * beta
-    uh = p + r - case.pmax[None, :]
+    uon = 1.0 if uo is None else uo
+    uh = p + r - case.pmax[None, :] * uon
     terms["zhead"] = float((wr * soft_relu(uh, eps_)).sum())
     dH = wr * soft_relu_grad(uh, eps_)
     gp += dH
     gr += dH
+    if uo is not None:
+        gu -= case.pmax * dH
+        lims = ((case.pmin * uo - p, gp, -1.0, case.pmin), (q - case.qmax * uo, gq, 1.0, -case.qmax),
+                (case.qmin * uo - q, gq, -1.0, case.qmin))
+        for viol, gvar, sgn, cu in lims:
+            terms["zhead"] += float((wr * soft_relu(viol, eps_)).sum())
+            dl = wr * soft_relu_grad(viol, eps_)
+            gvar += sgn * dl
+            gu += cu * dl
     if T > 1:
         lim = case.ramp[None, :] * dt[1:, None]
         up = p[1:] - p[:-1] - lim
@@ -529,7 +609,7 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
             gq2_all[t] = gq2
             gb_all[t] = gb
     terms["zctg"] = float(z_ctg.sum())
-    gp += gin_all[:, case.gen_bus]
+    gp += sg * gin_all[:, case.gen_bus]
     g_qf += np.where(use_qf, 2 * qf * gq2_all, 0.0)
     g_qt += np.where(~use_qf, 2 * qt * gq2_all, 0.0)
 
@@ -551,7 +631,7 @@ def evaluate(case, x, want_grad: bool = True, mode: str = "smw", eps: Optional[f
         # phi enters delta = theta_f - theta_o - phi (AC) and b = -y phi (contingency DC flows)
         gphi = -gd[:, xf] - net.y[xf][None, :] * gb_all[:, xf]
     obj = float(sum(terms.values()))
-    grad = pack(gv, gth, gp, gq, gr, gtau, gphi) if want_grad else None
+    grad = pack(gv, gth, gp, gq, gr, gtau, gphi, gu) if want_grad else None
     return Result(obj=obj, grad=grad, terms=terms, z_ctg=z_ctg, g_inj=gin_all)
 
 

@@ -538,7 +538,10 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   for (int b = 0; b < B; ++b)
     if (h->hi[b].Ks > 0) tiles += (long long)ceil_div(h->hi[b].M, CT_BM) * ceil_div(h->hi[b].Ks, CT_BK);
   const int ntc_all = (int)std::max(1LL, tiles > 0 ? CTG_WAVE / tiles : 1);
-  const int mg_all = (int)std::max(1LL, tiles / (4LL * CTG_WAVE));
+  // at most ~64 column partials per outage for stage 3 to sum serially
+  int max_nmt = 0;
+  for (int b = 0; b < B; ++b) max_nmt = std::max(max_nmt, ceil_div(h->hi[b].M, CT_BM));
+  const int mg_all = (int)std::max({1LL, tiles / (4LL * CTG_WAVE), (long long)ceil_div(max_nmt, 64)});
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];

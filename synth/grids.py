@@ -84,6 +84,19 @@ class Case:
     tau_max: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     phi_min: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))  # [X] rad
     phi_max: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    # devices: producers by default; consumers draw p, q (balance sign +) and earn their bid value.
+    # Block bids (Example 3): blk_price[g, l] per pu over blocks of width blk_width[g, l]; devices
+    # without blocks (all widths 0) use the quadratic cost a p^2 + b p.
+    dev_cons: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, bool))  # [G]
+    blk_price: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 0)))  # [G, L]
+    blk_width: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 0)))  # [G, L]
+    # on/off status (Example 2): with commit, per-period variables u in [0, 1] (relaxed binaries), an
+    # on cost c_on per hour, startup / shutdown costs c_su, c_sd per event, u_init before period 0
+    commit: bool = False
+    c_on: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))  # [G]
+    c_su: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    c_sd: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    u_init: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     # penalty prices / smoothing (chosen readings; the paper does not state them)
     c_p: float = 1e4
     c_q: float = 1e4
@@ -102,8 +115,12 @@ class Case:
         return int(self.xf_branch.shape[0])
 
     @property
+    def n_cons(self) -> int:
+        return int(np.count_nonzero(self.dev_cons))
+
+    @property
     def n_x(self) -> int:
-        return self.T * (2 * self.n_bus + 3 * self.n_gen + 2 * self.n_xf)
+        return self.T * (2 * self.n_bus + 3 * self.n_gen + 2 * self.n_xf + (self.n_gen if self.commit else 0))
 
     def offsets(self):
         """Start of the v, theta, p, q, r blocks in x (each block is T rows, period-major)."""
@@ -114,6 +131,10 @@ class Case:
         """Start of the tau and phi blocks (T x X each), after r."""
         o = self.T * (2 * self.n_bus + 3 * self.n_gen)
         return (o, o + self.T * self.n_xf)
+
+    def offset_u(self):
+        """Start of the on-status block u (T x G, after phi; empty without commit)."""
+        return self.T * (2 * self.n_bus + 3 * self.n_gen + 2 * self.n_xf)
 
     def flat_start(self, p: Optional[np.ndarray] = None, r: Optional[np.ndarray] = None) -> np.ndarray:
         """x with v = 1, theta = 0, q = 0 and the given dispatch (default: Pmax-proportional)."""
@@ -128,6 +149,8 @@ class Case:
             x[orr:orr + T * G] = np.asarray(r, dtype=np.float64).reshape(T * G)
         otau, _ = self.offsets_xf()
         x[otau:otau + T * self.n_xf] = 1.0  # tau = 1, phi = 0
+        if self.commit:
+            x[self.offset_u():] = 1.0  # every device on
         return x
 
 
@@ -436,6 +459,54 @@ def with_transformers(case: Case, frac: float = 0.15, seed: int = 0) -> Case:
                                phi_max=np.where(shifter, 0.3, 0.0))
 
 
+def with_block_bids(case: Case, n_blocks: int = 3, cons_frac: float = 0.3, seed: int = 0) -> Case:
+    """The same case with block bids (Example 3) on every device and a fraction of the buses given a
+    dispatchable consumer: each producer's [0, Pmax] split into n_blocks blocks of rising price (a
+    convex cost); consumers take part of their bus's load, p in [0, 1.2 x that part] bid in blocks of
+    falling value (a concave value), with q = 0.329 p bounds; the fixed load of those buses drops by
+    the consumers' nominal share."""
+    rng = np.random.default_rng(seed)
+    G, n, T = case.n_gen, case.n_bus, case.T
+    nc = max(1, int(round(cons_frac * n)))
+    cbus = np.sort(rng.choice(n, size=nc, replace=False)).astype(np.int32)
+    share = rng.uniform(0.2, 0.5, size=nc)
+    nominal = case.load_p[:, cbus].max(axis=0) * share
+    load_p = case.load_p.copy()
+    load_p[:, cbus] *= (1.0 - share)[None, :]
+    load_q = 0.329 * load_p
+    L = n_blocks
+    width = np.zeros((G + nc, L))
+    price = np.zeros((G + nc, L))
+    width[:G] = case.pmax[:, None] / L
+    base = case.cost_b + case.cost_a * case.pmax / L
+    steps = np.cumsum(rng.uniform(1.0, 8.0, size=(G, L)), axis=1)
+    price[:G] = base[:, None] + steps
+    cmax = 1.2 * nominal
+    width[G:] = cmax[:, None] / L
+    price[G:] = rng.uniform(60.0, 90.0, size=nc)[:, None] - np.cumsum(rng.uniform(2.0, 10.0, size=(nc, L)), axis=1)
+    cat = lambda a, b: np.concatenate([a, b])
+    return dataclasses.replace(
+        case, name=case.name + "_bids", n_gen=G + nc, gen_bus=cat(case.gen_bus, cbus),
+        gen_zone=cat(case.gen_zone, case.bus_zone[cbus]).astype(np.int32), cost_a=cat(case.cost_a, np.zeros(nc)),
+        cost_b=cat(case.cost_b, np.zeros(nc)), cost_r=cat(case.cost_r, np.zeros(nc)), pmin=cat(case.pmin, np.zeros(nc)),
+        pmax=cat(case.pmax, cmax), qmin=cat(case.qmin, np.zeros(nc)), qmax=cat(case.qmax, 0.329 * cmax),
+        ramp=cat(case.ramp, cmax), load_p=load_p, load_q=load_q,
+        dev_cons=cat(np.zeros(G, bool), np.ones(nc, bool)), blk_price=price, blk_width=width)
+
+
+def with_commitment(case: Case, seed: int = 0, off_frac: float = 0.2) -> Case:
+    """The same case with on/off status variables (Example 2): per device an on cost of 1-5 $/h per
+    pu of Pmax, startup cost of 10-40 and shutdown cost of 0-10 $ per pu of Pmax, and a fraction
+    off_frac of the devices off before period 0."""
+    rng = np.random.default_rng(seed)
+    G = case.n_gen
+    scale = np.maximum(case.pmax, 1e-3)
+    u_init = (rng.uniform(size=G) >= off_frac).astype(np.float64)
+    return dataclasses.replace(
+        case, name=case.name + "_uc", commit=True, c_on=rng.uniform(1.0, 5.0, G) * scale,
+        c_su=rng.uniform(10.0, 40.0, G) * scale, c_sd=rng.uniform(0.0, 10.0, G) * scale, u_init=u_init)
+
+
 def horizon_slice(case: Case, t0: int, t1: int) -> Case:
     """The same network over periods [t0, t1) of the horizon only."""
     return dataclasses.replace(case, T=t1 - t0, dt=case.dt[t0:t1].copy(), load_p=case.load_p[t0:t1].copy(),
@@ -463,8 +534,12 @@ def random_point(case: Case, seed: int, spread: float = 1.0) -> np.ndarray:
     p = rng.uniform(case.pmin, case.pmax, size=(T, G))
     q = rng.uniform(case.qmin, case.qmax, size=(T, G))
     r = rng.uniform(0.0, 0.3, size=(T, G)) * case.pmax
+    if case.n_cons:
+        r[:, case.dev_cons] = 0.0  # consumers hold no reserve
     parts = [v.ravel(), th.ravel(), p.ravel(), q.ravel(), r.ravel()]
     if case.n_xf:
         parts.append(rng.uniform(case.tau_min, case.tau_max, size=(T, case.n_xf)).ravel())
         parts.append(rng.uniform(case.phi_min, case.phi_max, size=(T, case.n_xf)).ravel())
+    if case.commit:
+        parts.append(rng.uniform(0.0, 1.0, size=(T, G)).ravel())
     return np.concatenate(parts)
