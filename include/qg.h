@@ -20,9 +20,9 @@
  *    qg_create*, qg_eval_grad_host, qg_breakdown and qg_get_state.
  *  - Variable layout of one instance (qg_layout): period-major blocks
  *        x = [ v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G)
- *              | tau (T x X) | phi (T x X) ]
- *    (the transformer blocks are empty when X = 0), and batched instances are
- *    concatenated in creation order.
+ *              | tau (T x X) | phi (T x X) | u (T x G) ]
+ *    (the transformer blocks are empty when X = 0, the on-status block u when
+ *    commit = 0), and batched instances are concatenated in creation order.
  *  - Per-unit quantities, periods of dt hours.
  */
 #ifndef QG_H
@@ -50,8 +50,8 @@ enum { QG_DC_AUTO = 0, QG_DC_DENSE = 1, QG_DC_SPARSE = 2 };      /* qg_options.d
 
 typedef struct qg_ctx qg_ctx; /* opaque handle; owns all device memory it allocates */
 
-/* Network of one instance (Sec. II-B reduced to v, theta, p, q, r and the
- * transformer variables tau, phi; integers relaxed and fixed on).
+/* Network of one instance (Sec. II-B reduced to v, theta, p, q, r, the
+ * transformer variables tau, phi and, optionally, relaxed on-status variables u).
  *   br_from/br_to [M]  bus indices in [0, n), from != to
  *   br_r, br_x [M]     series impedance r + jx (x > 0); g + jb = 1/(r + jx)
  *   br_b [M]           total line charging b_ch (pi model, b_ch/2 per end)
@@ -65,7 +65,24 @@ typedef struct qg_ctx qg_ctx; /* opaque handle; owns all device memory it alloca
  *                       shift phi at the "fr" end (Sec. II-F line-flow example; the AC flows
  *                       use v_f / tau and delta = theta_f - theta_o - phi) whose DC contingency
  *                       flow is -b_sr (theta_f - theta_o - phi) (Sec. II-E); tau, phi are
- *                       per-period variables in [tau_min, tau_max] (> 0), [phi_min, phi_max] */
+ *                       per-period variables in [tau_min, tau_max] (> 0), [phi_min, phi_max]
+ * Devices ("generators" above; every field below is optional: 0 / NULL keeps every device a
+ * producer with the quadratic cost that is always on):
+ *   dev_cons [G]        nonzero marks a consumer: its p, q are drawn from its bus (Example 4 adds
+ *                       them to the bus's consumption) and its cost curve is a value that the
+ *                       objective subtracts (market surplus); its reserve r is held at 0
+ *   n_blk, blk_price, blk_width [G x n_blk] row-major: bid blocks of Example 3; the energy cost
+ *                       (value) per hour is sum_l c_l max(min(p - P_{l-1}, w_l), 0) with
+ *                       P_{l-1} = w_1 + ... + w_{l-1}, its p-derivative the price of the block that
+ *                       p is entering (0 past the last block).  Widths >= 0; a device whose widths
+ *                       are all 0 keeps the quadratic cost a p^2 + b p
+ *   commit              1: per-period on-status u in [0, 1] (relaxed binaries) with the on cost
+ *                       d_t c_on u, startup c_su max(u_t - u_{t-1}, 0) and shutdown
+ *                       c_sd max(u_{t-1} - u_t, 0) (Example 2; u_{-1} = u_init in [0, 1]); the limits
+ *                       p + r <= pmax u, p >= pmin u, qmin u <= q <= qmax u become penalized linear
+ *                       constraints (weight rho beta, soft-ReLU), and the box keeps p in [0, pmax],
+ *                       q in [min(qmin, 0), max(qmax, 0)].  c_on, c_su, c_sd >= 0 and u_init [G]
+ *                       are required when commit = 1 */
 typedef struct {
   int32_t n_bus, n_branch, n_gen, n_zone, ref_bus;
   const int32_t *br_from, *br_to;
@@ -76,6 +93,11 @@ typedef struct {
   int32_t n_xf;
   const int32_t *xf_branch;
   const double *tau_min, *tau_max, *phi_min, *phi_max;
+  const int32_t *dev_cons;
+  int32_t n_blk;
+  const double *blk_price, *blk_width;
+  int32_t commit;
+  const double *c_on, *c_su, *c_sd, *u_init;
 } qg_network;
 
 /* Horizon: T periods of dt[t] hours; load_p, load_q are T x n period-major;
@@ -142,9 +164,9 @@ void qg_destroy(qg_ctx *h);
 int64_t qg_num_vars(const qg_ctx *h);
 
 /* Layout of instance `inst`: its first variable in the concatenated x, its
- * n_x = T (2n + 3G + 2X), and the starts of the v, theta, p, q, r, tau, phi
- * blocks relative to that first variable. */
-int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[7]);
+ * n_x = T (2n + 3G + 2X + commit G), and the starts of the v, theta, p, q, r, tau,
+ * phi, u blocks relative to that first variable. */
+int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[8]);
 
 /* Order all later device work on `stream` (a cudaStream_t; NULL = default). */
 int qg_set_stream(qg_ctx *h, void *stream);
@@ -183,8 +205,10 @@ int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g);
  * last qg_eval_grad on this handle (kept internally):
  *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; x -= lr mhat/(sqrt(vhat)+eps);
  *   x = clip(x, box) with v in [vmin, vmax], theta_ref = 0, p in [pmin, pmax],
- *   q in [qmin, qmax], r in [0, pmax].  The step counter i (bias correction) is
- *   kept in the handle and advanced by one. */
+ *   q in [qmin, qmax], r in [0, pmax] (0 for consumers), tau, phi in their
+ *   ranges, u in [0, 1] (with commit, p in [0, pmax], q in [min(qmin, 0),
+ *   max(qmax, 0)]).  The step counter i (bias correction) is kept in the handle
+ *   and advanced by one. */
 int qg_adam_step(qg_ctx *h, void *x, void *m, void *v, double lr, double beta1, double beta2);
 
 /* iters iterations of (qg_eval_grad; qg_adam_step) on x in place, with Adam
@@ -220,7 +244,9 @@ int qg_schedule(double *out, int32_t iters, double lr0, double lrf, double eps0,
 
 /* Per-instance penalty breakdown of the last evaluation, host array of
  * 8 x n_inst doubles: cost, z_p, z_q, z_s, z_rz, z_headroom, z_ramp, z_ctg.
- * Synchronizes the stream. */
+ * cost is energy cost minus consumer value plus reserve cost, and with commit the
+ * on, startup and shutdown costs; z_headroom holds every device-limit penalty
+ * (with commit the four u-scaled limits).  Synchronizes the stream. */
 int qg_breakdown(qg_ctx *h, double *out);
 
 /* Adam step counter (for checkpoint/resume together with x, m, v);

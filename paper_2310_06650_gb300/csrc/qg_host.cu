@@ -38,6 +38,12 @@ struct HostInst {
   std::vector<double> tau_lo, tau_hi, phi_lo, phi_hi;
   std::vector<double> r, x, bch, smax, sctg, ca, cb, cr, pmin, pmax, qmin, qmax, ramp, vmin, vmax;
   std::vector<double> dt, load_p, load_q, rreq;
+  // device models: consumers, bid blocks (Example 3), on-status with startup / shutdown (Example 2)
+  std::vector<int> cons;                         // [G] 1 = consumer
+  int L = 0;                                     // bid blocks per device
+  std::vector<double> blk_c, blk_w;              // [G x L]
+  bool commit = false;
+  std::vector<double> c_on, c_su, c_sd, u_init;  // [G]
   // derived (FP64)
   std::vector<double> y, gsr, bsr;
   int Gc = 0;                 // dense DC product columns: generator buses, then transformers
@@ -199,9 +205,31 @@ int read_instance(qg_ctx *h, const qg_network &N, const qg_horizon &H, const qg_
         return bad("transformer limits");
     }
   }
+  I.cons.assign(G, 0);
+  if (N.dev_cons)
+    for (int g = 0; g < G; ++g) I.cons[g] = N.dev_cons[g] != 0;
+  if (N.n_blk < 0 || N.n_blk > 64) return bad("n_blk out of range [0, 64]");
+  I.L = N.n_blk;
+  if (I.L > 0) {
+    if (!N.blk_price || !N.blk_width) return bad("null bid-block array");
+    I.blk_c = cp(N.blk_price, G * I.L);
+    I.blk_w = cp(N.blk_width, G * I.L);
+    for (double w : I.blk_w)
+      if (!(w >= 0.0)) return bad("bid-block widths must be >= 0");
+  }
+  if (N.commit != 0 && N.commit != 1) return bad("commit must be 0 or 1");
+  I.commit = N.commit == 1;
+  if (I.commit) {
+    if (!N.c_on || !N.c_su || !N.c_sd || !N.u_init) return bad("null commitment array");
+    I.c_on = cp(N.c_on, G); I.c_su = cp(N.c_su, G); I.c_sd = cp(N.c_sd, G); I.u_init = cp(N.u_init, G);
+    for (int g = 0; g < G; ++g)
+      if (!(I.c_on[g] >= 0.0) || !(I.c_su[g] >= 0.0) || !(I.c_sd[g] >= 0.0) || !(I.u_init[g] >= 0.0) ||
+          !(I.u_init[g] <= 1.0))
+        return bad("commitment costs must be >= 0 and u_init in [0, 1]");
+  }
   for (auto *v : {&I.r, &I.x, &I.bch, &I.smax, &I.sctg, &I.ca, &I.cb, &I.cr, &I.pmin, &I.pmax, &I.qmin, &I.qmax,
                   &I.ramp, &I.vmin, &I.vmax, &I.dt, &I.load_p, &I.load_q, &I.rreq, &I.tau_lo, &I.tau_hi, &I.phi_lo,
-                  &I.phi_hi})
+                  &I.phi_hi, &I.blk_c, &I.blk_w, &I.c_on, &I.c_su, &I.c_sd})
     if (!finite_all(*v)) return bad("non-finite input");
   return QG_OK;
 }
@@ -550,6 +578,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     D.Kp = ceil_div(H.Ks, 4) * 4;
     D.X = H.X; D.xf0 = xf0; D.Gc = H.Gc; D.tx0 = tx0;
     D.xtau0 = x0 + (long long)H.T * (2LL * H.n + 3LL * H.G);
+    D.xu0 = D.xtau0 + 2LL * H.T * H.X;
+    D.uc = H.commit ? 1 : 0;
     D.bus0 = bus0; D.br0 = br0; D.gen0 = gen0; D.zone0 = zone0; D.ctg0 = ctg0; D.gb0 = gb0; D.tp0 = tp0;
     D.n_mt = ceil_div(H.M, CT_BM);
     D.n_kt = ceil_div(H.Ks, CT_BK);
@@ -566,7 +596,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
     D.hours = 0.0;
     for (int t = 0; t < H.T; ++t) D.hours += H.dt[t];
     D.nfloor_ctg = (double)H.M * H.Ks - H.Ks;
-    x0 += (long long)H.T * (2LL * H.n + 3LL * H.G + 2LL * H.X);
+    x0 += (long long)H.T * (2LL * H.n + 3LL * H.G + 2LL * H.X + (H.commit ? H.G : 0));
     tx0 += (long long)H.T * H.X; xf0 += H.X;
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
     tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.Ks; pg0 += (long long)H.M * D.Gc; l0 += (long long)H.M * D.Kp;
@@ -695,7 +725,8 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   std::vector<int> br_kidx, gen_bus, gen_zone, gen_gb, gb_ptr{0}, gb_gen, zgen_ptr{0}, zgen, ctg_br, bal_code, bal_row,
       adj_code, adj_row, br_xf, xf_br;
   std::vector<double> br_g, br_b, br_hch, br_smax, br_s2, ga, gbv, gcr, gpmax, gramp, load_p, load_q, rreq, dt, lo, hi,
-      ltot, ptdfg, ptdfgT, cload, rsum, lodf;
+      ltot, ptdfg, ptdfgT, cload, rsum, lodf, gsgn, gpmin, gqmin, gqmax, gcon, gcsu, gcsd, guinit, blk_c, blk_lo, blk_w;
+  std::vector<int> blk_ptr{0};
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
     const Inst &D = P.tab.I[b];
@@ -720,6 +751,24 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
       gen_gb.push_back(H.gen_gb[g]);
       ga.push_back(H.ca[g]); gbv.push_back(H.cb[g]); gcr.push_back(H.cr[g]); gpmax.push_back(H.pmax[g]);
       gramp.push_back(H.ramp[g]);
+      gsgn.push_back(H.cons[g] ? -1.0 : 1.0);
+      gpmin.push_back(H.pmin[g]); gqmin.push_back(H.qmin[g]); gqmax.push_back(H.qmax[g]);
+      gcon.push_back(H.commit ? H.c_on[g] : 0.0); gcsu.push_back(H.commit ? H.c_su[g] : 0.0);
+      gcsd.push_back(H.commit ? H.c_sd[g] : 0.0); guinit.push_back(H.commit ? H.u_init[g] : 1.0);
+      // bid blocks: kept only for devices with a positive total width; the cumulative starts are
+      // summed in FP64 in block order
+      double tot = 0.0;
+      for (int l = 0; l < H.L; ++l) tot += H.blk_w[(size_t)g * H.L + l];
+      if (tot > 0.0) {
+        double cum = 0.0;
+        for (int l = 0; l < H.L; ++l) {
+          blk_c.push_back(H.blk_c[(size_t)g * H.L + l]);
+          blk_lo.push_back(cum);
+          blk_w.push_back(H.blk_w[(size_t)g * H.L + l]);
+          cum += H.blk_w[(size_t)g * H.L + l];
+        }
+      }
+      blk_ptr.push_back((int)blk_c.size());
     }
     std::vector<std::vector<int>> gbg(H.gbus.size()), zg(H.Z);
     for (int g = 0; g < H.G; ++g) {
@@ -770,16 +819,24 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
         lo.push_back(i == H.ref ? 0.0 : -inf);
         hi.push_back(i == H.ref ? 0.0 : inf);
       }
+    // with commitment the u-scaled limits are penalties and the box only keeps p >= 0 and q's range
+    // around 0; consumers hold no reserve
     for (int t = 0; t < H.T; ++t)
-      for (int g = 0; g < H.G; ++g) { lo.push_back(H.pmin[g]); hi.push_back(H.pmax[g]); }
+      for (int g = 0; g < H.G; ++g) { lo.push_back(H.commit ? 0.0 : H.pmin[g]); hi.push_back(H.pmax[g]); }
     for (int t = 0; t < H.T; ++t)
-      for (int g = 0; g < H.G; ++g) { lo.push_back(H.qmin[g]); hi.push_back(H.qmax[g]); }
+      for (int g = 0; g < H.G; ++g) {
+        lo.push_back(H.commit ? std::min(H.qmin[g], 0.0) : H.qmin[g]);
+        hi.push_back(H.commit ? std::max(H.qmax[g], 0.0) : H.qmax[g]);
+      }
     for (int t = 0; t < H.T; ++t)
-      for (int g = 0; g < H.G; ++g) { lo.push_back(0.0); hi.push_back(H.pmax[g]); }
+      for (int g = 0; g < H.G; ++g) { lo.push_back(0.0); hi.push_back(H.cons[g] ? 0.0 : H.pmax[g]); }
     for (int t = 0; t < H.T; ++t)
       for (int q = 0; q < H.X; ++q) { lo.push_back(H.tau_lo[q]); hi.push_back(H.tau_hi[q]); }
     for (int t = 0; t < H.T; ++t)
       for (int q = 0; q < H.X; ++q) { lo.push_back(H.phi_lo[q]); hi.push_back(H.phi_hi[q]); }
+    if (H.commit)
+      for (int t = 0; t < H.T; ++t)
+        for (int g = 0; g < H.G; ++g) { lo.push_back(0.0); hi.push_back(1.0); }
   }
   int rc = 0;
   {
@@ -798,6 +855,9 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   UPI(bal_row, bal_row) UPI(adj_code, adj_code) UPI(adj_row, adj_row) UPI(br_xf, br_xf) UPI(xf_br, xf_br)
   UPR(br_g, br_g) UPR(br_b, br_b) UPR(br_hch, br_hch) UPR(br_smax, br_smax) UPR(br_s2ctg, br_s2)
   UPR(gen_a, ga) UPR(gen_b, gbv) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax) UPR(gen_ramp, gramp)
+  UPR(gen_sgn, gsgn) UPR(gen_pmin, gpmin) UPR(gen_qmin, gqmin) UPR(gen_qmax, gqmax) UPR(gen_con, gcon)
+  UPR(gen_csu, gcsu) UPR(gen_csd, gcsd) UPR(gen_uinit, guinit) UPI(blk_ptr, blk_ptr) UPR(blk_c, blk_c)
+  UPR(blk_lo, blk_lo) UPR(blk_w, blk_w)
   UPR(load_p, load_p) UPR(load_q, load_q) UPR(rreq, rreq) UPR(dt, dt) UPR(lo, lo) UPR(hi, hi)
   UPD(ltot, ltot) UPD(ptdfg, ptdfg) UPD(ptdfgT, ptdfgT) UPD(cload, cload) UPD(rsum, rsum)
 #undef UPI
@@ -929,7 +989,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
 #define WR(field, cnt) if ((rc = dalloc(h, &w, (size_t)(cnt)))) return rc; d.field = w;
 #define WD(field, cnt) if ((rc = dalloc(h, &c, (size_t)(cnt)))) return rc; d.field = c;
 #define WF(field, cnt) if ((rc = dalloc(h, &fl, (size_t)(cnt)))) return rc; d.field = fl;
-  WR(pf, sTM) WR(qf, sTM) WR(pt, sTM) WR(qt, sTM) WR(qm2, sTM) WR(fre, sTM) WR(fk, sTK) WR(pold, sTG)
+  WR(pf, sTM) WR(qf, sTM) WR(pt, sTM) WR(qt, sTM) WR(qm2, sTM) WR(fre, sTM) WR(fk, sTK) WR(pold, sTG) WR(uold, sTG)
   WR(dP, sTn) WR(dQ, sTn) WR(dZ, sTZ) WR(pm, sPM) WR(pq, sPM) WR(pk, sPK) WR(gF, sTM) WR(avf, sTM) WR(avo, sTM)
   WR(ad, sTM) WR(atx, sTX)
   WD(gip, sGI)
@@ -1100,6 +1160,7 @@ size_t carve_scratch(const qg_ctx *h, unsigned char *base, size_t cap, Dev<Real,
   d.ad = (Real *)take(R * sTM); d.qside = take(sTM); d.f32 = (float *)take(4 * sTM);
   d.atx = (Real *)take(R * std::max(1LL, sTX));
   d.fk = (Real *)take(R * sTK); d.fk32 = (float *)take(4 * sTK); d.pold = (Real *)take(R * sTG);
+  d.uold = (Real *)take(R * sTG);
   d.dP = (Real *)take(R * sTn); d.dQ = (Real *)take(R * sTn); d.dZ = (Real *)take(R * sTZ);
   d.pm = (Real *)take(R * sPM); d.pq = (Real *)take(R * sPM); d.pk = (Real *)take(R * sPK);
   {
@@ -1260,15 +1321,15 @@ void qg_destroy(qg_ctx *h) {
 
 int64_t qg_num_vars(const qg_ctx *h) { return h ? h->n_x : 0; }
 
-int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[7]) {
+int qg_layout(const qg_ctx *h, int32_t inst, int64_t *first, int64_t *n_x, int64_t offsets[8]) {
   if (!h || inst < 0 || inst >= h->n_inst) return QG_ERR_INVALID_ARG;
   const Inst &I = h->plan.tab.I[inst];
   const int64_t Tn = (int64_t)I.T * I.n, TG = (int64_t)I.T * I.G, TX = (int64_t)I.T * I.X;
   if (first) *first = I.x0;
-  if (n_x) *n_x = 2 * Tn + 3 * TG + 2 * TX;
+  if (n_x) *n_x = 2 * Tn + 3 * TG + 2 * TX + (I.uc ? TG : 0);
   if (offsets) {
     offsets[0] = 0; offsets[1] = Tn; offsets[2] = 2 * Tn; offsets[3] = 2 * Tn + TG; offsets[4] = 2 * Tn + 2 * TG;
-    offsets[5] = 2 * Tn + 3 * TG; offsets[6] = 2 * Tn + 3 * TG + TX;
+    offsets[5] = 2 * Tn + 3 * TG; offsets[6] = 2 * Tn + 3 * TG + TX; offsets[7] = 2 * Tn + 3 * TG + 2 * TX;
   }
   return QG_OK;
 }
@@ -1532,6 +1593,6 @@ int32_t qg_launches_per_eval(const qg_ctx *h) {
   return 5 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0);
 }
 
-int qg_version(void) { return 201; }
+int qg_version(void) { return 300; }
 
 }  // extern "C"

@@ -46,6 +46,8 @@ struct Inst {
   long long gi0;         // adjoint DC products: [T][Gc + 1] (generator buses, transformers, then n mean(eta))
   long long tx0;         // per-period transformer arrays: [T][X]
   long long xtau0;       // first tau variable (x0 + T (2n + 3G)); phi follow after T X
+  long long xu0;         // first on-status variable (after phi; meaningful when uc)
+  int uc;                // 1: on-status variables u with startup / shutdown costs (Example 2)
   double inv_n;          // 1 / n
   double hours;          // sum of dt
   double nfloor_ctg;     // M K - K: elements whose soft-ReLU floor eps the contingency term adds in closed form
@@ -96,6 +98,11 @@ struct Dev {
   const Real *br_g, *br_b, *br_hch, *br_smax, *br_s2ctg;  // g_sr, b_sr, b_ch / 2, s_max, s_ctg^2
   const int *gen_bus, *gen_zone, *gen_gb;                 // local bus, local zone, local generator-bus index
   const Real *gen_a, *gen_b, *gen_cr, *gen_pmax, *gen_ramp;
+  const Real *gen_sgn;                // +1 producer, -1 consumer (sign of p, q as supply)
+  const Real *gen_pmin, *gen_qmin, *gen_qmax;             // limits scaled by u (commitment)
+  const Real *gen_con, *gen_csu, *gen_csd, *gen_uinit;    // on / startup / shutdown cost, u before period 0
+  const int *blk_ptr;                 // [sum G + 1] bid blocks of each device (Example 3); none: quadratic cost
+  const Real *blk_c, *blk_lo, *blk_w; // block price, cumulative start P_{l-1}, width
   const int *gb_ptr, *gb_gen;         // generator bus -> generators: one CSR over the batch's generator buses
   const int *zgen_ptr, *zgen;         // zone -> generators: one CSR over the batch's zones (global ids)
   const int *ctg_br;                  // [sum K] local branch id of each outage
@@ -153,6 +160,7 @@ struct Dev {
   Real *fk;                           // [sum T K] base flows on outaged branches
   float *fk32;                        // [sum T K]
   Real *pold;                         // [sum T G] dispatch snapshot for the fused Adam ramp terms
+  Real *uold;                         // [sum T G] on-status snapshot for the startup / shutdown terms
   Real *dP, *dQ;                      // [sum T n]
   Real *dZ;                           // [sum T Z]
   Real *pm, *pq, *pk;                 // contingency partials

@@ -386,18 +386,21 @@ __device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, con
   }
 }
 
-// Dispatch snapshot for the ramp terms of a fused Adam update (stage 5 reads the pre-update p of the
-// neighbouring periods): the periods [t0, t0 + 8) of a DC-flow block row, split evenly over the
-// row's blocks.
+// Dispatch (and on-status) snapshot for the ramp (and startup / shutdown) terms of a fused Adam
+// update (stage 5 reads the pre-update p, u of the neighbouring periods): the periods [t0, t0 + 8)
+// of a DC-flow block row, split evenly over the row's blocks.
 template <typename Real, typename Dc>
 __device__ __forceinline__ void pold_share(const Dev<Real, Dc> &d, const Inst &I, int t0, int sub,
-                                           const Real *__restrict__ p) {
+                                           const Real *__restrict__ x) {
   const int tn = min(DCF_TC, I.T - t0);
   const int n = tn * I.G, nsub = (I.M + DCF_BM - 1) / DCF_BM;
   const int per = (n + nsub - 1) / nsub;
   const int lo = min(n, sub * per), hi = min(n, lo + per);
   const long long base = (long long)t0 * I.G;
+  const Real *p = x + I.x0 + 2LL * I.T * I.n;
   for (int e = lo + threadIdx.x; e < hi; e += NTHR) d.pold[I.tg0 + base + e] = p[base + e];
+  if (I.uc)
+    for (int e = lo + threadIdx.x; e < hi; e += NTHR) d.uold[I.tg0 + base + e] = x[I.xu0 + base + e];
 }
 
 // Base DC flows of branches [m0, m0+32) in periods [t0, t0+8):
@@ -412,7 +415,7 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   const int tl = threadIdx.x >> 5, ml = threadIdx.x & 31;
   const int t = t0 + tl, m = m0 + ml;
   const Real *p = x + I.x0 + 2LL * I.T * I.n;
-  pold_share(d, I, t0, sub, p);
+  pold_share(d, I, t0, sub, x);
   Dc acc = DcOps<Dc>::zero();
   Dc tot = DcOps<Dc>::zero();  // running sum of p_G over generator buses for mu_t (warp tl)
   // columns: generator buses (their dispatch), then transformers (their phase-shift flow b = b_sr phi)
@@ -426,8 +429,10 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
       if (tt < I.T && cc < I.Gb) {
         const int gbp = I.gb0 + cc;  // global generator-bus id; gb_ptr is one CSR over the batch
         const int q0 = d.gb_ptr[gbp], q1 = d.gb_ptr[gbp + 1];
-        for (int q = q0; q < q1; ++q)
-          s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(p[(long long)tt * I.G + (d.gb_gen[q] - I.gen0)]));
+        for (int q = q0; q < q1; ++q) {  // producers add, consumers subtract
+          const int gq = d.gb_gen[q];
+          s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(d.gen_sgn[gq] * p[(long long)tt * I.G + (gq - I.gen0)]));
+        }
       } else if (tt < I.T) {
         const int xi = cc - I.Gb;
         const Real phi = x[I.xtau0 + (long long)(I.T + tt) * I.X + xi];
@@ -475,7 +480,7 @@ template <typename Real, typename Dc>
 __device__ void s1_sdcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, const Real *__restrict__ x) {
   const int t0 = tc * DCF_TC, m0 = sub * DCF_BM;
   const int t = t0 + (threadIdx.x >> 5), m = m0 + (threadIdx.x & 31);
-  pold_share(d, I, t0, sub, x + I.x0 + 2LL * I.T * I.n);
+  pold_share(d, I, t0, sub, x);
   const bool on = t < I.T && m < I.M;
   const int2 ft = d.br_end[I.br0 + (on ? m : 0)];
   const int pf = d.bus_pos[ft.x], po = d.bus_pos[ft.y];
@@ -544,10 +549,11 @@ __device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, co
   } else if (kind == 1) {
     P = d.pt[tm];
     Q = d.qt[tm];
-  } else if (kind == 2) {
+  } else if (kind == 2) {  // a producer supplies (-), a consumer draws (+)
     const Real *p = x + I.x0 + 2LL * I.T * I.n + (long long)t * I.G + id;
-    P = -p[0];
-    Q = -p[(long long)I.T * I.G];
+    const Real sg = d.gen_sgn[I.gen0 + id];
+    P = -sg * p[0];
+    Q = -sg * p[(long long)I.T * I.G];
   }
   if (seg_sum2(row, P, Q) && row >= 0) {
     const long long ti = I.tb0 + (long long)t * I.n + row;
@@ -1114,13 +1120,13 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
   }
 }
 
-// Generator-level data of one (generator, period), loaded before the wait (no stage writes it).
+// Device-level data of one (device, period), loaded before the wait (no stage writes it).
 template <typename Real>
 struct GenIn {
-  int bus, zn, gb;
-  Real a, bl, cr, pmax, ramp, p, r;
-  long long kp, kq, kr;
-  Real am[3], av[3], lo[3], hi[3];  // Adam moments and box of p, q, r (fused Adam only)
+  int bus, zn, gb, b0, b1;  // bus, zone, generator-bus index, bid blocks [b0, b1)
+  Real a, bl, cr, pmax, ramp, sg, p, q, r, u;
+  long long kp, kq, kr, ku;
+  Real am[4], av[4], lo[4], hi[4];  // Adam moments and box of p, q, r, u (fused Adam only)
 };
 
 template <typename Real, typename Dc, bool ADAM>
@@ -1130,51 +1136,111 @@ __device__ GenIn<Real> gen_load(const Dev<Real, Dc> &d, const Inst &I, int t, in
   g.bus = d.gen_bus[gg];
   g.zn = d.gen_zone[gg];
   g.gb = d.gen_gb[gg];
+  g.b0 = d.blk_ptr[gg];
+  g.b1 = d.blk_ptr[gg + 1];
   g.a = d.gen_a[gg];
   g.bl = d.gen_b[gg];
   g.cr = d.gen_cr[gg];
   g.pmax = d.gen_pmax[gg];
   g.ramp = d.gen_ramp[gg];
+  g.sg = d.gen_sgn[gg];
   g.kp = I.x0 + 2LL * I.T * I.n + (long long)t * I.G + gl;
   g.kq = g.kp + (long long)I.T * I.G;
   g.kr = g.kq + (long long)I.T * I.G;
+  g.ku = I.uc ? I.xu0 + (long long)t * I.G + gl : g.kp;
   g.p = x[g.kp];
+  g.q = x[g.kq];
   g.r = x[g.kr];
+  g.u = I.uc ? x[g.ku] : Real(1);
   if (ADAM) {
-    const long long k3[3] = {g.kp, g.kq, g.kr};
+    const long long k4[4] = {g.kp, g.kq, g.kr, g.ku};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      g.am[c] = d.am[k3[c]];
-      g.av[c] = d.av[k3[c]];
-      g.lo[c] = d.lo[k3[c]];
-      g.hi[c] = d.hi[k3[c]];
+    for (int c = 0; c < 4; ++c) {
+      g.am[c] = d.am[k4[c]];
+      g.av[c] = d.av[k4[c]];
+      g.lo[c] = d.lo[k4[c]];
+      g.hi[c] = d.hi[k4[c]];
     }
   }
   return g;
 }
 
-// Generator terms of period t (cost, reserve cost, headroom, ramps; Eq. nlp_updated) and the
-// gradient wrt p, q, r, with the injection adjoint eta_gb - mean(eta) (Eqs. 2nd_lin_sys,
-// correction) at the generator's bus; [+ the projected Adam update of p, q, r].
+// Energy cost (producer) or value (consumer) per hour of dispatch p and its derivative: bid blocks
+// (Example 3) sum_l c_l max(min(p - P_{l-1}, w_l), 0), the derivative being the price of the block
+// that p is entering (0 <= p - P_{l-1} < w_l); without blocks a p^2 + b p.
+template <typename Real, typename Dc>
+__device__ __forceinline__ void energy_cost(const Dev<Real, Dc> &d, const GenIn<Real> &g, Real &en, Real &den) {
+  const Real p = g.p;
+  if (g.b1 > g.b0) {
+    en = 0;
+    den = 0;
+    for (int l = g.b0; l < g.b1; ++l) {
+      const Real c = d.blk_c[l], w = d.blk_w[l], e = p - d.blk_lo[l];
+      en += c * fmax(fmin(e, w), Real(0));
+      if (e >= Real(0) && e < w) den += c;
+    }
+  } else {
+    en = g.a * p * p + g.bl * p;
+    den = 2 * g.a * p + g.bl;
+  }
+}
+
+// Device terms of period t (energy cost or value, reserve cost, headroom, ramps; with on-status
+// the on / startup / shutdown costs and the u-scaled limits; Eq. nlp_updated, Examples 2-4) and
+// the gradient wrt p, q, r (, u), with the injection adjoint eta_gb - mean(eta) (Eqs. 2nd_lin_sys,
+// correction) at the device's bus, signed by its role (producer +, consumer -);
+// [+ the projected Adam update of p, q, r (, u)].
 template <typename Real, typename Dc, bool ADAM>
 __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl, const GenIn<Real> &g, Dc eta,
                            const AdamCoef<Real> &ac, Obj3<Dc> &acc, Real *__restrict__ x) {
   const Real dt = d.dt[I.tp0 + t];
   const long long G = I.G;
-  const Real p = g.p, r = g.r;
+  const Real p = g.p, q = g.q, r = g.r, u = g.u, sg = g.sg;
   const long long tb = I.tb0 + (long long)t * I.n;
-  Real gp = dt * (2 * g.a * p + g.bl) - d.dP[tb + g.bus] + DcOps<Dc>::to_real(eta);
-  const Real gq = -d.dQ[tb + g.bus];
+  Real en, den;
+  energy_cost(d, g, en, den);
+  Real gp = dt * sg * den + sg * (DcOps<Dc>::to_real(eta) - d.dP[tb + g.bus]);
+  Real gq = -sg * d.dQ[tb + g.bus];
   Real gr = dt * g.cr - d.dZ[I.tz0 + (long long)t * I.Z + g.zn];
-  acc.v[0] = DcOps<Dc>::from_real(dt * (g.a * p * p + g.bl * p + g.cr * r));
+  Real gu = 0;
+  Real cost = dt * (sg * en + g.cr * r);
   const HP<Real> hp = hparams(d);
   const Real wr = d.rho * hp.beta;
   Real val, der;
-  soft_relu(p + r - g.pmax, hp.eps, val, der);
-  acc.v[1] = DcOps<Dc>::from_real(wr * val);
+  soft_relu(p + r - g.pmax * u, hp.eps, val, der);  // u = 1 without on-status variables
+  Real zh = wr * val;
   gp += wr * der;
   gr += wr * der;
   const long long ko = I.tg0 + (long long)t * G + gl;
+  if (I.uc) {
+    const int gg = I.gen0 + gl;
+    gu -= g.pmax * (wr * der);
+    const Real pmin = d.gen_pmin[gg], qmin = d.gen_qmin[gg], qmax = d.gen_qmax[gg];
+    soft_relu(pmin * u - p, hp.eps, val, der);
+    zh += wr * val;
+    gp -= wr * der;
+    gu += pmin * (wr * der);
+    soft_relu(q - qmax * u, hp.eps, val, der);
+    zh += wr * val;
+    gq += wr * der;
+    gu -= qmax * (wr * der);
+    soft_relu(qmin * u - q, hp.eps, val, der);
+    zh += wr * val;
+    gq -= wr * der;
+    gu += qmin * (wr * der);
+    // on cost, startup max(u_t - u_{t-1}, 0) and shutdown max(u_{t-1} - u_t, 0) (Example 2)
+    const Real csu = d.gen_csu[gg], csd = d.gen_csd[gg], con = d.gen_con[gg];
+    const Real up = t >= 1 ? (ADAM ? d.uold[ko - G] : x[g.ku - G]) : d.gen_uinit[gg];
+    const Real du = u - up;
+    cost += dt * con * u + csu * fmax(du, Real(0)) + csd * fmax(-du, Real(0));
+    gu += dt * con + (du > Real(0) ? csu : Real(0)) - (du < Real(0) ? csd : Real(0));
+    if (t + 1 < I.T) {
+      const Real dn = (ADAM ? d.uold[ko + G] : x[g.ku + G]) - u;
+      gu -= (dn > Real(0) ? csu : Real(0)) - (dn < Real(0) ? csd : Real(0));
+    }
+  }
+  acc.v[0] = DcOps<Dc>::from_real(cost);
+  acc.v[1] = DcOps<Dc>::from_real(zh);
   if (t >= 1) {  // ramp terms of period t
     const Real pp = ADAM ? d.pold[ko - G] : x[g.kp - G];
     const Real lim = g.ramp * dt;
@@ -1193,20 +1259,23 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
     gp += wr * (d2 - d1);
   }
   if (ADAM) {
-    const long long k3[3] = {g.kp, g.kq, g.kr};
-    const Real g3[3] = {gp, gq, gr};
+    const long long k4[4] = {g.kp, g.kq, g.kr, g.ku};
+    const Real g4[4] = {gp, gq, gr, gu};
+    const Real x4[4] = {p, q, r, u};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Real xk = c == 0 ? g.p : (c == 2 ? g.r : x[g.kq]), mk = g.am[c], vk = g.av[c];
-      adam_update(xk, g3[c], mk, vk, g.lo[c], g.hi[c], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps, d.paper_eps);
-      x[k3[c]] = xk;
-      d.am[k3[c]] = mk;
-      d.av[k3[c]] = vk;
+    for (int c = 0; c < 4; ++c) {
+      if (c == 3 && !I.uc) break;
+      Real xk = x4[c], mk = g.am[c], vk = g.av[c];
+      adam_update(xk, g4[c], mk, vk, g.lo[c], g.hi[c], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps, d.paper_eps);
+      x[k4[c]] = xk;
+      d.am[k4[c]] = mk;
+      d.av[k4[c]] = vk;
     }
   } else {
     d.g[g.kp] = gp;
     d.g[g.kq] = gq;
     d.g[g.kr] = gr;
+    if (I.uc) d.g[g.ku] = gu;
   }
 }
 
@@ -1428,8 +1497,10 @@ __global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Rea
     Dc s = DcOps<Dc>::neg(d.load_dc[I.tb0 + (long long)t * I.n + bus]);
     if (gb >= 0) {
       const int q0 = d.gb_ptr[I.gb0 + gb], q1 = d.gb_ptr[I.gb0 + gb + 1];
-      for (int q = q0; q < q1; ++q)
-        s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(p[(long long)t * I.G + (d.gb_gen[q] - I.gen0)]));
+      for (int q = q0; q < q1; ++q) {
+        const int gq = d.gb_gen[q];
+        s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(d.gen_sgn[gq] * p[(long long)t * I.G + (gq - I.gen0)]));
+      }
     }
     if (I.X > 0) {  // - E^T b: a phase-shift flow leaves its from end and enters its to end
       for (int q = d.inc_ptr[pos]; q < d.inc_ptr[pos + 1]; ++q) {
@@ -1443,7 +1514,8 @@ __global__ void __launch_bounds__(NTHR) k_sp_inj(const __grid_constant__ Dev<Rea
   } else {
     const int t = blockIdx.x - nb;
     Dc s = DcOps<Dc>::zero();
-    for (int g = threadIdx.x; g < I.G; g += NTHR) s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(p[(long long)t * I.G + g]));
+    for (int g = threadIdx.x; g < I.G; g += NTHR)
+      s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(d.gen_sgn[I.gen0 + g] * p[(long long)t * I.G + g]));
     s = block_sum_dc(s);
     if (threadIdx.x == 0)
       d.sp_mu[t] = DcOps<Dc>::mul(DcOps<Dc>::add(s, DcOps<Dc>::neg(d.ltot[I.tp0 + t])), DcOps<Dc>::inv_n(I));

@@ -42,7 +42,9 @@ class qg_network(C.Structure):
                 ("cost_a", _F64P), ("cost_b", _F64P), ("cost_r", _F64P), ("pmin", _F64P), ("pmax", _F64P),
                 ("qmin", _F64P), ("qmax", _F64P), ("ramp", _F64P), ("vmin", _F64P), ("vmax", _F64P),
                 ("n_xf", C.c_int32), ("xf_branch", _I32P), ("tau_min", _F64P), ("tau_max", _F64P),
-                ("phi_min", _F64P), ("phi_max", _F64P)]
+                ("phi_min", _F64P), ("phi_max", _F64P), ("dev_cons", _I32P), ("n_blk", C.c_int32),
+                ("blk_price", _F64P), ("blk_width", _F64P), ("commit", C.c_int32), ("c_on", _F64P),
+                ("c_su", _F64P), ("c_sd", _F64P), ("u_init", _F64P)]
 
 
 class qg_horizon(C.Structure):
@@ -180,6 +182,17 @@ def _structs(case, keep: _Keep):
         net.xf_branch = keep.i32(case.xf_branch)
         net.tau_min, net.tau_max = keep.f64(case.tau_min), keep.f64(case.tau_max)
         net.phi_min, net.phi_max = keep.f64(case.phi_min), keep.f64(case.phi_max)
+    cons = getattr(case, "dev_cons", None)
+    if cons is not None and len(cons) and np.any(cons):
+        net.dev_cons = keep.i32(np.asarray(cons, bool).astype(np.int32))
+    W = getattr(case, "blk_width", None)
+    if W is not None and W.size:
+        net.n_blk = W.shape[1]
+        net.blk_price, net.blk_width = keep.f64(case.blk_price), keep.f64(W)
+    if getattr(case, "commit", False):
+        net.commit = 1
+        net.c_on, net.c_su = keep.f64(case.c_on), keep.f64(case.c_su)
+        net.c_sd, net.u_init = keep.f64(case.c_sd), keep.f64(case.u_init)
     hor = qg_horizon(T=case.T, dt=keep.f64(case.dt), load_p=keep.f64(case.load_p), load_q=keep.f64(case.load_q),
                      reserve_req=keep.f64(case.reserve_req))
     ctg = qg_contingencies(K=case.K, branch=keep.i32(case.ctg) if case.K > 0 else None)
@@ -221,7 +234,7 @@ def qg_num_vars(h: int) -> int:
 
 def qg_layout(h: int, inst: int = 0):
     first, n_x = C.c_int64(), C.c_int64()
-    off = (C.c_int64 * 7)()
+    off = (C.c_int64 * 8)()
     _check(_lib.qg_layout(h, inst, C.byref(first), C.byref(n_x), off), h)
     return first.value, n_x.value, tuple(off)
 

@@ -155,6 +155,31 @@ def test_transformer_case_reaches_device_check(qg):
         _expect(qg, c, qg.QG_ERR_NO_DEVICE, dc_solver=dc)
 
 
+def _devices_case():
+    return synth.with_commitment(synth.with_block_bids(synth.tiny(), 3, 0.3, 1), seed=1)
+
+
+def test_device_model_inputs_are_validated(qg):
+    c = _devices_case()
+    w = c.blk_width.copy(); w[2, 1] = -0.1
+    _expect(qg, dataclasses.replace(c, blk_width=w), qg.QG_ERR_INVALID_ARG)
+    pr = c.blk_price.copy(); pr[0, 0] = np.nan
+    _expect(qg, dataclasses.replace(c, blk_price=pr), qg.QG_ERR_INVALID_ARG)
+    big = np.ones((c.n_gen, 65))
+    _expect(qg, dataclasses.replace(c, blk_price=big, blk_width=big), qg.QG_ERR_INVALID_ARG)
+    su = c.c_su.copy(); su[0] = -1.0
+    _expect(qg, dataclasses.replace(c, c_su=su), qg.QG_ERR_INVALID_ARG)
+    ui = c.u_init.copy(); ui[0] = 1.5
+    _expect(qg, dataclasses.replace(c, u_init=ui), qg.QG_ERR_INVALID_ARG)
+
+
+@pytest.mark.skipif(_gpu_present(), reason="checks the no-device path")
+def test_device_model_case_reaches_device_check(qg):
+    c = _devices_case()
+    for dc in (qg.QG_DC_DENSE, qg.QG_DC_SPARSE):
+        _expect(qg, c, qg.QG_ERR_NO_DEVICE, dc_solver=dc)
+
+
 @pytest.mark.parametrize("iters", [1, 2, 7, 500])
 def test_library_schedule_matches_the_closed_forms(qg, iters):
     """qg_schedule (host code of the library) against Eqs. norm_t, mag_scale and step_size as the
