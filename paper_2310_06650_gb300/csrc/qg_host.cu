@@ -631,41 +631,48 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
   for (int b = 0; b < B; ++b) add_span(P.s2, I[b].ctg_ntc * I[b].n_mg * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
   for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
-  for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
-  // generator blocks (stage 5)
-  int gen_slot = 0;
-  auto gen_span = [&](Spans &S, int per, int b) {
-    I[b].gen_first = S.n_blocks;
-    I[b].gen_nb = per * I[b].T;
-    I[b].gen_slot0 = gen_slot;
-    gen_slot += I[b].gen_nb;
-    add_span(S, per, I[b].T, b, R_GEN);
-  };
-  if (P.sp) add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
-  else
-    for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gc + 1, NTHR / 32), I[b].T, b, R_DCA);
-  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
-  for (int b = 0; b < B; ++b) gen_span(P.s5, ceil_div(I[b].G, NTHR), b);
-  for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].X, NTHR), I[b].T, b, R_XF);
-  P.n_gen_slots = gen_slot;
   // objective slots: the blocks of s1 and s2 in launch order, renumbered instance-major so that each
-  // instance's slots are one contiguous range; then one slot per s5 block
+  // instance's slots are one contiguous range; then the fold slots of stage 3 (one per fold block:
+  // the sum of up to NTHR stage-1/2 slots of one instance) and one slot per stage-5 device block
   std::vector<int> owner;
   for (const Spans *S : {&P.s1, &P.s2})
     for (int k = 0; k < S->n; ++k)
       for (int q = 0; q < S->s[k].per_t * S->s[k].nt; ++q) owner.push_back(S->s[k].inst);
   std::vector<int> count(B, 0);
   for (int o : owner) ++count[o];
-  int lo = 0;
+  int lo = 0, fold_slot = 0;
   for (int b = 0; b < B; ++b) {
     I[b].obj_lo = lo;
     I[b].obj_n = count[b];
     lo += count[b];
+    I[b].fold_nb = ceil_div(count[b], NTHR);
+    I[b].fold_slot0 = fold_slot;
+    fold_slot += I[b].fold_nb;
   }
+  P.n_fold_slots = fold_slot;
   slot_map.assign(owner.size(), 0);
   std::vector<int> next(B);
   for (int b = 0; b < B; ++b) next[b] = I[b].obj_lo;
   for (size_t q = 0; q < owner.size(); ++q) slot_map[q] = next[owner[q]]++;
+  // stage 3: the fold blocks first (they start while the branch blocks are dispatched), then branches
+  for (int b = 0; b < B; ++b) add_span(P.s3, I[b].fold_nb, 1, b, R_OBJ);
+  for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
+  if (P.sp) add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
+  else
+    for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gc + 1, NTHR / 32), I[b].T, b, R_DCA);
+  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
+  // stage 5: device blocks over the instance's (period, device) pairs packed densely, then the
+  // transformer blocks
+  int gen_slot = 0;
+  for (int b = 0; b < B; ++b) {
+    I[b].gen_first = P.s5.n_blocks;
+    I[b].gen_nb = ceil_div((long long)I[b].T * I[b].G, NTHR);
+    I[b].gen_slot0 = gen_slot;
+    gen_slot += I[b].gen_nb;
+    add_span(P.s5, I[b].gen_nb, 1, b, R_GEN);
+  }
+  for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].X, NTHR), I[b].T, b, R_XF);
+  P.n_gen_slots = gen_slot;
   return QG_OK;
 }
 
@@ -1007,7 +1014,8 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   d.pmf = pf;
   Dc *op;
   d.n_obj12 = (int)slot_map.size();
-  d.n_obj_slots = d.n_obj12 + P.n_gen_slots;
+  d.n_gen_slots = P.n_gen_slots;
+  d.n_obj_slots = d.n_obj12 + P.n_gen_slots + P.n_fold_slots;
   if ((rc = dalloc(h, &op, (size_t)d.n_obj_slots * N_TERMS))) return rc;
   d.objp = op;
   int *si;

@@ -52,14 +52,16 @@ struct Inst {
   double hours;          // sum of dt
   double nfloor_ctg;     // M K - K: elements whose soft-ReLU floor eps the contingency term adds in closed form
   int obj_lo, obj_n;     // this instance's stage-1/2 objective slots
-  int gen_first, gen_nb; // its generator blocks: first block in their launch, count
+  int gen_first, gen_nb; // its device blocks in stage 5: first block in their launch, count
   int gen_slot0;         // first reduction slot of those blocks (after the stage-1/2 slots)
+  int fold_nb, fold_slot0; // its stage-3 fold blocks (each sums up to NTHR stage-1/2 slots) and their
+                           // first slot (after the device-block slots)
 };
 
 // Roles of the blocks of the fused stage kernels.  R_DCF / R_DCA are the dense DC products;
 // R_SDCF / R_SDCA their counterparts around the sparse-factor solves (flows from the solved
 // angles; right-hand side of the adjoint solve).
-enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN, R_SDCF, R_SDCA, R_XF };
+enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN, R_SDCF, R_SDCA, R_XF, R_OBJ };
 
 constexpr int SP_RB = 64;   // dense tail product: rows per block
 constexpr int SP_BK = 32;   // dense tail product: columns per shared-memory chunk
@@ -173,8 +175,10 @@ struct Dev {
   Real *avf, *avo, *ad;               // branch-end adjoints [sum T M]
   Real *atx;                          // dPhi/dtau of the AC terms per transformer [sum T X]
   Dc *objp;                           // [n_obj_slots][N_TERMS] per-block objective terms: the
-                                      // stage-1/2 blocks' slots, instance-major, then one per stage-5 block
+                                      // stage-1/2 blocks' slots, instance-major, then one per stage-5
+                                      // device block, then one per stage-3 fold block
   int n_obj_slots, n_obj12;           // all slots; stage-1/2 slots
+  int n_gen_slots;                    // stage-5 device-block slots (the fold slots follow them)
   const int *slot_map;                // [n_obj12] stage-1/2 block (launch order) -> slot
   double *obj, *terms;                // [n_inst], [n_inst][N_TERMS]
   Real *g;                            // gradient [n_x]
@@ -197,7 +201,8 @@ struct Plan {
   long long n_x;
   int maxT;
   int maxTB;  // largest period chunk of a contingency block (sizes its shared memory)
-  int n_gen_slots;  // objective reduction slots of the generator blocks
+  int n_gen_slots;  // objective reduction slots of the stage-5 device blocks
+  int n_fold_slots; // objective reduction slots of the stage-3 fold blocks
   // sparse DC mode (instance 0 only): grids of the solve kernels
   int sp;
   int sp_inj_blocks;   // right-hand-side blocks of k_sp_inj (T more compute the mean injection)

@@ -10,13 +10,15 @@
 //   s2  bus P/Q balance by warp-segmented CSR reduction + soft-abs penalty |
 //       contingency flows F = f_m + L[m,k] f_k, overload penalty and both
 //       backward sums (the SMW rank-1 correction of Eq. rank_correct in flow space)
-//   s3  dz/df summed over contingency tiles; branch-end adjoints (chain rule)
+//   s3  dz/df summed over contingency tiles; branch-end adjoints (chain rule) |
+//       folds of the stage-1/2 objective slots
 //   s4  bus gather of branch-end adjoints (warp-segmented) -> g_v, g_theta
 //       [+ fused Adam] | adjoint DC products PTDF_G^T dz/df (Eq. 2nd_lin_sys)
 //       (sparse DC mode: the right-hand side of the adjoint solve)
-//   s5  generator gradients incl. the slack-corrected injection adjoint
-//       eta - mean(eta) (Eq. correction) [+ fused Adam]; the last block reduces
-//       the objective in FP64 and advances the Adam step counter.
+//   s5  device terms (costs and values, limits, ramps, on-status) and gradients
+//       incl. the slack-corrected injection adjoint eta - mean(eta) (Eq.
+//       correction) [+ fused Adam] | transformer gradients; the last block
+//       reduces the objective and advances the Adam step counter.
 // Sparse DC mode: k_sp_inj, k_sp_fwd, k_sp_tail, k_sp_back solve Yhat theta = b
 // through the sparse factor with a dense tail, before s1 and after s4.
 // No floating-point atomics: every sum has a fixed order, so repeated
@@ -854,12 +856,69 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
 // stage 3: dz/df per branch (sum of the contingency partials), branch-end adjoints
 // ---------------------------------------------------------------------------------------------
 
+// Loads through L2 only (no L1 copy that another block's writes could leave stale).
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ df32 ldcg(const df32 *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));  // slots are 8-byte aligned
+  return df32{v.x, v.y};
+}
+
+// Deterministic block sum of N_TERMS values per thread; the result is valid in thread 0.
+template <typename Dc>
+__device__ void block_sum_terms(Dc (&a)[N_TERMS]) {
+  __shared__ Dc red[NTHR / 32][N_TERMS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N_TERMS; ++k)
+#pragma unroll
+    for (int q = 16; q > 0; q >>= 1) a[k] = DcOps<Dc>::add(a[k], DcOps<Dc>::shfl_down(a[k], q));
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) red[wid][k] = a[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) {
+      Dc v = red[0][k];
+#pragma unroll
+      for (int q = 1; q < NTHR / 32; ++q) v = DcOps<Dc>::add(v, red[q][k]);
+      a[k] = v;
+    }
+}
+
+// Objective reduction, level 1, run by the fold blocks of stage 3 (off the critical path of the
+// last stage): fold block r of an instance sums its stage-1/2 slots [r NTHR, (r + 1) NTHR) (instance-
+// major, contiguous) into its fold slot.  Stage 3 waited on stage 2, which waited on stage 1, so
+// those slots are complete.
+template <typename Real, typename Dc>
+__device__ void fold_slots(const Dev<Real, Dc> &d, const Inst &I, int r) {
+  Dc a[N_TERMS];
+#pragma unroll
+  for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
+  const int s = r * NTHR + threadIdx.x;
+  if (s < I.obj_n)
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) a[k] = d.objp[(long long)(I.obj_lo + s) * N_TERMS + k];
+  block_sum_terms(a);
+  if (threadIdx.x == 0) {
+    Dc *dst = d.objp + (long long)(d.n_obj12 + d.n_gen_slots + I.fold_slot0 + r) * N_TERMS;
+#pragma unroll
+    for (int k = 0; k < N_TERMS; ++k) dst[k] = a[k];
+  }
+}
+
 template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x) {
   const Where w = locate(S);
   const Inst &I = tab.I[w.inst];
+  if (w.role == R_OBJ) {  // whole block
+    pdl_wait();
+    fold_slots(d, I, w.sub);
+    return;
+  }
   const int t = w.t;
   const int j = w.sub * NTHR + threadIdx.x;
   const bool on = j < I.M;
@@ -872,7 +931,6 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
   if (on) {
     const long long e = I.tm0 + (long long)t * I.M + j;
     Real gF = 0, gq2 = 0;
-#pragma unroll 8
     // row partials of the outage tiles whose 64-row tile had an overload (flagged by stage 2): few
     // tiles are read unconditionally and selected (no dependent load), many are skipped
     if (I.n_kt <= 16) {
@@ -1030,59 +1088,9 @@ __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Re
 // stage 5: generator gradients (+ Adam), objective reduction, step counter
 // ---------------------------------------------------------------------------------------------
 
-// Deterministic block sum of N_TERMS values per thread; the result is valid in thread 0.
-template <typename Dc>
-__device__ void block_sum_terms(Dc (&a)[N_TERMS]) {
-  __shared__ Dc red[NTHR / 32][N_TERMS];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < N_TERMS; ++k)
-#pragma unroll
-    for (int q = 16; q > 0; q >>= 1) a[k] = DcOps<Dc>::add(a[k], DcOps<Dc>::shfl_down(a[k], q));
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < N_TERMS; ++k) red[wid][k] = a[k];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < N_TERMS; ++k) {
-      Dc v = red[0][k];
-#pragma unroll
-      for (int q = 1; q < NTHR / 32; ++q) v = DcOps<Dc>::add(v, red[q][k]);
-      a[k] = v;
-    }
-}
-
-// Objective reduction, level 1, run by every generator block (stage 5 in the sparse mode, the
-// generator role of stage 4 otherwise): its own terms plus an equal share of its instance's
-// stage-1/2 block slots (instance-major, so a share is a contiguous range) go to the block's
-// reduction slot.  The stage-1/2 slots are complete: the generator blocks run after stage 3,
-// which waited on stages 2 and 1.
-template <typename Real, typename Dc>
-__device__ void reduce_share(const Dev<Real, Dc> &d, const Inst &I, int r, Obj3<Dc> own) {
-  const int nb = I.gen_nb;
-  const int chunk = (I.obj_n + nb - 1) / nb;
-  const int lo = I.obj_lo + min(I.obj_n, r * chunk), hi = I.obj_lo + min(I.obj_n, (r + 1) * chunk);
-  const int slot = d.n_obj12 + I.gen_slot0 + r;
-  write_obj(d.objp, slot, own);
-  Dc a[N_TERMS];
-#pragma unroll
-  for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
-  for (int s = lo + threadIdx.x; s < hi; s += NTHR)
-#pragma unroll
-    for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::add(a[k], d.objp[(long long)s * N_TERMS + k]);
-  block_sum_terms(a);
-  if (threadIdx.x == 0) {
-    Dc *dst = d.objp + (long long)slot * N_TERMS;
-#pragma unroll
-    for (int k = 0; k < N_TERMS; ++k) dst[k] = DcOps<Dc>::add(dst[k], a[k]);
-  }
-}
-
-// Objective reduction, level 2, run by the last block of the launch: per instance, the reduction
-// slots of its generator blocks in fixed order, plus the closed-form soft-ReLU floor of the
-// contingency term.
+// Objective reduction, level 2, run by the last block of stage 5: per instance, the slots of its
+// device blocks and of its fold blocks in fixed order (read through L2: other blocks wrote them),
+// plus the closed-form soft-ReLU floor of the contingency term.
 template <typename Real, typename Dc>
 __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
   for (int b = 0; b < tab.n_inst; ++b) {
@@ -1090,10 +1098,12 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
     Dc a[N_TERMS];
 #pragma unroll
     for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
-    for (int j = threadIdx.x; j < I.gen_nb; j += NTHR)
+    for (int j = threadIdx.x; j < I.gen_nb + I.fold_nb; j += NTHR) {
+      const long long slot = j < I.gen_nb ? d.n_obj12 + I.gen_slot0 + j
+                                          : d.n_obj12 + d.n_gen_slots + I.fold_slot0 + (j - I.gen_nb);
 #pragma unroll
-      for (int k = 0; k < N_TERMS; ++k)
-        a[k] = DcOps<Dc>::add(a[k], d.objp[(long long)(d.n_obj12 + I.gen_slot0 + j) * N_TERMS + k]);
+      for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::add(a[k], ldcg(d.objp + slot * N_TERMS + k));
+    }
     block_sum_terms(a);
     if (threadIdx.x == 0) {
       double tot = 0.0;
@@ -1287,18 +1297,19 @@ __device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab) {
   __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(d.ticket, 1u) == gridDim.x - 1;
+    // one acquire-release ticket: releases this block's slot (written by thread 0, the block's other
+    // writes are not read in this launch) and, in the last block, acquires every other block's
+    unsigned int prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(d.ticket) : "memory");
+    last = prev == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
-  __threadfence();
   final_reduce(d, tab);
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {  // the next launch sees these at the kernel boundary
     *d.ticket = 0;
     if (ADAM) *d.step += 1;
-    __threadfence();
   }
 }
 
@@ -1355,16 +1366,18 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
     s5_xf<Real, Dc, ADAM>(d, I, t, w.sub, x, ac);
   } else {
     Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
-    const int gl = w.sub * NTHR + threadIdx.x;
-    const bool on = gl < I.G;
-    const GenIn<Real> g = gen_load<Real, Dc, ADAM>(d, I, t, on ? gl : 0, x);
+    // (period, device) pairs packed densely over the instance's device blocks
+    const int e = w.sub * NTHR + threadIdx.x;
+    const bool on = e < I.T * I.G;
+    const int tg = on ? e / I.G : 0, gl = on ? e - tg * I.G : 0;
+    const GenIn<Real> g = gen_load<Real, Dc, ADAM>(d, I, tg, gl, x);
     pdl_wait();
     if (on) {
-      const Dc *et = d.gip + I.gi0 + (long long)t * (I.Gc + 1);  // written by stage 4 or the adjoint solve
+      const Dc *et = d.gip + I.gi0 + (long long)tg * (I.Gc + 1);  // written by stage 4 or the adjoint solve
       const Dc eta = DcOps<Dc>::add(et[g.gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gc], DcOps<Dc>::inv_n(I))));
-      gen_update<Real, Dc, ADAM>(d, I, t, gl, g, eta, ac, acc, x);
+      gen_update<Real, Dc, ADAM>(d, I, tg, gl, g, eta, ac, acc, x);
     }
-    reduce_share(d, I, blockIdx.x - I.gen_first, acc);
+    write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
   }
   finish_eval<Real, Dc, ADAM>(d, tab);
 }
