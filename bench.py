@@ -261,6 +261,7 @@ def gpu_leg(args, rank, world, local_rank):
     for label, prec in (("mixed", qg.QG_MIXED), ("fp64", qg.QG_FP64)):
         s = qg.Solver(case, precision=prec)
         x = torch.tensor(x0, dtype=s.dtype, device="cuda")
+        shape = qg.qg_autotune(s.h, x, 10)  # contingency-block shape timed at the start point
         for _ in range(max(args.warmup, 3)):
             qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
         torch.cuda.synchronize()
@@ -313,6 +314,7 @@ def gpu_leg(args, rank, world, local_rank):
         results[label] = {
             "step_ms": step_ms, "total_ms": total_ms, "phases": {k: statistics.mean(v) for k, v in phases.items()},
             "warm_ms": warm_ms, "e2e_s": e2e_s, "clocks": clk.summary(), "obj": float(s.obj[0].item()),
+            "ctg_block": {"periods": shape[0], "tiles_64": shape[1], "picked_by": "qg_autotune (10 evals per shape)"},
             "launches": qg.qg_launches_per_eval(s.h),
         }
         s.close()
@@ -340,7 +342,8 @@ def gpu_leg(args, rank, world, local_rank):
                    "step": "one full objective+gradient evaluation + projected Adam update (CUDA graph replay)",
                    "precision": "mixed: FP32 flows/penalties/adjoints/Adam, double-FP32 DC solves, FP64 objective",
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
-                   "x0": "copper-plate dispatch (stored), flat voltage, zero angles"},
+                   "x0": "copper-plate dispatch (stored), flat voltage, zero angles",
+                   "ctg_block": mix["ctg_block"]},
         "roofline": roof,
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
                          "sample": oracle_sample_text(cpu)},
@@ -381,6 +384,9 @@ def dayahead_leg(args, peaks, src, local_rank):
     setup_s = time.perf_counter() - t0
     x0 = warmstart.start_point(case)
     x = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    shape = qg.qg_autotune(s.h, x, 3)
+    tune_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     steps = max(5, min(args.steps, 50))
     for _ in range(max(args.warmup, 3)):
@@ -422,6 +428,8 @@ def dayahead_leg(args, peaks, src, local_rank):
                    "l2": "working set larger than L2 (line-outage block 280 MB); no flush",
                    "x0": "merit-order dispatch, flat voltage, zero angles"},
         "setup_s": setup_s,
+        "ctg_block": {"periods": shape[0], "tiles_64": shape[1], "picked_by": "qg_autotune (3 evals per shape)",
+                      "tune_s": tune_s},
         "gpu_launches": launches * steps,
         "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in ph.items()},
         "phases_note": "s1 includes the forward DC solve (injections, forward gather, tail product, backward "

@@ -281,6 +281,16 @@ int qg_phase_times(qg_ctx *h, float *ms, int32_t cap);
 int qg_ctg_select(qg_ctx *h, int32_t inst, const int32_t *ids, int32_t n);
 int qg_ctg_scores(qg_ctx *h, double *z);
 
+/* Autotuner of the contingency-block shape (stage 2, Eqs. rank_correct-zctg): for each candidate
+ * shape (periods per block x 64-branch tiles per block, deduplicated per handle) re-plans the
+ * handle and times `reps` evaluations at x (device, qg_num_vars elements; the point matters: the
+ * overload screen skips work), then keeps the fastest.  Only the order of the outage sums depends
+ * on the shape (results agree to rounding).  shape (host, may be NULL) receives instance 0's
+ * periods per block and tiles per block.  Synchronizes; a graph captured by qg_solve is dropped
+ * and re-captured on the next call.  qg_tile_shape reports the shape in use for an instance. */
+int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t shape[2]);
+int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]);
+
 /* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: the
  * 5 stage kernels, plus 3 to 7 solve kernels with the sparse DC solver.  Returns a negative
  * error code for a NULL handle. */

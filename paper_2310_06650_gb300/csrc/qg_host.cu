@@ -30,6 +30,12 @@ constexpr int SPARSE_AUTO_N = 4096; // QG_DC_AUTO picks the sparse factor above 
 constexpr int TAIL_DEGREE = 32;     // minimum-degree elimination stops above this degree
 constexpr long long CTG_WAVE = 152 * 3;  // contingency blocks resident at once (152 SMs x 3 blocks)
 
+// Contingency-block shape of a plan (stage 2): how many period chunks each 64 x 64 tile is split
+// into (ntc) and how many monitored-branch tiles one block walks (mg); 0 picks the heuristic.
+struct Knobs {
+  int ntc = 0, mg = 0;
+};
+
 struct HostInst {
   int n, M, G, Z, T, K, ref, X = 0;
   std::vector<int> from, to, gen_bus, gen_zone, ctg;
@@ -97,6 +103,7 @@ struct qg_ctx {
   double *lodf64_full = nullptr;       // screening, FP64 path: the full exact block
   int *d_sel = nullptr;                // screening: [sum Ks] selected outage indices per instance
   bool profiling = false;
+  Knobs knobs{};                       // the contingency-block shape in use (0: heuristic)
   cudaEvent_t ev[N_PHASES + 1] = {};
   std::string err;
 };
@@ -551,7 +558,7 @@ void add_span(Spans &S, int per_t, int nt, int inst, int role) {
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Instance table, spans of the five stage kernels and objective-slot owners.
-int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
+int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   Plan &P = h->plan;
   const int B = h->n_inst;
   std::memset(&P, 0, sizeof(P));
@@ -565,11 +572,12 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map) {
   long long tiles = 0;
   for (int b = 0; b < B; ++b)
     if (h->hi[b].Ks > 0) tiles += (long long)ceil_div(h->hi[b].M, CT_BM) * ceil_div(h->hi[b].Ks, CT_BK);
-  const int ntc_all = (int)std::max(1LL, tiles > 0 ? CTG_WAVE / tiles : 1);
+  const int ntc_all = kn.ntc > 0 ? kn.ntc : (int)std::max(1LL, tiles > 0 ? CTG_WAVE / tiles : 1);
   // at most ~64 column partials per outage for stage 3 to sum serially
   int max_nmt = 0;
   for (int b = 0; b < B; ++b) max_nmt = std::max(max_nmt, ceil_div(h->hi[b].M, CT_BM));
-  const int mg_all = (int)std::max({1LL, tiles / (4LL * CTG_WAVE), (long long)ceil_div(max_nmt, 64)});
+  const int mg_all = kn.mg > 0 ? kn.mg
+                               : (int)std::max({1LL, tiles / (4LL * CTG_WAVE), (long long)ceil_div(max_nmt, 64)});
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
@@ -1078,6 +1086,79 @@ int run_eval(qg_ctx *h, const void *x, bool adam, double lr, double b1, double b
   return QG_OK;
 }
 
+// Frees one device allocation made by dalloc / upload.
+void dfree(qg_ctx *h, const void *p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), const_cast<void *>(p));
+  if (it != h->allocs.end()) {
+    cudaFree(*it);
+    h->allocs.erase(it);
+  }
+}
+
+// Re-plans the handle with the contingency-block shape kn: new spans and instance offsets, and new
+// plan-dependent work buffers (outage-column partials, score partials, objective slots and the slot
+// map); every other device array stays.  The captured solve graph is dropped (re-captured on use).
+template <typename Real, typename Dc>
+int replan_dev(qg_ctx *h, Dev<Real, Dc> &d, const Knobs &kn) {
+  std::vector<int> slot_map;
+  int rc = build_plan(h, slot_map, kn);
+  if (rc) return rc;
+  const Plan &P = h->plan;
+  if (P.s1.n > MAXSPAN || P.s2.n > MAXSPAN) return fail(h, QG_ERR_UNSUPPORTED, "too many block spans");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // no launch in flight uses the old buffers
+  long long spk = 0;
+  for (int b = 0; b < h->n_inst; ++b) spk += (long long)P.tab.I[b].n_mg * P.tab.I[b].T * P.tab.I[b].K;
+  dfree(h, d.pk);
+  dfree(h, d.objp);
+  dfree(h, d.slot_map);
+  Real *pk;
+  if ((rc = dalloc(h, &pk, (size_t)std::max(1LL, spk)))) return rc;
+  d.pk = pk;
+  if (d.score) {
+    dfree(h, d.pz);
+    Real *pz;
+    if ((rc = dalloc(h, &pz, (size_t)std::max(1LL, spk)))) return rc;
+    d.pz = pz;
+  }
+  d.n_obj12 = (int)slot_map.size();
+  d.n_gen_slots = P.n_gen_slots;
+  d.n_obj_slots = d.n_obj12 + P.n_gen_slots + P.n_fold_slots;
+  Dc *op;
+  if ((rc = dalloc(h, &op, (size_t)d.n_obj_slots * N_TERMS))) return rc;
+  d.objp = op;
+  int *si;
+  if ((rc = upload(h, &si, slot_map))) return rc;
+  d.slot_map = si;
+  const cudaError_t e = prepare_eval<Real, Dc>(P.maxTB, h->screen);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // a refused attribute is not a sticky error
+    return fail(h, QG_ERR_UNSUPPORTED, std::string("prepare_eval: ") + cudaGetErrorString(e));
+  }
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->knobs = kn;
+  return QG_OK;
+}
+
+int replan(qg_ctx *h, const Knobs &kn) { return mixed(h) ? replan_dev(h, h->d32, kn) : replan_dev(h, h->d64, kn); }
+
+// Mean device time in ms of `reps` evaluations at x (after two untimed ones), or a negative code.
+double time_evals(qg_ctx *h, const void *x, int reps) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1.0;
+  double ms = -1.0;
+  bool ok = run_eval(h, x, false, 0, 0, 0, nullptr, 0) == QG_OK && run_eval(h, x, false, 0, 0, 0, nullptr, 0) == QG_OK;
+  ok = ok && cudaEventRecord(a, h->stream) == cudaSuccess;
+  for (int r = 0; ok && r < reps; ++r) ok = run_eval(h, x, false, 0, 0, 0, nullptr, 0) == QG_OK;
+  ok = ok && cudaEventRecord(b, h->stream) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess;
+  float t = 0.0f;
+  if (ok && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms = t / reps;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
 int run_adam(qg_ctx *h, void *x, void *m, void *v, double lr, double b1, double b2) {
   cudaError_t e;
   if (mixed(h))
@@ -1280,7 +1361,7 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
       if (rcs[b]) return reject(rcs[b], errs[b]);
   }
   std::vector<int> slot_map;
-  build_plan(h, slot_map);
+  build_plan(h, slot_map, h->knobs);
   if (h->plan.s1.n > MAXSPAN || h->plan.s2.n > MAXSPAN) return reject(QG_ERR_UNSUPPORTED, "too many block spans");
   // everything above is host-side validation and set-up; from here on the device is needed
   rc = check_device(h);
@@ -1601,6 +1682,65 @@ int32_t qg_launches_per_eval(const qg_ctx *h) {
   return 5 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0);
 }
 
-int qg_version(void) { return 300; }
+int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t shape[2]) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  if (!x || reps < 1) return fail(h, QG_ERR_INVALID_ARG, "qg_autotune needs x and reps >= 1");
+  int maxT = 0, max_nmt = 0;
+  bool any_ctg = false;
+  for (int b = 0; b < h->n_inst; ++b) {
+    maxT = std::max(maxT, h->plan.tab.I[b].T);
+    max_nmt = std::max(max_nmt, h->plan.tab.I[b].n_mt);
+    any_ctg = any_ctg || h->plan.tab.I[b].K > 0;
+  }
+  const Knobs start = h->knobs;
+  Knobs best = start;
+  double best_ms = -1.0;
+  if (any_ctg) {
+    // the shape each candidate gives every instance; candidates that repeat one are skipped
+    std::vector<std::vector<int>> seen;
+    auto shape_of = [&]() {
+      std::vector<int> v;
+      for (int b = 0; b < h->n_inst; ++b) {
+        v.push_back(h->plan.tab.I[b].ctg_tb);
+        v.push_back(h->plan.tab.I[b].ctg_mg);
+      }
+      return v;
+    };
+    std::vector<Knobs> cand{Knobs{}};
+    for (int ntc : {1, 2, 3, 4, 6, 8, 12, 16, 24, 48})
+      for (int mg : {1, 2, 3, 4, 6, 9, 12, 16, 24, 32})
+        if (ntc <= maxT && mg <= max_nmt) cand.push_back(Knobs{ntc, mg});
+    for (const Knobs &kn : cand) {
+      int rc = replan(h, kn);
+      if (rc == QG_ERR_UNSUPPORTED) continue;  // e.g. a period chunk whose shared memory does not fit
+      if (rc) return rc;
+      const std::vector<int> sig = shape_of();
+      if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+      seen.push_back(sig);
+      const double ms = time_evals(h, x, reps);
+      if (ms < 0) return fail(h, QG_ERR_CUDA, "qg_autotune: timing an evaluation failed");
+      if (best_ms < 0 || ms < best_ms) {
+        best_ms = ms;
+        best = kn;
+      }
+    }
+  }
+  int rc = replan(h, best);
+  if (rc) return rc;
+  if (shape) {
+    shape[0] = h->plan.tab.I[0].ctg_tb;
+    shape[1] = h->plan.tab.I[0].ctg_mg;
+  }
+  return QG_OK;
+}
+
+int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]) {
+  if (!h || inst < 0 || inst >= h->n_inst || !shape) return QG_ERR_INVALID_ARG;
+  shape[0] = h->plan.tab.I[inst].ctg_tb;
+  shape[1] = h->plan.tab.I[inst].ctg_mg;
+  return QG_OK;
+}
+
+int qg_version(void) { return 301; }
 
 }  // extern "C"

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <cstdint>
 #include <utility>
 
@@ -1023,6 +1024,7 @@ __device__ __forceinline__ void adam_update(Real &xk, Real gk, Real &mk, Real &v
 template <typename Real>
 struct AdamCoef {
   Real b1, b2, c1, c2, lr, eps;
+  long long step;  // the step counter this update reads (i - 1)
 };
 
 // Bias corrections 1 / (1 - beta^i) for the next step i, computed once per block: FP32 through
@@ -1041,12 +1043,15 @@ __device__ __forceinline__ void bias_corr(double b1, double b2, long long step, 
 template <typename Real, typename Dc>
 __device__ AdamCoef<Real> adam_coef(const Dev<Real, Dc> &d) {
   __shared__ Real sc[3];
+  __shared__ long long s_step;
   if (threadIdx.x == 0) {
-    bias_corr(d.b1, d.b2, *d.step, sc[0], sc[1]);
+    const long long step = *d.step;
+    bias_corr(d.b1, d.b2, step, sc[0], sc[1]);
     sc[2] = (Real)(d.sched ? d.sched[3 * sched_index(d)] : d.lr);  // step size (Eq. step_size schedule)
+    s_step = step;
   }
   __syncthreads();
-  return {(Real)d.b1, (Real)d.b2, sc[0], sc[1], sc[2], (Real)d.aeps};
+  return {(Real)d.b1, (Real)d.b2, sc[0], sc[1], sc[2], (Real)d.aeps, s_step};
 }
 
 template <typename Real, typename Dc, bool ADAM>
@@ -1098,13 +1103,22 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
     Dc a[N_TERMS];
 #pragma unroll
     for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::zero();
-    for (int j = threadIdx.x; j < I.gen_nb + I.fold_nb; j += NTHR) {
+    const int ns = I.gen_nb + I.fold_nb;
+    for (int j = threadIdx.x; j < ns; j += NTHR) {
       const long long slot = j < I.gen_nb ? d.n_obj12 + I.gen_slot0 + j
                                           : d.n_obj12 + d.n_gen_slots + I.fold_slot0 + (j - I.gen_nb);
 #pragma unroll
       for (int k = 0; k < N_TERMS; ++k) a[k] = DcOps<Dc>::add(a[k], ldcg(d.objp + slot * N_TERMS + k));
     }
-    block_sum_terms(a);
+    if (ns <= 32) {  // one warp holds every slot: a shuffle tree, no block barrier (block-uniform branch)
+      if (threadIdx.x >= 32) continue;
+#pragma unroll
+      for (int k = 0; k < N_TERMS; ++k)
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) a[k] = DcOps<Dc>::add(a[k], DcOps<Dc>::shfl_down(a[k], q));
+    } else {
+      block_sum_terms(a);
+    }
     if (threadIdx.x == 0) {
       double tot = 0.0;
       for (int k = 0; k < N_TERMS; ++k) {
@@ -1293,7 +1307,7 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
 // advances the Adam step counter.  Every block of the launch calls this (all its threads), after
 // its last read of the step counter.
 template <typename Real, typename Dc, bool ADAM>
-__device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab) {
+__device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab, long long step) {
   __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1306,10 +1320,9 @@ __device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab) {
   __syncthreads();
   if (!last) return;
   final_reduce(d, tab);
-  __syncthreads();
   if (threadIdx.x == 0) {  // the next launch sees these at the kernel boundary
     *d.ticket = 0;
-    if (ADAM) *d.step += 1;
+    if (ADAM) *d.step = step + 1;
   }
 }
 
@@ -1379,7 +1392,7 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
     }
     write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
   }
-  finish_eval<Real, Dc, ADAM>(d, tab);
+  finish_eval<Real, Dc, ADAM>(d, tab, ac.step);
 }
 
 // Right-hand side of the adjoint solve in the sparse mode (Eq. 2nd_lin_sys): w = E_hat^T Y_x dz/df
@@ -1818,11 +1831,19 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
   return e;
 }
 
+// The contingency kernel's dynamic shared-memory limit is a process-wide function attribute: it is
+// only ever raised, so that creating a handle with smaller blocks never breaks an existing one.
 template <typename Real, typename Dc>
 cudaError_t prepare_eval(int maxTB, bool score) {
-  const size_t sm = ctg_smem_bytes<Real>(maxTB, score);
+  static std::mutex mu;
+  static size_t cur = 0;
+  const size_t sm = std::max(ctg_smem_bytes<Real>(maxTB, score), ctg_smem_bytes<Real>(maxTB, false));
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(k_s2<Real, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  std::lock_guard<std::mutex> lock(mu);
+  if (sm <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_s2<Real, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) cur = sm;
+  return e;
 }
 
 template <typename Real>

@@ -75,6 +75,8 @@ def _load():
                                       C.POINTER(qg_contingencies), C.POINTER(qg_options)]),
         "qg_destroy": (None, [vp]),
         "qg_num_vars": (C.c_int64, [vp]),
+        "qg_autotune": (C.c_int, [vp, vp, C.c_int32, C.POINTER(C.c_int32)]),
+        "qg_tile_shape": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32)]),
         "qg_layout": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "qg_set_stream": (C.c_int, [vp, vp]),
         "qg_eval_grad": (C.c_int, [vp, vp, vp, vp]),
@@ -117,7 +119,7 @@ _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_eval_grad_noalloc", "qg_adam_step", "qg_solve", "qg_breakdown",
             "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_launches_per_eval",
-            "qg_solve_schedule", "qg_schedule", "qg_ctg_select", "qg_ctg_scores",
+            "qg_solve_schedule", "qg_schedule", "qg_ctg_select", "qg_ctg_scores", "qg_autotune", "qg_tile_shape",
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
@@ -330,6 +332,20 @@ def qg_last_error(h: Optional[int] = None) -> str:
 
 def qg_version() -> int:
     return int(_lib.qg_version())
+
+
+def qg_autotune(h: int, x, reps: int = 10):
+    """Times every candidate contingency-block shape at x and keeps the fastest; returns instance 0's
+    (periods per block, 64-branch tiles per block)."""
+    shape = (C.c_int32 * 2)()
+    _check(_lib.qg_autotune(h, _ptr(x), reps, shape), h)
+    return tuple(shape)
+
+
+def qg_tile_shape(h: int, inst: int = 0):
+    shape = (C.c_int32 * 2)()
+    _check(_lib.qg_tile_shape(h, inst, shape), h)
+    return tuple(shape)
 
 
 def qg_launches_per_eval(h: int) -> int:
