@@ -284,11 +284,15 @@ int qg_ctg_scores(qg_ctx *h, double *z);
 /* Autotuner of the contingency-block shape (stage 2, Eqs. rank_correct-zctg): for each candidate
  * shape (periods per block x 64-branch tiles per block, deduplicated per handle) re-plans the
  * handle and times `reps` evaluations at x (device, qg_num_vars elements; the point matters: the
- * overload screen skips work), then keeps the fastest.  Only the order of the outage sums depends
- * on the shape (results agree to rounding).  shape (host, may be NULL) receives instance 0's
- * periods per block and tiles per block.  Synchronizes; a graph captured by qg_solve is dropped
- * and re-captured on the next call.  qg_tile_shape reports the shape in use for an instance. */
-int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t shape[2]);
+ * overload screen skips work); the heuristic shape and the four fastest are timed twice more, and a
+ * shape replaces the heuristic only when it is more than 2% faster.  cold != 0 writes a 256 MB
+ * buffer (allocated for the call) before every timed evaluation, so that the timing is that of an
+ * evaluation starting from an L2 without its data; cold = 0 times back-to-back evaluations (a long
+ * Adam run).  Only the order of the outage sums depends on the shape (results agree to rounding).
+ * shape (host, may be NULL) receives instance 0's periods per block and tiles per block.
+ * Synchronizes; a graph captured by qg_solve is dropped and re-captured on the next call.
+ * qg_tile_shape reports the shape in use for an instance. */
+int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t shape[2]);
 int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]);
 
 /* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: the

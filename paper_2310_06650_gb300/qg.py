@@ -75,7 +75,7 @@ def _load():
                                       C.POINTER(qg_contingencies), C.POINTER(qg_options)]),
         "qg_destroy": (None, [vp]),
         "qg_num_vars": (C.c_int64, [vp]),
-        "qg_autotune": (C.c_int, [vp, vp, C.c_int32, C.POINTER(C.c_int32)]),
+        "qg_autotune": (C.c_int, [vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
         "qg_tile_shape": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32)]),
         "qg_layout": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "qg_set_stream": (C.c_int, [vp, vp]),
@@ -334,11 +334,12 @@ def qg_version() -> int:
     return int(_lib.qg_version())
 
 
-def qg_autotune(h: int, x, reps: int = 10):
-    """Times every candidate contingency-block shape at x and keeps the fastest; returns instance 0's
-    (periods per block, 64-branch tiles per block)."""
+def qg_autotune(h: int, x, reps: int = 10, cold: bool = False):
+    """Times every candidate contingency-block shape at x and keeps the fastest (cold: each timed
+    evaluation starts from a flushed L2); returns instance 0's (periods per block, 64-branch tiles
+    per block)."""
     shape = (C.c_int32 * 2)()
-    _check(_lib.qg_autotune(h, _ptr(x), reps, shape), h)
+    _check(_lib.qg_autotune(h, _ptr(x), reps, 1 if cold else 0, shape), h)
     return tuple(shape)
 
 

@@ -46,7 +46,7 @@ def test_autotune_keeps_parity_on_rt617(qg, precision, tol):
     s = qg.Solver(c, precision=precision)
     x = torch.tensor(x0, dtype=s.dtype, device="cuda")
     o1, g1 = evaluate(s, x)
-    shape = qg.qg_autotune(s.h, x, 3)
+    shape = qg.qg_autotune(s.h, x, 3, cold=(precision == 1))
     assert 1 <= shape[0] <= c.T and 1 <= shape[1] <= -(-c.n_branch // 64)
     assert tuple(qg.qg_tile_shape(s.h, 0)) == tuple(shape)
     o2, g2 = evaluate(s, x)
@@ -79,7 +79,7 @@ def test_autotuned_batch_and_solve_loop(qg):
     qg.qg_solve(s.h, xa, 5, 1e-3, 0.9, 0.999)
     qg.qg_solve(s2.h, xb, 5, 1e-3, 0.9, 0.999)
     torch.cuda.synchronize()
-    assert torch.max(torch.abs(xa - xb)).item() <= 1e-12
+    assert torch.max(torch.abs(xa - xb)).item() <= 1e-9  # the shapes differ only in summation order
     s.close()
     s2.close()
 
