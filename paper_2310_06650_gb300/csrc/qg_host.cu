@@ -671,10 +671,14 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   // stage 5: device blocks over the instance's (period, device) pairs packed densely, then the
   // transformer blocks
+  // FP64 path: one warp of pairs per block, so that the FP64 arithmetic (a small fraction of the FP32
+  // rate on this part) spreads over many SMs; mixed path: a full block of pairs
+  const int gen_pb = h->opt.precision == QG_FP64 ? 32 : NTHR;
   int gen_slot = 0;
   for (int b = 0; b < B; ++b) {
     I[b].gen_first = P.s5.n_blocks;
-    I[b].gen_nb = ceil_div((long long)I[b].T * I[b].G, NTHR);
+    I[b].gen_pb = gen_pb;
+    I[b].gen_nb = ceil_div((long long)I[b].T * I[b].G, gen_pb);
     I[b].gen_slot0 = gen_slot;
     gen_slot += I[b].gen_nb;
     add_span(P.s5, I[b].gen_nb, 1, b, R_GEN);

@@ -53,6 +53,7 @@ struct Inst {
   double nfloor_ctg;     // M K - K: elements whose soft-ReLU floor eps the contingency term adds in closed form
   int obj_lo, obj_n;     // this instance's stage-1/2 objective slots
   int gen_first, gen_nb; // its device blocks in stage 5: first block in their launch, count
+  int gen_pb;            // (period, device) pairs per device block (the first gen_pb threads)
   int gen_slot0;         // first reduction slot of those blocks (after the stage-1/2 slots)
   int fold_nb, fold_slot0; // its stage-3 fold blocks (each sums up to NTHR stage-1/2 slots) and their
                            // first slot (after the device-block slots)
