@@ -295,6 +295,21 @@ int qg_ctg_scores(qg_ctx *h, double *z);
 int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t shape[2]);
 int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]);
 
+/* Batch rounding (Alg. 1) with a device projection stand-in, for handles whose instances have
+ * on-status variables (commit = 1; other instances are skipped).  One call is one round after a
+ * solve: every unfixed (period, device) pair is projected on its own (the paper's per-device MILP of
+ * Proj. bin_proj needs a MILP solver): u in {0, 1} with the nearer of (u = 1: p, q, r moved to the
+ * nearest point of pmin <= p <= pmax, 0 <= r <= rcap, p + r <= pmax, qmin <= q <= qmax, rcap = pmax
+ * for producers and 0 for consumers) and (u = 0: p = q = r = 0), ties to u = 1, ramp limits left to
+ * the penalized objective; then ceil(frac x unfixed) pairs of each instance whose projection moved
+ * them least (squared distance over p, q, r, u; ties by pair index) are fixed: x (device,
+ * qg_num_vars elements) takes their projected values and the clip box pins them (u, and with u = 0
+ * also p, q, r, at their values; with u = 1 the box becomes the u = 1 limits).  n_fixed and
+ * n_binaries (host, may be NULL) receive the fixed and total pair counts over the handle.  frac in
+ * (0, 1].  Synchronizes.  qg_round_reset unfixes every pair and restores the original box. */
+int qg_round_batch(qg_ctx *h, void *x, double frac, int64_t *n_fixed, int64_t *n_binaries);
+int qg_round_reset(qg_ctx *h);
+
 /* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: the
  * 5 stage kernels, plus 3 to 7 solve kernels with the sparse DC solver.  Returns a negative
  * error code for a NULL handle. */

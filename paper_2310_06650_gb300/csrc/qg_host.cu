@@ -104,6 +104,13 @@ struct qg_ctx {
   int *d_sel = nullptr;                // screening: [sum Ks] selected outage indices per instance
   bool profiling = false;
   Knobs knobs{};                       // the contingency-block shape in use (0: heuristic)
+  // batch rounding (Alg. 1): fixed flags, distances, projections, the original box (allocated on the
+  // first round), and the host copy of the fixed flags
+  unsigned char *d_fixed = nullptr;
+  double *d_dist = nullptr;
+  void *d_proj = nullptr, *d_lo0 = nullptr, *d_hi0 = nullptr;
+  int *d_idx = nullptr;
+  std::vector<unsigned char> fixed;
   cudaEvent_t ev[N_PHASES + 1] = {};
   std::string err;
 };
@@ -1008,6 +1015,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
 #define WR(field, cnt) if ((rc = dalloc(h, &w, (size_t)(cnt)))) return rc; d.field = w;
 #define WD(field, cnt) if ((rc = dalloc(h, &c, (size_t)(cnt)))) return rc; d.field = c;
 #define WF(field, cnt) if ((rc = dalloc(h, &fl, (size_t)(cnt)))) return rc; d.field = fl;
+  d.n_pairs = sTG;
   WR(pf, sTM) WR(qf, sTM) WR(pt, sTM) WR(qt, sTM) WR(qm2, sTM) WR(fre, sTM) WR(fk, sTK) WR(pold, sTG) WR(uold, sTG)
   WR(dP, sTn) WR(dQ, sTn) WR(dZ, sTZ) WR(pm, sPM) WR(pq, sPM) WR(pk, sPK) WR(gF, sTM) WR(avf, sTM) WR(avo, sTM)
   WR(ad, sTM) WR(atx, sTX)
@@ -1779,6 +1787,87 @@ int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t sh
     shape[0] = h->plan.tab.I[0].ctg_tb;
     shape[1] = h->plan.tab.I[0].ctg_mg;
   }
+  return QG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One round of batch rounding on the device data of precision Real.
+template <typename Real, typename Dc>
+int round_batch_dev(qg_ctx *h, Dev<Real, Dc> &d, void *xv, double frac, int64_t *n_fixed, int64_t *n_bin) {
+  Real *x = static_cast<Real *>(xv);
+  const long long sTG = d.n_pairs;
+  int rc;
+  if (!h->d_fixed) {
+    if ((rc = dalloc(h, &h->d_fixed, (size_t)sTG)) || (rc = dalloc(h, &h->d_dist, (size_t)sTG)) ||
+        (rc = dalloc(h, (Real **)&h->d_proj, (size_t)(4 * sTG))) || (rc = dalloc(h, &h->d_idx, (size_t)sTG)) ||
+        (rc = dalloc(h, (Real **)&h->d_lo0, (size_t)h->n_x)) || (rc = dalloc(h, (Real **)&h->d_hi0, (size_t)h->n_x)))
+      return rc;
+    CUDA_TRY(h, cudaMemcpy(h->d_lo0, d.lo, sizeof(Real) * h->n_x, cudaMemcpyDeviceToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_hi0, d.hi, sizeof(Real) * h->n_x, cudaMemcpyDeviceToDevice));
+    h->fixed.assign((size_t)sTG, 0);
+  }
+  for (int b = 0; b < h->n_inst; ++b) {
+    const Inst &I = h->plan.tab.I[b];
+    if (!I.uc) continue;
+    CUDA_TRY(h, (launch_round_project<Real, Dc>(d, I, x, h->d_fixed, h->d_dist, (Real *)h->d_proj, h->stream)));
+  }
+  std::vector<double> dist((size_t)sTG);
+  CUDA_TRY(h, cudaMemcpyAsync(dist.data(), h->d_dist, sizeof(double) * sTG, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  long long nf = 0, nb = 0;
+  for (int b = 0; b < h->n_inst; ++b) {
+    const Inst &I = h->plan.tab.I[b];
+    if (!I.uc) continue;
+    const long long TG = (long long)I.T * I.G;
+    std::vector<int> freev;
+    for (long long e = 0; e < TG; ++e)
+      if (!h->fixed[I.tg0 + e]) freev.push_back((int)e);
+    const long long take = std::min<long long>((long long)freev.size(), (long long)std::ceil(frac * freev.size()));
+    // the unfixed pairs whose projection moved them least; ties by pair index
+    std::stable_sort(freev.begin(), freev.end(),
+                     [&](int a, int c) { return dist[I.tg0 + a] < dist[I.tg0 + c]; });
+    std::vector<int> pick(freev.begin(), freev.begin() + take);
+    std::sort(pick.begin(), pick.end());
+    if (!pick.empty()) {
+      CUDA_TRY(h, cudaMemcpyAsync(h->d_idx, pick.data(), sizeof(int) * pick.size(), cudaMemcpyHostToDevice, h->stream));
+      CUDA_TRY(h, (launch_round_fix<Real, Dc>(d, I, x, const_cast<Real *>(d.lo), const_cast<Real *>(d.hi), h->d_idx,
+                                              (int)pick.size(), h->d_fixed, (const Real *)h->d_proj, h->stream)));
+      CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // the index list is reused by the next instance
+    }
+    for (int e : pick) h->fixed[I.tg0 + e] = 1;
+    for (long long e = 0; e < TG; ++e) nf += h->fixed[I.tg0 + e];
+    nb += TG;
+  }
+  if (n_fixed) *n_fixed = nf;
+  if (n_bin) *n_bin = nb;
+  return QG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qg_round_batch(qg_ctx *h, void *x, double frac, int64_t *n_fixed, int64_t *n_binaries) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  if (!x || !(frac > 0.0) || !(frac <= 1.0)) return fail(h, QG_ERR_INVALID_ARG, "qg_round_batch needs x and 0 < frac <= 1");
+  return mixed(h) ? round_batch_dev(h, h->d32, x, frac, n_fixed, n_binaries)
+                  : round_batch_dev(h, h->d64, x, frac, n_fixed, n_binaries);
+}
+
+int qg_round_reset(qg_ctx *h) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  if (!h->d_fixed) return QG_OK;
+  const size_t rs = mixed(h) ? sizeof(float) : sizeof(double);
+  void *lo = mixed(h) ? (void *)h->d32.lo : (void *)h->d64.lo;
+  void *hi = mixed(h) ? (void *)h->d32.hi : (void *)h->d64.hi;
+  CUDA_TRY(h, cudaMemcpyAsync(lo, h->d_lo0, rs * h->n_x, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(hi, h->d_hi0, rs * h->n_x, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_fixed, 0, h->fixed.size(), h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  std::fill(h->fixed.begin(), h->fixed.end(), 0);
   return QG_OK;
 }
 

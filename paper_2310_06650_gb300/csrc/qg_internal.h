@@ -180,6 +180,7 @@ struct Dev {
                                       // device block, then one per stage-3 fold block
   int n_obj_slots, n_obj12;           // all slots; stage-1/2 slots
   int n_gen_slots;                    // stage-5 device-block slots (the fold slots follow them)
+  long long n_pairs;                  // sum over instances of T G ((period, device) pairs)
   const int *slot_map;                // [n_obj12] stage-1/2 block (launch order) -> slot
   double *obj, *terms;                // [n_inst], [n_inst][N_TERMS]
   Real *g;                            // gradient [n_x]
@@ -221,6 +222,14 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *x, bo
 
 template <typename Real, typename Dc>
 cudaError_t prepare_eval(int maxTB, bool score);
+
+template <typename Real, typename Dc>
+cudaError_t launch_round_project(const Dev<Real, Dc> &d, const Inst &I, const Real *x, const unsigned char *fixed,
+                                 double *dist, Real *proj, cudaStream_t s);
+
+template <typename Real, typename Dc>
+cudaError_t launch_round_fix(const Dev<Real, Dc> &d, const Inst &I, Real *x, Real *lo, Real *hi, const int *idx,
+                             int n, unsigned char *fixed, const Real *proj, cudaStream_t s);
 
 template <typename Real>
 cudaError_t launch_adam(Real *x, Real *m, Real *v, const Real *g, const Real *lo, const Real *hi, long long n,

@@ -1868,6 +1868,116 @@ cudaError_t launch_adam(Real *x, Real *m, Real *v, const Real *g, const Real *lo
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// batch rounding (Alg. 1) with a per-pair projection stand-in
+// ---------------------------------------------------------------------------------------------
+
+// Squared distance ((dp^2 + dq^2) + dr^2) + du^2 in FP64 without contraction (the same order and
+// rounding as a plain left-to-right sum of squares).
+__device__ __forceinline__ double dist4(double dp, double dq, double dr, double du) {
+  double s = __dmul_rn(dp, dp);
+  s = __dadd_rn(s, __dmul_rn(dq, dq));
+  s = __dadd_rn(s, __dmul_rn(dr, dr));
+  return __dadd_rn(s, __dmul_rn(du, du));
+}
+
+// Every (period, device) pair of one instance with on-status variables: the projection of (p, q, r, u)
+// onto u in {0, 1} and the limits u implies (u = 1: pmin <= p <= pmax, 0 <= r <= rcap, p + r <= pmax,
+// qmin <= q <= qmax, rcap = pmax for producers and 0 for consumers; u = 0: p = q = r = 0), whichever is
+// nearer (ties to u = 1), and the squared distance moved (+inf for pairs already fixed).  The (p, r)
+// projection is the box projection when it meets p + r <= pmax, else the nearest point of the segment
+// p + r = pmax inside the box.  proj holds [u | p | q | r], each [T G].
+template <typename Real, typename Dc>
+__global__ void k_round_project(const __grid_constant__ Dev<Real, Dc> d, const __grid_constant__ Inst I,
+                                const Real *__restrict__ x, const unsigned char *__restrict__ fixed,
+                                double *__restrict__ dist, Real *__restrict__ proj) {
+  const long long TG = (long long)I.T * I.G;
+  const long long e = (long long)blockIdx.x * NTHR + threadIdx.x;
+  if (e >= TG) return;
+  const int g = (int)(e % I.G), gg = I.gen0 + g;
+  const long long kp = I.x0 + 2LL * I.T * I.n + e, kq = kp + TG, kr = kq + TG, ku = I.xu0 + e;
+  const double p0 = x[kp], q0 = x[kq], r0 = x[kr], u0 = x[ku];
+  const double pmin = d.gen_pmin[gg], pmax = d.gen_pmax[gg], qmin = d.gen_qmin[gg], qmax = d.gen_qmax[gg];
+  const double rcap = d.gen_sgn[gg] < 0 ? 0.0 : pmax;
+  double p1 = fmin(fmax(p0, pmin), pmax), r1 = fmin(fmax(r0, 0.0), rcap);
+  if (p1 + r1 > pmax) {
+    double pl = 0.5 * (p0 + pmax - r0);
+    pl = fmin(fmax(pl, fmax(pmin, pmax - rcap)), pmax);
+    p1 = pl;
+    r1 = pmax - pl;
+  }
+  const double q1 = fmin(fmax(q0, qmin), qmax);
+  const double d1 = dist4(p0 - p1, q0 - q1, r0 - r1, u0 - 1.0);
+  const double d0 = dist4(p0, q0, r0, u0);
+  const bool on = d1 <= d0;
+  const long long tg = I.tg0 + e;
+  dist[tg] = fixed[tg] ? INFINITY : (on ? d1 : d0);
+  const long long sTG = d.n_pairs;
+  proj[tg] = on ? Real(1) : Real(0);
+  proj[sTG + tg] = on ? (Real)p1 : Real(0);
+  proj[2 * sTG + tg] = on ? (Real)q1 : Real(0);
+  proj[3 * sTG + tg] = on ? (Real)r1 : Real(0);
+}
+
+// Fixes the listed pairs (indices into the instance's [T G] pairs) at their projection: x takes the
+// projected p, q, r, u; the box pins u, and with u = 0 also p, q, r at 0, while with u = 1 it becomes
+// the u = 1 limits (p in [pmin, pmax], q in [qmin, qmax], r in [0, rcap]).
+template <typename Real, typename Dc>
+__global__ void k_round_fix(const __grid_constant__ Dev<Real, Dc> d, const __grid_constant__ Inst I,
+                            Real *__restrict__ x, Real *__restrict__ lo, Real *__restrict__ hi,
+                            const int *__restrict__ idx, int n, unsigned char *__restrict__ fixed,
+                            const Real *__restrict__ proj) {
+  const int j = blockIdx.x * NTHR + threadIdx.x;
+  if (j >= n) return;
+  const long long TG = (long long)I.T * I.G, e = idx[j], tg = I.tg0 + e, sTG = d.n_pairs;
+  const int gg = I.gen0 + (int)(e % I.G);
+  const long long kp = I.x0 + 2LL * I.T * I.n + e, kq = kp + TG, kr = kq + TG, ku = I.xu0 + e;
+  const Real u = proj[tg];
+  x[ku] = u;
+  x[kp] = proj[sTG + tg];
+  x[kq] = proj[2 * sTG + tg];
+  x[kr] = proj[3 * sTG + tg];
+  lo[ku] = hi[ku] = u;
+  if (u == Real(0)) {
+    lo[kp] = hi[kp] = lo[kq] = hi[kq] = lo[kr] = hi[kr] = Real(0);
+  } else {
+    lo[kp] = d.gen_pmin[gg];
+    hi[kp] = d.gen_pmax[gg];
+    lo[kq] = d.gen_qmin[gg];
+    hi[kq] = d.gen_qmax[gg];
+    lo[kr] = Real(0);
+    hi[kr] = d.gen_sgn[gg] < 0 ? Real(0) : d.gen_pmax[gg];
+  }
+  fixed[tg] = 1;
+}
+
+template <typename Real, typename Dc>
+cudaError_t launch_round_project(const Dev<Real, Dc> &d, const Inst &I, const Real *x, const unsigned char *fixed,
+                                 double *dist, Real *proj, cudaStream_t s) {
+  const long long TG = (long long)I.T * I.G;
+  if (TG == 0) return cudaSuccess;
+  k_round_project<Real, Dc><<<(int)((TG + NTHR - 1) / NTHR), NTHR, 0, s>>>(d, I, x, fixed, dist, proj);
+  return cudaGetLastError();
+}
+
+template <typename Real, typename Dc>
+cudaError_t launch_round_fix(const Dev<Real, Dc> &d, const Inst &I, Real *x, Real *lo, Real *hi, const int *idx,
+                             int n, unsigned char *fixed, const Real *proj, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_round_fix<Real, Dc><<<(n + NTHR - 1) / NTHR, NTHR, 0, s>>>(d, I, x, lo, hi, idx, n, fixed, proj);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_round_project<double, double>(const Dev<double, double> &, const Inst &, const double *,
+                                                          const unsigned char *, double *, double *, cudaStream_t);
+template cudaError_t launch_round_project<float, df32>(const Dev<float, df32> &, const Inst &, const float *,
+                                                       const unsigned char *, double *, float *, cudaStream_t);
+template cudaError_t launch_round_fix<double, double>(const Dev<double, double> &, const Inst &, double *, double *,
+                                                      double *, const int *, int, unsigned char *, const double *,
+                                                      cudaStream_t);
+template cudaError_t launch_round_fix<float, df32>(const Dev<float, df32> &, const Inst &, float *, float *, float *,
+                                                   const int *, int, unsigned char *, const float *, cudaStream_t);
+
 template cudaError_t launch_eval<double, double>(const Dev<double, double> &, const Plan &, const void *, bool,
                                                  cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Plan &, const void *, bool,

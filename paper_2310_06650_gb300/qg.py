@@ -77,6 +77,8 @@ def _load():
         "qg_num_vars": (C.c_int64, [vp]),
         "qg_autotune": (C.c_int, [vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
         "qg_tile_shape": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int32)]),
+        "qg_round_batch": (C.c_int, [vp, vp, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "qg_round_reset": (C.c_int, [vp]),
         "qg_layout": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "qg_set_stream": (C.c_int, [vp, vp]),
         "qg_eval_grad": (C.c_int, [vp, vp, vp, vp]),
@@ -119,7 +121,7 @@ _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_eval_grad_noalloc", "qg_adam_step", "qg_solve", "qg_breakdown",
             "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_launches_per_eval",
-            "qg_solve_schedule", "qg_schedule", "qg_ctg_select", "qg_ctg_scores", "qg_autotune", "qg_tile_shape",
+            "qg_solve_schedule", "qg_schedule", "qg_ctg_select", "qg_ctg_scores", "qg_autotune", "qg_tile_shape", "qg_round_batch", "qg_round_reset",
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
@@ -347,6 +349,17 @@ def qg_tile_shape(h: int, inst: int = 0):
     shape = (C.c_int32 * 2)()
     _check(_lib.qg_tile_shape(h, inst, shape), h)
     return tuple(shape)
+
+
+def qg_round_batch(h: int, x, frac: float):
+    """One round of batch rounding (Alg. 1); returns (fixed pairs, all pairs)."""
+    nf, nb = C.c_int64(), C.c_int64()
+    _check(_lib.qg_round_batch(h, _ptr(x), frac, C.byref(nf), C.byref(nb)), h)
+    return nf.value, nb.value
+
+
+def qg_round_reset(h: int) -> None:
+    _check(_lib.qg_round_reset(h), h)
 
 
 def qg_launches_per_eval(h: int) -> int:
