@@ -261,7 +261,8 @@ def gpu_leg(args, rank, world, local_rank):
     for label, prec in (("mixed", qg.QG_MIXED), ("fp64", qg.QG_FP64)):
         s = qg.Solver(case, precision=prec)
         x = torch.tensor(x0, dtype=s.dtype, device="cuda")
-        shape = qg.qg_autotune(s.h, x, 10, cold=True)  # block shape timed at x0, L2 flushed as below
+        shape = (qg.qg_tile_shape(s.h) if args.no_autotune
+                 else qg.qg_autotune(s.h, x, 10, cold=True))  # block shape timed at x0, L2 flushed as below
         for _ in range(max(args.warmup, 3)):
             qg.qg_solve(s.h, x, 1, 1e-3, 0.9, 0.999)
         torch.cuda.synchronize()
@@ -315,7 +316,8 @@ def gpu_leg(args, rank, world, local_rank):
             "step_ms": step_ms, "total_ms": total_ms, "phases": {k: statistics.mean(v) for k, v in phases.items()},
             "warm_ms": warm_ms, "e2e_s": e2e_s, "clocks": clk.summary(), "obj": float(s.obj[0].item()),
             "ctg_block": {"periods": shape[0], "tiles_64": shape[1],
-                          "picked_by": "qg_autotune at x0 (10 evals per shape, L2 flushed before each)"},
+                          "picked_by": "heuristic (--no-autotune)" if args.no_autotune
+                          else "qg_autotune at x0 (10 evals per shape, L2 flushed before each)"},
             "launches": qg.qg_launches_per_eval(s.h),
         }
         s.close()
@@ -386,7 +388,7 @@ def dayahead_leg(args, peaks, src, local_rank):
     x0 = warmstart.start_point(case)
     x = torch.tensor(x0, dtype=torch.float32, device="cuda")
     t0 = time.perf_counter()
-    shape = qg.qg_autotune(s.h, x, 3, cold=False)
+    shape = qg.qg_tile_shape(s.h) if args.no_autotune else qg.qg_autotune(s.h, x, 3, cold=False)
     tune_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     steps = max(5, min(args.steps, 50))
@@ -429,7 +431,8 @@ def dayahead_leg(args, peaks, src, local_rank):
                    "l2": "working set larger than L2 (line-outage block 280 MB); no flush",
                    "x0": "merit-order dispatch, flat voltage, zero angles"},
         "setup_s": setup_s,
-        "ctg_block": {"periods": shape[0], "tiles_64": shape[1], "picked_by": "qg_autotune (3 evals per shape)",
+        "ctg_block": {"periods": shape[0], "tiles_64": shape[1],
+                      "picked_by": "heuristic (--no-autotune)" if args.no_autotune else "qg_autotune (3 evals per shape)",
                       "tune_s": tune_s},
         "gpu_launches": launches * steps,
         "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in ph.items()},
@@ -486,6 +489,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-dayahead", action="store_true", help="skip the day-ahead grid")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the heuristic contingency-block shapes (fewer launches before the timed steps)")
     ap.add_argument("--dayahead-only", action="store_true",
                     help="time only the day-ahead grid and print its object as the line (profiling runs)")
     args = ap.parse_args()
