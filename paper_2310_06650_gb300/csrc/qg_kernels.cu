@@ -627,8 +627,8 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   float *s_fm = reinterpret_cast<float *>(smem_raw);  // [TB][BM] base flow of the monitored branch
   float *s_qs = s_fm + TBM * CT_BM;                   // [TB][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
   float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK] base flow of the outaged branch
-  Real *s_s2 = reinterpret_cast<Real *>(s_fk + TBM * CT_BK);  // [BM] s_ctg^2
-  Real *s_gm = s_s2 + CT_BM;                          // [TCH][BM]
+  Real *s_s2 = reinterpret_cast<Real *>(s_fk + TBM * CT_BK);  // [2][BM] s_ctg^2, then s_ctg
+  Real *s_gm = s_s2 + 2 * CT_BM;                      // [TCH][BM]
   Real *s_gq = s_gm + TCH * CT_BM;                    // [TCH][BM]
   Real *s_gk = s_gq + TCH * CT_BM;                    // [TCH][8][BK]
   Real *s_ga = s_gk + TCH * 8 * CT_BK;                // [TB][BK] column sums over the group
@@ -636,6 +636,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   Real *s_f64k = s_f64m + (F64 ? TBM * CT_BM : 0);    // [TB][BK] (FP64 path only)
   Real *s_gz = s_f64k + (F64 ? TBM * CT_BK : 0);      // [TCH][8][BK] score column sums (screening only)
   Real *s_za = s_gz + (d.score ? TCH * 8 * CT_BK : 0);  // [TB][BK] scores over the group (screening only)
+  Real *s_q2 = s_za + (d.score ? TBM * CT_BK : 0);    // [TB][BM] qmax2 of the monitored branch
   const bool score = d.score != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rq = threadIdx.x >> 4, cq = threadIdx.x & 15;
@@ -681,7 +682,11 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
       }
     }
     __syncthreads();  // the previous tile is done with s_fm, s_qs, s_s2
-    if (threadIdx.x < CT_BM) s_s2[threadIdx.x] = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
+    if (threadIdx.x < CT_BM) {
+      const Real s2 = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
+      s_s2[threadIdx.x] = s2;
+      s_s2[CT_BM + threadIdx.x] = dsqrt(s2);
+    }
 #pragma unroll 8
     for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) {
       const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
@@ -696,6 +701,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
       }
       s_fm[tt * CT_BM + c] = f;
       s_qs[tt * CT_BM + c] = qs;
+      s_q2[tt * CT_BM + c] = m < I.M ? d.qm2[I.tm0 + (long long)(t0 + tt) * I.M + m] : Real(0);
       if (F64) s_f64m[tt * CT_BM + c] = f64;
     }
     __syncthreads();
@@ -709,17 +715,18 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         const float fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w}, qs[4] = {qs4.x, qs4.y, qs4.z, qs4.w};
         const float fk[4] = {fk4.x, fk4.y, fk4.z, fk4.w};
         float F[4][4];
-        float mx = -INFINITY;
+        float mr[4];  // one max per row, combined as a tree: a short dependency chain
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            F[i][j] = __fmaf_rn(L[i][j], fk[j], fm[i]);
-            mx = fmaxf(mx, __fmaf_rn(F[i][j], F[i][j], qs[i]));  // NaN operands are ignored
-          }
+          for (int j = 0; j < 4; ++j) F[i][j] = __fmaf_rn(L[i][j], fk[j], fm[i]);
+          mr[i] = fmaxf(fmaxf(__fmaf_rn(F[i][0], F[i][0], qs[i]), __fmaf_rn(F[i][1], F[i][1], qs[i])),
+                        fmaxf(__fmaf_rn(F[i][2], F[i][2], qs[i]), __fmaf_rn(F[i][3], F[i][3], qs[i])));
+        }
+        const float mx = fmaxf(fmaxf(mr[0], mr[1]), fmaxf(mr[2], mr[3]));  // NaN operands are ignored
         if (!__any_sync(0xffffffffu, mx > 0.f)) continue;
         // a (candidate) post-contingency overload in this warp
-        const Real w = d.dt[I.tp0 + t] * d.c_s * hp.beta;
+        const Real w = __ldg(d.dt + I.tp0 + t) * d.c_s * hp.beta;
         Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
         if (mx > 0.f) {
 #pragma unroll
@@ -728,8 +735,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               if (!(__fmaf_rn(F[i][j], F[i][j], qs[i]) > 0.f)) continue;  // NaN (pad, outaged branch) fails too
-              const long long tmi = I.tm0 + (long long)t * I.M + m0 + mm;
-              const Real q2 = d.qm2[tmi];
+              const Real q2 = s_q2[tl * CT_BM + mm];
               Real Fx, Lx;
               if (F64) {
                 Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.Kp + kc + j];
@@ -741,7 +747,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
               }
               const Real sv = dsqrt(Fx * Fx + q2);
               Real val, der;
-              soft_relu(sv - dsqrt(s_s2[mm]), eps, val, der);
+              soft_relu(sv - s_s2[CT_BM + mm], eps, val, der);
               obj += w * (val - eps);
               zc[j] += w * (val - eps);
               const Real dd = w * der / sv;  // dz/dF = w sigma' F / s
@@ -1761,7 +1767,8 @@ size_t ctg_smem_bytes(int TB, bool score) {
   return sizeof(float) * (size_t)TB * (2 * CT_BM + CT_BK) +
          sizeof(Real) * ((size_t)TB * CT_BK + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
                          (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0) +
-                         (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0));
+                         (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0) +
+                         (size_t)TB * CT_BM + CT_BM);
 }
 
 // Record a timing event on s; inside stream capture it becomes an external event node.
