@@ -449,7 +449,18 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
       s_pt[r][c] = (m0 + r < I.M) ? d.ptdfg[I.pg0 + (long long)(m0 + r) * I.Gc + c0 + c] : DcOps<Dc>::zero();
     }
     __syncthreads();
-    for (int c = 0; c < cn; ++c) DcOps<Dc>::mac(acc, s_pt[ml][c], s_pg[tl][c]);
+    {  // four independent accumulation chains (the double-FP32 add is a long dependency)
+      Dc a1 = DcOps<Dc>::zero(), a2 = DcOps<Dc>::zero(), a3 = DcOps<Dc>::zero();
+      int c = 0;
+      for (; c + 4 <= cn; c += 4) {
+        DcOps<Dc>::mac(acc, s_pt[ml][c], s_pg[tl][c]);
+        DcOps<Dc>::mac(a1, s_pt[ml][c + 1], s_pg[tl][c + 1]);
+        DcOps<Dc>::mac(a2, s_pt[ml][c + 2], s_pg[tl][c + 2]);
+        DcOps<Dc>::mac(a3, s_pt[ml][c + 3], s_pg[tl][c + 3]);
+      }
+      for (; c < cn; ++c) DcOps<Dc>::mac(acc, s_pt[ml][c], s_pg[tl][c]);
+      acc = DcOps<Dc>::add(acc, DcOps<Dc>::add(DcOps<Dc>::add(a1, a2), a3));
+    }
     for (int c = ml; c < cn && c0 + c < I.Gb; c += 32) tot = DcOps<Dc>::add(tot, s_pg[tl][c]);
   }
 #pragma unroll
