@@ -331,6 +331,7 @@ __device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub,
   const Real vf = v[ft.x] / tau, vo = v[ft.y];
   const Real dl = th[ft.x] - th[ft.y] - phi;
   const Real g = d.br_g[jg], bb = d.br_b[jg], hch = d.br_hch[jg], smax = d.br_smax[jg];
+  const Real wt = d.dt[I.tp0 + t] * d.c_s * hp.beta;  // loaded before the stores below
   Real sn, cs;
   dsincos(dl, &sn, &cs);
   const Real vv = vf * vo;
@@ -359,7 +360,7 @@ __device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub,
     Real der;
     soft_relu(dsqrt(sm2) - smax, hp.eps, val, der);
   }
-  acc.v[0] = DcOps<Dc>::from_real(d.dt[I.tp0 + t] * d.c_s * hp.beta * val);
+  acc.v[0] = DcOps<Dc>::from_real(wt * val);
 }
 
 // Zonal reserve shortfall of zone `sub` in period t: the block sums the zone's reserve
@@ -945,9 +946,26 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
   const int2 ft = d.br_end[jg];
   const int kx = d.br_kidx[jg];
   const Real g = d.br_g[jg], bb = d.br_b[jg], hch = d.br_hch[jg], smax = d.br_smax[jg];
+  int xi0 = -1;
+  if (I.X > 0) xi0 = d.br_xf[jg];
   pdl_wait();
   if (on) {
     const long long e = I.tm0 + (long long)t * I.M + j;
+    // every load of the earlier stages' results is issued before the first store (a store to a
+    // possibly aliasing array would keep later loads behind it): end adjoints, flows, voltages
+    const long long tb = I.tb0 + (long long)t * I.n;
+    Real gpf = d.dP[tb + ft.x], gpt = d.dP[tb + ft.y];
+    Real gqf = d.dQ[tb + ft.x], gqt = d.dQ[tb + ft.y];
+    const Real pf = d.pf[e], qf = d.qf[e], pt = d.pt[e], qt = d.qt[e];
+    const bool qto = d.qside[e] != 0;
+    const Real *v = x + I.x0 + (long long)t * I.n;
+    const Real *th = v + (long long)I.T * I.n;
+    const Real vf0 = v[ft.x], vo = v[ft.y], thf = th[ft.x], tho = th[ft.y];
+    Real tau = Real(1), phi = Real(0);
+    if (xi0 >= 0) {
+      tau = x[I.xtau0 + (long long)t * I.X + xi0];
+      phi = x[I.xtau0 + (long long)(I.T + t) * I.X + xi0];
+    }
     Real gF = 0, gq2 = 0;
     // row partials of the outage tiles whose 64-row tile had an overload (flagged by stage 2): few
     // tiles are read unconditionally and selected (no dependent load), many are skipped
@@ -968,22 +986,16 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
         gq2 += d.pq[q];
       }
     }
+    Real zk = 0;
     if (kx >= 0) {
-      Real gk = 0, zk = 0;
+      Real gk = 0;
 #pragma unroll 8
       for (int mg = 0; mg < I.n_mg; ++mg) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
       gF += gk;
-      if (d.score) {
+      if (d.score)
         for (int mg = 0; mg < I.n_mg; ++mg) zk += d.pz[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
-        d.zs[I.tk0 + (long long)t * I.K + kx] = zk;
-      }
     }
-    d.gF[e] = gF;
     // adjoints of the four end flows
-    const long long tb = I.tb0 + (long long)t * I.n;
-    Real gpf = d.dP[tb + ft.x], gpt = d.dP[tb + ft.y];
-    Real gqf = d.dQ[tb + ft.x], gqt = d.dQ[tb + ft.y];
-    const Real pf = d.pf[e], qf = d.qf[e], pt = d.pt[e], qt = d.qt[e];
     const Real sf2 = pf * pf + qf * qf, st2 = pt * pt + qt * qt;
     if (fmax(sf2, st2) > smax * smax) {  // thermal (Example 1)
       const Real sf = dsqrt(sf2), st = dsqrt(st2);
@@ -1000,21 +1012,19 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
         gqt += k * qt;
       }
     }
-    if (d.qside[e]) gqt += Real(2) * qt * gq2;  // contingency reactive part, larger-|q| end
+    if (qto) gqt += Real(2) * qt * gq2;  // contingency reactive part, larger-|q| end
     else gqf += Real(2) * qf * gq2;
-    const Real *v = x + I.x0 + (long long)t * I.n;
-    const Real *th = v + (long long)I.T * I.n;
-    Real tau, phi;
-    int xi;
-    branch_tap(d, I, t, jg, x, tau, phi, xi);
-    const Real vf = v[ft.x] / tau, vo = v[ft.y];  // vf stands for v_f / tau
+    const int xi = xi0;
+    const Real vf = vf0 / tau;  // vf stands for v_f / tau
     Real sn, cs;
-    dsincos(th[ft.x] - th[ft.y] - phi, &sn, &cs);
+    dsincos(thf - tho - phi, &sn, &cs);
     const Real bc = bb + hch;
     const Real vv = vf * vo;
     const Real A = -g * cs - bb * sn, B = bb * cs - g * sn, C = -g * cs + bb * sn, D = bb * cs + g * sn;
     // adjoint of v_f / tau; d/dv_f = (1/tau) d/d(v_f/tau), d/dtau = -(v_f/tau^2) d/d(v_f/tau)
     const Real au = gpf * (2 * g * vf + A * vo) + gqf * (-2 * bc * vf + B * vo) + gpt * (C * vo) + gqt * (D * vo);
+    d.gF[e] = gF;
+    if (kx >= 0 && d.score) d.zs[I.tk0 + (long long)t * I.K + kx] = zk;
     d.avf[e] = au / tau;
     if (xi >= 0) d.atx[I.tx0 + (long long)t * I.X + xi] = -au * vf / tau;
     d.avo[e] = gpf * (A * vf) + gqf * (B * vf) + gpt * (2 * g * vo + C * vf) + gqt * (-2 * bc * vo + D * vf);
@@ -1088,8 +1098,23 @@ __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Re
   const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
   const bool on = pk < I.n_adj_pack;
   const int e = I.adj0 + (on ? pk : 0) * PACK + (threadIdx.x & 31);
-  // static CSR entries first, then wait for stage 3's branch-end adjoints
+  // static CSR entries and (fused Adam) the bus's optimizer state first, then wait for stage 3's
+  // branch-end adjoints (no earlier stage of this evaluation writes x, m, v or the box)
   const int code = d.adj_code[e], row = on ? d.adj_row[e] : -1;
+  const long long kv = I.x0 + (long long)t * I.n + (row >= 0 ? row : 0);
+  const long long kth = kv + (long long)I.T * I.n;
+  Real s_x[2] = {0, 0}, s_m[2] = {0, 0}, s_v[2] = {0, 0}, s_lo[2] = {0, 0}, s_hi[2] = {0, 0};
+  if (ADAM && row >= 0) {
+    const long long k2[2] = {kv, kth};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      s_x[c] = x[k2[c]];
+      s_m[c] = d.am[k2[c]];
+      s_v[c] = d.av[k2[c]];
+      s_lo[c] = d.lo[k2[c]];
+      s_hi[c] = d.hi[k2[c]];
+    }
+  }
   pdl_wait();
   if (!on) return;  // whole warp (the caller's block-wide steps come before this role)
   const int kind = code & 3;
@@ -1103,13 +1128,17 @@ __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Re
     gth = -d.ad[tm];
   }
   if (seg_sum2(row, gv, gth) && row >= 0) {
-    const long long kv = I.x0 + (long long)t * I.n + row;
-    const long long kth = kv + (long long)I.T * I.n;
     if (ADAM) {
-      adam_update(x[kv], gv, d.am[kv], d.av[kv], d.lo[kv], d.hi[kv], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
-                  d.paper_eps);
-      adam_update(x[kth], gth, d.am[kth], d.av[kth], d.lo[kth], d.hi[kth], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr,
-                  ac.eps, d.paper_eps);
+      const long long k2[2] = {kv, kth};
+      const Real g2[2] = {gv, gth};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        adam_update(s_x[c], g2[c], s_m[c], s_v[c], s_lo[c], s_hi[c], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
+                    d.paper_eps);
+        x[k2[c]] = s_x[c];
+        d.am[k2[c]] = s_m[c];
+        d.av[k2[c]] = s_v[c];
+      }
     } else {
       d.g[kv] = gv;
       d.g[kth] = gth;

@@ -193,6 +193,50 @@ def test_solve_trajectory_matches_oracle(qg):
     s.close()
 
 
+def test_tiny_config_500_iteration_trajectory(qg):
+    """The tiny configuration as specified: 500 projected-Adam iterations (lr 1e-3) from the
+    copper-plate dispatch with flat voltage.  Every iterate of the GPU run is checked against the
+    oracle at the GPU's own point (objective, gradient, and the Adam step from the GPU's moments):
+    two independent 500-step runs drift apart through rounding (Adam's normalized steps amplify the
+    sign of near-zero gradients), so the comparison is per step.  The graph-replayed loop with the
+    fused update (qg_solve) then follows the step-by-step run until the same drift sets in."""
+    c = case_named("tiny")
+    x0 = point(c, "lp")
+    iters = 500
+    lo, hi = oracle.box(c)
+    s = qg.Solver(c, precision=qg.QG_FP64)
+    xt = torch.tensor(x0, dtype=torch.float64, device="cuda")
+    m = torch.zeros_like(xt)
+    v = torch.zeros_like(xt)
+    objs = []
+    for i in range(1, iters + 1):
+        obj, g = s.eval_grad(xt)
+        xn, gn = xt.cpu().numpy().copy(), g.cpu().numpy().copy()
+        mn, vn = m.cpu().numpy().copy(), v.cpu().numpy().copy()
+        ref = oracle.evaluate(c, xn)
+        objs.append(obj[0].item())
+        assert rel(objs[-1], ref.obj) <= 1e-10, i
+        assert np.linalg.norm(gn - ref.grad) <= 1e-10 * np.linalg.norm(ref.grad), i
+        qg.qg_adam_step(s.h, xt, m, v, 1e-3, 0.9, 0.999)
+        xr, _, _ = oracle.adam_step(xn, mn, vn, gn, i, 1e-3, 0.9, 0.999, 1e-8, lo, hi)
+        assert np.max(np.abs(xt.cpu().numpy() - xr)) <= 1e-13, i
+    assert objs[-1] < 0.5 * objs[0]  # the run makes progress
+    s2 = qg.Solver(c, precision=qg.QG_FP64)
+    xs = torch.tensor(x0, dtype=torch.float64, device="cuda")
+    trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
+    qg.qg_solve(s2.h, xs, iters, 1e-3, 0.9, 0.999, trace)
+    torch.cuda.synchronize()
+    tr = trace.cpu().numpy()
+    dev = np.array([rel(a, b) for a, b in zip(tr, objs)])
+    # the fused and the step-by-step runs round differently (not bitwise equal): they agree closely
+    # until the amplification described above sets in (measured: first gap above 1e-12 at iteration
+    # 78, 2.9e-9 by iteration 100, 10% at most over 500), and both make the same progress
+    assert dev[:60].max() <= 1e-9
+    assert dev.max() <= 0.25 and tr[-1] < 0.5 * tr[0]
+    s.close()
+    s2.close()
+
+
 def test_batch_config_sampled_parity(qg):
     """The 32-instance uneven batch (73/200/617/1576 buses, 12/18/24/48 periods) in one handle;
     one instance of each shape checked against the oracle on objective and gradient."""
