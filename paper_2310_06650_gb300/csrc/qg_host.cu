@@ -91,6 +91,7 @@ struct qg_ctx {
   unsigned int *d_ticket = nullptr;
   // cached CUDA graph of one (evaluation + fused Adam) iteration for qg_solve
   cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec_u = nullptr;  // SOLVE_UNROLL iterations in one graph (same parameters)
   const void *g_x = nullptr;
   double g_lr = 0, g_b1 = 0, g_b2 = 0;
   double *g_trace = nullptr;
@@ -1063,9 +1064,16 @@ int check_device(qg_ctx *h) {
   return QG_OK;
 }
 
-void free_all(qg_ctx *h) {
+constexpr int SOLVE_UNROLL = 8;  // Adam iterations per graph launch in long solves
+
+void drop_graphs(qg_ctx *h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
+  if (h->gexec_u) cudaGraphExecDestroy(h->gexec_u);
+  h->gexec = h->gexec_u = nullptr;
+}
+
+void free_all(qg_ctx *h) {
+  drop_graphs(h);
   for (auto &e : h->ev)
     if (e) {
       cudaEventDestroy(e);
@@ -1079,19 +1087,23 @@ bool mixed(const qg_ctx *h) { return h->opt.precision == QG_MIXED; }
 
 // One evaluation; with adam, the projected Adam update is fused into stages 4 and 5 using the
 // handle's moments and the given hyper-parameters.
+// step_off: this iteration's place in a graph of several (it reads step + step_off); defer: leave
+// the objective sum and the step count to a closing run_finish (fused iterations without a trace).
 int run_eval(qg_ctx *h, const void *x, bool adam, double lr, double b1, double b2, double *trace, int trace_len,
-             const double *sched = nullptr, int sched_len = 0) {
+             const double *sched = nullptr, int sched_len = 0, int step_off = 0, bool defer = false) {
   cudaEvent_t *ev = h->profiling ? h->ev : nullptr;
   cudaError_t e;
   if (mixed(h)) {
     Dev<float, df32> d = h->d32;
     d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
     d.trace = trace; d.trace_len = trace_len; d.sched = sched; d.sched_len = sched_len;
+    d.step_off = step_off; d.defer_final = defer ? 1 : 0;
     e = launch_eval<float, df32>(d, h->plan, x, adam, h->stream, ev);
   } else {
     Dev<double, double> d = h->d64;
     d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
     d.trace = trace; d.trace_len = trace_len; d.sched = sched; d.sched_len = sched_len;
+    d.step_off = step_off; d.defer_final = defer ? 1 : 0;
     e = launch_eval<double, double>(d, h->plan, x, adam, h->stream, ev);
   }
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("evaluation launch: ") + cudaGetErrorString(e));
@@ -1147,8 +1159,7 @@ int replan_dev(qg_ctx *h, Dev<Real, Dc> &d, const Knobs &kn) {
     cudaGetLastError();  // a refused attribute is not a sticky error
     return fail(h, QG_ERR_UNSUPPORTED, std::string("prepare_eval: ") + cudaGetErrorString(e));
   }
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
+  drop_graphs(h);
   h->knobs = kn;
   return QG_OK;
 }
@@ -1181,6 +1192,23 @@ double time_evals(qg_ctx *h, const void *x, int reps, void *flush, size_t flush_
   for (auto &e : ev)
     if (e) cudaEventDestroy(e);
   return ok ? ms / reps : -1.0;
+}
+
+// Closing kernel of n deferred iterations: the objective of the last one (read at its schedule
+// row), then step += n.
+int run_finish(qg_ctx *h, int n, const double *sched, int sched_len) {
+  cudaError_t e;
+  if (mixed(h)) {
+    Dev<float, df32> d = h->d32;
+    d.sched = sched; d.sched_len = sched_len; d.step_off = n - 1;
+    e = launch_finish<float, df32>(d, h->plan, n, h->stream);
+  } else {
+    Dev<double, double> d = h->d64;
+    d.sched = sched; d.sched_len = sched_len; d.step_off = n - 1;
+    e = launch_finish<double, double>(d, h->plan, n, h->stream);
+  }
+  if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("closing kernel launch: ") + cudaGetErrorString(e));
+  return QG_OK;
 }
 
 int run_adam(qg_ctx *h, void *x, void *m, void *v, double lr, double b1, double b2) {
@@ -1524,11 +1552,9 @@ int solve_graph(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, doub
   if (!obj_trace && !sched) len = 0;
   const bool same = h->gexec && h->g_x == x && h->g_lr == lr && h->g_b1 == beta1 && h->g_b2 == beta2 &&
                     h->g_trace == obj_trace && h->g_sched == sched && h->g_trace_len == len;
-  if (!same) {
-    if (h->gexec) {
-      cudaGraphExecDestroy(h->gexec);
-      h->gexec = nullptr;
-    }
+  if (!same) drop_graphs(h);
+  // capture `n` iterations (evaluation + fused Adam) into one graph
+  auto capture = [&](cudaGraphExec_t *out, int n) -> int {
     cudaStream_t cs;
     CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaStream_t saved = h->stream;
@@ -1537,10 +1563,15 @@ int solve_graph(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, doub
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int rc = QG_OK;
     if (e == cudaSuccess) {
-      rc = run_eval(h, x, true, lr, beta1, beta2, obj_trace, obj_trace ? len : 0, sched, sched ? len : 0);
+      // without a trace the objective is summed once, after the last iteration of the graph
+      const bool defer = obj_trace == nullptr && !h->profiling;
+      for (int k = 0; k < n && !rc; ++k)
+        rc = run_eval(h, x, true, lr, beta1, beta2, obj_trace, obj_trace ? len : 0, sched, sched ? len : 0,
+                      defer ? k : 0, defer);
+      if (!rc && defer) rc = run_finish(h, n, sched, sched ? len : 0);
       cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
       if (!rc && e2 == cudaSuccess) {
-        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        e = cudaGraphInstantiate(out, graph, 0);
         cudaGraphDestroy(graph);
       } else if (!rc) {
         e = e2;
@@ -1550,10 +1581,23 @@ int solve_graph(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, doub
     cudaStreamDestroy(cs);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    return QG_OK;
+  };
+  if (!h->gexec) {
+    int rc = capture(&h->gexec, 1);
+    if (rc) return rc;
     h->g_x = x; h->g_lr = lr; h->g_b1 = beta1; h->g_b2 = beta2; h->g_trace = obj_trace; h->g_sched = sched;
     h->g_trace_len = len;
   }
-  for (int it = 0; it < iters; ++it) CUDA_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
+  // long solves: SOLVE_UNROLL iterations per launch (no graph-launch gap between them); the timed
+  // per-kernel mode keeps one iteration per launch
+  const int n_u = h->profiling ? 0 : iters / SOLVE_UNROLL;
+  if (n_u > 0 && !h->gexec_u) {
+    int rc = capture(&h->gexec_u, SOLVE_UNROLL);
+    if (rc) return rc;
+  }
+  for (int it = 0; it < n_u; ++it) CUDA_TRY(h, cudaGraphLaunch(h->gexec_u, h->stream));
+  for (int it = n_u * SOLVE_UNROLL; it < iters; ++it) CUDA_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
   return QG_OK;
 }
 
@@ -1625,8 +1669,7 @@ int qg_set_profiling(qg_ctx *h, int on) {
   if (on && !h->ev[0])
     for (auto &e : h->ev) CUDA_TRY(h, cudaEventCreate(&e));
   if ((on != 0) != h->profiling && h->gexec) {  // the cached graph must be re-captured
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
+    drop_graphs(h);
   }
   h->profiling = on != 0;
   return QG_OK;

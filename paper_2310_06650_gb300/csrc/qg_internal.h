@@ -186,6 +186,9 @@ struct Dev {
   Real *g;                            // gradient [n_x]
   unsigned int *ticket;               // last-block counter of stage 5
   long long *step;                    // Adam step counter
+  int step_off;                       // iteration k of a graph of several: it reads step + k
+  int defer_final;                    // 1: stage 5 leaves the objective sum and the step count to
+                                      // the graph's closing kernel (fused iterations without a trace)
   // fused Adam (qg_solve): moments and hyper-parameters
   Real *am, *av;
   double lr, b1, b2, aeps;
@@ -222,6 +225,11 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *x, bo
 
 template <typename Real, typename Dc>
 cudaError_t prepare_eval(int maxTB, bool score);
+
+// Closing kernel of a graph of n fused iterations with deferred objective sums: the last iteration's
+// objective, then step += n.
+template <typename Real, typename Dc>
+cudaError_t launch_finish(const Dev<Real, Dc> &d, const Plan &P, int n, cudaStream_t s);
 
 template <typename Real, typename Dc>
 cudaError_t launch_round_project(const Dev<Real, Dc> &d, const Inst &I, const Real *x, const unsigned char *fixed,

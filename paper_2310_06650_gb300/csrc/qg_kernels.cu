@@ -250,7 +250,7 @@ struct HP {
 
 template <typename Real, typename Dc>
 __device__ __forceinline__ long long sched_index(const Dev<Real, Dc> &d) {
-  long long it = *d.step - *d.trace_step0;
+  long long it = *d.step + d.step_off - *d.trace_step0;
   return it < 0 ? 0 : (it >= d.sched_len ? d.sched_len - 1 : it);
 }
 
@@ -419,7 +419,13 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   const int tl = threadIdx.x >> 5, ml = threadIdx.x & 31;
   const int t = t0 + tl, m = m0 + ml;
   const Real *p = x + I.x0 + 2LL * I.T * I.n;
-  pold_share(d, I, t0, sub, x);
+  // the output's own terms first (none depends on the products): load latency overlaps the products
+  const bool out = t < I.T && m < I.M;
+  const long long e = I.tm0 + (long long)(out ? t : 0) * I.M + (out ? m : 0);
+  const Dc cl = d.cload[e], rs = d.rsum[I.br0 + (out ? m : 0)];
+  const Dc lt = d.ltot[I.tp0 + (t < I.T ? t : 0)];
+  const int xi = d.br_xf[I.br0 + (out ? m : 0)], kx = d.br_kidx[I.br0 + (out ? m : 0)];
+  const Real bphi = (out && xi >= 0) ? d.br_b[I.br0 + m] * x[I.xtau0 + (long long)(I.T + t) * I.X + xi] : Real(0);
   Dc acc = DcOps<Dc>::zero();
   Dc tot = DcOps<Dc>::zero();  // running sum of p_G over generator buses for mu_t (warp tl)
   // columns: generator buses (their dispatch), then transformers (their phase-shift flow b = b_sr phi)
@@ -467,25 +473,22 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tot = DcOps<Dc>::add(tot, DcOps<Dc>::shfl_down(tot, o));
   if (ml == 0 && t < I.T)
-    s_mu[tl] = DcOps<Dc>::mul(DcOps<Dc>::add(tot, DcOps<Dc>::neg(d.ltot[I.tp0 + t])), DcOps<Dc>::inv_n(I));
+    s_mu[tl] = DcOps<Dc>::mul(DcOps<Dc>::add(tot, DcOps<Dc>::neg(lt)), DcOps<Dc>::inv_n(I));
   __syncthreads();
-  if (t < I.T && m < I.M) {
-    const long long e = I.tm0 + (long long)t * I.M + m;
-    Dc f = DcOps<Dc>::add(acc, DcOps<Dc>::neg(d.cload[e]));
-    f = DcOps<Dc>::add(f, DcOps<Dc>::neg(DcOps<Dc>::mul(s_mu[tl], d.rsum[I.br0 + m])));
-    const int xi = d.br_xf[I.br0 + m];  // a phase shifter's own flow b adds to the monitored flow
-    if (xi >= 0)
-      f = DcOps<Dc>::add(f, DcOps<Dc>::from_real(d.br_b[I.br0 + m] * x[I.xtau0 + (long long)(I.T + t) * I.X + xi]));
+  if (out) {
+    Dc f = DcOps<Dc>::add(acc, DcOps<Dc>::neg(cl));
+    f = DcOps<Dc>::add(f, DcOps<Dc>::neg(DcOps<Dc>::mul(s_mu[tl], rs)));
+    if (xi >= 0) f = DcOps<Dc>::add(f, DcOps<Dc>::from_real(bphi));  // a phase shifter's own flow b
     const Real fr = DcOps<Dc>::to_real(f);
     d.fre[e] = fr;
     d.f32[e] = DcOps<Dc>::to_float(f);
-    const int kx = d.br_kidx[I.br0 + m];
     if (kx >= 0) {
       const long long ek = I.tk0 + (long long)t * I.K + kx;
       d.fk[ek] = fr;
       d.fk32[ek] = DcOps<Dc>::to_float(f);
     }
   }
+  pold_share(d, I, t0, sub, x);  // after the loads above: its stores would otherwise hold them back
 }
 
 // Base DC flows in the sparse mode, from the angles theta' = Yhat^-1 p_inj solved by the sparse
@@ -675,7 +678,34 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         for (int j = 0; j < 4; ++j) L[i][j] = f_nan();
       }
     }
+    // staging of one 64-row tile's per-row data (the flows, q_max^2 - s_ctg^2 and q_max^2 of the
+    // monitored branches) for entry e of [TB][64]
+    auto stage_m = [&](int e) {
+      const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
+      float f = 0.f, qs = 0.f;
+      Real f64 = 0, q2 = 0;
+      if (m < I.M) {
+        const long long idx = I.tm0 + (long long)(t0 + tt) * I.M + m;
+        f = d.f32[idx];
+        q2 = d.qm2[idx];
+        const Real s2 = d.br_s2ctg[I.br0 + m];
+        qs = F64 ? (float)(q2 - s2) + 1e-4f * (float)s2 : (float)(q2 - s2);
+        if (F64) f64 = d.fre[idx];
+      }
+      s_fm[tt * CT_BM + c] = f;
+      s_qs[tt * CT_BM + c] = qs;
+      s_q2[tt * CT_BM + c] = q2;
+      if (F64) s_f64m[tt * CT_BM + c] = f64;
+    };
+    const Real s2m = (threadIdx.x < CT_BM && m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
+    if (mt > mt0) __syncthreads();  // the previous tile is done with s_fm, s_qs, s_s2, s_q2
+    if (threadIdx.x < CT_BM) {
+      s_s2[threadIdx.x] = s2m;
+      s_s2[CT_BM + threadIdx.x] = dsqrt(s2m);
+    }
     if (mt == mt0) {
+      // first tile: the outage columns' data and the rows' data in one pass (CT_BK == CT_BM), so
+      // that both loads are in flight together
       pdl_wait();
 #pragma unroll 4
       for (int e = threadIdx.x; e < TB * CT_BK; e += NTHR) {
@@ -687,34 +717,15 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           f = d.fk32[idx];
           if (F64) f64 = d.fk[idx];
         }
+        stage_m(e);
         s_fk[tt * CT_BK + c] = f;
         if (F64) s_f64k[tt * CT_BK + c] = f64;
         s_ga[tt * CT_BK + c] = 0;
         if (score) s_za[tt * CT_BK + c] = 0;
       }
-    }
-    __syncthreads();  // the previous tile is done with s_fm, s_qs, s_s2
-    if (threadIdx.x < CT_BM) {
-      const Real s2 = (m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
-      s_s2[threadIdx.x] = s2;
-      s_s2[CT_BM + threadIdx.x] = dsqrt(s2);
-    }
+    } else {
 #pragma unroll 8
-    for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) {
-      const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
-      float f = 0.f, qs = 0.f;
-      Real f64 = 0;
-      if (m < I.M) {
-        const long long idx = I.tm0 + (long long)(t0 + tt) * I.M + m;
-        f = d.f32[idx];
-        const Real q2 = d.qm2[idx], s2 = d.br_s2ctg[I.br0 + m];
-        qs = F64 ? (float)(q2 - s2) + 1e-4f * (float)s2 : (float)(q2 - s2);
-        if (F64) f64 = d.fre[idx];
-      }
-      s_fm[tt * CT_BM + c] = f;
-      s_qs[tt * CT_BM + c] = qs;
-      s_q2[tt * CT_BM + c] = m < I.M ? d.qm2[I.tm0 + (long long)(t0 + tt) * I.M + m] : Real(0);
-      if (F64) s_f64m[tt * CT_BM + c] = f64;
+      for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) stage_m(e);
     }
     __syncthreads();
     for (int tc0 = 0; tc0 < TB; tc0 += TCH) {
@@ -928,7 +939,7 @@ __device__ void fold_slots(const Dev<Real, Dc> &d, const Inst &I, int r) {
 }
 
 template <typename Real, typename Dc>
-__global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, Dc> d,
+__global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x) {
   const Where w = locate(S);
@@ -970,7 +981,7 @@ __global__ void __launch_bounds__(NTHR) k_s3(const __grid_constant__ Dev<Real, D
     // row partials of the outage tiles whose 64-row tile had an overload (flagged by stage 2): few
     // tiles are read unconditionally and selected (no dependent load), many are skipped
     if (I.n_kt <= 16) {
-#pragma unroll 8
+#pragma unroll 4
       for (int kt = 0; kt < I.n_kt; ++kt) {
         const long long q = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
         const bool f = d.pmf[I.pf0 + ((long long)kt * I.T + t) * I.n_mt + (j >> 6)] != 0;
@@ -1083,7 +1094,7 @@ __device__ AdamCoef<Real> adam_coef(const Dev<Real, Dc> &d) {
   __shared__ Real sc[3];
   __shared__ long long s_step;
   if (threadIdx.x == 0) {
-    const long long step = *d.step;
+    const long long step = *d.step + d.step_off;
     bias_corr(d.b1, d.b2, step, sc[0], sc[1]);
     sc[2] = (Real)(d.sched ? d.sched[3 * sched_index(d)] : d.lr);  // step size (Eq. step_size schedule)
     s_step = step;
@@ -1194,7 +1205,7 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
       }
       d.obj[b] = tot;
       if (d.trace) {
-        const long long it = *d.step - *d.trace_step0;
+        const long long it = *d.step + d.step_off - *d.trace_step0;
         if (it >= 0 && it < d.trace_len) d.trace[it * tab.n_inst + b] = tot;
       }
     }
@@ -1365,6 +1376,7 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
 // its last read of the step counter.
 template <typename Real, typename Dc, bool ADAM>
 __device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab, long long step) {
+  if (d.defer_final) return;  // the graph's closing kernel sums the objective and counts the steps
   __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1839,6 +1851,19 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cud
 }
 
 template <typename Real, typename Dc>
+__global__ void __launch_bounds__(NTHR) k_finish(const __grid_constant__ Dev<Real, Dc> d,
+                                                 const __grid_constant__ InstTab tab, int n) {
+  pdl_wait();
+  final_reduce(d, tab);
+  if (threadIdx.x == 0) *d.step += n;
+}
+
+template <typename Real, typename Dc>
+cudaError_t launch_finish(const Dev<Real, Dc> &d, const Plan &P, int n, cudaStream_t s) {
+  return launch_pdl(k_finish<Real, Dc>, 1, 0, s, d, P.tab, n);
+}
+
+template <typename Real, typename Dc>
 cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, bool adam, cudaStream_t s,
                         cudaEvent_t *ev) {
   Real *x = const_cast<Real *>(static_cast<const Real *>(xv));
@@ -2030,6 +2055,8 @@ template cudaError_t launch_eval<double, double>(const Dev<double, double> &, co
 template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Plan &, const void *, bool,
                                               cudaStream_t, cudaEvent_t *);
 template cudaError_t prepare_eval<double, double>(int, bool);
+template cudaError_t launch_finish<double, double>(const Dev<double, double> &, const Plan &, int, cudaStream_t);
+template cudaError_t launch_finish<float, df32>(const Dev<float, df32> &, const Plan &, int, cudaStream_t);
 template cudaError_t prepare_eval<float, df32>(int, bool);
 template cudaError_t launch_adam<double>(double *, double *, double *, const double *, const double *, const double *,
                                          long long, long long *, unsigned int *, double, double, double, double, int,

@@ -237,6 +237,28 @@ def test_tiny_config_500_iteration_trajectory(qg):
     s2.close()
 
 
+def test_unrolled_solve_graph_equals_single_iterations(qg):
+    """Long solves replay a graph of several iterations; the result is bitwise that of replaying the
+    one-iteration graph as often (the same kernels in the same order)."""
+    c = case_named("mid")
+    x0 = point(c, "lp_perturbed")
+    iters = 19
+    out = []
+    for chunk in (iters, 1):
+        s = qg.Solver(c, precision=qg.QG_MIXED)
+        xt = torch.tensor(x0, dtype=torch.float32, device="cuda")
+        if chunk == iters:
+            qg.qg_solve(s.h, xt, iters, 1e-3, 0.9, 0.999)
+        else:
+            for _ in range(iters):
+                qg.qg_solve(s.h, xt, 1, 1e-3, 0.9, 0.999)
+        torch.cuda.synchronize()
+        out.append((xt.cpu().clone(), qg.qg_get_step(s.h)))
+        s.close()
+    assert out[0][1] == out[1][1] == iters
+    assert torch.equal(out[0][0], out[1][0])
+
+
 def test_batch_config_sampled_parity(qg):
     """The 32-instance uneven batch (73/200/617/1576 buses, 12/18/24/48 periods) in one handle;
     one instance of each shape checked against the oracle on objective and gradient."""
