@@ -216,7 +216,9 @@ int qg_adam_step(qg_ctx *h, void *x, void *m, void *v, double lr, double beta1, 
  * qg_set_step(h, 0)), replayed from a CUDA graph that is captured on the first
  * call and re-captured when x, lr, beta1, beta2, obj_trace or (with a trace) iters change.  Does not
  * synchronize.  obj_trace (device, iters x n_inst doubles, may be NULL) receives the objective
- * evaluated at the start of each iteration. */
+ * evaluated at the start of each iteration.  Long runs replay a graph of 8 iterations (bitwise the
+ * same result).  Without a trace the objective is summed once per graph replay, for its last
+ * iteration (what qg_breakdown then reports). */
 int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace);
 
 /* qg_solve with the schedules of Sec. II-F: iteration i of a scheduled run takes its Adam step size,
