@@ -313,8 +313,8 @@ int qg_round_batch(qg_ctx *h, void *x, double frac, int64_t *n_fixed, int64_t *n
 int qg_round_reset(qg_ctx *h);
 
 /* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: the
- * 5 stage kernels, plus 3 to 7 solve kernels with the sparse DC solver.  Returns a negative
- * error code for a NULL handle. */
+ * 5 stage kernels, plus 3 to 7 solve kernels with the sparse DC solver (a qg_solve graph replay
+ * without a trace adds one closing kernel).  Returns a negative error code for a NULL handle. */
 int32_t qg_launches_per_eval(const qg_ctx *h);
 
 const char *qg_last_error(const qg_ctx *h);
