@@ -580,7 +580,13 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   long long tiles = 0;
   for (int b = 0; b < B; ++b)
     if (h->hi[b].Ks > 0) tiles += (long long)ceil_div(h->hi[b].M, CT_BM) * ceil_div(h->hi[b].Ks, CT_BK);
-  const int ntc_all = kn.ntc > 0 ? kn.ntc : (int)std::max(1LL, tiles > 0 ? CTG_WAVE / tiles : 1);
+  // heuristic: about one wave of blocks when tiles are few; at most 24 periods per block (the shared
+  // memory of longer chunks leaves fewer than 3 blocks on an SM)
+  int maxT_all = 1;
+  for (int b = 0; b < B; ++b) maxT_all = std::max(maxT_all, h->hi[b].T);
+  const int ntc_all = kn.ntc > 0 ? kn.ntc
+                                 : (int)std::max({1LL, tiles > 0 ? CTG_WAVE / tiles : 1LL,
+                                                  (long long)ceil_div(maxT_all, 24)});
   // at most ~64 column partials per outage for stage 3 to sum serially
   int max_nmt = 0;
   for (int b = 0; b < B; ++b) max_nmt = std::max(max_nmt, ceil_div(h->hi[b].M, CT_BM));
