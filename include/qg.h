@@ -198,7 +198,9 @@ int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g);
 
 /* qg_eval_grad on host buffers: copies x (qg_num_vars doubles) to the device,
  * evaluates, and copies obj (n_inst doubles) and g (qg_num_vars doubles, may be
- * NULL) back; synchronizes.  In QG_MIXED mode the copies convert to/from float. */
+ * NULL) back; synchronizes.  In QG_MIXED mode the copies convert to/from float.
+ * With page-locked buffers the copies and the evaluation replay from a graph
+ * cached for those buffers (re-captured when they change). */
 int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g);
 
 /* One projected Adam step (Alg. 3) on every variable, using the gradient of the

@@ -92,6 +92,9 @@ struct qg_ctx {
   // cached CUDA graph of one (evaluation + fused Adam) iteration for qg_solve
   cudaGraphExec_t gexec = nullptr;
   cudaGraphExec_t gexec_u = nullptr;  // SOLVE_UNROLL iterations in one graph (same parameters)
+  // cached graph of qg_eval_grad_host for one set of pinned host buffers
+  cudaGraphExec_t hexec = nullptr;
+  const void *h_x = nullptr, *h_obj = nullptr, *h_g = nullptr;
   const void *g_x = nullptr;
   double g_lr = 0, g_b1 = 0, g_b2 = 0;
   double *g_trace = nullptr;
@@ -1075,7 +1078,8 @@ constexpr int SOLVE_UNROLL = 8;  // Adam iterations per graph launch in long sol
 void drop_graphs(qg_ctx *h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gexec_u) cudaGraphExecDestroy(h->gexec_u);
-  h->gexec = h->gexec_u = nullptr;
+  if (h->hexec) cudaGraphExecDestroy(h->hexec);
+  h->gexec = h->gexec_u = h->hexec = nullptr;
 }
 
 void free_all(qg_ctx *h) {
@@ -1507,8 +1511,12 @@ int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g) {
   return mixed(h) ? eval_noalloc<float, df32>(h, h->d32, x, obj, g) : eval_noalloc<double, double>(h, h->d64, x, obj, g);
 }
 
-int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {
-  if (!h || !x) return h ? fail(h, QG_ERR_INVALID_ARG, "x is NULL") : QG_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// The work of qg_eval_grad_host on h->stream: copy x in, evaluate, copy the gradient and objective out.
+int host_eval_work(qg_ctx *h, const double *x, double *obj, double *g) {
   const long long n = h->n_x;
   const int nb = (int)std::min<long long>((n + 255) / 256, 152 * 8);
   if (mixed(h)) {
@@ -1528,6 +1536,60 @@ int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {
     }
   }
   if (obj) CUDA_TRY(h, cudaMemcpyAsync(obj, h->d_obj, sizeof(double) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+  return QG_OK;
+}
+
+bool pinned(const void *p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {
+  if (!h || !x) return h ? fail(h, QG_ERR_INVALID_ARG, "x is NULL") : QG_ERR_INVALID_ARG;
+  // pinned buffers (and no per-kernel timing): one cached graph of the copies and the evaluation,
+  // re-captured when the buffers change
+  const bool graph = !h->profiling && pinned(x) && pinned(obj) && pinned(g);
+  if (graph) {
+    if (!(h->hexec && h->h_x == x && h->h_obj == obj && h->h_g == g)) {
+      if (h->hexec) cudaGraphExecDestroy(h->hexec);
+      h->hexec = nullptr;
+      cudaStream_t cs;
+      CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaStream_t saved = h->stream;
+      h->stream = cs;
+      cudaGraph_t gr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      int rc = QG_OK;
+      if (e == cudaSuccess) {
+        rc = host_eval_work(h, x, obj, g);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+        if (!rc && e2 == cudaSuccess) {
+          e = cudaGraphInstantiate(&h->hexec, gr, 0);
+          cudaGraphDestroy(gr);
+        } else if (!rc) {
+          e = e2;
+        }
+      }
+      h->stream = saved;
+      cudaStreamDestroy(cs);
+      if (rc) return rc;
+      if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      h->h_x = x; h->h_obj = obj; h->h_g = g;
+    }
+    CUDA_TRY(h, cudaGraphLaunch(h->hexec, h->stream));
+  } else {
+    const int rc = host_eval_work(h, x, obj, g);
+    if (rc) return rc;
+  }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   CUDA_TRY(h, cudaGetLastError());
   return QG_OK;

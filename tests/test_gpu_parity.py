@@ -151,6 +151,26 @@ def test_host_entry_matches_device_entry(qg):
         s.close()
 
 
+def test_host_entry_with_pinned_buffers_replays_a_graph(qg):
+    """Page-locked host buffers take the cached-graph route: the same results as the device entry,
+    call after call, with new contents in the same buffers and with other buffers."""
+    c = case_named("mid")
+    for prec in (qg.QG_FP64, qg.QG_MIXED):
+        s = qg.Solver(c, precision=prec)
+        xs = [point(c, "lp_perturbed"), point(c, "3")]
+        bufs = [(torch.zeros(c.n_x, dtype=torch.float64).pin_memory(), torch.zeros(1, dtype=torch.float64).pin_memory(),
+                 torch.zeros(c.n_x, dtype=torch.float64).pin_memory()) for _ in range(2)]
+        for k, x in enumerate(xs + xs):
+            xb, ob, gb = bufs[k // 2 % 2]
+            xb.copy_(torch.from_numpy(x))
+            qg.qg_eval_grad_host(s.h, xb.numpy(), ob.numpy(), gb.numpy())
+            obj, g = s.eval_grad(torch.tensor(x, dtype=s.dtype, device="cuda"))
+            torch.cuda.synchronize()
+            assert ob.item() == obj.item(), k
+            assert np.array_equal(gb.numpy(), g.double().cpu().numpy()), k
+        s.close()
+
+
 def test_adam_step_parity(qg):
     c = case_named("mid")
     x = point(c, "lp_perturbed")
