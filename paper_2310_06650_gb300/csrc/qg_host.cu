@@ -1556,10 +1556,11 @@ extern "C" {
 int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {
   if (!h || !x) return h ? fail(h, QG_ERR_INVALID_ARG, "x is NULL") : QG_ERR_INVALID_ARG;
   // pinned buffers (and no per-kernel timing): one cached graph of the copies and the evaluation,
-  // re-captured when the buffers change
-  const bool graph = !h->profiling && pinned(x) && pinned(obj) && pinned(g);
+  // re-captured when the buffers change (the same buffers as the cached graph's skip the check)
+  const bool cached = h->hexec && h->h_x == x && h->h_obj == obj && h->h_g == g;
+  const bool graph = !h->profiling && (cached || (pinned(x) && pinned(obj) && pinned(g)));
   if (graph) {
-    if (!(h->hexec && h->h_x == x && h->h_obj == obj && h->h_g == g)) {
+    if (!cached) {
       if (h->hexec) cudaGraphExecDestroy(h->hexec);
       h->hexec = nullptr;
       cudaStream_t cs;
