@@ -310,8 +310,8 @@ def gpu_leg(args, rank, world, local_rank):
         gh = torch.zeros(case.n_x, dtype=torch.float64).pin_memory().numpy()
         for _ in range(3):
             qg.qg_eval_grad_host(s.h, xh, oh, gh)
-        # three rounds of K calls, the median round reported: a host-side stall (the machine's host is
-        # shared) in one round does not stand for the call's cost
+        # three rounds of K calls, the median round reported: a stall of the host (other processes
+        # on it) in one round does not stand for the call's cost
         rounds = []
         for _ in range(3):
             t0 = time.perf_counter()
