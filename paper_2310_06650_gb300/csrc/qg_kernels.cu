@@ -371,6 +371,12 @@ __device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, con
   __shared__ Real red[NTHR / 32];
   const int zg = I.zone0 + z;  // global zone id; zgen_ptr is one CSR over all zones of the batch
   const Real *r = x + I.x0 + 2LL * I.T * I.n + 2LL * I.T * I.G + (long long)t * I.G;
+  const long long k = I.tz0 + (long long)t * I.Z + z;
+  Real req = 0, w = 0;
+  if (threadIdx.x == 0) {  // loaded ahead of the sum (no dependence on it)
+    req = d.rreq[k];
+    w = d.dt[I.tp0 + t] * d.c_rz * hp.beta;
+  }
   const int e0 = d.zgen_ptr[zg], e1 = d.zgen_ptr[zg + 1];
   Real sr = 0;
   for (int e = e0 + threadIdx.x; e < e1; e += NTHR) sr += r[d.zgen[e] - I.gen0];
@@ -380,11 +386,9 @@ __device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, con
   if (threadIdx.x == 0) {
     Real tot = 0;
 #pragma unroll
-    for (int w = 0; w < NTHR / 32; ++w) tot += red[w];
-    const long long k = I.tz0 + (long long)t * I.Z + z;
+    for (int q = 0; q < NTHR / 32; ++q) tot += red[q];
     Real val, der;
-    soft_relu(d.rreq[k] - tot, hp.eps, val, der);
-    const Real w = d.dt[I.tp0 + t] * d.c_rz * hp.beta;
+    soft_relu(req - tot, hp.eps, val, der);
     d.dZ[k] = w * der;
     acc.v[0] = DcOps<Dc>::from_real(w * val);
   }
@@ -559,6 +563,12 @@ __device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, co
   const int e = I.bal0 + pk * PACK + (threadIdx.x & 31);
   const int code = d.bal_code[e], row = d.bal_row[e];
   const int kind = code & 3, id = code >> 2;
+  // data no earlier stage writes first (loads, weights, the device's role), then wait for stage 1
+  const long long ti = I.tb0 + (long long)t * I.n + (row >= 0 ? row : 0);
+  const Real lp = d.load_p[ti], lq = d.load_q[ti];
+  const Real dtw = d.dt[I.tp0 + t];
+  const Real sg = kind == 2 ? d.gen_sgn[I.gen0 + id] : Real(1);
+  pdl_wait();
   Real P = 0, Q = 0;
   const long long tm = I.tm0 + (long long)t * I.M + id;
   if (kind == 0) {
@@ -569,19 +579,16 @@ __device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, co
     Q = d.qt[tm];
   } else if (kind == 2) {  // a producer supplies (-), a consumer draws (+)
     const Real *p = x + I.x0 + 2LL * I.T * I.n + (long long)t * I.G + id;
-    const Real sg = d.gen_sgn[I.gen0 + id];
     P = -sg * p[0];
     Q = -sg * p[(long long)I.T * I.G];
   }
   if (seg_sum2(row, P, Q) && row >= 0) {
-    const long long ti = I.tb0 + (long long)t * I.n + row;
-    P += d.load_p[ti];
-    Q += d.load_q[ti];
+    P += lp;
+    Q += lq;
     Real vp, dp, vq, dq;
     soft_abs(P, hp.eps, vp, dp);
     soft_abs(Q, hp.eps, vq, dq);
-    const Real dt = d.dt[I.tp0 + t];
-    const Real wp = dt * d.c_p * hp.beta, wq = dt * d.c_q * hp.beta;
+    const Real wp = dtw * d.c_p * hp.beta, wq = dtw * d.c_q * hp.beta;
     d.dP[ti] = wp * dp;
     d.dQ[ti] = wq * dq;
     acc.v[0] = DcOps<Dc>::from_real(wp * vp);
@@ -873,8 +880,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
   if (w.role == R_BUS) {
     acc.id[0] = T_ZP;
     acc.id[1] = T_ZQ;
-    pdl_wait();
-    s2_bus(d, I, w.t, w.sub, x, acc, hparams(d));
+    s2_bus(d, I, w.t, w.sub, x, acc, hparams(d));  // waits after its static loads
   } else {
     acc.id[0] = T_ZCTG;
     s2_ctg(d, I, w.sub, acc, hparams(d));
@@ -1853,9 +1859,10 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cud
 template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_finish(const __grid_constant__ Dev<Real, Dc> d,
                                                  const __grid_constant__ InstTab tab, int n) {
+  const long long step = *d.step;  // only closing kernels write it in this mode
   pdl_wait();
   final_reduce(d, tab);
-  if (threadIdx.x == 0) *d.step += n;
+  if (threadIdx.x == 0) *d.step = step + n;
 }
 
 template <typename Real, typename Dc>
