@@ -41,7 +41,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) per launch of the dominant kernel, the mean over the launches of one ncu
 # capture of the current kernel code (profiles/rt617_stage_kernels_launches.md); a kernel without a
 # capture of its current code gets None
-NCU_TRAFFIC = {("rt617", "s2", True): 2658624.0, ("rt617", "s2", False): 3398656.0}
+NCU_TRAFFIC = {("rt617", "s2", True): 2657900.0, ("rt617", "s2", False): 3395968.0}
 FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
 
 
