@@ -82,7 +82,7 @@ def _load():
         "qg_layout": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "qg_set_stream": (C.c_int, [vp, vp]),
         "qg_eval_grad": (C.c_int, [vp, vp, vp, vp]),
-        "qg_eval_grad_host": (C.c_int, [vp, _F64P, _F64P, _F64P]),
+        "qg_eval_grad_host": (C.c_int, [vp, vp, vp, vp]),
         "qg_eval_grad_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "qg_adam_step": (C.c_int, [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double]),
         "qg_solve": (C.c_int, [vp, vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp]),
@@ -256,11 +256,16 @@ def qg_eval_grad_noalloc(h: int, x, obj, g) -> None:
     _check(_lib.qg_eval_grad_noalloc(h, _ptr(x), _ptr(obj), _ptr(g)), h)
 
 
+def _host_addr(a: np.ndarray) -> int:
+    """Address of a contiguous float64 host array (the cheapest route; this call sits in the
+    end-to-end loop)."""
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise ValueError("host buffers must be contiguous float64 arrays")
+    return a.__array_interface__["data"][0]
+
+
 def qg_eval_grad_host(h: int, x: np.ndarray, obj: np.ndarray, g: Optional[np.ndarray] = None) -> None:
-    for a in (x, obj) + ((g,) if g is not None else ()):
-        assert a.dtype == np.float64 and a.flags.c_contiguous
-    _check(_lib.qg_eval_grad_host(h, x.ctypes.data_as(_F64P), obj.ctypes.data_as(_F64P),
-                                  g.ctypes.data_as(_F64P) if g is not None else None), h)
+    _check(_lib.qg_eval_grad_host(h, _host_addr(x), _host_addr(obj), _host_addr(g) if g is not None else None), h)
 
 
 def qg_adam_step(h: int, x, m, v, lr: float, beta1: float = 0.9, beta2: float = 0.999) -> None:
