@@ -180,6 +180,43 @@ def test_device_model_case_reaches_device_check(qg):
         _expect(qg, c, qg.QG_ERR_NO_DEVICE, dc_solver=dc)
 
 
+def _star(leaves):
+    """A hub bus joined to `leaves` buses, the generator on the first leaf: the hub's balance and
+    adjoint rows hold one entry per incident branch end."""
+    c = synth.tiny()
+    n = leaves + 1
+    M = leaves
+    return dataclasses.replace(
+        c, name="star", n_bus=n, n_branch=M, br_from=np.zeros(M, np.int32), br_to=np.arange(1, n, dtype=np.int32),
+        br_r=np.full(M, 0.01), br_x=np.full(M, 0.1), br_b=np.zeros(M), s_max=np.ones(M), s_max_ctg=np.ones(M),
+        n_gen=1, gen_bus=np.array([1], np.int32), gen_zone=np.array([0], np.int32), cost_a=np.ones(1),
+        cost_b=np.ones(1), cost_r=np.ones(1), pmin=np.zeros(1), pmax=np.full(1, 9.0), qmin=-np.ones(1),
+        qmax=np.ones(1), ramp=np.ones(1), vmin=np.full(n, 0.9), vmax=np.full(n, 1.1),
+        load_p=np.full((c.T, n), 0.01), load_q=np.zeros((c.T, n)), bus_zone=np.zeros(n, np.int32),
+        ctg=np.zeros(0, np.int32))
+
+
+def test_bus_incidence_limit(qg):
+    """A bus's balance and adjoint rows are reduced by one warp: more than 32 incident entries is a
+    size this build rejects (before any device work)."""
+    msg = _expect(qg, _star(33), qg.QG_ERR_UNSUPPORTED)
+    assert "more than 32" in msg
+
+
+@pytest.mark.skipif(_gpu_present(), reason="checks the no-device path")
+def test_limit_and_degenerate_inputs_reach_device_check(qg):
+    """32 entries at a bus, 64 bid blocks per device, no outages (K = 0), a single period and the
+    two-bus grid pass validation and the whole host set-up."""
+    c = synth.tiny()
+    cases = [_star(32), synth.with_block_bids(c, 64, 0.3, 5), dataclasses.replace(c, ctg=np.zeros(0, np.int32)),
+             dataclasses.replace(c, T=1, dt=c.dt[:1], load_p=c.load_p[:1], load_q=c.load_q[:1],
+                                 reserve_req=c.reserve_req[:1]),
+             dataclasses.replace(_star(1), gen_bus=np.array([0], np.int32))]
+    for case in cases:
+        for dc in (qg.QG_DC_DENSE, qg.QG_DC_SPARSE):
+            _expect(qg, case, qg.QG_ERR_NO_DEVICE, dc_solver=dc)
+
+
 @pytest.mark.parametrize("iters", [1, 2, 7, 500])
 def test_library_schedule_matches_the_closed_forms(qg, iters):
     """qg_schedule (host code of the library) against Eqs. norm_t, mag_scale and step_size as the
