@@ -38,9 +38,11 @@ extern "C" {
 #define QG_ERR_INVALID_ARG (-1)   /* a size, index, pointer or parameter is out of range      */
 #define QG_ERR_ISLANDING (-2)     /* an outage disconnects the grid (1 - PTDF_kk ~ 0)          */
 #define QG_ERR_CUDA (-3)          /* a CUDA runtime call failed (message has the CUDA error)   */
-#define QG_ERR_NOT_CONVERGED (-4) /* an iterative solve hit its iteration cap                  */
-#define QG_ERR_TIMEOUT (-5)       /* a device-side wait ran out of its cycle budget            */
-#define QG_ERR_NONFINITE (-6)     /* NaN/Inf found in x or in the objective                    */
+#define QG_ERR_NOT_CONVERGED (-4) /* reserved: no call of this build returns it (the DC solves
+                                   * are direct, nothing iterates to a tolerance)              */
+#define QG_ERR_TIMEOUT (-5)       /* reserved: no call of this build returns it (no kernel
+                                   * waits on another block or launch)                         */
+#define QG_ERR_NONFINITE (-6)     /* qg_eval_grad_host: an objective came back NaN or Inf      */
 #define QG_ERR_NO_DEVICE (-7)     /* no CUDA device, or not an sm_103 device                   */
 #define QG_ERR_UNSUPPORTED (-8)   /* a valid request this build does not implement             */
 
@@ -200,7 +202,9 @@ int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g);
  * evaluates, and copies obj (n_inst doubles) and g (qg_num_vars doubles, may be
  * NULL) back; synchronizes.  In QG_MIXED mode the copies convert to/from float.
  * With page-locked buffers the copies and the evaluation replay from a graph
- * cached for those buffers (re-captured when they change). */
+ * cached for those buffers (re-captured when they change).  Returns
+ * QG_ERR_NONFINITE when an instance's objective is NaN or Inf (x holds one, or
+ * a term overflowed); obj and g are written as computed all the same. */
 int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g);
 
 /* One projected Adam step (Alg. 3) on every variable, using the gradient of the

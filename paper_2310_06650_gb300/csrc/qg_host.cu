@@ -1593,6 +1593,12 @@ int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   CUDA_TRY(h, cudaGetLastError());
+  // the objective is on the host now: a NaN or Inf (from x or from an overflow) is reported, with
+  // every output written as computed
+  if (obj)
+    for (int b = 0; b < h->n_inst; ++b)
+      if (!std::isfinite(obj[b]))
+        return fail(h, QG_ERR_NONFINITE, "instance " + std::to_string(b) + ": the objective is not finite");
   return QG_OK;
 }
 
@@ -1990,6 +1996,6 @@ int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]) {
   return QG_OK;
 }
 
-int qg_version(void) { return 301; }
+int qg_version(void) { return 302; }
 
 }  // extern "C"

@@ -171,6 +171,26 @@ def test_host_entry_with_pinned_buffers_replays_a_graph(qg):
         s.close()
 
 
+def test_host_entry_reports_a_nonfinite_objective(qg):
+    """A NaN in x makes the objective NaN: the host entry writes its outputs, returns
+    QG_ERR_NONFINITE, and the handle evaluates the next finite point normally."""
+    c = case_named("tiny")
+    for prec in (qg.QG_FP64, qg.QG_MIXED):
+        s = qg.Solver(c, precision=prec)
+        x = point(c, "1")
+        bad = x.copy()
+        bad[c.offsets()[0] + 3] = np.nan
+        obj, g = np.zeros(1), np.zeros(c.n_x)
+        with pytest.raises(qg.QGError) as ei:
+            qg.qg_eval_grad_host(s.h, bad, obj, g)
+        assert ei.value.code == qg.QG_ERR_NONFINITE and "not finite" in str(ei.value)
+        assert np.isnan(obj[0])
+        qg.qg_eval_grad_host(s.h, x, obj, g)
+        ref = oracle.evaluate(c, x if prec == qg.QG_FP64 else as_f32(x))
+        assert rel(obj[0], ref.obj) <= (TOL64 if prec == qg.QG_FP64 else TOL32)
+        s.close()
+
+
 def test_adam_step_parity(qg):
     c = case_named("mid")
     x = point(c, "lp_perturbed")
