@@ -16,8 +16,12 @@
  *  - Device arrays are contiguous; their element type is double in QG_FP64
  *    mode and float in QG_MIXED mode (obj is always double).
  *  - All device work is ordered on the stream set by qg_set_stream (default:
- *    the legacy default stream); no call synchronizes the device except
- *    qg_create*, qg_eval_grad_host, qg_breakdown and qg_get_state.
+ *    the legacy default stream).  The calls that return host data or re-plan
+ *    wait for that stream: qg_eval_grad_host, qg_breakdown, qg_get_step,
+ *    qg_set_step, qg_phase_times, qg_ctg_select, qg_ctg_scores, qg_autotune
+ *    and qg_round_batch; qg_create*, qg_destroy and the MLP set-up and
+ *    destroy calls wait for the device.
+ *    Every other call only enqueues work.
  *  - Variable layout of one instance (qg_layout): period-major blocks
  *        x = [ v (T x n) | theta (T x n) | p (T x G) | q (T x G) | r (T x G)
  *              | tau (T x X) | phi (T x X) | u (T x G) ]
