@@ -155,7 +155,9 @@ void qg_default_options(qg_options *opt);
  * the line-outage block L[m,k] = PTDF_mk / (1 - PTDF_kk) of the rank-1 (SMW)
  * correction (Eq. rank_correct, in flow space) with the denominators in FP64,
  * and uploads everything to the current CUDA device.  Returns
- * QG_ERR_ISLANDING if an outage has |1 - PTDF_kk| < 1e-9. */
+ * QG_ERR_ISLANDING if an outage has |1 - PTDF_kk| < 1e-9, and QG_ERR_INVALID_ARG
+ * for an instance whose T (2n + 4G + 2X), T M, T Z or G n_blk reaches 2^31
+ * (per-instance element counts are indexed in 32 bits). */
 int qg_create(qg_ctx **out, const qg_network *net, const qg_horizon *hor, const qg_contingencies *ctg,
               const qg_options *opt);
 

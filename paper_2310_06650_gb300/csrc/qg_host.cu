@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -168,6 +169,13 @@ int read_instance(qg_ctx *h, const qg_network &N, const qg_horizon &H, const qg_
   auto bad = [&](const std::string &m) { return fail(h, QG_ERR_INVALID_ARG, "instance " + std::to_string(b) + ": " + m); };
   if (N.n_bus < 2 || N.n_branch < 1 || N.n_gen < 1 || N.n_zone < 1 || H.T < 1 || C.K < 0) return bad("sizes out of range");
   if (N.ref_bus < 0 || N.ref_bus >= N.n_bus) return bad("ref_bus out of range");
+  {  // per-instance element counts index 32-bit: checked before any array is read
+    const long long T = H.T, xf = std::max(N.n_xf, 0), blk = std::max(N.n_blk, 0);
+    const long long n_x = T * (2LL * N.n_bus + 4LL * N.n_gen + 2 * xf);  // with an on-status block
+    if (n_x > INT32_MAX || T * N.n_branch > INT32_MAX || T * N.n_zone > INT32_MAX ||
+        (long long)N.n_gen * blk > INT32_MAX)
+      return bad("sizes too large: T (2n + 4G + 2X), T M, T Z and G n_blk must stay below 2^31");
+  }
   if (!N.br_from || !N.br_to || !N.br_r || !N.br_x || !N.br_b || !N.s_max || !N.s_max_ctg || !N.gen_bus ||
       !N.gen_zone || !N.cost_a || !N.cost_b || !N.cost_r || !N.pmin || !N.pmax || !N.qmin || !N.qmax || !N.ramp ||
       !N.vmin || !N.vmax || !H.dt || !H.load_p || !H.load_q || !H.reserve_req || (C.K > 0 && !C.branch))

@@ -196,6 +196,15 @@ def _star(leaves):
         ctg=np.zeros(0, np.int32))
 
 
+def test_sizes_beyond_32_bit_indices_are_rejected(qg):
+    """Per-instance counts are indexed in 32 bits: a horizon that would take an instance's variable
+    count past 2^31 is refused from the sizes alone, before any array is read (the arrays here keep
+    their small shapes, so reading them would run past their ends)."""
+    c = synth.tiny()
+    msg = _expect(qg, dataclasses.replace(c, T=2 ** 26), qg.QG_ERR_INVALID_ARG)
+    assert "sizes too large" in msg
+
+
 def test_bus_incidence_limit(qg):
     """A bus's balance and adjoint rows are reduced by one warp: more than 32 incident entries is a
     size this build rejects (before any device work)."""
