@@ -143,3 +143,15 @@ def test_reductions_to_the_copper_plate_bound():
     loose = dataclasses.replace(c, s_max_ctg=np.full(c.n_branch, 1e3))
     bl, _, _, nl = contingency_bound(loose)
     assert nl == 0 and bl == pytest.approx(cp, rel=1e-9)
+
+
+def test_bound_on_a_meshed_73_bus_grid():
+    """On the 73-bus grid the contingency overloads are avoidable at little cost: the bound stays
+    valid and lies just above the copper-plate bound."""
+    c = synth.mid()
+    cp, pc, rc = copper_plate(c)
+    b, p, r, nS = contingency_bound(c)
+    assert nS > 0 and cp * (1 - 1e-12) <= b <= 1.05 * cp
+    lo, hi = oracle.box(c)
+    for xp in [c.flat_start(pc, rc), c.flat_start(p, r)] + [synth.random_point(c, s) for s in range(3)]:
+        assert oracle.evaluate(c, np.clip(xp, lo, hi), eps=0.0, want_grad=False).obj >= b * (1 - 1e-12)
