@@ -162,7 +162,8 @@ int qg_create(qg_ctx **out, const qg_network *net, const qg_horizon *hor, const 
               const qg_options *opt);
 
 /* Same for n_inst independent instances (arrays of n_inst structs) evaluated
- * together by every later call; instance sizes may differ. */
+ * together by every later call; instance sizes may differ.  1 <= n_inst <= 32
+ * (QG_ERR_UNSUPPORTED above: the instance table travels as a kernel parameter). */
 int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const qg_horizon *hor,
                     const qg_contingencies *ctg, const qg_options *opt);
 

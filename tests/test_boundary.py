@@ -205,6 +205,18 @@ def test_sizes_beyond_32_bit_indices_are_rejected(qg):
     assert "sizes too large" in msg
 
 
+def test_instance_count_limit(qg):
+    c = synth.tiny()
+    with pytest.raises(qg.QGError) as ei:
+        qg.qg_create_batch([c] * 33, qg.case_options(c))
+    assert ei.value.code == qg.QG_ERR_UNSUPPORTED and "at most 32" in str(ei.value)
+    import ctypes
+    h = ctypes.c_void_p()
+    opt = qg.case_options(c)
+    assert qg._lib.qg_create_batch(ctypes.byref(h), 0, None, None, None, ctypes.byref(opt)) == qg.QG_ERR_INVALID_ARG
+    assert h.value is None
+
+
 def test_bus_incidence_limit(qg):
     """A bus's balance and adjoint rows are reduced by one warp: more than 32 incident entries is a
     size this build rejects (before any device work)."""
