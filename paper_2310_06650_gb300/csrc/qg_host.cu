@@ -563,6 +563,10 @@ std::vector<df32> to_dc<df32>(const std::vector<double> &v) {
   return o;
 }
 
+// A stage holds at most three spans per instance (stage 1: DC flows, branches, zones) plus one
+// for the sparse solver's adjoint right-hand side, so MAXB instances never overflow the table.
+static_assert(MAXSPAN >= 3 * MAXB + 1, "span table too small for MAXB instances");
+
 void add_span(Spans &S, int per_t, int nt, int inst, int role) {
   if (per_t <= 0 || nt <= 0) return;
   Span &s = S.s[S.n++];
