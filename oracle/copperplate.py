@@ -30,6 +30,13 @@ import scipy.sparse as sp
 from scipy.optimize import linprog
 
 
+def _require_plain_devices(case, what):
+    """Both LPs model producers with quadratic costs only; the device models of Examples 2-4 would
+    need their own relaxations, so such cases are refused rather than bounded wrongly."""
+    if (np.size(case.blk_width) and np.any(np.asarray(case.blk_width) > 0)) or np.any(case.dev_cons) or case.commit:
+        raise ValueError(f"{what}: bid blocks, consumers and on-status are not modelled")
+
+
 def _base_lp(case):
     """Variables, bounds, linear cost and rows of the copper-plate LP (without the cost cuts).
 
@@ -124,6 +131,7 @@ def _cost_gap(case, idx, xs):
 
 def copper_plate(case, tol: float = 1e-9, max_rounds: int = 60, init_cuts: int = 6):
     """Returns (bound, p [T, G], r [T, G])."""
+    _require_plain_devices(case, "copper_plate")
     T, G = case.T, case.n_gen
     nTG = T * G
     idx, nv, cost, lb, ub, base_rows = _base_lp(case)
@@ -186,6 +194,9 @@ def contingency_bound(case, tol: float = 1e-9, max_rounds: int = 80, init_cuts: 
     value is then within that margin of the relaxation's minimum.  The model is exact in p: F is
     the method's own DC contingency flow.
     Returns (bound, p [T, G], r [T, G], number of triples in S)."""
+    _require_plain_devices(case, "contingency_bound")
+    if len(case.xf_branch):
+        raise ValueError("contingency_bound: phase shifters add flow terms the maps leave out")
     T, G = case.T, case.n_gen
     nTG = T * G
     ctg = np.asarray(case.ctg)

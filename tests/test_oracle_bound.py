@@ -155,3 +155,14 @@ def test_bound_on_a_meshed_73_bus_grid():
     lo, hi = oracle.box(c)
     for xp in [c.flat_start(pc, rc), c.flat_start(p, r)] + [synth.random_point(c, s) for s in range(3)]:
         assert oracle.evaluate(c, np.clip(xp, lo, hi), eps=0.0, want_grad=False).obj >= b * (1 - 1e-12)
+
+
+def test_device_models_and_phase_shifters_are_refused():
+    c = synth.tiny()
+    for bad in (synth.with_block_bids(c, 3, 0.3, 1), synth.with_commitment(c, seed=1)):
+        with pytest.raises(ValueError):
+            copper_plate(bad)
+        with pytest.raises(ValueError):
+            contingency_bound(bad)
+    with pytest.raises(ValueError):
+        contingency_bound(synth.with_transformers(c, 0.3, 4))
