@@ -18,8 +18,9 @@
  *  - All device work is ordered on the stream set by qg_set_stream (default:
  *    the legacy default stream).  The calls that return host data or re-plan
  *    wait for that stream: qg_eval_grad_host, qg_breakdown, qg_get_step,
- *    qg_set_step, qg_phase_times, qg_ctg_select, qg_ctg_scores, qg_autotune
- *    and qg_round_batch; qg_create*, qg_destroy and the MLP set-up and
+ *    qg_set_step, qg_get_state, qg_set_state, qg_phase_times,
+ *    qg_ctg_select, qg_ctg_scores, qg_autotune and qg_round_batch;
+ *    qg_create*, qg_destroy and the MLP set-up and
  *    destroy calls wait for the device.
  *    Every other call only enqueues work.
  *  - Variable layout of one instance (qg_layout): period-major blocks
@@ -196,9 +197,12 @@ int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g);
  * qg_num_vars elements, required).  Results equal those of qg_eval_grad.
  *  - Handles whose work buffers need more than 16 MiB (e.g. large batches) are rejected with
  *    QG_ERR_UNSUPPORTED and a message giving the size needed; so are handles on the sparse DC
- *    solver (QG_DC_SPARSE), whose solve buffers are not carved from the array.
+ *    solver (QG_DC_SPARSE), whose solve buffers are not carved from the array, and handles with
+ *    contingency screening (0 < ctg_frac < 1), whose compacted line-outage block is not either.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- *    that first call before any stream capture on that device.
+ *    that first call before any stream capture on that device.  The address is kept per device
+ *    ordinal for the device's primary context (the one the CUDA runtime uses): it does not follow
+ *    a cudaDeviceReset, after which this library's handles are not valid anyway.
  *  - All calls share the one array, which keeps the last call's contents: calls that overlap on
  *    the GPU (other streams, other handles, other threads) race and must be serialized by the
  *    caller.
@@ -268,6 +272,28 @@ int qg_breakdown(qg_ctx *h, double *out);
  * qg_set_step(h, 0) also zeroes the moments that qg_solve keeps in the handle. */
 int qg_get_step(qg_ctx *h, int64_t *step);
 int qg_set_step(qg_ctx *h, int64_t step);
+
+/* Checkpoint and resume of a solve.  Alg. 3's iteration carries (x, m, v, i); a run on the
+ * schedules of Sec. II-F also carries its position in the schedule, contingency screening (Alg. 2)
+ * the current outage selection of every instance, and batch rounding (Alg. 1) the fixed pairs and
+ * the clip box they pinned.  x belongs to the caller; everything else is in the handle and travels
+ * in one opaque state blob:
+ *   header (magic "QGS1", version, precision, n_inst, qg_num_vars, step counter i, step count at the
+ *   start of the current scheduled run), the moments m and v that qg_solve / qg_solve_schedule keep
+ *   in the handle (qg_num_vars elements each, float in QG_MIXED, double in QG_FP64), then, when the
+ *   handle screens contingencies, the selection of every instance (int32), and, once qg_round_batch
+ *   has run, the fixed flags of the (period, device) pairs and the current clip box.
+ * qg_state_size returns the blob's size in bytes now (it grows once rounding starts), or a negative
+ * error code.  qg_get_state writes it to buf (host memory, size bytes; QG_ERR_INVALID_ARG if size
+ * is too small).  qg_set_state restores a blob written by a handle created from the same inputs and
+ * options (QG_ERR_INVALID_ARG when the header does not match this handle: precision, instance
+ * count, variable count, selection sizes).  A run continued from a restored blob with the restored
+ * x produces bitwise the iterates of the uninterrupted run (same kernels, same order).
+ * qg_get_state and qg_set_state wait for the handle's stream; qg_set_state may allocate the
+ * rounding buffers, and a blob written before any rounding round unfixes every pair. */
+int64_t qg_state_size(qg_ctx *h);
+int qg_get_state(qg_ctx *h, void *buf, int64_t size);
+int qg_set_state(qg_ctx *h, const void *buf, int64_t size);
 
 /* Per-kernel timing (CUDA events, no profiler): when on, every evaluation and
  * Adam step records an event after each stage, also inside qg_solve's graph.

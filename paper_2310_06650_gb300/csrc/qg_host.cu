@@ -764,6 +764,30 @@ int gather_lodf(qg_ctx *h, const Dev<Real, Dc> &d, int b) {
   return QG_OK;
 }
 
+// Make instance b's current selection (hi[b].sel) the outages later evaluations cover: the
+// outage index of every branch, the outaged branch of every selected column and the compacted
+// line-outage block(s).  Synchronizes the stream.
+int upload_selection(qg_ctx *h, int b) {
+  const HostInst &H = h->hi[b];
+  const Inst &I = h->plan.tab.I[b];
+  const int n = (int)H.sel.size();
+  std::vector<int> kidx(H.M, -1), cbr(n);
+  for (int j = 0; j < n; ++j) {
+    kidx[H.ctg[H.sel[j]]] = j;
+    cbr[j] = H.ctg[H.sel[j]];
+  }
+  const bool mx = h->opt.precision == QG_MIXED;
+  const int *d_kidx = mx ? h->d32.br_kidx : h->d64.br_kidx;
+  const int *d_cbr = mx ? h->d32.ctg_br : h->d64.ctg_br;
+  CUDA_TRY(h, cudaMemcpyAsync(const_cast<int *>(d_kidx) + I.br0, kidx.data(), sizeof(int) * H.M, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(const_cast<int *>(d_cbr) + I.ctg0, cbr.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_sel + I.ctg0, H.sel.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  const int rc = mx ? gather_lodf(h, h->d32, b) : gather_lodf(h, h->d64, b);
+  if (rc) return rc;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // the host vectors above are freed on return
+  return QG_OK;
+}
+
 // Build every device array of one precision flavour.
 template <typename Real, typename Dc>
 int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) {
@@ -902,12 +926,19 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   UPI(gb_gen, gb_gen) UPI(zgen_ptr, zgen_ptr) UPI(zgen, zgen) UPI(ctg_br, ctg_br) UPI(bal_code, bal_code)
   UPI(bal_row, bal_row) UPI(adj_code, adj_code) UPI(adj_row, adj_row) UPI(br_xf, br_xf) UPI(xf_br, xf_br)
   UPR(br_g, br_g) UPR(br_b, br_b) UPR(br_hch, br_hch) UPR(br_smax, br_smax) UPR(br_s2ctg, br_s2)
-  UPR(gen_a, ga) UPR(gen_b, gbv) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax) UPR(gen_ramp, gramp)
+  UPR(gen_a, ga) UPR(gen_b, gbv) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax)
   UPR(gen_sgn, gsgn) UPR(gen_pmin, gpmin) UPR(gen_qmin, gqmin) UPR(gen_qmax, gqmax) UPR(gen_con, gcon)
   UPR(gen_csu, gcsu) UPR(gen_csd, gcsd) UPR(gen_uinit, guinit) UPI(blk_ptr, blk_ptr) UPR(blk_c, blk_c)
   UPR(blk_lo, blk_lo) UPR(blk_w, blk_w)
-  UPR(load_p, load_p) UPR(load_q, load_q) UPR(rreq, rreq) UPR(dt, dt) UPR(lo, lo) UPR(hi, hi)
+  UPR(load_p, load_p) UPR(load_q, load_q) UPR(dt, dt) UPR(lo, lo) UPR(hi, hi)
   UPD(ltot, ltot) UPD(ptdfg, ptdfg) UPD(ptdfgT, ptdfgT) UPD(cload, cload) UPD(rsum, rsum)
+  {
+    double *q64;
+#define UP64(field, vec) if ((rc = upload(h, &q64, vec))) return rc; d.field = q64;
+    UP64(lim_pmax, gpmax) UP64(lim_pmin, gpmin) UP64(lim_qmin, gqmin) UP64(lim_qmax, gqmax) UP64(lim_ramp, gramp)
+    UP64(lim_rreq, rreq) UP64(lim_dt, dt)
+#undef UP64
+  }
 #undef UPI
 #undef UPR
 #undef UPD
@@ -1751,6 +1782,175 @@ int qg_set_step(qg_ctx *h, int64_t step) {
   return QG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Solver state blob (qg_get_state / qg_set_state): a fixed header, then the sections below, each
+// starting on an 8-byte boundary.
+constexpr uint32_t STATE_MAGIC = 0x31534751u;  // "QGS1" in little-endian byte order
+constexpr uint32_t STATE_VERSION = 1;
+constexpr int32_t STATE_SEL = 1, STATE_ROUND = 2;
+
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t precision, n_inst;
+  int64_t n_x;
+  int64_t step, step0;  // Adam step counter; its value at the start of the current scheduled run
+  int32_t flags;        // STATE_SEL: selections follow the moments; STATE_ROUND: rounding state follows
+  int32_t n_sel;        // selected outages over all instances
+  int64_t n_pairs;      // (period, device) pairs of the rounding flags
+};
+
+size_t pad8(size_t b) { return (b + 7) & ~size_t(7); }
+
+template <typename Real, typename Dc>
+int round_alloc(qg_ctx *h, Dev<Real, Dc> &d);
+
+// The header this handle would write now, and the blob's size.
+size_t state_layout(const qg_ctx *h, StateHeader *hd) {
+  StateHeader H{};
+  H.magic = STATE_MAGIC;
+  H.version = STATE_VERSION;
+  H.precision = h->opt.precision;
+  H.n_inst = h->n_inst;
+  H.n_x = h->n_x;
+  H.flags = (h->screen ? STATE_SEL : 0) | (h->d_fixed ? STATE_ROUND : 0);
+  for (const HostInst &I : h->hi) H.n_sel += h->screen ? (int32_t)I.sel.size() : 0;
+  H.n_pairs = h->d_fixed ? (int64_t)h->fixed.size() : 0;
+  if (hd) *hd = H;
+  const size_t rs = h->opt.precision == QG_MIXED ? sizeof(float) : sizeof(double);
+  size_t n = pad8(sizeof(StateHeader)) + 2 * pad8(rs * h->n_x);
+  if (H.flags & STATE_SEL) n += pad8(sizeof(int32_t) * H.n_sel);
+  if (H.flags & STATE_ROUND) n += pad8((size_t)H.n_pairs) + 2 * pad8(rs * h->n_x);
+  return n;
+}
+
+template <typename Real, typename Dc>
+int set_state_dev(qg_ctx *h, Dev<Real, Dc> &d, const unsigned char *buf, int64_t size) {
+  StateHeader H;
+  std::memcpy(&H, buf, sizeof(H));
+  if (H.magic != STATE_MAGIC || H.version != STATE_VERSION)
+    return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: not a state blob of this library version");
+  StateHeader mine;
+  state_layout(h, &mine);
+  if (H.precision != mine.precision || H.n_inst != mine.n_inst || H.n_x != mine.n_x)
+    return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: the blob belongs to a handle of another precision or size");
+  if ((H.flags & STATE_SEL) != (mine.flags & STATE_SEL) || ((H.flags & STATE_SEL) && H.n_sel != mine.n_sel))
+    return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: contingency screening differs from this handle's");
+  if ((H.flags & STATE_ROUND) && H.n_pairs != (int64_t)d.n_pairs)
+    return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: rounding state of another device count");
+  if (H.step < 0 || H.step0 < 0 || H.step0 > H.step) return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: bad step counters");
+  const size_t rs = sizeof(Real), nx = (size_t)h->n_x;
+  size_t need = pad8(sizeof(StateHeader)) + 2 * pad8(rs * nx);
+  if (H.flags & STATE_SEL) need += pad8(sizeof(int32_t) * H.n_sel);
+  if (H.flags & STATE_ROUND) need += pad8((size_t)H.n_pairs) + 2 * pad8(rs * nx);
+  if ((size_t)size < need) return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: blob truncated");
+  size_t o = pad8(sizeof(StateHeader));
+  const unsigned char *m = buf + o;
+  o += pad8(rs * nx);
+  const unsigned char *v = buf + o;
+  o += pad8(rs * nx);
+  if (H.flags & STATE_SEL) {  // validate every selection before changing anything
+    const int32_t *sel = reinterpret_cast<const int32_t *>(buf + o);
+    long long j = 0;
+    for (const HostInst &I : h->hi) {
+      std::vector<char> seen(I.K, 0);
+      for (int k = 0; k < I.Ks; ++k, ++j) {
+        const int32_t id = sel[j];
+        if (id < 0 || id >= I.K || seen[id]) return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: bad outage selection");
+        seen[id] = 1;
+      }
+    }
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_m, m, rs * nx, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_v, v, rs * nx, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_step, &H.step, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_step0, &H.step0, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // H lives on this stack frame
+  if (H.flags & STATE_SEL) {
+    const int32_t *sel = reinterpret_cast<const int32_t *>(buf + o);
+    for (int b = 0; b < h->n_inst; ++b) {
+      HostInst &I = h->hi[b];
+      I.sel.assign(sel, sel + I.Ks);
+      sel += I.Ks;
+      const int rc = upload_selection(h, b);
+      if (rc) return rc;
+    }
+    o += pad8(sizeof(int32_t) * H.n_sel);
+  }
+  if (H.flags & STATE_ROUND) {
+    int rc = round_alloc(h, d);  // keeps this handle's own original box as the one to reset to
+    if (rc) return rc;
+    const unsigned char *fx = buf + o;
+    o += pad8((size_t)H.n_pairs);
+    h->fixed.assign(fx, fx + H.n_pairs);
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_fixed, h->fixed.data(), (size_t)H.n_pairs, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(const_cast<Real *>(d.lo), buf + o, rs * nx, cudaMemcpyHostToDevice, h->stream));
+    o += pad8(rs * nx);
+    CUDA_TRY(h, cudaMemcpyAsync(const_cast<Real *>(d.hi), buf + o, rs * nx, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  } else if (h->d_fixed) {
+    const int rc = qg_round_reset(h);  // the blob predates rounding: no pair is fixed
+    if (rc) return rc;
+  }
+  return QG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t qg_state_size(qg_ctx *h) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  return (int64_t)state_layout(h, nullptr);
+}
+
+int qg_get_state(qg_ctx *h, void *buf, int64_t size) {
+  if (!h || !buf) return h ? fail(h, QG_ERR_INVALID_ARG, "qg_get_state: null buffer") : QG_ERR_INVALID_ARG;
+  StateHeader H;
+  const size_t need = state_layout(h, &H);
+  if (size < 0 || (size_t)size < need)
+    return fail(h, QG_ERR_INVALID_ARG, "qg_get_state: the buffer needs " + std::to_string(need) + " bytes");
+  unsigned char *out = static_cast<unsigned char *>(buf);
+  std::memset(out, 0, need);
+  const size_t rs = mixed(h) ? sizeof(float) : sizeof(double), nx = (size_t)h->n_x;
+  size_t o = pad8(sizeof(StateHeader));
+  CUDA_TRY(h, cudaMemcpyAsync(out + o, h->d_m, rs * nx, cudaMemcpyDeviceToHost, h->stream));
+  o += pad8(rs * nx);
+  CUDA_TRY(h, cudaMemcpyAsync(out + o, h->d_v, rs * nx, cudaMemcpyDeviceToHost, h->stream));
+  o += pad8(rs * nx);
+  long long st[2] = {0, 0};
+  CUDA_TRY(h, cudaMemcpyAsync(&st[0], h->d_step, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(&st[1], h->d_step0, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  if (H.flags & STATE_SEL) {
+    int32_t *sel = reinterpret_cast<int32_t *>(out + o);
+    for (const HostInst &I : h->hi) sel = std::copy(I.sel.begin(), I.sel.end(), sel);
+    o += pad8(sizeof(int32_t) * H.n_sel);
+  }
+  if (H.flags & STATE_ROUND) {
+    std::copy(h->fixed.begin(), h->fixed.end(), out + o);
+    o += pad8((size_t)H.n_pairs);
+    const void *lo = mixed(h) ? (const void *)h->d32.lo : (const void *)h->d64.lo;
+    const void *hi = mixed(h) ? (const void *)h->d32.hi : (const void *)h->d64.hi;
+    CUDA_TRY(h, cudaMemcpyAsync(out + o, lo, rs * nx, cudaMemcpyDeviceToHost, h->stream));
+    o += pad8(rs * nx);
+    CUDA_TRY(h, cudaMemcpyAsync(out + o, hi, rs * nx, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  H.step = st[0];
+  H.step0 = st[1];
+  std::memcpy(out, &H, sizeof(H));
+  return QG_OK;
+}
+
+int qg_set_state(qg_ctx *h, const void *buf, int64_t size) {
+  if (!h || !buf) return h ? fail(h, QG_ERR_INVALID_ARG, "qg_set_state: null buffer") : QG_ERR_INVALID_ARG;
+  if (size < (int64_t)sizeof(StateHeader)) return fail(h, QG_ERR_INVALID_ARG, "qg_set_state: blob truncated");
+  const unsigned char *in = static_cast<const unsigned char *>(buf);
+  return mixed(h) ? set_state_dev(h, h->d32, in, size) : set_state_dev(h, h->d64, in, size);
+}
+
 int qg_set_profiling(qg_ctx *h, int on) {
   if (!h) return QG_ERR_INVALID_ARG;
   if (on && !h->ev[0])
@@ -1787,7 +1987,6 @@ int qg_ctg_select(qg_ctx *h, int32_t inst, const int32_t *ids, int32_t n) {
   if (!h->screen) return fail(h, QG_ERR_UNSUPPORTED, "qg_ctg_select: the handle has no contingency screening");
   if (inst < 0 || inst >= h->n_inst || !ids) return fail(h, QG_ERR_INVALID_ARG, "qg_ctg_select: bad instance or ids");
   HostInst &H = h->hi[inst];
-  const Inst &I = h->plan.tab.I[inst];
   if (n != H.Ks) return fail(h, QG_ERR_INVALID_ARG, "qg_ctg_select: n must equal the instance's Ks = " + std::to_string(H.Ks));
   std::vector<char> seen(H.K, 0);
   for (int j = 0; j < n; ++j) {
@@ -1795,21 +1994,7 @@ int qg_ctg_select(qg_ctx *h, int32_t inst, const int32_t *ids, int32_t n) {
     seen[ids[j]] = 1;
   }
   H.sel.assign(ids, ids + n);
-  std::vector<int> kidx(H.M, -1), cbr(n);
-  for (int j = 0; j < n; ++j) {
-    kidx[H.ctg[H.sel[j]]] = j;
-    cbr[j] = H.ctg[H.sel[j]];
-  }
-  const bool mx = mixed(h);
-  const int *d_kidx = mx ? h->d32.br_kidx : h->d64.br_kidx;
-  const int *d_cbr = mx ? h->d32.ctg_br : h->d64.ctg_br;
-  CUDA_TRY(h, cudaMemcpyAsync(const_cast<int *>(d_kidx) + I.br0, kidx.data(), sizeof(int) * H.M, cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(const_cast<int *>(d_cbr) + I.ctg0, cbr.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_sel + I.ctg0, H.sel.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
-  const int rc = mx ? gather_lodf(h, h->d32, inst) : gather_lodf(h, h->d64, inst);
-  if (rc) return rc;
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  return QG_OK;
+  return upload_selection(h, inst);
 }
 
 int qg_ctg_scores(qg_ctx *h, double *z) {
@@ -1924,21 +2109,30 @@ int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t sh
 
 namespace {
 
+// Buffers of batch rounding, allocated on first use: fixed flags, distances, projections, the
+// index list, and a copy of the original clip box (taken now, before any pair is fixed).
+template <typename Real, typename Dc>
+int round_alloc(qg_ctx *h, Dev<Real, Dc> &d) {
+  if (h->d_fixed) return QG_OK;
+  const long long sTG = d.n_pairs;
+  int rc;
+  if ((rc = dalloc(h, &h->d_fixed, (size_t)sTG)) || (rc = dalloc(h, &h->d_dist, (size_t)sTG)) ||
+      (rc = dalloc(h, (Real **)&h->d_proj, (size_t)(4 * sTG))) || (rc = dalloc(h, &h->d_idx, (size_t)sTG)) ||
+      (rc = dalloc(h, (Real **)&h->d_lo0, (size_t)h->n_x)) || (rc = dalloc(h, (Real **)&h->d_hi0, (size_t)h->n_x)))
+    return rc;
+  CUDA_TRY(h, cudaMemcpy(h->d_lo0, d.lo, sizeof(Real) * h->n_x, cudaMemcpyDeviceToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_hi0, d.hi, sizeof(Real) * h->n_x, cudaMemcpyDeviceToDevice));
+  h->fixed.assign((size_t)sTG, 0);
+  return QG_OK;
+}
+
 // One round of batch rounding on the device data of precision Real.
 template <typename Real, typename Dc>
 int round_batch_dev(qg_ctx *h, Dev<Real, Dc> &d, void *xv, double frac, int64_t *n_fixed, int64_t *n_bin) {
   Real *x = static_cast<Real *>(xv);
   const long long sTG = d.n_pairs;
   int rc;
-  if (!h->d_fixed) {
-    if ((rc = dalloc(h, &h->d_fixed, (size_t)sTG)) || (rc = dalloc(h, &h->d_dist, (size_t)sTG)) ||
-        (rc = dalloc(h, (Real **)&h->d_proj, (size_t)(4 * sTG))) || (rc = dalloc(h, &h->d_idx, (size_t)sTG)) ||
-        (rc = dalloc(h, (Real **)&h->d_lo0, (size_t)h->n_x)) || (rc = dalloc(h, (Real **)&h->d_hi0, (size_t)h->n_x)))
-      return rc;
-    CUDA_TRY(h, cudaMemcpy(h->d_lo0, d.lo, sizeof(Real) * h->n_x, cudaMemcpyDeviceToDevice));
-    CUDA_TRY(h, cudaMemcpy(h->d_hi0, d.hi, sizeof(Real) * h->n_x, cudaMemcpyDeviceToDevice));
-    h->fixed.assign((size_t)sTG, 0);
-  }
+  if ((rc = round_alloc(h, d))) return rc;
   for (int b = 0; b < h->n_inst; ++b) {
     const Inst &I = h->plan.tab.I[b];
     if (!I.uc) continue;

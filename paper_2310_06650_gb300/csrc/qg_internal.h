@@ -100,10 +100,17 @@ struct Dev {
   const int *br_kidx;                 // [sum M] outage index of the branch within its instance, -1 if none
   const Real *br_g, *br_b, *br_hch, *br_smax, *br_s2ctg;  // g_sr, b_sr, b_ch / 2, s_max, s_ctg^2
   const int *gen_bus, *gen_zone, *gen_gb;                 // local bus, local zone, local generator-bus index
-  const Real *gen_a, *gen_b, *gen_cr, *gen_pmax, *gen_ramp;
+  const Real *gen_a, *gen_b, *gen_cr, *gen_pmax;
   const Real *gen_sgn;                // +1 producer, -1 consumer (sign of p, q as supply)
   const Real *gen_pmin, *gen_qmin, *gen_qmax;             // limits scaled by u (commitment)
   const Real *gen_con, *gen_csu, *gen_csd, *gen_uinit;    // on / startup / shutdown cost, u before period 0
+  // FP64 copies of the limits the penalized linear constraints subtract (Eq. nlp_updated; Example 2's
+  // u-scaled limits) and of the zonal requirements: both paths form those residuals in FP64.  At a
+  // solution the constraints are active, so each residual cancels O(1) terms, and the soft-ReLU's
+  // derivative moves by 1/eps per unit of residual error.
+  const double *lim_pmax, *lim_pmin, *lim_qmin, *lim_qmax, *lim_ramp;  // [sum G]
+  const double *lim_rreq;             // [sum T Z]
+  const double *lim_dt;               // [sum T]
   const int *blk_ptr;                 // [sum G + 1] bid blocks of each device (Example 3); none: quadratic cost
   const Real *blk_c, *blk_lo, *blk_w; // block price, cumulative start P_{l-1}, width
   const int *gb_ptr, *gb_gen;         // generator bus -> generators: one CSR over the batch's generator buses
@@ -114,7 +121,6 @@ struct Dev {
   const int *bal_code, *bal_row;      // balance CSR packs: code = j<<2|kind (0 from-end, 1 to-end, 2 generator, 3 pad)
   const int *adj_code, *adj_row;      // branch-end CSR packs (kind 0 / 1 / 3)
   const Real *load_p, *load_q;        // [sum T n]
-  const Real *rreq;                   // [sum T Z]
   const Real *dt;                     // [sum T]
   const Dc *ltot;                     // [sum T] total load per period
   const Dc *load_dc;                  // [T n] active load in the DC product type (sparse mode)

@@ -364,31 +364,32 @@ __device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub,
 }
 
 // Zonal reserve shortfall of zone `sub` in period t: the block sums the zone's reserve
-// offers (fixed order), then sigma_s(R_zt - sum r) and its derivative.
+// offers (fixed order, FP64 in both paths), then sigma_s(R_zt - sum r) and its derivative.
 template <typename Real, typename Dc>
 __device__ void s1_zone(const Dev<Real, Dc> &d, const Inst &I, int t, int z, const Real *__restrict__ x,
                         Obj3<Dc> &acc, const HP<Real> hp) {
-  __shared__ Real red[NTHR / 32];
+  __shared__ double red[NTHR / 32];
   const int zg = I.zone0 + z;  // global zone id; zgen_ptr is one CSR over all zones of the batch
   const Real *r = x + I.x0 + 2LL * I.T * I.n + 2LL * I.T * I.G + (long long)t * I.G;
   const long long k = I.tz0 + (long long)t * I.Z + z;
-  Real req = 0, w = 0;
+  double req = 0;
+  Real w = 0;
   if (threadIdx.x == 0) {  // loaded ahead of the sum (no dependence on it)
-    req = d.rreq[k];
+    req = d.lim_rreq[k];
     w = d.dt[I.tp0 + t] * d.c_rz * hp.beta;
   }
   const int e0 = d.zgen_ptr[zg], e1 = d.zgen_ptr[zg + 1];
-  Real sr = 0;
-  for (int e = e0 + threadIdx.x; e < e1; e += NTHR) sr += r[d.zgen[e] - I.gen0];
+  double sr = 0;
+  for (int e = e0 + threadIdx.x; e < e1; e += NTHR) sr += (double)r[d.zgen[e] - I.gen0];
   sr = warp_sum(sr);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sr;
   __syncthreads();
   if (threadIdx.x == 0) {
-    Real tot = 0;
+    double tot = 0;
 #pragma unroll
     for (int q = 0; q < NTHR / 32; ++q) tot += red[q];
     Real val, der;
-    soft_relu(req - tot, hp.eps, val, der);
+    soft_relu(Real(req - tot), hp.eps, val, der);
     d.dZ[k] = w * der;
     acc.v[0] = DcOps<Dc>::from_real(w * val);
   }
@@ -627,8 +628,10 @@ __host__ __device__ constexpr int ctg_tch() { return 8; }
 // Thread (row quad rq, column quad cq) holds a 4 x 4 piece of the line-outage tile in registers;
 // per period it reads f, qmax2 - s_ctg^2 of its rows and f_k of its columns as three 128-bit
 // shared loads and screens its 16 elements in FP32 with two FMAs and a max each: an element can
-// only be overloaded if F^2 + qmax2 - s_ctg^2 > 0 (the FP64 path adds a 1e-4 s_ctg^2 margin and
-// recomputes candidates exactly from the FP64 block).  Pads and the outaged branch itself carry
+// only be overloaded if F^2 + qmax2 - s_ctg^2 > 0.  The FP64 path recomputes candidates exactly
+// from the FP64 block; its screen adds a margin derived from a bound on the FP32 errors, so every
+// element whose FP64 value is over the limit is a candidate (the bound is at the screen's margin
+// below).  Pads and the outaged branch itself carry
 // L = NaN, which the max ignores and every compare rejects.  Only warps with a candidate take
 // the exact path and write partial sums (the buffers are zeroed per chunk of periods): row sums
 // (dz/df_m, dz/dqmax2_m) by shuffles across the 16 column quads, flushed to the partials pm, pq
@@ -696,7 +699,9 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         f = d.f32[idx];
         q2 = d.qm2[idx];
         const Real s2 = d.br_s2ctg[I.br0 + m];
-        qs = F64 ? (float)(q2 - s2) + 1e-4f * (float)s2 : (float)(q2 - s2);
+        // FP64 path: q2 - s2 plus the part of the screen's margin that covers the roundings of q2 - s2
+        // (the part that covers F is added per period in the screen)
+        qs = F64 ? (float)((q2 - s2) + 0x1p-22 * (fabs(q2 - s2) + s2)) : (float)(q2 - s2);
         if (F64) f64 = d.fre[idx];
       }
       s_fm[tt * CT_BM + c] = f;
@@ -735,6 +740,14 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
       for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) stage_m(e);
     }
     __syncthreads();
+    // FP64 path: max_j |L[i][j]| of this thread's four columns, per row (a NaN column is ignored;
+    // a row of four NaN columns screens nothing)
+    float Lrow[4];
+    if (F64) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        Lrow[i] = fmaxf(fmaxf(fabsf(L[i][0]), fabsf(L[i][1])), fmaxf(fabsf(L[i][2]), fabsf(L[i][3])));
+    }
     for (int tc0 = 0; tc0 < TB; tc0 += TCH) {
       const int tn = min(TCH, TB - tc0);
       for (int tt = 0; tt < tn; ++tt) {
@@ -742,8 +755,21 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         const float4 fm4 = *reinterpret_cast<const float4 *>(s_fm + tl * CT_BM + rq * 4);
         const float4 qs4 = *reinterpret_cast<const float4 *>(s_qs + tl * CT_BM + rq * 4);
         const float4 fk4 = *reinterpret_cast<const float4 *>(s_fk + tl * CT_BK + cq * 4);
-        const float fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w}, qs[4] = {qs4.x, qs4.y, qs4.z, qs4.w};
+        const float fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w};
+        float qs[4] = {qs4.x, qs4.y, qs4.z, qs4.w};
         const float fk[4] = {fk4.x, fk4.y, fk4.z, fk4.w};
+        if (F64) {
+          // the rest of the screen's margin: the FP32 value of F = f_m + L f_k is off by at most
+          // 3.0001 u (|f_m| + |L||f_k|) (u = 2^-24; three roundings: L, f_k, f_m to FP32 and the fma),
+          // so |F32^2 - F^2| <= 6.0003 u A^2 with A <= Ahat = |f_m| + max|L| max|f_k| over the
+          // thread's columns; 2^-21 Ahat^2 = 8 u Ahat^2 covers it and the FP64 rounding of the exact test
+          const float fkq = fmaxf(fmaxf(fabsf(fk[0]), fabsf(fk[1])), fmaxf(fabsf(fk[2]), fabsf(fk[3])));
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float ah = __fmaf_rn(Lrow[i], fkq, fabsf(fm[i]));
+            qs[i] = __fadd_rn(qs[i], __fmul_rn(__fmul_rn(ah, ah), 0x1p-21f));
+          }
+        }
         float F[4][4];
         float mr[4];  // one max per row, combined as a tree: a short dependency chain
 #pragma unroll
@@ -754,17 +780,20 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
                         fmaxf(__fmaf_rn(F[i][2], F[i][2], qs[i]), __fmaf_rn(F[i][3], F[i][3], qs[i])));
         }
         const float mx = fmaxf(fmaxf(mr[0], mr[1]), fmaxf(mr[2], mr[3]));  // NaN operands are ignored
-        if (!__any_sync(0xffffffffu, mx > 0.f)) continue;
+        // a candidate: F^2 + qmax2 - s_ctg^2 > 0 (mixed path: its classification), or, on the FP64
+        // path, >= 0 with the margin (a positive exact sum cannot round to a negative one)
+        if (!__any_sync(0xffffffffu, F64 ? mx >= 0.f : mx > 0.f)) continue;
         // a (candidate) post-contingency overload in this warp
         const Real w = __ldg(d.dt + I.tp0 + t) * d.c_s * hp.beta;
         Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
-        if (mx > 0.f) {
+        if (F64 ? mx >= 0.f : mx > 0.f) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int mm = rq * 4 + i;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              if (!(__fmaf_rn(F[i][j], F[i][j], qs[i]) > 0.f)) continue;  // NaN (pad, outaged branch) fails too
+              const float y = __fmaf_rn(F[i][j], F[i][j], qs[i]);
+              if (!(F64 ? y >= 0.f : y > 0.f)) continue;  // NaN (pad, outaged branch) fails too
               const Real q2 = s_q2[tl * CT_BM + mm];
               Real Fx, Lx;
               if (F64) {
@@ -1222,7 +1251,8 @@ __device__ void final_reduce(const Dev<Real, Dc> &d, const InstTab &tab) {
 template <typename Real>
 struct GenIn {
   int bus, zn, gb, b0, b1;  // bus, zone, generator-bus index, bid blocks [b0, b1)
-  Real a, bl, cr, pmax, ramp, sg, p, q, r, u;
+  Real a, bl, cr, pmax, sg, p, q, r, u;
+  double pmax64, ramp64;  // limits of the headroom and ramp residuals (formed in FP64)
   long long kp, kq, kr, ku;
   Real am[4], av[4], lo[4], hi[4];  // Adam moments and box of p, q, r, u (fused Adam only)
 };
@@ -1240,7 +1270,8 @@ __device__ GenIn<Real> gen_load(const Dev<Real, Dc> &d, const Inst &I, int t, in
   g.bl = d.gen_b[gg];
   g.cr = d.gen_cr[gg];
   g.pmax = d.gen_pmax[gg];
-  g.ramp = d.gen_ramp[gg];
+  g.pmax64 = d.lim_pmax[gg];
+  g.ramp64 = d.lim_ramp[gg];
   g.sg = d.gen_sgn[gg];
   g.kp = I.x0 + 2LL * I.T * I.n + (long long)t * I.G + gl;
   g.kq = g.kp + (long long)I.T * I.G;
@@ -1305,7 +1336,9 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
   const HP<Real> hp = hparams(d);
   const Real wr = d.rho * hp.beta;
   Real val, der;
-  soft_relu(p + r - g.pmax * u, hp.eps, val, der);  // u = 1 without on-status variables
+  // residuals of the penalized linear constraints in FP64 (p, q, r, u are exact in it)
+  const double p64 = p, q64 = q, r64 = r, u64 = u;
+  soft_relu(Real(p64 + r64 - g.pmax64 * u64), hp.eps, val, der);  // u = 1 without on-status variables
   Real zh = wr * val;
   gp += wr * der;
   gr += wr * der;
@@ -1314,15 +1347,16 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
     const int gg = I.gen0 + gl;
     gu -= g.pmax * (wr * der);
     const Real pmin = d.gen_pmin[gg], qmin = d.gen_qmin[gg], qmax = d.gen_qmax[gg];
-    soft_relu(pmin * u - p, hp.eps, val, der);
+    const double pmin64 = d.lim_pmin[gg], qmin64 = d.lim_qmin[gg], qmax64 = d.lim_qmax[gg];
+    soft_relu(Real(pmin64 * u64 - p64), hp.eps, val, der);
     zh += wr * val;
     gp -= wr * der;
     gu += pmin * (wr * der);
-    soft_relu(q - qmax * u, hp.eps, val, der);
+    soft_relu(Real(q64 - qmax64 * u64), hp.eps, val, der);
     zh += wr * val;
     gq += wr * der;
     gu -= qmax * (wr * der);
-    soft_relu(qmin * u - q, hp.eps, val, der);
+    soft_relu(Real(qmin64 * u64 - q64), hp.eps, val, der);
     zh += wr * val;
     gq -= wr * der;
     gu += qmin * (wr * der);
@@ -1340,20 +1374,20 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
   acc.v[0] = DcOps<Dc>::from_real(cost);
   acc.v[1] = DcOps<Dc>::from_real(zh);
   if (t >= 1) {  // ramp terms of period t
-    const Real pp = ADAM ? d.pold[ko - G] : x[g.kp - G];
-    const Real lim = g.ramp * dt;
+    const double pp = ADAM ? d.pold[ko - G] : x[g.kp - G];
+    const double lim = g.ramp64 * d.lim_dt[I.tp0 + t];
     Real v1, d1, v2, d2;
-    soft_relu(p - pp - lim, hp.eps, v1, d1);
-    soft_relu(pp - p - lim, hp.eps, v2, d2);
+    soft_relu(Real(p64 - pp - lim), hp.eps, v1, d1);
+    soft_relu(Real(pp - p64 - lim), hp.eps, v2, d2);
     acc.v[2] = DcOps<Dc>::from_real(wr * (v1 + v2));
     gp += wr * (d1 - d2);
   }
   if (t + 1 < I.T) {  // ramp terms of period t + 1 that involve p_t
-    const Real pn = ADAM ? d.pold[ko + G] : x[g.kp + G];
-    const Real lim = g.ramp * d.dt[I.tp0 + t + 1];
+    const double pn = ADAM ? d.pold[ko + G] : x[g.kp + G];
+    const double lim = g.ramp64 * d.lim_dt[I.tp0 + t + 1];
     Real v1, d1, v2, d2;
-    soft_relu(pn - p - lim, hp.eps, v1, d1);
-    soft_relu(p - pn - lim, hp.eps, v2, d2);
+    soft_relu(Real(pn - p64 - lim), hp.eps, v1, d1);
+    soft_relu(Real(p64 - pn - lim), hp.eps, v2, d2);
     gp += wr * (d2 - d1);
   }
   if (ADAM) {

@@ -89,6 +89,9 @@ def _load():
         "qg_breakdown": (C.c_int, [vp, _F64P]),
         "qg_get_step": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "qg_set_step": (C.c_int, [vp, C.c_int64]),
+        "qg_state_size": (C.c_int64, [vp]),
+        "qg_get_state": (C.c_int, [vp, vp, C.c_int64]),
+        "qg_set_state": (C.c_int, [vp, vp, C.c_int64]),
         "qg_set_profiling": (C.c_int, [vp, C.c_int]),
         "qg_phase_times": (C.c_int, [vp, C.POINTER(C.c_float), C.c_int32]),
         "qg_last_error": (C.c_char_p, [vp]),
@@ -120,7 +123,7 @@ def _load():
 _lib = _load()
 EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", "qg_num_vars", "qg_layout",
             "qg_set_stream", "qg_eval_grad", "qg_eval_grad_host", "qg_eval_grad_noalloc", "qg_adam_step", "qg_solve", "qg_breakdown",
-            "qg_get_step", "qg_set_step", "qg_set_profiling", "qg_phase_times", "qg_launches_per_eval",
+            "qg_get_step", "qg_set_step", "qg_state_size", "qg_get_state", "qg_set_state", "qg_set_profiling", "qg_phase_times", "qg_launches_per_eval",
             "qg_solve_schedule", "qg_schedule", "qg_ctg_select", "qg_ctg_scores", "qg_autotune", "qg_tile_shape", "qg_round_batch", "qg_round_reset",
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
@@ -319,6 +322,26 @@ def qg_get_step(h: int) -> int:
 
 def qg_set_step(h: int, step: int) -> None:
     _check(_lib.qg_set_step(h, step), h)
+
+
+def qg_state_size(h: int) -> int:
+    n = int(_lib.qg_state_size(h))
+    if n < 0:
+        _check(n, h)
+    return n
+
+
+def qg_get_state(h: int) -> bytes:
+    """The handle's solver state (Adam moments, step counters, screening selections, rounding state)
+    as an opaque blob."""
+    buf = C.create_string_buffer(qg_state_size(h))
+    _check(_lib.qg_get_state(h, buf, len(buf)), h)
+    return buf.raw
+
+
+def qg_set_state(h: int, blob: bytes) -> None:
+    buf = C.create_string_buffer(bytes(blob), len(blob))
+    _check(_lib.qg_set_state(h, buf, len(blob)), h)
 
 
 def qg_set_profiling(h: int, on: bool) -> None:

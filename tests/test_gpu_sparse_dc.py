@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import synth
+from gradcheck import check_at, check_grad
 from oracle.copperplate import lambda_dispatch
 
 pytestmark = pytest.mark.gpu
@@ -75,10 +76,10 @@ def gpu_eval(qg, case, x, precision, **kw):
     return out
 
 
-def check(res, ref, tol, skip_terms=()):
+def check(res, ref, tol, case, skip_terms=()):
     obj, g, terms = res
     assert rel(obj[0], ref.obj) <= tol, (obj[0], ref.obj)
-    assert grel(g, ref.grad) <= tol, grel(g, ref.grad)
+    check_at(g, ref.grad, case, tol)
     for k, name in enumerate(oracle.TERM_NAMES):
         if name in skip_terms:
             continue
@@ -89,14 +90,14 @@ def check(res, ref, tol, skip_terms=()):
 def test_sparse_fp64_parity(qg, name):
     c = case_named(name)
     x = start(c)
-    check(gpu_eval(qg, c, x, qg.QG_FP64, dc_solver=qg.QG_DC_SPARSE), oracle.evaluate(c, x), TOL64)
+    check(gpu_eval(qg, c, x, qg.QG_FP64, dc_solver=qg.QG_DC_SPARSE), oracle.evaluate(c, x), TOL64, c)
 
 
 @pytest.mark.parametrize("name", ["mid", "rt617", "b1576", "t70"])
 def test_sparse_mixed_parity(qg, name):
     c = case_named(name)
     x = as_f32(start(c))
-    check(gpu_eval(qg, c, x, qg.QG_MIXED, dc_solver=qg.QG_DC_SPARSE), oracle.evaluate(c, x), TOL32)
+    check(gpu_eval(qg, c, x, qg.QG_MIXED, dc_solver=qg.QG_DC_SPARSE), oracle.evaluate(c, x), TOL32, c)
 
 
 def test_sparse_and_dense_solvers_agree(qg):
@@ -106,7 +107,7 @@ def test_sparse_and_dense_solvers_agree(qg):
     od, gd, td = gpu_eval(qg, c, x, qg.QG_FP64, dc_solver=qg.QG_DC_DENSE)
     osp, gsp, tsp = gpu_eval(qg, c, x, qg.QG_FP64, dc_solver=qg.QG_DC_SPARSE)
     assert rel(osp[0], od[0]) <= 1e-12
-    assert grel(gsp, gd) <= 1e-11
+    check_grad(gsp, gd, c, 1e-11, 1e-11)
     assert np.allclose(tsp, td, rtol=1e-11, atol=1e-9)
 
 
@@ -156,7 +157,7 @@ def test_dayahead_network_one_period_parity(qg, precision):
     if precision == 1:
         x, tol = as_f32(x), TOL32
     res = gpu_eval(qg, c, x, precision)  # QG_DC_AUTO: sparse above 4,096 buses
-    check(res, oracle.evaluate(c, x, net=dayahead_net()), tol)
+    check(res, oracle.evaluate(c, x, net=dayahead_net()), tol, c)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -178,6 +179,6 @@ def test_dayahead_full_horizon_sampled_period(qg, precision):
             assert abs(terms[0, k] - ref.terms[name]) <= tol * max(abs(ref.terms[name]), 1e-6 * abs(ref.obj)), name
     assert terms[0, oracle.TERM_NAMES.index("zctg")] >= ref.terms["zctg"]
     T, n, G = c.T, c.n_bus, c.n_gen
-    rows = np.concatenate([np.arange(t * n, (t + 1) * n), T * n + np.arange(t * n, (t + 1) * n)] +
-                          [2 * T * n + k * T * G + np.arange(t * G, (t + 1) * G) for k in range(3)])
-    assert grel(g[rows], ref.grad[rows]) <= tol, grel(g[rows], ref.grad[rows])
+    rows = [("v", np.arange(t * n, (t + 1) * n)), ("theta", T * n + np.arange(t * n, (t + 1) * n))]
+    rows += [(name, 2 * T * n + k * T * G + np.arange(t * G, (t + 1) * G)) for k, name in enumerate("pqr")]
+    check_at(g, ref.grad, None, tol, f"period {t}", classes=rows)
