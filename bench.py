@@ -38,9 +38,9 @@ UNIT = "evals/s"
 WORKLOAD = "rt617"
 DOMINANT = "s2"  # the contingency stage
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# DRAM bytes (read + write) per launch of the dominant kernel, the mean over the launches of one ncu
-# capture of the current kernel code (profiles/rt617_stage_kernels_launches.md); a kernel without a
-# capture of its current code gets None
+# DRAM bytes (read + write) per launch of the dominant kernel: the mean over the launches of one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, a few launches) of the current
+# kernel code; a kernel whose code changed since its capture gets None
 NCU_TRAFFIC = {("rt617", "s2", True): 2657900.0, ("rt617", "s2", False): 3395968.0}
 FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
 
@@ -337,7 +337,7 @@ def gpu_leg(args, rank, world, local_rank):
     value = job_throughput(K, world, mix["total_ms"])
     phases = mix["phases"]
     # the dominant kernel: the contingency stage, the largest kernel of the step in the ncu launch
-    # list of both paths (profiles/rt617_stage_kernels_launches.md); the per-stage event times below
+    # list of both paths; the per-stage event times below
     # include each launch's own latency and put stages 1, 2 and 5 within a few percent of each other
     dom = DOMINANT
     roof = roofline(case, dom, phases[dom], True, peaks, src, mix["clocks"])

@@ -298,11 +298,13 @@ int qg_set_state(qg_ctx *h, const void *buf, int64_t size);
 /* Per-kernel timing (CUDA events, no profiler): when on, every evaluation and
  * Adam step records an event after each stage, also inside qg_solve's graph.
  * qg_phase_times writes the durations in ms of the last evaluation's five
- * stages in launch order (s1: branch flows, zonal sums and base DC flows;
- * s2: bus balance and contingencies; s3: contingency sums and branch adjoints;
- * s4: bus adjoint gather and adjoint DC products; s5: generator gradients and
- * the objective; with the sparse DC solver s1 includes the forward solve and
- * s4 the adjoint solve), then that of a stand-alone qg_adam_step if one
+ * stages in launch order (s1: branch flows, bus balances, zonal sums and base
+ * DC flows; s2: contingencies; s3: contingency sums and branch adjoints; s4:
+ * bus adjoint gather and adjoint DC products, and on the mixed path with the
+ * dense DC products also the device gradients and the objective, s5 then
+ * being 0; s5: device gradients and the objective; with the sparse DC solver
+ * s1 includes the forward solve and s4 the adjoint solve), then that of a
+ * stand-alone qg_adam_step if one
  * followed, up to cap entries; returns how many it wrote or a negative error
  * code.  Waits for those events. */
 int qg_set_profiling(qg_ctx *h, int on);
@@ -351,9 +353,11 @@ int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]);
 int qg_round_batch(qg_ctx *h, void *x, double frac, int64_t *n_fixed, int64_t *n_binaries);
 int qg_round_reset(qg_ctx *h);
 
-/* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: the
- * 5 stage kernels, plus 3 to 7 solve kernels with the sparse DC solver (a qg_solve graph replay
- * without a trace adds one closing kernel).  Returns a negative error code for a NULL handle. */
+/* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: 4
+ * stage kernels on the mixed path with the dense DC products (stage 4 updates the devices), 5 on
+ * the FP64 path, 5 plus 3 to 7 solve kernels with the sparse DC solver; one fewer without
+ * contingencies (a qg_solve graph replay without a trace adds one closing kernel).  Returns a
+ * negative error code for a NULL handle. */
 int32_t qg_launches_per_eval(const qg_ctx *h);
 
 const char *qg_last_error(const qg_ctx *h);

@@ -624,7 +624,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     D.n_mg = ceil_div(D.n_mt, D.ctg_mg);
     D.ctg_tb = ceil_div(H.T, std::min(ntc_all, H.T));
     D.ctg_ntc = ceil_div(H.T, D.ctg_tb);
-    D.n_sb = ceil_div(H.M, NTHR);
+    D.n_sb = ceil_div(H.M, NTHR / S3_SPLIT);
     D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
     D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
     D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
@@ -665,9 +665,9 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   const int dcf = P.sp ? R_SDCF : R_DCF;
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, DCF_BM), ceil_div(I[b].T, DCF_TC), b, dcf);
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, NTHR), I[b].T, b, R_BRANCH);
+  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
   for (int b = 0; b < B; ++b) add_span(P.s2, I[b].ctg_ntc * I[b].n_mg * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
-  for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   // objective slots: the blocks of s1 and s2 in launch order, renumbered instance-major so that each
   // instance's slots are one contiguous range; then the fold slots of stage 3 (one per fold block:
   // the sum of up to NTHR stage-1/2 slots of one instance) and one slot per stage-5 device block
@@ -694,25 +694,41 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   // stage 3: the fold blocks first (they start while the branch blocks are dispatched), then branches
   for (int b = 0; b < B; ++b) add_span(P.s3, I[b].fold_nb, 1, b, R_OBJ);
   for (int b = 0; b < B; ++b) add_span(P.s3, I[b].n_sb, I[b].T, b, R_BRANCH);
-  if (P.sp) add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
-  else
-    for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].Gc + 1, NTHR / 32), I[b].T, b, R_DCA);
-  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
-  // stage 5: device blocks over the instance's (period, device) pairs packed densely, then the
-  // transformer blocks
-  // FP64 path: one warp of pairs per block, so that the FP64 arithmetic (a small fraction of the FP32
-  // rate on this part) spreads over many SMs; mixed path: a full block of pairs
-  const int gen_pb = h->opt.precision == QG_FP64 ? 32 : NTHR;
+  // adjoint DC products and devices.  Dense mode: one warp per (period, generator bus or transformer
+  // column) in stage 4 computes the adjoint product; on the mixed path the warp also updates the
+  // devices at the bus (stage 4 is the last stage); the FP64 path leaves the devices to stage 5 blocks
+  // of 32 (period, device) pairs, so that each warp's FP64 instructions serve 32 devices.  Sparse
+  // mode: the adjoint solve follows stage 4, and stage 5 updates the devices (FP64 path: one warp of
+  // pairs per block; mixed path: a full block of pairs), then the transformers.
+  const bool fuse = !P.sp && h->opt.precision == QG_MIXED;
   int gen_slot = 0;
-  for (int b = 0; b < B; ++b) {
-    I[b].gen_first = P.s5.n_blocks;
-    I[b].gen_pb = gen_pb;
-    I[b].gen_nb = ceil_div((long long)I[b].T * I[b].G, gen_pb);
-    I[b].gen_slot0 = gen_slot;
-    gen_slot += I[b].gen_nb;
-    add_span(P.s5, I[b].gen_nb, 1, b, R_GEN);
+  if (!P.sp)
+    for (int b = 0; b < B; ++b) {
+      const int per_t = ceil_div(I[b].Gc, NTHR / 32);
+      if (fuse) {
+        I[b].gen_first = P.s4.n_blocks;
+        I[b].gen_pb = 0;
+        I[b].gen_nb = per_t * I[b].T;
+        I[b].gen_slot0 = gen_slot;
+        gen_slot += I[b].gen_nb;
+      }
+      add_span(P.s4, per_t, I[b].T, b, R_GBUS);
+    }
+  else
+    add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
+  if (!fuse) {
+    const int gen_pb = h->opt.precision == QG_FP64 ? 32 : NTHR;
+    for (int b = 0; b < B; ++b) {
+      I[b].gen_first = P.s5.n_blocks;
+      I[b].gen_pb = gen_pb;
+      I[b].gen_nb = ceil_div((long long)I[b].T * I[b].G, gen_pb);
+      I[b].gen_slot0 = gen_slot;
+      gen_slot += I[b].gen_nb;
+      add_span(P.s5, I[b].gen_nb, 1, b, R_GEN);
+    }
+    for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].X, NTHR), I[b].T, b, R_XF);
   }
-  for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].X, NTHR), I[b].T, b, R_XF);
+  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK * S4_PACKS), I[b].T, b, R_BUS);
   P.n_gen_slots = gen_slot;
   return QG_OK;
 }
@@ -794,10 +810,11 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   const int B = h->n_inst;
   const Plan &P = h->plan;
   std::vector<int2> br_end;
-  std::vector<int> br_kidx, gen_bus, gen_zone, gen_gb, gb_ptr{0}, gb_gen, zgen_ptr{0}, zgen, ctg_br, bal_code, bal_row,
+  std::vector<int> br_kidx, gen_bus, gen_zone, gen_gb, gb_ptr{0}, gb_gen, gb_dev0, gb_ndev, zgen_ptr{0}, zgen, ctg_br,
+      bal_code, bal_row,
       adj_code, adj_row, br_xf, xf_br;
   std::vector<double> br_g, br_b, br_hch, br_smax, br_s2, ga, gbv, gcr, gpmax, gramp, load_p, load_q, rreq, dt, lo, hi,
-      ltot, ptdfg, ptdfgT, cload, rsum, lodf, gsgn, gpmin, gqmin, gqmax, gcon, gcsu, gcsd, guinit, blk_c, blk_lo, blk_w;
+      ltot, ptdfg, ptdfaT, cload, rsum, lodf, gsgn, gpmin, gqmin, gqmax, gcon, gcsu, gcsd, guinit, blk_c, blk_lo, blk_w;
   std::vector<int> blk_ptr{0};
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
@@ -848,6 +865,8 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
       zg[H.gen_zone[g]].push_back(D.gen0 + g);
     }
     for (auto &v : gbg) {
+      gb_dev0.push_back(v.empty() ? -1 : v[0]);
+      gb_ndev.push_back((int)v.size());
       gb_gen.insert(gb_gen.end(), v.begin(), v.end());
       gb_ptr.push_back((int)gb_gen.size());
     }
@@ -866,9 +885,13 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
     ltot.insert(ltot.end(), H.ltot.begin(), H.ltot.end());
     if (!H.sparse) {
       ptdfg.insert(ptdfg.end(), H.ptdfg.begin(), H.ptdfg.end());
-      const int Gc = H.Gc;
+      // columns of the adjoint DC products (Eqs. 2nd_lin_sys, correction), one row per column: the
+      // injection adjoint at a generator bus minus its mean over all buses is
+      // sum_m dz/df_m (PTDF[m, gb] - (PTDF 1)[m] / n), so the slack's mean is folded into the column;
+      // transformer columns are used as they are
+      const int Gc = H.Gc, Gb = (int)H.gbus.size();
       for (int q = 0; q < Gc; ++q)
-        for (int m = 0; m < H.M; ++m) ptdfgT.push_back(H.ptdfg[(size_t)m * Gc + q]);
+        for (int m = 0; m < H.M; ++m) ptdfaT.push_back(H.ptdfg[(size_t)m * Gc + q] - (q < Gb ? H.rsum[m] / H.n : 0.0));
       cload.insert(cload.end(), H.cload.begin(), H.cload.end());
     }
     rsum.insert(rsum.end(), H.rsum.begin(), H.rsum.end());
@@ -923,7 +946,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
 #define UPR(field, vec) { auto tmp_ = cast<Real>(vec); if ((rc = upload(h, &r, tmp_))) return rc; d.field = r; }
 #define UPD(field, vec) { auto tmp_ = to_dc<Dc>(vec); if ((rc = upload(h, &z, tmp_))) return rc; d.field = z; }
   UPI(br_kidx, br_kidx) UPI(gen_bus, gen_bus) UPI(gen_zone, gen_zone) UPI(gen_gb, gen_gb) UPI(gb_ptr, gb_ptr)
-  UPI(gb_gen, gb_gen) UPI(zgen_ptr, zgen_ptr) UPI(zgen, zgen) UPI(ctg_br, ctg_br) UPI(bal_code, bal_code)
+  UPI(gb_gen, gb_gen) UPI(gb_dev0, gb_dev0) UPI(gb_ndev, gb_ndev) UPI(zgen_ptr, zgen_ptr) UPI(zgen, zgen) UPI(ctg_br, ctg_br) UPI(bal_code, bal_code)
   UPI(bal_row, bal_row) UPI(adj_code, adj_code) UPI(adj_row, adj_row) UPI(br_xf, br_xf) UPI(xf_br, xf_br)
   UPR(br_g, br_g) UPR(br_b, br_b) UPR(br_hch, br_hch) UPR(br_smax, br_smax) UPR(br_s2ctg, br_s2)
   UPR(gen_a, ga) UPR(gen_b, gbv) UPR(gen_cr, gcr) UPR(gen_pmax, gpmax)
@@ -931,7 +954,7 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   UPR(gen_csu, gcsu) UPR(gen_csd, gcsd) UPR(gen_uinit, guinit) UPI(blk_ptr, blk_ptr) UPR(blk_c, blk_c)
   UPR(blk_lo, blk_lo) UPR(blk_w, blk_w)
   UPR(load_p, load_p) UPR(load_q, load_q) UPR(dt, dt) UPR(lo, lo) UPR(hi, hi)
-  UPD(ltot, ltot) UPD(ptdfg, ptdfg) UPD(ptdfgT, ptdfgT) UPD(cload, cload) UPD(rsum, rsum)
+  UPD(ltot, ltot) UPD(ptdfg, ptdfg) UPD(ptdfaT, ptdfaT) UPD(cload, cload) UPD(rsum, rsum)
   {
     double *q64;
 #define UP64(field, vec) if ((rc = upload(h, &q64, vec))) return rc; d.field = q64;
@@ -2017,8 +2040,9 @@ int qg_ctg_scores(qg_ctx *h, double *z) {
 int32_t qg_launches_per_eval(const qg_ctx *h) {
   if (!h) return QG_ERR_INVALID_ARG;
   const Plan &P = h->plan;
-  if (!P.sp) return 5;
-  return 5 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0);
+  const int s2 = P.s2.n_blocks > 0 ? 1 : 0;  // no contingencies: no stage 2
+  if (!P.sp) return 3 + s2 + (P.s5.n_blocks > 0 ? 1 : 0);  // the mixed path's dense mode updates the devices in stage 4
+  return 4 + s2 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0);
 }
 
 int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t shape[2]) {

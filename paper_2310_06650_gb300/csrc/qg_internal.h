@@ -19,6 +19,8 @@ constexpr int CT_BM = 64, CT_BK = 64;  // contingency tile: monitored branches x
 constexpr int DCF_BM = 32, DCF_TC = 8; // forward DC tile: 32 branches x 8 periods
 constexpr int PACK = 32;               // CSR entries per warp pack (rows never straddle packs)
 constexpr int PACKS_PER_BLOCK = NTHR / 32;
+constexpr int S4_PACKS = 2;            // branch-end CSR packs per warp in the bus gather of stage 4
+constexpr int S3_SPLIT = 4;            // threads per branch-period in stage 3 (partial sums split over them)
 
 // One instance of a batch.  Entity ids inside the kernels are global (offset by
 // bus0 / br0 / gen0 / zone0 / ctg0 / gb0); per-period arrays are period-major
@@ -34,7 +36,7 @@ struct Inst {
   int n_mt, n_kt;        // contingency tiles along monitored branches / outages
   int ctg_mg, n_mg;      // monitored-branch tiles per contingency block, and the number of such groups
   int ctg_tb, ctg_ntc;   // periods per contingency block, and the number of period chunks
-  int n_sb;              // stage-3 branch blocks per period
+  int n_sb;              // stage-3 branch blocks per period (NTHR / S3_SPLIT branches each)
   int bal0, n_bal_pack;  // first entry / number of warp packs of the balance CSR
   int adj0, n_adj_pack;  // same for the branch-end adjoint CSR
   long long x0;          // first variable of this instance
@@ -43,7 +45,8 @@ struct Inst {
   long long l0;          // line-outage block, M x Kp, row m
   long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mg][T][K]
   long long pf0;         // flags of the row partials: [n_kt][T][n_mt], 1 where a 64-row tile has any
-  long long gi0;         // adjoint DC products: [T][Gc + 1] (generator buses, transformers, then n mean(eta))
+  long long gi0;         // adjoint DC products of the sparse mode: [T][Gc + 1] (generator buses,
+                         // transformers, then n mean(eta))
   long long tx0;         // per-period transformer arrays: [T][X]
   long long xtau0;       // first tau variable (x0 + T (2n + 3G)); phi follow after T X
   long long xu0;         // first on-status variable (after phi; meaningful when uc)
@@ -52,17 +55,19 @@ struct Inst {
   double hours;          // sum of dt
   double nfloor_ctg;     // M K - K: elements whose soft-ReLU floor eps the contingency term adds in closed form
   int obj_lo, obj_n;     // this instance's stage-1/2 objective slots
-  int gen_first, gen_nb; // its device blocks in stage 5: first block in their launch, count
+  int gen_first, gen_nb; // its device blocks (R_GBUS in stage 4, or R_GEN in stage 5 of the sparse mode):
+                         // first block in their launch, count
   int gen_pb;            // (period, device) pairs per device block (the first gen_pb threads)
   int gen_slot0;         // first reduction slot of those blocks (after the stage-1/2 slots)
   int fold_nb, fold_slot0; // its stage-3 fold blocks (each sums up to NTHR stage-1/2 slots) and their
                            // first slot (after the device-block slots)
 };
 
-// Roles of the blocks of the fused stage kernels.  R_DCF / R_DCA are the dense DC products;
-// R_SDCF / R_SDCA their counterparts around the sparse-factor solves (flows from the solved
-// angles; right-hand side of the adjoint solve).
-enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_DCA, R_GEN, R_SDCF, R_SDCA, R_XF, R_OBJ };
+// Roles of the blocks of the fused stage kernels.  R_DCF is the dense forward DC product and R_GBUS
+// the dense adjoint product with the device updates at each generator bus; R_SDCF / R_SDCA are their
+// counterparts around the sparse-factor solves (flows from the solved angles; right-hand side of
+// the adjoint solve), whose device updates are R_GEN / R_XF blocks of stage 5.
+enum Role : int { R_BRANCH = 0, R_ZONE, R_DCF, R_BUS, R_CTG, R_GBUS, R_GEN, R_SDCF, R_SDCA, R_XF, R_OBJ };
 
 constexpr int SP_RB = 64;   // dense tail product: rows per block
 constexpr int SP_BK = 32;   // dense tail product: columns per shared-memory chunk
@@ -114,6 +119,7 @@ struct Dev {
   const int *blk_ptr;                 // [sum G + 1] bid blocks of each device (Example 3); none: quadratic cost
   const Real *blk_c, *blk_lo, *blk_w; // block price, cumulative start P_{l-1}, width
   const int *gb_ptr, *gb_gen;         // generator bus -> generators: one CSR over the batch's generator buses
+  const int *gb_dev0, *gb_ndev;       // [sum Gb] each generator bus's first device (global id) and count
   const int *zgen_ptr, *zgen;         // zone -> generators: one CSR over the batch's zones (global ids)
   const int *ctg_br;                  // [sum K] local branch id of each outage
   const int *br_xf;                   // [sum M] local transformer index of each branch, -1 for lines
@@ -125,7 +131,8 @@ struct Dev {
   const Dc *ltot;                     // [sum T] total load per period
   const Dc *load_dc;                  // [T n] active load in the DC product type (sparse mode)
   const Dc *ptdfg;                    // [sum M Gb] PTDF columns of generator buses, row m
-  const Dc *ptdfgT;                   // [sum Gb M] the same, row gb
+  const Dc *ptdfaT;                   // [sum Gc M] adjoint columns, row c: PTDF[m, gb] - (PTDF 1)[m] / n for a
+                                      // generator bus (the slack's mean folded in), PSDF[m, x] for a transformer
   const Dc *cload;                    // [sum T M] PTDF * load_t
   const Dc *rsum;                     // [sum M] PTDF * 1
   const void *lodf;                   // [sum M Kp]: float / bf16 / bf16x2 (mixed) or float screening copy

@@ -80,6 +80,7 @@ struct DcOps<double> {
   __device__ static double to_real(double a) { return a; }
   __device__ static float to_float(double a) { return (float)a; }
   __device__ static double shfl_down(double a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+  __device__ static double bcast(double a) { return __shfl_sync(0xffffffffu, a, 0); }
 };
 
 template <>
@@ -103,6 +104,7 @@ struct DcOps<df32> {
   __device__ static df32 shfl_down(df32 a, int o) {
     return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
   }
+  __device__ static df32 bcast(df32 a) { return {__shfl_sync(0xffffffffu, a.hi, 0), __shfl_sync(0xffffffffu, a.lo, 0)}; }
 };
 
 __device__ __forceinline__ double to_double(double a) { return a; }
@@ -315,35 +317,44 @@ __device__ __forceinline__ void branch_tap(const Dev<Real, Dc> &d, const Inst &I
 
 constexpr int GBC = 128;  // generator-bus chunk of the DC products
 
+// Pi-model flows at both ends of branch jg (global id) in period t (Sec. II-F line-flow example): a
+// transformer's tap enters through v_f / tau, its phase shift through d = theta_f - theta_o - phi.
+// Written without the cancellation of g vf^2 against g vf vo cos(d) (vf standing for v_f / tau):
+//   p_fr = g vf (vf - vo) + g vf vo (1 - cos d) - b vf vo sin d,  and likewise for the others,
+// with 1 - cos d = sin^2 d / (1 + cos d) while cos d > 0.
 template <typename Real, typename Dc>
-__device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
-                          Obj3<Dc> &acc, const HP<Real> hp) {
-  const int j = sub * NTHR + threadIdx.x;
-  if (j >= I.M) return;
-  const int jg = I.br0 + j;
+__device__ __forceinline__ void pi_flow(const Dev<Real, Dc> &d, const Inst &I, int t, int jg, const Real *__restrict__ x,
+                                        Real &pf, Real &qf, Real &pt, Real &qt) {
   const int2 ft = d.br_end[jg];
   const Real *v = x + I.x0 + (long long)t * I.n;
   const Real *th = v + (long long)I.T * I.n;
   Real tau, phi;
   int xi;
   branch_tap(d, I, t, jg, x, tau, phi, xi);
-  // a transformer's tap enters through vf / tau, its phase shift through d = theta_f - theta_o - phi
   const Real vf = v[ft.x] / tau, vo = v[ft.y];
   const Real dl = th[ft.x] - th[ft.y] - phi;
-  const Real g = d.br_g[jg], bb = d.br_b[jg], hch = d.br_hch[jg], smax = d.br_smax[jg];
-  const Real wt = d.dt[I.tp0 + t] * d.c_s * hp.beta;  // loaded before the stores below
+  const Real g = d.br_g[jg], bb = d.br_b[jg], hch = d.br_hch[jg];
   Real sn, cs;
   dsincos(dl, &sn, &cs);
   const Real vv = vf * vo;
-  // Pi model (vf standing for v_f / tau) without the cancellation of g vf^2 against g vf vo cos(d):
-  //   p_fr = g vf (vf - vo) + g vf vo (1 - cos d) - b vf vo sin d,  and likewise for the others,
-  // with 1 - cos d = sin^2 d / (1 + cos d) while cos d > 0.
   const Real dv = vf - vo;
   const Real omc = cs > Real(0) ? sn * sn / (Real(1) + cs) : Real(1) - cs;
-  const Real pf = g * vf * dv + g * vv * omc - bb * vv * sn;
-  const Real pt = -g * vo * dv + g * vv * omc + bb * vv * sn;
-  const Real qf = -bb * vf * dv - hch * vf * vf - bb * vv * omc - g * vv * sn;
-  const Real qt = bb * vo * dv - hch * vo * vo - bb * vv * omc + g * vv * sn;
+  pf = g * vf * dv + g * vv * omc - bb * vv * sn;
+  pt = -g * vo * dv + g * vv * omc + bb * vv * sn;
+  qf = -bb * vf * dv - hch * vf * vf - bb * vv * omc - g * vv * sn;
+  qt = bb * vo * dv - hch * vo * vo - bb * vv * omc + g * vv * sn;
+}
+
+template <typename Real, typename Dc>
+__device__ void s1_branch(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
+                          Obj3<Dc> &acc, const HP<Real> hp) {
+  const int j = sub * NTHR + threadIdx.x;
+  if (j >= I.M) return;
+  const int jg = I.br0 + j;
+  const Real smax = d.br_smax[jg];
+  const Real wt = d.dt[I.tp0 + t] * d.c_s * hp.beta;  // loaded before the stores below
+  Real pf, qf, pt, qt;
+  pi_flow(d, I, t, jg, x, pf, qf, pt, qt);
   const long long e = I.tm0 + (long long)t * I.M + j;
   d.pf[e] = pf;
   d.qf[e] = qf;
@@ -436,30 +447,60 @@ __device__ void s1_dcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, c
   // columns: generator buses (their dispatch), then transformers (their phase-shift flow b = b_sr phi)
   for (int c0 = 0; c0 < I.Gc; c0 += GBC) {
     const int cn = min(GBC, I.Gc - c0);
-    __syncthreads();
-#pragma unroll 4
-    for (int e = threadIdx.x; e < DCF_TC * cn; e += NTHR) {
-      const int r = e / cn, c = e % cn, tt = t0 + r, cc = c0 + c;
+    if (c0 > 0) __syncthreads();  // the previous chunk's products are done with s_pt, s_pg
+    // the PTDF tile first, as asynchronous copies to shared memory: they proceed during the gather
+#pragma unroll 8
+    for (int e = threadIdx.x; e < DCF_BM * cn; e += NTHR) {
+      const int r = e / cn, c = e % cn;
+      if (m0 + r < I.M) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_pt[r][c]);
+        const Dc *src = d.ptdfg + I.pg0 + (long long)(m0 + r) * I.Gc + c0 + c;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+      } else {
+        s_pt[r][c] = DcOps<Dc>::zero();
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // the signed dispatch of each generator bus in the block's periods: round 1 loads each entry's
+    // first device and device count (static), round 2 its dispatch; a thread's entries are all in
+    // flight together; further devices of a bus (rare) take more rounds
+    constexpr int EPT = (DCF_TC * GBC + NTHR - 1) / NTHR;
+    int dv[EPT], dn[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = threadIdx.x + k * NTHR, r = e / cn, c = e - r * cn;
+      const bool gen = e < DCF_TC * cn && t0 + r < I.T && c0 + c < I.Gb;
+      dv[k] = gen ? d.gb_dev0[I.gb0 + c0 + c] : -1;
+      dn[k] = gen ? d.gb_ndev[I.gb0 + c0 + c] : 0;
+    }
+    Real pv[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = threadIdx.x + k * NTHR, r = e / cn;
+      pv[k] = dv[k] >= 0 ? d.gen_sgn[dv[k]] * p[(long long)(t0 + r) * I.G + (dv[k] - I.gen0)] : Real(0);
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = threadIdx.x + k * NTHR, r = e / cn, c = e - r * cn, tt = t0 + r, cc = c0 + c;
+      if (e >= DCF_TC * cn) break;
       Dc s = DcOps<Dc>::zero();
-      if (tt < I.T && cc < I.Gb) {
-        const int gbp = I.gb0 + cc;  // global generator-bus id; gb_ptr is one CSR over the batch
-        const int q0 = d.gb_ptr[gbp], q1 = d.gb_ptr[gbp + 1];
-        for (int q = q0; q < q1; ++q) {  // producers add, consumers subtract
-          const int gq = d.gb_gen[q];
-          s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(d.gen_sgn[gq] * p[(long long)tt * I.G + (gq - I.gen0)]));
+      if (dv[k] >= 0) {  // producers add, consumers subtract (CSR order)
+        s = DcOps<Dc>::from_real(pv[k]);
+        if (dn[k] > 1) {
+          const int q0 = d.gb_ptr[I.gb0 + cc];
+          for (int q = q0 + 1; q < q0 + dn[k]; ++q) {
+            const int gq = d.gb_gen[q];
+            s = DcOps<Dc>::add(s, DcOps<Dc>::from_real(d.gen_sgn[gq] * p[(long long)tt * I.G + (gq - I.gen0)]));
+          }
         }
-      } else if (tt < I.T) {
+      } else if (tt < I.T && cc >= I.Gb) {  // a transformer column
         const int xi = cc - I.Gb;
         const Real phi = x[I.xtau0 + (long long)(I.T + tt) * I.X + xi];
         s = DcOps<Dc>::from_real(d.br_b[I.br0 + d.xf_br[I.xf0 + xi]] * phi);
       }
       s_pg[r][c] = s;
     }
-#pragma unroll 8
-    for (int e = threadIdx.x; e < DCF_BM * cn; e += NTHR) {
-      const int r = e / cn, c = e % cn;
-      s_pt[r][c] = (m0 + r < I.M) ? d.ptdfg[I.pg0 + (long long)(m0 + r) * I.Gc + c0 + c] : DcOps<Dc>::zero();
-    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     {  // four independent accumulation chains (the double-FP32 add is a long dependency)
       Dc a1 = DcOps<Dc>::zero(), a2 = DcOps<Dc>::zero(), a3 = DcOps<Dc>::zero();
@@ -529,12 +570,52 @@ __device__ void s1_sdcf(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, 
   }
 }
 
+// Bus balance (Example 4): P_it = load + sum of end flows - sum of generation, as a
+// warp-segmented reduction over the bus's CSR entries (each branch end's flow computed in place
+// from v, theta: the balance does not wait for the branch role); soft-abs penalty and its derivative.
+template <typename Real, typename Dc>
+__device__ void s1_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
+                       Obj3<Dc> &acc, const HP<Real> hp) {
+  const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
+  if (pk >= I.n_bal_pack) return;  // whole warp
+  const int e = I.bal0 + pk * PACK + (threadIdx.x & 31);
+  const int code = d.bal_code[e], row = d.bal_row[e];
+  const int kind = code & 3, id = code >> 2;
+  const long long ti = I.tb0 + (long long)t * I.n + (row >= 0 ? row : 0);
+  Real P = 0, Q = 0;
+  if (kind <= 1) {
+    Real pf, qf, pt, qt;
+    pi_flow(d, I, t, I.br0 + id, x, pf, qf, pt, qt);
+    P = kind == 0 ? pf : pt;
+    Q = kind == 0 ? qf : qt;
+  } else if (kind == 2) {  // a producer supplies (-), a consumer draws (+)
+    const Real sg = d.gen_sgn[I.gen0 + id];
+    const Real *p = x + I.x0 + 2LL * I.T * I.n + (long long)t * I.G + id;
+    P = -sg * p[0];
+    Q = -sg * p[(long long)I.T * I.G];
+  }
+  if (seg_sum2(row, P, Q) && row >= 0) {
+    P += d.load_p[ti];
+    Q += d.load_q[ti];
+    Real vp, dp, vq, dq;
+    soft_abs(P, hp.eps, vp, dp);
+    soft_abs(Q, hp.eps, vq, dq);
+    const Real dtw = d.dt[I.tp0 + t];
+    const Real wp = dtw * d.c_p * hp.beta, wq = dtw * d.c_q * hp.beta;
+    d.dP[ti] = wp * dp;
+    d.dQ[ti] = wq * dq;
+    acc.v[0] = DcOps<Dc>::from_real(wp * vp);
+    acc.v[1] = DcOps<Dc>::from_real(wq * vq);
+  }
+}
+
 template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x, int slot0) {
   const Where w = locate(S);
-  const Inst &I = tab.I[w.inst];
+  const Inst &I = tab.I[tab.n_inst == 1 ? 0 : w.inst];  // one instance: no wait on the span search
+  const int slot = d.slot_map[slot0 + blockIdx.x];  // issued first: it is not needed until the end
   Obj3<Dc> acc = obj3<Dc>(-1);
   if (w.role == R_DCF) {
     s1_dcf(d, I, w.t, w.sub, x);
@@ -543,59 +624,20 @@ __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, D
   } else if (w.role == R_BRANCH) {
     acc.id[0] = T_ZS;
     s1_branch(d, I, w.t, w.sub, x, acc, hparams(d));
+  } else if (w.role == R_BUS) {
+    acc.id[0] = T_ZP;
+    acc.id[1] = T_ZQ;
+    s1_bus(d, I, w.t, w.sub, x, acc, hparams(d));
   } else {
     acc.id[0] = T_ZRZ;
     s1_zone(d, I, w.t, w.sub, x, acc, hparams(d));
   }
-  write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
+  write_obj(d.objp, slot, acc);
 }
 
 // ---------------------------------------------------------------------------------------------
 // stage 2
 // ---------------------------------------------------------------------------------------------
-
-// Bus balance (Example 4): P_it = load + sum of end flows - sum of generation, as a
-// warp-segmented reduction over the bus's CSR entries; soft-abs penalty and its derivative.
-template <typename Real, typename Dc>
-__device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
-                       Obj3<Dc> &acc, const HP<Real> hp) {
-  const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
-  if (pk >= I.n_bal_pack) return;  // whole warp
-  const int e = I.bal0 + pk * PACK + (threadIdx.x & 31);
-  const int code = d.bal_code[e], row = d.bal_row[e];
-  const int kind = code & 3, id = code >> 2;
-  // data no earlier stage writes first (loads, weights, the device's role), then wait for stage 1
-  const long long ti = I.tb0 + (long long)t * I.n + (row >= 0 ? row : 0);
-  const Real lp = d.load_p[ti], lq = d.load_q[ti];
-  const Real dtw = d.dt[I.tp0 + t];
-  const Real sg = kind == 2 ? d.gen_sgn[I.gen0 + id] : Real(1);
-  pdl_wait();
-  Real P = 0, Q = 0;
-  const long long tm = I.tm0 + (long long)t * I.M + id;
-  if (kind == 0) {
-    P = d.pf[tm];
-    Q = d.qf[tm];
-  } else if (kind == 1) {
-    P = d.pt[tm];
-    Q = d.qt[tm];
-  } else if (kind == 2) {  // a producer supplies (-), a consumer draws (+)
-    const Real *p = x + I.x0 + 2LL * I.T * I.n + (long long)t * I.G + id;
-    P = -sg * p[0];
-    Q = -sg * p[(long long)I.T * I.G];
-  }
-  if (seg_sum2(row, P, Q) && row >= 0) {
-    P += lp;
-    Q += lq;
-    Real vp, dp, vq, dq;
-    soft_abs(P, hp.eps, vp, dp);
-    soft_abs(Q, hp.eps, vq, dq);
-    const Real wp = dtw * d.c_p * hp.beta, wq = dtw * d.c_q * hp.beta;
-    d.dP[ti] = wp * dp;
-    d.dQ[ti] = wq * dq;
-    acc.v[0] = DcOps<Dc>::from_real(wp * vp);
-    acc.v[1] = DcOps<Dc>::from_real(wq * vq);
-  }
-}
 
 // Four consecutive entries of the line-outage block (row stride padded to a multiple of 4, so
 // the group is one aligned vector load) as floats.
@@ -662,12 +704,14 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   Real *s_gz = s_f64k + (F64 ? TBM * CT_BK : 0);      // [TCH][8][BK] score column sums (screening only)
   Real *s_za = s_gz + (d.score ? TCH * 8 * CT_BK : 0);  // [TB][BK] scores over the group (screening only)
   Real *s_q2 = s_za + (d.score ? TBM * CT_BK : 0);    // [TB][BM] qmax2 of the monitored branch
+  Real *s_w = s_q2 + TBM * CT_BM;                     // [TB] d_t c_s beta of each period
   const bool score = d.score != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rq = threadIdx.x >> 4, cq = threadIdx.x & 15;
   const int kc = k0 + cq * 4;  // first of this thread's four outages
   __shared__ int s_hit[ctg_tch<Real>()];  // per period of the chunk: some row of the tile has a partial
   if (threadIdx.x < TCH) s_hit[threadIdx.x] = 0;
+  if (threadIdx.x < TB) s_w[threadIdx.x] = d.dt[I.tp0 + t0 + threadIdx.x] * d.c_s * hp.beta;
   for (int e = threadIdx.x; e < TCH * CT_BM; e += NTHR) s_gm[e] = s_gq[e] = 0;
   for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gk[e] = 0;
   if (score)
@@ -751,7 +795,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
     for (int tc0 = 0; tc0 < TB; tc0 += TCH) {
       const int tn = min(TCH, TB - tc0);
       for (int tt = 0; tt < tn; ++tt) {
-        const int tl = tc0 + tt, t = t0 + tl;
+        const int tl = tc0 + tt;
         const float4 fm4 = *reinterpret_cast<const float4 *>(s_fm + tl * CT_BM + rq * 4);
         const float4 qs4 = *reinterpret_cast<const float4 *>(s_qs + tl * CT_BM + rq * 4);
         const float4 fk4 = *reinterpret_cast<const float4 *>(s_fk + tl * CT_BK + cq * 4);
@@ -784,7 +828,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         // path, >= 0 with the margin (a positive exact sum cannot round to a negative one)
         if (!__any_sync(0xffffffffu, F64 ? mx >= 0.f : mx > 0.f)) continue;
         // a (candidate) post-contingency overload in this warp
-        const Real w = __ldg(d.dt + I.tp0 + t) * d.c_s * hp.beta;
+        const Real w = s_w[tl];
         Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
         if (F64 ? mx >= 0.f : mx > 0.f) {
 #pragma unroll
@@ -904,17 +948,11 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x, int slot0) {
   const Where w = locate(S);
-  const Inst &I = tab.I[w.inst];
-  Obj3<Dc> acc = obj3<Dc>(-1);
-  if (w.role == R_BUS) {
-    acc.id[0] = T_ZP;
-    acc.id[1] = T_ZQ;
-    s2_bus(d, I, w.t, w.sub, x, acc, hparams(d));  // waits after its static loads
-  } else {
-    acc.id[0] = T_ZCTG;
-    s2_ctg(d, I, w.sub, acc, hparams(d));
-  }
-  write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
+  const Inst &I = tab.I[tab.n_inst == 1 ? 0 : w.inst];  // one instance: no wait on the span search
+  const int slot = d.slot_map[slot0 + blockIdx.x];  // issued first: it is not needed until the end
+  Obj3<Dc> acc = obj3<Dc>(T_ZCTG);
+  s2_ctg(d, I, w.sub, acc, hparams(d));
+  write_obj(d.objp, slot, acc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -978,14 +1016,18 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x) {
   const Where w = locate(S);
-  const Inst &I = tab.I[w.inst];
+  const Inst &I = tab.I[tab.n_inst == 1 ? 0 : w.inst];  // one instance: no wait on the span search
   if (w.role == R_OBJ) {  // whole block
     pdl_wait();
     fold_slots(d, I, w.sub);
     return;
   }
   const int t = w.t;
-  const int j = w.sub * NTHR + threadIdx.x;
+  // S3_SPLIT threads per branch: each sums every S3_SPLIT-th partial, then a fixed-order shuffle
+  // tree combines them (the same bits in every thread of the group); the group's first thread
+  // loads the branch's flows and adjoints meanwhile and finishes the branch
+  const int q = threadIdx.x % S3_SPLIT;
+  const int j = w.sub * (NTHR / S3_SPLIT) + threadIdx.x / S3_SPLIT;
   const bool on = j < I.M;
   const int jg = I.br0 + (on ? j : 0);
   // network data first (independent of the earlier stages), then wait
@@ -995,52 +1037,72 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
   int xi0 = -1;
   if (I.X > 0) xi0 = d.br_xf[jg];
   pdl_wait();
-  if (on) {
-    const long long e = I.tm0 + (long long)t * I.M + j;
-    // every load of the earlier stages' results is issued before the first store (a store to a
-    // possibly aliasing array would keep later loads behind it): end adjoints, flows, voltages
-    const long long tb = I.tb0 + (long long)t * I.n;
-    Real gpf = d.dP[tb + ft.x], gpt = d.dP[tb + ft.y];
-    Real gqf = d.dQ[tb + ft.x], gqt = d.dQ[tb + ft.y];
-    const Real pf = d.pf[e], qf = d.qf[e], pt = d.pt[e], qt = d.qt[e];
-    const bool qto = d.qside[e] != 0;
+  const bool lead = on && q == 0;
+  const long long e = I.tm0 + (long long)t * I.M + (on ? j : 0);
+  // every load of the earlier stages' results is issued before the first store (a store to a
+  // possibly aliasing array would keep later loads behind it): end adjoints, flows, voltages
+  const long long tb = I.tb0 + (long long)t * I.n;
+  Real gpf = 0, gpt = 0, gqf = 0, gqt = 0, pf = 0, qf = 0, pt = 0, qt = 0, vf0 = 1, vo = 1, thf = 0, tho = 0;
+  bool qto = false;
+  Real tau = Real(1), phi = Real(0);
+  if (lead) {
+    gpf = d.dP[tb + ft.x];
+    gpt = d.dP[tb + ft.y];
+    gqf = d.dQ[tb + ft.x];
+    gqt = d.dQ[tb + ft.y];
+    pf = d.pf[e];
+    qf = d.qf[e];
+    pt = d.pt[e];
+    qt = d.qt[e];
+    qto = d.qside[e] != 0;
     const Real *v = x + I.x0 + (long long)t * I.n;
     const Real *th = v + (long long)I.T * I.n;
-    const Real vf0 = v[ft.x], vo = v[ft.y], thf = th[ft.x], tho = th[ft.y];
-    Real tau = Real(1), phi = Real(0);
+    vf0 = v[ft.x];
+    vo = v[ft.y];
+    thf = th[ft.x];
+    tho = th[ft.y];
     if (xi0 >= 0) {
       tau = x[I.xtau0 + (long long)t * I.X + xi0];
       phi = x[I.xtau0 + (long long)(I.T + t) * I.X + xi0];
     }
-    Real gF = 0, gq2 = 0;
+  }
+  Real gF = 0, gq2 = 0, gk = 0, zk = 0;
+  if (on) {
     // row partials of the outage tiles whose 64-row tile had an overload (flagged by stage 2): few
     // tiles are read unconditionally and selected (no dependent load), many are skipped
-    if (I.n_kt <= 16) {
+    if (I.n_kt <= 16 * S3_SPLIT) {
 #pragma unroll 4
-      for (int kt = 0; kt < I.n_kt; ++kt) {
-        const long long q = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
+      for (int kt = q; kt < I.n_kt; kt += S3_SPLIT) {
+        const long long pq = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
         const bool f = d.pmf[I.pf0 + ((long long)kt * I.T + t) * I.n_mt + (j >> 6)] != 0;
-        const Real a = d.pm[q], b = d.pq[q];
+        const Real a = d.pm[pq], b = d.pq[pq];
         gF += f ? a : Real(0);
         gq2 += f ? b : Real(0);
       }
     } else {
-      for (int kt = 0; kt < I.n_kt; ++kt) {
+      for (int kt = q; kt < I.n_kt; kt += S3_SPLIT) {
         if (!d.pmf[I.pf0 + ((long long)kt * I.T + t) * I.n_mt + (j >> 6)]) continue;
-        const long long q = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
-        gF += d.pm[q];
-        gq2 += d.pq[q];
+        const long long pq = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
+        gF += d.pm[pq];
+        gq2 += d.pq[pq];
       }
     }
-    Real zk = 0;
     if (kx >= 0) {
-      Real gk = 0;
-#pragma unroll 8
-      for (int mg = 0; mg < I.n_mg; ++mg) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
-      gF += gk;
+#pragma unroll 4
+      for (int mg = q; mg < I.n_mg; mg += S3_SPLIT) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
       if (d.score)
-        for (int mg = 0; mg < I.n_mg; ++mg) zk += d.pz[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
+        for (int mg = q; mg < I.n_mg; mg += S3_SPLIT) zk += d.pz[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
     }
+  }
+#pragma unroll
+  for (int o = 1; o < S3_SPLIT; o <<= 1) {
+    gF += __shfl_xor_sync(0xffffffffu, gF, o);
+    gq2 += __shfl_xor_sync(0xffffffffu, gq2, o);
+    gk += __shfl_xor_sync(0xffffffffu, gk, o);
+    zk += __shfl_xor_sync(0xffffffffu, zk, o);
+  }
+  gF += gk;
+  if (lead) {
     // adjoints of the four end flows
     const Real sf2 = pf * pf + qf * qf, st2 = pt * pt + qt * qt;
     if (fmax(sf2, st2) > smax * smax) {  // thermal (Example 1)
@@ -1141,53 +1203,68 @@ __device__ AdamCoef<Real> adam_coef(const Dev<Real, Dc> &d) {
 template <typename Real, typename Dc, bool ADAM>
 __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x,
                        const AdamCoef<Real> &ac) {
-  const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
-  const bool on = pk < I.n_adj_pack;
-  const int e = I.adj0 + (on ? pk : 0) * PACK + (threadIdx.x & 31);
+  // S4_PACKS consecutive packs per warp: the loads of all of them are issued together
+  Real s_x[S4_PACKS][2], s_m[S4_PACKS][2], s_v[S4_PACKS][2], s_lo[S4_PACKS][2], s_hi[S4_PACKS][2];
+  int code[S4_PACKS], row[S4_PACKS];
+  long long kv[S4_PACKS];
+  bool on[S4_PACKS];
   // static CSR entries and (fused Adam) the bus's optimizer state first, then wait for stage 3's
   // branch-end adjoints (no earlier stage of this evaluation writes x, m, v or the box)
-  const int code = d.adj_code[e], row = on ? d.adj_row[e] : -1;
-  const long long kv = I.x0 + (long long)t * I.n + (row >= 0 ? row : 0);
-  const long long kth = kv + (long long)I.T * I.n;
-  Real s_x[2] = {0, 0}, s_m[2] = {0, 0}, s_v[2] = {0, 0}, s_lo[2] = {0, 0}, s_hi[2] = {0, 0};
-  if (ADAM && row >= 0) {
-    const long long k2[2] = {kv, kth};
+#pragma unroll
+  for (int u = 0; u < S4_PACKS; ++u) {
+    const int pk = (sub * PACKS_PER_BLOCK + (threadIdx.x >> 5)) * S4_PACKS + u;
+    on[u] = pk < I.n_adj_pack;
+    const int e = I.adj0 + (on[u] ? pk : 0) * PACK + (threadIdx.x & 31);
+    code[u] = d.adj_code[e];
+    row[u] = on[u] ? d.adj_row[e] : -1;
+    kv[u] = I.x0 + (long long)t * I.n + (row[u] >= 0 ? row[u] : 0);
+    const long long k2[2] = {kv[u], kv[u] + (long long)I.T * I.n};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      s_x[c] = x[k2[c]];
-      s_m[c] = d.am[k2[c]];
-      s_v[c] = d.av[k2[c]];
-      s_lo[c] = d.lo[k2[c]];
-      s_hi[c] = d.hi[k2[c]];
+      s_x[u][c] = s_m[u][c] = s_v[u][c] = s_lo[u][c] = s_hi[u][c] = Real(0);
+      if (ADAM && row[u] >= 0) {
+        s_x[u][c] = x[k2[c]];
+        s_m[u][c] = d.am[k2[c]];
+        s_v[u][c] = d.av[k2[c]];
+        s_lo[u][c] = d.lo[k2[c]];
+        s_hi[u][c] = d.hi[k2[c]];
+      }
     }
   }
   pdl_wait();
-  if (!on) return;  // whole warp (the caller's block-wide steps come before this role)
-  const int kind = code & 3;
-  Real gv = 0, gth = 0;
-  const long long tm = I.tm0 + (long long)t * I.M + (code >> 2);
-  if (kind == 0) {
-    gv = d.avf[tm];
-    gth = d.ad[tm];
-  } else if (kind == 1) {
-    gv = d.avo[tm];
-    gth = -d.ad[tm];
-  }
-  if (seg_sum2(row, gv, gth) && row >= 0) {
-    if (ADAM) {
-      const long long k2[2] = {kv, kth};
-      const Real g2[2] = {gv, gth};
+  Real gv[S4_PACKS], gth[S4_PACKS];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        adam_update(s_x[c], g2[c], s_m[c], s_v[c], s_lo[c], s_hi[c], ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps,
-                    d.paper_eps);
-        x[k2[c]] = s_x[c];
-        d.am[k2[c]] = s_m[c];
-        d.av[k2[c]] = s_v[c];
+  for (int u = 0; u < S4_PACKS; ++u) {
+    const int kind = code[u] & 3;
+    gv[u] = gth[u] = Real(0);
+    const long long tm = I.tm0 + (long long)t * I.M + (code[u] >> 2);
+    if (on[u] && kind == 0) {
+      gv[u] = d.avf[tm];
+      gth[u] = d.ad[tm];
+    } else if (on[u] && kind == 1) {
+      gv[u] = d.avo[tm];
+      gth[u] = -d.ad[tm];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < S4_PACKS; ++u) {
+    if (!on[u]) break;  // whole warp (packs past the end)
+    if (seg_sum2(row[u], gv[u], gth[u]) && row[u] >= 0) {
+      const long long k2[2] = {kv[u], kv[u] + (long long)I.T * I.n};
+      if (ADAM) {
+        const Real g2[2] = {gv[u], gth[u]};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          adam_update(s_x[u][c], g2[c], s_m[u][c], s_v[u][c], s_lo[u][c], s_hi[u][c], ac.b1, ac.b2, ac.c1, ac.c2,
+                      ac.lr, ac.eps, d.paper_eps);
+          x[k2[c]] = s_x[u][c];
+          d.am[k2[c]] = s_m[u][c];
+          d.av[k2[c]] = s_v[u][c];
+        }
+      } else {
+        d.g[k2[0]] = gv[u];
+        d.g[k2[1]] = gth[u];
       }
-    } else {
-      d.g[kv] = gv;
-      d.g[kth] = gth;
     }
   }
 }
@@ -1439,23 +1516,14 @@ __device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab, long lon
 // adjoint of delta) + b_sr dPhi/db, where dPhi/db = dz/dp_x - (E_hat eta)_x is the contingency
 // term's phase-shift gradient (Eq. 2nd_lin_sys_phase plus the direct term of p = f + b);
 // [+ the projected Adam update of tau and phi].
+// Gradients of transformer xi in period t (tau: the AC terms; phi: the AC terms and the phase-shift
+// flow b = b_sr phi, whose adjoint is dz/df of the branch plus the adjoint DC term `eterm`)
+// [+ the projected Adam update].
 template <typename Real, typename Dc, bool ADAM>
-__device__ void s5_xf(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x,
-                      const AdamCoef<Real> &ac) {
-  const int xi = sub * NTHR + threadIdx.x;
-  if (xi >= I.X) return;
+__device__ void xf_update(const Dev<Real, Dc> &d, const Inst &I, int t, int xi, Real eterm, Real *__restrict__ x,
+                          const AdamCoef<Real> &ac) {
   const int j = d.xf_br[I.xf0 + xi];
   const long long e = I.tm0 + (long long)t * I.M + j;
-  Real eterm;
-  if (d.sp) {
-    const int2 ft = d.br_end[I.br0 + j];
-    const int pf = d.bus_pos[ft.x], po = d.bus_pos[ft.y];
-    const Dc ef = pf >= 0 ? d.sp_th[(long long)pf * I.T + t] : DcOps<Dc>::zero();
-    const Dc eo = po >= 0 ? d.sp_th[(long long)po * I.T + t] : DcOps<Dc>::zero();
-    eterm = -DcOps<Dc>::to_real(DcOps<Dc>::add(ef, DcOps<Dc>::neg(eo)));
-  } else {
-    eterm = DcOps<Dc>::to_real(d.gip[I.gi0 + (long long)t * (I.Gc + 1) + I.Gb + xi]);
-  }
   const Real gb = d.gF[e] + eterm;
   const Real gphi = -d.ad[e] + d.br_b[I.br0 + j] * gb;
   const Real gtau = d.atx[I.tx0 + (long long)t * I.X + xi];
@@ -1471,15 +1539,34 @@ __device__ void s5_xf(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Rea
   }
 }
 
-// Stage 5: generators of one period, with eta from stage 4's adjoint DC products (dense DC mode) or
-// from the adjoint solve (sparse mode) | transformers of one period; the last block reduces the
-// objective.
+template <typename Real, typename Dc, bool ADAM>
+__device__ void s5_xf(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x,
+                      const AdamCoef<Real> &ac) {
+  const int xi = sub * NTHR + threadIdx.x;
+  if (xi >= I.X) return;
+  Real eterm;
+  if (d.sp) {  // the adjoint term of the phase-shift flow is -(eta_f - eta_o) at the branch's ends
+    const int j = d.xf_br[I.xf0 + xi];
+    const int2 ft = d.br_end[I.br0 + j];
+    const int pf = d.bus_pos[ft.x], po = d.bus_pos[ft.y];
+    const Dc ef = pf >= 0 ? d.sp_th[(long long)pf * I.T + t] : DcOps<Dc>::zero();
+    const Dc eo = po >= 0 ? d.sp_th[(long long)po * I.T + t] : DcOps<Dc>::zero();
+    eterm = -DcOps<Dc>::to_real(DcOps<Dc>::add(ef, DcOps<Dc>::neg(eo)));
+  } else {  // stage 4's product of the transformer's column
+    eterm = DcOps<Dc>::to_real(d.gip[I.gi0 + (long long)t * (I.Gc + 1) + I.Gb + xi]);
+  }
+  xf_update<Real, Dc, ADAM>(d, I, t, xi, eterm, x, ac);
+}
+
+// Stage 5 (sparse DC mode, and the FP64 path's dense mode): devices of one period, with eta from the
+// adjoint solve or from stage 4's products (whose columns already subtract the mean) | transformers
+// of one period; the last block reduces the objective.
 template <typename Real, typename Dc, bool ADAM>
 __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              Real *__restrict__ x) {
   const Where w = locate(S);
-  const Inst &I = tab.I[w.inst];
+  const Inst &I = tab.I[tab.n_inst == 1 ? 0 : w.inst];  // one instance: no wait on the span search
   const int t = w.t;
   AdamCoef<Real> ac{};
   if (ADAM) ac = adam_coef(d);
@@ -1496,7 +1583,8 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
     pdl_wait();
     if (on) {
       const Dc *et = d.gip + I.gi0 + (long long)tg * (I.Gc + 1);  // written by stage 4 or the adjoint solve
-      const Dc eta = DcOps<Dc>::add(et[g.gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gc], DcOps<Dc>::inv_n(I))));
+      const Dc eta = d.sp ? DcOps<Dc>::add(et[g.gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gc], DcOps<Dc>::inv_n(I))))
+                          : et[g.gb];
       gen_update<Real, Dc, ADAM>(d, I, tg, gl, g, eta, ac, acc, x);
     }
     write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
@@ -1532,53 +1620,102 @@ __device__ void s4_sdca(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub) 
   if (lane == 0 && t < I.T) d.sp_part[(long long)sub * I.T + t] = s;
 }
 
-// Adjoint DC products (Eq. 2nd_lin_sys at the generator buses): one warp per output,
-//   eta[t, gb] = sum_m dz/df[t,m] PTDF[m, gb]       (gb < Gb),
-//   eta[t, Gb + x] = -sum_m dz/df[t,m] PSDF[m, x] = -(E_hat eta)_x   (transformer x, Eq.
-//                                                    2nd_lin_sys_phase),
-//   eta[t, Gc] = sum_m dz/df[t,m] (PTDF 1)[m]        (n times the mean of eta, Eq. correction),
-// lanes striding over the branches, then a fixed-order shuffle reduction.
-template <typename Real, typename Dc>
-__device__ void s4_dca(const Dev<Real, Dc> &d, const Inst &I, int t, int sub) {
-  const int o = sub * (NTHR / 32) + (threadIdx.x >> 5);
+// Adjoint DC products and device updates of the dense DC mode (the last stage).  Warp w of the
+// block takes column c = sub * 8 + w of period t:
+//   eta'[t, c] = sum_m dz/df[t,m] A[c, m],   A[gb, m] = PTDF[m, gb] - (PTDF 1)[m] / n  (c = gb < Gb:
+//   the injection adjoint at generator bus gb minus its mean over all buses, Eqs. 2nd_lin_sys and
+//   correction, the mean folded into the column at set-up) | A[Gb + x, m] = PSDF[m, x] (transformer x,
+//   Eq. 2nd_lin_sys_phase),
+// lanes striding over the branches, a fixed-order shuffle reduction, and the sum broadcast to the
+// warp; then (mixed path) its lanes update the devices at the bus, one per lane, or lane 0 the
+// transformer.  The FP64 path stores the products for stage 5 instead, which updates 32 devices per
+// warp: the FP64 pipe takes about as long for a warp with one active lane as for a full one.
+template <typename Real, typename Dc, bool ADAM>
+__device__ void s4_gbus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const AdamCoef<Real> &ac,
+                        Obj3<Dc> &acc, Real *__restrict__ x) {
   const int lane = threadIdx.x & 31;
-  if (o > I.Gc) return;
-  const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
-  const Dc *col = o < I.Gc ? d.ptdfgT + I.pg0 + (long long)o * I.M : d.rsum + I.br0;
-  Dc a0 = DcOps<Dc>::zero(), a1 = a0, a2 = a0, a3 = a0;
-  int m = lane;
-  for (; m + 96 < I.M; m += 128) {
-    DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
-    DcOps<Dc>::mac(a1, col[m + 32], DcOps<Dc>::from_real(gf[m + 32]));
-    DcOps<Dc>::mac(a2, col[m + 64], DcOps<Dc>::from_real(gf[m + 64]));
-    DcOps<Dc>::mac(a3, col[m + 96], DcOps<Dc>::from_real(gf[m + 96]));
+  const int c = sub * (NTHR / 32) + (threadIdx.x >> 5);
+  const bool col = c < I.Gc;
+  constexpr bool FUSE = sizeof(Real) == 4;
+  // data no earlier stage writes: the bus's first 32 devices (more take further rounds after the wait)
+  int q0 = 0, q1 = 0;
+  if (FUSE && col && c < I.Gb) {
+    q0 = d.gb_ptr[I.gb0 + c];
+    q1 = d.gb_ptr[I.gb0 + c + 1];
   }
-  for (; m < I.M; m += 32) DcOps<Dc>::mac(a0, col[m], DcOps<Dc>::from_real(gf[m]));
-  Dc acc = DcOps<Dc>::add(DcOps<Dc>::add(a0, a1), DcOps<Dc>::add(a2, a3));
+  const bool dev0 = q0 + lane < q1;
+  const int gl0 = dev0 ? d.gb_gen[q0 + lane] - I.gen0 : 0;
+  const GenIn<Real> g = gen_load<Real, Dc, ADAM>(d, I, t, gl0, x);
+  const Dc *A = d.ptdfaT + I.pg0 + (long long)(col ? c : 0) * I.M;
+  if (col)  // the column is static: start bringing its lines to L2 before the wait
+    for (long long off = (long long)lane * 128; off < (long long)I.M * (long long)sizeof(Dc); off += 32 * 128)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(A) + off));
+  pdl_wait();
+  if (!col) return;  // whole warp
+  const Real *gf = d.gF + I.tm0 + (long long)t * I.M;
+  Dc a[4] = {DcOps<Dc>::zero(), DcOps<Dc>::zero(), DcOps<Dc>::zero(), DcOps<Dc>::zero()};
+  for (int m0 = 0; m0 < I.M; m0 += 8 * 32) {  // 8 strides per batch: their loads are issued together
+    Dc av[8];
+    Real gv[8];
 #pragma unroll
-  for (int k = 16; k > 0; k >>= 1) acc = DcOps<Dc>::add(acc, DcOps<Dc>::shfl_down(acc, k));
-  if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gc + 1) + o] = acc;
+    for (int k = 0; k < 8; ++k) {
+      const int m = m0 + k * 32 + lane;
+      av[k] = m < I.M ? A[m] : DcOps<Dc>::zero();
+      gv[k] = m < I.M ? gf[m] : Real(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) DcOps<Dc>::mac(a[k & 3], av[k], DcOps<Dc>::from_real(gv[k]));
+  }
+  Dc eta = DcOps<Dc>::add(DcOps<Dc>::add(a[0], a[1]), DcOps<Dc>::add(a[2], a[3]));
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) eta = DcOps<Dc>::add(eta, DcOps<Dc>::shfl_down(eta, k));
+  if (!FUSE) {
+    if (lane == 0) d.gip[I.gi0 + (long long)t * (I.Gc + 1) + c] = eta;
+    return;
+  }
+  eta = DcOps<Dc>::bcast(eta);
+  if (c >= I.Gb) {
+    if (lane == 0) xf_update<Real, Dc, ADAM>(d, I, t, c - I.Gb, DcOps<Dc>::to_real(eta), x, ac);
+    return;
+  }
+  Obj3<Dc> one = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
+  if (dev0) {
+    gen_update<Real, Dc, ADAM>(d, I, t, gl0, g, eta, ac, one, x);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc.v[k] = DcOps<Dc>::add(acc.v[k], one.v[k]);
+  }
+  for (int q = q0 + 32 + lane; q < q1; q += 32) {  // a bus with more than 32 devices
+    const int gl = d.gb_gen[q] - I.gen0;
+    const GenIn<Real> g2 = gen_load<Real, Dc, ADAM>(d, I, t, gl, x);
+    one = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
+    gen_update<Real, Dc, ADAM>(d, I, t, gl, g2, eta, ac, one, x);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc.v[k] = DcOps<Dc>::add(acc.v[k], one.v[k]);
+  }
 }
 
-// Stage 4: bus gather of the branch-end adjoints (-> g_v, g_theta) [+ Adam on v, theta]; the
-// adjoint DC products at the generator buses (dense DC mode) or the right-hand side of the
-// adjoint solve (sparse mode).
+// Stage 4: bus gather of the branch-end adjoints (-> g_v, g_theta) [+ Adam on v, theta]; in the
+// dense DC mode also the adjoint DC products with the device and transformer updates (the last
+// stage: its last block reduces the objective); in the sparse mode the right-hand side of the
+// adjoint solve.
 template <typename Real, typename Dc, bool ADAM>
 __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              Real *__restrict__ x) {
   const Where w = locate(S);
-  const Inst &I = tab.I[w.inst];
+  const Inst &I = tab.I[tab.n_inst == 1 ? 0 : w.inst];  // one instance: no wait on the span search
+  AdamCoef<Real> ac{};
+  if (ADAM) ac = adam_coef(d);
   if (w.role == R_BUS) {
-    AdamCoef<Real> ac{};
-    if (ADAM) ac = adam_coef(d);
     s4_bus<Real, Dc, ADAM>(d, I, w.t, w.sub, x, ac);
   } else if (w.role == R_SDCA) {
     s4_sdca(d, I, w.t, w.sub);
-  } else {
-    pdl_wait();
-    s4_dca(d, I, w.t, w.sub);
+  } else {  // R_GBUS
+    Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
+    s4_gbus<Real, Dc, ADAM>(d, I, w.t, w.sub, ac, acc, x);
+    if (sizeof(Real) == 4) write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
   }
+  if (!d.sp && sizeof(Real) == 4) finish_eval<Real, Dc, ADAM>(d, tab, ac.step);  // the last stage
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1860,7 +1997,7 @@ size_t ctg_smem_bytes(int TB, bool score) {
          sizeof(Real) * ((size_t)TB * CT_BK + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
                          (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0) +
                          (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0) +
-                         (size_t)TB * CT_BM + CT_BM);
+                         (size_t)TB * CT_BM + CT_BM + (size_t)TB);
 }
 
 // Record a timing event on s; inside stream capture it becomes an external event node.
@@ -1935,7 +2072,8 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     e = cudaGetLastError();
   }
   mark(ev, 1, s);
-  go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB, d.score != 0), d, P.tab, P.s2, (const Real *)x, o2);
+  if (P.s2.n_blocks > 0)  // no contingencies: nothing for stage 2
+    go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB, d.score != 0), d, P.tab, P.s2, (const Real *)x, o2);
   mark(ev, 2, s);
   go(k_s3<Real, Dc>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
   mark(ev, 3, s);
@@ -1949,11 +2087,14 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     if (P.sp_bwa_blocks > 0) go(k_sp_back<Real, Dc, true>, P.sp_bwa_blocks, 0, d, I);
   }
   mark(ev, 4, s);
-  if (adam) go(k_s5<Real, Dc, true>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
-  else go(k_s5<Real, Dc, false>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
+  if (P.s5.n_blocks > 0) {  // the mixed path's dense mode updates the devices in stage 4
+    if (adam) go(k_s5<Real, Dc, true>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
+    else go(k_s5<Real, Dc, false>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
+  }
   mark(ev, 5, s);
   return e;
 }
+
 
 // The contingency kernel's dynamic shared-memory limit is a process-wide function attribute: it is
 // only ever raised, so that creating a handle with smaller blocks never breaks an existing one.
@@ -1969,6 +2110,7 @@ cudaError_t prepare_eval(int maxTB, bool score) {
   if (e == cudaSuccess) cur = sm;
   return e;
 }
+
 
 template <typename Real>
 cudaError_t launch_adam(Real *x, Real *m, Real *v, const Real *g, const Real *lo, const Real *hi, long long n,
