@@ -624,7 +624,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     D.n_mg = ceil_div(D.n_mt, D.ctg_mg);
     D.ctg_tb = ceil_div(H.T, std::min(ntc_all, H.T));
     D.ctg_ntc = ceil_div(H.T, D.ctg_tb);
-    D.n_sb = ceil_div(H.M, NTHR / S3_SPLIT);
+    D.n_sb = ceil_div(H.M, NTHR / (h->opt.precision == QG_MIXED ? s3_split<float>() : s3_split<double>()));
     D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
     D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
     D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
@@ -665,9 +665,15 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   const int dcf = P.sp ? R_SDCF : R_DCF;
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, DCF_BM), ceil_div(I[b].T, DCF_TC), b, dcf);
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, NTHR), I[b].T, b, R_BRANCH);
-  for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
+  // bus balances: stage 1 on the mixed path (each branch end's flow recomputed in place: the balance
+  // does not wait for the branch role); stage 2 on the FP64 path (from stage 1's flows)
+  const bool bal1 = h->opt.precision == QG_MIXED;
+  if (bal1)
+    for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
   for (int b = 0; b < B; ++b) add_span(P.s2, I[b].ctg_ntc * I[b].n_mg * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
+  if (!bal1)
+    for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   // objective slots: the blocks of s1 and s2 in launch order, renumbered instance-major so that each
   // instance's slots are one contiguous range; then the fold slots of stage 3 (one per fold block:
   // the sum of up to NTHR stage-1/2 slots of one instance) and one slot per stage-5 device block

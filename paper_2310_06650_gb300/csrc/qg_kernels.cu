@@ -639,6 +639,49 @@ __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, D
 // stage 2
 // ---------------------------------------------------------------------------------------------
 
+// Bus balance of the FP64 path (Example 4), in stage 2: the same sums as s1_bus from the flows that
+// stage 1 stored (recomputing them would cost the FP64 path its slow sincos a second time).
+template <typename Real, typename Dc>
+__device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
+                       Obj3<Dc> &acc, const HP<Real> hp) {
+  const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
+  if (pk >= I.n_bal_pack) return;  // whole warp
+  const int e = I.bal0 + pk * PACK + (threadIdx.x & 31);
+  const int code = d.bal_code[e], row = d.bal_row[e];
+  const int kind = code & 3, id = code >> 2;
+  // data no earlier stage writes first (loads, weights, the device's role), then wait for stage 1
+  const long long ti = I.tb0 + (long long)t * I.n + (row >= 0 ? row : 0);
+  const Real lp = d.load_p[ti], lq = d.load_q[ti];
+  const Real dtw = d.dt[I.tp0 + t];
+  const Real sg = kind == 2 ? d.gen_sgn[I.gen0 + id] : Real(1);
+  pdl_wait();
+  Real P = 0, Q = 0;
+  const long long tm = I.tm0 + (long long)t * I.M + id;
+  if (kind == 0) {
+    P = d.pf[tm];
+    Q = d.qf[tm];
+  } else if (kind == 1) {
+    P = d.pt[tm];
+    Q = d.qt[tm];
+  } else if (kind == 2) {  // a producer supplies (-), a consumer draws (+)
+    const Real *p = x + I.x0 + 2LL * I.T * I.n + (long long)t * I.G + id;
+    P = -sg * p[0];
+    Q = -sg * p[(long long)I.T * I.G];
+  }
+  if (seg_sum2(row, P, Q) && row >= 0) {
+    P += lp;
+    Q += lq;
+    Real vp, dp, vq, dq;
+    soft_abs(P, hp.eps, vp, dp);
+    soft_abs(Q, hp.eps, vq, dq);
+    const Real wp = dtw * d.c_p * hp.beta, wq = dtw * d.c_q * hp.beta;
+    d.dP[ti] = wp * dp;
+    d.dQ[ti] = wq * dq;
+    acc.v[0] = DcOps<Dc>::from_real(wp * vp);
+    acc.v[1] = DcOps<Dc>::from_real(wq * vq);
+  }
+}
+
 // Four consecutive entries of the line-outage block (row stride padded to a multiple of 4, so
 // the group is one aligned vector load) as floats.
 __device__ __forceinline__ void lodf_load4(const void *base, long long idx, int dtype, float (&v)[4]) {
@@ -950,8 +993,15 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
   const Where w = locate(S);
   const Inst &I = tab.I[tab.n_inst == 1 ? 0 : w.inst];  // one instance: no wait on the span search
   const int slot = d.slot_map[slot0 + blockIdx.x];  // issued first: it is not needed until the end
-  Obj3<Dc> acc = obj3<Dc>(T_ZCTG);
-  s2_ctg(d, I, w.sub, acc, hparams(d));
+  Obj3<Dc> acc = obj3<Dc>(-1);
+  if (w.role == R_BUS) {  // FP64 path
+    acc.id[0] = T_ZP;
+    acc.id[1] = T_ZQ;
+    s2_bus(d, I, w.t, w.sub, x, acc, hparams(d));  // waits after its static loads
+  } else {
+    acc.id[0] = T_ZCTG;
+    s2_ctg(d, I, w.sub, acc, hparams(d));
+  }
   write_obj(d.objp, slot, acc);
 }
 
@@ -1023,11 +1073,12 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
     return;
   }
   const int t = w.t;
-  // S3_SPLIT threads per branch: each sums every S3_SPLIT-th partial, then a fixed-order shuffle
+  // s3_split threads per branch: each sums every s3_split-th partial, then a fixed-order shuffle
   // tree combines them (the same bits in every thread of the group); the group's first thread
   // loads the branch's flows and adjoints meanwhile and finishes the branch
-  const int q = threadIdx.x % S3_SPLIT;
-  const int j = w.sub * (NTHR / S3_SPLIT) + threadIdx.x / S3_SPLIT;
+  constexpr int SPLIT = s3_split<Real>();
+  const int q = threadIdx.x % SPLIT;
+  const int j = w.sub * (NTHR / SPLIT) + threadIdx.x / SPLIT;
   const bool on = j < I.M;
   const int jg = I.br0 + (on ? j : 0);
   // network data first (independent of the earlier stages), then wait
@@ -1070,9 +1121,9 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
   if (on) {
     // row partials of the outage tiles whose 64-row tile had an overload (flagged by stage 2): few
     // tiles are read unconditionally and selected (no dependent load), many are skipped
-    if (I.n_kt <= 16 * S3_SPLIT) {
+    if (I.n_kt <= 16 * SPLIT) {
 #pragma unroll 4
-      for (int kt = q; kt < I.n_kt; kt += S3_SPLIT) {
+      for (int kt = q; kt < I.n_kt; kt += SPLIT) {
         const long long pq = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
         const bool f = d.pmf[I.pf0 + ((long long)kt * I.T + t) * I.n_mt + (j >> 6)] != 0;
         const Real a = d.pm[pq], b = d.pq[pq];
@@ -1080,7 +1131,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
         gq2 += f ? b : Real(0);
       }
     } else {
-      for (int kt = q; kt < I.n_kt; kt += S3_SPLIT) {
+      for (int kt = q; kt < I.n_kt; kt += SPLIT) {
         if (!d.pmf[I.pf0 + ((long long)kt * I.T + t) * I.n_mt + (j >> 6)]) continue;
         const long long pq = I.pm0 + ((long long)kt * I.T + t) * I.M + j;
         gF += d.pm[pq];
@@ -1089,13 +1140,13 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
     }
     if (kx >= 0) {
 #pragma unroll 4
-      for (int mg = q; mg < I.n_mg; mg += S3_SPLIT) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
+      for (int mg = q; mg < I.n_mg; mg += SPLIT) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
       if (d.score)
-        for (int mg = q; mg < I.n_mg; mg += S3_SPLIT) zk += d.pz[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
+        for (int mg = q; mg < I.n_mg; mg += SPLIT) zk += d.pz[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
     }
   }
 #pragma unroll
-  for (int o = 1; o < S3_SPLIT; o <<= 1) {
+  for (int o = 1; o < SPLIT; o <<= 1) {
     gF += __shfl_xor_sync(0xffffffffu, gF, o);
     gq2 += __shfl_xor_sync(0xffffffffu, gq2, o);
     gk += __shfl_xor_sync(0xffffffffu, gk, o);
