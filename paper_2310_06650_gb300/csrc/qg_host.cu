@@ -30,6 +30,7 @@ constexpr int DENSE_MAX_N = 8192;  // the dense inverse used at set-up holds n^2
 constexpr int SPARSE_AUTO_N = 4096; // QG_DC_AUTO picks the sparse factor above this many buses
 constexpr int TAIL_DEGREE = 32;     // minimum-degree elimination stops above this degree
 constexpr long long CTG_WAVE = 152 * 3;  // contingency blocks resident at once (152 SMs x 3 blocks)
+constexpr long long SMALL_PLAN = 65536;  // branch-periods of a plan that takes the latency layouts
 
 // Contingency-block shape of a plan (stage 2): how many period chunks each 64 x 64 tile is split
 // into (ntc) and how many monitored-branch tiles one block walks (mg); 0 picks the heuristic.
@@ -607,6 +608,15 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   for (int b = 0; b < B; ++b) max_nmt = std::max(max_nmt, ceil_div(h->hi[b].M, CT_BM));
   const int mg_all = kn.mg > 0 ? kn.mg
                                : (int)std::max({1LL, tiles / (4LL * CTG_WAVE), (long long)ceil_div(max_nmt, 64)});
+  // Small plans (at most SMALL_PLAN branch-periods in all) are latency bound: on the mixed path they
+  // take layouts that cut dependent memory rounds at the price of some repeated work (the bus
+  // balances in stage 1 recompute the branch flows; stage 3 splits each branch's sums over four
+  // threads; stage 4's warps form the adjoint products and update the devices at once, one objective
+  // slot per block).  Larger plans are throughput bound and keep the leaner layouts.
+  long long bp = 0;
+  for (int b = 0; b < B; ++b) bp += (long long)h->hi[b].M * h->hi[b].T;
+  const bool small_mixed = h->opt.precision == QG_MIXED && bp <= SMALL_PLAN;
+  P.tab.s3q = small_mixed ? S3_SPLIT_MAX : 1;
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
     const HostInst &H = h->hi[b];
@@ -624,7 +634,10 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     D.n_mg = ceil_div(D.n_mt, D.ctg_mg);
     D.ctg_tb = ceil_div(H.T, std::min(ntc_all, H.T));
     D.ctg_ntc = ceil_div(H.T, D.ctg_tb);
-    D.n_sb = ceil_div(H.M, NTHR / (h->opt.precision == QG_MIXED ? s3_split<float>() : s3_split<double>()));
+    // latency layouts of small plans on the mixed path (see `small` below): four threads per
+    // branch-period in stage 3, two CSR packs per warp in stage 4
+    D.s4p = small_mixed ? S4_PACKS : 1;
+    D.n_sb = ceil_div(H.M, NTHR / P.tab.s3q);
     D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
     D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
     D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
@@ -667,7 +680,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].M, NTHR), I[b].T, b, R_BRANCH);
   // bus balances: stage 1 on the mixed path (each branch end's flow recomputed in place: the balance
   // does not wait for the branch role); stage 2 on the FP64 path (from stage 1's flows)
-  const bool bal1 = h->opt.precision == QG_MIXED;
+  const bool bal1 = small_mixed;
   if (bal1)
     for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
@@ -706,7 +719,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   // of 32 (period, device) pairs, so that each warp's FP64 instructions serve 32 devices.  Sparse
   // mode: the adjoint solve follows stage 4, and stage 5 updates the devices (FP64 path: one warp of
   // pairs per block; mixed path: a full block of pairs), then the transformers.
-  const bool fuse = !P.sp && h->opt.precision == QG_MIXED;
+  const bool fuse = !P.sp && small_mixed;
+  P.tab.fuse = fuse ? 1 : 0;
   int gen_slot = 0;
   if (!P.sp)
     for (int b = 0; b < B; ++b) {
@@ -734,7 +748,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     }
     for (int b = 0; b < B; ++b) add_span(P.s5, ceil_div(I[b].X, NTHR), I[b].T, b, R_XF);
   }
-  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK * S4_PACKS), I[b].T, b, R_BUS);
+  for (int b = 0; b < B; ++b) add_span(P.s4, ceil_div(I[b].n_adj_pack, PACKS_PER_BLOCK * I[b].s4p), I[b].T, b, R_BUS);
   P.n_gen_slots = gen_slot;
   return QG_OK;
 }

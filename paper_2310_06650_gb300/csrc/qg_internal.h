@@ -19,12 +19,8 @@ constexpr int CT_BM = 64, CT_BK = 64;  // contingency tile: monitored branches x
 constexpr int DCF_BM = 32, DCF_TC = 8; // forward DC tile: 32 branches x 8 periods
 constexpr int PACK = 32;               // CSR entries per warp pack (rows never straddle packs)
 constexpr int PACKS_PER_BLOCK = NTHR / 32;
-constexpr int S4_PACKS = 2;            // branch-end CSR packs per warp in the bus gather of stage 4
-// threads per branch-period in stage 3 (its partial sums split over them): 4 on the mixed path; 1 on
-// the FP64 path, whose FP64 adjoint arithmetic would otherwise run in one lane of four (the FP64 pipe
-// takes about as long for a warp with few active lanes as for a full one)
-template <typename Real>
-__host__ __device__ constexpr int s3_split() { return sizeof(Real) == 4 ? 4 : 1; }
+constexpr int S4_PACKS = 2;            // branch-end CSR packs per warp in the bus gather of stage 4, at most
+constexpr int S3_SPLIT_MAX = 4;        // threads per branch-period in stage 3 (InstTab::s3q), at most
 
 // One instance of a batch.  Entity ids inside the kernels are global (offset by
 // bus0 / br0 / gen0 / zone0 / ctg0 / gb0); per-period arrays are period-major
@@ -40,7 +36,8 @@ struct Inst {
   int n_mt, n_kt;        // contingency tiles along monitored branches / outages
   int ctg_mg, n_mg;      // monitored-branch tiles per contingency block, and the number of such groups
   int ctg_tb, ctg_ntc;   // periods per contingency block, and the number of period chunks
-  int n_sb;              // stage-3 branch blocks per period (NTHR / s3_split branches each)
+  int n_sb;              // stage-3 branch blocks per period (NTHR / InstTab::s3q branches each)
+  int s4p;               // branch-end CSR packs per warp in stage 4 (1 or S4_PACKS)
   int bal0, n_bal_pack;  // first entry / number of warp packs of the balance CSR
   int adj0, n_adj_pack;  // same for the branch-end adjoint CSR
   long long x0;          // first variable of this instance
@@ -92,6 +89,8 @@ struct Spans {
 struct InstTab {
   Inst I[MAXB];
   int n_inst;
+  int fuse;  // 1: stage 4's warps update the devices (the last stage); 0: stage 5 does
+  int s3q;   // threads per branch-period in stage 3 (1 or S3_SPLIT_MAX; the kernel's template argument)
 };
 
 // Double-FP32 value (unevaluated sum hi + lo) carrying the FP64-accurate DC

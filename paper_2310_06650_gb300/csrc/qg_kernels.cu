@@ -747,14 +747,12 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   Real *s_gz = s_f64k + (F64 ? TBM * CT_BK : 0);      // [TCH][8][BK] score column sums (screening only)
   Real *s_za = s_gz + (d.score ? TCH * 8 * CT_BK : 0);  // [TB][BK] scores over the group (screening only)
   Real *s_q2 = s_za + (d.score ? TBM * CT_BK : 0);    // [TB][BM] qmax2 of the monitored branch
-  Real *s_w = s_q2 + TBM * CT_BM;                     // [TB] d_t c_s beta of each period
   const bool score = d.score != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rq = threadIdx.x >> 4, cq = threadIdx.x & 15;
   const int kc = k0 + cq * 4;  // first of this thread's four outages
   __shared__ int s_hit[ctg_tch<Real>()];  // per period of the chunk: some row of the tile has a partial
   if (threadIdx.x < TCH) s_hit[threadIdx.x] = 0;
-  if (threadIdx.x < TB) s_w[threadIdx.x] = d.dt[I.tp0 + t0 + threadIdx.x] * d.c_s * hp.beta;
   for (int e = threadIdx.x; e < TCH * CT_BM; e += NTHR) s_gm[e] = s_gq[e] = 0;
   for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gk[e] = 0;
   if (score)
@@ -871,7 +869,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         // path, >= 0 with the margin (a positive exact sum cannot round to a negative one)
         if (!__any_sync(0xffffffffu, F64 ? mx >= 0.f : mx > 0.f)) continue;
         // a (candidate) post-contingency overload in this warp
-        const Real w = s_w[tl];
+        const Real w = __ldg(d.dt + I.tp0 + t0 + tl) * d.c_s * hp.beta;
         Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
         if (F64 ? mx >= 0.f : mx > 0.f) {
 #pragma unroll
@@ -992,7 +990,6 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
                                              const Real *__restrict__ x, int slot0) {
   const Where w = locate(S);
   const Inst &I = tab.I[tab.n_inst == 1 ? 0 : w.inst];  // one instance: no wait on the span search
-  const int slot = d.slot_map[slot0 + blockIdx.x];  // issued first: it is not needed until the end
   Obj3<Dc> acc = obj3<Dc>(-1);
   if (w.role == R_BUS) {  // FP64 path
     acc.id[0] = T_ZP;
@@ -1002,7 +999,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
     acc.id[0] = T_ZCTG;
     s2_ctg(d, I, w.sub, acc, hparams(d));
   }
-  write_obj(d.objp, slot, acc);
+  write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1061,7 +1058,7 @@ __device__ void fold_slots(const Dev<Real, Dc> &d, const Inst &I, int r) {
   }
 }
 
-template <typename Real, typename Dc>
+template <typename Real, typename Dc, int SPLIT>
 __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x) {
@@ -1073,10 +1070,10 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
     return;
   }
   const int t = w.t;
-  // s3_split threads per branch: each sums every s3_split-th partial, then a fixed-order shuffle
+  // SPLIT threads per branch: each sums every SPLIT-th partial, then a fixed-order shuffle
   // tree combines them (the same bits in every thread of the group); the group's first thread
   // loads the branch's flows and adjoints meanwhile and finishes the branch
-  constexpr int SPLIT = s3_split<Real>();
+
   const int q = threadIdx.x % SPLIT;
   const int j = w.sub * (NTHR / SPLIT) + threadIdx.x / SPLIT;
   const bool on = j < I.M;
@@ -1139,12 +1136,13 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s3(const __
       }
     }
     if (kx >= 0) {
-#pragma unroll 4
+#pragma unroll 8
       for (int mg = q; mg < I.n_mg; mg += SPLIT) gk += d.pk[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
       if (d.score)
         for (int mg = q; mg < I.n_mg; mg += SPLIT) zk += d.pz[I.pk0 + ((long long)mg * I.T + t) * I.K + kx];
     }
   }
+#pragma unroll
 #pragma unroll
   for (int o = 1; o < SPLIT; o <<= 1) {
     gF += __shfl_xor_sync(0xffffffffu, gF, o);
@@ -1254,7 +1252,7 @@ __device__ AdamCoef<Real> adam_coef(const Dev<Real, Dc> &d) {
 template <typename Real, typename Dc, bool ADAM>
 __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Real *__restrict__ x,
                        const AdamCoef<Real> &ac) {
-  // S4_PACKS consecutive packs per warp: the loads of all of them are issued together
+  // I.s4p (<= S4_PACKS) consecutive packs per warp: the loads of all of them are issued together
   Real s_x[S4_PACKS][2], s_m[S4_PACKS][2], s_v[S4_PACKS][2], s_lo[S4_PACKS][2], s_hi[S4_PACKS][2];
   int code[S4_PACKS], row[S4_PACKS];
   long long kv[S4_PACKS];
@@ -1263,8 +1261,8 @@ __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Re
   // branch-end adjoints (no earlier stage of this evaluation writes x, m, v or the box)
 #pragma unroll
   for (int u = 0; u < S4_PACKS; ++u) {
-    const int pk = (sub * PACKS_PER_BLOCK + (threadIdx.x >> 5)) * S4_PACKS + u;
-    on[u] = pk < I.n_adj_pack;
+    const int pk = (sub * PACKS_PER_BLOCK + (threadIdx.x >> 5)) * I.s4p + u;
+    on[u] = u < I.s4p && pk < I.n_adj_pack;
     const int e = I.adj0 + (on[u] ? pk : 0) * PACK + (threadIdx.x & 31);
     code[u] = d.adj_code[e];
     row[u] = on[u] ? d.adj_row[e] : -1;
@@ -1679,15 +1677,16 @@ __device__ void s4_sdca(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub) 
 //   Eq. 2nd_lin_sys_phase),
 // lanes striding over the branches, a fixed-order shuffle reduction, and the sum broadcast to the
 // warp; then (mixed path) its lanes update the devices at the bus, one per lane, or lane 0 the
-// transformer.  The FP64 path stores the products for stage 5 instead, which updates 32 devices per
-// warp: the FP64 pipe takes about as long for a warp with one active lane as for a full one.
-template <typename Real, typename Dc, bool ADAM>
+// transformer (plans whose tab.fuse is set: small ones on the mixed path).  Otherwise the products are
+// stored for stage 5, which updates 32 (FP64 path) or 256 devices per block: the FP64 pipe takes
+// about as long for a warp with one active lane as for a full one, and large plans would get one
+// objective slot per stage-4 block.
+template <typename Real, typename Dc, bool ADAM, bool FUSE>
 __device__ void s4_gbus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const AdamCoef<Real> &ac,
                         Obj3<Dc> &acc, Real *__restrict__ x) {
   const int lane = threadIdx.x & 31;
   const int c = sub * (NTHR / 32) + (threadIdx.x >> 5);
   const bool col = c < I.Gc;
-  constexpr bool FUSE = sizeof(Real) == 4;
   // data no earlier stage writes: the bus's first 32 devices (more take further rounds after the wait)
   int q0 = 0, q1 = 0;
   if (FUSE && col && c < I.Gb) {
@@ -1749,7 +1748,7 @@ __device__ void s4_gbus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, c
 // dense DC mode also the adjoint DC products with the device and transformer updates (the last
 // stage: its last block reduces the objective); in the sparse mode the right-hand side of the
 // adjoint solve.
-template <typename Real, typename Dc, bool ADAM>
+template <typename Real, typename Dc, bool ADAM, bool FUSE>
 __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              Real *__restrict__ x) {
@@ -1763,10 +1762,10 @@ __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, D
     s4_sdca(d, I, w.t, w.sub);
   } else {  // R_GBUS
     Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
-    s4_gbus<Real, Dc, ADAM>(d, I, w.t, w.sub, ac, acc, x);
-    if (sizeof(Real) == 4) write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
+    s4_gbus<Real, Dc, ADAM, FUSE>(d, I, w.t, w.sub, ac, acc, x);
+    if (FUSE) write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
   }
-  if (!d.sp && sizeof(Real) == 4) finish_eval<Real, Dc, ADAM>(d, tab, ac.step);  // the last stage
+  if (FUSE) finish_eval<Real, Dc, ADAM>(d, tab, ac.step);  // the last stage
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2048,7 +2047,7 @@ size_t ctg_smem_bytes(int TB, bool score) {
          sizeof(Real) * ((size_t)TB * CT_BK + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
                          (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0) +
                          (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0) +
-                         (size_t)TB * CT_BM + CT_BM + (size_t)TB);
+                         (size_t)TB * CT_BM + CT_BM);
 }
 
 // Record a timing event on s; inside stream capture it becomes an external event node.
@@ -2126,10 +2125,18 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
   if (P.s2.n_blocks > 0)  // no contingencies: nothing for stage 2
     go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB, d.score != 0), d, P.tab, P.s2, (const Real *)x, o2);
   mark(ev, 2, s);
-  go(k_s3<Real, Dc>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
+  if (P.tab.s3q > 1) go(k_s3<Real, Dc, S3_SPLIT_MAX>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
+  else go(k_s3<Real, Dc, 1>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
   mark(ev, 3, s);
-  if (adam) go(k_s4<Real, Dc, true>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
-  else go(k_s4<Real, Dc, false>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
+  // stage 4 with the device updates (small plans on the mixed path) or without them (a separate
+  // instantiation: the fused role's registers would cost the lean one its occupancy)
+  if (P.tab.fuse) {
+    if (adam) go(k_s4<Real, Dc, true, true>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
+    else go(k_s4<Real, Dc, false, true>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
+  } else {
+    if (adam) go(k_s4<Real, Dc, true, false>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
+    else go(k_s4<Real, Dc, false, false>, P.s4.n_blocks, 0, d, P.tab, P.s4, x);
+  }
   if (P.sp) {
     // sparse mode: adjoint solve eta = Yhat^-1 w at the generator buses, and 1^T eta
     const Inst &I = P.tab.I[0];
