@@ -301,10 +301,10 @@ int qg_set_state(qg_ctx *h, const void *buf, int64_t size);
  * stages in launch order (s1: branch flows, bus balances, zonal sums and base
  * DC flows; s2: contingencies; s3: contingency sums and branch adjoints; s4:
  * bus adjoint gather and adjoint DC products, and on the mixed path with the
- * dense DC products also the device gradients and the objective, s5 then
- * being 0; s5: device gradients and the objective; with the sparse DC solver
- * s1 includes the forward solve and s4 the adjoint solve), then that of a
- * stand-alone qg_adam_step if one
+ * dense DC products also the device gradients; s5: the device gradients where
+ * stage 4 does not update them, then the closing kernel that sums the
+ * objective; with the sparse DC solver s1 includes the forward solve and s4
+ * the adjoint solve), then that of a stand-alone qg_adam_step if one
  * followed, up to cap entries; returns how many it wrote or a negative error
  * code.  Waits for those events. */
 int qg_set_profiling(qg_ctx *h, int on);
@@ -353,11 +353,12 @@ int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]);
 int qg_round_batch(qg_ctx *h, void *x, double frac, int64_t *n_fixed, int64_t *n_binaries);
 int qg_round_reset(qg_ctx *h);
 
-/* Kernel launches of one evaluation (with or without the fused Adam update) on this handle: 4
- * stage kernels on the mixed path with the dense DC products (stage 4 updates the devices), 5 on
- * the FP64 path, 5 plus 3 to 7 solve kernels with the sparse DC solver; one fewer without
- * contingencies (a qg_solve graph replay without a trace adds one closing kernel).  Returns a
- * negative error code for a NULL handle. */
+/* Kernel launches of one evaluation (with or without the fused Adam update) on this handle, the
+ * closing kernel that sums the objective included: 4 stage kernels on the mixed path with the
+ * dense DC products (stage 4 updates the devices), 5 on the FP64 path, 5 plus 3 to 7 solve kernels
+ * with the sparse DC solver, one fewer without contingencies; plus 1.  qg_solve without a trace
+ * runs its iterations in graphs of 8 that share one closing kernel, so there an iteration costs
+ * one launch less, plus 1/8.  Returns a negative error code for a NULL handle. */
 int32_t qg_launches_per_eval(const qg_ctx *h);
 
 const char *qg_last_error(const qg_ctx *h);
@@ -365,8 +366,8 @@ const char *qg_last_error(const qg_ctx *h);
 /* ---------------------------------------------------------------------------------------------
  * Learned warm start (an AI-systems addition; the paper's future-work remark in Sec. V motivates
  * it): an MLP  Y = W3 relu(W2 relu(W1 X + b1) + b2) + b3  mapping a load profile to an initial
- * point, trained on the GPU by the library's own BF16 tensor-core GEMMs (FP32 accumulation) and
- * an Adam step.  GEMM operands (X, the weights, the hidden activations, and the back-propagated
+ * point, trained on the GPU by the library's own BF16 tensor-core GEMMs (tcgen05.mma with a TMEM
+ * accumulator and TMA-staged operands; FP32 accumulation) and an Adam step.  GEMM operands (X, the weights, the hidden activations, and the back-propagated
  * dY, dZ2, dZ1) are rounded to BF16 where they enter a GEMM; the master weights, biases, bias
  * gradients and Adam moments are FP32.  Parameters are laid out as W1 (H x I, row-major), b1
  * (H), W2 (H x H), b2, W3 (O x H), b3 (O).  All pointers are device pointers; x is batch x I
@@ -374,6 +375,8 @@ const char *qg_last_error(const qg_ctx *h);
  * ------------------------------------------------------------------------------------------- */
 typedef struct qg_mlp qg_mlp;
 
+/* max_batch <= 64 (the batch is one 64-column tile of the tensor-core GEMMs); QG_ERR_UNSUPPORTED
+ * above that, and when the driver does not provide the TMA descriptor encoder. */
 int qg_mlp_create(qg_mlp **out, int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, uint64_t seed);
 void qg_mlp_destroy(qg_mlp *m);
 int64_t qg_mlp_num_params(const qg_mlp *m);
@@ -394,6 +397,12 @@ int qg_mlp_get_params(qg_mlp *m, float *w);
 int qg_mlp_set_params(qg_mlp *m, const float *w);
 int qg_mlp_get_grads(qg_mlp *m, float *g);
 const char *qg_mlp_last_error(const qg_mlp *m);
+
+/* Synchronizes the MLP's stream and reports whether a tensor-core GEMM since the handle was
+ * created gave up on a pipeline wait (each wait is bounded at 1 s; the block then drains its
+ * copies in flight, frees its tensor memory and exits, leaving its output invalid): QG_ERR_CUDA
+ * with a message if so, else QG_OK. */
+int qg_mlp_check(qg_mlp *m);
 
 /* Build identification: major*10000 + minor*100 + patch. */
 int qg_version(void);

@@ -1184,7 +1184,8 @@ bool mixed(const qg_ctx *h) { return h->opt.precision == QG_MIXED; }
 // One evaluation; with adam, the projected Adam update is fused into stages 4 and 5 using the
 // handle's moments and the given hyper-parameters.
 // step_off: this iteration's place in a graph of several (it reads step + step_off); defer: leave
-// the objective sum and the step count to a closing run_finish (fused iterations without a trace).
+// the objective sum and the step count to a run_finish after the graph's last iteration (fused
+// iterations without a trace); otherwise the evaluation ends with its own closing kernel.
 int run_eval(qg_ctx *h, const void *x, bool adam, double lr, double b1, double b2, double *trace, int trace_len,
              const double *sched = nullptr, int sched_len = 0, int step_off = 0, bool defer = false) {
   cudaEvent_t *ev = h->profiling ? h->ev : nullptr;
@@ -1193,14 +1194,14 @@ int run_eval(qg_ctx *h, const void *x, bool adam, double lr, double b1, double b
     Dev<float, df32> d = h->d32;
     d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
     d.trace = trace; d.trace_len = trace_len; d.sched = sched; d.sched_len = sched_len;
-    d.step_off = step_off; d.defer_final = defer ? 1 : 0;
-    e = launch_eval<float, df32>(d, h->plan, x, adam, h->stream, ev);
+    d.step_off = step_off;
+    e = launch_eval<float, df32>(d, h->plan, x, adam, !defer, h->stream, ev);
   } else {
     Dev<double, double> d = h->d64;
     d.lr = lr; d.b1 = b1; d.b2 = b2; d.aeps = h->opt.adam_eps; d.paper_eps = h->opt.adam_paper_eps;
     d.trace = trace; d.trace_len = trace_len; d.sched = sched; d.sched_len = sched_len;
-    d.step_off = step_off; d.defer_final = defer ? 1 : 0;
-    e = launch_eval<double, double>(d, h->plan, x, adam, h->stream, ev);
+    d.step_off = step_off;
+    e = launch_eval<double, double>(d, h->plan, x, adam, !defer, h->stream, ev);
   }
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("evaluation launch: ") + cudaGetErrorString(e));
   return QG_OK;
@@ -1427,10 +1428,9 @@ int eval_noalloc(qg_ctx *h, Dev<Real, Dc> d, const void *x, double *obj, void *g
   d.g = static_cast<Real *>(g);
   d.trace = nullptr;
   d.trace_len = 0;
-  // the stage-5 completion counter must start at zero (the rest is fully written before it is read)
-  CUDA_TRY(h, cudaMemsetAsync(d.ticket, 0, sizeof(unsigned int), h->stream));
+  // the closing kernel reads and rewrites the step counter (the rest is fully written before it is read)
   CUDA_TRY(h, cudaMemsetAsync(d.step, 0, sizeof(long long), h->stream));
-  cudaError_t e = launch_eval<Real, Dc>(d, h->plan, x, false, h->stream, nullptr);
+  cudaError_t e = launch_eval<Real, Dc>(d, h->plan, x, false, true, h->stream, nullptr);
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("evaluation launch: ") + cudaGetErrorString(e));
   return QG_OK;
 }
@@ -2061,8 +2061,9 @@ int32_t qg_launches_per_eval(const qg_ctx *h) {
   if (!h) return QG_ERR_INVALID_ARG;
   const Plan &P = h->plan;
   const int s2 = P.s2.n_blocks > 0 ? 1 : 0;  // no contingencies: no stage 2
-  if (!P.sp) return 3 + s2 + (P.s5.n_blocks > 0 ? 1 : 0);  // the mixed path's dense mode updates the devices in stage 4
-  return 4 + s2 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0);
+  // + 1: the closing kernel (the mixed path's dense mode updates the devices in stage 4)
+  if (!P.sp) return 3 + s2 + (P.s5.n_blocks > 0 ? 1 : 0) + 1;
+  return 4 + s2 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0) + 1;
 }
 
 int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t shape[2]) {

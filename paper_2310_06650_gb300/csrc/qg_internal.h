@@ -200,11 +200,9 @@ struct Dev {
   const int *slot_map;                // [n_obj12] stage-1/2 block (launch order) -> slot
   double *obj, *terms;                // [n_inst], [n_inst][N_TERMS]
   Real *g;                            // gradient [n_x]
-  unsigned int *ticket;               // last-block counter of stage 5
-  long long *step;                    // Adam step counter
+  unsigned int *ticket;               // last-block counter of the stand-alone Adam kernel
+  long long *step;                    // Adam step counter (written by closing kernels and that kernel)
   int step_off;                       // iteration k of a graph of several: it reads step + k
-  int defer_final;                    // 1: stage 5 leaves the objective sum and the step count to
-                                      // the graph's closing kernel (fused iterations without a trace)
   // fused Adam (qg_solve): moments and hyper-parameters
   Real *am, *av;
   double lr, b1, b2, aeps;
@@ -235,15 +233,18 @@ struct Plan {
   int sp_bwa_blocks;   // k_sp_back adjoint pass
 };
 
+// One evaluation (with adam, the fused projected Adam update); with close, ended by the closing
+// kernel (the objective sum; step += 1 with adam), else the objective is left in the slots for a
+// later launch_finish.
 template <typename Real, typename Dc>
-cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *x, bool adam, cudaStream_t s,
-                        cudaEvent_t *ev);
+cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *x, bool adam, bool close,
+                        cudaStream_t s, cudaEvent_t *ev);
 
 template <typename Real, typename Dc>
 cudaError_t prepare_eval(int maxTB, bool score);
 
-// Closing kernel of a graph of n fused iterations with deferred objective sums: the last iteration's
-// objective, then step += n.
+// Closing kernel of a graph of n fused iterations whose evaluations were launched without one: the
+// last iteration's objective, then step += n.
 template <typename Real, typename Dc>
 cudaError_t launch_finish(const Dev<Real, Dc> &d, const Plan &P, int n, cudaStream_t s);
 

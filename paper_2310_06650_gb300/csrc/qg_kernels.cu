@@ -239,6 +239,29 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 
 __device__ __forceinline__ float f_nan() { return __int_as_float(0x7fc00000); }
 
+// Two FP32 values in one 64-bit register pair (x in the low half) and the sm_100+ paired FMA on
+// them: each half is rounded exactly as a scalar fma.rn of the same operands would be.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// max of three FP32 values (sm_100+); like fmaxf, a NaN operand is ignored
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 struct Where {
   int role, inst, t, sub;
 };
@@ -710,9 +733,10 @@ __host__ __device__ constexpr int ctg_tch() { return 8; }
 // monitored-branch tiles of one group (64 branches each) and one chunk of periods:
 //   F[t,m,k] = f[t,m] + L[m,k] f[t,k],   s = sqrt(F^2 + qmax2[t,m]),
 //   z += w sigma_s(s - s_ctg_m),  dz/dF = w sigma' F / s.
-// Thread (row quad rq, column quad cq) holds a 4 x 4 piece of the line-outage tile in registers;
-// per period it reads f, qmax2 - s_ctg^2 of its rows and f_k of its columns as three 128-bit
-// shared loads and screens its 16 elements in FP32 with two FMAs and a max each: an element can
+// Thread (row quad rq, column quad cq) holds a 4 x 4 piece of the line-outage tile in registers,
+// as pairs of rows per column; per period it reads f, qmax2 - s_ctg^2 of its rows and f_k of its
+// columns (stored twice, as the pair {f_k, f_k}) as four 128-bit shared loads and screens its 16
+// elements in FP32: two paired FMAs per two elements and a three-input max tree; an element can
 // only be overloaded if F^2 + qmax2 - s_ctg^2 > 0.  The FP64 path recomputes candidates exactly
 // from the FP64 block; its screen adds a margin derived from a bound on the FP32 errors, so every
 // element whose FP64 value is over the limit is a candidate (the bound is at the screen's margin
@@ -729,15 +753,16 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
   const int T = I.T, TBM = I.ctg_tb;
-  const int per_chunk = I.n_mg * I.n_kt;
-  const int tci = sub / per_chunk, rem = sub % per_chunk, mg = rem / I.n_kt, kt = rem % I.n_kt;
+  // the period chunks of one (group, outage tile) are adjacent blocks: they run together and read
+  // the same line-outage rows, the later ones from L2
+  const int tci = sub % I.ctg_ntc, rem = sub / I.ctg_ntc, mg = rem / I.n_kt, kt = rem % I.n_kt;
   const int t0 = tci * TBM, TB = min(TBM, T - t0);
   const int k0 = kt * CT_BK;
   const int mt0 = mg * I.ctg_mg, mt1 = min(I.n_mt, mt0 + I.ctg_mg);
   float *s_fm = reinterpret_cast<float *>(smem_raw);  // [TB][BM] base flow of the monitored branch
   float *s_qs = s_fm + TBM * CT_BM;                   // [TB][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
-  float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK] base flow of the outaged branch
-  Real *s_s2 = reinterpret_cast<Real *>(s_fk + TBM * CT_BK);  // [2][BM] s_ctg^2, then s_ctg
+  float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK][2] base flow of the outaged branch, twice
+  Real *s_s2 = reinterpret_cast<Real *>(s_fk + 2 * TBM * CT_BK);  // [2][BM] s_ctg^2, then s_ctg
   Real *s_gm = s_s2 + 2 * CT_BM;                      // [TCH][BM]
   Real *s_gq = s_gm + TCH * CT_BM;                    // [TCH][BM]
   Real *s_gk = s_gq + TCH * CT_BM;                    // [TCH][8][BK]
@@ -773,6 +798,11 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         for (int j = 0; j < 4; ++j) L[i][j] = f_nan();
       }
     }
+    f32x2 Lp[2][4];  // {L[2h][j], L[2h + 1][j]}
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Lp[h][j] = pack2(L[2 * h][j], L[2 * h + 1][j]);
     // staging of one 64-row tile's per-row data (the flows, q_max^2 - s_ctg^2 and q_max^2 of the
     // monitored branches) for entry e of [TB][64]
     auto stage_m = [&](int e) {
@@ -815,7 +845,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           if (F64) f64 = d.fk[idx];
         }
         stage_m(e);
-        s_fk[tt * CT_BK + c] = f;
+        *reinterpret_cast<float2 *>(s_fk + 2 * (tt * CT_BK + c)) = make_float2(f, f);
         if (F64) s_f64k[tt * CT_BK + c] = f64;
         s_ga[tt * CT_BK + c] = 0;
         if (score) s_za[tt * CT_BK + c] = 0;
@@ -839,32 +869,40 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         const int tl = tc0 + tt;
         const float4 fm4 = *reinterpret_cast<const float4 *>(s_fm + tl * CT_BM + rq * 4);
         const float4 qs4 = *reinterpret_cast<const float4 *>(s_qs + tl * CT_BM + rq * 4);
-        const float4 fk4 = *reinterpret_cast<const float4 *>(s_fk + tl * CT_BK + cq * 4);
+        const float4 fka = *reinterpret_cast<const float4 *>(s_fk + 2 * (tl * CT_BK + cq * 4));
+        const float4 fkb = *reinterpret_cast<const float4 *>(s_fk + 2 * (tl * CT_BK + cq * 4) + 4);
         const float fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w};
         float qs[4] = {qs4.x, qs4.y, qs4.z, qs4.w};
-        const float fk[4] = {fk4.x, fk4.y, fk4.z, fk4.w};
+        const f32x2 fkd[4] = {pack2(fka.x, fka.y), pack2(fka.z, fka.w), pack2(fkb.x, fkb.y), pack2(fkb.z, fkb.w)};
         if (F64) {
           // the rest of the screen's margin: the FP32 value of F = f_m + L f_k is off by at most
           // 3.0001 u (|f_m| + |L||f_k|) (u = 2^-24; three roundings: L, f_k, f_m to FP32 and the fma),
           // so |F32^2 - F^2| <= 6.0003 u A^2 with A <= Ahat = |f_m| + max|L| max|f_k| over the
           // thread's columns; 2^-21 Ahat^2 = 8 u Ahat^2 covers it and the FP64 rounding of the exact test
-          const float fkq = fmaxf(fmaxf(fabsf(fk[0]), fabsf(fk[1])), fmaxf(fabsf(fk[2]), fabsf(fk[3])));
+          const float fkq = fmaxf(fmaxf(fabsf(fka.x), fabsf(fka.z)), fmaxf(fabsf(fkb.x), fabsf(fkb.z)));
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float ah = __fmaf_rn(Lrow[i], fkq, fabsf(fm[i]));
             qs[i] = __fadd_rn(qs[i], __fmul_rn(__fmul_rn(ah, ah), 0x1p-21f));
           }
         }
-        float F[4][4];
-        float mr[4];  // one max per row, combined as a tree: a short dependency chain
+        const f32x2 fmp[2] = {pack2(fm[0], fm[1]), pack2(fm[2], fm[3])};
+        const f32x2 qsp[2] = {pack2(qs[0], qs[1]), pack2(qs[2], qs[3])};
+        // F = fma(L, f_k, f_m), y = fma(F, F, qmax2 - s_ctg^2): two paired FMAs per two rows
+        float F[4][4], y[4][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) F[i][j] = __fmaf_rn(L[i][j], fk[j], fm[i]);
-          mr[i] = fmaxf(fmaxf(__fmaf_rn(F[i][0], F[i][0], qs[i]), __fmaf_rn(F[i][1], F[i][1], qs[i])),
-                        fmaxf(__fmaf_rn(F[i][2], F[i][2], qs[i]), __fmaf_rn(F[i][3], F[i][3], qs[i])));
-        }
-        const float mx = fmaxf(fmaxf(mr[0], mr[1]), fmaxf(mr[2], mr[3]));  // NaN operands are ignored
+          for (int j = 0; j < 4; ++j) {
+            const f32x2 Fh = fma2(Lp[h][j], fkd[j], fmp[h]);
+            unpack2(Fh, F[2 * h][j], F[2 * h + 1][j]);
+            unpack2(fma2(Fh, Fh, qsp[h]), y[2 * h][j], y[2 * h + 1][j]);
+          }
+        // the largest of the 16 (NaN operands are ignored), as a three-input max tree of depth 3
+        const float a0 = fmax3(y[0][0], y[0][1], y[0][2]), a1 = fmax3(y[0][3], y[1][0], y[1][1]);
+        const float a2 = fmax3(y[1][2], y[1][3], y[2][0]), a3 = fmax3(y[2][1], y[2][2], y[2][3]);
+        const float a4 = fmax3(y[3][0], y[3][1], y[3][2]);
+        const float mx = fmaxf(fmax3(a0, a1, a2), fmax3(a3, a4, y[3][3]));
         // a candidate: F^2 + qmax2 - s_ctg^2 > 0 (mixed path: its classification), or, on the FP64
         // path, >= 0 with the margin (a positive exact sum cannot round to a negative one)
         if (!__any_sync(0xffffffffu, F64 ? mx >= 0.f : mx > 0.f)) continue;
@@ -877,24 +915,36 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
             const int mm = rq * 4 + i;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              const float y = __fmaf_rn(F[i][j], F[i][j], qs[i]);
-              if (!(F64 ? y >= 0.f : y > 0.f)) continue;  // NaN (pad, outaged branch) fails too
+              if (!(F64 ? y[i][j] >= 0.f : y[i][j] > 0.f)) continue;  // NaN (pad, outaged branch) fails too
               const Real q2 = s_q2[tl * CT_BM + mm];
-              Real Fx, Lx;
+              Real Fx, Lx, sv, dd;
               if (F64) {
                 Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.Kp + kc + j];
                 Fx = s_f64m[tl * CT_BM + mm] + Lx * s_f64k[tl * CT_BK + cq * 4 + j];
                 if (Fx * Fx + q2 - s_s2[mm] <= Real(0)) continue;
+                sv = dsqrt(Fx * Fx + q2);
+                Real val, der;
+                soft_relu(sv - s_s2[CT_BM + mm], eps, val, der);
+                obj += w * (val - eps);
+                zc[j] += w * (val - eps);
+                dd = w * der / sv;  // dz/dF = w sigma' F / s
               } else {
-                Lx = (Real)L[i][j];
-                Fx = (Real)F[i][j];
+                // mixed path: s = sqrt(F^2 + qmax2) and the soft-ReLU through reciprocal square
+                // roots (a few units in the last place, below the FP32 error of F itself)
+                float l0, l1;
+                unpack2(Lp[i >> 1][j], l0, l1);
+                Lx = (i & 1) ? l1 : l0;
+                Fx = F[i][j];
+                const float a2 = __fmaf_rn(F[i][j], F[i][j], (float)q2);
+                const float ra = rsqrtf(a2);
+                const float u = fmaxf(__fmaf_rn(a2, ra, -(float)s_s2[CT_BM + mm]), 0.f);
+                const float b2 = __fmaf_rn(u, u, (float)(eps * eps));
+                const float rb = rsqrtf(b2);
+                const float val = b2 * rb;  // sqrt(u^2 + eps^2)
+                obj += w * (val - eps);
+                zc[j] += w * (val - eps);
+                dd = w * (u * rb) * ra;  // w sigma'(s - s_ctg) / s
               }
-              const Real sv = dsqrt(Fx * Fx + q2);
-              Real val, der;
-              soft_relu(sv - s_s2[CT_BM + mm], eps, val, der);
-              obj += w * (val - eps);
-              zc[j] += w * (val - eps);
-              const Real dd = w * der / sv;  // dz/dF = w sigma' F / s
               gm[i] += dd * Fx;
               gk[j] += dd * Fx * Lx;
               gq[i] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
@@ -902,21 +952,26 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           }
         }
         // row sums across the 16 column quads of each half-warp, when some row of this warp has an
-        // overload (the buffers hold zeros otherwise)
+        // overload (the buffers hold zeros otherwise): a reduce-scatter of the thread's 8 values
+        // (gm, gq of its 4 rows); each exchange halves what a lane holds, so after three of them
+        // lane pair (2v, 2v + 1) of the half-warp holds value v, and a fourth completes its sum
         if (__any_sync(0xffffffffu, (gq[0] != Real(0)) | (gq[1] != Real(0)) | (gq[2] != Real(0)) | (gq[3] != Real(0)))) {
+          const bool h8 = cq & 8, h4 = cq & 4, h2 = cq & 2;
+          Real r4[4], r2[2];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int q = 0; q < 4; ++q) {  // values 0-3: gm, 4-7: gq; lanes with bit 3 keep 4-7
+            const Real lo = gm[q], hi = gq[q];
+            r4[q] = (h8 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h8 ? lo : hi, 8);
+          }
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-              gm[i] += __shfl_xor_sync(0xffffffffu, gm[i], o);
-              gq[i] += __shfl_xor_sync(0xffffffffu, gq[i], o);
-            }
-          if (cq == 0)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              s_gm[tt * CT_BM + rq * 4 + i] = gm[i];
-              s_gq[tt * CT_BM + rq * 4 + i] = gq[i];
-            }
+          for (int q = 0; q < 2; ++q)  // bit 2 keeps entries 2-3 of the four
+            r2[q] = (h4 ? r4[q + 2] : r4[q]) + __shfl_xor_sync(0xffffffffu, h4 ? r4[q] : r4[q + 2], 4);
+          Real r1 = (h2 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? r2[0] : r2[1], 2);
+          r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+          if (!(cq & 1)) {  // value v = 4 h8 + 2 h4 + h2: row v & 3 of gm (v < 4) or gq
+            const int v = cq >> 1;
+            ((v & 4) ? s_gq : s_gm)[tt * CT_BM + rq * 4 + (v & 3)] = r1;
+          }
           if (lane == 0) s_hit[tt] = 1;
         }
         // column sums across the two row quads of this warp, then per warp through shared memory
@@ -1322,7 +1377,7 @@ __device__ void s4_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, Re
 // stage 5: generator gradients (+ Adam), objective reduction, step counter
 // ---------------------------------------------------------------------------------------------
 
-// Objective reduction, level 2, run by the last block of stage 5: per instance, the slots of its
+// Objective reduction, level 2, run by the closing kernel: per instance, the slots of its
 // device blocks and of its fold blocks in fixed order (read through L2: other blocks wrote them),
 // plus the closed-form soft-ReLU floor of the contingency term.
 template <typename Real, typename Dc>
@@ -1537,30 +1592,6 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
   }
 }
 
-// End of an evaluation: the last block of the launch to finish (ticket) reduces the objective and
-// advances the Adam step counter.  Every block of the launch calls this (all its threads), after
-// its last read of the step counter.
-template <typename Real, typename Dc, bool ADAM>
-__device__ void finish_eval(const Dev<Real, Dc> &d, const InstTab &tab, long long step) {
-  if (d.defer_final) return;  // the graph's closing kernel sums the objective and counts the steps
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // one acquire-release ticket: releases this block's slot (written by thread 0, the block's other
-    // writes are not read in this launch) and, in the last block, acquires every other block's
-    unsigned int prev;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(d.ticket) : "memory");
-    last = prev == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  final_reduce(d, tab);
-  if (threadIdx.x == 0) {  // the next launch sees these at the kernel boundary
-    *d.ticket = 0;
-    if (ADAM) *d.step = step + 1;
-  }
-}
-
 // Transformer x of period t: dPhi/dtau from the AC terms (stage 3), and dPhi/dphi = -(the AC
 // adjoint of delta) + b_sr dPhi/db, where dPhi/db = dz/dp_x - (E_hat eta)_x is the contingency
 // term's phase-shift gradient (Eq. 2nd_lin_sys_phase plus the direct term of p = f + b);
@@ -1638,7 +1669,6 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
     }
     write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
   }
-  finish_eval<Real, Dc, ADAM>(d, tab, ac.step);
 }
 
 // Right-hand side of the adjoint solve in the sparse mode (Eq. 2nd_lin_sys): w = E_hat^T Y_x dz/df
@@ -1765,7 +1795,6 @@ __global__ void __launch_bounds__(NTHR) k_s4(const __grid_constant__ Dev<Real, D
     s4_gbus<Real, Dc, ADAM, FUSE>(d, I, w.t, w.sub, ac, acc, x);
     if (FUSE) write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
   }
-  if (FUSE) finish_eval<Real, Dc, ADAM>(d, tab, ac.step);  // the last stage
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -2043,7 +2072,7 @@ template <typename Real>
 size_t ctg_smem_bytes(int TB, bool score) {
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
-  return sizeof(float) * (size_t)TB * (2 * CT_BM + CT_BK) +
+  return sizeof(float) * (size_t)TB * (2 * CT_BM + 2 * CT_BK) +
          sizeof(Real) * ((size_t)TB * CT_BK + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
                          (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0) +
                          (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0) +
@@ -2077,10 +2106,13 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cud
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// Closing kernel of an evaluation, or of a graph of n fused iterations: one block sums the
+// objective of the last one from the slots the stage kernels left, then step += n (n = 0 for a
+// plain evaluation).
 template <typename Real, typename Dc>
 __global__ void __launch_bounds__(NTHR) k_finish(const __grid_constant__ Dev<Real, Dc> d,
                                                  const __grid_constant__ InstTab tab, int n) {
-  const long long step = *d.step;  // only closing kernels write it in this mode
+  const long long step = *d.step;  // no stage kernel writes it
   pdl_wait();
   final_reduce(d, tab);
   if (threadIdx.x == 0) *d.step = step + n;
@@ -2092,8 +2124,8 @@ cudaError_t launch_finish(const Dev<Real, Dc> &d, const Plan &P, int n, cudaStre
 }
 
 template <typename Real, typename Dc>
-cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, bool adam, cudaStream_t s,
-                        cudaEvent_t *ev) {
+cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, bool adam, bool close,
+                        cudaStream_t s, cudaEvent_t *ev) {
   Real *x = const_cast<Real *>(static_cast<const Real *>(xv));
   const int o2 = P.s1.n_blocks;
   // with timing events between the kernels, launch them plainly so each event brackets one kernel
@@ -2149,6 +2181,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     if (adam) go(k_s5<Real, Dc, true>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
     else go(k_s5<Real, Dc, false>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
   }
+  if (close) go(k_finish<Real, Dc>, 1, 0, d, P.tab, adam ? 1 : 0);  // the objective, step += 1 with Adam
   mark(ev, 5, s);
   return e;
 }
@@ -2292,8 +2325,8 @@ template cudaError_t launch_round_fix<float, df32>(const Dev<float, df32> &, con
                                                    const int *, int, unsigned char *, const float *, cudaStream_t);
 
 template cudaError_t launch_eval<double, double>(const Dev<double, double> &, const Plan &, const void *, bool,
-                                                 cudaStream_t, cudaEvent_t *);
-template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Plan &, const void *, bool,
+                                                 bool, cudaStream_t, cudaEvent_t *);
+template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Plan &, const void *, bool, bool,
                                               cudaStream_t, cudaEvent_t *);
 template cudaError_t prepare_eval<double, double>(int, bool);
 template cudaError_t launch_finish<double, double>(const Dev<double, double> &, const Plan &, int, cudaStream_t);

@@ -8,6 +8,17 @@
 // back-propagated dY, dZ2, dZ1); accumulation is FP32; master weights, biases, moments and the
 // loss are FP32 / FP64.  Every reduction has a fixed order (split-K partials are summed in a
 // second pass), so results are bitwise repeatable.
+//
+// The GEMMs run on the fifth-generation tensor cores: C[m][n] = sum_k A[m][k] B[n][k] with both
+// operands BF16 and K-contiguous, staged by TMA (128-byte swizzle) through a ring of shared-memory
+// stages, multiplied by tcgen05.mma (M = 128) issued from one thread into a TMEM accumulator, and
+// read back with tcgen05.ld for the FP32 partial-sum epilogue.  Every product of the network is
+// put in that form: the layers run with the weights as A (their rows fill the 128 TMEM lanes) and
+// the batch as B (N = 64), writing the transposed tile; the weight gradients take transposed BF16
+// copies of the activations and back-propagated terms (batch-contiguous), the input gradients
+// transposed BF16 copies of W2 and W3.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -15,6 +26,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -24,135 +36,318 @@ namespace {
 
 thread_local std::string g_mlp_error;
 
-constexpr int BM = 64, BN = 64, BK = 32;  // GEMM block tile
-constexpr int GEMM_THREADS = 128;         // 4 warps as 2 x 2, each 32 x 32
+constexpr int UM = 128;              // tile rows: the MMA's M, one TMEM lane each
+constexpr int UK = 64;               // K per stage: 64 BF16 = one 128-byte swizzle span per row
+constexpr int UTHREADS = 128;        // warp 0: TMA producer, warp 1: MMA issuer, warp 2: TMEM owner; all: epilogue
+constexpr unsigned long long WAIT_NS = 1000000000ull;  // a wait gives up after 1 s (error flag, clean exit)
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// Partial C[s][m][n] = sum over k in split s of A(m, k) B(k, n), where A(m, k) = A[m sam + k sak]
-// and B(k, n) = B[k sbk + n sbn] (BF16, any strides), with warp-level BF16 MMA (m16n8k16, FP32
-// accumulate).  Grid: (ceil(N/64), ceil(M/64), splits); each split covers kchunk of K.
-__global__ void __launch_bounds__(GEMM_THREADS) k_gemm(const __nv_bfloat16 *__restrict__ A, long long sam, long long sak,
-                                                       const __nv_bfloat16 *__restrict__ B, long long sbk, long long sbn,
-                                                       float *__restrict__ C, int M, int N, int K, int kchunk) {
-  __shared__ __nv_bfloat16 sA[BM][BK + 8];
-  __shared__ __nv_bfloat16 sB[BN][BK + 8];  // stored [n][k]
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int wm = wid >> 1, wn = wid & 1;
-  const int g = lane >> 2, tq = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int k0 = kb; k0 < ke; k0 += BK) {
-    // stage tiles; walk along whichever index is contiguous in memory
-    for (int e = tid; e < BM * BK; e += GEMM_THREADS) {
-      int r, c;
-      if (sak == 1) { r = e / BK; c = e % BK; } else { c = e / BM; r = e % BM; }
-      const int m = m0 + r, k = k0 + c;
-      sA[r][c] = (m < M && k < ke) ? A[(long long)m * sam + (long long)k * sak] : zero;
-    }
-    for (int e = tid; e < BN * BK; e += GEMM_THREADS) {
-      int r, c;
-      if (sbk == 1) { r = e / BK; c = e % BK; } else { c = e / BN; r = e % BN; }
-      const int n = n0 + r, k = k0 + c;
-      sB[r][c] = (n < N && k < ke) ? B[(long long)k * sbk + (long long)n * sbn] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      uint32_t af[2][4], bf[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm * 32 + i * 16 + g, c = kk + 2 * tq;
-        af[i][0] = pack2(sA[r][c], sA[r][c + 1]);
-        af[i][1] = pack2(sA[r + 8][c], sA[r + 8][c + 1]);
-        af[i][2] = pack2(sA[r][c + 8], sA[r][c + 9]);
-        af[i][3] = pack2(sA[r + 8][c + 8], sA[r + 8][c + 9]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = wn * 32 + j * 8 + g, c = kk + 2 * tq;
-        bf[j][0] = pack2(sB[r][c], sB[r][c + 1]);
-        bf[j][1] = pack2(sB[r][c + 8], sB[r][c + 9]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
-    }
-    __syncthreads();
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for the completion of the barrier's phase `parity`.  Gives up after WAIT_NS (or 2^30 polls),
+// or at once when another thread of the block has given up (abort != 0 and honour_abort); returns
+// whether the phase completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort, bool honour_abort) {
+  const unsigned long long t0 = gtime();
+  for (unsigned it = 0; it < (1u << 30); ++it) {
+    if (mbar_test(b, parity)) return true;
+    if (honour_abort && *abort) return false;
+    if (gtime() - t0 > WAIT_NS) break;
   }
-  float *Cs = C + (long long)blockIdx.z * M * N;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = m0 + wm * 32 + i * 16 + g, c = n0 + wn * 32 + j * 8 + 2 * tq;
-      if (r < M && c < N) Cs[(long long)r * N + c] = acc[i][j][0];
-      if (r < M && c + 1 < N) Cs[(long long)r * N + c + 1] = acc[i][j][1];
-      if (r + 8 < M && c < N) Cs[(long long)(r + 8) * N + c] = acc[i][j][2];
-      if (r + 8 < M && c + 1 < N) Cs[(long long)(r + 8) * N + c + 1] = acc[i][j][3];
-    }
+  *abort = 1;
+  return false;
 }
 
-// Epilogue of the forward layers: Z = sum of split-K partials + bias; optionally ReLU; writes Z
-// (FP32) and the BF16 copy of the activation for the next GEMM.
+// TMA: the box at (c0 = K offset in elements, c1 = row) of a 2-D BF16 tensor map into shared memory,
+// completing `bytes` on the barrier.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the 128-byte swizzle: rows
+// of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1, layout
+// SWIZZLE_128B; the leading byte offset is unused for this layout.  The tile starts on a 1024-byte
+// boundary, so the K step inside a row is a plain start-address offset (32 bytes per 16 elements).
+__device__ __forceinline__ uint64_t umma_desc(const void *tile) {
+  const uint32_t a = smem_u32(tile);
+  return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t umma_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// the barrier completes once every tcgen05.mma this thread issued before has completed
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN, int STAGES>
+constexpr size_t umma_smem_bytes() {
+  return (size_t)STAGES * (UM * UK * 2 + BN * UK * 2) + 1024;  // + alignment of the first tile to 1024 bytes
+}
+
+// Partial C[s] of split s (FP32, M x N row-major, or its transpose N x M when trans) =
+//   sum over the K blocks [s kbps, (s + 1) kbps) of A[m][k] B[n][k],
+// A (M x K) and B (N x K) BF16 behind the tensor maps tA (box 64 x 128) and tB (box 64 x BN); rows
+// and K beyond the tensors read as zeros.  Grid (ceil(M/128), ceil(N/BN), splits), 128 threads.
+// A wait that runs out sets *err, drains what this block started and returns.
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(UTHREADS, 1)
+    k_umma_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, float *__restrict__ P,
+                int M, int N, int nkb, int kbps, int trans, int *err) {
+  constexpr uint32_t A_BYTES = UM * UK * 2, B_BYTES = BN * UK * 2;
+  constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;  // a power of two >= 32
+  static_assert((BN & (BN - 1)) == 0 && BN >= 16 && BN <= 256, "BN");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char *sA = base, *sB = base + STAGES * A_BYTES;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort, s_issued, s_consumed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * UM, n0 = blockIdx.y * BN;
+  const int kb0 = blockIdx.z * kbps, nk = min(kbps, nkb - kb0);  // >= 1: the host sizes the splits so
+  volatile int *abort = &s_abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accf, 1);
+    s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  if (warp == 0 && lane == 0) {  // producer: stage s holds K block kb, its u-th use
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t u = (uint32_t)(kb / STAGES);
+      if (kb >= STAGES && !mbar_wait(&empty[s], (u - 1) & 1, abort, true)) break;
+      mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+      const int kx = (kb0 + kb) * UK;  // a multiple of 64 elements: 128-byte aligned
+      tma_load_2d(sA + s * A_BYTES, &tA, &full[s], kx, m0);
+      tma_load_2d(sB + s * B_BYTES, &tB, &full[s], kx, n0);
+      issued = kb + 1;
+    }
+    s_issued = issued;
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    constexpr uint32_t IDESC = umma_idesc<BN>();
+    int consumed = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (uint32_t)(kb / STAGES) & 1, abort, true)) break;
+      tc_fence_after();
+      const uint64_t ad = umma_desc(sA + s * A_BYTES), bd = umma_desc(sB + s * B_BYTES);
+#pragma unroll
+      for (int j = 0; j < UK / 16; ++j)  // K = 16 per MMA: 32 bytes (2 descriptor units) along the row
+        umma_bf16(tmem, ad + 2 * j, bd + 2 * j, IDESC, (kb | j) != 0);
+      umma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+      consumed = kb + 1;
+    }
+    s_consumed = consumed;
+    umma_commit(&accf);  // every MMA above has completed (also after an abort)
+  }
+  __syncwarp();
+  // the accumulator is complete (or, after an abort, no MMA is in flight any more); the flag is read
+  // after a barrier so that every warp takes the same branch into the warp-collective TMEM loads
+  mbar_wait(&accf, 0, abort, false);
+  tc_fence_after();
+  __syncthreads();
+  if (!*abort) {
+    const int m = m0 + warp * 32 + lane;
+    float *Ps = P + (long long)blockIdx.z * M * N;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (m >= M) continue;
+      if (trans) {  // C^T: for each column the warp's 32 lanes write 32 consecutive floats
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (n0 + c0 + i < N) Ps[(long long)(n0 + c0 + i) * M + m] = v[i];
+      } else {
+        float *row = Ps + (long long)m * N + n0 + c0;
+        if (n0 + c0 + 16 <= N && (N & 3) == 0) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(row + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (n0 + c0 + i < N) row[i] = v[i];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort) {
+    atomicExch(err, 1);
+    // copies still in flight land in this block's shared memory: wait for them (bounded) before exit
+    for (int kb = s_consumed; kb < s_issued; ++kb) mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1, abort, false);
+  }
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Transposed BF16 copy: dst[c][r] (row stride ldd) = src[r][c] (FP32, rows x cols, row stride lds),
+// through a 32 x 33 shared tile so that both sides are coalesced.  Grid (ceil(cols/32), ceil(rows/32)),
+// block (32, 8).
+__global__ void k_transpose_bf16(const float *__restrict__ src, long long lds, __nv_bfloat16 *__restrict__ dst,
+                                 long long ldd, int rows, int cols) {
+  __shared__ float t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    t[i][threadIdx.x] = (r < rows && c < cols) ? src[(long long)r * lds + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[(long long)c * ldd + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+  }
+}
+
+// BF16 copy with a padded row stride: dst[r][c] (stride ldd) = src[r][c] (FP32, stride lds).
+__global__ void k_rows_bf16(const float *__restrict__ src, long long lds, __nv_bfloat16 *__restrict__ dst, long long ldd,
+                            int rows, int cols) {
+  const long long total = (long long)rows * cols;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / cols, c = i - r * cols;
+    dst[r * ldd + c] = __float2bfloat16_rn(src[r * lds + c]);
+  }
+}
+
+// Epilogue of the forward layers: Z = sum of split-K partials + bias (M x N); optionally ReLU;
+// writes Z (FP32) and the activation in BF16 for the next GEMMs: row-major with row stride ldh
+// (Hb) and transposed with row stride ldt (HbT, batch-contiguous).
 __global__ void k_fwd_epi(const float *__restrict__ P, int splits, const float *__restrict__ bias, float *__restrict__ Z,
-                          __nv_bfloat16 *__restrict__ Hb, int M, int N, int relu) {
+                          __nv_bfloat16 *__restrict__ Hb, long long ldh, __nv_bfloat16 *__restrict__ HbT, long long ldt,
+                          int M, int N, int relu) {
   const long long total = (long long)M * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     float z = 0.f;
     for (int s = 0; s < splits; ++s) z += P[s * total + i];
-    z += bias[i % N];
+    const long long r = i / N, c = i - r * N;
+    z += bias[c];
     Z[i] = z;
-    if (Hb) Hb[i] = __float2bfloat16_rn(relu ? fmaxf(z, 0.f) : z);
+    const __nv_bfloat16 h = __float2bfloat16_rn(relu ? fmaxf(z, 0.f) : z);
+    if (Hb) Hb[r * ldh + c] = h;
+    if (HbT) HbT[c * ldt + r] = h;
   }
 }
 
-// Backward epilogue: D = sum of split-K partials, masked by relu'(Zmask) when given; FP32 and BF16 copies.
+// Backward epilogue: D = sum of split-K partials (rows x cols), masked by relu'(Zmask) when given;
+// FP32 (D, dense), BF16 row-major with row stride ldd (Db) and BF16 transposed with row stride
+// ldt (DbT).
 __global__ void k_bwd_epi(const float *__restrict__ P, int splits, const float *__restrict__ Zmask, float *__restrict__ D,
-                          __nv_bfloat16 *__restrict__ Db, long long total) {
+                          __nv_bfloat16 *__restrict__ Db, long long ldd, __nv_bfloat16 *__restrict__ DbT, long long ldt,
+                          int rows, int cols) {
+  const long long total = (long long)rows * cols;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     float v = 0.f;
     for (int s = 0; s < splits; ++s) v += P[s * total + i];
     if (Zmask && !(Zmask[i] > 0.f)) v = 0.f;
     if (D) D[i] = v;
-    if (Db) Db[i] = __float2bfloat16_rn(v);
+    if (Db || DbT) {
+      const long long r = i / cols, c = i - r * cols;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      if (Db) Db[r * ldd + c] = h;
+      if (DbT) DbT[c * ldt + r] = h;
+    }
   }
-}
-
-__global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *__restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = __float2bfloat16_rn(a[i]);
 }
 
 // dY = 2 (Y - target) / (B * N) (BF16 for the backward GEMMs) and per-block partial sums of the
 // squared error (FP64, fixed order).
 __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ Y, const float *__restrict__ Tg,
-                                              __nv_bfloat16 *__restrict__ dYb, float *__restrict__ dY, double *part,
-                                              long long total) {
+                                              __nv_bfloat16 *__restrict__ dYb, long long ldo,
+                                              __nv_bfloat16 *__restrict__ dYbT, long long ldt, float *__restrict__ dY,
+                                              double *part, int rows, int cols) {
   __shared__ double red[8];
   double acc = 0.0;
+  const long long total = (long long)rows * cols;
   const float sc = 2.0f / (float)total;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const float r = Y[i] - Tg[i];
     acc += (double)r * (double)r;
     dY[i] = sc * r;
-    dYb[i] = __float2bfloat16_rn(sc * r);
+    const long long b = i / cols, o = i - b * cols;
+    const __nv_bfloat16 h = __float2bfloat16_rn(sc * r);
+    dYb[b * ldo + o] = h;
+    dYbT[o * ldt + b] = h;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -214,19 +409,26 @@ __global__ void k_init(float *__restrict__ w, long long n, float scale, uint64_t
 
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8)); }
 
+long long pad8(long long n) { return (n + 7) / 8 * 8; }  // BF16 row strides: multiples of 16 bytes (TMA)
+
 }  // namespace
 
 struct qg_mlp {
   int n_in, n_h, n_out, max_b;
+  long long ld_i, ld_h, ld_o, ld_b;  // padded BF16 row strides for rows of I, H, O and batch elements
   long long n_par;
   long long o_w1, o_b1, o_w2, o_b2, o_w3, o_b3;
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
   float *w = nullptr, *gw = nullptr, *am = nullptr, *av = nullptr;
-  __nv_bfloat16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr;
-  __nv_bfloat16 *xb = nullptr, *h1b = nullptr, *h2b = nullptr, *dyb = nullptr, *dz2b = nullptr, *dz1b = nullptr;
+  // BF16 GEMM operands, all K-contiguous: weights [H][ld_i], [H][ld_h], [O][ld_h] and the transposed
+  // W2^T [H][ld_h], W3^T [H][ld_o]; activations row-major [B][ld_*] and transposed [features][ld_b]
+  __nv_bfloat16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr, *w2t = nullptr, *w3t = nullptr;
+  __nv_bfloat16 *xb = nullptr, *xt = nullptr, *h1b = nullptr, *h1t = nullptr, *h2b = nullptr, *h2t = nullptr;
+  __nv_bfloat16 *dyb = nullptr, *dyt = nullptr, *dz2b = nullptr, *dz2t = nullptr, *dz1t = nullptr;
   float *z1 = nullptr, *z2 = nullptr, *y = nullptr, *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr, *part = nullptr;
   double *lpart = nullptr;
+  int *d_err = nullptr;  // set by a GEMM block whose pipeline wait ran out
   long long part_elems = 0;
   long long step = 0;
   std::string err;
@@ -248,36 +450,120 @@ int mal(qg_mlp *m, T **p, size_t n) {
   return QG_OK;
 }
 
-// C (M x N, FP32 split-K partials in m->part) = A B; returns the number of splits used.
-int gemm(qg_mlp *mm, const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B, long long sbk,
-         long long sbn, int M, int N, int K) {
-  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  int splits = std::max(1, std::min(64, (152 * 2 + tiles - 1) / tiles));
-  splits = std::min(splits, std::max(1, K / 256));
-  while ((long long)splits * M * N > mm->part_elems && splits > 1) --splits;
-  int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + BK - 1) / BK * BK;
-  splits = (K + kchunk - 1) / kchunk;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
-  k_gemm<<<grid, GEMM_THREADS, 0, mm->stream>>>(A, sam, sak, B, sbk, sbn, mm->part, M, N, K, kchunk);
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2-D tensor map of a BF16 matrix (rows x cols, row stride ld elements, a multiple of 8) with a box
+// of 64 columns (128 bytes, the swizzle span) x box_rows rows; reads outside the matrix give zeros.
+int make_map(qg_mlp *m, CUtensorMap *map, const __nv_bfloat16 *ptr, long long rows, long long cols, long long ld,
+             int box_rows) {
+  const auto enc = tensor_map_encoder();
+  if (!enc) return mfail(m, QG_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)UK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return mfail(m, QG_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return QG_OK;
+}
+
+template <int BN, int STAGES>
+cudaError_t umma_prepare() {
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    e = cudaFuncSetAttribute(k_umma_gemm<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)umma_smem_bytes<BN, STAGES>());
+  });
+  return e;
+}
+
+// Split-K partials of C = A B^T (A: M x K with row stride lda, B: N x K with row stride ldb, both BF16)
+// into mm->part: [splits][M][N], or [splits][N][M] with trans.  Returns the number of splits, or 0
+// after recording an error.  Narrow products (N <= 64: the batch) take 64-column tiles and a
+// 4-stage ring; wide ones (the weight gradients, K = the batch) 256-column tiles and 2 stages.
+int gemm(qg_mlp *mm, const __nv_bfloat16 *A, long long lda, int M, const __nv_bfloat16 *B, long long ldb, int N, int K,
+         bool trans) {
+  const bool narrow = N <= 64;
+  const int BN = narrow ? 64 : 256;
+  const long long tiles = (long long)((M + UM - 1) / UM) * ((N + BN - 1) / BN);
+  const int nkb = (K + UK - 1) / UK;
+  int splits = (int)std::max(1LL, std::min<long long>({64LL, (long long)nkb, (2LL * 152 + tiles - 1) / tiles}));
+  while (splits > 1 && (long long)splits * M * N > mm->part_elems) --splits;
+  const int kbps = (nkb + splits - 1) / splits;
+  splits = (nkb + kbps - 1) / kbps;  // every split has at least one K block
+  CUtensorMap ta, tb;
+  int rc = make_map(mm, &ta, A, M, K, lda, UM);
+  if (!rc) rc = make_map(mm, &tb, B, N, K, ldb, BN);
+  if (rc) return 0;
+  const dim3 grid((M + UM - 1) / UM, (N + BN - 1) / BN, splits);
+  cudaError_t e;
+  if (narrow) {
+    e = umma_prepare<64, 4>();
+    if (e == cudaSuccess)
+      k_umma_gemm<64, 4><<<grid, UTHREADS, umma_smem_bytes<64, 4>(), mm->stream>>>(ta, tb, mm->part, M, N, nkb, kbps,
+                                                                                  trans ? 1 : 0, mm->d_err);
+  } else {
+    e = umma_prepare<256, 2>();
+    if (e == cudaSuccess)
+      k_umma_gemm<256, 2><<<grid, UTHREADS, umma_smem_bytes<256, 2>(), mm->stream>>>(ta, tb, mm->part, M, N, nkb, kbps,
+                                                                                    trans ? 1 : 0, mm->d_err);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mfail(mm, QG_ERR_CUDA, std::string("tensor-core GEMM launch: ") + cudaGetErrorString(e));
+    return 0;
+  }
   return splits;
 }
 
-void forward(qg_mlp *m, int B) {
-  const int H = m->n_h, I = m->n_in, O = m->n_out;
-  int s = gemm(m, m->xb, I, 1, m->w1b, 1, I, B, H, I);
-  k_fwd_epi<<<grid_for((long long)B * H), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b1, m->z1, m->h1b, B, H, 1);
-  s = gemm(m, m->h1b, H, 1, m->w2b, 1, H, B, H, H);
-  k_fwd_epi<<<grid_for((long long)B * H), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b2, m->z2, m->h2b, B, H, 1);
-  s = gemm(m, m->h2b, H, 1, m->w3b, 1, H, B, O, H);
-  k_fwd_epi<<<grid_for((long long)B * O), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b3, m->y, nullptr, B, O, 0);
+// x (batch x I, FP32) into the BF16 operands xb [B][ld_i] and xt [I][ld_b]
+void load_x(qg_mlp *m, const float *x, int B) {
+  k_rows_bf16<<<grid_for((long long)B * m->n_in), 256, 0, m->stream>>>(x, m->n_in, m->xb, m->ld_i, B, m->n_in);
+  k_transpose_bf16<<<dim3((m->n_in + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, m->stream>>>(x, m->n_in, m->xt, m->ld_b,
+                                                                                            B, m->n_in);
 }
 
+// Forward pass: the layers as C^T = W act^T (weights as the 128-row operand, the batch as N).
+int forward(qg_mlp *m, int B) {
+  const int H = m->n_h, I = m->n_in, O = m->n_out;
+  int s = gemm(m, m->w1b, m->ld_i, H, m->xb, m->ld_i, B, I, true);
+  if (!s) return QG_ERR_CUDA;
+  k_fwd_epi<<<grid_for((long long)B * H), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b1, m->z1, m->h1b, m->ld_h, m->h1t,
+                                                               m->ld_b, B, H, 1);
+  if (!(s = gemm(m, m->w2b, m->ld_h, H, m->h1b, m->ld_h, B, H, true))) return QG_ERR_CUDA;
+  k_fwd_epi<<<grid_for((long long)B * H), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b2, m->z2, m->h2b, m->ld_h, m->h2t,
+                                                               m->ld_b, B, H, 1);
+  if (!(s = gemm(m, m->w3b, m->ld_h, O, m->h2b, m->ld_h, B, H, true))) return QG_ERR_CUDA;
+  k_fwd_epi<<<grid_for((long long)B * O), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b3, m->y, nullptr, 0, nullptr, 0,
+                                                               B, O, 0);
+  return QG_OK;
+}
+
+// BF16 operand copies of the FP32 master weights: W1, W2, W3 row-major (padded) and W2^T, W3^T.
 void refresh_bf16(qg_mlp *m) {
-  const long long n1 = (long long)m->n_h * m->n_in, n2 = (long long)m->n_h * m->n_h, n3 = (long long)m->n_out * m->n_h;
-  k_to_bf16<<<grid_for(n1), 256, 0, m->stream>>>(m->w + m->o_w1, m->w1b, n1);
-  k_to_bf16<<<grid_for(n2), 256, 0, m->stream>>>(m->w + m->o_w2, m->w2b, n2);
-  k_to_bf16<<<grid_for(n3), 256, 0, m->stream>>>(m->w + m->o_w3, m->w3b, n3);
+  const int H = m->n_h, I = m->n_in, O = m->n_out;
+  cudaStream_t s = m->stream;
+  k_rows_bf16<<<grid_for((long long)H * I), 256, 0, s>>>(m->w + m->o_w1, I, m->w1b, m->ld_i, H, I);
+  k_rows_bf16<<<grid_for((long long)H * H), 256, 0, s>>>(m->w + m->o_w2, H, m->w2b, m->ld_h, H, H);
+  k_rows_bf16<<<grid_for((long long)O * H), 256, 0, s>>>(m->w + m->o_w3, H, m->w3b, m->ld_h, O, H);
+  k_transpose_bf16<<<dim3((H + 31) / 32, (H + 31) / 32), dim3(32, 8), 0, s>>>(m->w + m->o_w2, H, m->w2t, m->ld_h, H, H);
+  k_transpose_bf16<<<dim3((H + 31) / 32, (O + 31) / 32), dim3(32, 8), 0, s>>>(m->w + m->o_w3, H, m->w3t, m->ld_o, O, H);
 }
 
 }  // namespace
@@ -289,24 +575,31 @@ int qg_mlp_create(qg_mlp **out, int32_t n_in, int32_t n_hidden, int32_t n_out, i
   if (!out) return mfail(nullptr, QG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n_in < 1 || n_hidden < 1 || n_out < 1 || max_batch < 1) return mfail(nullptr, QG_ERR_INVALID_ARG, "sizes");
+  if (max_batch > 64) return mfail(nullptr, QG_ERR_UNSUPPORTED, "max_batch above 64 (one 64-column GEMM tile)");
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) return mfail(nullptr, QG_ERR_NO_DEVICE, "no CUDA device");
+  if (!tensor_map_encoder()) return mfail(nullptr, QG_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
   qg_mlp *m = new qg_mlp();
   m->n_in = n_in; m->n_h = n_hidden; m->n_out = n_out; m->max_b = max_batch;
+  m->ld_i = pad8(n_in); m->ld_h = pad8(n_hidden); m->ld_o = pad8(n_out); m->ld_b = pad8(max_batch);
   m->o_w1 = 0; m->o_b1 = m->o_w1 + (long long)n_hidden * n_in;
   m->o_w2 = m->o_b1 + n_hidden; m->o_b2 = m->o_w2 + (long long)n_hidden * n_hidden;
   m->o_w3 = m->o_b2 + n_hidden; m->o_b3 = m->o_w3 + (long long)n_out * n_hidden;
   m->n_par = m->o_b3 + n_out;
   const long long B = max_batch, H = n_hidden, I = n_in, O = n_out;
-  m->part_elems = std::max({64 * B * H, 64 * B * O, 8 * H * I, 8 * O * H, 8 * H * H, 8 * B * I});
+  const long long li = m->ld_i, lh = m->ld_h, lo = m->ld_o, lb = m->ld_b;
+  m->part_elems = std::max({64 * B * H, 64 * B * O, H * I, O * H, H * H});
   int rc = 0;
   if ((rc = mal(m, &m->w, m->n_par)) || (rc = mal(m, &m->gw, m->n_par)) || (rc = mal(m, &m->am, m->n_par)) ||
-      (rc = mal(m, &m->av, m->n_par)) || (rc = mal(m, &m->w1b, H * I)) || (rc = mal(m, &m->w2b, H * H)) ||
-      (rc = mal(m, &m->w3b, O * H)) || (rc = mal(m, &m->xb, B * I)) || (rc = mal(m, &m->h1b, B * H)) ||
-      (rc = mal(m, &m->h2b, B * H)) || (rc = mal(m, &m->dyb, B * O)) || (rc = mal(m, &m->dz2b, B * H)) ||
-      (rc = mal(m, &m->dz1b, B * H)) || (rc = mal(m, &m->z1, B * H)) || (rc = mal(m, &m->z2, B * H)) ||
-      (rc = mal(m, &m->y, B * O)) || (rc = mal(m, &m->dy, B * O)) || (rc = mal(m, &m->dz2, B * H)) ||
-      (rc = mal(m, &m->dz1, B * H)) || (rc = mal(m, &m->part, m->part_elems)) || (rc = mal(m, &m->lpart, 152 * 8))) {
+      (rc = mal(m, &m->av, m->n_par)) || (rc = mal(m, &m->w1b, H * li)) || (rc = mal(m, &m->w2b, H * lh)) ||
+      (rc = mal(m, &m->w3b, O * lh)) || (rc = mal(m, &m->w2t, H * lh)) || (rc = mal(m, &m->w3t, H * lo)) ||
+      (rc = mal(m, &m->xb, B * li)) || (rc = mal(m, &m->xt, I * lb)) || (rc = mal(m, &m->h1b, B * lh)) ||
+      (rc = mal(m, &m->h1t, H * lb)) || (rc = mal(m, &m->h2b, B * lh)) || (rc = mal(m, &m->h2t, H * lb)) ||
+      (rc = mal(m, &m->dyb, B * lo)) || (rc = mal(m, &m->dyt, O * lb)) || (rc = mal(m, &m->dz2b, B * lh)) ||
+      (rc = mal(m, &m->dz2t, H * lb)) || (rc = mal(m, &m->dz1t, H * lb)) || (rc = mal(m, &m->z1, B * H)) ||
+      (rc = mal(m, &m->z2, B * H)) || (rc = mal(m, &m->y, B * O)) || (rc = mal(m, &m->dy, B * O)) ||
+      (rc = mal(m, &m->dz2, B * H)) || (rc = mal(m, &m->dz1, B * H)) || (rc = mal(m, &m->part, m->part_elems)) ||
+      (rc = mal(m, &m->lpart, 152 * 8)) || (rc = mal(m, &m->d_err, 1))) {
     qg_mlp_destroy(m);
     return rc;
   }
@@ -314,6 +607,7 @@ int qg_mlp_create(qg_mlp **out, int32_t n_in, int32_t n_hidden, int32_t n_out, i
   cudaMemset(m->am, 0, m->n_par * sizeof(float));
   cudaMemset(m->av, 0, m->n_par * sizeof(float));
   cudaMemset(m->w, 0, m->n_par * sizeof(float));
+  cudaMemset(m->d_err, 0, sizeof(int));
   // He initialisation for the ReLU layers, a smaller scale for the linear output layer; zero biases
   k_init<<<grid_for(H * I), 256>>>(m->w + m->o_w1, H * I, sqrtf(2.f / (float)I), seed, 0);
   k_init<<<grid_for(H * H), 256>>>(m->w + m->o_w2, H * H, sqrtf(2.f / (float)H), seed, H * I);
@@ -345,9 +639,9 @@ int qg_mlp_set_stream(qg_mlp *m, void *stream) {
 
 int qg_mlp_forward(qg_mlp *m, const float *x, int32_t batch, float *y) {
   if (!m || !x || !y || batch < 1 || batch > m->max_b) return m ? mfail(m, QG_ERR_INVALID_ARG, "forward arguments") : QG_ERR_INVALID_ARG;
-  const long long nx = (long long)batch * m->n_in;
-  k_to_bf16<<<grid_for(nx), 256, 0, m->stream>>>(x, m->xb, nx);
-  forward(m, batch);
+  load_x(m, x, batch);
+  int rc = forward(m, batch);
+  if (rc) return rc;
   cudaError_t e = cudaMemcpyAsync(y, m->y, sizeof(float) * batch * m->n_out, cudaMemcpyDeviceToDevice, m->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? QG_OK : mfail(m, QG_ERR_CUDA, cudaGetErrorString(e));
@@ -359,27 +653,29 @@ int qg_mlp_train_step(qg_mlp *m, const float *x, const float *target, int32_t ba
     return m ? mfail(m, QG_ERR_INVALID_ARG, "train arguments") : QG_ERR_INVALID_ARG;
   const int B = batch, H = m->n_h, I = m->n_in, O = m->n_out;
   cudaStream_t s = m->stream;
-  k_to_bf16<<<grid_for((long long)B * I), 256, 0, s>>>(x, m->xb, (long long)B * I);
-  forward(m, B);
+  load_x(m, x, B);
+  int rc = forward(m, B);
+  if (rc) return rc;
   const long long ny = (long long)B * O;
   const int lb = grid_for(ny);
-  k_loss<<<lb, 256, 0, s>>>(m->y, target, m->dyb, m->dy, m->lpart, ny);
+  k_loss<<<lb, 256, 0, s>>>(m->y, target, m->dyb, m->ld_o, m->dyt, m->ld_b, m->dy, m->lpart, B, O);
   if (loss) k_loss_final<<<1, 32, 0, s>>>(m->lpart, lb, ny, loss);
-  // layer 3: dW3 = dY^T H2, db3 = colsum(dY), dH2 = dY W3 masked by relu'(Z2)
-  int sp = gemm(m, m->dyb, 1, O, m->h2b, H, 1, O, H, B);
-  k_bwd_epi<<<grid_for((long long)O * H), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w3, nullptr, (long long)O * H);
+  // layer 3: dW3 = dY^T H2 (K = the batch), db3 = colsum(dY), dH2 = dY W3 masked by relu'(Z2)
+  int sp = gemm(m, m->dyt, m->ld_b, O, m->h2t, m->ld_b, H, B, false);
+  if (!sp) return QG_ERR_CUDA;
+  k_bwd_epi<<<grid_for((long long)O * H), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w3, nullptr, 0, nullptr, 0, O, H);
   k_colsum<<<(O + 255) / 256, 256, 0, s>>>(m->dy, B, O, m->gw + m->o_b3);
-  sp = gemm(m, m->dyb, O, 1, m->w3b, H, 1, B, H, O);
-  k_bwd_epi<<<grid_for((long long)B * H), 256, 0, s>>>(m->part, sp, m->z2, m->dz2, m->dz2b, (long long)B * H);
+  if (!(sp = gemm(m, m->w3t, m->ld_o, H, m->dyb, m->ld_o, B, O, true))) return QG_ERR_CUDA;
+  k_bwd_epi<<<grid_for((long long)B * H), 256, 0, s>>>(m->part, sp, m->z2, m->dz2, m->dz2b, m->ld_h, m->dz2t, m->ld_b, B, H);
   // layer 2
-  sp = gemm(m, m->dz2b, 1, H, m->h1b, H, 1, H, H, B);
-  k_bwd_epi<<<grid_for((long long)H * H), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w2, nullptr, (long long)H * H);
+  if (!(sp = gemm(m, m->dz2t, m->ld_b, H, m->h1t, m->ld_b, H, B, false))) return QG_ERR_CUDA;
+  k_bwd_epi<<<grid_for((long long)H * H), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w2, nullptr, 0, nullptr, 0, H, H);
   k_colsum<<<(H + 255) / 256, 256, 0, s>>>(m->dz2, B, H, m->gw + m->o_b2);
-  sp = gemm(m, m->dz2b, H, 1, m->w2b, H, 1, B, H, H);
-  k_bwd_epi<<<grid_for((long long)B * H), 256, 0, s>>>(m->part, sp, m->z1, m->dz1, m->dz1b, (long long)B * H);
+  if (!(sp = gemm(m, m->w2t, m->ld_h, H, m->dz2b, m->ld_h, B, H, true))) return QG_ERR_CUDA;
+  k_bwd_epi<<<grid_for((long long)B * H), 256, 0, s>>>(m->part, sp, m->z1, m->dz1, nullptr, 0, m->dz1t, m->ld_b, B, H);
   // layer 1
-  sp = gemm(m, m->dz1b, 1, H, m->xb, I, 1, H, I, B);
-  k_bwd_epi<<<grid_for((long long)H * I), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w1, nullptr, (long long)H * I);
+  if (!(sp = gemm(m, m->dz1t, m->ld_b, H, m->xt, m->ld_b, I, B, false))) return QG_ERR_CUDA;
+  k_bwd_epi<<<grid_for((long long)H * I), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w1, nullptr, 0, nullptr, 0, H, I);
   k_colsum<<<(H + 255) / 256, 256, 0, s>>>(m->dz1, B, H, m->gw + m->o_b1);
   // Adam
   if (lr > 0) {
@@ -392,6 +688,16 @@ int qg_mlp_train_step(qg_mlp *m, const float *x, const float *target, int32_t ba
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? QG_OK : mfail(m, QG_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int qg_mlp_check(qg_mlp *m) {
+  if (!m) return QG_ERR_INVALID_ARG;
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mfail(m, QG_ERR_CUDA, cudaGetErrorString(e));
+  if (flag) return mfail(m, QG_ERR_CUDA, "a tensor-core GEMM pipeline wait ran out (1 s); its results are invalid");
+  return QG_OK;
 }
 
 int qg_mlp_get_params(qg_mlp *m, float *w) {

@@ -112,6 +112,7 @@ def _load():
         "qg_mlp_set_params": (C.c_int, [vp, vp]),
         "qg_mlp_get_grads": (C.c_int, [vp, vp]),
         "qg_mlp_last_error": (C.c_char_p, [vp]),
+        "qg_mlp_check": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -127,7 +128,8 @@ EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", 
             "qg_solve_schedule", "qg_schedule", "qg_ctg_select", "qg_ctg_scores", "qg_autotune", "qg_tile_shape", "qg_round_batch", "qg_round_reset",
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
-            "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error")
+            "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error",
+            "qg_mlp_check")
 PHASES = ("s1", "s2", "s3", "s4", "s5", "adam")
 
 
@@ -485,3 +487,8 @@ def qg_mlp_get_grads(m: int, g) -> None:
 
 def qg_mlp_last_error(m: Optional[int] = None) -> str:
     return _lib.qg_mlp_last_error(m).decode(errors="replace")
+
+
+def qg_mlp_check(m: int) -> None:
+    """Synchronizes; raises QGError if a tensor-core GEMM of this network gave up on a pipeline wait."""
+    _mcheck(_lib.qg_mlp_check(m), m)

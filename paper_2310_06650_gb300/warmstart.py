@@ -262,29 +262,38 @@ def time_to(times_ms: np.ndarray, objs: np.ndarray, target: float) -> float:
 # experiment driver
 # ------------------------------------------------------------------------------------------------
 
+ARMS = (("plain_fp64", "FP64 from the copper-plate start"), ("mixed_lp", "mixed from the copper-plate start"),
+        ("fp64_learned", "FP64 from the learned start"), ("warm_mixed", "mixed from the learned start"))
+
+
 def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, eval_iters: int, every: int,
                seed: int = 5000, hidden: int = 1024, schedule=SCHEDULE, warm_skip: float = 0.25,
-               const_arm: bool = False, log=print) -> dict:
-    """Train on n_train generated solves, then for n_test held-out profiles compare
-    (a) plain FP64 Adam from the copper-plate start with (b) mixed-precision Adam from the learned
-    start, on GPU time to an objective within 1% of the copper-plate bound (eps = 0 scoring).  When
-    arm (a) misses that target within eval_iters, the target becomes the best objective arm (a)
-    reaches.  Both arms follow the Sec. II-F schedule of eval_iters iterations (schedule=None: a
-    constant lr of 1e-3); arm (b) enters it after the first warm_skip fraction (the learned start
-    takes the place of the early large steps) and its time includes the MLP inference.  const_arm
-    adds, for context, plain FP64 Adam with a constant lr of 1e-3."""
+               const_arm: bool = False, bounds=None, log=print) -> dict:
+    """Train on n_train generated solves, then for n_test held-out profiles compare four Adam arms,
+    {FP64, mixed precision} x {copper-plate start, learned start}, on GPU time to a target objective
+    (eps = 0 scoring).  The target is 1% above the copper-plate bound when plain FP64 Adam from the
+    copper-plate start gets there within eval_iters, else 1% above the best objective that arm
+    reaches.  Every arm follows the Sec. II-F schedule of eval_iters iterations (schedule=None: a
+    constant lr of 1e-3); the learned-start arms enter it after the first warm_skip fraction (the
+    learned start takes the place of the early large steps) and their time includes the MLP
+    inference.  Held-out profiles come from their own generator (seed + 1), so they do not depend on
+    n_train.  bounds: optional per-profile lower bounds of Phi (dicts with "copper_plate" and
+    "contingency_bound"), against which the target is also stated.  const_arm adds, for context,
+    plain FP64 Adam with a constant lr of 1e-3."""
     import synth
     torch = __import__("torch")
     t0 = time.time()
-    prof = synth.load_profiles(case, n_train + n_test, seed)
+    prof = synth.load_profiles(case, n_train, seed)
+    prof_test = synth.load_profiles(case, n_test, seed + 1)
     cases = [synth.with_loads(case, lp) for lp in prof]
+    tests = [synth.with_loads(case, lp) for lp in prof_test]
     starts = [start_point(c) for c in cases]
-    sols = solve_many(cases[:n_train], starts[:n_train], solve_iters, schedule=schedule)
+    sols = solve_many(cases, starts, solve_iters, schedule=schedule)
     t_gen = time.time() - t0
     log(f"generated {n_train} solves in {t_gen:.1f} s")
     ws = WarmStart(case, hidden=hidden, seed=seed)
     t1 = time.time()
-    hist = ws.train(prof[:n_train], starts[:n_train], sols, epochs)
+    hist = ws.train(prof, starts, sols, epochs)
     t_train = time.time() - t1
     log(f"trained {epochs} epochs in {t_train:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}")
     table = schedule_table(eval_iters, schedule) if schedule else None
@@ -292,41 +301,85 @@ def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, e
     table_b = table[skip:].contiguous() if table is not None else None
     rows = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for i in range(n_test):
-        c = cases[n_train + i]
+    for i, c in enumerate(tests):
         bound = merit_order_bound(c)
+        x_lp = start_point(c)
         e0.record()
-        pred = ws.predict(prof[n_train + i:n_train + i + 1], starts[n_train + i:n_train + i + 1])[0]
+        pred = ws.predict(prof_test[i:i + 1], [x_lp])[0]
         e1.record()
         e1.synchronize()
         t_mlp = e0.elapsed_time(e1)
-        ta, oa = solve_trace(c, starts[n_train + i], qg.QG_FP64, eval_iters, every, table=table)
-        tb, ob = solve_trace(c, pred, qg.QG_MIXED, eval_iters, every, table=table_b, t_start_ms=t_mlp)
+        traces = {
+            "plain_fp64": solve_trace(c, x_lp, qg.QG_FP64, eval_iters, every, table=table),
+            "mixed_lp": solve_trace(c, x_lp, qg.QG_MIXED, eval_iters, every, table=table),
+            "fp64_learned": solve_trace(c, pred, qg.QG_FP64, eval_iters - skip, every, table=table_b, t_start_ms=t_mlp),
+            "warm_mixed": solve_trace(c, pred, qg.QG_MIXED, eval_iters - skip, every, table=table_b, t_start_ms=t_mlp),
+        }
+        ta, oa = traces["plain_fp64"]
         target = 1.01 * bound
         kind = "1% of copper-plate bound"
         if not np.isfinite(time_to(ta, oa, target)):
-            target = float(oa.min())
-            kind = "best objective of plain FP64 Adam"
-        row = {"bound": bound, "target": target, "target_kind": kind, "mlp_ms": t_mlp,
-               "plain_fp64": {"ms": time_to(ta, oa, target), "phi0": float(oa[0]), "best": float(oa.min()),
-                              "ms_total": float(ta[-1])},
-               "warm_mixed": {"ms": time_to(tb, ob, target), "phi0": float(ob[0]), "best": float(ob.min()),
-                              "ms_total": float(tb[-1])}}
+            target = 1.01 * float(oa.min())
+            kind = "1% above the best objective of plain FP64 Adam"
+        row = {"bound": bound, "target": target, "target_kind": kind, "mlp_ms": t_mlp}
+        if bounds is not None and i < len(bounds):
+            row["target_over_copper_plate"] = target / bounds[i]["copper_plate"]
+            row["target_over_contingency_bound"] = target / bounds[i]["contingency_bound"]
+        for name, (tt, oo) in traces.items():
+            row[name] = {"ms": time_to(tt, oo, target), "phi0": float(oo[0]), "best": float(oo.min()),
+                         "ms_total": float(tt[-1])}
         if const_arm:
-            tc, oc = solve_trace(c, starts[n_train + i], qg.QG_FP64, eval_iters, every)
+            tc, oc = solve_trace(c, x_lp, qg.QG_FP64, eval_iters, every)
             row["plain_fp64_const_lr"] = {"ms": time_to(tc, oc, target), "best": float(oc.min())}
         rows.append(row)
         log(row)
     ws.close()
-    fin = [r for r in rows if np.isfinite(r["plain_fp64"]["ms"]) and np.isfinite(r["warm_mixed"]["ms"])]
+
+    def median(arm):
+        v = [r[arm]["ms"] for r in rows if np.isfinite(r[arm]["ms"])]
+        return float(np.median(v)) if len(v) == len(rows) and v else None
+
     return {"n_train": n_train, "n_test": n_test, "solve_iters": solve_iters, "epochs": epochs,
             "eval_iters": eval_iters, "every": every, "schedule": list(schedule) if schedule else None,
             "warm_skip": warm_skip if schedule else 0.0, "gen_s": t_gen, "train_s": t_train,
             "loss_first": hist[0], "loss_last": hist[-1], "rows": rows,
-            "median_ms_plain": float(np.median([r["plain_fp64"]["ms"] for r in fin])) if fin else None,
-            "median_ms_warm": float(np.median([r["warm_mixed"]["ms"] for r in fin])) if fin else None,
+            "median_ms": {arm: median(arm) for arm, _ in ARMS},
+            "reached": {arm: int(sum(np.isfinite(r[arm]["ms"]) for r in rows)) for arm, _ in ARMS},
             "warm_faster": int(sum(r["warm_mixed"]["ms"] < r["plain_fp64"]["ms"] for r in rows)),
-            "reached_1pct": int(sum(r["target_kind"].startswith("1%") for r in rows))}
+            "reached_1pct": int(sum(r["target_kind"].startswith("1% of") for r in rows))}
+
+
+# Schedule variants for the attainable-objective study: (name, spec) with spec the qg_schedule
+# arguments (lr0, lrf, eps0, epsf, beta0, beta1, lag), or None for a constant lr of 1e-3.
+VARIANTS = (("default", SCHEDULE),
+            ("lr0 1e-1", (1e-1, 1e-5, 5e-2, 1e-5, 0.1, 1.0, 0.25)),
+            ("lr0 3e-3", (3e-3, 1e-6, 5e-2, 1e-5, 0.1, 1.0, 0.25)),
+            ("no homotopy", (1e-2, 1e-5, 5e-2, 1e-5, 1.0, 1.0, 0.25)),
+            ("constant lr 1e-3", None))
+
+
+def attainable(case, profiles: Sequence[int], iters: int, seed: int = 5001, variants=VARIANTS,
+               precision: int = qg.QG_FP64, log=print) -> dict:
+    """The objective (eps = 0) that long Adam runs reach from the copper-plate start of the held-out
+    profiles (synth.load_profiles(case, max(profiles) + 1, seed), the generator experiment() draws
+    its held-out profiles from), under each schedule variant of `iters` iterations: per profile and
+    variant the best Phi seen (scored every iters / 50 iterations) and the GPU time of the run."""
+    import synth
+    prof = synth.load_profiles(case, max(profiles) + 1, seed)
+    every = max(1, iters // 50)
+    out = []
+    for i in profiles:
+        c = synth.with_loads(case, prof[i])
+        x0 = start_point(c)
+        row = {"profile": i, "copper_plate_merit_order": merit_order_bound(c), "variants": {}}
+        for name, spec in variants:
+            table = schedule_table(iters, spec) if spec is not None else None
+            tt, oo = solve_trace(c, x0, precision, iters, every, table=table)
+            row["variants"][name] = {"best": float(oo.min()), "final": float(oo[-1]), "ms": float(tt[-1])}
+            log(i, name, row["variants"][name])
+        out.append(row)
+    return {"iters": iters, "precision": "fp64" if precision == qg.QG_FP64 else "mixed", "rows": out,
+            "variants": {name: (list(spec) if spec else "constant lr 1e-3") for name, spec in variants}}
 
 
 def main(argv=None):
@@ -347,10 +400,21 @@ def main(argv=None):
     ap.add_argument("--warm-skip", type=float, default=0.25)
     ap.add_argument("--constant-lr", action="store_true", help="constant lr 1e-3 instead of the Sec. II-F schedule")
     ap.add_argument("--const-arm", action="store_true", help="add plain FP64 Adam at a constant lr for context")
+    ap.add_argument("--attainable", type=int, default=0, metavar="ITERS",
+                    help="instead: the best objective of long FP64 runs (ITERS iterations) per schedule variant")
+    ap.add_argument("--profiles", type=int, default=4, help="held-out profiles for --attainable")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     from .build import build
     build()
+    if a.attainable:
+        res = attainable(synth.rt617(), list(range(a.profiles)), a.attainable, log=lambda *s: print(*s, flush=True))
+        line = json.dumps(res)
+        print(line)
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(line + "\n")
+        return
     res = experiment(synth.rt617(), a.train, a.test, a.solve_iters, a.epochs, a.eval_iters, a.every, hidden=a.hidden,
                      schedule=None if a.constant_lr else SCHEDULE, warm_skip=a.warm_skip, const_arm=a.const_arm,
                      log=lambda *s: print(*s, flush=True))

@@ -22,7 +22,9 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("n_in,n_h,n_out,B", [(300, 128, 200, 16), (1111, 256, 777, 37)])
+# shapes: ragged features and batch (TMA reads beyond the tensors as zeros), several 128-row and
+# 256-column tiles, a long K split over many blocks (n_in 5003: 79 K blocks), the full 64-row batch
+@pytest.mark.parametrize("n_in,n_h,n_out,B", [(300, 128, 200, 16), (1111, 256, 777, 37), (5003, 384, 1500, 64)])
 def test_mlp_forward_and_gradients_match_oracle(qg, n_in, n_h, n_out, B):
     from oracle import mlp
     m = qg.qg_mlp_create(n_in, n_h, n_out, 64, seed=7)
@@ -57,6 +59,7 @@ def test_mlp_forward_and_gradients_match_oracle(qg, n_in, n_h, n_out, B):
     for k, sz in enumerate(sizes):
         assert rel(G[o:o + sz], Gr[o:o + sz]) <= 5e-3, k
         o += sz
+    qg.qg_mlp_check(m)  # no GEMM pipeline wait ran out
     qg.qg_mlp_destroy(m)
 
 
@@ -74,4 +77,25 @@ def test_mlp_training_reduces_the_loss(qg):
         qg.qg_mlp_train_step(m, X, Tg, B, 1e-3, 0.9, 0.999, loss)
     torch.cuda.synchronize()
     assert loss.item() < 0.05 * l0
+    qg.qg_mlp_check(m)
+    qg.qg_mlp_destroy(m)
+
+
+def test_mlp_batch_limit(qg):
+    with pytest.raises(qg.QGError) as ei:
+        qg.qg_mlp_create(16, 32, 8, 65, seed=1)
+    assert ei.value.code == qg.QG_ERR_UNSUPPORTED
+
+
+def test_mlp_forward_is_bitwise_repeatable(qg):
+    """Split-K partials are summed in a fixed order: the same input gives the same bits."""
+    n_in, n_h, n_out, B = 2222, 256, 640, 48
+    m = qg.qg_mlp_create(n_in, n_h, n_out, 64, seed=5)
+    x = torch.randn(B, n_in, generator=torch.Generator().manual_seed(2)).cuda()
+    y1 = torch.zeros(B, n_out, device="cuda")
+    y2 = torch.zeros(B, n_out, device="cuda")
+    qg.qg_mlp_forward(m, x, B, y1)
+    qg.qg_mlp_forward(m, x, B, y2)
+    qg.qg_mlp_check(m)
+    assert torch.equal(y1, y2) and bool(torch.isfinite(y1).all())
     qg.qg_mlp_destroy(m)
