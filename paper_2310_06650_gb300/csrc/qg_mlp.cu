@@ -121,6 +121,9 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// programmatic dependent launch: wait for the preceding kernels' results (a no-op without it)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -147,11 +150,13 @@ constexpr size_t umma_smem_bytes() {
 //   sum over the K blocks [s kbps, (s + 1) kbps) of A[m][k] B[n][k],
 // A (M x K) and B (N x K) BF16 behind the tensor maps tA (box 64 x 128) and tB (box 64 x BN); rows
 // and K beyond the tensors read as zeros.  Grid (ceil(M/128), ceil(N/BN), splits), 128 threads.
+// Launched as a programmatic dependent of the previous kernel: with a_static (A is not written by
+// the two kernels before it: the weights) the first stages' A tiles are requested before the wait.
 // A wait that runs out sets *err, drains what this block started and returns.
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(UTHREADS, 1)
     k_umma_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, float *__restrict__ P,
-                int M, int N, int nkb, int kbps, int trans, int *err) {
+                int M, int N, int nkb, int kbps, int trans, int a_static, int *err) {
   constexpr uint32_t A_BYTES = UM * UK * 2, B_BYTES = BN * UK * 2;
   constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;  // a power of two >= 32
   static_assert((BN & (BN - 1)) == 0 && BN >= 16 && BN <= 256, "BN");
@@ -159,12 +164,14 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char *sA = base, *sB = base + STAGES * A_BYTES;
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf;
+  __shared__ float s_ep[4][32][33];  // per warp: 32 rows x 32 columns of the tile, for row-wise stores
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_issued, s_consumed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * UM, n0 = blockIdx.y * BN;
   const int kb0 = blockIdx.z * kbps, nk = min(kbps, nkb - kb0);  // >= 1: the host sizes the splits so
   volatile int *abort = &s_abort;
+  const int pre = a_static ? min(nk, STAGES) : 0;  // stages whose A tile is requested before the wait
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -176,6 +183,10 @@ __global__ void __launch_bounds__(UTHREADS, 1)
     s_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int kb = 0; kb < pre; ++kb) {
+      mbar_expect_tx(&full[kb], A_BYTES + B_BYTES);
+      tma_load_2d(sA + kb * A_BYTES, &tA, &full[kb], (kb0 + kb) * UK, m0);
+    }
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -187,19 +198,22 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
+  pdl_wait();  // B, and the partial buffer this kernel overwrites, belong to the kernels before it
   if (warp == 0 && lane == 0) {  // producer: stage s holds K block kb, its u-th use
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t u = (uint32_t)(kb / STAGES);
-      if (kb >= STAGES && !mbar_wait(&empty[s], (u - 1) & 1, abort, true)) break;
-      mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
       const int kx = (kb0 + kb) * UK;  // a multiple of 64 elements: 128-byte aligned
-      tma_load_2d(sA + s * A_BYTES, &tA, &full[s], kx, m0);
+      if (kb >= pre) {
+        if (kb >= STAGES && !mbar_wait(&empty[s], (u - 1) & 1, abort, true)) break;
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        tma_load_2d(sA + s * A_BYTES, &tA, &full[s], kx, m0);
+      }
       tma_load_2d(sB + s * B_BYTES, &tB, &full[s], kx, n0);
       issued = kb + 1;
     }
-    s_issued = issued;
+    s_issued = max(issued, pre);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     constexpr uint32_t IDESC = umma_idesc<BN>();
     int consumed = 0;
@@ -226,25 +240,34 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   if (!*abort) {
     const int m = m0 + warp * 32 + lane;
     float *Ps = P + (long long)blockIdx.z * M * N;
+    if (trans) {  // C^T: for each column the warp's 32 lanes (rows) write 32 consecutive floats
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (m >= M) continue;
-      if (trans) {  // C^T: for each column the warp's 32 lanes write 32 consecutive floats
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (n0 + c0 + i < N) Ps[(long long)(n0 + c0 + i) * M + m] = v[i];
-      } else {
-        float *row = Ps + (long long)m * N + n0 + c0;
-        if (n0 + c0 + 16 <= N && (N & 3) == 0) {
-#pragma unroll
-          for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(row + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        } else {
+      for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (m < M)
 #pragma unroll
           for (int i = 0; i < 16; ++i)
-            if (n0 + c0 + i < N) row[i] = v[i];
+            if (n0 + c0 + i < N) Ps[(long long)(n0 + c0 + i) * M + m] = v[i];
+      }
+    } else {  // C: 32 x 32 pieces turned around in shared memory, each row written by the warp's lanes
+      float(*t)[33] = s_ep[warp];
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 32) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) t[lane][i] = v[i];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + 16), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) t[lane][16 + i] = v[i];
+        __syncwarp();
+        const int n = n0 + c0 + lane;
+        for (int r = 0; r < 32; ++r) {
+          const int mr = m0 + warp * 32 + r;
+          if (mr < M && n < N) Ps[(long long)mr * N + n] = t[r][lane];
         }
+        __syncwarp();
       }
     }
   }
@@ -267,6 +290,7 @@ __global__ void __launch_bounds__(UTHREADS, 1)
 // block (32, 8).
 __global__ void k_transpose_bf16(const float *__restrict__ src, long long lds, __nv_bfloat16 *__restrict__ dst,
                                  long long ldd, int rows, int cols) {
+  pdl_wait();
   __shared__ float t[32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
@@ -281,13 +305,13 @@ __global__ void k_transpose_bf16(const float *__restrict__ src, long long lds, _
 }
 
 // BF16 copy with a padded row stride: dst[r][c] (stride ldd) = src[r][c] (FP32, stride lds).
+// Grid (column chunks of 256, rows; the rows strided by gridDim.y): no index division per element.
 __global__ void k_rows_bf16(const float *__restrict__ src, long long lds, __nv_bfloat16 *__restrict__ dst, long long ldd,
                             int rows, int cols) {
-  const long long total = (long long)rows * cols;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / cols, c = i - r * cols;
-    dst[r * ldd + c] = __float2bfloat16_rn(src[r * lds + c]);
-  }
+  pdl_wait();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) dst[(long long)r * ldd + c] = __float2bfloat16_rn(src[(long long)r * lds + c]);
 }
 
 // Epilogue of the forward layers: Z = sum of split-K partials + bias (M x N); optionally ReLU;
@@ -296,6 +320,7 @@ __global__ void k_rows_bf16(const float *__restrict__ src, long long lds, __nv_b
 __global__ void k_fwd_epi(const float *__restrict__ P, int splits, const float *__restrict__ bias, float *__restrict__ Z,
                           __nv_bfloat16 *__restrict__ Hb, long long ldh, __nv_bfloat16 *__restrict__ HbT, long long ldt,
                           int M, int N, int relu) {
+  pdl_wait();
   const long long total = (long long)M * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     float z = 0.f;
@@ -315,6 +340,7 @@ __global__ void k_fwd_epi(const float *__restrict__ P, int splits, const float *
 __global__ void k_bwd_epi(const float *__restrict__ P, int splits, const float *__restrict__ Zmask, float *__restrict__ D,
                           __nv_bfloat16 *__restrict__ Db, long long ldd, __nv_bfloat16 *__restrict__ DbT, long long ldt,
                           int rows, int cols) {
+  pdl_wait();
   const long long total = (long long)rows * cols;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     float v = 0.f;
@@ -336,6 +362,7 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ Y, const
                                               __nv_bfloat16 *__restrict__ dYb, long long ldo,
                                               __nv_bfloat16 *__restrict__ dYbT, long long ldt, float *__restrict__ dY,
                                               double *part, int rows, int cols) {
+  pdl_wait();
   __shared__ double red[8];
   double acc = 0.0;
   const long long total = (long long)rows * cols;
@@ -359,16 +386,26 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ Y, const
   }
 }
 
-__global__ void k_loss_final(const double *part, int n, long long total, double *loss) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *loss = s / (double)total;
+// The mean of the block partials: one block of 256 threads, strided sums then a shuffle and
+// shared-memory tree (a fixed order).
+__global__ void __launch_bounds__(256) k_loss_final(const double *part, int n, long long total, double *loss) {
+  pdl_wait();
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    *loss = t / (double)total;
   }
 }
 
 // Bias gradient: column sums of D (B x N) in row order.
 __global__ void k_colsum(const float *__restrict__ D, int B, int N, float *__restrict__ out) {
+  pdl_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   float s = 0.f;
@@ -379,6 +416,7 @@ __global__ void k_colsum(const float *__restrict__ D, int B, int N, float *__res
 // Adam on the FP32 master parameters; the BF16 weight copies follow.
 __global__ void k_mlp_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
                            long long n, float lr, float b1, float b2, float c1, float c2, float eps) {
+  pdl_wait();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -405,6 +443,23 @@ __global__ void k_init(float *__restrict__ w, long long n, float scale, uint64_t
     const float u2 = (b >> 40) * (1.0f / 16777216.0f);
     w[i] = scale * sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
   }
+}
+
+// Launch as a programmatic dependent of the previous kernel in the stream (each kernel waits with
+// griddepcontrol.wait before it touches what earlier kernels wrote or read).
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8)); }
@@ -494,16 +549,17 @@ cudaError_t umma_prepare() {
 }
 
 // Split-K partials of C = A B^T (A: M x K with row stride lda, B: N x K with row stride ldb, both BF16)
-// into mm->part: [splits][M][N], or [splits][N][M] with trans.  Returns the number of splits, or 0
+// into mm->part: [splits][M][N], or [splits][N][M] with trans; with dst, C itself (one split) into dst.  Returns the number of splits, or 0
 // after recording an error.  Narrow products (N <= 64: the batch) take 64-column tiles and a
 // 4-stage ring; wide ones (the weight gradients, K = the batch) 256-column tiles and 2 stages.
+// a_static: A is a weight copy (not written by the kernels just before), requested before the wait.
 int gemm(qg_mlp *mm, const __nv_bfloat16 *A, long long lda, int M, const __nv_bfloat16 *B, long long ldb, int N, int K,
-         bool trans) {
+         bool trans, bool a_static, float *dst = nullptr) {
   const bool narrow = N <= 64;
   const int BN = narrow ? 64 : 256;
   const long long tiles = (long long)((M + UM - 1) / UM) * ((N + BN - 1) / BN);
   const int nkb = (K + UK - 1) / UK;
-  int splits = (int)std::max(1LL, std::min<long long>({64LL, (long long)nkb, (2LL * 152 + tiles - 1) / tiles}));
+  int splits = dst ? 1 : (int)std::max(1LL, std::min<long long>({64LL, (long long)nkb, (2LL * 152 + tiles - 1) / tiles}));
   while (splits > 1 && (long long)splits * M * N > mm->part_elems) --splits;
   const int kbps = (nkb + splits - 1) / splits;
   splits = (nkb + kbps - 1) / kbps;  // every split has at least one K block
@@ -512,17 +568,18 @@ int gemm(qg_mlp *mm, const __nv_bfloat16 *A, long long lda, int M, const __nv_bf
   if (!rc) rc = make_map(mm, &tb, B, N, K, ldb, BN);
   if (rc) return 0;
   const dim3 grid((M + UM - 1) / UM, (N + BN - 1) / BN, splits);
+  float *out = dst ? dst : mm->part;
   cudaError_t e;
   if (narrow) {
     e = umma_prepare<64, 4>();
     if (e == cudaSuccess)
-      k_umma_gemm<64, 4><<<grid, UTHREADS, umma_smem_bytes<64, 4>(), mm->stream>>>(ta, tb, mm->part, M, N, nkb, kbps,
-                                                                                  trans ? 1 : 0, mm->d_err);
+      e = pdl_launch(k_umma_gemm<64, 4>, grid, dim3(UTHREADS), umma_smem_bytes<64, 4>(), mm->stream, ta, tb, out, M,
+                     N, nkb, kbps, trans ? 1 : 0, a_static ? 1 : 0, mm->d_err);
   } else {
     e = umma_prepare<256, 2>();
     if (e == cudaSuccess)
-      k_umma_gemm<256, 2><<<grid, UTHREADS, umma_smem_bytes<256, 2>(), mm->stream>>>(ta, tb, mm->part, M, N, nkb, kbps,
-                                                                                    trans ? 1 : 0, mm->d_err);
+      e = pdl_launch(k_umma_gemm<256, 2>, grid, dim3(UTHREADS), umma_smem_bytes<256, 2>(), mm->stream, ta, tb, out,
+                     M, N, nkb, kbps, trans ? 1 : 0, a_static ? 1 : 0, mm->d_err);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -532,26 +589,29 @@ int gemm(qg_mlp *mm, const __nv_bfloat16 *A, long long lda, int M, const __nv_bf
   return splits;
 }
 
-// x (batch x I, FP32) into the BF16 operands xb [B][ld_i] and xt [I][ld_b]
-void load_x(qg_mlp *m, const float *x, int B) {
-  k_rows_bf16<<<grid_for((long long)B * m->n_in), 256, 0, m->stream>>>(x, m->n_in, m->xb, m->ld_i, B, m->n_in);
-  k_transpose_bf16<<<dim3((m->n_in + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, m->stream>>>(x, m->n_in, m->xt, m->ld_b,
-                                                                                            B, m->n_in);
+// x (batch x I, FP32) into the BF16 operand xb [B][ld_i] and, for training (the first layer's weight
+// gradient), xt [I][ld_b]
+void load_x(qg_mlp *m, const float *x, int B, bool transposed) {
+  pdl_launch(k_rows_bf16, dim3((m->n_in + 255) / 256, std::min(B, 65535)), dim3(256), 0, m->stream, x, m->n_in, m->xb,
+             m->ld_i, B, m->n_in);
+  if (transposed)
+    pdl_launch(k_transpose_bf16, dim3((m->n_in + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, m->stream, x, m->n_in, m->xt,
+               m->ld_b, B, m->n_in);
 }
 
 // Forward pass: the layers as C^T = W act^T (weights as the 128-row operand, the batch as N).
 int forward(qg_mlp *m, int B) {
   const int H = m->n_h, I = m->n_in, O = m->n_out;
-  int s = gemm(m, m->w1b, m->ld_i, H, m->xb, m->ld_i, B, I, true);
+  int s = gemm(m, m->w1b, m->ld_i, H, m->xb, m->ld_i, B, I, true, true);
   if (!s) return QG_ERR_CUDA;
-  k_fwd_epi<<<grid_for((long long)B * H), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b1, m->z1, m->h1b, m->ld_h, m->h1t,
-                                                               m->ld_b, B, H, 1);
-  if (!(s = gemm(m, m->w2b, m->ld_h, H, m->h1b, m->ld_h, B, H, true))) return QG_ERR_CUDA;
-  k_fwd_epi<<<grid_for((long long)B * H), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b2, m->z2, m->h2b, m->ld_h, m->h2t,
-                                                               m->ld_b, B, H, 1);
-  if (!(s = gemm(m, m->w3b, m->ld_h, O, m->h2b, m->ld_h, B, H, true))) return QG_ERR_CUDA;
-  k_fwd_epi<<<grid_for((long long)B * O), 256, 0, m->stream>>>(m->part, s, m->w + m->o_b3, m->y, nullptr, 0, nullptr, 0,
-                                                               B, O, 0);
+  pdl_launch(k_fwd_epi, dim3(grid_for((long long)B * H)), dim3(256), 0, m->stream, m->part, s, m->w + m->o_b1, m->z1,
+             m->h1b, m->ld_h, m->h1t, m->ld_b, B, H, 1);
+  if (!(s = gemm(m, m->w2b, m->ld_h, H, m->h1b, m->ld_h, B, H, true, true))) return QG_ERR_CUDA;
+  pdl_launch(k_fwd_epi, dim3(grid_for((long long)B * H)), dim3(256), 0, m->stream, m->part, s, m->w + m->o_b2, m->z2,
+             m->h2b, m->ld_h, m->h2t, m->ld_b, B, H, 1);
+  if (!(s = gemm(m, m->w3b, m->ld_h, O, m->h2b, m->ld_h, B, H, true, true))) return QG_ERR_CUDA;
+  pdl_launch(k_fwd_epi, dim3(grid_for((long long)B * O)), dim3(256), 0, m->stream, m->part, s, m->w + m->o_b3, m->y,
+             nullptr, 0, nullptr, 0, B, O, 0);
   return QG_OK;
 }
 
@@ -559,11 +619,16 @@ int forward(qg_mlp *m, int B) {
 void refresh_bf16(qg_mlp *m) {
   const int H = m->n_h, I = m->n_in, O = m->n_out;
   cudaStream_t s = m->stream;
-  k_rows_bf16<<<grid_for((long long)H * I), 256, 0, s>>>(m->w + m->o_w1, I, m->w1b, m->ld_i, H, I);
-  k_rows_bf16<<<grid_for((long long)H * H), 256, 0, s>>>(m->w + m->o_w2, H, m->w2b, m->ld_h, H, H);
-  k_rows_bf16<<<grid_for((long long)O * H), 256, 0, s>>>(m->w + m->o_w3, H, m->w3b, m->ld_h, O, H);
-  k_transpose_bf16<<<dim3((H + 31) / 32, (H + 31) / 32), dim3(32, 8), 0, s>>>(m->w + m->o_w2, H, m->w2t, m->ld_h, H, H);
-  k_transpose_bf16<<<dim3((H + 31) / 32, (O + 31) / 32), dim3(32, 8), 0, s>>>(m->w + m->o_w3, H, m->w3t, m->ld_o, O, H);
+  pdl_launch(k_rows_bf16, dim3((I + 255) / 256, std::min(H, 65535)), dim3(256), 0, s, m->w + m->o_w1, I, m->w1b, m->ld_i,
+             H, I);
+  pdl_launch(k_rows_bf16, dim3((H + 255) / 256, std::min(H, 65535)), dim3(256), 0, s, m->w + m->o_w2, H, m->w2b, m->ld_h,
+             H, H);
+  pdl_launch(k_rows_bf16, dim3((H + 255) / 256, std::min(O, 65535)), dim3(256), 0, s, m->w + m->o_w3, H, m->w3b, m->ld_h,
+             O, H);
+  pdl_launch(k_transpose_bf16, dim3((H + 31) / 32, (H + 31) / 32), dim3(32, 8), 0, s, m->w + m->o_w2, H, m->w2t,
+             m->ld_h, H, H);
+  pdl_launch(k_transpose_bf16, dim3((H + 31) / 32, (O + 31) / 32), dim3(32, 8), 0, s, m->w + m->o_w3, H, m->w3t,
+             m->ld_o, O, H);
 }
 
 }  // namespace
@@ -639,7 +704,7 @@ int qg_mlp_set_stream(qg_mlp *m, void *stream) {
 
 int qg_mlp_forward(qg_mlp *m, const float *x, int32_t batch, float *y) {
   if (!m || !x || !y || batch < 1 || batch > m->max_b) return m ? mfail(m, QG_ERR_INVALID_ARG, "forward arguments") : QG_ERR_INVALID_ARG;
-  load_x(m, x, batch);
+  load_x(m, x, batch, false);
   int rc = forward(m, batch);
   if (rc) return rc;
   cudaError_t e = cudaMemcpyAsync(y, m->y, sizeof(float) * batch * m->n_out, cudaMemcpyDeviceToDevice, m->stream);
@@ -653,37 +718,38 @@ int qg_mlp_train_step(qg_mlp *m, const float *x, const float *target, int32_t ba
     return m ? mfail(m, QG_ERR_INVALID_ARG, "train arguments") : QG_ERR_INVALID_ARG;
   const int B = batch, H = m->n_h, I = m->n_in, O = m->n_out;
   cudaStream_t s = m->stream;
-  load_x(m, x, B);
+  load_x(m, x, B, true);
   int rc = forward(m, B);
   if (rc) return rc;
   const long long ny = (long long)B * O;
   const int lb = grid_for(ny);
-  k_loss<<<lb, 256, 0, s>>>(m->y, target, m->dyb, m->ld_o, m->dyt, m->ld_b, m->dy, m->lpart, B, O);
-  if (loss) k_loss_final<<<1, 32, 0, s>>>(m->lpart, lb, ny, loss);
-  // layer 3: dW3 = dY^T H2 (K = the batch), db3 = colsum(dY), dH2 = dY W3 masked by relu'(Z2)
-  int sp = gemm(m, m->dyt, m->ld_b, O, m->h2t, m->ld_b, H, B, false);
+  pdl_launch(k_loss, dim3(lb), dim3(256), 0, s, m->y, target, m->dyb, m->ld_o, m->dyt, m->ld_b, m->dy, m->lpart, B,
+             O);
+  if (loss) pdl_launch(k_loss_final, dim3(1), dim3(256), 0, s, m->lpart, lb, ny, loss);
+  // layer 3: dW3 = dY^T H2 (K = the batch: one split, written straight into the gradient),
+  // db3 = colsum(dY), dH2 = dY W3 masked by relu'(Z2)
+  int sp = gemm(m, m->dyt, m->ld_b, O, m->h2t, m->ld_b, H, B, false, false, m->gw + m->o_w3);
   if (!sp) return QG_ERR_CUDA;
-  k_bwd_epi<<<grid_for((long long)O * H), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w3, nullptr, 0, nullptr, 0, O, H);
-  k_colsum<<<(O + 255) / 256, 256, 0, s>>>(m->dy, B, O, m->gw + m->o_b3);
-  if (!(sp = gemm(m, m->w3t, m->ld_o, H, m->dyb, m->ld_o, B, O, true))) return QG_ERR_CUDA;
-  k_bwd_epi<<<grid_for((long long)B * H), 256, 0, s>>>(m->part, sp, m->z2, m->dz2, m->dz2b, m->ld_h, m->dz2t, m->ld_b, B, H);
+  pdl_launch(k_colsum, dim3((O + 255) / 256), dim3(256), 0, s, m->dy, B, O, m->gw + m->o_b3);
+  if (!(sp = gemm(m, m->w3t, m->ld_o, H, m->dyb, m->ld_o, B, O, true, true))) return QG_ERR_CUDA;
+  pdl_launch(k_bwd_epi, dim3(grid_for((long long)B * H)), dim3(256), 0, s, m->part, sp, m->z2, m->dz2, m->dz2b, m->ld_h,
+             m->dz2t, m->ld_b, B, H);
   // layer 2
-  if (!(sp = gemm(m, m->dz2t, m->ld_b, H, m->h1t, m->ld_b, H, B, false))) return QG_ERR_CUDA;
-  k_bwd_epi<<<grid_for((long long)H * H), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w2, nullptr, 0, nullptr, 0, H, H);
-  k_colsum<<<(H + 255) / 256, 256, 0, s>>>(m->dz2, B, H, m->gw + m->o_b2);
-  if (!(sp = gemm(m, m->w2t, m->ld_h, H, m->dz2b, m->ld_h, B, H, true))) return QG_ERR_CUDA;
-  k_bwd_epi<<<grid_for((long long)B * H), 256, 0, s>>>(m->part, sp, m->z1, m->dz1, nullptr, 0, m->dz1t, m->ld_b, B, H);
+  if (!(sp = gemm(m, m->dz2t, m->ld_b, H, m->h1t, m->ld_b, H, B, false, false, m->gw + m->o_w2))) return QG_ERR_CUDA;
+  pdl_launch(k_colsum, dim3((H + 255) / 256), dim3(256), 0, s, m->dz2, B, H, m->gw + m->o_b2);
+  if (!(sp = gemm(m, m->w2t, m->ld_h, H, m->dz2b, m->ld_h, B, H, true, true))) return QG_ERR_CUDA;
+  pdl_launch(k_bwd_epi, dim3(grid_for((long long)B * H)), dim3(256), 0, s, m->part, sp, m->z1, m->dz1, nullptr, 0,
+             m->dz1t, m->ld_b, B, H);
   // layer 1
-  if (!(sp = gemm(m, m->dz1t, m->ld_b, H, m->xt, m->ld_b, I, B, false))) return QG_ERR_CUDA;
-  k_bwd_epi<<<grid_for((long long)H * I), 256, 0, s>>>(m->part, sp, nullptr, m->gw + m->o_w1, nullptr, 0, nullptr, 0, H, I);
-  k_colsum<<<(H + 255) / 256, 256, 0, s>>>(m->dz1, B, H, m->gw + m->o_b1);
+  if (!(sp = gemm(m, m->dz1t, m->ld_b, H, m->xt, m->ld_b, I, B, false, false, m->gw + m->o_w1))) return QG_ERR_CUDA;
+  pdl_launch(k_colsum, dim3((H + 255) / 256), dim3(256), 0, s, m->dz1, B, H, m->gw + m->o_b1);
   // Adam
   if (lr > 0) {
     m->step += 1;
     const double c1 = 1.0 / (1.0 - std::pow(beta1, (double)m->step));
     const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)m->step));
-    k_mlp_adam<<<grid_for(m->n_par), 256, 0, s>>>(m->w, m->gw, m->am, m->av, m->n_par, (float)lr, (float)beta1,
-                                                  (float)beta2, (float)c1, (float)c2, 1e-8f);
+    pdl_launch(k_mlp_adam, dim3(grid_for(m->n_par)), dim3(256), 0, s, m->w, m->gw, m->am, m->av, m->n_par, (float)lr,
+               (float)beta1, (float)beta2, (float)c1, (float)c2, 1e-8f);
     refresh_bf16(m);
   }
   cudaError_t e = cudaGetLastError();

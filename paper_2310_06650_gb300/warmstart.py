@@ -268,7 +268,7 @@ ARMS = (("plain_fp64", "FP64 from the copper-plate start"), ("mixed_lp", "mixed 
 
 def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, eval_iters: int, every: int,
                seed: int = 5000, hidden: int = 1024, schedule=SCHEDULE, warm_skip: float = 0.25,
-               const_arm: bool = False, bounds=None, log=print) -> dict:
+               const_arm: bool = False, bounds=None, eval_schedule="same", target_ratio=None, log=print) -> dict:
     """Train on n_train generated solves, then for n_test held-out profiles compare four Adam arms,
     {FP64, mixed precision} x {copper-plate start, learned start}, on GPU time to a target objective
     (eps = 0 scoring).  The target is 1% above the copper-plate bound when plain FP64 Adam from the
@@ -278,8 +278,10 @@ def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, e
     learned start takes the place of the early large steps) and their time includes the MLP
     inference.  Held-out profiles come from their own generator (seed + 1), so they do not depend on
     n_train.  bounds: optional per-profile lower bounds of Phi (dicts with "copper_plate" and
-    "contingency_bound"), against which the target is also stated.  const_arm adds, for context,
-    plain FP64 Adam with a constant lr of 1e-3."""
+    "contingency_bound"), against which the target is also stated; with target_ratio the target is
+    target_ratio x the profile's contingency-aware bound instead.  eval_schedule: the schedule spec of
+    the compared runs ("same": the training solves' schedule).  const_arm adds, for context, plain FP64
+    Adam with a constant lr of 1e-3."""
     import synth
     torch = __import__("torch")
     t0 = time.time()
@@ -296,7 +298,8 @@ def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, e
     hist = ws.train(prof, starts, sols, epochs)
     t_train = time.time() - t1
     log(f"trained {epochs} epochs in {t_train:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}")
-    table = schedule_table(eval_iters, schedule) if schedule else None
+    espec = schedule if isinstance(eval_schedule, str) and eval_schedule == "same" else eval_schedule
+    table = schedule_table(eval_iters, espec) if espec else None
     skip = int(round(warm_skip * eval_iters)) if schedule else 0
     table_b = table[skip:].contiguous() if table is not None else None
     rows = []
@@ -316,11 +319,15 @@ def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, e
             "warm_mixed": solve_trace(c, pred, qg.QG_MIXED, eval_iters - skip, every, table=table_b, t_start_ms=t_mlp),
         }
         ta, oa = traces["plain_fp64"]
-        target = 1.01 * bound
-        kind = "1% of copper-plate bound"
-        if not np.isfinite(time_to(ta, oa, target)):
-            target = 1.01 * float(oa.min())
-            kind = "1% above the best objective of plain FP64 Adam"
+        if target_ratio is not None and bounds is not None:
+            target = target_ratio * bounds[i]["contingency_bound"]
+            kind = f"{target_ratio} x the contingency-aware bound"
+        else:
+            target = 1.01 * bound
+            kind = "1% of copper-plate bound"
+            if not np.isfinite(time_to(ta, oa, target)):
+                target = 1.01 * float(oa.min())
+                kind = "1% above the best objective of plain FP64 Adam"
         row = {"bound": bound, "target": target, "target_kind": kind, "mlp_ms": t_mlp}
         if bounds is not None and i < len(bounds):
             row["target_over_copper_plate"] = target / bounds[i]["copper_plate"]
@@ -341,12 +348,54 @@ def experiment(case, n_train: int, n_test: int, solve_iters: int, epochs: int, e
 
     return {"n_train": n_train, "n_test": n_test, "solve_iters": solve_iters, "epochs": epochs,
             "eval_iters": eval_iters, "every": every, "schedule": list(schedule) if schedule else None,
+            "eval_schedule": list(espec) if espec else None,
             "warm_skip": warm_skip if schedule else 0.0, "gen_s": t_gen, "train_s": t_train,
             "loss_first": hist[0], "loss_last": hist[-1], "rows": rows,
             "median_ms": {arm: median(arm) for arm, _ in ARMS},
             "reached": {arm: int(sum(np.isfinite(r[arm]["ms"]) for r in rows)) for arm, _ in ARMS},
             "warm_faster": int(sum(r["warm_mixed"]["ms"] < r["plain_fp64"]["ms"] for r in rows)),
             "reached_1pct": int(sum(r["target_kind"].startswith("1% of") for r in rows))}
+
+
+def mlp_bench(case, hidden: int = 1024, batch: int = 64, reps: int = 20, seed: int = 0) -> dict:
+    """Device time of the warm-start network at the case's size (input T n, output n_x): the mean of
+    `reps` forward passes (x -> y: three tensor-core GEMMs and their epilogues), each after a 512 MB
+    write that evicts the weights from L2, and of `reps` training steps (forward, backward, Adam,
+    BF16 weight refresh).  The forward pass reads every BF16 weight once: its floor is those bytes
+    at the HBM bandwidth."""
+    torch = __import__("torch")
+    n_in, n_out = case.T * case.n_bus, case.n_x
+    m = qg.qg_mlp_create(n_in, hidden, n_out, batch, seed)
+    stream = torch.cuda.current_stream()
+    qg.qg_mlp_set_stream(m, stream.cuda_stream)
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn(batch, n_in, generator=g).cuda()
+    tgt = 0.1 * torch.randn(batch, n_out, generator=g).cuda()
+    y = torch.zeros(batch, n_out, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        qg.qg_mlp_forward(m, x, batch, y)
+        qg.qg_mlp_train_step(m, x, tgt, batch, 1e-4, 0.9, 0.999, loss)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k, (a, b) in enumerate(ev):
+        flush.fill_(k & 0xFF)
+        a.record(stream)
+        qg.qg_mlp_forward(m, x, batch, y)
+        b.record(stream)
+    et = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in et:
+        a.record(stream)
+        qg.qg_mlp_train_step(m, x, tgt, batch, 1e-4, 0.9, 0.999, loss)
+        b.record(stream)
+    torch.cuda.synchronize()
+    qg.qg_mlp_check(m)
+    qg.qg_mlp_destroy(m)
+    fwd = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    train = float(np.mean([a.elapsed_time(b) for a, b in et]))
+    wbytes = 2.0 * hidden * (n_in + hidden + n_out)
+    return {"shape": f"{n_in} -> {hidden} -> {hidden} -> {n_out}, batch {batch}", "forward_ms": fwd,
+            "train_step_ms": train, "weight_bytes_bf16": wbytes, "finite": bool(torch.isfinite(y).all().item())}
 
 
 # Schedule variants for the attainable-objective study: (name, spec) with spec the qg_schedule
@@ -403,10 +452,17 @@ def main(argv=None):
     ap.add_argument("--attainable", type=int, default=0, metavar="ITERS",
                     help="instead: the best objective of long FP64 runs (ITERS iterations) per schedule variant")
     ap.add_argument("--profiles", type=int, default=4, help="held-out profiles for --attainable")
+    ap.add_argument("--mlp-bench", action="store_true", help="instead: time the network at the rt617 size")
+    ap.add_argument("--eval-variant", default=None, help="schedule variant (VARIANTS name) of the compared runs")
+    ap.add_argument("--target-ratio", type=float, default=None,
+                    help="target = this x the contingency-aware bound (tests/golden/rt617_ttt_bounds.json)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     from .build import build
     build()
+    if a.mlp_bench:
+        print(json.dumps(mlp_bench(synth.rt617())))
+        return
     if a.attainable:
         res = attainable(synth.rt617(), list(range(a.profiles)), a.attainable, log=lambda *s: print(*s, flush=True))
         line = json.dumps(res)
@@ -415,8 +471,16 @@ def main(argv=None):
             with open(a.out, "w") as f:
                 f.write(line + "\n")
         return
+    bounds = None
+    bpath = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                         "rt617_ttt_bounds.json")
+    if os.path.exists(bpath):
+        with open(bpath) as f:
+            bounds = json.load(f)["rows"]
+    espec = dict(VARIANTS)[a.eval_variant] if a.eval_variant else "same"
     res = experiment(synth.rt617(), a.train, a.test, a.solve_iters, a.epochs, a.eval_iters, a.every, hidden=a.hidden,
                      schedule=None if a.constant_lr else SCHEDULE, warm_skip=a.warm_skip, const_arm=a.const_arm,
+                     bounds=bounds, eval_schedule=espec, target_ratio=a.target_ratio,
                      log=lambda *s: print(*s, flush=True))
     line = json.dumps(res)
     print(line)

@@ -166,3 +166,21 @@ def test_device_models_and_phase_shifters_are_refused():
             contingency_bound(bad)
     with pytest.raises(ValueError):
         contingency_bound(synth.with_transformers(c, 0.3, 4))
+
+
+def test_stored_time_to_target_bounds_match_the_oracle():
+    """tests/golden/rt617_ttt_bounds.json (written by make_ttt_bounds.py) holds the bounds that the
+    time-to-target comparison states its target against: recompute both bounds of the quickest
+    profile (the contingency-aware LP takes about 40 s there) and check the ordering of the rest."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rt617_ttt_bounds.json")
+    rows = json.load(open(path))["rows"]
+    base = synth.rt617()
+    prof = synth.load_profiles(base, len(rows), 5001)
+    for r in rows:
+        assert r["contingency_bound"] >= r["copper_plate"] > 0
+    quick = min(rows, key=lambda r: r["triples"])
+    c = synth.with_loads(base, prof[quick["profile"]])
+    assert copper_plate(c)[0] == pytest.approx(quick["copper_plate"], rel=1e-9)
+    assert contingency_bound(c)[0] == pytest.approx(quick["contingency_bound"], rel=1e-7)
