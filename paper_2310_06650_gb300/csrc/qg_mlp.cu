@@ -164,7 +164,6 @@ __global__ void __launch_bounds__(UTHREADS, 1)
   unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char *sA = base, *sB = base + STAGES * A_BYTES;
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf;
-  __shared__ float s_ep[4][32][33];  // per warp: 32 rows x 32 columns of the tile, for row-wise stores
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_issued, s_consumed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -250,8 +249,10 @@ __global__ void __launch_bounds__(UTHREADS, 1)
           for (int i = 0; i < 16; ++i)
             if (n0 + c0 + i < N) Ps[(long long)(n0 + c0 + i) * M + m] = v[i];
       }
-    } else {  // C: 32 x 32 pieces turned around in shared memory, each row written by the warp's lanes
-      float(*t)[33] = s_ep[warp];
+    } else {  // C: 32 x 32 pieces turned around in shared memory, each row written by the warp's lanes;
+      // the stage buffers are free by now (every TMA copy was consumed, every MMA has completed)
+      static_assert(4 * 32 * 33 * sizeof(float) <= STAGES * (A_BYTES + B_BYTES), "epilogue tile");
+      float(*t)[33] = reinterpret_cast<float(*)[33]>(base) + warp * 32;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN && n0 + c0 < N; c0 += 32) {
         float v[16];
