@@ -41,7 +41,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) per launch of the dominant kernel: the mean over the launches of one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, a few launches) of the current
 # kernel code; a kernel whose code changed since its capture gets None
-NCU_TRAFFIC = {("rt617", "s2", True): 2657900.0, ("rt617", "s2", False): 3395968.0}
+NCU_TRAFFIC = {("rt617", "s2", True): 2276096.0, ("rt617", "s2", False): 3390720.0}
 FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
 
 
@@ -187,6 +187,11 @@ def algorithmic(case, phase, mixed):
 def roofline(case, phase, ms, mixed, peaks, src, clocks):
     out = _roofline(case, phase, ms, mixed, peaks, src, clocks)
     out["traffic"] = NCU_TRAFFIC.get((case.name, phase, mixed))
+    if phase == "s2":
+        out["count"] = ("4 flop per (t, m, k) element: the two FMAs of F = f_m + L f_k and of the overload test, the "
+                        "method's work for every element (a non-overloaded one contributes the closed-form eps floor); "
+                        "the overloaded elements' soft-ReLU and sums are not counted")
+        out["traffic_source"] = "dram__bytes_read.sum + dram__bytes_write.sum of one single-kernel ncu capture of this code"
     return out
 
 
@@ -206,10 +211,11 @@ def _roofline(case, phase, ms, mixed, peaks, src, clocks):
         # double-FP32 emulation: ~11 FP32 instructions per FP64-class multiply-add
         amount = amount / 2.0 * 11.0 * 2.0
         peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-        note = "FP32 lanes x 2 x max SM clock; df32 counted as 11 FP32 ops per multiply-add"
+        note = "derived, not measured: FP32 lanes x 2 x max SM clock; df32 counted as 11 FP32 ops per multiply-add"
     else:
         peak = (N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12) if mixed else FP64_NOMINAL_TFLOPS
-        note = "152 SM x 128 FP32 lanes x 2 flop x max SM clock" if mixed else "FP64 nominal"
+        note = ("derived, not measured: 152 SM x 128 FP32 lanes x 2 flop x max SM clock" if mixed
+                else "FP64 nominal (not measured)")
     ach = amount / sec / 1e12
     return {"bound": "alu", "kernel": phase, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": None, "peak_source": note}

@@ -1453,6 +1453,7 @@ void qg_default_options(qg_options *o) {
 
 int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const qg_horizon *hor,
                     const qg_contingencies *ctg, const qg_options *opt) {
+  NvtxRange range("qg_create (set-up)");
   g_create_error.clear();
   if (!out) return fail(nullptr, QG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -1578,6 +1579,7 @@ int qg_set_stream(qg_ctx *h, void *stream) {
 }
 
 int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g) {
+  NvtxRange range("qg_eval_grad");
   if (!h || !x) return h ? fail(h, QG_ERR_INVALID_ARG, "x is NULL") : QG_ERR_INVALID_ARG;
   int rc = run_eval(h, x, false, 0, 0, 0, nullptr, 0);
   if (rc) return rc;
@@ -1640,6 +1642,7 @@ bool pinned(const void *p) {
 extern "C" {
 
 int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g) {
+  NvtxRange range("qg_eval_grad_host");
   if (!h || !x) return h ? fail(h, QG_ERR_INVALID_ARG, "x is NULL") : QG_ERR_INVALID_ARG;
   // pinned buffers (and no per-kernel timing): one cached graph of the copies and the evaluation,
   // re-captured when the buffers change (the same buffers as the cached graph's skip the check)
@@ -1773,11 +1776,13 @@ double mag_scale(double t) {
 extern "C" {
 
 int qg_solve(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, double beta2, double *obj_trace) {
+  NvtxRange range("qg_solve");
   return solve_graph(h, x, iters, lr, beta1, beta2, obj_trace, nullptr, iters, true);
 }
 
 int qg_solve_schedule(qg_ctx *h, void *x, int32_t iters, const double *sched, int32_t sched_len, int32_t restart,
                       double beta1, double beta2, double *obj_trace) {
+  NvtxRange range("qg_solve_schedule");
   if (!sched || sched_len < 1) return h ? fail(h, QG_ERR_INVALID_ARG, "empty schedule") : QG_ERR_INVALID_ARG;
   return solve_graph(h, x, iters, 0.0, beta1, beta2, obj_trace, sched, sched_len, restart != 0);
 }
@@ -2067,6 +2072,7 @@ int32_t qg_launches_per_eval(const qg_ctx *h) {
 }
 
 int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t shape[2]) {
+  NvtxRange range("qg_autotune");
   if (!h) return QG_ERR_INVALID_ARG;
   if (!x || reps < 1) return fail(h, QG_ERR_INVALID_ARG, "qg_autotune needs x and reps >= 1");
   int maxT = 0, max_nmt = 0;

@@ -4,8 +4,19 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only NVTX v3: a no-op unless a profiler injects itself
 
 #include "../../include/qg.h"
+
+namespace qg {
+// A named NVTX range over a scope (a stage launch, a public call), visible on a profiler's timeline.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace qg
 
 namespace qg {
 

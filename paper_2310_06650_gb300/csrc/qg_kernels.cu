@@ -2140,6 +2140,7 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     }
   };
   mark(ev, 0, s);
+  nvtxRangePushA("qg stage 1");  // one NVTX range per stage, closed at the next stage's launch
   if (P.sp) {
     // sparse mode: forward solve theta' = Yhat^-1 p_inj before the flows of stage 1
     const Inst &I = P.tab.I[0];
@@ -2154,12 +2155,18 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     e = cudaGetLastError();
   }
   mark(ev, 1, s);
+  nvtxRangePop();
+  nvtxRangePushA("qg stage 2 (contingencies)");
   if (P.s2.n_blocks > 0)  // no contingencies: nothing for stage 2
     go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB, d.score != 0), d, P.tab, P.s2, (const Real *)x, o2);
   mark(ev, 2, s);
+  nvtxRangePop();
+  nvtxRangePushA("qg stage 3");
   if (P.tab.s3q > 1) go(k_s3<Real, Dc, S3_SPLIT_MAX>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
   else go(k_s3<Real, Dc, 1>, P.s3.n_blocks, 0, d, P.tab, P.s3, (const Real *)x);
   mark(ev, 3, s);
+  nvtxRangePop();
+  nvtxRangePushA("qg stage 4");
   // stage 4 with the device updates (small plans on the mixed path) or without them (a separate
   // instantiation: the fused role's registers would cost the lean one its occupancy)
   if (P.tab.fuse) {
@@ -2177,11 +2184,14 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
     if (P.sp_bwa_blocks > 0) go(k_sp_back<Real, Dc, true>, P.sp_bwa_blocks, 0, d, I);
   }
   mark(ev, 4, s);
+  nvtxRangePop();
+  nvtxRangePushA("qg stage 5 + closing kernel");
   if (P.s5.n_blocks > 0) {  // the mixed path's dense mode updates the devices in stage 4
     if (adam) go(k_s5<Real, Dc, true>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
     else go(k_s5<Real, Dc, false>, P.s5.n_blocks, 0, d, P.tab, P.s5, x);
   }
   if (close) go(k_finish<Real, Dc>, 1, 0, d, P.tab, adam ? 1 : 0);  // the objective, step += 1 with Adam
+  nvtxRangePop();
   mark(ev, 5, s);
   return e;
 }
