@@ -404,6 +404,15 @@ const char *qg_mlp_last_error(const qg_mlp *m);
  * with a message if so, else QG_OK. */
 int qg_mlp_check(qg_mlp *m);
 
+/* Index-checked builds (the library compiled with QG_CHECK_BOUNDS, `python -m
+ * paper_2310_06650_gb300.build --check-bounds`): every access of the stage kernels to one of the
+ * library's device arrays (or to a caller's array a handle was given) is checked against the
+ * address ranges of those arrays; an access that falls outside all of them reads or writes a
+ * dummy word instead, and the first one is recorded.  qg_bounds_report synchronizes the device and
+ * returns 1 with that access's source line (of qg_kernels.cu) and address (host pointers, may be
+ * NULL), or 0 if none was seen; QG_ERR_UNSUPPORTED in the normal build. */
+int qg_bounds_report(int64_t *line, uint64_t *addr);
+
 /* Build identification: major*10000 + minor*100 + patch. */
 int qg_version(void);
 

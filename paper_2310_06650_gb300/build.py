@@ -36,16 +36,59 @@ def _newest_source_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths if os.path.exists(p))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if stale) and return the path of libqg.so."""
-    os.makedirs(OUT, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_source_mtime():
-        return LIB
+def checked_source(text: str) -> str:
+    """The index-checked form of qg_kernels.cu: every d.<array>[i] becomes qg_at(d.<array>, i, __LINE__)
+    (nested accesses too); no line breaks are added, so __LINE__ stays the original line."""
+    out, i, n = [], 0, len(text)
+    ident = set("abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ0123456789_.")
+    while i < n:
+        j = text.find("d.", i)
+        if j < 0:
+            out.append(text[i:])
+            break
+        k = j + 2
+        while k < n and (text[k].isalnum() or text[k] == "_"):
+            k += 1
+        if (j > 0 and text[j - 1] in ident) or k == j + 2 or k >= n or text[k] != "[":
+            out.append(text[i:j + 2])
+            i = j + 2
+            continue
+        depth, e = 0, k
+        while e < n:  # the matching bracket
+            if text[e] == "[":
+                depth += 1
+            elif text[e] == "]":
+                depth -= 1
+                if depth == 0:
+                    break
+            e += 1
+        out.append(text[i:j])
+        out.append(f"qg_at({text[j:k]}, (long long)({checked_source(text[k + 1:e])}), __LINE__)")
+        i = e + 1
+    return "".join(out)
+
+
+def build(force: bool = False, verbose: bool = False, check_bounds: bool = False) -> str:
+    """Compile (if stale) and return the path of libqg.so.  check_bounds: the index-checked library
+    (QG_CHECK_BOUNDS, every d.<array>[i] of the stage kernels checked) in _build/checked/."""
+    out = os.path.join(OUT, "checked") if check_bounds else OUT
+    lib = os.path.join(out, "libqg.so")
+    os.makedirs(out, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_source_mtime():
+        return lib
     nvcc = _nvcc()
+    extra = ["-DQG_CHECK_BOUNDS", "-I", CSRC] if check_bounds else []
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out, os.path.splitext(src)[0] + ".o")
+        path = os.path.join(CSRC, src)
+        if check_bounds and src == "qg_kernels.cu":
+            with open(path) as f:
+                text = f.read()
+            path = os.path.join(out, src)
+            with open(path, "w") as f:
+                f.write(f'#line 1 "{os.path.join(CSRC, src)}"\n' + checked_source(text))
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", path, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -55,13 +98,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check_bounds="--check-bounds" in sys.argv))

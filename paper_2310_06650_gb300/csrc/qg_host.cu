@@ -142,6 +142,7 @@ int dalloc(qg_ctx *h, T **p, size_t count) {
   cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   h->allocs.push_back(*p);
+  bounds_register(*p, count * sizeof(T));
   e = cudaMemset(*p, 0, count * sizeof(T));
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
   return QG_OK;
@@ -1175,7 +1176,10 @@ void free_all(qg_ctx *h) {
       cudaEventDestroy(e);
       e = nullptr;
     }
-  for (void *p : h->allocs) cudaFree(p);
+  for (void *p : h->allocs) {
+    bounds_unregister(p);
+    cudaFree(p);
+  }
   h->allocs.clear();
 }
 
@@ -1212,6 +1216,7 @@ void dfree(qg_ctx *h, const void *p) {
   if (!p) return;
   auto it = std::find(h->allocs.begin(), h->allocs.end(), const_cast<void *>(p));
   if (it != h->allocs.end()) {
+    bounds_unregister(*it);
     cudaFree(*it);
     h->allocs.erase(it);
   }
@@ -1366,6 +1371,7 @@ int noalloc_scratch(qg_ctx *h, unsigned char **out) {
     if (e != cudaSuccess || !ptr)
       return fail(h, QG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+    bounds_register(ptr, NOALLOC_SCRATCH_BYTES);
   }
   *out = g_noalloc_ptr[dev];
   return QG_OK;
@@ -1428,6 +1434,8 @@ int eval_noalloc(qg_ctx *h, Dev<Real, Dc> d, const void *x, double *obj, void *g
   d.g = static_cast<Real *>(g);
   d.trace = nullptr;
   d.trace_len = 0;
+  bounds_register(obj, sizeof(double) * h->n_inst);  // the caller's arrays (index-checked builds)
+  bounds_register(g, sizeof(Real) * h->n_x);
   // the closing kernel reads and rewrites the step counter (the rest is fully written before it is read)
   CUDA_TRY(h, cudaMemsetAsync(d.step, 0, sizeof(long long), h->stream));
   cudaError_t e = launch_eval<Real, Dc>(d, h->plan, x, false, true, h->stream, nullptr);
@@ -1714,6 +1722,8 @@ int solve_graph(qg_ctx *h, void *x, int32_t iters, double lr, double beta1, doub
   if ((obj_trace || sched) && restart)
     CUDA_TRY(h, cudaMemcpyAsync(h->d_step0, h->d_step, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
   if (!obj_trace && !sched) len = 0;
+  if (obj_trace) bounds_register(obj_trace, sizeof(double) * (size_t)len * h->n_inst);  // index-checked builds
+  if (sched) bounds_register(sched, sizeof(double) * 3 * (size_t)len);
   const bool same = h->gexec && h->g_x == x && h->g_lr == lr && h->g_b1 == beta1 && h->g_b2 == beta2 &&
                     h->g_trace == obj_trace && h->g_sched == sched && h->g_trace_len == len;
   if (!same) drop_graphs(h);
@@ -2251,6 +2261,16 @@ int qg_tile_shape(const qg_ctx *h, int32_t inst, int32_t shape[2]) {
   shape[0] = h->plan.tab.I[inst].ctg_tb;
   shape[1] = h->plan.tab.I[inst].ctg_mg;
   return QG_OK;
+}
+
+int qg_bounds_report(int64_t *line, uint64_t *addr) {
+  long long l = 0;
+  unsigned long long a = 0;
+  const int r = bounds_report(&l, &a);
+  if (r < 0) return QG_ERR_UNSUPPORTED;
+  if (line) *line = l;
+  if (addr) *addr = a;
+  return r;
 }
 
 int qg_version(void) { return 302; }

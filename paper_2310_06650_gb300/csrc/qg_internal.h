@@ -244,6 +244,15 @@ struct Plan {
   int sp_bwa_blocks;   // k_sp_back adjoint pass
 };
 
+// Index-checked build (compiled with QG_CHECK_BOUNDS): the device keeps the address ranges of the
+// library's device arrays (and of the caller's arrays a handle stores), and every access
+// d.<array>[i] in the stage kernels is checked against them; a miss records the first bad source line
+// and address and reads or writes a dummy word instead.  In the normal build these are no-ops.
+void bounds_register(const void *p, size_t bytes);
+void bounds_unregister(const void *p);
+// 1: a checked access missed (line, address of the first); 0: none; -1: not an index-checked build.
+int bounds_report(long long *line, unsigned long long *addr);
+
 // One evaluation (with adam, the fused projected Adam update); with close, ended by the closing
 // kernel (the objective sum; step += 1 with adam), else the objective is left in the slots for a
 // later launch_finish.

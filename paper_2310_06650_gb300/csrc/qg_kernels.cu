@@ -27,13 +27,95 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <cstdint>
 #include <utility>
+#include <vector>
 
 #include "qg_internal.h"
 
 namespace qg {
+
+// ---------------------------------------------------------------------------------------------
+// index-checked build (QG_CHECK_BOUNDS): the build step rewrites every d.<array>[i] of this file
+// as qg_at(d.<array>, i, __LINE__), which checks the element's address against the registered
+// device arrays
+// ---------------------------------------------------------------------------------------------
+
+#ifdef QG_CHECK_BOUNDS
+constexpr int QG_MAX_RANGES = 8192;
+struct QgRange {
+  unsigned long long lo, hi;  // [lo, hi)
+};
+__device__ QgRange g_qg_ranges[QG_MAX_RANGES];  // sorted by lo, disjoint
+__device__ int g_qg_nranges;
+__device__ int g_qg_bad_line;                 // first failing access: its source line (0: none)
+__device__ unsigned long long g_qg_bad_addr;  // and its address
+__device__ __align__(16) unsigned char g_qg_dummy[64];
+
+template <typename T>
+__device__ __forceinline__ T &qg_at(T *p, long long i, int line) {
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p + i);
+  int lo = 0, hi = g_qg_nranges - 1;
+  while (lo <= hi) {  // the last range starting at or below a
+    const int mid = (lo + hi) >> 1;
+    if (g_qg_ranges[mid].lo <= a) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  if (hi >= 0 && a + sizeof(T) <= g_qg_ranges[hi].hi) return p[i];
+  if (atomicCAS(&g_qg_bad_line, 0, line) == 0) g_qg_bad_addr = a;
+  return *reinterpret_cast<T *>(g_qg_dummy);
+}
+
+namespace {
+std::mutex g_ranges_mu;
+std::map<unsigned long long, unsigned long long> g_ranges;  // base -> bytes, every live registration
+
+void upload_ranges() {
+  std::vector<QgRange> v;
+  for (const auto &r : g_ranges) v.push_back({r.first, r.first + r.second});
+  if (v.size() > (size_t)QG_MAX_RANGES) v.resize(QG_MAX_RANGES);
+  const int n = (int)v.size();
+  cudaDeviceSynchronize();  // no kernel reads the table while it changes (debug build)
+  if (n) cudaMemcpyToSymbol(g_qg_ranges, v.data(), sizeof(QgRange) * n);
+  cudaMemcpyToSymbol(g_qg_nranges, &n, sizeof(int));
+}
+}  // namespace
+
+void bounds_register(const void *p, size_t bytes) {
+  if (!p || !bytes) return;
+  std::lock_guard<std::mutex> lock(g_ranges_mu);
+  auto &b = g_ranges[reinterpret_cast<unsigned long long>(p)];
+  if (b == bytes) return;
+  b = bytes;
+  upload_ranges();
+}
+
+void bounds_unregister(const void *p) {
+  std::lock_guard<std::mutex> lock(g_ranges_mu);
+  if (g_ranges.erase(reinterpret_cast<unsigned long long>(p))) upload_ranges();
+}
+
+int bounds_report(long long *line, unsigned long long *addr) {
+  int l = 0;
+  unsigned long long a = 0;
+  cudaDeviceSynchronize();
+  cudaMemcpyFromSymbol(&l, g_qg_bad_line, sizeof(int));
+  cudaMemcpyFromSymbol(&a, g_qg_bad_addr, sizeof(a));
+  if (line) *line = l;
+  if (addr) *addr = a;
+  return l ? 1 : 0;
+}
+#else
+void bounds_register(const void *, size_t) {}
+void bounds_unregister(const void *) {}
+int bounds_report(long long *line, unsigned long long *addr) {
+  if (line) *line = 0;
+  if (addr) *addr = 0;
+  return -1;
+}
+#endif
 
 // ---------------------------------------------------------------------------------------------
 // double-FP32 arithmetic (Knuth's TwoSum, FMA-based TwoProd)

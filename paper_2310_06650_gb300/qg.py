@@ -63,9 +63,11 @@ class qg_options(C.Structure):
 
 
 def _load():
-    if not os.path.exists(LIB):
-        raise ImportError(f"libqg.so is not built ({LIB}); run paper_2310_06650_gb300.build.build()")
-    lib = C.CDLL(LIB)
+    # QG_LIBRARY: another build of the same library (the index-checked one of build(check_bounds=True))
+    path = os.environ.get("QG_LIBRARY") or LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libqg.so is not built ({path}); run paper_2310_06650_gb300.build.build()")
+    lib = C.CDLL(path)
     vp = C.c_void_p
     sig = {
         "qg_default_options": (None, [C.POINTER(qg_options)]),
@@ -113,6 +115,7 @@ def _load():
         "qg_mlp_get_grads": (C.c_int, [vp, vp]),
         "qg_mlp_last_error": (C.c_char_p, [vp]),
         "qg_mlp_check": (C.c_int, [vp]),
+        "qg_bounds_report": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -129,7 +132,7 @@ EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", 
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error",
-            "qg_mlp_check")
+            "qg_mlp_check", "qg_bounds_report")
 PHASES = ("s1", "s2", "s3", "s4", "s5", "adam")
 
 
@@ -487,6 +490,16 @@ def qg_mlp_get_grads(m: int, g) -> None:
 
 def qg_mlp_last_error(m: Optional[int] = None) -> str:
     return _lib.qg_mlp_last_error(m).decode(errors="replace")
+
+
+def qg_bounds_report():
+    """Index-checked builds: None if no checked access missed, else (source line, address) of the first;
+    raises QGError (QG_ERR_UNSUPPORTED) on the normal build."""
+    line, addr = C.c_int64(0), C.c_uint64(0)
+    rc = _lib.qg_bounds_report(C.byref(line), C.byref(addr))
+    if rc < 0:
+        raise QGError(rc, "qg_bounds_report: not an index-checked build")
+    return (line.value, addr.value) if rc == 1 else None
 
 
 def qg_mlp_check(m: int) -> None:

@@ -249,3 +249,24 @@ def test_library_schedule_matches_the_closed_forms(qg, iters):
     assert np.all(np.diff(got[:, 0]) <= 0) and np.all(np.diff(got[:, 1]) <= 0)
     with pytest.raises(qg.QGError):
         qg.qg_schedule(0, 5e-3, 1e-5, 1e-1, 1e-5)
+
+
+def test_normal_build_has_no_index_checks(qg):
+    """qg_bounds_report answers only in the index-checked build."""
+    with pytest.raises(qg.QGError) as ei:
+        qg.qg_bounds_report()
+    assert ei.value.code == qg.QG_ERR_UNSUPPORTED
+
+
+def test_checked_source_transform():
+    """The checked build's rewrite of qg_kernels.cu: every d.<array>[i] (nested ones too) becomes a
+    checked access; other subscripts are untouched and no line is added."""
+    from paper_2310_06650_gb300.build import CSRC, checked_source
+    t = "a = d.x[d.y[i] + 1] * ad.z[3] + d.w + d.q[t[2]];\nb = tab.I[0]; d.g[k] = v;"
+    out = checked_source(t)
+    assert out == ("a = qg_at(d.x, (long long)(qg_at(d.y, (long long)(i), __LINE__) + 1), __LINE__) * ad.z[3] + d.w + "
+                   "qg_at(d.q, (long long)(t[2]), __LINE__);\nb = tab.I[0]; qg_at(d.g, (long long)(k), __LINE__) = v;")
+    src = open(os.path.join(CSRC, "qg_kernels.cu")).read()
+    chk = checked_source(src)
+    assert chk.count("\n") == src.count("\n")
+    assert chk.count("qg_at(d.") > 200
