@@ -368,7 +368,9 @@ def gpu_leg(args, rank, world, local_rank):
         "e2e": {"value": world * K / mix["e2e_s"], "unit": UNIT, "rounds": "median of 3 rounds of K calls",
                 "h2d_bytes_per_step": 8 * case.n_x,
                 "d2h_bytes_per_step": 8 * (case.n_x + 1),
-                "call": "qg_eval_grad_host (pinned host x -> device, evaluation, objective + gradient -> host)"},
+                "call": "qg_eval_grad_host (pinned host x -> device, evaluation, objective + gradient -> host; the "
+                        "conversion kernels read x and write g and the objective through the pinned buffers' device "
+                        "mappings)"},
         "gpu_launches": mix["launches"] * K,
         "clocks": mix["clocks"],
         "phases_ms": {k: round(v * 1e3, 3) / 1e3 for k, v in phases.items()},

@@ -209,11 +209,12 @@ int qg_eval_grad(qg_ctx *h, const void *x, double *obj, void *g);
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
 int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g);
 
-/* qg_eval_grad on host buffers: copies x (qg_num_vars doubles) to the device,
- * evaluates, and copies obj (n_inst doubles) and g (qg_num_vars doubles, may be
- * NULL) back; synchronizes.  In QG_MIXED mode the copies convert to/from float.
- * With page-locked buffers the copies and the evaluation replay from a graph
- * cached for those buffers (re-captured when they change).  Returns
+/* qg_eval_grad on host buffers: moves x (qg_num_vars doubles) to the device,
+ * evaluates, and moves obj (n_inst doubles) and g (qg_num_vars doubles, may be
+ * NULL) back; synchronizes.  In QG_MIXED mode the moves convert to/from float.
+ * With page-locked buffers the evaluation replays from a graph cached for those
+ * buffers (re-captured when they change), in which kernels read x and write obj
+ * and g through the buffers' device mappings (copies when a buffer has none).  Returns
  * QG_ERR_NONFINITE when an instance's objective is NaN or Inf (x holds one, or
  * a term overflowed); obj and g are written as computed all the same. */
 int qg_eval_grad_host(qg_ctx *h, const double *x, double *obj, double *g);

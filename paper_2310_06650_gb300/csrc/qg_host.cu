@@ -1341,6 +1341,23 @@ __global__ void k_f2d(const float *a, double *b, long long n) {
     b[i] = (double)a[i];
 }
 
+// Host-buffer evaluation through the caller's page-locked buffers' device mappings: x read into the
+// handle's variable array (rounded to FP32 on the mixed path) ...
+template <typename Real>
+__global__ void k_host_in(const double *hx, Real *xs, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    xs[i] = (Real)hx[i];
+}
+
+// ... and the gradient and the objectives written back (each may be NULL).
+template <typename Real>
+__global__ void k_host_out(const Real *g, double *hg, long long n, const double *obj, double *hobj, int n_inst) {
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (hobj && i0 < n_inst) hobj[i0] = obj[i0];
+  if (!hg) return;
+  for (long long i = i0; i < n; i += (long long)gridDim.x * blockDim.x) hg[i] = (double)g[i];
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -1612,9 +1629,37 @@ int qg_eval_grad_noalloc(qg_ctx *h, const void *x, double *obj, void *g) {
 namespace {
 
 // The work of qg_eval_grad_host on h->stream: copy x in, evaluate, copy the gradient and objective out.
+// The device address through which a kernel reaches the page-locked host buffer p (NULL for NULL,
+// for pageable memory, or when the buffer has no device mapping).
+void *device_view(const void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int host_eval_work(qg_ctx *h, const double *x, double *obj, double *g) {
   const long long n = h->n_x;
   const int nb = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  // page-locked buffers that kernels can reach: read x and write g, obj from the kernels themselves
+  // (no copy nodes); otherwise copies through the handle's staging array
+  const double *dx = static_cast<const double *>(device_view(x));
+  double *dobj = static_cast<double *>(device_view(obj)), *dg = static_cast<double *>(device_view(g));
+  if (dx && (!obj || dobj) && (!g || dg)) {
+    bounds_register(dx, sizeof(double) * n);  // index-checked builds: the caller's arrays
+    if (mixed(h)) k_host_in<float><<<nb, 256, 0, h->stream>>>(dx, (float *)h->d_xs, n);
+    else k_host_in<double><<<nb, 256, 0, h->stream>>>(dx, (double *)h->d_xs, n);
+    CUDA_TRY(h, cudaGetLastError());
+    int rc = run_eval(h, h->d_xs, false, 0, 0, 0, nullptr, 0);
+    if (rc) return rc;
+    if (mixed(h)) k_host_out<float><<<nb, 256, 0, h->stream>>>((const float *)h->d_g, dg, g ? n : 0, h->d_obj, dobj, h->n_inst);
+    else k_host_out<double><<<nb, 256, 0, h->stream>>>((const double *)h->d_g, dg, g ? n : 0, h->d_obj, dobj, h->n_inst);
+    CUDA_TRY(h, cudaGetLastError());
+    return QG_OK;
+  }
   if (mixed(h)) {
     CUDA_TRY(h, cudaMemcpyAsync(h->d_xd, x, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
     k_d2f<<<nb, 256, 0, h->stream>>>(h->d_xd, (float *)h->d_xs, n);
