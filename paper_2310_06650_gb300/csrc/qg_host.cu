@@ -738,8 +738,10 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   else
     add_span(P.s4, ceil_div(H0.n - 1, 32), ceil_div(H0.T, DCF_TC), 0, R_SDCA);
   if (!fuse) {
-    const int gen_pb = h->opt.precision == QG_FP64 ? 32 : NTHR;
+    // FP64: one warp of pairs per block (GB300's FP64 pipe costs as much for a warp with one active
+    // lane as for a full one), 8 pairs of four lanes each without on-status, else 32 of one
     for (int b = 0; b < B; ++b) {
+      const int gen_pb = h->opt.precision == QG_FP64 ? (I[b].uc ? 32 : 8) : NTHR;
       I[b].gen_first = P.s5.n_blocks;
       I[b].gen_pb = gen_pb;
       I[b].gen_nb = ceil_div((long long)I[b].T * I[b].G, gen_pb);

@@ -201,21 +201,36 @@ __device__ __forceinline__ float dsqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ void dsincos(double a, double *s, double *c) { sincos(a, s, c); }
 __device__ __forceinline__ void dsincos(float a, float *s, float *c) { sincosf(a, s, c); }
 
-// soft-ReLU sigma_s(u) = sqrt(max(u,0)^2 + eps^2) and its derivative (Sec. II-C footnote)
+__device__ __forceinline__ double drsqrt(double v) { return rsqrt(v); }
+__device__ __forceinline__ float drsqrt(float v) { return rsqrtf(v); }
+
+// sqrt(a) and w / sqrt(a) for a >= 0 through one reciprocal square root r (CUDA's rsqrt: a few ulp):
+// the value a r and the derivative factor w r, where the square root and the division would each be a
+// long FP64 sequence on GB300's FP64 pipe; a = 0 gives (0, 0)
+template <typename Real>
+__device__ __forceinline__ void root_and_ratio(Real a, Real w, Real &s, Real &q) {
+  if (a > Real(0)) {
+    const Real r = drsqrt(a);
+    s = a * r;
+    q = w * r;
+  } else {
+    s = Real(0);
+    q = Real(0);
+  }
+}
+
+// soft-ReLU sigma_s(u) = sqrt(max(u,0)^2 + eps^2) and its derivative max(u,0) / sigma_s(u)
+// (Sec. II-C footnote)
 template <typename Real>
 __device__ __forceinline__ void soft_relu(Real u, Real eps, Real &val, Real &der) {
   const Real m = u > Real(0) ? u : Real(0);
-  const Real s = dsqrt(m * m + eps * eps);
-  val = s;
-  der = s > Real(0) ? m / s : Real(0);
+  root_and_ratio(m * m + eps * eps, m, val, der);
 }
 
-// soft-abs |u|_s = sqrt(u^2 + eps^2) and its derivative
+// soft-abs |u|_s = sqrt(u^2 + eps^2) and its derivative u / |u|_s
 template <typename Real>
 __device__ __forceinline__ void soft_abs(Real u, Real eps, Real &val, Real &der) {
-  const Real s = dsqrt(u * u + eps * eps);
-  val = s;
-  der = s > Real(0) ? u / s : Real(0);
+  root_and_ratio(u * u + eps * eps, u, val, der);
 }
 
 template <typename T>
@@ -1674,6 +1689,77 @@ __device__ void gen_update(const Dev<Real, Dc> &d, const Inst &I, int t, int gl,
   }
 }
 
+// The FP64 path's device update without on-status variables, one (period, device) pair over four
+// lanes (part = lane & 3): 0 the energy cost, eta, the balance adjoint, the headroom and the ramp
+// into period t, and p's update; 1 q's; 2 r's (with the headroom derivative from lane 0); 3 the
+// ramp terms of period t + 1 that involve p_t (handed to lane 0).  Each gradient is summed in the
+// order of gen_update, so the results are bitwise its; the dependent FP64 chain (square roots and
+// divisions of the soft-ReLUs and of Adam) is about a third as long, and the work spreads over
+// four times as many warps.  Every lane of the warp calls it (the shuffles are warp-wide).
+template <typename Real, typename Dc, bool ADAM>
+__device__ void gen_update_lanes(const Dev<Real, Dc> &d, const Inst &I, int t, int gl, int part, bool on,
+                                 const GenIn<Real> &g, Dc eta, const AdamCoef<Real> &ac, Obj3<Dc> &acc,
+                                 Real *__restrict__ x) {
+  const long long G = I.G;
+  const HP<Real> hp = hparams(d);
+  const Real wr = d.rho * hp.beta;
+  Real grad = 0, hd = 0, rp = 0;
+  if (on) {
+    const Real dt = d.dt[I.tp0 + t];
+    const long long tb = I.tb0 + (long long)t * I.n;
+    const long long ko = I.tg0 + (long long)t * G + gl;
+    const double p64 = g.p;
+    if (part == 0) {
+      Real en, den, val, der;
+      energy_cost(d, g, en, den);
+      grad = dt * g.sg * den + g.sg * (DcOps<Dc>::to_real(eta) - d.dP[tb + g.bus]);
+      acc.v[0] = DcOps<Dc>::from_real(dt * (g.sg * en + g.cr * g.r));
+      soft_relu(Real(p64 + (double)g.r - g.pmax64), hp.eps, val, der);
+      acc.v[1] = DcOps<Dc>::from_real(wr * val);
+      hd = wr * der;
+      grad += hd;
+      if (t >= 1) {  // ramp terms of period t
+        const double pp = ADAM ? d.pold[ko - G] : x[g.kp - G];
+        const double lim = g.ramp64 * d.lim_dt[I.tp0 + t];
+        Real v1, d1, v2, d2;
+        soft_relu(Real(p64 - pp - lim), hp.eps, v1, d1);
+        soft_relu(Real(pp - p64 - lim), hp.eps, v2, d2);
+        acc.v[2] = DcOps<Dc>::from_real(wr * (v1 + v2));
+        grad += wr * (d1 - d2);
+      }
+    } else if (part == 1) {
+      grad = -g.sg * d.dQ[tb + g.bus];
+    } else if (part == 2) {
+      grad = dt * g.cr - d.dZ[I.tz0 + (long long)t * I.Z + g.zn];
+    } else if (t + 1 < I.T) {  // ramp terms of period t + 1 that involve p_t
+      const double pn = ADAM ? d.pold[ko + G] : x[g.kp + G];
+      const double lim = g.ramp64 * d.lim_dt[I.tp0 + t + 1];
+      Real v1, d1, v2, d2;
+      soft_relu(Real(pn - p64 - lim), hp.eps, v1, d1);
+      soft_relu(Real(p64 - pn - lim), hp.eps, v2, d2);
+      rp = wr * (d2 - d1);
+    }
+  }
+  const Real from3 = __shfl_xor_sync(0xffffffffu, rp, 3);  // lane 3 -> lane 0 of the pair
+  const Real from0 = __shfl_xor_sync(0xffffffffu, hd, 2);  // lane 0 -> lane 2 of the pair
+  if (!on || part == 3) return;
+  if (part == 0 && t + 1 < I.T) grad += from3;
+  if (part == 2) grad += from0;
+  const long long k = part == 0 ? g.kp : part == 1 ? g.kq : g.kr;
+  if (ADAM) {
+    Real xk = part == 0 ? g.p : part == 1 ? g.q : g.r;
+    Real mk = g.am[0], vk = g.av[0], lo = g.lo[0], hi = g.hi[0];
+    if (part == 1) { mk = g.am[1]; vk = g.av[1]; lo = g.lo[1]; hi = g.hi[1]; }
+    if (part == 2) { mk = g.am[2]; vk = g.av[2]; lo = g.lo[2]; hi = g.hi[2]; }
+    adam_update(xk, grad, mk, vk, lo, hi, ac.b1, ac.b2, ac.c1, ac.c2, ac.lr, ac.eps, d.paper_eps);
+    x[k] = xk;
+    d.am[k] = mk;
+    d.av[k] = vk;
+  } else {
+    d.g[k] = grad;
+  }
+}
+
 // Transformer x of period t: dPhi/dtau from the AC terms (stage 3), and dPhi/dphi = -(the AC
 // adjoint of delta) + b_sr dPhi/db, where dPhi/db = dz/dp_x - (E_hat eta)_x is the contingency
 // term's phase-shift gradient (Eq. 2nd_lin_sys_phase plus the direct term of p = f + b);
@@ -1735,6 +1821,20 @@ __global__ void __launch_bounds__(NTHR) k_s5(const __grid_constant__ Dev<Real, D
   if (w.role == R_XF) {
     pdl_wait();
     s5_xf<Real, Dc, ADAM>(d, I, t, w.sub, x, ac);
+  } else if (sizeof(Real) == 8 && !I.uc) {  // FP64 without on-status: four lanes per pair
+    Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
+    const int e = w.sub * I.gen_pb + (int)(threadIdx.x >> 2), part = threadIdx.x & 3;
+    const bool on = (int)threadIdx.x < 4 * I.gen_pb && e < I.T * I.G;
+    const int tg = on ? e / I.G : 0, gl = on ? e - tg * I.G : 0;
+    const GenIn<Real> g = gen_load<Real, Dc, ADAM>(d, I, tg, gl, x);
+    pdl_wait();
+    Dc eta = DcOps<Dc>::zero();
+    if (on && part == 0) {
+      const Dc *et = d.gip + I.gi0 + (long long)tg * (I.Gc + 1);  // written by stage 4 or the adjoint solve
+      eta = d.sp ? DcOps<Dc>::add(et[g.gb], DcOps<Dc>::neg(DcOps<Dc>::mul(et[I.Gc], DcOps<Dc>::inv_n(I)))) : et[g.gb];
+    }
+    if (threadIdx.x < 32) gen_update_lanes<Real, Dc, ADAM>(d, I, tg, gl, part, on, g, eta, ac, acc, x);
+    write_obj(d.objp, d.n_obj12 + I.gen_slot0 + (blockIdx.x - I.gen_first), acc);
   } else {
     Obj3<Dc> acc = obj3<Dc>(T_COST, T_ZHEAD, T_ZRAMP);
     // (period, device) pairs packed densely over the instance's device blocks
