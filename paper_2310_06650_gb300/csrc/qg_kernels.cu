@@ -204,18 +204,22 @@ __device__ __forceinline__ void dsincos(float a, float *s, float *c) { sincosf(a
 __device__ __forceinline__ double drsqrt(double v) { return rsqrt(v); }
 __device__ __forceinline__ float drsqrt(float v) { return rsqrtf(v); }
 
-// sqrt(a) and w / sqrt(a) for a >= 0 through one reciprocal square root r (CUDA's rsqrt: a few ulp):
-// the value a r and the derivative factor w r, where the square root and the division would each be a
-// long FP64 sequence on GB300's FP64 pipe; a = 0 gives (0, 0)
+// sqrt(a) and w / sqrt(a) for a >= 0.  Finite a > 0: through one reciprocal square root r (CUDA's
+// rsqrt: a few ulp), the value a r and the factor w r, where the square root and the division would
+// each be a long FP64 sequence on GB300's FP64 pipe; a = 0 gives (0, 0); +inf and NaN take the plain
+// square root and division, so that they propagate as they would there.
 template <typename Real>
 __device__ __forceinline__ void root_and_ratio(Real a, Real w, Real &s, Real &q) {
-  if (a > Real(0)) {
+  if (a == Real(0)) {
+    s = Real(0);
+    q = Real(0);
+  } else if (a < Real(INFINITY)) {
     const Real r = drsqrt(a);
     s = a * r;
     q = w * r;
   } else {
-    s = Real(0);
-    q = Real(0);
+    s = dsqrt(a);
+    q = w / s;
   }
 }
 
