@@ -41,7 +41,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) per launch of the dominant kernel: the mean over the launches of one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, a few launches) of the current
 # kernel code; a kernel whose code changed since its capture gets None
-NCU_TRAFFIC = {("rt617", "s2", True): 2276096.0, ("rt617", "s2", False): 3390720.0}
+NCU_TRAFFIC = {("rt617", "s2", True): 2272000.0, ("rt617", "s2", False): 3396608.0}
 FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
 
 
