@@ -269,6 +269,13 @@ int qg_schedule(double *out, int32_t iters, double lr0, double lrf, double eps0,
  * (with commit the four u-scaled limits).  Synchronizes the stream. */
 int qg_breakdown(qg_ctx *h, double *out);
 
+/* The base DC flows f_t of the last evaluation (Eq. p_flow with the uniform slack of Sec. II-E and
+ * the phase shifters' own flows), as the FP32 values the contingency screen reads: host array of
+ * sum over instances of T M floats, instance-major, each instance [T][M].  On the mixed path they
+ * are the double-FP32 products rounded once to FP32, on the FP64 path the FP64 flows rounded once.
+ * Synchronizes the stream. */
+int qg_dc_flows(qg_ctx *h, float *out);
+
 /* Adam step counter (for checkpoint/resume together with x, m, v);
  * qg_set_step(h, 0) also zeroes the moments that qg_solve keeps in the handle. */
 int qg_get_step(qg_ctx *h, int64_t *step);

@@ -1865,6 +1865,16 @@ int qg_breakdown(qg_ctx *h, double *out) {
   return QG_OK;
 }
 
+int qg_dc_flows(qg_ctx *h, float *out) {
+  if (!h || !out) return QG_ERR_INVALID_ARG;
+  long long n = 0;
+  for (int b = 0; b < h->n_inst; ++b) n += (long long)h->plan.tab.I[b].T * h->plan.tab.I[b].M;
+  const float *src = mixed(h) ? h->d32.f32 : h->d64.f32;
+  CUDA_TRY(h, cudaMemcpyAsync(out, src, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return QG_OK;
+}
+
 int qg_get_step(qg_ctx *h, int64_t *step) {
   if (!h || !step) return QG_ERR_INVALID_ARG;
   long long s = 0;

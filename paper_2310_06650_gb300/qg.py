@@ -116,6 +116,7 @@ def _load():
         "qg_mlp_last_error": (C.c_char_p, [vp]),
         "qg_mlp_check": (C.c_int, [vp]),
         "qg_bounds_report": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
+        "qg_dc_flows": (C.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -132,7 +133,7 @@ EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", 
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error",
-            "qg_mlp_check", "qg_bounds_report")
+            "qg_mlp_check", "qg_bounds_report", "qg_dc_flows")
 PHASES = ("s1", "s2", "s3", "s4", "s5", "adam")
 
 
@@ -490,6 +491,13 @@ def qg_mlp_get_grads(m: int, g) -> None:
 
 def qg_mlp_last_error(m: Optional[int] = None) -> str:
     return _lib.qg_mlp_last_error(m).decode(errors="replace")
+
+
+def qg_dc_flows(h: int, n: int) -> np.ndarray:
+    """The last evaluation's base DC flows as the contingency screen reads them (n = sum of T M)."""
+    out = np.zeros(n, dtype=np.float32)
+    _check(_lib.qg_dc_flows(h, out.ctypes.data_as(C.c_void_p)), h)
+    return out
 
 
 def qg_bounds_report():
