@@ -54,6 +54,8 @@ extern "C" {
 enum { QG_FP64 = 0, QG_MIXED = 1 };                              /* qg_options.precision */
 enum { QG_LODF_F32 = 0, QG_LODF_BF16 = 1, QG_LODF_BF16X2 = 2 };  /* qg_options.lodf_dtype (mixed) */
 enum { QG_DC_AUTO = 0, QG_DC_DENSE = 1, QG_DC_SPARSE = 2 };      /* qg_options.dc_solver */
+enum { QG_CTG_BOUND_AUTO = 0, QG_CTG_BOUND_OFF = 1,               /* qg_options.ctg_bound */
+       QG_CTG_BOUND_EAGER = 2, QG_CTG_BOUND_LAZY = 3 };
 
 typedef struct qg_ctx qg_ctx; /* opaque handle; owns all device memory it allocates */
 
@@ -145,6 +147,19 @@ typedef struct {
                         * Ks = ceil(ctg_frac K) outages per instance (qg_ctg_select; initially the
                         * first Ks), through a compacted line-outage block, and records their
                         * scores (qg_ctg_scores) */
+  int32_t ctg_bound;   /* bound test ahead of the contingency screen (Sec. II-E): each warp of the
+                        * contingency kernel first bounds its 8 branches x 64 outages over 8 periods by
+                        * max|L| max|f_k| against the branches' clearance, and screens elements only
+                        * where that bound fails.  The classification, and so every result, is
+                        * bitwise the same with or without it.  QG_CTG_BOUND_OFF: no bound test;
+                        * QG_CTG_BOUND_EAGER: the test, with the line-outage tile loaded up front;
+                        * QG_CTG_BOUND_LAZY: the tests of a batch of tiles first, from per-branch
+                        * clearances computed once per evaluation (one more kernel), and tiles staged,
+                        * loaded and screened only where the test fails; QG_CTG_BOUND_AUTO (0, the
+                        * default): the test, lazy where instances with M Ks >= 2^22 hold at least
+                        * half of the handle's T M Ks elements (large grids, where most of it passes),
+                        * eager otherwise.  Device memory: 1,024 ceil(M/64) ceil(Ks/64) + 256 T
+                        * ceil(M/64) bytes per instance. */
 } qg_options;
 
 /* Fill *opt with the defaults: c_p = c_q = 1e4, c_s = c_rz = rho = 1e3,

@@ -31,6 +31,7 @@ constexpr int SPARSE_AUTO_N = 4096; // QG_DC_AUTO picks the sparse factor above 
 constexpr int TAIL_DEGREE = 32;     // minimum-degree elimination stops above this degree
 constexpr long long CTG_WAVE = 152 * 3;  // contingency blocks resident at once (152 SMs x 3 blocks)
 constexpr long long SMALL_PLAN = 65536;  // branch-periods of a plan that takes the latency layouts
+constexpr long long CTG_LARGE = 1LL << 22;  // (monitored branch, outage) pairs per period of a large grid
 
 // Contingency-block shape of a plan (stage 2): how many period chunks each 64 x 64 tile is split
 // into (ntc) and how many monitored-branch tiles one block walks (mg); 0 picks the heuristic.
@@ -589,7 +590,7 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   std::memset(&P, 0, sizeof(P));
   P.tab.n_inst = B;
   long long x0 = 0, tb0 = 0, tm0 = 0, tg0 = 0, tz0 = 0, tk0 = 0, pg0 = 0, l0 = 0, pm0 = 0, pk0 = 0, gi0 = 0, tx0 = 0,
-            pf0 = 0;
+            pf0 = 0, lm0 = 0, rm0 = 0;
   int xf0 = 0;
   // Contingency block shape, shared by the batch: about one wave of CTG_WAVE blocks when the
   // 64 x 64 tiles are few (the periods split across blocks), several waves when they are many
@@ -617,6 +618,20 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
   long long bp = 0;
   for (int b = 0; b < B; ++b) bp += (long long)h->hi[b].M * h->hi[b].T;
   const bool small_mixed = h->opt.precision == QG_MIXED && bp <= SMALL_PLAN;
+  // bound test of the contingency screen: on unless switched off.  The on-demand path pays where most
+  // (warp, chunk) pairs pass the test, as on large meshed grids, whose line-outage rows are mostly
+  // small entries: by default it is taken when instances of at least CTG_LARGE (monitored branch,
+  // outage) pairs per period hold at least half of the plan's elements; otherwise the eager path
+  // (each tile staged and loaded up front)
+  long long el_all = 0, el_large = 0;
+  for (int b = 0; b < B; ++b) {
+    const long long mk = (long long)h->hi[b].M * h->hi[b].Ks, el = mk * h->hi[b].T;
+    el_all += el;
+    if (mk >= CTG_LARGE) el_large += el;
+  }
+  const int cb = h->opt.ctg_bound;
+  const int ctg_bound = cb != QG_CTG_BOUND_OFF;
+  const int ctg_lazy = cb == QG_CTG_BOUND_LAZY || (cb == QG_CTG_BOUND_AUTO && el_all > 0 && 2 * el_large >= el_all);
   P.tab.s3q = small_mixed ? S3_SPLIT_MAX : 1;
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
@@ -642,7 +657,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     D.bal0 = bal0; D.n_bal_pack = (int)H.bal_code.size() / PACK;
     D.adj0 = adj0; D.n_adj_pack = (int)H.adj_code.size() / PACK;
     D.x0 = x0; D.tb0 = tb0; D.tm0 = tm0; D.tg0 = tg0; D.tz0 = tz0; D.tk0 = tk0; D.pg0 = pg0; D.l0 = l0;
-    D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0; D.pf0 = pf0;
+    D.pm0 = pm0; D.pk0 = pk0; D.gi0 = gi0; D.pf0 = pf0; D.lm0 = lm0; D.rm0 = rm0;
+    D.ctg_bound = ctg_bound; D.ctg_lazy = ctg_lazy;
     D.inv_n = 1.0 / H.n;
     D.hours = 0.0;
     for (int t = 0; t < H.T; ++t) D.hours += H.dt[t];
@@ -652,6 +668,9 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     tb0 += (long long)H.T * H.n; tm0 += (long long)H.T * H.M; tg0 += (long long)H.T * H.G;
     tz0 += (long long)H.T * H.Z; tk0 += (long long)H.T * H.Ks; pg0 += (long long)H.M * D.Gc; l0 += (long long)H.M * D.Kp;
     pf0 += (long long)D.n_kt * H.T * D.n_mt;
+    lm0 += (long long)D.n_kt * 4 * D.n_mt * CT_BM;
+    rm0 += (long long)H.T * D.n_mt * CT_BM;  // ctg_ntc ceil(ctg_tb / 8) <= T chunks, whatever the shape
+    if (D.ctg_lazy && D.n_kt > 0) P.ctg_lazy = 1;
     pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.Ks; gi0 += (long long)H.T * (D.Gc + 1);
     bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.Ks; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();
@@ -799,6 +818,7 @@ int gather_lodf(qg_ctx *h, const Dev<Real, Dc> &d, int b) {
   }
   if (e == cudaSuccess && d.lodf64)
     e = launch_gather<double>(h->lodf64_full, d.lodf64, sel, f0, I.l0, H.M, Kpf, I.K, I.Kp, 0.0, h->stream);
+  if (e == cudaSuccess) e = launch_lmax(d.lodf, d.lodf_dtype, const_cast<float *>(d.lmax), I, h->stream);
   if (e != cudaSuccess) return fail(h, QG_ERR_CUDA, std::string("line-outage gather: ") + cudaGetErrorString(e));
   return QG_OK;
 }
@@ -1023,6 +1043,16 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
     if ((rc = upload(h, &q, lodf))) return rc;
     d.lodf64 = q;
   }
+  {  // row maxima of the line-outage block for the stage-2 bound test
+    long long nl = 0;
+    for (int b = 0; b < B; ++b) nl += (long long)P.tab.I[b].n_kt * 4 * P.tab.I[b].n_mt * CT_BM;
+    float *lm;
+    if ((rc = dalloc(h, &lm, (size_t)std::max(nl, 1LL)))) return rc;
+    d.lmax = lm;
+  }
+  if (!h->screen)
+    for (int b = 0; b < B; ++b)
+      CUDA_TRY(h, launch_lmax(d.lodf, d.lodf_dtype, const_cast<float *>(d.lmax), P.tab.I[b], h->stream));
   if (h->screen) {  // the uploaded blocks are the full ones; the kernels read compacted copies
     h->lodf_full = const_cast<void *>(d.lodf);
     h->lodf64_full = const_cast<double *>(d.lodf64);
@@ -1131,6 +1161,13 @@ int build_device(qg_ctx *h, Dev<Real, Dc> &d, const std::vector<int> &slot_map) 
   unsigned char *pf;
   if ((rc = dalloc(h, &pf, (size_t)std::max(1LL, sPF)))) return rc;
   d.pmf = pf;
+  {
+    long long sRM = 0;
+    for (int b = 0; b < B; ++b) sRM += (long long)P.tab.I[b].T * P.tab.I[b].n_mt * CT_BM;
+    float *rm;
+    if ((rc = dalloc(h, &rm, (size_t)std::max(1LL, sRM)))) return rc;
+    d.ctg_rmin = rm;
+  }
   Dc *op;
   d.n_obj12 = (int)slot_map.size();
   d.n_gen_slots = P.n_gen_slots;
@@ -1258,7 +1295,7 @@ int replan_dev(qg_ctx *h, Dev<Real, Dc> &d, const Knobs &kn) {
   int *si;
   if ((rc = upload(h, &si, slot_map))) return rc;
   d.slot_map = si;
-  const cudaError_t e = prepare_eval<Real, Dc>(P.maxTB, h->screen);
+  const cudaError_t e = prepare_eval<Real, Dc>(P.maxTB, h->screen, P.ctg_lazy != 0);
   if (e != cudaSuccess) {
     cudaGetLastError();  // a refused attribute is not a sticky error
     return fail(h, QG_ERR_UNSUPPORTED, std::string("prepare_eval: ") + cudaGetErrorString(e));
@@ -1430,6 +1467,9 @@ size_t carve_scratch(const qg_ctx *h, unsigned char *base, size_t cap, Dev<Real,
     long long sPF = 0;
     for (int b = 0; b < h->n_inst; ++b) sPF += (long long)P.tab.I[b].n_kt * P.tab.I[b].T * P.tab.I[b].n_mt;
     d.pmf = take(std::max(1LL, sPF));
+    long long sRM = 0;
+    for (int b = 0; b < h->n_inst; ++b) sRM += (long long)P.tab.I[b].T * P.tab.I[b].n_mt * CT_BM;
+    d.ctg_rmin = (float *)take(4 * std::max(1LL, sRM));
   }
   d.gip = (Dc *)take(D * sGI); d.objp = (Dc *)take(D * (size_t)d.n_obj_slots * N_TERMS);
   d.terms = (double *)take(sizeof(double) * N_TERMS * h->n_inst);
@@ -1500,6 +1540,7 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
   if (o.lodf_dtype < 0 || o.lodf_dtype > 2) return reject(QG_ERR_INVALID_ARG, "lodf_dtype");
   if (o.dc_solver < QG_DC_AUTO || o.dc_solver > QG_DC_SPARSE) return reject(QG_ERR_INVALID_ARG, "dc_solver");
   if (!(o.ctg_frac >= 0.0) || !std::isfinite(o.ctg_frac)) return reject(QG_ERR_INVALID_ARG, "ctg_frac");
+  if (o.ctg_bound < QG_CTG_BOUND_AUTO || o.ctg_bound > QG_CTG_BOUND_LAZY) return reject(QG_ERR_INVALID_ARG, "ctg_bound");
   if (o.dc_solver == QG_DC_SPARSE && n_inst > 1)
     return reject(QG_ERR_UNSUPPORTED, "the sparse DC solver takes one instance per handle");
   if (!(o.eps >= 0) || !(o.beta >= 0) || !(o.c_p >= 0) || !(o.c_q >= 0) || !(o.c_s >= 0) || !(o.c_rz >= 0) ||
@@ -1555,8 +1596,8 @@ int qg_create_batch(qg_ctx **out, int32_t n_inst, const qg_network *net, const q
   }
   rc = mixed(h) ? build_device<float, df32>(h, h->d32, slot_map) : build_device<double, double>(h, h->d64, slot_map);
   if (!rc) {
-    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->plan.maxTB, h->screen)
-                             : prepare_eval<double, double>(h->plan.maxTB, h->screen);
+    cudaError_t e = mixed(h) ? prepare_eval<float, df32>(h->plan.maxTB, h->screen, h->plan.ctg_lazy != 0)
+                             : prepare_eval<double, double>(h->plan.maxTB, h->screen, h->plan.ctg_lazy != 0);
     if (e != cudaSuccess) rc = fail(h, QG_ERR_UNSUPPORTED, std::string("prepare_eval: ") + cudaGetErrorString(e));
   }
   if (rc) {
@@ -2132,7 +2173,8 @@ int qg_ctg_scores(qg_ctx *h, double *z) {
 int32_t qg_launches_per_eval(const qg_ctx *h) {
   if (!h) return QG_ERR_INVALID_ARG;
   const Plan &P = h->plan;
-  const int s2 = P.s2.n_blocks > 0 ? 1 : 0;  // no contingencies: no stage 2
+  // no contingencies: no stage 2; the on-demand contingency path adds the clearance kernel before it
+  const int s2 = P.s2.n_blocks > 0 ? 1 + (P.ctg_lazy ? 1 : 0) : 0;
   // + 1: the closing kernel (the mixed path's dense mode updates the devices in stage 4)
   if (!P.sp) return 3 + s2 + (P.s5.n_blocks > 0 ? 1 : 0) + 1;
   return 4 + s2 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0) + 1;

@@ -57,6 +57,13 @@ struct Inst {
   long long l0;          // line-outage block, M x Kp, row m
   long long pm0, pk0;    // contingency partials: [n_kt][T][M] and [n_mg][T][K]
   long long pf0;         // flags of the row partials: [n_kt][T][n_mt], 1 where a 64-row tile has any
+  long long lm0;         // bound-test row maxima of the line-outage block: [n_kt 4][n_mt 64]
+  long long rm0;         // clearance minima per chunk of 8 periods (on-demand path): [ctg_ntc NCH][n_mt 64]
+                         // with NCH = ceil(ctg_tb / 8), inside T n_mt 64 floats
+  int ctg_bound;         // 1: stage 2 bounds each (warp, chunk of periods) before its element screen
+  int ctg_lazy;          // 1: on-demand path: the bound tests of a batch of tiles come first, from the
+                         // clearance minima of k_ctg_margin; only tiles where some warp fails are
+                         // staged, and only failing warps load their piece of the line-outage tile
   long long gi0;         // adjoint DC products of the sparse mode: [T][Gc + 1] (generator buses,
                          // transformers, then n mean(eta))
   long long tx0;         // per-period transformer arrays: [T][X]
@@ -152,6 +159,10 @@ struct Dev {
   const void *lodf;                   // [sum M Kp]: float / bf16 / bf16x2 (mixed) or float screening copy
                                       // (FP64); NaN at pads and at each outage's own branch
   const double *lodf64;               // [sum M Kp] FP64 path only
+  float *ctg_rmin;                    // per instance at rm0: clearance minima of k_ctg_margin (on-demand path)
+  const float *lmax;                  // per instance at lm0, [n_kt 4][n_mt 64]: the largest |L[m, k]| over each
+                                      // group of 16 outage columns (as the stage-2 screen reads L; NaN
+                                      // ignored), 0 on pad rows; the bound test of the contingency screen
   const Real *lo, *hi;                // clip box [n_x]
   // sparse DC mode (one instance): node positions = eliminated nodes in elimination order, then
   // the tail nodes whose Schur complement S is held through its inverse; node-major work arrays
@@ -231,6 +242,7 @@ struct Plan {
   long long n_x;
   int maxT;
   int maxTB;  // largest period chunk of a contingency block (sizes its shared memory)
+  int ctg_lazy;  // some instance takes the on-demand contingency path (k_ctg_margin runs before stage 2)
   int n_gen_slots;  // objective reduction slots of the stage-5 device blocks
   int n_fold_slots; // objective reduction slots of the stage-3 fold blocks
   // sparse DC mode (instance 0 only): grids of the solve kernels
@@ -261,7 +273,11 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *x, bo
                         cudaStream_t s, cudaEvent_t *ev);
 
 template <typename Real, typename Dc>
-cudaError_t prepare_eval(int maxTB, bool score);
+cudaError_t prepare_eval(int maxTB, bool score, bool lazy);
+
+// Row maxima of instance I's line-outage block for the stage-2 bound test (Dev::lmax at I.lm0), from
+// the block as stored (lodf, of type dtype); rerun whenever the block changes.
+cudaError_t launch_lmax(const void *lodf, int dtype, float *lmax, const Inst &I, cudaStream_t s);
 
 // Closing kernel of a graph of n fused iterations whose evaluations were launched without one: the
 // last iteration's objective, then step += n.

@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -360,6 +361,12 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
   float d;
   asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+// min of three FP32 values (sm_100+); like fminf, a NaN operand is ignored
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
   return d;
 }
 
@@ -830,6 +837,67 @@ __device__ __forceinline__ void lodf_load4(const void *base, long long idx, int 
 template <typename Real>
 __host__ __device__ constexpr int ctg_tch() { return 8; }
 
+// Clearance of a monitored branch in one period for the bound test of the contingency screen: a
+// value r <= sqrt(-(qmax2 - s_ctg^2)) (1 - 2^-20) - |f_m|, every step rounded down, or -1 where that
+// margin is not at least 2^-40 (no clearance; NaN inputs included).
+__device__ __forceinline__ float clear_margin(float f, float qs) {
+  const float r = __fsub_rd(__fmul_rd(__fsqrt_rd(-qs), 1.f - 0x1p-20f), fabsf(f));
+  return r >= 0x1p-40f ? r : -1.f;
+}
+
+// The screen's q-term of a monitored branch in one period, qmax2 - s_ctg^2 in FP32; the FP64 path adds
+// the part of its margin that covers the roundings of that difference (the part that covers F is
+// added per period in the screen).
+template <typename Real>
+__device__ __forceinline__ float ctg_qs(Real q2, Real s2) {
+  if constexpr (sizeof(Real) == 8) return (float)((q2 - s2) + 0x1p-22 * (fabs(q2 - s2) + s2));
+  else return (float)(q2 - s2);
+}
+
+// Bound test of one thread's 4 rows over a chunk: Lmax fc < r for each row, with Lmax the rows' largest
+// |L| over the thread's 16-outage group, fc that group's largest |f_k| over the chunk and r the rows'
+// smallest clearance (all finite, so no NaN can arise).
+__device__ __forceinline__ bool bound_clear(float4 lm, float4 rm, float fc) {
+  float a0, a1, a2, a3;
+  unpack2(fma2(pack2(-lm.x, -lm.y), pack2(fc, fc), pack2(rm.x, rm.y)), a0, a1);
+  unpack2(fma2(pack2(-lm.z, -lm.w), pack2(fc, fc), pack2(rm.z, rm.w)), a2, a3);
+  return fminf(fmin3(a0, a1, a2), a3) > 0.f;
+}
+
+constexpr int CT_TBATCH = 12;  // tiles per batch of bound tests on the on-demand path
+
+// Clearance minima for the on-demand contingency path: for every instance that takes it, chunk
+// q = tci NCH + ch (periods [tci ctg_tb + 8 ch, +8) of period range tci) and monitored branch m, the
+// smallest clear_margin of the branch over the chunk's periods (FLT_MAX on the pad rows of the last
+// 64-row tile), from the FP32 values the stage-2 screen reads.  Once per evaluation, instead of once
+// per outage tile.
+template <typename Real, typename Dc>
+__global__ void __launch_bounds__(NTHR) k_ctg_margin(const __grid_constant__ Dev<Real, Dc> d,
+                                                     const __grid_constant__ InstTab tab) {
+  pdl_wait();
+  for (int b = 0; b < tab.n_inst; ++b) {
+    const Inst &I = tab.I[b];
+    if (!I.ctg_lazy || I.n_kt == 0) continue;
+    const int rows = I.n_mt * CT_BM, nchm = (I.ctg_tb + 7) / 8;
+    const long long n = (long long)I.ctg_ntc * nchm * rows;
+    for (long long e = blockIdx.x * (long long)NTHR + threadIdx.x; e < n; e += (long long)gridDim.x * NTHR) {
+      const int q = (int)(e / rows), m = (int)(e % rows);
+      const int tci = q / nchm, ch = q % nchm;
+      const int tb0 = tci * I.ctg_tb, TB = min(I.ctg_tb, I.T - tb0);
+      const int ta = tb0 + ch * 8, tz = tb0 + min(TB, ch * 8 + 8);
+      float r = FLT_MAX;
+      if (m < I.M) {
+        const Real s2 = d.br_s2ctg[I.br0 + m];
+        for (int t = ta; t < tz; ++t) {
+          const long long idx = I.tm0 + (long long)t * I.M + m;
+          r = fminf(r, clear_margin(d.f32[idx], ctg_qs<Real>(d.qm2[idx], s2)));
+        }
+      }
+      d.ctg_rmin[I.rm0 + e] = r;
+    }
+  }
+}
+
 // Contingency block (Sec. II-E, Eqs. rank_correct, sfr_pen-zctg) for outages [k0, k0 + 64), the
 // monitored-branch tiles of one group (64 branches each) and one chunk of periods:
 //   F[t,m,k] = f[t,m] + L[m,k] f[t,k],   s = sqrt(F^2 + qmax2[t,m]),
@@ -841,29 +909,55 @@ __host__ __device__ constexpr int ctg_tch() { return 8; }
 // only be overloaded if F^2 + qmax2 - s_ctg^2 > 0.  The FP64 path recomputes candidates exactly
 // from the FP64 block; its screen adds a margin derived from a bound on the FP32 errors, so every
 // element whose FP64 value is over the limit is a candidate (the bound is at the screen's margin
-// below).  Pads and the outaged branch itself carry
-// L = NaN, which the max ignores and every compare rejects.  Only warps with a candidate take
-// the exact path and write partial sums (the buffers are zeroed per chunk of periods): row sums
-// (dz/df_m, dz/dqmax2_m) by shuffles across the 16 column quads, flushed to the partials pm, pq
-// per outage tile; column sums (dz/df_k through L[m,k]) across the block's row quads through
-// shared memory, accumulated over the group's tiles and written to pk per group.  The soft-ReLU
-// floor eps of every non-violating element is added in closed form by the final reduction.
-template <typename Real, typename Dc>
+// below).  Pads and the outaged branch itself carry L = NaN, which the max ignores and every
+// compare rejects.
+//
+// Bound test (I.ctg_bound): before that screen, each warp bounds its 8 rows x 64 outages over a
+// chunk of 8 periods at once.  With Lmax the largest |L| of a row over the 16 outages of a thread's
+// column group (Dev::lmax, static), fc the largest |f_k| of that group over the chunk and r the
+// smallest clearance of the row over the chunk (clear_margin), Lmax fc < r implies, for every
+// element, |F32| <= (|L||f_k| + |f_m|)(1 + 2^-24) < sqrt(s_ctg^2 - qmax2) (1 - 2^-20)(1 + 2^-24),
+// so the screen's value F32^2 + qmax2 - s_ctg^2 is negative by at least 2^-19 (s_ctg^2 - qmax2)
+// (1 - 2^-23): no element is a candidate on either path (the FP64 path's margin adds at most
+// 2^-21 (1 + 2^-20) of that), and the warp skips the chunk.  The classification, and so every
+// result, is bitwise that of the element screen alone.  The eager path stages each tile's rows
+// (flows, q-terms and their clearances), loads every warp's piece of the line-outage tile and tests
+// per chunk.  The on-demand path (large plans) takes the clearances per chunk from k_ctg_margin
+// (computed once per evaluation rather than once per outage tile), tests every (tile, chunk) of a
+// batch of up to CT_TBATCH tiles at once, and stages, loads and screens only the tiles and chunks
+// where some warp of the block fails; a warp loads its piece of a tile only if it fails there.
+//
+// Only warps with a candidate take the exact path and write partial sums (the buffers are zeroed
+// per chunk of periods): row sums (dz/df_m, dz/dqmax2_m) by shuffles across the 16 column quads,
+// flushed to the partials pm, pq per outage tile; column sums (dz/df_k through L[m,k]) across the
+// block's row quads through shared memory, accumulated over the group's tiles and written to pk per
+// group; a chunk in which no warp of the block had a candidate skips the flush.  The soft-ReLU
+// floor eps of every non-violating element is added in closed form by the final reduction.  LAZY:
+// the on-demand path (Inst::ctg_lazy, the same for every instance of a plan), compiled apart so that
+// the eager path keeps its registers.
+template <typename Real, typename Dc, bool LAZY>
 __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> &acc, const HP<Real> hp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
+  static_assert(NTHR == 4 * CT_BM && CT_BM == CT_BK, "staging maps a thread to one row and every fourth chunk");
   const int T = I.T, TBM = I.ctg_tb;
+  const int NCHM = (TBM + TCH - 1) / TCH;  // chunks of the longest period range
   // the period chunks of one (group, outage tile) are adjacent blocks: they run together and read
   // the same line-outage rows, the later ones from L2
   const int tci = sub % I.ctg_ntc, rem = sub / I.ctg_ntc, mg = rem / I.n_kt, kt = rem % I.n_kt;
-  const int t0 = tci * TBM, TB = min(TBM, T - t0);
+  const int t0 = tci * TBM, TB = min(TBM, T - t0), nch = (TB + TCH - 1) / TCH;
   const int k0 = kt * CT_BK;
   const int mt0 = mg * I.ctg_mg, mt1 = min(I.n_mt, mt0 + I.ctg_mg);
   float *s_fm = reinterpret_cast<float *>(smem_raw);  // [TB][BM] base flow of the monitored branch
   float *s_qs = s_fm + TBM * CT_BM;                   // [TB][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
   float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK][2] base flow of the outaged branch, twice
-  Real *s_s2 = reinterpret_cast<Real *>(s_fk + 2 * TBM * CT_BK);  // [2][BM] s_ctg^2, then s_ctg
+  float *s_rmin = s_fk + 2 * TBM * CT_BK;             // [NCH][BM] smallest clearance of the row over the chunk
+  float *s_fkc = s_rmin + NCHM * CT_BM;               // [NCH][4] largest |f_k| of a 16-outage group over the chunk
+  constexpr bool lazy = LAZY;
+  float *s_lmb = s_fkc + 4 * NCHM;                    // on-demand path: [TBATCH][4][BM] Lmax of the batch's tiles
+  float *s_rmb = s_lmb + (lazy ? CT_TBATCH * 4 * CT_BM : 0);  // on-demand path: [TBATCH][NCH][BM] clearance minima
+  Real *s_s2 = reinterpret_cast<Real *>(s_rmb + (lazy ? CT_TBATCH * NCHM * CT_BM : 0));  // [2][BM] s_ctg^2, then s_ctg
   Real *s_gm = s_s2 + 2 * CT_BM;                      // [TCH][BM]
   Real *s_gq = s_gm + TCH * CT_BM;                    // [TCH][BM]
   Real *s_gk = s_gq + TCH * CT_BM;                    // [TCH][8][BK]
@@ -872,72 +966,35 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   Real *s_f64k = s_f64m + (F64 ? TBM * CT_BM : 0);    // [TB][BK] (FP64 path only)
   Real *s_gz = s_f64k + (F64 ? TBM * CT_BK : 0);      // [TCH][8][BK] score column sums (screening only)
   Real *s_za = s_gz + (d.score ? TCH * 8 * CT_BK : 0);  // [TB][BK] scores over the group (screening only)
-  Real *s_q2 = s_za + (d.score ? TBM * CT_BK : 0);    // [TB][BM] qmax2 of the monitored branch
   const bool score = d.score != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rq = threadIdx.x >> 4, cq = threadIdx.x & 15;
   const int kc = k0 + cq * 4;  // first of this thread's four outages
+  const int sc = threadIdx.x & (CT_BM - 1), sp = threadIdx.x >> 6;  // staging: row / column sc, chunks sp, sp + 4, ...
   __shared__ int s_hit[ctg_tch<Real>()];  // per period of the chunk: some row of the tile has a partial
+  __shared__ int s_cand[2];               // per chunk (alternating): some warp of the block had a candidate
+  __shared__ int s_fail[CT_TBATCH][8];    // on-demand path: per tile of the batch and warp, the chunks failing the bound test
+  __shared__ int s_anyf[CT_TBATCH];       // on-demand path: their union over the block's warps
   if (threadIdx.x < TCH) s_hit[threadIdx.x] = 0;
+  if (threadIdx.x < 2) s_cand[threadIdx.x] = 0;
   for (int e = threadIdx.x; e < TCH * CT_BM; e += NTHR) s_gm[e] = s_gq[e] = 0;
   for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gk[e] = 0;
   if (score)
     for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gz[e] = 0;
   Real obj = 0;
   const Real eps = hp.eps;
-  for (int mt = mt0; mt < mt1; ++mt) {
-    const int m0 = mt * CT_BM;
-    // the line-outage block does not depend on stage 1 (the first tile loads before waiting)
-    float L[4][4];
+  const bool bound = I.ctg_bound != 0;
+  int cpar = 0;  // chunk parity (s_cand slot)
+  // first tile: the outage columns' data (f_k twice, the FP64 copy, zeroed column sums) and the
+  // largest |f_k| per 16-outage group and chunk, for column sc over chunks sp, sp + 4, ...
+  auto stage_k = [&]() {
+    for (int ch = sp; ch < nch; ch += 4) {
+      const int k = k0 + sc;
+      float fkm = 0.f;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int m = m0 + rq * 4 + i;
-      if (m < I.M && kc < I.Kp) {
-        lodf_load4(d.lodf, I.l0 + (long long)m * I.Kp + kc, d.lodf_dtype, L[i]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) L[i][j] = f_nan();
-      }
-    }
-    f32x2 Lp[2][4];  // {L[2h][j], L[2h + 1][j]}
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) Lp[h][j] = pack2(L[2 * h][j], L[2 * h + 1][j]);
-    // staging of one 64-row tile's per-row data (the flows, q_max^2 - s_ctg^2 and q_max^2 of the
-    // monitored branches) for entry e of [TB][64]
-    auto stage_m = [&](int e) {
-      const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
-      float f = 0.f, qs = 0.f;
-      Real f64 = 0, q2 = 0;
-      if (m < I.M) {
-        const long long idx = I.tm0 + (long long)(t0 + tt) * I.M + m;
-        f = d.f32[idx];
-        q2 = d.qm2[idx];
-        const Real s2 = d.br_s2ctg[I.br0 + m];
-        // FP64 path: q2 - s2 plus the part of the screen's margin that covers the roundings of q2 - s2
-        // (the part that covers F is added per period in the screen)
-        qs = F64 ? (float)((q2 - s2) + 0x1p-22 * (fabs(q2 - s2) + s2)) : (float)(q2 - s2);
-        if (F64) f64 = d.fre[idx];
-      }
-      s_fm[tt * CT_BM + c] = f;
-      s_qs[tt * CT_BM + c] = qs;
-      s_q2[tt * CT_BM + c] = q2;
-      if (F64) s_f64m[tt * CT_BM + c] = f64;
-    };
-    const Real s2m = (threadIdx.x < CT_BM && m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
-    if (mt > mt0) __syncthreads();  // the previous tile is done with s_fm, s_qs, s_s2, s_q2
-    if (threadIdx.x < CT_BM) {
-      s_s2[threadIdx.x] = s2m;
-      s_s2[CT_BM + threadIdx.x] = dsqrt(s2m);
-    }
-    if (mt == mt0) {
-      // first tile: the outage columns' data and the rows' data in one pass (CT_BK == CT_BM), so
-      // that both loads are in flight together
-      pdl_wait();
-#pragma unroll 4
-      for (int e = threadIdx.x; e < TB * CT_BK; e += NTHR) {
-        const int tt = e / CT_BK, c = e % CT_BK, k = k0 + c;
+      for (int j = 0; j < TCH; ++j) {
+        const int tt = ch * TCH + j;
+        if (tt >= TB) break;
         float f = 0.f;
         Real f64 = 0;
         if (k < I.K) {
@@ -945,188 +1002,325 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
           f = d.fk32[idx];
           if (F64) f64 = d.fk[idx];
         }
-        stage_m(e);
-        *reinterpret_cast<float2 *>(s_fk + 2 * (tt * CT_BK + c)) = make_float2(f, f);
-        if (F64) s_f64k[tt * CT_BK + c] = f64;
-        s_ga[tt * CT_BK + c] = 0;
-        if (score) s_za[tt * CT_BK + c] = 0;
+        *reinterpret_cast<float2 *>(s_fk + 2 * (tt * CT_BK + sc)) = make_float2(f, f);
+        if (F64) s_f64k[tt * CT_BK + sc] = f64;
+        s_ga[tt * CT_BK + sc] = 0;
+        if (score) s_za[tt * CT_BK + sc] = 0;
+        fkm = fmaxf(fkm, fabsf(f));  // a NaN flow is ignored: its elements are no candidates either
       }
-    } else {
-#pragma unroll 8
-      for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) stage_m(e);
-    }
-    __syncthreads();
-    // FP64 path: max_j |L[i][j]| of this thread's four columns, per row (a NaN column is ignored;
-    // a row of four NaN columns screens nothing)
-    float Lrow[4];
-    if (F64) {
+      // over the 16 outages of the group (16 consecutive lanes); finite, so that the bound test
+      // never forms 0 x infinity
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        Lrow[i] = fmaxf(fmaxf(fabsf(L[i][0]), fabsf(L[i][1])), fmaxf(fabsf(L[i][2]), fabsf(L[i][3])));
+      for (int o = 8; o > 0; o >>= 1) fkm = fmaxf(fkm, __shfl_xor_sync(0xffffffffu, fkm, o));
+      if ((sc & 15) == 0) s_fkc[ch * 4 + (sc >> 4)] = fminf(fkm, FLT_MAX);
     }
-    for (int tc0 = 0; tc0 < TB; tc0 += TCH) {
-      const int tn = min(TCH, TB - tc0);
-      for (int tt = 0; tt < tn; ++tt) {
-        const int tl = tc0 + tt;
-        const float4 fm4 = *reinterpret_cast<const float4 *>(s_fm + tl * CT_BM + rq * 4);
-        const float4 qs4 = *reinterpret_cast<const float4 *>(s_qs + tl * CT_BM + rq * 4);
-        const float4 fka = *reinterpret_cast<const float4 *>(s_fk + 2 * (tl * CT_BK + cq * 4));
-        const float4 fkb = *reinterpret_cast<const float4 *>(s_fk + 2 * (tl * CT_BK + cq * 4) + 4);
-        const float fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w};
-        float qs[4] = {qs4.x, qs4.y, qs4.z, qs4.w};
-        const f32x2 fkd[4] = {pack2(fka.x, fka.y), pack2(fka.z, fka.w), pack2(fkb.x, fkb.y), pack2(fkb.z, fkb.w)};
-        if (F64) {
-          // the rest of the screen's margin: the FP32 value of F = f_m + L f_k is off by at most
-          // 3.0001 u (|f_m| + |L||f_k|) (u = 2^-24; three roundings: L, f_k, f_m to FP32 and the fma),
-          // so |F32^2 - F^2| <= 6.0003 u A^2 with A <= Ahat = |f_m| + max|L| max|f_k| over the
-          // thread's columns; 2^-21 Ahat^2 = 8 u Ahat^2 covers it and the FP64 rounding of the exact test
-          const float fkq = fmaxf(fmaxf(fabsf(fka.x), fabsf(fka.z)), fmaxf(fabsf(fkb.x), fabsf(fkb.z)));
+  };
+  const int rows = I.n_mt * CT_BM;
+  // tiles in batches: on the on-demand path, the bound tests of a batch of up to CT_TBATCH tiles come
+  // first; the eager path takes all of the group's tiles as one batch and tests per chunk
+  for (int mb = mt0; mb < mt1; mb += lazy ? CT_TBATCH : max(1, mt1 - mt0)) {
+    const int me = lazy ? min(mt1, mb + CT_TBATCH) : mt1;
+    if (lazy) {
+      // the batch's test inputs: Lmax (static, before the wait) and the clearance minima of
+      // k_ctg_margin
+      for (int e = threadIdx.x; e < (me - mb) * 4 * CT_BM; e += NTHR) {
+        const int bt = e / (4 * CT_BM), g = (e / CT_BM) & 3, r = e % CT_BM;
+        s_lmb[e] = d.lmax[I.lm0 + (long long)(kt * 4 + g) * rows + (mb + bt) * CT_BM + r];
+      }
+      if (threadIdx.x < CT_TBATCH) s_anyf[threadIdx.x] = 0;
+      if (mb == mt0) {
+        pdl_wait();
+        stage_k();
+      }
+      for (int e = threadIdx.x; e < (me - mb) * nch * CT_BM; e += NTHR) {
+        const int bt = e / (nch * CT_BM), ch = (e / CT_BM) % nch, r = e % CT_BM;
+        s_rmb[(bt * NCHM + ch) * CT_BM + r] = d.ctg_rmin[I.rm0 + (long long)(tci * NCHM + ch) * rows + (mb + bt) * CT_BM + r];
+      }
+      __syncthreads();
+      // per tile of the batch and warp: the chunks whose bound test fails
+      for (int bt = 0; bt < me - mb; ++bt) {
+        const float4 lm = *reinterpret_cast<const float4 *>(s_lmb + (bt * 4 + (cq >> 2)) * CT_BM + rq * 4);
+        int fail = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+          const float4 rm = *reinterpret_cast<const float4 *>(s_rmb + (bt * NCHM + ch) * CT_BM + rq * 4);
+          if (!__all_sync(0xffffffffu, bound_clear(lm, rm, s_fkc[ch * 4 + (cq >> 2)]))) fail |= 1 << ch;
+        }
+        if (lane == 0) {
+          s_fail[bt][wid] = fail;
+          if (fail) atomicOr(&s_anyf[bt], fail);  // an OR: the same in any order
+        }
+      }
+      __syncthreads();
+    }
+    for (int mt = mb; mt < me; ++mt) {
+      const int m0 = mt * CT_BM;
+      // on-demand path: chunks where this warp / some warp of the block must screen (s_fail, s_anyf)
+      const int bt = mt - mb;
+      if (lazy && !s_anyf[bt]) {  // every warp passes every chunk: no partial of this tile, zero flags
+        if (threadIdx.x < TB) d.pmf[I.pf0 + ((long long)kt * T + t0 + threadIdx.x) * I.n_mt + mt] = 0;
+        continue;
+      }
+      // this thread's piece of the line-outage tile, as row pairs (FP64 path: the largest |L| of each
+      // row over its four columns; a NaN column is ignored); static data, loaded before any wait
+      f32x2 Lp[2][4];  // {L[2h][j], L[2h + 1][j]}
+      float Lrow[4];
+      auto load_L = [&]() {
+        float L[4][4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float ah = __fmaf_rn(Lrow[i], fkq, fabsf(fm[i]));
-            qs[i] = __fadd_rn(qs[i], __fmul_rn(__fmul_rn(ah, ah), 0x1p-21f));
+        for (int i = 0; i < 4; ++i) {
+          const int m = m0 + rq * 4 + i;
+          if (m < I.M && kc < I.Kp) {
+            lodf_load4(d.lodf, I.l0 + (long long)m * I.Kp + kc, d.lodf_dtype, L[i]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) L[i][j] = f_nan();
           }
         }
-        const f32x2 fmp[2] = {pack2(fm[0], fm[1]), pack2(fm[2], fm[3])};
-        const f32x2 qsp[2] = {pack2(qs[0], qs[1]), pack2(qs[2], qs[3])};
-        // F = fma(L, f_k, f_m), y = fma(F, F, qmax2 - s_ctg^2): two paired FMAs per two rows
-        float F[4][4], y[4][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const f32x2 Fh = fma2(Lp[h][j], fkd[j], fmp[h]);
-            unpack2(Fh, F[2 * h][j], F[2 * h + 1][j]);
-            unpack2(fma2(Fh, Fh, qsp[h]), y[2 * h][j], y[2 * h + 1][j]);
+          for (int j = 0; j < 4; ++j) Lp[h][j] = pack2(L[2 * h][j], L[2 * h + 1][j]);
+        if (F64) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            Lrow[i] = fmaxf(fmaxf(fabsf(L[i][0]), fabsf(L[i][1])), fmaxf(fabsf(L[i][2]), fabsf(L[i][3])));
+        }
+      };
+      bool have_L = false;
+      if (!lazy) {
+        load_L();
+        have_L = true;
+      } else if (s_fail[bt][wid]) {  // the failing warps' loads overlap the staging below
+        load_L();
+        have_L = true;
+      }
+      const Real s2m = (threadIdx.x < CT_BM && m0 + threadIdx.x < I.M) ? d.br_s2ctg[I.br0 + m0 + threadIdx.x] : Real(0);
+      if (threadIdx.x < CT_BM) {
+        s_s2[threadIdx.x] = s2m;
+        s_s2[CT_BM + threadIdx.x] = dsqrt(s2m);
+      }
+      if (!lazy && mt == mt0) {
+        pdl_wait();
+        stage_k();
+      }
+      // the rows' data: flows, q_max^2 - s_ctg^2 and the FP64 flows for row sc over chunks sp, sp + 4,
+      // ..., and on the eager path the smallest clearance per chunk (FLT_MAX on pad rows: they never
+      // fail the test)
+      for (int ch = sp; ch < nch; ch += 4) {
+        const int m = m0 + sc;
+        const Real s2 = m < I.M ? d.br_s2ctg[I.br0 + m] : Real(0);
+        float rmin = FLT_MAX;
+#pragma unroll
+        for (int j = 0; j < TCH; ++j) {
+          const int tt = ch * TCH + j;
+          if (tt >= TB) break;
+          float f = 0.f, qs = 0.f;
+          Real f64 = 0;
+          if (m < I.M) {
+            const long long idx = I.tm0 + (long long)(t0 + tt) * I.M + m;
+            f = d.f32[idx];
+            qs = ctg_qs<Real>(d.qm2[idx], s2);
+            if (F64) f64 = d.fre[idx];
+            if (!lazy) rmin = fminf(rmin, clear_margin(f, qs));
           }
-        // the largest of the 16 (NaN operands are ignored), as a three-input max tree of depth 3
-        const float a0 = fmax3(y[0][0], y[0][1], y[0][2]), a1 = fmax3(y[0][3], y[1][0], y[1][1]);
-        const float a2 = fmax3(y[1][2], y[1][3], y[2][0]), a3 = fmax3(y[2][1], y[2][2], y[2][3]);
-        const float a4 = fmax3(y[3][0], y[3][1], y[3][2]);
-        const float mx = fmaxf(fmax3(a0, a1, a2), fmax3(a3, a4, y[3][3]));
-        // a candidate: F^2 + qmax2 - s_ctg^2 > 0 (mixed path: its classification), or, on the FP64
-        // path, >= 0 with the margin (a positive exact sum cannot round to a negative one)
-        if (!__any_sync(0xffffffffu, F64 ? mx >= 0.f : mx > 0.f)) continue;
-        // a (candidate) post-contingency overload in this warp
-        const Real w = __ldg(d.dt + I.tp0 + t0 + tl) * d.c_s * hp.beta;
-        Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
-        if (F64 ? mx >= 0.f : mx > 0.f) {
+          s_fm[tt * CT_BM + sc] = f;
+          s_qs[tt * CT_BM + sc] = qs;
+          if (F64) s_f64m[tt * CT_BM + sc] = f64;
+        }
+        if (!lazy) s_rmin[ch * CT_BM + sc] = rmin;
+      }
+      __syncthreads();
+      for (int tc0 = 0, ch = 0; tc0 < TB; tc0 += TCH, ++ch, cpar ^= 1) {
+        const int tn = min(TCH, TB - tc0);
+        bool skip = false;
+        if (lazy) {
+          if (!((s_anyf[bt] >> ch) & 1)) {  // no warp screens this chunk (block-uniform): zero flags only
+            if (threadIdx.x < tn) d.pmf[I.pf0 + ((long long)kt * T + t0 + tc0 + threadIdx.x) * I.n_mt + mt] = 0;
+            continue;
+          }
+          skip = !((s_fail[bt][wid] >> ch) & 1);
+        } else if (bound) {
+          // bound test of the warp's 8 rows x 64 outages over the chunk; Lmax of this thread's rows over
+          // its column group (static) is reread per chunk from L1, so that no register holds it
+          // through the screen
+          const float4 lm = __ldg(reinterpret_cast<const float4 *>(d.lmax + I.lm0 + (long long)(kt * 4 + (cq >> 2)) * rows +
+                                                                  m0 + rq * 4));
+          const float4 rm = *reinterpret_cast<const float4 *>(s_rmin + ch * CT_BM + rq * 4);
+          skip = __all_sync(0xffffffffu, bound_clear(lm, rm, s_fkc[ch * 4 + (cq >> 2)]));
+        }
+        if (!skip && !have_L) {
+          load_L();
+          have_L = true;
+        }
+        for (int tt = 0; tt < tn && !skip; ++tt) {
+          const int tl = tc0 + tt;
+          const float4 fm4 = *reinterpret_cast<const float4 *>(s_fm + tl * CT_BM + rq * 4);
+          const float4 qs4 = *reinterpret_cast<const float4 *>(s_qs + tl * CT_BM + rq * 4);
+          const float4 fka = *reinterpret_cast<const float4 *>(s_fk + 2 * (tl * CT_BK + cq * 4));
+          const float4 fkb = *reinterpret_cast<const float4 *>(s_fk + 2 * (tl * CT_BK + cq * 4) + 4);
+          const float fm[4] = {fm4.x, fm4.y, fm4.z, fm4.w};
+          float qs[4] = {qs4.x, qs4.y, qs4.z, qs4.w};
+          const f32x2 fkd[4] = {pack2(fka.x, fka.y), pack2(fka.z, fka.w), pack2(fkb.x, fkb.y), pack2(fkb.z, fkb.w)};
+          if (F64) {
+            // the rest of the screen's margin: the FP32 value of F = f_m + L f_k is off by at most
+            // 3.0001 u (|f_m| + |L||f_k|) (u = 2^-24; three roundings: L, f_k, f_m to FP32 and the fma),
+            // so |F32^2 - F^2| <= 6.0003 u A^2 with A <= Ahat = |f_m| + max|L| max|f_k| over the
+            // thread's columns; 2^-21 Ahat^2 = 8 u Ahat^2 covers it and the FP64 rounding of the exact test
+            const float fkq = fmaxf(fmaxf(fabsf(fka.x), fabsf(fka.z)), fmaxf(fabsf(fkb.x), fabsf(fkb.z)));
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int mm = rq * 4 + i;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (!(F64 ? y[i][j] >= 0.f : y[i][j] > 0.f)) continue;  // NaN (pad, outaged branch) fails too
-              const Real q2 = s_q2[tl * CT_BM + mm];
-              Real Fx, Lx, sv, dd;
-              if (F64) {
-                Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.Kp + kc + j];
-                Fx = s_f64m[tl * CT_BM + mm] + Lx * s_f64k[tl * CT_BK + cq * 4 + j];
-                if (Fx * Fx + q2 - s_s2[mm] <= Real(0)) continue;
-                sv = dsqrt(Fx * Fx + q2);
-                Real val, der;
-                soft_relu(sv - s_s2[CT_BM + mm], eps, val, der);
-                obj += w * (val - eps);
-                zc[j] += w * (val - eps);
-                dd = w * der / sv;  // dz/dF = w sigma' F / s
-              } else {
-                // mixed path: s = sqrt(F^2 + qmax2) and the soft-ReLU through reciprocal square
-                // roots (a few units in the last place, below the FP32 error of F itself)
-                float l0, l1;
-                unpack2(Lp[i >> 1][j], l0, l1);
-                Lx = (i & 1) ? l1 : l0;
-                Fx = F[i][j];
-                const float a2 = __fmaf_rn(F[i][j], F[i][j], (float)q2);
-                const float ra = rsqrtf(a2);
-                const float u = fmaxf(__fmaf_rn(a2, ra, -(float)s_s2[CT_BM + mm]), 0.f);
-                const float b2 = __fmaf_rn(u, u, (float)(eps * eps));
-                const float rb = rsqrtf(b2);
-                const float val = b2 * rb;  // sqrt(u^2 + eps^2)
-                obj += w * (val - eps);
-                zc[j] += w * (val - eps);
-                dd = w * (u * rb) * ra;  // w sigma'(s - s_ctg) / s
-              }
-              gm[i] += dd * Fx;
-              gk[j] += dd * Fx * Lx;
-              gq[i] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
+            for (int i = 0; i < 4; ++i) {
+              const float ah = __fmaf_rn(Lrow[i], fkq, fabsf(fm[i]));
+              qs[i] = __fadd_rn(qs[i], __fmul_rn(__fmul_rn(ah, ah), 0x1p-21f));
             }
           }
-        }
-        // row sums across the 16 column quads of each half-warp, when some row of this warp has an
-        // overload (the buffers hold zeros otherwise): a reduce-scatter of the thread's 8 values
-        // (gm, gq of its 4 rows); each exchange halves what a lane holds, so after three of them
-        // lane pair (2v, 2v + 1) of the half-warp holds value v, and a fourth completes its sum
-        if (__any_sync(0xffffffffu, (gq[0] != Real(0)) | (gq[1] != Real(0)) | (gq[2] != Real(0)) | (gq[3] != Real(0)))) {
-          const bool h8 = cq & 8, h4 = cq & 4, h2 = cq & 2;
-          Real r4[4], r2[2];
+          const f32x2 fmp[2] = {pack2(fm[0], fm[1]), pack2(fm[2], fm[3])};
+          const f32x2 qsp[2] = {pack2(qs[0], qs[1]), pack2(qs[2], qs[3])};
+          // F = fma(L, f_k, f_m), y = fma(F, F, qmax2 - s_ctg^2): two paired FMAs per two rows
+          float F[4][4], y[4][4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {  // values 0-3: gm, 4-7: gq; lanes with bit 3 keep 4-7
-            const Real lo = gm[q], hi = gq[q];
-            r4[q] = (h8 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h8 ? lo : hi, 8);
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const f32x2 Fh = fma2(Lp[h][j], fkd[j], fmp[h]);
+              unpack2(Fh, F[2 * h][j], F[2 * h + 1][j]);
+              unpack2(fma2(Fh, Fh, qsp[h]), y[2 * h][j], y[2 * h + 1][j]);
+            }
+          // the largest of the 16 (NaN operands are ignored), as a three-input max tree of depth 3
+          const float a0 = fmax3(y[0][0], y[0][1], y[0][2]), a1 = fmax3(y[0][3], y[1][0], y[1][1]);
+          const float a2 = fmax3(y[1][2], y[1][3], y[2][0]), a3 = fmax3(y[2][1], y[2][2], y[2][3]);
+          const float a4 = fmax3(y[3][0], y[3][1], y[3][2]);
+          const float mx = fmaxf(fmax3(a0, a1, a2), fmax3(a3, a4, y[3][3]));
+          // a candidate: F^2 + qmax2 - s_ctg^2 > 0 (mixed path: its classification), or, on the FP64
+          // path, >= 0 with the margin (a positive exact sum cannot round to a negative one)
+          if (!__any_sync(0xffffffffu, F64 ? mx >= 0.f : mx > 0.f)) continue;
+          // a (candidate) post-contingency overload in this warp
+          if (lane == 0) s_cand[cpar] = 1;
+          const Real w = __ldg(d.dt + I.tp0 + t0 + tl) * d.c_s * hp.beta;
+          Real gm[4] = {0, 0, 0, 0}, gq[4] = {0, 0, 0, 0}, gk[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
+          if (F64 ? mx >= 0.f : mx > 0.f) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int mm = rq * 4 + i;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                if (!(F64 ? y[i][j] >= 0.f : y[i][j] > 0.f)) continue;  // NaN (pad, outaged branch) fails too
+                const Real q2 = d.qm2[I.tm0 + (long long)(t0 + tl) * I.M + m0 + mm];
+                Real Fx, Lx, sv, dd;
+                if (F64) {
+                  Lx = (Real)d.lodf64[I.l0 + (long long)(m0 + mm) * I.Kp + kc + j];
+                  Fx = s_f64m[tl * CT_BM + mm] + Lx * s_f64k[tl * CT_BK + cq * 4 + j];
+                  if (Fx * Fx + q2 - s_s2[mm] <= Real(0)) continue;
+                  sv = dsqrt(Fx * Fx + q2);
+                  Real val, der;
+                  soft_relu(sv - s_s2[CT_BM + mm], eps, val, der);
+                  obj += w * (val - eps);
+                  zc[j] += w * (val - eps);
+                  dd = w * der / sv;  // dz/dF = w sigma' F / s
+                } else {
+                  // mixed path: s = sqrt(F^2 + qmax2) and the soft-ReLU through reciprocal square
+                  // roots (a few units in the last place, below the FP32 error of F itself)
+                  float l0, l1;
+                  unpack2(Lp[i >> 1][j], l0, l1);
+                  Lx = (i & 1) ? l1 : l0;
+                  Fx = F[i][j];
+                  const float a2 = __fmaf_rn(F[i][j], F[i][j], (float)q2);
+                  const float ra = rsqrtf(a2);
+                  const float u = fmaxf(__fmaf_rn(a2, ra, -(float)s_s2[CT_BM + mm]), 0.f);
+                  const float b2 = __fmaf_rn(u, u, (float)(eps * eps));
+                  const float rb = rsqrtf(b2);
+                  const float val = b2 * rb;  // sqrt(u^2 + eps^2)
+                  obj += w * (val - eps);
+                  zc[j] += w * (val - eps);
+                  dd = w * (u * rb) * ra;  // w sigma'(s - s_ctg) / s
+                }
+                gm[i] += dd * Fx;
+                gk[j] += dd * Fx * Lx;
+                gq[i] += Real(0.5) * dd;     // dz/dqmax2 = w sigma' / (2 s)
+              }
+            }
           }
+          // row sums across the 16 column quads of each half-warp, when some row of this warp has an
+          // overload (the buffers hold zeros otherwise): a reduce-scatter of the thread's 8 values
+          // (gm, gq of its 4 rows); each exchange halves what a lane holds, so after three of them
+          // lane pair (2v, 2v + 1) of the half-warp holds value v, and a fourth completes its sum
+          if (__any_sync(0xffffffffu, (gq[0] != Real(0)) | (gq[1] != Real(0)) | (gq[2] != Real(0)) | (gq[3] != Real(0)))) {
+            const bool h8 = cq & 8, h4 = cq & 4, h2 = cq & 2;
+            Real r4[4], r2[2];
 #pragma unroll
-          for (int q = 0; q < 2; ++q)  // bit 2 keeps entries 2-3 of the four
-            r2[q] = (h4 ? r4[q + 2] : r4[q]) + __shfl_xor_sync(0xffffffffu, h4 ? r4[q] : r4[q + 2], 4);
-          Real r1 = (h2 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? r2[0] : r2[1], 2);
-          r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
-          if (!(cq & 1)) {  // value v = 4 h8 + 2 h4 + h2: row v & 3 of gm (v < 4) or gq
-            const int v = cq >> 1;
-            ((v & 4) ? s_gq : s_gm)[tt * CT_BM + rq * 4 + (v & 3)] = r1;
+            for (int q = 0; q < 4; ++q) {  // values 0-3: gm, 4-7: gq; lanes with bit 3 keep 4-7
+              const Real lo = gm[q], hi = gq[q];
+              r4[q] = (h8 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h8 ? lo : hi, 8);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)  // bit 2 keeps entries 2-3 of the four
+              r2[q] = (h4 ? r4[q + 2] : r4[q]) + __shfl_xor_sync(0xffffffffu, h4 ? r4[q] : r4[q + 2], 4);
+            Real r1 = (h2 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? r2[0] : r2[1], 2);
+            r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+            if (!(cq & 1)) {  // value v = 4 h8 + 2 h4 + h2: row v & 3 of gm (v < 4) or gq
+              const int v = cq >> 1;
+              ((v & 4) ? s_gq : s_gm)[tt * CT_BM + rq * 4 + (v & 3)] = r1;
+            }
+            if (lane == 0) s_hit[tt] = 1;
           }
-          if (lane == 0) s_hit[tt] = 1;
-        }
-        // column sums across the two row quads of this warp, then per warp through shared memory
+          // column sums across the two row quads of this warp, then per warp through shared memory
 #pragma unroll
-        for (int j = 0; j < 4; ++j) gk[j] += __shfl_xor_sync(0xffffffffu, gk[j], 16);
-        if (lane < 16)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) s_gk[(tt * 8 + wid) * CT_BK + cq * 4 + j] = gk[j];
-        if (score) {  // per-outage scores for the screening list, the same way as the column sums
-#pragma unroll
-          for (int j = 0; j < 4; ++j) zc[j] += __shfl_xor_sync(0xffffffffu, zc[j], 16);
+          for (int j = 0; j < 4; ++j) gk[j] += __shfl_xor_sync(0xffffffffu, gk[j], 16);
           if (lane < 16)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) s_gz[(tt * 8 + wid) * CT_BK + cq * 4 + j] = zc[j];
-        }
-      }
-      __syncthreads();
-      // flush the chunk: the row partials of periods with an overload (and their flags); each
-      // entry is read and re-zeroed by the same thread
-      for (int e = threadIdx.x; e < tn * CT_BM; e += NTHR) {
-        const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
-        if (!s_hit[tt]) continue;
-        if (m < I.M) {
-          const long long q = I.pm0 + ((long long)kt * T + t0 + tc0 + tt) * I.M + m;
-          d.pm[q] = s_gm[e];
-          d.pq[q] = s_gq[e];
-        }
-        s_gm[e] = s_gq[e] = 0;
-      }
-      if (threadIdx.x < tn) d.pmf[I.pf0 + ((long long)kt * T + t0 + tc0 + threadIdx.x) * I.n_mt + mt] = (unsigned char)s_hit[threadIdx.x];
-      for (int e = threadIdx.x; e < tn * CT_BK; e += NTHR) {
-        const int tt = e / CT_BK, c = e % CT_BK;
-        Real sum = s_ga[(tc0 + tt) * CT_BK + c];
+            for (int j = 0; j < 4; ++j) s_gk[(tt * 8 + wid) * CT_BK + cq * 4 + j] = gk[j];
+          if (score) {  // per-outage scores for the screening list, the same way as the column sums
 #pragma unroll
-        for (int ww = 0; ww < 8; ++ww) {
-          Real &g = s_gk[(tt * 8 + ww) * CT_BK + c];
-          sum += g;
-          g = 0;
+            for (int j = 0; j < 4; ++j) zc[j] += __shfl_xor_sync(0xffffffffu, zc[j], 16);
+            if (lane < 16)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) s_gz[(tt * 8 + wid) * CT_BK + cq * 4 + j] = zc[j];
+          }
         }
-        s_ga[(tc0 + tt) * CT_BK + c] = sum;
-        if (score) {
-          Real zsum = s_za[(tc0 + tt) * CT_BK + c];
+        __syncthreads();
+        const long long pfq = I.pf0 + ((long long)kt * T + t0 + tc0) * I.n_mt + mt;
+        if (!s_cand[cpar]) {  // no candidate in the block: no partials, the buffers still hold zeros
+          if (threadIdx.x < tn) d.pmf[pfq + (long long)threadIdx.x * I.n_mt] = 0;
+          continue;
+        }
+        // flush the chunk: the row partials of periods with an overload (and their flags); each
+        // entry is read and re-zeroed by the same thread
+        for (int e = threadIdx.x; e < tn * CT_BM; e += NTHR) {
+          const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
+          if (!s_hit[tt]) continue;
+          if (m < I.M) {
+            const long long q = I.pm0 + ((long long)kt * T + t0 + tc0 + tt) * I.M + m;
+            d.pm[q] = s_gm[e];
+            d.pq[q] = s_gq[e];
+          }
+          s_gm[e] = s_gq[e] = 0;
+        }
+        if (threadIdx.x < tn) d.pmf[pfq + (long long)threadIdx.x * I.n_mt] = (unsigned char)s_hit[threadIdx.x];
+        for (int e = threadIdx.x; e < tn * CT_BK; e += NTHR) {
+          const int tt = e / CT_BK, c = e % CT_BK;
+          Real sum = s_ga[(tc0 + tt) * CT_BK + c];
 #pragma unroll
           for (int ww = 0; ww < 8; ++ww) {
-            Real &zz = s_gz[(tt * 8 + ww) * CT_BK + c];
-            zsum += zz;
-            zz = 0;
+            Real &g = s_gk[(tt * 8 + ww) * CT_BK + c];
+            sum += g;
+            g = 0;
           }
-          s_za[(tc0 + tt) * CT_BK + c] = zsum;
+          s_ga[(tc0 + tt) * CT_BK + c] = sum;
+          if (score) {
+            Real zsum = s_za[(tc0 + tt) * CT_BK + c];
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) {
+              Real &zz = s_gz[(tt * 8 + ww) * CT_BK + c];
+              zsum += zz;
+              zz = 0;
+            }
+            s_za[(tc0 + tt) * CT_BK + c] = zsum;
+          }
         }
+        __syncthreads();
+        if (threadIdx.x < TCH) s_hit[threadIdx.x] = 0;
+        if (threadIdx.x == 0) s_cand[cpar] = 0;
+        __syncthreads();
       }
-      __syncthreads();
-      if (threadIdx.x < TCH) s_hit[threadIdx.x] = 0;
-      __syncthreads();
     }
   }
   for (int e = threadIdx.x; e < TB * CT_BK; e += NTHR) {
@@ -1140,7 +1334,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   acc.v[0] = DcOps<Dc>::from_real(obj);
 }
 
-template <typename Real, typename Dc>
+template <typename Real, typename Dc, bool LAZY>
 __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x, int slot0) {
@@ -1153,7 +1347,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
     s2_bus(d, I, w.t, w.sub, x, acc, hparams(d));  // waits after its static loads
   } else {
     acc.id[0] = T_ZCTG;
-    s2_ctg(d, I, w.sub, acc, hparams(d));
+    s2_ctg<Real, Dc, LAZY>(d, I, w.sub, acc, hparams(d));
   }
   write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
 }
@@ -2255,14 +2449,15 @@ __global__ void __launch_bounds__(NTHR) k_sp_back(const __grid_constant__ Dev<Re
 // ---------------------------------------------------------------------------------------------
 
 template <typename Real>
-size_t ctg_smem_bytes(int TB, bool score) {
+size_t ctg_smem_bytes(int TB, bool score, bool lazy) {
   constexpr bool F64 = sizeof(Real) == 8;
   constexpr int TCH = ctg_tch<Real>();
-  return sizeof(float) * (size_t)TB * (2 * CT_BM + 2 * CT_BK) +
-         sizeof(Real) * ((size_t)TB * CT_BK + CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
+  const size_t nch = (TB + TCH - 1) / TCH;
+  return sizeof(float) * ((size_t)TB * (2 * CT_BM + 2 * CT_BK) + nch * (CT_BM + 4) +
+                          (lazy ? (size_t)CT_TBATCH * (4 + nch) * CT_BM : 0)) +
+         sizeof(Real) * ((size_t)TB * CT_BK + 2 * CT_BM + (size_t)TCH * (2 * CT_BM + 8 * CT_BK) +
                          (F64 ? (size_t)TB * (CT_BM + CT_BK) : 0) +
-                         (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0) +
-                         (size_t)TB * CT_BM + CT_BM);
+                         (score ? (size_t)TCH * 8 * CT_BK + (size_t)TB * CT_BK : 0));
 }
 
 // Record a timing event on s; inside stream capture it becomes an external event node.
@@ -2343,8 +2538,12 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
   mark(ev, 1, s);
   nvtxRangePop();
   nvtxRangePushA("qg stage 2 (contingencies)");
-  if (P.s2.n_blocks > 0)  // no contingencies: nothing for stage 2
-    go(k_s2<Real, Dc>, P.s2.n_blocks, ctg_smem_bytes<Real>(P.maxTB, d.score != 0), d, P.tab, P.s2, (const Real *)x, o2);
+  if (P.s2.n_blocks > 0) {  // no contingencies: nothing for stage 2
+    if (P.ctg_lazy) go(k_ctg_margin<Real, Dc>, 152 * 4, 0, d, P.tab);
+    const size_t sm2 = ctg_smem_bytes<Real>(P.maxTB, d.score != 0, P.ctg_lazy != 0);
+    if (P.ctg_lazy) go(k_s2<Real, Dc, true>, P.s2.n_blocks, sm2, d, P.tab, P.s2, (const Real *)x, o2);
+    else go(k_s2<Real, Dc, false>, P.s2.n_blocks, sm2, d, P.tab, P.s2, (const Real *)x, o2);
+  }
   mark(ev, 2, s);
   nvtxRangePop();
   nvtxRangePushA("qg stage 3");
@@ -2386,18 +2585,48 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
 // The contingency kernel's dynamic shared-memory limit is a process-wide function attribute: it is
 // only ever raised, so that creating a handle with smaller blocks never breaks an existing one.
 template <typename Real, typename Dc>
-cudaError_t prepare_eval(int maxTB, bool score) {
+cudaError_t prepare_eval(int maxTB, bool score, bool lazy) {
   static std::mutex mu;
-  static size_t cur = 0;
-  const size_t sm = std::max(ctg_smem_bytes<Real>(maxTB, score), ctg_smem_bytes<Real>(maxTB, false));
+  static size_t cur[2] = {0, 0};  // per instantiation (eager, on-demand)
+  const size_t sm = ctg_smem_bytes<Real>(maxTB, score, lazy);
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lock(mu);
-  if (sm <= cur) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_s2<Real, Dc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e == cudaSuccess) cur = sm;
+  if (sm <= cur[lazy]) return cudaSuccess;
+  const cudaError_t e = lazy ? cudaFuncSetAttribute(k_s2<Real, Dc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                             : cudaFuncSetAttribute(k_s2<Real, Dc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) cur[lazy] = sm;
   return e;
 }
 
+// Row maxima for the bound test of the contingency screen: lmax[g][m] = max |L[m, k]| over the 16
+// outage columns k of group g, read through the same decoding as the screen (NaN pads and each
+// outage's own branch ignored), capped at FLT_MAX, and 0 on the pad rows of the last 64-row tile.
+__global__ void k_lmax(const void *__restrict__ lodf, int dtype, float *__restrict__ lmax, int M, int Kp,
+                       long long l0, int rows, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(i / rows), m = (int)(i % rows);
+    float mx = 0.f;
+    if (m < M)
+      for (int q = 0; q < 4; ++q) {
+        const int k = g * 16 + q * 4;
+        if (k >= Kp) break;
+        float v[4];
+        lodf_load4(lodf, l0 + (long long)m * Kp + k, dtype, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mx = fmaxf(mx, fabsf(v[j]));
+      }
+    lmax[i] = fminf(mx, FLT_MAX);
+  }
+}
+
+cudaError_t launch_lmax(const void *lodf, int dtype, float *lmax, const Inst &I, cudaStream_t s) {
+  const int rows = I.n_mt * CT_BM;
+  const long long n = (long long)I.n_kt * 4 * rows;
+  if (n == 0) return cudaSuccess;
+  const int nb = (int)std::max(1LL, std::min((n + NTHR - 1) / NTHR, 152LL * 16));
+  k_lmax<<<nb, NTHR, 0, s>>>(lodf, dtype, lmax + I.lm0, I.M, I.Kp, I.l0, rows, n);
+  return cudaGetLastError();
+}
 
 template <typename Real>
 cudaError_t launch_adam(Real *x, Real *m, Real *v, const Real *g, const Real *lo, const Real *hi, long long n,
@@ -2524,10 +2753,10 @@ template cudaError_t launch_eval<double, double>(const Dev<double, double> &, co
                                                  bool, cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_eval<float, df32>(const Dev<float, df32> &, const Plan &, const void *, bool, bool,
                                               cudaStream_t, cudaEvent_t *);
-template cudaError_t prepare_eval<double, double>(int, bool);
+template cudaError_t prepare_eval<double, double>(int, bool, bool);
 template cudaError_t launch_finish<double, double>(const Dev<double, double> &, const Plan &, int, cudaStream_t);
 template cudaError_t launch_finish<float, df32>(const Dev<float, df32> &, const Plan &, int, cudaStream_t);
-template cudaError_t prepare_eval<float, df32>(int, bool);
+template cudaError_t prepare_eval<float, df32>(int, bool, bool);
 template cudaError_t launch_adam<double>(double *, double *, double *, const double *, const double *, const double *,
                                          long long, long long *, unsigned int *, double, double, double, double, int,
                                          cudaStream_t);

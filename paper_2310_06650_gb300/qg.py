@@ -28,6 +28,7 @@ QG_ERR_UNSUPPORTED = -8
 QG_FP64, QG_MIXED = 0, 1
 QG_LODF_F32, QG_LODF_BF16, QG_LODF_BF16X2 = 0, 1, 2
 QG_DC_AUTO, QG_DC_DENSE, QG_DC_SPARSE = 0, 1, 2
+QG_CTG_BOUND_AUTO, QG_CTG_BOUND_OFF, QG_CTG_BOUND_EAGER, QG_CTG_BOUND_LAZY = 0, 1, 2, 3
 
 TERM_NAMES = ("cost", "zp", "zq", "zs", "zrz", "zhead", "zramp", "zctg")
 
@@ -59,7 +60,7 @@ class qg_options(C.Structure):
     _fields_ = [("c_p", C.c_double), ("c_q", C.c_double), ("c_s", C.c_double), ("c_rz", C.c_double),
                 ("rho", C.c_double), ("eps", C.c_double), ("beta", C.c_double), ("adam_eps", C.c_double),
                 ("precision", C.c_int32), ("lodf_dtype", C.c_int32), ("adam_paper_eps", C.c_int32),
-                ("dc_solver", C.c_int32), ("ctg_frac", C.c_double)]
+                ("dc_solver", C.c_int32), ("ctg_frac", C.c_double), ("ctg_bound", C.c_int32)]
 
 
 def _load():
