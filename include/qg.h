@@ -156,9 +156,9 @@ typedef struct {
                         * QG_CTG_BOUND_LAZY: the tests of a batch of tiles first, from per-branch
                         * clearances computed once per evaluation (one more kernel), and tiles staged,
                         * loaded and screened only where the test fails; QG_CTG_BOUND_AUTO (0, the
-                        * default): the test, lazy where instances with M Ks >= 2^22 hold at least
-                        * half of the handle's T M Ks elements (large grids, where most of it passes),
-                        * eager otherwise.  Device memory: 1,024 ceil(M/64) ceil(Ks/64) + 256 T
+                        * default): lazy where instances with M Ks >= 2^22 hold at least half of the
+                        * handle's T M Ks elements (large grids, where most of it passes), no test
+                        * otherwise (small grids, where too little passes to pay).  Device memory: 1,024 ceil(M/64) ceil(Ks/64) + 256 T
                         * ceil(M/64) bytes per instance. */
 } qg_options;
 

@@ -629,9 +629,10 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     el_all += el;
     if (mk >= CTG_LARGE) el_large += el;
   }
+  // (on small grids the test clears too few chunks to pay for itself: no test by default)
   const int cb = h->opt.ctg_bound;
-  const int ctg_bound = cb != QG_CTG_BOUND_OFF;
   const int ctg_lazy = cb == QG_CTG_BOUND_LAZY || (cb == QG_CTG_BOUND_AUTO && el_all > 0 && 2 * el_large >= el_all);
+  const int ctg_bound = ctg_lazy || cb == QG_CTG_BOUND_EAGER;
   P.tab.s3q = small_mixed ? S3_SPLIT_MAX : 1;
   int bus0 = 0, br0 = 0, gen0 = 0, zone0 = 0, ctg0 = 0, gb0 = 0, tp0 = 0, bal0 = 0, adj0 = 0;
   for (int b = 0; b < B; ++b) {
@@ -670,7 +671,8 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     pf0 += (long long)D.n_kt * H.T * D.n_mt;
     lm0 += (long long)D.n_kt * 4 * D.n_mt * CT_BM;
     rm0 += (long long)H.T * D.n_mt * CT_BM;  // ctg_ntc ceil(ctg_tb / 8) <= T chunks, whatever the shape
-    if (D.ctg_lazy && D.n_kt > 0) P.ctg_lazy = 1;
+    P.ctg_lazy = ctg_lazy;
+    P.ctg_bound = ctg_bound;
     pm0 += (long long)D.n_kt * H.T * H.M; pk0 += (long long)D.n_mg * H.T * H.Ks; gi0 += (long long)H.T * (D.Gc + 1);
     bus0 += H.n; br0 += H.M; gen0 += H.G; zone0 += H.Z; ctg0 += H.Ks; gb0 += D.Gb; tp0 += H.T;
     bal0 += (int)H.bal_code.size(); adj0 += (int)H.adj_code.size();

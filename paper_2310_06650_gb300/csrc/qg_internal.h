@@ -242,7 +242,8 @@ struct Plan {
   long long n_x;
   int maxT;
   int maxTB;  // largest period chunk of a contingency block (sizes its shared memory)
-  int ctg_lazy;  // some instance takes the on-demand contingency path (k_ctg_margin runs before stage 2)
+  int ctg_bound;  // stage 2 runs its bound test (eager or on-demand path; the same for every instance)
+  int ctg_lazy;   // stage 2 takes the on-demand path (k_ctg_margin runs before it)
   int n_gen_slots;  // objective reduction slots of the stage-5 device blocks
   int n_fold_slots; // objective reduction slots of the stage-3 fold blocks
   // sparse DC mode (instance 0 only): grids of the solve kernels

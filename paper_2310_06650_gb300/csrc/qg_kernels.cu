@@ -932,10 +932,10 @@ __global__ void __launch_bounds__(NTHR) k_ctg_margin(const __grid_constant__ Dev
 // flushed to the partials pm, pq per outage tile; column sums (dz/df_k through L[m,k]) across the
 // block's row quads through shared memory, accumulated over the group's tiles and written to pk per
 // group; a chunk in which no warp of the block had a candidate skips the flush.  The soft-ReLU
-// floor eps of every non-violating element is added in closed form by the final reduction.  LAZY:
-// the on-demand path (Inst::ctg_lazy, the same for every instance of a plan), compiled apart so that
-// the eager path keeps its registers.
-template <typename Real, typename Dc, bool LAZY>
+// floor eps of every non-violating element is added in closed form by the final reduction.  MODE
+// (Inst::ctg_bound / ctg_lazy, the same for every instance of a plan), compiled apart so that each
+// keeps its registers: 0 no bound test, 1 the eager path, 2 the on-demand path.
+template <typename Real, typename Dc, int MODE>
 __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> &acc, const HP<Real> hp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool F64 = sizeof(Real) == 8;
@@ -954,7 +954,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK][2] base flow of the outaged branch, twice
   float *s_rmin = s_fk + 2 * TBM * CT_BK;             // [NCH][BM] smallest clearance of the row over the chunk
   float *s_fkc = s_rmin + NCHM * CT_BM;               // [NCH][4] largest |f_k| of a 16-outage group over the chunk
-  constexpr bool lazy = LAZY;
+  constexpr bool lazy = MODE == 2, bound = MODE != 0;
   float *s_lmb = s_fkc + 4 * NCHM;                    // on-demand path: [TBATCH][4][BM] Lmax of the batch's tiles
   float *s_rmb = s_lmb + (lazy ? CT_TBATCH * 4 * CT_BM : 0);  // on-demand path: [TBATCH][NCH][BM] clearance minima
   Real *s_s2 = reinterpret_cast<Real *>(s_rmb + (lazy ? CT_TBATCH * NCHM * CT_BM : 0));  // [2][BM] s_ctg^2, then s_ctg
@@ -983,10 +983,10 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
     for (int e = threadIdx.x; e < TCH * 8 * CT_BK; e += NTHR) s_gz[e] = 0;
   Real obj = 0;
   const Real eps = hp.eps;
-  const bool bound = I.ctg_bound != 0;
   int cpar = 0;  // chunk parity (s_cand slot)
   // first tile: the outage columns' data (f_k twice, the FP64 copy, zeroed column sums) and the
   // largest |f_k| per 16-outage group and chunk, for column sc over chunks sp, sp + 4, ...
+  // (with the bound test; without it the first tile's row staging below does the same per entry)
   auto stage_k = [&]() {
     for (int ch = sp; ch < nch; ch += 4) {
       const int k = k0 + sc;
@@ -1101,12 +1101,43 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
       }
       if (!lazy && mt == mt0) {
         pdl_wait();
-        stage_k();
+        if (bound) stage_k();
       }
-      // the rows' data: flows, q_max^2 - s_ctg^2 and the FP64 flows for row sc over chunks sp, sp + 4,
-      // ..., and on the eager path the smallest clearance per chunk (FLT_MAX on pad rows: they never
-      // fail the test)
-      for (int ch = sp; ch < nch; ch += 4) {
+      // the rows' data: flows, q_max^2 - s_ctg^2 and the FP64 flows; on the eager path with the bound
+      // test, for row sc over chunks sp, sp + 4, ... with the smallest clearance per chunk (FLT_MAX on
+      // pad rows: they never fail the test), else entries e = (period, row) over every thread
+      if (MODE != 1) {
+        // without the bound test the first tile also stages the outage columns' data here (CT_BK ==
+        // CT_BM), so that both loads are in flight together
+        const bool with_k = MODE == 0 && mt == mt0;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < TB * CT_BM; e += NTHR) {
+          const int tt = e / CT_BM, c = e % CT_BM, m = m0 + c;
+          float f = 0.f, qs = 0.f, fk = 0.f;
+          Real f64 = 0, fk64 = 0;
+          if (with_k && k0 + c < I.K) {
+            const long long idx = I.tk0 + (long long)(t0 + tt) * I.K + k0 + c;
+            fk = d.fk32[idx];
+            if (F64) fk64 = d.fk[idx];
+          }
+          if (m < I.M) {
+            const long long idx = I.tm0 + (long long)(t0 + tt) * I.M + m;
+            f = d.f32[idx];
+            qs = ctg_qs<Real>(d.qm2[idx], d.br_s2ctg[I.br0 + m]);
+            if (F64) f64 = d.fre[idx];
+          }
+          s_fm[tt * CT_BM + c] = f;
+          s_qs[tt * CT_BM + c] = qs;
+          if (F64) s_f64m[tt * CT_BM + c] = f64;
+          if (with_k) {
+            *reinterpret_cast<float2 *>(s_fk + 2 * (tt * CT_BK + c)) = make_float2(fk, fk);
+            if (F64) s_f64k[tt * CT_BK + c] = fk64;
+            s_ga[tt * CT_BK + c] = 0;
+            if (score) s_za[tt * CT_BK + c] = 0;
+          }
+        }
+      }
+      for (int ch = sp; MODE == 1 && ch < nch; ch += 4) {
         const int m = m0 + sc;
         const Real s2 = m < I.M ? d.br_s2ctg[I.br0 + m] : Real(0);
         float rmin = FLT_MAX;
@@ -1121,13 +1152,13 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
             f = d.f32[idx];
             qs = ctg_qs<Real>(d.qm2[idx], s2);
             if (F64) f64 = d.fre[idx];
-            if (!lazy) rmin = fminf(rmin, clear_margin(f, qs));
+            rmin = fminf(rmin, clear_margin(f, qs));
           }
           s_fm[tt * CT_BM + sc] = f;
           s_qs[tt * CT_BM + sc] = qs;
           if (F64) s_f64m[tt * CT_BM + sc] = f64;
         }
-        if (!lazy) s_rmin[ch * CT_BM + sc] = rmin;
+        s_rmin[ch * CT_BM + sc] = rmin;
       }
       __syncthreads();
       for (int tc0 = 0, ch = 0; tc0 < TB; tc0 += TCH, ++ch, cpar ^= 1) {
@@ -1334,7 +1365,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   acc.v[0] = DcOps<Dc>::from_real(obj);
 }
 
-template <typename Real, typename Dc, bool LAZY>
+template <typename Real, typename Dc, int MODE>
 __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __grid_constant__ Dev<Real, Dc> d,
                                              const __grid_constant__ InstTab tab, const __grid_constant__ Spans S,
                                              const Real *__restrict__ x, int slot0) {
@@ -1347,7 +1378,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(Real) == 4 ? 3 : 2) k_s2(const __
     s2_bus(d, I, w.t, w.sub, x, acc, hparams(d));  // waits after its static loads
   } else {
     acc.id[0] = T_ZCTG;
-    s2_ctg<Real, Dc, LAZY>(d, I, w.sub, acc, hparams(d));
+    s2_ctg<Real, Dc, MODE>(d, I, w.sub, acc, hparams(d));
   }
   write_obj(d.objp, d.slot_map[slot0 + blockIdx.x], acc);
 }
@@ -2541,8 +2572,9 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
   if (P.s2.n_blocks > 0) {  // no contingencies: nothing for stage 2
     if (P.ctg_lazy) go(k_ctg_margin<Real, Dc>, 152 * 4, 0, d, P.tab);
     const size_t sm2 = ctg_smem_bytes<Real>(P.maxTB, d.score != 0, P.ctg_lazy != 0);
-    if (P.ctg_lazy) go(k_s2<Real, Dc, true>, P.s2.n_blocks, sm2, d, P.tab, P.s2, (const Real *)x, o2);
-    else go(k_s2<Real, Dc, false>, P.s2.n_blocks, sm2, d, P.tab, P.s2, (const Real *)x, o2);
+    if (P.ctg_lazy) go(k_s2<Real, Dc, 2>, P.s2.n_blocks, sm2, d, P.tab, P.s2, (const Real *)x, o2);
+    else if (P.ctg_bound) go(k_s2<Real, Dc, 1>, P.s2.n_blocks, sm2, d, P.tab, P.s2, (const Real *)x, o2);
+    else go(k_s2<Real, Dc, 0>, P.s2.n_blocks, sm2, d, P.tab, P.s2, (const Real *)x, o2);
   }
   mark(ev, 2, s);
   nvtxRangePop();
@@ -2587,14 +2619,15 @@ cudaError_t launch_eval(const Dev<Real, Dc> &d, const Plan &P, const void *xv, b
 template <typename Real, typename Dc>
 cudaError_t prepare_eval(int maxTB, bool score, bool lazy) {
   static std::mutex mu;
-  static size_t cur[2] = {0, 0};  // per instantiation (eager, on-demand)
+  static size_t cur = 0;  // the same limit for every instantiation
   const size_t sm = ctg_smem_bytes<Real>(maxTB, score, lazy);
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lock(mu);
-  if (sm <= cur[lazy]) return cudaSuccess;
-  const cudaError_t e = lazy ? cudaFuncSetAttribute(k_s2<Real, Dc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                             : cudaFuncSetAttribute(k_s2<Real, Dc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e == cudaSuccess) cur[lazy] = sm;
+  if (sm <= cur) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_s2<Real, Dc, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_s2<Real, Dc, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_s2<Real, Dc, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) cur = sm;
   return e;
 }
 
