@@ -379,10 +379,16 @@ int qg_round_reset(qg_ctx *h);
 /* Kernel launches of one evaluation (with or without the fused Adam update) on this handle, the
  * closing kernel that sums the objective included: 4 stage kernels on the mixed path with the
  * dense DC products (stage 4 updates the devices), 5 on the FP64 path, 5 plus 3 to 7 solve kernels
- * with the sparse DC solver, one fewer without contingencies; plus 1.  qg_solve without a trace
+ * with the sparse DC solver, one fewer without contingencies, one more on the on-demand contingency
+ * path (the clearance kernel, qg_ctg_path = 2); plus 1.  qg_solve without a trace
  * runs its iterations in graphs of 8 that share one closing kernel, so there an iteration costs
  * one launch less, plus 1/8.  Returns a negative error code for a NULL handle. */
 int32_t qg_launches_per_eval(const qg_ctx *h);
+
+/* The contingency stage's path on this handle (qg_options.ctg_bound after QG_CTG_BOUND_AUTO is
+ * resolved): 0 no bound test, 1 the bound test with every tile staged and loaded (eager), 2 the
+ * on-demand path.  Returns a negative error code for a NULL handle. */
+int32_t qg_ctg_path(const qg_ctx *h);
 
 const char *qg_last_error(const qg_ctx *h);
 

@@ -2182,6 +2182,11 @@ int32_t qg_launches_per_eval(const qg_ctx *h) {
   return 4 + s2 + 3 + (P.sp_tail_blocks > 0 ? 2 : 0) + (P.sp_bw_blocks > 0 ? 1 : 0) + (P.sp_bwa_blocks > 0 ? 1 : 0) + 1;
 }
 
+int32_t qg_ctg_path(const qg_ctx *h) {
+  if (!h) return QG_ERR_INVALID_ARG;
+  return h->plan.ctg_lazy ? 2 : h->plan.ctg_bound ? 1 : 0;
+}
+
 int qg_autotune(qg_ctx *h, const void *x, int32_t reps, int32_t cold, int32_t shape[2]) {
   NvtxRange range("qg_autotune");
   if (!h) return QG_ERR_INVALID_ARG;

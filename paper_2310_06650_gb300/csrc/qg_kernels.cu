@@ -886,12 +886,19 @@ __global__ void __launch_bounds__(NTHR) k_ctg_margin(const __grid_constant__ Dev
       const int tb0 = tci * I.ctg_tb, TB = min(I.ctg_tb, I.T - tb0);
       const int ta = tb0 + ch * 8, tz = tb0 + min(TB, ch * 8 + 8);
       float r = FLT_MAX;
-      if (m < I.M) {
+      if (m < I.M && ta < tz) {
+        // the chunk's loads all in flight at once: periods past its end repeat its last one
         const Real s2 = d.br_s2ctg[I.br0 + m];
-        for (int t = ta; t < tz; ++t) {
-          const long long idx = I.tm0 + (long long)t * I.M + m;
-          r = fminf(r, clear_margin(d.f32[idx], ctg_qs<Real>(d.qm2[idx], s2)));
+        float f[8];
+        Real q2[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const long long idx = I.tm0 + (long long)min(ta + j, tz - 1) * I.M + m;
+          f[j] = d.f32[idx];
+          q2[j] = d.qm2[idx];
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) r = fminf(r, clear_margin(f[j], ctg_qs<Real>(q2[j], s2)));
       }
       d.ctg_rmin[I.rm0 + e] = r;
     }

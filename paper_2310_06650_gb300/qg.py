@@ -118,6 +118,7 @@ def _load():
         "qg_mlp_check": (C.c_int, [vp]),
         "qg_bounds_report": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
         "qg_dc_flows": (C.c_int, [vp, vp]),
+        "qg_ctg_path": (C.c_int32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -134,7 +135,7 @@ EXPORTED = ("qg_default_options", "qg_create", "qg_create_batch", "qg_destroy", 
             "qg_last_error", "qg_version",
             "qg_mlp_create", "qg_mlp_destroy", "qg_mlp_num_params", "qg_mlp_set_stream", "qg_mlp_forward",
             "qg_mlp_train_step", "qg_mlp_get_params", "qg_mlp_set_params", "qg_mlp_get_grads", "qg_mlp_last_error",
-            "qg_mlp_check", "qg_bounds_report", "qg_dc_flows")
+            "qg_mlp_check", "qg_bounds_report", "qg_dc_flows", "qg_ctg_path")
 PHASES = ("s1", "s2", "s3", "s4", "s5", "adam")
 
 
@@ -499,6 +500,13 @@ def qg_dc_flows(h: int, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.float32)
     _check(_lib.qg_dc_flows(h, out.ctypes.data_as(C.c_void_p)), h)
     return out
+
+
+def qg_ctg_path(h: int) -> int:
+    """The contingency stage's path: 0 no bound test, 1 eager bound test, 2 on-demand path."""
+    r = _lib.qg_ctg_path(h)
+    _check(min(r, 0), h)
+    return r
 
 
 def qg_bounds_report():

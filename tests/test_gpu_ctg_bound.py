@@ -135,3 +135,16 @@ def test_bound_test_solve_trajectory(qg, precision):
 def test_bound_option_is_validated(qg):
     with pytest.raises(qg.QGError):
         qg.Solver(case_named("tiny"), precision=0, ctg_bound=4)
+
+
+def test_resolved_path_and_launch_count(qg):
+    """rt617 (small grid) resolves QG_CTG_BOUND_AUTO to no bound test; the on-demand path adds the
+    clearance kernel to an evaluation's launches."""
+    c = case_named("rt617")
+    counts = {}
+    for mode, path in ((0, 0), (1, 0), (2, 1), (3, 2)):
+        s = qg.Solver(c, precision=1, ctg_bound=mode)
+        assert qg.qg_ctg_path(s.h) == path
+        counts[mode] = qg.qg_launches_per_eval(s.h)
+        s.close()
+    assert counts[0] == counts[1] == counts[2] == counts[3] - 1
