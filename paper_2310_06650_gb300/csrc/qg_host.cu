@@ -707,8 +707,18 @@ int build_plan(qg_ctx *h, std::vector<int> &slot_map, const Knobs &kn) {
     for (int b = 0; b < B; ++b) add_span(P.s1, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
   for (int b = 0; b < B; ++b) add_span(P.s1, I[b].Z, I[b].T, b, R_ZONE);
   for (int b = 0; b < B; ++b) add_span(P.s2, I[b].ctg_ntc * I[b].n_mg * I[b].n_kt, I[b].K > 0 ? 1 : 0, b, R_CTG);
-  if (!bal1)
-    for (int b = 0; b < B; ++b) add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), I[b].T, b, R_BUS);
+  if (!bal1) {
+    // a stage-2 bus-balance block is a few microseconds of work: on large plans each covers several
+    // periods, so that they stay within about four waves of the launch's blocks (they take the
+    // contingency blocks' shared memory, so an SM holds as few of them)
+    long long nbus = 0;
+    for (int b = 0; b < B; ++b) nbus += (long long)ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK) * I[b].T;
+    const int tc = (int)std::max(1LL, std::min(8LL, nbus / (4 * CTG_WAVE)));
+    for (int b = 0; b < B; ++b) {
+      I[b].bus_tc = tc;
+      add_span(P.s2, ceil_div(I[b].n_bal_pack, PACKS_PER_BLOCK), ceil_div(I[b].T, tc), b, R_BUS);
+    }
+  }
   // objective slots: the blocks of s1 and s2 in launch order, renumbered instance-major so that each
   // instance's slots are one contiguous range; then the fold slots of stage 3 (one per fold block:
   // the sum of up to NTHR stage-1/2 slots of one instance) and one slot per stage-5 device block

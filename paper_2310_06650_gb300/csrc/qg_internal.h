@@ -50,6 +50,7 @@ struct Inst {
   int n_sb;              // stage-3 branch blocks per period (NTHR / InstTab::s3q branches each)
   int s4p;               // branch-end CSR packs per warp in stage 4 (1 or S4_PACKS)
   int bal0, n_bal_pack;  // first entry / number of warp packs of the balance CSR
+  int bus_tc;            // periods per stage-2 bus-balance block (several on large plans)
   int adj0, n_adj_pack;  // same for the branch-end adjoint CSR
   long long x0;          // first variable of this instance
   long long tb0, tm0, tg0, tz0, tk0;

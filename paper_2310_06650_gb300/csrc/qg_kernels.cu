@@ -770,47 +770,60 @@ __global__ void __launch_bounds__(NTHR) k_s1(const __grid_constant__ Dev<Real, D
 // stage 2
 // ---------------------------------------------------------------------------------------------
 
-// Bus balance of the FP64 path (Example 4), in stage 2: the same sums as s1_bus from the flows that
-// stage 1 stored (recomputing them would cost the FP64 path its slow sincos a second time).
+// Bus balance (Example 4) in stage 2 (the FP64 path, and the mixed path of larger plans): the same
+// sums as s1_bus from the flows that stage 1 stored (recomputing them would cost the FP64 path its
+// slow sincos a second time).  A block covers I.bus_tc consecutive periods of its CSR packs (period
+// chunk tc), its objective partials summed over them in period order.
 template <typename Real, typename Dc>
-__device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int t, int sub, const Real *__restrict__ x,
+__device__ void s2_bus(const Dev<Real, Dc> &d, const Inst &I, int tc, int sub, const Real *__restrict__ x,
                        Obj3<Dc> &acc, const HP<Real> hp) {
   const int pk = sub * PACKS_PER_BLOCK + (threadIdx.x >> 5);
   if (pk >= I.n_bal_pack) return;  // whole warp
   const int e = I.bal0 + pk * PACK + (threadIdx.x & 31);
   const int code = d.bal_code[e], row = d.bal_row[e];
   const int kind = code & 3, id = code >> 2;
+  const int ta = tc * I.bus_tc, tz = min(I.T, ta + I.bus_tc);
   // data no earlier stage writes first (loads, weights, the device's role), then wait for stage 1
-  const long long ti = I.tb0 + (long long)t * I.n + (row >= 0 ? row : 0);
-  const Real lp = d.load_p[ti], lq = d.load_q[ti];
-  const Real dtw = d.dt[I.tp0 + t];
   const Real sg = kind == 2 ? d.gen_sgn[I.gen0 + id] : Real(1);
+  const long long ti0 = I.tb0 + (long long)ta * I.n + (row >= 0 ? row : 0);
+  Real lp = d.load_p[ti0], lq = d.load_q[ti0];
   pdl_wait();
-  Real P = 0, Q = 0;
-  const long long tm = I.tm0 + (long long)t * I.M + id;
-  if (kind == 0) {
-    P = d.pf[tm];
-    Q = d.qf[tm];
-  } else if (kind == 1) {
-    P = d.pt[tm];
-    Q = d.qt[tm];
-  } else if (kind == 2) {  // a producer supplies (-), a consumer draws (+)
-    const Real *p = x + I.x0 + 2LL * I.T * I.n + (long long)t * I.G + id;
-    P = -sg * p[0];
-    Q = -sg * p[(long long)I.T * I.G];
+  Dc zp = DcOps<Dc>::zero(), zq = DcOps<Dc>::zero();
+  for (int t = ta; t < tz; ++t) {
+    const long long ti = I.tb0 + (long long)t * I.n + (row >= 0 ? row : 0);
+    if (t > ta) {
+      lp = d.load_p[ti];
+      lq = d.load_q[ti];
+    }
+    const Real dtw = d.dt[I.tp0 + t];
+    Real P = 0, Q = 0;
+    const long long tm = I.tm0 + (long long)t * I.M + id;
+    if (kind == 0) {
+      P = d.pf[tm];
+      Q = d.qf[tm];
+    } else if (kind == 1) {
+      P = d.pt[tm];
+      Q = d.qt[tm];
+    } else if (kind == 2) {  // a producer supplies (-), a consumer draws (+)
+      const Real *p = x + I.x0 + 2LL * I.T * I.n + (long long)t * I.G + id;
+      P = -sg * p[0];
+      Q = -sg * p[(long long)I.T * I.G];
+    }
+    if (seg_sum2(row, P, Q) && row >= 0) {
+      P += lp;
+      Q += lq;
+      Real vp, dp, vq, dq;
+      soft_abs(P, hp.eps, vp, dp);
+      soft_abs(Q, hp.eps, vq, dq);
+      const Real wp = dtw * d.c_p * hp.beta, wq = dtw * d.c_q * hp.beta;
+      d.dP[ti] = wp * dp;
+      d.dQ[ti] = wq * dq;
+      zp = DcOps<Dc>::add(zp, DcOps<Dc>::from_real(wp * vp));
+      zq = DcOps<Dc>::add(zq, DcOps<Dc>::from_real(wq * vq));
+    }
   }
-  if (seg_sum2(row, P, Q) && row >= 0) {
-    P += lp;
-    Q += lq;
-    Real vp, dp, vq, dq;
-    soft_abs(P, hp.eps, vp, dp);
-    soft_abs(Q, hp.eps, vq, dq);
-    const Real wp = dtw * d.c_p * hp.beta, wq = dtw * d.c_q * hp.beta;
-    d.dP[ti] = wp * dp;
-    d.dQ[ti] = wq * dq;
-    acc.v[0] = DcOps<Dc>::from_real(wp * vp);
-    acc.v[1] = DcOps<Dc>::from_real(wq * vq);
-  }
+  acc.v[0] = zp;
+  acc.v[1] = zq;
 }
 
 // Four consecutive entries of the line-outage block (row stride padded to a multiple of 4, so
