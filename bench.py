@@ -41,10 +41,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) per launch of the dominant kernel: the mean over the launches of one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, a few launches) of the current
 # kernel code; a kernel whose code changed since its capture gets None
-NCU_TRAFFIC = {("rt617", "s2", True): 2272000.0, ("rt617", "s2", False): 3396608.0}
+NCU_TRAFFIC = {("rt617", "s2", True): 2271232.0, ("rt617", "s2", False): 3386112.0}
 # day-ahead contingency stage (on-demand path): DRAM bytes read + written per evaluation by the
 # clearance kernel and the contingency kernel, from their single-kernel ncu captures
-DAYAHEAD_S2_DRAM_BYTES = 13596672.0 + 89402880.0 + 21934080.0
+DAYAHEAD_S2_DRAM_BYTES = 13591552.0 + 89315072.0 + 22222080.0
 FP32_LANES_PER_SM, N_SM, FP64_NOMINAL_TFLOPS = 128, 152, 1.25
 
 
