@@ -972,7 +972,7 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
   float *s_fm = reinterpret_cast<float *>(smem_raw);  // [TB][BM] base flow of the monitored branch
   float *s_qs = s_fm + TBM * CT_BM;                   // [TB][BM] qmax2 - s_ctg^2 (+ margin on the FP64 path)
   float *s_fk = s_qs + TBM * CT_BM;                   // [TB][BK][2] base flow of the outaged branch, twice
-  float *s_rmin = s_fk + 2 * TBM * CT_BK;             // [NCH][BM] smallest clearance of the row over the chunk
+  float *s_rmin = s_fk + 2 * TBM * CT_BK;             // [NCH][BM] eager bound test: smallest clearance of the row over the chunk
   float *s_fkc = s_rmin + NCHM * CT_BM;               // [NCH][4] largest |f_k| of a 16-outage group over the chunk
   constexpr bool lazy = MODE == 2, bound = MODE != 0;
   float *s_lmb = s_fkc + 4 * NCHM;                    // on-demand path: [TBATCH][4][BM] Lmax of the batch's tiles
@@ -1081,7 +1081,8 @@ __device__ void s2_ctg(const Dev<Real, Dc> &d, const Inst &I, int sub, Obj3<Dc> 
         continue;
       }
       // this thread's piece of the line-outage tile, as row pairs (FP64 path: the largest |L| of each
-      // row over its four columns; a NaN column is ignored); static data, loaded before any wait
+      // row over its four columns; a NaN column is ignored); static data, which the eager paths load
+      // before any wait and the on-demand path only in failing warps
       f32x2 Lp[2][4];  // {L[2h][j], L[2h + 1][j]}
       float Lrow[4];
       auto load_L = [&]() {
