@@ -577,8 +577,8 @@ def dayahead_leg(args, peaks, src, local_rank):
                             "without screening them, so this is a coverage rate, not an operation rate",
                "dram_bytes": s2_dram, "dram_gbs": s2_dram / s2_s / 1e9, "hbm_frac": s2_dram / s2_s / 1e9 / peaks["hbm_gbs"],
                "dram_source": "dram__bytes_read.sum + dram__bytes_write.sum of the two kernels' single-kernel ncu "
-                              "captures (profiles/k_s2_dayahead.md, at the heuristic block shape of 24 periods x 9 "
-                              "tiles); the full FP32 line-outage block is 280 MB"},
+                              "captures, at the heuristic block shape of 24 periods x 9 tiles; the full FP32 "
+                              "line-outage block is 280 MB"},
         "clocks": clk.summary(),
     }
     s.close()
