@@ -59,3 +59,52 @@ def test_struct_sizes_and_offsets_match(c_layout):
         assert ctypes.sizeof(cls) == layout[(name, "size")], name
         for field, _ in cls._fields_:
             assert getattr(cls, field).offset == layout[(name, field)], (name, field)
+
+
+def _header_prototypes():
+    """{name: (return type, argument count)} of every qg_* function the header declares."""
+    import re
+    text = open(os.path.join(ROOT, "include", "qg.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(qg_\w+)\s*\(([^;{}]*?)\)\s*;", text):
+        ret, name, args = " ".join(m.group(1).split()), m.group(2), m.group(3).strip()
+        if ret.startswith("typedef"):
+            continue
+        n = 0 if args in ("", "void") else len(args.split(","))
+        out[name] = (ret, n)
+    return out
+
+
+def _binding_signatures():
+    """{name: (restype, argument count)} of the binding's ctypes table, read from qg.py's source."""
+    import ast
+    tree = ast.parse(open(os.path.join(ROOT, "paper_2310_06650_gb300", "qg.py")).read())
+    load = next(n for n in tree.body if isinstance(n, ast.FunctionDef) and n.name == "_load")
+    sig = next(s for s in load.body if isinstance(s, ast.Assign) and getattr(s.targets[0], "id", "") == "sig")
+    env = {"C": ctypes, "vp": ctypes.c_void_p, "_I32P": ctypes.POINTER(ctypes.c_int32),
+           "_F64P": ctypes.POINTER(ctypes.c_double), **_load_binding_structs()}
+    table = eval(compile(ast.Expression(sig.value), "qg.py", "eval"), env)
+    return {name: (res, len(args)) for name, (res, args) in table.items()}
+
+
+RET = {"void": None, "int": 4, "int32_t": 4, "int64_t": 8, "const char *": "str"}
+
+
+def _ret_kind(res):
+    if res is None:
+        return None
+    if res is ctypes.c_char_p:
+        return "str"
+    return ctypes.sizeof(res)
+
+
+def test_every_prototype_has_a_matching_ctypes_signature():
+    protos, sigs = _header_prototypes(), _binding_signatures()
+    assert set(protos) == set(sigs), (sorted(set(protos) - set(sigs)), sorted(set(sigs) - set(protos)))
+    for name, (ret, n) in protos.items():
+        res, m = sigs[name]
+        assert n == m, (name, n, m)
+        assert ret in RET, (name, ret)
+        assert RET[ret] == _ret_kind(res), (name, ret, res)
