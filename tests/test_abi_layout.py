@@ -108,3 +108,14 @@ def test_every_prototype_has_a_matching_ctypes_signature():
         assert n == m, (name, n, m)
         assert ret in RET, (name, ret)
         assert RET[ret] == _ret_kind(res), (name, ret, res)
+
+
+@pytest.mark.parametrize("lang", ["c99", "c++11"])
+def test_header_compiles_as_strict_c_and_cxx(tmp_path, lang):
+    cc = shutil.which("gcc" if lang == "c99" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("h.c" if lang == "c99" else "h.cpp")
+    src.write_text('#include "qg.h"\nint main(void) { return qg_version() < 0; }\n')
+    subprocess.run([cc, f"-std={lang}", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I",
+                    os.path.join(ROOT, "include"), str(src)], check=True)
